@@ -20,7 +20,8 @@ def test_shape_of_config1():
     mode = np.bincount(L).argmax()
     assert 12 <= mode <= 15
     assert set(bytes(r.chars).decode()) <= set(ALPHABET)
-    assert all(s[0] == "C" for s in r.strings()[:500])
+    # the leading C survives unless the point substitution hits position 0
+    assert sum(s[0] == "C" for s in r.strings()[:1000]) > 900
     # repeats exist (shared templates), as in real repertoires
     assert len(set(r.strings())) < r.n
 
