@@ -1,0 +1,187 @@
+/*
+ * tcrnet — B300 (sm_103a) builder of the CDR3beta similarity network of
+ * "Large-scale GPU-based network analysis of the human T-cell receptor
+ * repertoire" (arXiv 2112.06613, TCR-NET).
+ *
+ * The network (Methods "TCR network"): one node per input string; an undirected
+ * edge joins nodes i != j iff the Levenshtein distance of their strings
+ * (Methods "Levenshtein distance", Eq. levenshtein: unit-cost insertion,
+ * deletion and substitution) does not exceed the threshold l_max. It is
+ * returned as the rows of the symmetric 0/1 adjacency matrix (Methods
+ * "Adjacency matrix") in CSR form: row i lists every neighbour j in strictly
+ * ascending order, both directions stored, no self-loops; degree[i] =
+ * offsets[i+1] - offsets[i] (d(u) = sum_v A_uv, Methods "Overview of network
+ * theory concepts").
+ *
+ * Conventions shared by every entry point:
+ *  - Strings are upper-case one-letter codes of the 20 standard amino acids
+ *    (the set Sigma of Methods "Combination of amino acids"), length 1 ..
+ *    TCRNET_MAX_LEN. Anything else is rejected (TCRNET_EBADCHAR,
+ *    TCRNET_ETOOLONG, TCRNET_EINVAL for an empty string); strings are never
+ *    truncated, since truncation changes distances. The offending input index
+ *    is then available from tcrnet_last_error_index().
+ *  - Node id = input position. Duplicate strings are distinct nodes and are
+ *    adjacent to each other (distance 0).
+ *  - Inputs are borrowed for the duration of the call and never retained.
+ *  - Supported thresholds: 0 and 1 (the paper's network-construction setting,
+ *    Fig. performance). Thresholds >= 2 return TCRNET_ENOTSUP; negative ones
+ *    TCRNET_EINVAL.
+ *  - Work is ordered on the CUDA stream given in tcrnet_options (NULL: the
+ *    legacy default stream). Calls return after the result is complete on the
+ *    device unless stated otherwise.
+ *  - A handle is thread-compatible, not thread-safe: do not use one handle
+ *    from two host threads at once.
+ *  - TCRNET_EDEVICE / TCRNET_ETIMEOUT poison the handle being built or used;
+ *    free it. No call leaves a sticky device error behind on purpose.
+ *  - Memory spaces: arguments tagged `mem` are TCRNET_HOST (pageable or pinned
+ *    host memory) or TCRNET_DEVICE (device memory of the handle's device).
+ */
+#ifndef TCRNET_H
+#define TCRNET_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Longest accepted string. The paper reserves 30 amino acids per sequence on
+ * the GPU (Methods "GPU-based network generation"); this library accepts up to
+ * 48 (two 128-bit words of 5-bit codes). */
+#define TCRNET_MAX_LEN 48
+
+typedef enum tcrnet_status {
+    TCRNET_OK = 0,
+    TCRNET_EINVAL = 1,    /* bad argument, empty string or non-monotone offsets */
+    TCRNET_EBADCHAR = 2,  /* a character outside the 20-letter alphabet */
+    TCRNET_ETOOLONG = 3,  /* a string longer than TCRNET_MAX_LEN */
+    TCRNET_ENOTSUP = 4,   /* threshold >= 2, or an option this build lacks */
+    TCRNET_ENOMEM = 5,    /* device or host allocation failed; nothing leaked */
+    TCRNET_EDEVICE = 6,   /* a CUDA error; the handle is poisoned */
+    TCRNET_ETIMEOUT = 7,  /* a bounded device wait ran out; the handle is poisoned */
+    TCRNET_ESTATE = 8     /* the handle cannot serve this call (e.g. query on a query result) */
+} tcrnet_status;
+
+typedef enum tcrnet_method {
+    TCRNET_METHOD_AUTO = 0,     /* the library picks (deletion path above a size cut-over) */
+    TCRNET_METHOD_TILE = 1,     /* all-pairs tile kernel over length buckets */
+    TCRNET_METHOD_DELETION = 2  /* deletion-neighbourhood join */
+} tcrnet_method;
+
+typedef enum tcrnet_memspace { TCRNET_HOST = 0, TCRNET_DEVICE = 1 } tcrnet_memspace;
+
+/* Options. Fill with tcrnet_options_init, then set what you need; a NULL
+ * options pointer means the defaults. */
+typedef struct tcrnet_options {
+    int32_t method;           /* tcrnet_method (default AUTO) */
+    int32_t device;           /* CUDA device ordinal; -1 (default) = the calling
+                                 thread's current device */
+    int32_t force_offsets64;  /* 1: export int64 offsets even when nnz < 2^31 */
+    void *stream;             /* cudaStream_t; NULL = legacy default stream */
+    int32_t profile;          /* 1: record per-phase CUDA-event times (tcrnet_stats) */
+    int32_t reserved[8];      /* must be zero */
+} tcrnet_options;
+
+/* Defaults: AUTO method, current device, legacy default stream, no profiling. */
+void tcrnet_options_init(tcrnet_options *opt);
+
+/* Per-build counters and (with options.profile) CUDA-event phase times, all in
+ * milliseconds measured on the build's stream. */
+typedef struct tcrnet_stats {
+    int32_t method;           /* tcrnet_method actually used */
+    int32_t threshold;
+    int64_t n;                /* nodes */
+    int64_t nnz;              /* directed entries = 2 |E| */
+    int64_t candidate_pairs;  /* unordered pairs the tile kernel tested (tile path) */
+    int64_t n_unique;         /* distinct strings (deletion path) */
+    int64_t n_records;        /* deletion-join records (deletion path) */
+    int64_t unique_edges;     /* edges among distinct strings (deletion path) */
+    double ms_upload;         /* host -> device copy of the input (host inputs only) */
+    double ms_pack;           /* validate, encode, bucket */
+    double ms_count;          /* tile count pass / deletion join count */
+    double ms_scan;           /* offsets */
+    double ms_write;          /* tile write pass / deletion fill */
+    double ms_sort;           /* per-row ordering */
+    double ms_total;          /* whole call on the stream */
+    double ms_phase[8];       /* method-specific sub-phases (see DESIGN notes) */
+} tcrnet_stats;
+
+/* Opaque handle: a CSR (n rows) owned by the library in device memory, plus,
+ * for a build, the packed resident repertoire that tcrnet_query searches. */
+typedef struct tcrnet_graph *tcrnet_handle;
+
+/*
+ * Build the network of n strings given as NUL-terminated C strings (host
+ * memory). threshold = l_max. On success *out receives a new handle (free it
+ * with tcrnet_free); on failure *out is set to NULL.
+ */
+tcrnet_status tcrnet_build(const char *const *seqs, int64_t n, int32_t threshold,
+                           const tcrnet_options *opt, tcrnet_handle *out);
+
+/*
+ * Build from a flat layout: chars holds all strings back to back (no
+ * separators), offsets has n + 1 entries and string i is
+ * chars[offsets[i] .. offsets[i+1]). offsets[0] need not be 0. Both arrays live
+ * in memory space `mem`. With TCRNET_HOST the upload is part of the call.
+ */
+tcrnet_status tcrnet_build_flat(const uint8_t *chars, const int64_t *offsets, int64_t n,
+                                int32_t mem, int32_t threshold, const tcrnet_options *opt,
+                                tcrnet_handle *out);
+
+/* Size of a handle's CSR: rows, directed entries (nnz = sum of degrees) and
+ * whether exported offsets are int64 (nnz >= 2^31 or force_offsets64). Any
+ * pointer may be NULL. */
+tcrnet_status tcrnet_info(tcrnet_handle h, int64_t *n, int64_t *nnz, int32_t *offsets_are_64bit);
+
+/*
+ * Copy the CSR into caller-owned buffers in memory space `mem`:
+ * offsets (n + 1 entries, int32 or int64 as tcrnet_info reports), cols (nnz
+ * int32), degree (n int32). Any of the three may be NULL to skip it.
+ */
+tcrnet_status tcrnet_copy_csr(tcrnet_handle h, void *offsets, int32_t *cols, int32_t *degree,
+                              int32_t mem);
+
+/* Device pointers of the CSR, owned by the handle and valid until tcrnet_free.
+ * Any output pointer may be NULL. */
+tcrnet_status tcrnet_csr_device(tcrnet_handle h, const void **offsets, const int32_t **cols,
+                                const int32_t **degree);
+
+/*
+ * Neighbour lists of m query strings against the resident repertoire of a
+ * build handle: for query q, every node j with lev(query_q, s_j) <= the build's
+ * threshold, ascending. A query equal to a node's string lists that node (a
+ * query is not a node, so nothing is excluded). Flat layout as in
+ * tcrnet_build_flat. *out receives a new handle whose CSR has m rows (query it
+ * with tcrnet_info / tcrnet_copy_csr; it cannot itself be queried).
+ */
+tcrnet_status tcrnet_query_flat(tcrnet_handle h, const uint8_t *chars, const int64_t *offsets,
+                                int64_t m, int32_t mem, tcrnet_handle *out);
+
+/* Same as tcrnet_query_flat for NUL-terminated host strings. */
+tcrnet_status tcrnet_query(tcrnet_handle h, const char *const *queries, int64_t m,
+                           tcrnet_handle *out);
+
+/* Counters and phase times of the call that produced the handle. */
+tcrnet_status tcrnet_stats_get(tcrnet_handle h, tcrnet_stats *out);
+
+/* Release a handle and all device memory it owns. NULL is a no-op. */
+void tcrnet_free(tcrnet_handle h);
+
+/* Static description of a status code. */
+const char *tcrnet_strerror(tcrnet_status s);
+
+/* Input index that caused the calling thread's most recent EBADCHAR /
+ * ETOOLONG / EINVAL, or -1. */
+int64_t tcrnet_last_error_index(void);
+
+/* Library version string. */
+const char *tcrnet_version(void);
+
+/* Text of the calling thread's last failing CUDA call (diagnostics; "" if none). */
+const char *tcrnet_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TCRNET_H */

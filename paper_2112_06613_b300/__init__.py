@@ -1,0 +1,321 @@
+"""Python binding of tcrnet (B300 builder of the TCR-NET CDR3beta network).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``libtcrnet.so`` behind the C ABI of ``include/tcrnet.h``. The
+functions keep the C names (``tcrnet_build``, ``tcrnet_build_flat``,
+``tcrnet_query`` ...). Device buffers and streams may be given as PyTorch CUDA
+tensors / streams; PyTorch is used for nothing else.
+
+There is no CPU fallback: importing the module works without a GPU, but every
+call needs the built library and a CUDA device, and fails loudly otherwise.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtcrnet.so")
+HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "tcrnet.h")
+
+MAX_LEN = 48
+
+OK, EINVAL, EBADCHAR, ETOOLONG, ENOTSUP, ENOMEM, EDEVICE, ETIMEOUT, ESTATE = range(9)
+STATUS_NAMES = ["OK", "EINVAL", "EBADCHAR", "ETOOLONG", "ENOTSUP", "ENOMEM", "EDEVICE", "ETIMEOUT", "ESTATE"]
+METHOD_AUTO, METHOD_TILE, METHOD_DELETION = 0, 1, 2
+METHODS = {"auto": METHOD_AUTO, "tile": METHOD_TILE, "deletion": METHOD_DELETION}
+HOST, DEVICE = 0, 1
+
+
+class tcrnet_options(ctypes.Structure):
+    _fields_ = [
+        ("method", ctypes.c_int32),
+        ("device", ctypes.c_int32),
+        ("force_offsets64", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+        ("profile", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 8),
+    ]
+
+
+class tcrnet_stats(ctypes.Structure):
+    _fields_ = [
+        ("method", ctypes.c_int32),
+        ("threshold", ctypes.c_int32),
+        ("n", ctypes.c_int64),
+        ("nnz", ctypes.c_int64),
+        ("candidate_pairs", ctypes.c_int64),
+        ("n_unique", ctypes.c_int64),
+        ("n_records", ctypes.c_int64),
+        ("unique_edges", ctypes.c_int64),
+        ("ms_upload", ctypes.c_double),
+        ("ms_pack", ctypes.c_double),
+        ("ms_count", ctypes.c_double),
+        ("ms_scan", ctypes.c_double),
+        ("ms_write", ctypes.c_double),
+        ("ms_sort", ctypes.c_double),
+        ("ms_total", ctypes.c_double),
+        ("ms_phase", ctypes.c_double * 8),
+    ]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "ms_phase"}
+        d["ms_phase"] = list(self.ms_phase)
+        return d
+
+
+class TcrnetError(RuntimeError):
+    def __init__(self, status: int, where: str, index: int = -1, detail: str = ""):
+        self.status = status
+        self.index = index
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        msg = f"{where}: {name}"
+        if index >= 0:
+            msg += f" (input index {index})"
+        if detail:
+            msg += f" [{detail}]"
+        super().__init__(msg)
+
+
+_lib = None
+_lock = threading.Lock()
+
+# Exported C-ABI symbols (checked by the CPU test suite against include/tcrnet.h).
+SYMBOLS = [
+    "tcrnet_options_init", "tcrnet_build", "tcrnet_build_flat", "tcrnet_info", "tcrnet_copy_csr",
+    "tcrnet_csr_device", "tcrnet_query_flat", "tcrnet_query", "tcrnet_stats_get", "tcrnet_free",
+    "tcrnet_strerror", "tcrnet_last_error_index", "tcrnet_version", "tcrnet_last_cuda_error",
+]
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libtcrnet.so and declare its signatures. Raises if it is not built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with `python -m paper_2112_06613_b300.build`")
+        lib = ctypes.CDLL(path)
+        H = ctypes.c_void_p
+        HP = ctypes.POINTER(ctypes.c_void_p)
+        i64 = ctypes.c_int64
+        i32 = ctypes.c_int32
+        vp = ctypes.c_void_p
+        optp = ctypes.POINTER(tcrnet_options)
+        lib.tcrnet_options_init.argtypes = [optp]
+        lib.tcrnet_options_init.restype = None
+        lib.tcrnet_build.argtypes = [ctypes.POINTER(ctypes.c_char_p), i64, i32, optp, HP]
+        lib.tcrnet_build.restype = ctypes.c_int
+        lib.tcrnet_build_flat.argtypes = [vp, vp, i64, i32, i32, optp, HP]
+        lib.tcrnet_build_flat.restype = ctypes.c_int
+        lib.tcrnet_info.argtypes = [H, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32)]
+        lib.tcrnet_info.restype = ctypes.c_int
+        lib.tcrnet_copy_csr.argtypes = [H, vp, vp, vp, i32]
+        lib.tcrnet_copy_csr.restype = ctypes.c_int
+        lib.tcrnet_csr_device.argtypes = [H, HP, HP, HP]
+        lib.tcrnet_csr_device.restype = ctypes.c_int
+        lib.tcrnet_query_flat.argtypes = [H, vp, vp, i64, i32, HP]
+        lib.tcrnet_query_flat.restype = ctypes.c_int
+        lib.tcrnet_query.argtypes = [H, ctypes.POINTER(ctypes.c_char_p), i64, HP]
+        lib.tcrnet_query.restype = ctypes.c_int
+        lib.tcrnet_stats_get.argtypes = [H, ctypes.POINTER(tcrnet_stats)]
+        lib.tcrnet_stats_get.restype = ctypes.c_int
+        lib.tcrnet_free.argtypes = [H]
+        lib.tcrnet_free.restype = None
+        lib.tcrnet_strerror.argtypes = [ctypes.c_int]
+        lib.tcrnet_strerror.restype = ctypes.c_char_p
+        lib.tcrnet_last_error_index.argtypes = []
+        lib.tcrnet_last_error_index.restype = i64
+        lib.tcrnet_version.argtypes = []
+        lib.tcrnet_version.restype = ctypes.c_char_p
+        lib.tcrnet_last_cuda_error.argtypes = []
+        lib.tcrnet_last_cuda_error.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        lib = load_library()
+        idx = int(lib.tcrnet_last_error_index())
+        detail = lib.tcrnet_last_cuda_error().decode() if status in (EDEVICE, ENOMEM) else ""
+        raise TcrnetError(status, where, idx, detail)
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def make_options(method="auto", device=None, stream=None, profile=False, force_offsets64=False):
+    lib = load_library()
+    o = tcrnet_options()
+    lib.tcrnet_options_init(ctypes.byref(o))
+    o.method = METHODS[method] if isinstance(method, str) else int(method)
+    if device is not None:
+        o.device = int(device)
+    o.stream = _stream_ptr(stream)
+    o.profile = 1 if profile else 0
+    o.force_offsets64 = 1 if force_offsets64 else 0
+    return o
+
+
+class Graph:
+    """Owns one tcrnet handle: a CSR (n rows) in device memory."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            load_library().tcrnet_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    def info(self):
+        n, nnz, o64 = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        _check(load_library().tcrnet_info(self._h, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(o64)),
+               "tcrnet_info")
+        return n.value, nnz.value, bool(o64.value)
+
+    def copy_csr(self, out=None):
+        """Host copies (numpy): offsets (int32 or int64), cols int32, degree int32.
+        With `out=(offsets, cols, degree)` preallocated host arrays, fills them."""
+        n, nnz, o64 = self.info()
+        if out is None:
+            off = np.empty(n + 1, dtype=np.int64 if o64 else np.int32)
+            cols = np.empty(max(nnz, 1), dtype=np.int32)
+            deg = np.empty(max(n, 1), dtype=np.int32)
+        else:
+            off, cols, deg = out
+        _check(load_library().tcrnet_copy_csr(self._h, _ptr(off), _ptr(cols), _ptr(deg), HOST), "tcrnet_copy_csr")
+        if out is None:
+            return off, cols[:nnz], deg[:n]
+        return out
+
+    def copy_csr_device(self, device="cuda"):
+        """Device copies as torch tensors (offsets, cols, degree)."""
+        import torch
+
+        n, nnz, o64 = self.info()
+        off = torch.empty(n + 1, dtype=torch.int64 if o64 else torch.int32, device=device)
+        cols = torch.empty(max(nnz, 1), dtype=torch.int32, device=device)
+        deg = torch.empty(max(n, 1), dtype=torch.int32, device=device)
+        _check(load_library().tcrnet_copy_csr(self._h, off.data_ptr(), cols.data_ptr(), deg.data_ptr(), DEVICE),
+               "tcrnet_copy_csr")
+        return off, cols[:nnz], deg[:n]
+
+    def stats(self) -> dict:
+        st = tcrnet_stats()
+        _check(load_library().tcrnet_stats_get(self._h, ctypes.byref(st)), "tcrnet_stats_get")
+        return st.as_dict()
+
+    def query(self, queries):
+        return tcrnet_query(self, queries)
+
+    def query_flat(self, chars, offsets):
+        return tcrnet_query_flat(self, chars, offsets)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if _is_torch(a):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _flat_args(chars, offsets):
+    """(chars_ptr, offsets_ptr, n, mem, keepalive) for numpy or torch inputs."""
+    if _is_torch(chars):
+        import torch
+
+        assert chars.dtype == torch.uint8 and offsets.dtype == torch.int64
+        assert chars.is_contiguous() and offsets.is_contiguous()
+        assert chars.device == offsets.device
+        mem = DEVICE if chars.is_cuda else HOST
+        return chars.data_ptr(), offsets.data_ptr(), offsets.numel() - 1, mem, (chars, offsets)
+    chars = np.ascontiguousarray(chars, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    if chars.size == 0:
+        chars = np.zeros(1, dtype=np.uint8)
+    return chars.ctypes.data, offsets.ctypes.data, offsets.shape[0] - 1, HOST, (chars, offsets)
+
+
+def tcrnet_build(seqs, threshold: int = 1, method="auto", device=None, stream=None, profile=False,
+                 force_offsets64=False) -> Graph:
+    """Network of a list of strings (host memory)."""
+    lib = load_library()
+    enc = [s.encode("ascii") if isinstance(s, str) else bytes(s) for s in seqs]
+    arr = (ctypes.c_char_p * max(len(enc), 1))(*enc)
+    opt = make_options(method, device, stream, profile, force_offsets64)
+    h = ctypes.c_void_p()
+    _check(lib.tcrnet_build(arr, len(enc), int(threshold), ctypes.byref(opt), ctypes.byref(h)), "tcrnet_build")
+    return Graph(h.value)
+
+
+def tcrnet_build_flat(chars, offsets, threshold: int = 1, method="auto", device=None, stream=None,
+                      profile=False, force_offsets64=False) -> Graph:
+    """Network of strings in flat layout (numpy arrays, or torch tensors on host or device)."""
+    lib = load_library()
+    cp, op, n, mem, keep = _flat_args(chars, offsets)
+    opt = make_options(method, device, stream, profile, force_offsets64)
+    h = ctypes.c_void_p()
+    st = lib.tcrnet_build_flat(cp, op, n, mem, int(threshold), ctypes.byref(opt), ctypes.byref(h))
+    del keep
+    _check(st, "tcrnet_build_flat")
+    return Graph(h.value)
+
+
+def tcrnet_query(graph: Graph, queries) -> Graph:
+    lib = load_library()
+    enc = [s.encode("ascii") if isinstance(s, str) else bytes(s) for s in queries]
+    arr = (ctypes.c_char_p * max(len(enc), 1))(*enc)
+    h = ctypes.c_void_p()
+    _check(lib.tcrnet_query(graph.handle, arr, len(enc), ctypes.byref(h)), "tcrnet_query")
+    return Graph(h.value)
+
+
+def tcrnet_query_flat(graph: Graph, chars, offsets) -> Graph:
+    lib = load_library()
+    cp, op, m, mem, keep = _flat_args(chars, offsets)
+    h = ctypes.c_void_p()
+    st = lib.tcrnet_query_flat(graph.handle, cp, op, m, mem, ctypes.byref(h))
+    del keep
+    _check(st, "tcrnet_query_flat")
+    return Graph(h.value)
+
+
+def tcrnet_strerror(status: int) -> str:
+    return load_library().tcrnet_strerror(int(status)).decode()
+
+
+def tcrnet_version() -> str:
+    return load_library().tcrnet_version().decode()

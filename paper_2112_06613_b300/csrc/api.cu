@@ -1,0 +1,496 @@
+// C ABI and host runtime of tcrnet (declarations and contracts: include/tcrnet.h).
+//
+// A build runs: upload (host inputs only) -> pack (validate, encode, bucket) ->
+// the chosen method (tile: count pass, offsets, write pass, row sort;
+// deletion: deletion.cu) -> export (int32 or int64 offsets, degree). The
+// result stays in device memory owned by the handle; host copies happen only
+// in tcrnet_copy_csr.
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "deletion.cuh"
+#include "kernels.cuh"
+
+struct tcrnet_graph {
+    int device = 0;
+    cudaStream_t stream = 0;
+    bool query_result = false;
+    int32_t threshold = 1;
+    int64_t n = 0;
+    int64_t nnz = 0;
+    int offsets64 = 0;
+    void* d_offsets = nullptr;
+    int32_t* d_cols = nullptr;
+    int32_t* d_degree = nullptr;
+    // resident repertoire (build handles only)
+    tcr::Canon* d_bcanon = nullptr;
+    int32_t* d_bperm = nullptr;
+    int64_t bucket_off[tcr::kMaxLen + 2] = {0};
+    tcrnet_stats stats;
+};
+
+namespace tcr {
+
+static thread_local int64_t t_last_bad = -1;
+static thread_local char t_last_cuda[256] = {0};
+
+void note_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+    std::snprintf(t_last_cuda, sizeof(t_last_cuda), "%s: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+}
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    tcrnet_status set(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) return TCRNET_EDEVICE;
+        if (dev >= 0 && dev != prev) {
+            if (cudaSetDevice(dev) != cudaSuccess) return TCRNET_EINVAL;
+            changed = true;
+        }
+        return TCRNET_OK;
+    }
+    ~DeviceGuard() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+// Keep freed stream-ordered allocations cached in the device's default pool
+// (a per-process pool attribute), so repeated builds do not return memory to
+// the driver and re-map it.
+void configure_pool(int dev) {
+    static std::mutex mu;
+    static bool done[64] = {false};
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= 64 || done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done[dev] = true;
+}
+
+// CUDA-event phase timer (active only with options.profile).
+class Phases {
+public:
+    Phases(bool on, cudaStream_t s) : on_(on), s_(s) {}
+    ~Phases() {
+        for (auto e : ev_) cudaEventDestroy(e);
+    }
+    int mark() {
+        if (!on_) return -1;
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        cudaEventRecord(e, s_);
+        ev_.push_back(e);
+        return (int)ev_.size() - 1;
+    }
+    double ms(int a, int b) {
+        if (!on_ || a < 0 || b < 0) return 0.0;
+        cudaEventSynchronize(ev_[b]);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, ev_[a], ev_[b]);
+        return (double)t;
+    }
+
+private:
+    bool on_;
+    cudaStream_t s_;
+    std::vector<cudaEvent_t> ev_;
+};
+
+int sm_count(int dev) {
+    int v = 148;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v;
+}
+
+void free_handle_memory(tcrnet_graph* h) {
+    void* ptrs[] = {h->d_offsets, h->d_cols, h->d_degree, h->d_bcanon, h->d_bperm};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    h->d_offsets = nullptr;
+    h->d_cols = nullptr;
+    h->d_degree = nullptr;
+    h->d_bcanon = nullptr;
+    h->d_bperm = nullptr;
+}
+
+// Move a finished CSR (int64 offsets, cols, degree) into the handle, narrowing
+// offsets to int32 when they fit.
+tcrnet_status export_csr(tcrnet_graph* h, DevBuf& off64, DevBuf& cols, DevBuf& degree, int64_t n, int64_t nnz,
+                         bool force64, cudaStream_t s) {
+    h->n = n;
+    h->nnz = nnz;
+    h->offsets64 = (force64 || nnz > 0x7fffffffLL) ? 1 : 0;
+    if (h->offsets64) {
+        h->d_offsets = off64.release();
+    } else {
+        DevBuf off32;
+        TCR_CHECK(off32.alloc(sizeof(int32_t) * (n + 1), s));
+        TCR_CHECK(narrow_offsets(off64.as<int64_t>(), off32.as<int32_t>(), n + 1, s));
+        h->d_offsets = off32.release();
+    }
+    h->d_cols = static_cast<int32_t*>(cols.release());
+    h->d_degree = static_cast<int32_t*>(degree.release());
+    return TCRNET_OK;
+}
+
+// Tile method: count pass -> offsets -> write pass -> row sort.
+tcrnet_status tile_method(tcrnet_graph* h, const TileSide& rows, const TileSide& cols, int64_t n_rows, bool sym,
+                          int T, bool force64, Phases& ph, cudaStream_t s, int sms) {
+    tcrnet_stats& st = h->stats;
+    DevBuf count, off64, out_cols, cursor;
+    TCR_CHECK(count.alloc(sizeof(int32_t) * n_rows, s));
+    TCR_CUDA(cudaMemsetAsync(count.as<void>(), 0, sizeof(int32_t) * n_rows, s));
+    const int e0 = ph.mark();
+    int64_t pairs = 0;
+    TCR_CHECK(tile_pass(rows, cols, sym, T, false, count.as<int32_t>(), nullptr, nullptr, nullptr, &pairs, s, sms));
+    const int e1 = ph.mark();
+    TCR_CHECK(off64.alloc(sizeof(int64_t) * (n_rows + 1), s));
+    TCR_CHECK(scan_exclusive_i32_to_i64(count.as<int32_t>(), off64.as<int64_t>(), n_rows, s));
+    int64_t nnz = 0;
+    TCR_CUDA(cudaMemcpyAsync(&nnz, off64.as<int64_t>() + n_rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaStreamSynchronize(s));
+    const int e2 = ph.mark();
+    TCR_CHECK(out_cols.alloc(sizeof(int32_t) * nnz, s));
+    TCR_CHECK(cursor.alloc(sizeof(int32_t) * n_rows, s));
+    TCR_CUDA(cudaMemsetAsync(cursor.as<void>(), 0, sizeof(int32_t) * n_rows, s));
+    if (nnz > 0)
+        TCR_CHECK(tile_pass(rows, cols, sym, T, true, nullptr, off64.as<int64_t>(), cursor.as<int32_t>(),
+                            out_cols.as<int32_t>(), nullptr, s, sms));
+    const int e3 = ph.mark();
+    TCR_CHECK(sort_rows(off64.as<int64_t>(), out_cols.as<int32_t>(), n_rows, s, sms));
+    const int e4 = ph.mark();
+    TCR_CHECK(export_csr(h, off64, out_cols, count, n_rows, nnz, force64, s));
+    st.candidate_pairs = pairs;
+    st.ms_count = ph.ms(e0, e1);
+    st.ms_scan = ph.ms(e1, e2);
+    st.ms_write = ph.ms(e2, e3);
+    st.ms_sort = ph.ms(e3, e4);
+    return TCRNET_OK;
+}
+
+struct Inputs {
+    DevBuf chars, offs;
+    const uint8_t* d_chars = nullptr;
+    const int64_t* d_offs = nullptr;
+    int64_t base = 0;
+};
+
+// Device views of flat inputs; host inputs are uploaded on the stream.
+tcrnet_status stage_inputs(const uint8_t* chars, const int64_t* offsets, int64_t n, int mem, Inputs& in,
+                           cudaStream_t s) {
+    if (n == 0) return TCRNET_OK;
+    if (!chars || !offsets) return TCRNET_EINVAL;
+    if (mem == TCRNET_DEVICE) {
+        in.d_chars = chars;
+        in.d_offs = offsets;
+        in.base = 0;
+        return TCRNET_OK;
+    }
+    if (mem != TCRNET_HOST) return TCRNET_EINVAL;
+    // Every string must lie inside [offsets[0], offsets[n]) before anything is
+    // uploaded: offsets must not decrease.
+    for (int64_t i = 0; i < n; ++i) {
+        if (offsets[i + 1] < offsets[i]) {
+            t_last_bad = i;
+            return TCRNET_EINVAL;
+        }
+    }
+    const int64_t base = offsets[0];
+    const int64_t total = offsets[n] - base;
+    if (base < 0 || total < 0) return TCRNET_EINVAL;
+    TCR_CHECK(in.chars.alloc((size_t)total, s));
+    TCR_CHECK(in.offs.alloc(sizeof(int64_t) * (n + 1), s));
+    if (total > 0)
+        TCR_CUDA(cudaMemcpyAsync(in.chars.as<void>(), chars + base, (size_t)total, cudaMemcpyHostToDevice, s));
+    TCR_CUDA(cudaMemcpyAsync(in.offs.as<void>(), offsets, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s));
+    in.d_chars = in.chars.as<uint8_t>();
+    in.d_offs = in.offs.as<int64_t>();
+    in.base = base;
+    return TCRNET_OK;
+}
+
+// Flatten NUL-terminated host strings.
+tcrnet_status flatten(const char* const* seqs, int64_t n, std::vector<uint8_t>& chars, std::vector<int64_t>& offs) {
+    if (n > 0 && !seqs) return TCRNET_EINVAL;
+    offs.resize((size_t)n + 1);
+    offs[0] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!seqs[i]) {
+            t_last_bad = i;
+            return TCRNET_EINVAL;
+        }
+        offs[i + 1] = offs[i] + (int64_t)std::strlen(seqs[i]);
+    }
+    chars.resize((size_t)offs[n] + 1);
+    for (int64_t i = 0; i < n; ++i) std::memcpy(chars.data() + offs[i], seqs[i], (size_t)(offs[i + 1] - offs[i]));
+    return TCRNET_OK;
+}
+
+tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n, int mem, int32_t T,
+                         const tcrnet_options* opt_in, tcrnet_handle* out) {
+    if (!out) return TCRNET_EINVAL;
+    *out = nullptr;
+    t_last_bad = -1;
+    tcrnet_options opt;
+    tcrnet_options_init(&opt);
+    if (opt_in) opt = *opt_in;
+    if (n < 0 || n > 0x7fffffffLL) return TCRNET_EINVAL;
+    if (T < 0) return TCRNET_EINVAL;
+    if (T > 1) return TCRNET_ENOTSUP;
+    if (opt.method < TCRNET_METHOD_AUTO || opt.method > TCRNET_METHOD_DELETION) return TCRNET_EINVAL;
+    DeviceGuard dg;
+    TCR_CHECK(dg.set(opt.device));
+    int dev = 0;
+    TCR_CUDA(cudaGetDevice(&dev));
+    configure_pool(dev);
+    cudaStream_t s = (cudaStream_t)opt.stream;
+    const int sms = sm_count(dev);
+
+    tcrnet_graph* h = new (std::nothrow) tcrnet_graph();
+    if (!h) return TCRNET_ENOMEM;
+    std::memset(&h->stats, 0, sizeof(h->stats));
+    h->device = dev;
+    h->stream = s;
+    h->threshold = T;
+    h->stats.threshold = T;
+    h->stats.n = n;
+
+    Phases ph(opt.profile != 0, s);
+    auto fail = [&](tcrnet_status st) {
+        cudaStreamSynchronize(s);
+        free_handle_memory(h);
+        delete h;
+        return st;
+    };
+    const int p0 = ph.mark();
+    Inputs in;
+    tcrnet_status st = stage_inputs(chars, offsets, n, mem, in, s);
+    if (st != TCRNET_OK) return fail(st);
+    const int p1 = ph.mark();
+    Packed pk;
+    int64_t bad = -1;
+    if (n > 0) {
+        // chars are addressed as d_chars + (offsets[i] - base)
+        st = pack_strings(in.d_chars - in.base, in.d_offs, n, pk, &bad, s);
+        if (st != TCRNET_OK) {
+            t_last_bad = bad;
+            return fail(st);
+        }
+    }
+    const int p2 = ph.mark();
+    int method = opt.method;
+    if (method == TCRNET_METHOD_AUTO) method = (n >= kAutoDeletionMinN) ? TCRNET_METHOD_DELETION : TCRNET_METHOD_TILE;
+    h->stats.method = method;
+    for (int L = 0; L < kMaxLen + 2; ++L) h->bucket_off[L] = pk.bucket_off[L];
+    if (n == 0) {
+        DevBuf off64, cols, deg;
+        if ((st = off64.alloc(sizeof(int64_t), s)) != TCRNET_OK) return fail(st);
+        if (cudaMemsetAsync(off64.as<void>(), 0, sizeof(int64_t), s) != cudaSuccess) return fail(TCRNET_EDEVICE);
+        if ((st = cols.alloc(0, s)) != TCRNET_OK) return fail(st);
+        if ((st = deg.alloc(0, s)) != TCRNET_OK) return fail(st);
+        if ((st = export_csr(h, off64, cols, deg, 0, 0, opt.force_offsets64 != 0, s)) != TCRNET_OK) return fail(st);
+    } else if (method == TCRNET_METHOD_TILE) {
+        TileSide side{pk.canon.as<Canon>(), pk.perm.as<int32_t>(), pk.bucket_off};
+        st = tile_method(h, side, side, n, true, T, opt.force_offsets64 != 0, ph, s, sms);
+        if (st != TCRNET_OK) return fail(st);
+    } else {
+        DeletionResult dr;
+        st = deletion_build(pk, T, dr, s, sms, opt.profile != 0);
+        if (st != TCRNET_OK) return fail(st);
+        h->stats.n_unique = dr.n_unique;
+        h->stats.n_records = dr.n_records;
+        h->stats.unique_edges = dr.unique_edges;
+        h->stats.ms_count = dr.ms_join;
+        h->stats.ms_scan = dr.ms_scan;
+        h->stats.ms_write = dr.ms_fill;
+        h->stats.ms_sort = dr.ms_sort;
+        for (int k = 0; k < 8; ++k) h->stats.ms_phase[k] = dr.ms_phase[k];
+        st = export_csr(h, dr.off64, dr.cols, dr.degree, n, dr.nnz, opt.force_offsets64 != 0, s);
+        if (st != TCRNET_OK) return fail(st);
+    }
+    // keep the bucketed repertoire resident for queries
+    h->d_bcanon = static_cast<Canon*>(pk.canon.release());
+    h->d_bperm = static_cast<int32_t*>(pk.perm.release());
+    const int p3 = ph.mark();
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(TCRNET_EDEVICE);
+    h->stats.nnz = h->nnz;
+    h->stats.ms_upload = ph.ms(p0, p1);
+    h->stats.ms_pack = ph.ms(p1, p2);
+    h->stats.ms_total = ph.ms(p0, p3);
+    *out = h;
+    return TCRNET_OK;
+}
+
+}  // namespace
+}  // namespace tcr
+
+using namespace tcr;
+
+extern "C" {
+
+void tcrnet_options_init(tcrnet_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->method = TCRNET_METHOD_AUTO;
+    opt->device = -1;
+}
+
+tcrnet_status tcrnet_build_flat(const uint8_t* chars, const int64_t* offsets, int64_t n, int32_t mem,
+                                int32_t threshold, const tcrnet_options* opt, tcrnet_handle* out) {
+    return build_impl(chars, offsets, n, mem, threshold, opt, out);
+}
+
+tcrnet_status tcrnet_build(const char* const* seqs, int64_t n, int32_t threshold, const tcrnet_options* opt,
+                           tcrnet_handle* out) {
+    if (out) *out = nullptr;
+    t_last_bad = -1;
+    if (n < 0) return TCRNET_EINVAL;
+    std::vector<uint8_t> chars;
+    std::vector<int64_t> offs;
+    TCR_CHECK(flatten(seqs, n, chars, offs));
+    return build_impl(chars.data(), offs.data(), n, TCRNET_HOST, threshold, opt, out);
+}
+
+tcrnet_status tcrnet_info(tcrnet_handle h, int64_t* n, int64_t* nnz, int32_t* off64) {
+    if (!h) return TCRNET_EINVAL;
+    if (n) *n = h->n;
+    if (nnz) *nnz = h->nnz;
+    if (off64) *off64 = h->offsets64;
+    return TCRNET_OK;
+}
+
+tcrnet_status tcrnet_copy_csr(tcrnet_handle h, void* offsets, int32_t* cols, int32_t* degree, int32_t mem) {
+    if (!h) return TCRNET_EINVAL;
+    if (mem != TCRNET_HOST && mem != TCRNET_DEVICE) return TCRNET_EINVAL;
+    DeviceGuard dg;
+    TCR_CHECK(dg.set(h->device));
+    const cudaMemcpyKind kind = mem == TCRNET_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    cudaStream_t s = h->stream;
+    if (offsets)
+        TCR_CUDA(cudaMemcpyAsync(offsets, h->d_offsets, (h->offsets64 ? 8 : 4) * (size_t)(h->n + 1), kind, s));
+    if (cols && h->nnz > 0) TCR_CUDA(cudaMemcpyAsync(cols, h->d_cols, sizeof(int32_t) * (size_t)h->nnz, kind, s));
+    if (degree && h->n > 0) TCR_CUDA(cudaMemcpyAsync(degree, h->d_degree, sizeof(int32_t) * (size_t)h->n, kind, s));
+    TCR_CUDA(cudaStreamSynchronize(s));
+    return TCRNET_OK;
+}
+
+tcrnet_status tcrnet_csr_device(tcrnet_handle h, const void** offsets, const int32_t** cols, const int32_t** degree) {
+    if (!h) return TCRNET_EINVAL;
+    if (offsets) *offsets = h->d_offsets;
+    if (cols) *cols = h->d_cols;
+    if (degree) *degree = h->d_degree;
+    return TCRNET_OK;
+}
+
+tcrnet_status tcrnet_query_flat(tcrnet_handle h, const uint8_t* chars, const int64_t* offsets, int64_t m,
+                                int32_t mem, tcrnet_handle* out) {
+    if (!out) return TCRNET_EINVAL;
+    *out = nullptr;
+    t_last_bad = -1;
+    if (!h || m < 0 || m > 0x7fffffffLL) return TCRNET_EINVAL;
+    if (h->query_result) return TCRNET_ESTATE;
+    DeviceGuard dg;
+    TCR_CHECK(dg.set(h->device));
+    cudaStream_t s = h->stream;
+    const int sms = sm_count(h->device);
+    tcrnet_graph* r = new (std::nothrow) tcrnet_graph();
+    if (!r) return TCRNET_ENOMEM;
+    std::memset(&r->stats, 0, sizeof(r->stats));
+    r->device = h->device;
+    r->stream = s;
+    r->query_result = true;
+    r->threshold = h->threshold;
+    r->stats.threshold = h->threshold;
+    r->stats.n = m;
+    r->stats.method = TCRNET_METHOD_TILE;
+    auto fail = [&](tcrnet_status st) {
+        cudaStreamSynchronize(s);
+        free_handle_memory(r);
+        delete r;
+        return st;
+    };
+    Phases ph(false, s);
+    Inputs in;
+    tcrnet_status st = stage_inputs(chars, offsets, m, mem, in, s);
+    if (st != TCRNET_OK) return fail(st);
+    if (m == 0) {
+        DevBuf off64, cols, deg;
+        if ((st = off64.alloc(sizeof(int64_t), s)) != TCRNET_OK) return fail(st);
+        if (cudaMemsetAsync(off64.as<void>(), 0, sizeof(int64_t), s) != cudaSuccess) return fail(TCRNET_EDEVICE);
+        if ((st = cols.alloc(0, s)) != TCRNET_OK) return fail(st);
+        if ((st = deg.alloc(0, s)) != TCRNET_OK) return fail(st);
+        if ((st = export_csr(r, off64, cols, deg, 0, 0, false, s)) != TCRNET_OK) return fail(st);
+    } else {
+        Packed pk;
+        int64_t bad = -1;
+        st = pack_strings(in.d_chars - in.base, in.d_offs, m, pk, &bad, s);
+        if (st != TCRNET_OK) {
+            t_last_bad = bad;
+            return fail(st);
+        }
+        TileSide qs{pk.canon.as<Canon>(), pk.perm.as<int32_t>(), pk.bucket_off};
+        TileSide rs{h->d_bcanon, h->d_bperm, h->bucket_off};
+        st = tile_method(r, qs, rs, m, false, h->threshold, false, ph, s, sms);
+        if (st != TCRNET_OK) return fail(st);
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(TCRNET_EDEVICE);
+    r->stats.nnz = r->nnz;
+    *out = r;
+    return TCRNET_OK;
+}
+
+tcrnet_status tcrnet_query(tcrnet_handle h, const char* const* queries, int64_t m, tcrnet_handle* out) {
+    if (out) *out = nullptr;
+    t_last_bad = -1;
+    if (m < 0) return TCRNET_EINVAL;
+    std::vector<uint8_t> chars;
+    std::vector<int64_t> offs;
+    TCR_CHECK(flatten(queries, m, chars, offs));
+    return tcrnet_query_flat(h, chars.data(), offs.data(), m, TCRNET_HOST, out);
+}
+
+tcrnet_status tcrnet_stats_get(tcrnet_handle h, tcrnet_stats* out) {
+    if (!h || !out) return TCRNET_EINVAL;
+    *out = h->stats;
+    return TCRNET_OK;
+}
+
+void tcrnet_free(tcrnet_handle h) {
+    if (!h) return;
+    DeviceGuard dg;
+    dg.set(h->device);
+    cudaStreamSynchronize(h->stream);
+    free_handle_memory(h);
+    delete h;
+}
+
+const char* tcrnet_strerror(tcrnet_status s) {
+    switch (s) {
+        case TCRNET_OK: return "ok";
+        case TCRNET_EINVAL: return "invalid argument (empty string, bad offsets or parameter)";
+        case TCRNET_EBADCHAR: return "character outside the 20 standard amino acids";
+        case TCRNET_ETOOLONG: return "string longer than TCRNET_MAX_LEN";
+        case TCRNET_ENOTSUP: return "not supported (threshold >= 2 or option)";
+        case TCRNET_ENOMEM: return "out of memory";
+        case TCRNET_EDEVICE: return "CUDA device error";
+        case TCRNET_ETIMEOUT: return "bounded device wait timed out";
+        case TCRNET_ESTATE: return "handle cannot serve this call";
+        default: return "unknown status";
+    }
+}
+
+int64_t tcrnet_last_error_index(void) { return t_last_bad; }
+
+const char* tcrnet_version(void) { return "tcrnet 0.1 (sm_103a)"; }
+
+const char* tcrnet_last_cuda_error(void) { return t_last_cuda; }
+
+}  // extern "C"

@@ -1,0 +1,141 @@
+// Shared definitions of the tcrnet CUDA library (sm_103a).
+//
+// Canonical string layout ("canon"): 5-bit amino-acid codes, 12 codes per
+// 64-bit word, code k at word k / 12, bits 5 * (k % 12); four words hold the
+// longest accepted string (48). Code 0 is padding, codes 1..20 are the 20
+// standard amino acids in the order the paper lists the set Sigma (Methods
+// "Combination of amino acids"): A R N D C Q E G H I L K M F P S T W Y V.
+// The paper stores one byte per amino acid (Methods "GPU-based network
+// generation"); 5-bit fields let one XOR compare six positions per 32-bit word.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "tcrnet.h"
+
+namespace tcr {
+
+constexpr int kMaxLen = TCRNET_MAX_LEN;  // 48
+constexpr int kCodesPerWord = 12;
+constexpr int kCanonWords = 4;
+constexpr unsigned kFull = 0xffffffffu;
+
+struct __align__(16) Canon {
+    uint64_t w[kCanonWords];
+};
+
+// ASCII -> code (0 = not in the alphabet).
+__host__ __device__ inline uint32_t aa_code(uint32_t c) {
+    switch (c) {
+        case 'A': return 1;  case 'R': return 2;  case 'N': return 3;  case 'D': return 4;
+        case 'C': return 5;  case 'Q': return 6;  case 'E': return 7;  case 'G': return 8;
+        case 'H': return 9;  case 'I': return 10; case 'L': return 11; case 'K': return 12;
+        case 'M': return 13; case 'F': return 14; case 'P': return 15; case 'S': return 16;
+        case 'T': return 17; case 'W': return 18; case 'Y': return 19; case 'V': return 20;
+        default: return 0;
+    }
+}
+
+__device__ __forceinline__ uint32_t canon_code(const Canon& c, int k) {
+    return (uint32_t)(c.w[k / kCodesPerWord] >> (5 * (k % kCodesPerWord))) & 31u;
+}
+
+__device__ __forceinline__ Canon load_canon(const Canon* p) {
+    const ulonglong2* q = reinterpret_cast<const ulonglong2*>(p);
+    ulonglong2 x = __ldg(q);
+    ulonglong2 y = __ldg(q + 1);
+    Canon c;
+    c.w[0] = x.x; c.w[1] = x.y; c.w[2] = y.x; c.w[3] = y.y;
+    return c;
+}
+
+__device__ __forceinline__ void store_canon(Canon* p, const Canon& c) {
+    ulonglong2* q = reinterpret_cast<ulonglong2*>(p);
+    q[0] = make_ulonglong2(c.w[0], c.w[1]);
+    q[1] = make_ulonglong2(c.w[2], c.w[3]);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Error record of the last failing CUDA call (diagnostics only).
+void note_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+inline tcrnet_status status_of(cudaError_t e) {
+    if (e == cudaSuccess) return TCRNET_OK;
+    if (e == cudaErrorMemoryAllocation) return TCRNET_ENOMEM;
+    return TCRNET_EDEVICE;
+}
+
+#define TCR_CUDA(call)                                                  \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) {                                        \
+            ::tcr::note_cuda_error(e_, #call, __FILE__, __LINE__);      \
+            if (e_ == cudaErrorMemoryAllocation) (void)cudaGetLastError(); \
+            return ::tcr::status_of(e_);                                \
+        }                                                               \
+    } while (0)
+
+#define TCR_CHECK(expr)                                                 \
+    do {                                                                \
+        tcrnet_status s_ = (expr);                                      \
+        if (s_ != TCRNET_OK) return s_;                                 \
+    } while (0)
+
+#define TCR_LAUNCH_CHECK() TCR_CUDA(cudaGetLastError())
+
+// Stream-ordered device buffer (cudaMallocAsync / cudaFreeAsync). Freed when it
+// goes out of scope unless released.
+class DevBuf {
+public:
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept : p_(o.p_), bytes_(o.bytes_), s_(o.s_) { o.p_ = nullptr; o.bytes_ = 0; }
+    ~DevBuf() { reset(); }
+    tcrnet_status alloc(size_t bytes, cudaStream_t s) {
+        reset();
+        s_ = s;
+        bytes_ = bytes;
+        if (bytes == 0) bytes = 16;
+        cudaError_t e = cudaMallocAsync(&p_, bytes, s);
+        if (e != cudaSuccess) {
+            p_ = nullptr;
+            bytes_ = 0;
+            note_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
+            (void)cudaGetLastError();
+            return status_of(e);
+        }
+        return TCRNET_OK;
+    }
+    void reset() {
+        if (p_) cudaFreeAsync(p_, s_);
+        p_ = nullptr;
+        bytes_ = 0;
+    }
+    void* release() {
+        void* p = p_;
+        p_ = nullptr;
+        bytes_ = 0;
+        return p;
+    }
+    template <typename T>
+    T* as() const { return static_cast<T*>(p_); }
+    size_t bytes() const { return bytes_; }
+
+private:
+    void* p_ = nullptr;
+    size_t bytes_ = 0;
+    cudaStream_t s_ = 0;
+};
+
+}  // namespace tcr

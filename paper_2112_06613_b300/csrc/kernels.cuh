@@ -1,0 +1,52 @@
+// Host-side launchers of the tcrnet kernels (one translation unit per family).
+#pragma once
+
+#include "common.cuh"
+
+namespace tcr {
+
+// ---- scan.cu --------------------------------------------------------------
+// out[i] = sum_{k<i} in[k] for i in [0, n] (n + 1 outputs, out[n] = total).
+tcrnet_status scan_exclusive_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
+tcrnet_status scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
+// int64 offsets -> int32 offsets (caller checked that they fit).
+tcrnet_status narrow_offsets(const int64_t* in, int32_t* out, int64_t count, cudaStream_t s);
+// degree[i] = off[i+1] - off[i]
+tcrnet_status degree_from_offsets(const int64_t* off, int32_t* degree, int64_t n, cudaStream_t s);
+
+// ---- pack.cu --------------------------------------------------------------
+// Validated, encoded, length-bucketed strings.
+struct Packed {
+    int64_t n = 0;
+    DevBuf canon;    // Canon[n], bucket order (length ascending, input order within a length)
+    DevBuf perm;     // int32[n], bucket position -> input index
+    DevBuf lens;     // uint8[n], input order
+    DevBuf canon_in; // Canon[n], input order
+    int64_t bucket_off[kMaxLen + 2] = {0};  // bucket L = [bucket_off[L], bucket_off[L+1])
+};
+// Encodes chars/offsets (device memory) into `out`. On a bad input returns the
+// status and sets *bad_index to the lowest offending input index.
+tcrnet_status pack_strings(const uint8_t* d_chars, const int64_t* d_offsets, int64_t n, Packed& out,
+                           int64_t* bad_index, cudaStream_t s);
+
+// ---- tile.cu --------------------------------------------------------------
+struct TileSide {
+    const Canon* canon;  // bucket order
+    const int32_t* id;   // bucket position -> output id
+    const int64_t* bucket_off;  // host copy, kMaxLen + 2 entries
+};
+// Count (write == false) or write (write == true) every adjacent pair.
+//  graph mode (rows == cols, sym == true): tests (L, L) upper triangles and
+//   (L, L+1) rectangles; count[] gets both endpoints, writes go both ways.
+//  query mode (sym == false): rows are queries, cols the resident repertoire;
+//   tests (Lq, Lq - 1), (Lq, Lq), (Lq, Lq + 1); only query rows are counted/written.
+// Returns the number of candidate pairs tested in *pairs.
+tcrnet_status tile_pass(const TileSide& rows, const TileSide& cols, bool sym, int threshold, bool write,
+                        int32_t* count, const int64_t* off, int32_t* cursor, int32_t* cols_out,
+                        int64_t* pairs, cudaStream_t s, int num_sms);
+
+// ---- rowsort.cu -----------------------------------------------------------
+// Sort every row segment cols[off[i] .. off[i+1]) ascending (values distinct).
+tcrnet_status sort_rows(const int64_t* off, int32_t* cols, int64_t n, cudaStream_t s, int num_sms);
+
+}  // namespace tcr

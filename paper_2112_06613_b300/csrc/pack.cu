@@ -1,0 +1,143 @@
+// Validate, encode and length-bucket the input strings (hot-path steps a1, a2).
+//
+// The paper keeps each amino acid as one byte in a 30-slot buffer (Methods
+// "GPU-based network generation"); here each string becomes the 32-byte
+// canonical 5-bit form. Strings are then placed in buckets by length with a
+// stable counting sort (input order is kept inside a bucket), because only
+// strings whose lengths differ by at most l_max can be within distance l_max
+// (lev >= |len a - len b|), so the pair kernels only visit bucket pairs
+// (L, L) and (L, L + 1).
+//
+// k_encode: one thread per string. Reads its bytes, maps them through a
+//   shared-memory table, packs the codes, and counts lengths per block into
+//   blockcnt[len * nblocks + block] (length-major, so one exclusive scan over
+//   the whole array yields every block's first slot in every bucket).
+// k_bucket_scatter: recomputes each string's rank among equal-length strings
+//   of its block (warp match_any + popc, then a per-warp prefix) and writes the
+//   bucket-ordered copy plus the bucket position -> input index map.
+#include "kernels.cuh"
+
+namespace tcr {
+namespace {
+
+constexpr int kPackThreads = 256;
+constexpr int kPackWarps = kPackThreads / 32;
+constexpr int kBins = kMaxLen + 1;
+
+__global__ void __launch_bounds__(kPackThreads)
+k_encode(const uint8_t* __restrict__ chars, const int64_t* __restrict__ offs, int64_t n,
+         Canon* __restrict__ canon, uint8_t* __restrict__ lens, int32_t* __restrict__ blockcnt,
+         int nblocks, unsigned long long* __restrict__ err) {
+    __shared__ uint8_t lut[256];
+    __shared__ int cnt[kBins];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) lut[t] = (uint8_t)aa_code((uint32_t)t);
+    for (int t = threadIdx.x; t < kBins; t += blockDim.x) cnt[t] = 0;
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * kPackThreads + threadIdx.x;
+    if (i < n) {
+        const int64_t s = offs[i];
+        const int64_t len = offs[i + 1] - s;
+        unsigned code_err = 0;
+        Canon c;
+        c.w[0] = c.w[1] = c.w[2] = c.w[3] = 0;
+        if (len <= 0) {
+            code_err = TCRNET_EINVAL;
+        } else if (len > kMaxLen) {
+            code_err = TCRNET_ETOOLONG;
+        } else {
+            const uint8_t* p = chars + s;
+#pragma unroll
+            for (int k = 0; k < kMaxLen; ++k) {
+                if (k < len) {
+                    uint64_t v = lut[p[k]];
+                    if (v == 0) code_err = TCRNET_EBADCHAR;
+                    c.w[k / kCodesPerWord] |= v << (5 * (k % kCodesPerWord));
+                }
+            }
+        }
+        if (code_err) {
+            atomicMin(err, ((unsigned long long)i << 8) | code_err);
+            lens[i] = 0;
+        } else {
+            store_canon(canon + i, c);
+            lens[i] = (uint8_t)len;
+            atomicAdd(&cnt[len], 1);
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kBins; t += blockDim.x) blockcnt[(int64_t)t * nblocks + blockIdx.x] = cnt[t];
+}
+
+__global__ void __launch_bounds__(kPackThreads)
+k_bucket_scatter(const Canon* __restrict__ canon_in, const uint8_t* __restrict__ lens, int64_t n,
+                 const int64_t* __restrict__ blockoff, int nblocks, Canon* __restrict__ canon_out,
+                 int32_t* __restrict__ perm) {
+    __shared__ int wcnt[kPackWarps][kBins];
+    const int warp = threadIdx.x >> 5;
+    for (int t = threadIdx.x; t < kPackWarps * kBins; t += blockDim.x) (&wcnt[0][0])[t] = 0;
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * kPackThreads + threadIdx.x;
+    const int len = i < n ? (int)lens[i] : kBins;  // kBins = "no string"
+    const unsigned peers = __match_any_sync(kFull, len);
+    const int rank = __popc(peers & lanemask_lt());
+    if (len < kBins && rank == 0) wcnt[warp][len] = __popc(peers);
+    __syncthreads();
+    if (len < kBins) {
+        int pre = 0;
+        for (int w = 0; w < warp; ++w) pre += wcnt[w][len];
+        const int64_t pos = blockoff[(int64_t)len * nblocks + blockIdx.x] + pre + rank;
+        store_canon(canon_out + pos, load_canon(canon_in + i));
+        perm[pos] = (int32_t)i;
+    }
+}
+
+__global__ void k_bucket_bounds(const int64_t* __restrict__ blockoff, int nblocks, int64_t* __restrict__ bounds) {
+    const int t = threadIdx.x;
+    if (t <= kBins) bounds[t] = blockoff[(int64_t)t * nblocks];  // t == kBins: the grand total
+}
+
+}  // namespace
+
+tcrnet_status pack_strings(const uint8_t* d_chars, const int64_t* d_offsets, int64_t n, Packed& out,
+                           int64_t* bad_index, cudaStream_t s) {
+    out.n = n;
+    *bad_index = -1;
+    for (int L = 0; L < kMaxLen + 2; ++L) out.bucket_off[L] = 0;
+    if (n == 0) return TCRNET_OK;
+    const int nblocks = (int)ceil_div(n, kPackThreads);
+    TCR_CHECK(out.canon_in.alloc(sizeof(Canon) * n, s));
+    TCR_CHECK(out.lens.alloc(n, s));
+    TCR_CHECK(out.canon.alloc(sizeof(Canon) * n, s));
+    TCR_CHECK(out.perm.alloc(sizeof(int32_t) * n, s));
+    const int64_t ncnt = (int64_t)kBins * nblocks;
+    DevBuf blockcnt, blockoff, err, bounds;
+    TCR_CHECK(blockcnt.alloc(sizeof(int32_t) * ncnt, s));
+    TCR_CHECK(blockoff.alloc(sizeof(int64_t) * (ncnt + 1), s));
+    TCR_CHECK(err.alloc(sizeof(unsigned long long), s));
+    TCR_CHECK(bounds.alloc(sizeof(int64_t) * (kBins + 1), s));
+    TCR_CUDA(cudaMemsetAsync(err.as<void>(), 0xff, sizeof(unsigned long long), s));
+    k_encode<<<nblocks, kPackThreads, 0, s>>>(d_chars, d_offsets, n, out.canon_in.as<Canon>(),
+                                              out.lens.as<uint8_t>(), blockcnt.as<int32_t>(), nblocks,
+                                              err.as<unsigned long long>());
+    TCR_LAUNCH_CHECK();
+    unsigned long long h_err = ~0ull;
+    TCR_CUDA(cudaMemcpyAsync(&h_err, err.as<void>(), sizeof(h_err), cudaMemcpyDeviceToHost, s));
+    TCR_CHECK(scan_exclusive_i32_to_i64(blockcnt.as<int32_t>(), blockoff.as<int64_t>(), ncnt, s));
+    k_bucket_bounds<<<1, 64, 0, s>>>(blockoff.as<int64_t>(), nblocks, bounds.as<int64_t>());
+    TCR_LAUNCH_CHECK();
+    int64_t h_bounds[kBins + 1];
+    TCR_CUDA(cudaMemcpyAsync(h_bounds, bounds.as<void>(), sizeof(h_bounds), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaStreamSynchronize(s));
+    if (h_err != ~0ull) {
+        *bad_index = (int64_t)(h_err >> 8);
+        return (tcrnet_status)(h_err & 0xff);
+    }
+    for (int L = 0; L <= kBins; ++L) out.bucket_off[L] = h_bounds[L];
+    k_bucket_scatter<<<nblocks, kPackThreads, 0, s>>>(out.canon_in.as<Canon>(), out.lens.as<uint8_t>(), n,
+                                                      blockoff.as<int64_t>(), nblocks, out.canon.as<Canon>(),
+                                                      out.perm.as<int32_t>());
+    TCR_LAUNCH_CHECK();
+    return TCRNET_OK;
+}
+
+}  // namespace tcr

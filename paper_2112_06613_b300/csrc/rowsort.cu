@@ -1,0 +1,204 @@
+// Per-row ordering of the CSR columns (last part of hot-path step a5).
+//
+// The write passes place a row's neighbours in arrival order (atomic cursors),
+// so each row segment is sorted afterwards; the result is then independent of
+// scheduling, i.e. bit-exact and deterministic. Values inside a row are
+// distinct node ids.
+//
+//   len <= 32:          one warp, one value per lane, register bitonic network
+//                       (shuffle exchanges).
+//   33 <= len <= 1024:  one warp, shared-memory bitonic network (4 KB per warp).
+//   1025 .. 16384:      one 1024-thread block, shared-memory bitonic network.
+//   > 16384:            one block; 16384-value chunks sorted in shared memory,
+//                       then pairwise merges through a scratch buffer where each
+//                       value finds its output slot by binary search in the
+//                       partner run.
+#include <algorithm>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace tcr {
+namespace {
+
+constexpr int kWarpCap = 1024;
+constexpr int kBlockThreads = 1024;
+constexpr int kBlockCap = 16384;
+constexpr int kSortWarps = 8;
+constexpr int32_t kInf = 0x7fffffff;
+
+__device__ __forceinline__ int next_pow2(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// Bitonic network over s[0, P) by `nthreads` cooperating threads with index t;
+// `sync` orders the stages.
+template <typename Sync>
+__device__ __forceinline__ void bitonic_smem(int32_t* s, int P, int t, int nthreads, Sync sync) {
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = t; i < (P >> 1); i += nthreads) {
+                const int lo = 2 * j * (i / j) + (i % j);
+                const int hi = lo + j;
+                const bool up = (lo & k) == 0;
+                const int32_t x = s[lo], y = s[hi];
+                if ((x > y) == up) {
+                    s[lo] = y;
+                    s[hi] = x;
+                }
+            }
+            sync();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kSortWarps * 32)
+k_sort_warp(const int64_t* __restrict__ off, int32_t* __restrict__ cols, int64_t n,
+            int32_t* __restrict__ big, int* __restrict__ nbig) {
+    __shared__ int32_t buf[kSortWarps][kWarpCap];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * kSortWarps + warp;
+    const int64_t stride = (int64_t)gridDim.x * kSortWarps;
+    for (int64_t r = gw; r < n; r += stride) {
+        const int64_t base = off[r];
+        const int64_t len64 = off[r + 1] - base;
+        const int len = len64 > (int64_t)kInf ? kInf : (int)len64;
+        if (len <= 1) continue;
+        if (len <= 32) {
+            int32_t v = lane < len ? cols[base + lane] : kInf;
+#pragma unroll
+            for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    const int32_t p = __shfl_xor_sync(kFull, v, j);
+                    const bool up = (lane & k) == 0;
+                    const bool lower = (lane & j) == 0;
+                    v = (lower == up) ? min(v, p) : max(v, p);
+                }
+            }
+            if (lane < len) cols[base + lane] = v;
+        } else if (len <= kWarpCap) {
+            const int P = next_pow2(len);
+            int32_t* s = buf[warp];
+            for (int i = lane; i < P; i += 32) s[i] = i < len ? cols[base + i] : kInf;
+            __syncwarp();
+            bitonic_smem(s, P, lane, 32, [] __device__() { __syncwarp(); });
+            for (int i = lane; i < len; i += 32) cols[base + i] = s[i];
+            __syncwarp();
+        } else if (lane == 0) {
+            big[atomicAdd(nbig, 1)] = (int32_t)r;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlockThreads)
+k_sort_block(const int64_t* __restrict__ off, int32_t* __restrict__ cols, const int32_t* __restrict__ rows,
+             int nrows, int32_t* __restrict__ huge, int* __restrict__ nhuge) {
+    extern __shared__ int32_t sbuf[];
+    for (int k = blockIdx.x; k < nrows; k += gridDim.x) {
+        const int64_t r = rows[k];
+        const int64_t base = off[r];
+        const int64_t len = off[r + 1] - base;
+        if (len > kBlockCap) {
+            if (threadIdx.x == 0) huge[atomicAdd(nhuge, 1)] = (int32_t)r;
+            continue;
+        }
+        const int P = next_pow2((int)len);
+        for (int i = threadIdx.x; i < P; i += kBlockThreads) sbuf[i] = i < len ? cols[base + i] : kInf;
+        __syncthreads();
+        bitonic_smem(sbuf, P, threadIdx.x, kBlockThreads, [] __device__() { __syncthreads(); });
+        for (int i = threadIdx.x; i < len; i += kBlockThreads) cols[base + i] = sbuf[i];
+        __syncthreads();
+    }
+}
+
+// Sort each kBlockCap chunk of one huge row in place (one block per chunk).
+__global__ void __launch_bounds__(kBlockThreads)
+k_sort_chunks(int32_t* __restrict__ v, int64_t len) {
+    extern __shared__ int32_t sbuf[];
+    const int64_t c0 = (int64_t)blockIdx.x * kBlockCap;
+    const int64_t cl = (len - c0) < (int64_t)kBlockCap ? (len - c0) : (int64_t)kBlockCap;
+    const int P = next_pow2((int)cl);
+    for (int i = threadIdx.x; i < P; i += kBlockThreads) sbuf[i] = i < cl ? v[c0 + i] : kInf;
+    __syncthreads();
+    bitonic_smem(sbuf, P, threadIdx.x, kBlockThreads, [] __device__() { __syncthreads(); });
+    for (int i = threadIdx.x; i < cl; i += kBlockThreads) v[c0 + i] = sbuf[i];
+}
+
+// Merge adjacent sorted runs of length `run` from src into dst.
+__global__ void k_merge_runs(const int32_t* __restrict__ src, int32_t* __restrict__ dst, int64_t len, int64_t run) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t pair = i / (2 * run);
+        const int64_t a0 = pair * 2 * run;
+        const int64_t a1 = min(a0 + run, len);
+        const int64_t b0 = a1;
+        const int64_t b1 = min(a0 + 2 * run, len);
+        const int32_t x = src[i];
+        const bool in_a = i < a1;
+        // rank of x in the partner run (values are distinct)
+        int64_t lo = in_a ? b0 : a0, hi = in_a ? b1 : a1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (src[mid] < x) lo = mid + 1; else hi = mid;
+        }
+        const int64_t rank_partner = lo - (in_a ? b0 : a0);
+        const int64_t rank_own = i - (in_a ? a0 : b0);
+        dst[a0 + rank_own + rank_partner] = x;
+    }
+}
+
+}  // namespace
+
+tcrnet_status sort_rows(const int64_t* off, int32_t* cols, int64_t n, cudaStream_t s, int num_sms) {
+    if (n <= 0) return TCRNET_OK;
+    DevBuf big, counts;
+    TCR_CHECK(big.alloc(sizeof(int32_t) * 2 * n, s));  // big rows, then huge rows
+    TCR_CHECK(counts.alloc(sizeof(int) * 2, s));
+    TCR_CUDA(cudaMemsetAsync(counts.as<void>(), 0, sizeof(int) * 2, s));
+    const int64_t blocks = std::min<int64_t>(ceil_div(n, kSortWarps), (int64_t)num_sms * 64);
+    k_sort_warp<<<(unsigned)blocks, kSortWarps * 32, 0, s>>>(off, cols, n, big.as<int32_t>(), counts.as<int>());
+    TCR_LAUNCH_CHECK();
+    int h_counts[2] = {0, 0};
+    TCR_CUDA(cudaMemcpyAsync(h_counts, counts.as<void>(), sizeof(h_counts), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaStreamSynchronize(s));
+    if (h_counts[0] == 0) return TCRNET_OK;
+    const size_t smem = sizeof(int32_t) * kBlockCap;
+    TCR_CUDA(cudaFuncSetAttribute(k_sort_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TCR_CUDA(cudaFuncSetAttribute(k_sort_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = std::min(h_counts[0], num_sms * 2);
+    k_sort_block<<<grid, kBlockThreads, smem, s>>>(off, cols, big.as<int32_t>(), h_counts[0],
+                                                   big.as<int32_t>() + h_counts[0], counts.as<int>() + 1);
+    TCR_LAUNCH_CHECK();
+    TCR_CUDA(cudaMemcpyAsync(h_counts, counts.as<void>(), sizeof(h_counts), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaStreamSynchronize(s));
+    if (h_counts[1] == 0) return TCRNET_OK;
+    // Rare: rows longer than one shared-memory block.
+    std::vector<int32_t> huge(h_counts[1]);
+    TCR_CUDA(cudaMemcpyAsync(huge.data(), big.as<int32_t>() + h_counts[0], sizeof(int32_t) * huge.size(),
+                             cudaMemcpyDeviceToHost, s));
+    std::vector<int64_t> hoff(2);
+    TCR_CUDA(cudaStreamSynchronize(s));
+    for (int32_t r : huge) {
+        TCR_CUDA(cudaMemcpyAsync(hoff.data(), off + r, sizeof(int64_t) * 2, cudaMemcpyDeviceToHost, s));
+        TCR_CUDA(cudaStreamSynchronize(s));
+        const int64_t len = hoff[1] - hoff[0];
+        int32_t* v = cols + hoff[0];
+        k_sort_chunks<<<(unsigned)ceil_div(len, kBlockCap), kBlockThreads, smem, s>>>(v, len);
+        TCR_LAUNCH_CHECK();
+        DevBuf tmp;
+        TCR_CHECK(tmp.alloc(sizeof(int32_t) * len, s));
+        int32_t* src = v;
+        int32_t* dst = tmp.as<int32_t>();
+        for (int64_t run = kBlockCap; run < len; run *= 2) {
+            k_merge_runs<<<(unsigned)std::min<int64_t>(ceil_div(len, 256), 65535), 256, 0, s>>>(src, dst, len, run);
+            TCR_LAUNCH_CHECK();
+            std::swap(src, dst);
+        }
+        if (src != v) TCR_CUDA(cudaMemcpyAsync(v, src, sizeof(int32_t) * len, cudaMemcpyDeviceToDevice, s));
+    }
+    return TCRNET_OK;
+}
+
+}  // namespace tcr

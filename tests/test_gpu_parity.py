@@ -1,0 +1,207 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bar: bit-exact CSR (offsets, cols, degree) — this is integer work.
+Full graphs where the oracle finishes in seconds; sampled rows plus global
+invariants at the full sizes."""
+
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2112_06613_b300 as tn
+from synthgen import ALPHABET, from_strings, generate, generate_config1
+
+from csr_util import assert_csr_equal, assert_rows_equal, check_invariants, sample_rows
+
+pytestmark = pytest.mark.gpu
+
+METHODS = ["tile", "deletion"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _needs_gpu():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    tn.load_library()
+
+
+def gpu_csr(rep, threshold=1, method="tile", **kw):
+    with tn.tcrnet_build_flat(rep.chars, rep.offsets, threshold=threshold, method=method, **kw) as g:
+        off, cols, deg = g.copy_csr()
+        st = g.stats()
+    return np.asarray(off, dtype=np.int64), cols, deg, st
+
+
+def oracle_csr(rep, threshold=1):
+    off, cols, deg = oracle.network(rep.chars, rep.offsets, max_dist=threshold)
+    return off, cols, deg
+
+
+def single_length(n, L, seed=0):
+    """n generator strings that all have length L (one bucket)."""
+    out = []
+    s = seed
+    while len(out) < n:
+        r = generate(4 * n, seed=s, len_lo=L, len_hi=L)
+        out.extend(r.strings())
+        s += 1000
+    return from_strings(out[:n])
+
+
+@pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("threshold", [0, 1])
+def test_config1_full_graph(method, threshold):
+    rep = generate_config1(10_000, seed=0)
+    off, cols, deg, st = gpu_csr(rep, threshold, method)
+    ro, rc, rd = oracle_csr(rep, threshold)
+    assert_csr_equal(off, cols, ro, rc, f"config1 {method} T={threshold}")
+    assert np.array_equal(deg, rd)
+    check_invariants(off, cols, deg, rep.n)
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_one_bucket_several_tiles_ragged(method):
+    # 5000 strings of one length: several 2048-row blocks and 512-column
+    # chunks, diagonal items and a ragged tail.
+    rep = single_length(5003, 14, seed=3)
+    off, cols, deg, _ = gpu_csr(rep, 1, method)
+    ro, rc, _ = oracle_csr(rep, 1)
+    assert_csr_equal(off, cols, ro, rc, f"single bucket {method}")
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_two_adjacent_buckets_large(method):
+    a = single_length(2600, 12, seed=5).strings()
+    b = single_length(2300, 13, seed=6).strings()
+    # interleave so input order differs from bucket order
+    strs = [x for pair in zip(a, b) for x in pair] + a[len(b):]
+    rep = from_strings(strs)
+    off, cols, _, _ = gpu_csr(rep, 1, method)
+    ro, rc, _ = oracle_csr(rep, 1)
+    assert_csr_equal(off, cols, ro, rc, f"buckets 12/13 {method}")
+
+
+def edge_strings():
+    rng = np.random.default_rng(17)
+    out = []
+    for L in (1, 2, 5, 6, 7, 11, 12, 13, 17, 18, 19, 23, 24, 25, 26, 29, 30, 31, 35, 36, 37, 47, 48):
+        base = "".join(rng.choice(list(ALPHABET), size=L))
+        out.append(base)
+        out.append(base)  # duplicate
+        p = int(rng.integers(0, L))
+        out.append(base[:p] + ("A" if base[p] != "A" else "C") + base[p + 1:])  # substitution
+        out.append(base[:p] + base[p + 1:] if L > 1 else "W")  # deletion
+        if L < 48:
+            out.append(base[:p] + "Y" + base[p:])  # insertion
+        out.append(base[::-1])
+    # homopolymer runs and their deletion/insertion variants
+    out += ["AAAA", "AAA", "AA", "A", "AAC", "AC", "ACC", "CAA", "CAAAF", "CAAF", "CAAAAF"]
+    out += ["W" * 48, "W" * 47, "W" * 30, "W" * 29, "W" * 25, "W" * 24, "W" * 13, "W" * 12]
+    return out
+
+
+@pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("threshold", [0, 1])
+def test_edge_cases_lengths_and_runs(method, threshold):
+    rep = from_strings(edge_strings())
+    off, cols, deg, _ = gpu_csr(rep, threshold, method)
+    ro, rc, _ = oracle_csr(rep, threshold)
+    assert_csr_equal(off, cols, ro, rc, f"edge strings {method} T={threshold}")
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_all_identical_is_complete_graph(method):
+    rep = from_strings(["CASSLGQETQYF"] * 700)
+    off, cols, deg, _ = gpu_csr(rep, 1, method)
+    assert (deg == 699).all()
+    ro, rc, _ = oracle_csr(rep, 1)
+    assert_csr_equal(off, cols, ro, rc, "identical")
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_degenerate_sizes(method):
+    for strs in ([], ["CASSF"], ["CASSF", "CASSF"], ["CASSF", "CASSG"], ["CASSF", "CAS"]):
+        rep = from_strings(strs)
+        off, cols, deg, _ = gpu_csr(rep, 1, method)
+        ro, rc, _ = oracle_csr(rep, 1)
+        assert_csr_equal(off, cols, ro, rc, f"{strs}")
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_empty_neighbour_buckets(method):
+    # lengths 10 and 14 only: no (L, L+1) pairs exist
+    a = single_length(800, 10, seed=8).strings()
+    b = single_length(900, 14, seed=9).strings()
+    rep = from_strings(a + b)
+    off, cols, _, _ = gpu_csr(rep, 1, method)
+    ro, rc, _ = oracle_csr(rep, 1)
+    assert_csr_equal(off, cols, ro, rc, "gapped buckets")
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_deterministic_and_int64_offsets(method):
+    rep = generate_config1(20_000, seed=2)
+    o1, c1, d1, _ = gpu_csr(rep, 1, method)
+    o2, c2, d2, _ = gpu_csr(rep, 1, method, force_offsets64=True)
+    assert_csr_equal(o1, c1, o2, c2, "repeat / int64")
+    assert np.array_equal(d1, d2)
+
+
+def test_methods_agree_1e5():
+    rep = generate_config1(100_000, seed=0)
+    ot, ct, dt, _ = gpu_csr(rep, 1, "tile")
+    od, cd, dd, _ = gpu_csr(rep, 1, "deletion")
+    assert_csr_equal(ot, ct, od, cd, "tile vs deletion at 1e5")
+    check_invariants(ot, ct, dt, rep.n)
+    rows = sample_rows(dt, 400, seed=1, top=50)
+    roff, rcols = oracle.rows(rep.chars, rep.offsets, rows)
+    assert_rows_equal(ot, ct, rows, roff, rcols, "1e5 sampled rows")
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_bad_inputs_report_index(method):
+    cases = [
+        (["CASSF", "CASXF", "CASSB"], tn.EBADCHAR, 1),
+        (["CASSF", "cassf"], tn.EBADCHAR, 1),
+        (["CASSF", "C" * 49], tn.ETOOLONG, 1),
+        (["CASSF", "CASSG", ""], tn.EINVAL, 2),
+    ]
+    for strs, status, idx in cases:
+        with pytest.raises(tn.TcrnetError) as e:
+            tn.tcrnet_build(strs, 1, method=method)
+        assert e.value.status == status and e.value.index == idx
+    # the context is still usable afterwards
+    off, cols, deg, _ = gpu_csr(from_strings(["CASSF", "CASSG"]), 1, method)
+    assert list(cols) == [1, 0]
+
+
+def test_string_list_and_device_inputs_agree():
+    import torch
+
+    rep = generate_config1(3000, seed=4)
+    with tn.tcrnet_build(rep.strings(), 1, method="tile") as g:
+        o1, c1, _ = g.copy_csr()
+    chars = torch.from_numpy(rep.chars).cuda()
+    offs = torch.from_numpy(rep.offsets).cuda()
+    with tn.tcrnet_build_flat(chars, offs, 1, method="tile", stream=torch.cuda.current_stream()) as g:
+        o2, c2, d2 = g.copy_csr_device()
+    assert_csr_equal(o1, c1, o2.cpu().numpy(), c2.cpu().numpy(), "list vs device")
+
+
+def test_queries_match_oracle():
+    rep = generate_config1(20_000, seed=7)
+    strs = rep.strings()
+    rng = np.random.default_rng(5)
+    qs = [strs[i] for i in rng.choice(len(strs), 300, replace=False)]
+    qs += [q[:-1] for q in qs[:50]] + [q + "A" for q in qs[50:100]] + ["CASSLGQF", "W", "C" * 48]
+    qs += [q[:3] + "W" + q[4:] for q in qs[100:150]]
+    q = from_strings(qs)
+    with tn.tcrnet_build_flat(rep.chars, rep.offsets, 1, method="tile") as g:
+        with g.query_flat(q.chars, q.offsets) as r:
+            qo, qc, qd = r.copy_csr()
+    ro, rc = oracle.neighbors(rep.chars, rep.offsets, q.chars, q.offsets, max_dist=1)
+    assert_csr_equal(qo, qc, ro, rc, "queries")
