@@ -79,7 +79,9 @@ typedef struct tcrnet_options {
     int32_t force_offsets64;  /* 1: export int64 offsets even when nnz < 2^31 */
     void *stream;             /* cudaStream_t; NULL = legacy default stream */
     int32_t profile;          /* 1: record per-phase CUDA-event times (tcrnet_stats) */
-    int32_t reserved[8];      /* must be zero */
+    int32_t partition_cap;    /* testing: deletion-join partitions larger than this
+                                 take the exact quadratic fallback; 0 = default */
+    int32_t reserved[7];      /* must be zero */
 } tcrnet_options;
 
 /* Defaults: AUTO method, current device, legacy default stream, no profiling. */
@@ -96,6 +98,7 @@ typedef struct tcrnet_stats {
     int64_t n_unique;         /* distinct strings (deletion path) */
     int64_t n_records;        /* deletion-join records (deletion path) */
     int64_t unique_edges;     /* edges among distinct strings (deletion path) */
+    int64_t n_fallback;       /* deletion-join partitions joined by the exact fallback */
     double ms_upload;         /* host -> device copy of the input (host inputs only) */
     double ms_pack;           /* validate, encode, bucket */
     double ms_count;          /* tile count pass / deletion join count */

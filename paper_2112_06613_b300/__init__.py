@@ -38,7 +38,8 @@ class tcrnet_options(ctypes.Structure):
         ("force_offsets64", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
         ("profile", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 8),
+        ("partition_cap", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 7),
     ]
 
 
@@ -52,6 +53,7 @@ class tcrnet_stats(ctypes.Structure):
         ("n_unique", ctypes.c_int64),
         ("n_records", ctypes.c_int64),
         ("unique_edges", ctypes.c_int64),
+        ("n_fallback", ctypes.c_int64),
         ("ms_upload", ctypes.c_double),
         ("ms_pack", ctypes.c_double),
         ("ms_count", ctypes.c_double),
@@ -159,7 +161,8 @@ def _stream_ptr(stream):
     return int(stream.cuda_stream)
 
 
-def make_options(method="auto", device=None, stream=None, profile=False, force_offsets64=False):
+def make_options(method="auto", device=None, stream=None, profile=False, force_offsets64=False,
+                 partition_cap=0):
     lib = load_library()
     o = tcrnet_options()
     lib.tcrnet_options_init(ctypes.byref(o))
@@ -169,6 +172,7 @@ def make_options(method="auto", device=None, stream=None, profile=False, force_o
     o.stream = _stream_ptr(stream)
     o.profile = 1 if profile else 0
     o.force_offsets64 = 1 if force_offsets64 else 0
+    o.partition_cap = int(partition_cap)
     return o
 
 
@@ -282,11 +286,11 @@ def tcrnet_build(seqs, threshold: int = 1, method="auto", device=None, stream=No
 
 
 def tcrnet_build_flat(chars, offsets, threshold: int = 1, method="auto", device=None, stream=None,
-                      profile=False, force_offsets64=False) -> Graph:
+                      profile=False, force_offsets64=False, partition_cap=0) -> Graph:
     """Network of strings in flat layout (numpy arrays, or torch tensors on host or device)."""
     lib = load_library()
     cp, op, n, mem, keep = _flat_args(chars, offsets)
-    opt = make_options(method, device, stream, profile, force_offsets64)
+    opt = make_options(method, device, stream, profile, force_offsets64, partition_cap)
     h = ctypes.c_void_p()
     st = lib.tcrnet_build_flat(cp, op, n, mem, int(threshold), ctypes.byref(opt), ctypes.byref(h))
     del keep

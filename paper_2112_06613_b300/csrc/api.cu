@@ -303,11 +303,12 @@ tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n
         if (st != TCRNET_OK) return fail(st);
     } else {
         DeletionResult dr;
-        st = deletion_build(pk, T, dr, s, sms, opt.profile != 0);
+        st = deletion_build(pk, T, dr, s, sms, opt.profile != 0, opt.partition_cap);
         if (st != TCRNET_OK) return fail(st);
         h->stats.n_unique = dr.n_unique;
         h->stats.n_records = dr.n_records;
         h->stats.unique_edges = dr.unique_edges;
+        h->stats.n_fallback = dr.n_fallback;
         h->stats.ms_count = dr.ms_join;
         h->stats.ms_scan = dr.ms_scan;
         h->stats.ms_write = dr.ms_fill;

@@ -101,6 +101,17 @@ public:
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
     DevBuf(DevBuf&& o) noexcept : p_(o.p_), bytes_(o.bytes_), s_(o.s_) { o.p_ = nullptr; o.bytes_ = 0; }
+    DevBuf& operator=(DevBuf&& o) noexcept {
+        if (this != &o) {
+            reset();
+            p_ = o.p_;
+            bytes_ = o.bytes_;
+            s_ = o.s_;
+            o.p_ = nullptr;
+            o.bytes_ = 0;
+        }
+        return *this;
+    }
     ~DevBuf() { reset(); }
     tcrnet_status alloc(size_t bytes, cudaStream_t s) {
         reset();

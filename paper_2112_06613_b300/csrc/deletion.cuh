@@ -6,7 +6,10 @@
 namespace tcr {
 
 // AUTO picks the deletion method from this many strings on.
-constexpr int64_t kAutoDeletionMinN = 1LL << 62;
+constexpr int64_t kAutoDeletionMinN = 2048;
+
+// Largest input the deletion records can address (distinct-string ids use 25 bits).
+constexpr int64_t kDeletionMaxN = 1LL << 25;
 
 struct DeletionResult {
     DevBuf off64;   // int64[n + 1]
@@ -16,11 +19,14 @@ struct DeletionResult {
     int64_t n_unique = 0;
     int64_t n_records = 0;
     int64_t unique_edges = 0;
+    int64_t n_fallback = 0;  // partitions joined by the exact quadratic fallback
     double ms_join = 0, ms_scan = 0, ms_fill = 0, ms_sort = 0;
-    double ms_phase[8] = {0};
+    double ms_phase[8] = {0};  // dedup, records, join count, join write, degrees, fill, sort, total
 };
 
+// Test knob: partitions larger than `partition_cap` (<= the shared-memory
+// capacity; 0 = default) take the quadratic fallback.
 tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaStream_t s, int num_sms,
-                             bool profile);
+                             bool profile, int partition_cap = 0);
 
 }  // namespace tcr

@@ -205,3 +205,21 @@ def test_queries_match_oracle():
             qo, qc, qd = r.copy_csr()
     ro, rc = oracle.neighbors(rep.chars, rep.offsets, q.chars, q.offsets, max_dist=1)
     assert_csr_equal(qo, qc, ro, rc, "queries")
+
+
+def test_deletion_exact_fallback_join():
+    # a tiny partition capacity sends most partitions to the exact quadratic join
+    rep = generate_config1(10_000, seed=11)
+    off, cols, deg, st = gpu_csr(rep, 1, "deletion", partition_cap=4)
+    assert st["n_fallback"] > 0
+    ro, rc, _ = oracle_csr(rep, 1)
+    assert_csr_equal(off, cols, ro, rc, "fallback join")
+
+
+def test_deletion_counts_distinct_strings():
+    rep = generate_config1(30_000, seed=12)
+    _, _, _, st = gpu_csr(rep, 1, "deletion")
+    strs = rep.strings()
+    assert st["n_unique"] == len(set(strs))
+    assert st["n_records"] == sum(len(s) + 1 for s in set(strs))
+    assert st["n_fallback"] == 0
