@@ -1,0 +1,444 @@
+#!/usr/bin/env python
+"""Benchmark of the TCR-NET network-construction hot path on B300.
+
+One step = one complete network build of the N = 800,000-string synthetic
+repertoire (seed = rank) at l_max = 1 through the library's default method
+(validate + encode + bucket, distinct-string collapse, deletion-neighbourhood
+join, offsets, fill, per-row sort, int32 CSR export), with the inputs already
+in device memory. `value` is all-pairs comparisons resolved per second,
+N (N - 1) / 2 per build, summed over ranks (weak scaling: every rank builds its
+own repertoire; there is no collective on the data path).
+
+The same JSON line also carries:
+  edges_per_s    undirected edges produced per second;
+  tile           the all-pairs tile kernel (count pass) on the same workload:
+                 candidate pair tests per second and its integer-ALU roofline;
+  query          p50/p99 latency of query batches against the resident
+                 repertoire (host strings in, host neighbour lists out);
+  e2e            the same metric through the public API from pinned host
+                 buffers, including the upload and the read-back of the CSR;
+  roofline       the dominant phase of the step against measured HBM bandwidth;
+  cpu_baseline   the CPU oracle (plain Wagner-Fischer) on a bounded row sample.
+
+`--impl reference` times the CPU oracle alone (there is no reference library
+to install: the paper's code is not available) and prints the same metric.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "pair comparisons/s and edges/s at N=8e5 (frac of int/HBM roofline); query p50/p99"
+UNIT = "pairs/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6400.0
+SMS = 148
+# 32-bit integer ALU results per clock per SM (logic, add, shift), 4 partitions x 16 lanes
+INT_LANES_PER_SM = 64
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=800_000)
+    ap.add_argument("--method", default="auto", choices=["auto", "deletion", "tile"])
+    ap.add_argument("--tile-steps", type=int, default=2)
+    ap.add_argument("--query-batches", type=int, default=30)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-extras", action="store_true", help="skip tile/query/e2e/cpu legs")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2032.0)), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, 2032.0, "fallback"
+
+
+def workload(n, seed):
+    from synthgen import generate_config2
+
+    return generate_config2(n, seed=seed)
+
+
+def workload_config(args, method):
+    return {
+        "workload": f"config 2: N={args.n} synthetic CDR3beta strings (V-insertion-J templates, "
+                    f"insertion 0-6 aa, lengths 10-20, Zipf(1) background), l_max=1, int32 CSR",
+        "n": args.n,
+        "threshold": 1,
+        "method": method,
+        "seed": "rank",
+        "inputs_resident": True,
+        "l2": "flushed between timed steps (512 MB write)",
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                mx.append(float(parts[2].split()[0]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle legs
+
+def oracle_rate(rep, seconds, seed=0, rows_per_call=None):
+    """Oracle (plain Wagner-Fischer, all host cores) on sampled rows of the
+    network; returns (pairs/s, cores, rows, elapsed)."""
+    import oracle
+
+    cores = oracle.max_threads()
+    rng = np.random.default_rng(seed)
+    per = rows_per_call or max(1, cores)
+    done, pairs, t0 = 0, 0, time.perf_counter()
+    while True:
+        rows = rng.choice(rep.n, size=per, replace=False).astype(np.int64)
+        oracle.rows(rep.chars, rep.offsets, rows, max_dist=1, nthreads=cores)
+        done += per
+        pairs += per * (rep.n - 1)
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            return pairs / el, cores, done, el
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+
+    rep = workload(args.n, 0)
+    cores = oracle.max_threads()
+    rng = np.random.default_rng(1)
+    per = max(1, cores)  # one row per core per step (about 0.3 s)
+
+    def step():
+        rows = rng.choice(rep.n, size=per, replace=False).astype(np.int64)
+        oracle.rows(rep.chars, rep.offsets, rows, max_dist=1, nthreads=cores)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    value = args.steps * per * (rep.n - 1) / el
+    sample = (f"{per} sampled rows per step (each row: the query string against all {rep.n} strings), "
+              f"{args.steps} steps")
+    line = {
+        "impl": "reference",
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+        "config": dict(workload_config(args, "cpu-oracle"), inputs_resident=False, l2="not applicable (host)"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# ours
+
+def tile_ops_per_pair(lengths):
+    """Algorithmic 32-bit integer operations of the tile test, summed over the
+    candidate pairs of every bucket pair (tile kernel)."""
+    cnt = np.bincount(lengths, minlength=50).astype(np.float64)
+    ops = 0.0
+    pairs = 0.0
+    for L in range(1, 49):
+        nl = cnt[L]
+        if nl == 0:
+            continue
+        W = math.ceil(L / 6)
+        same = nl * (nl - 1) / 2
+        ops += same * (6 * W + 3)
+        pairs += same
+        if L + 1 < 50 and cnt[L + 1] > 0:
+            W1 = math.ceil((L + 1) / 6)
+            ind = nl * cnt[L + 1]
+            ops += ind * (12 * W1 + 4)
+            pairs += ind
+    return ops, pairs
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2112_06613_b300 as tn
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group(backend="nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    hbm_peak, sm_max_nominal, peak_kind = load_peaks()
+
+    rep = workload(args.n, rank)
+    chars = torch.from_numpy(rep.chars).to(dev)
+    offs = torch.from_numpy(rep.offsets).to(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def build(method=args.method, profile=True):
+        return tn.tcrnet_build_flat(chars, offs, 1, method=method, stream=stream, profile=profile)
+
+    for _ in range(args.warmup):
+        build().free()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        evs[k][0].record(stream)
+        g = build()
+        evs[k][1].record(stream)
+        stats.append(g.stats())
+        g.free()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = statistics.mean(step_ms)
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    st0 = stats[-1]
+    n = args.n
+    pairs_per_build = n * (n - 1) / 2
+    edges = st0["nnz"] / 2
+    value = world * pairs_per_build / (ms / 1e3)
+    edges_per_s = world * edges / (ms / 1e3)
+    launches = int(sum(s["kernel_launches"] for s in stats))
+
+    is_tile = st0["method"] == 1
+    # dominant phase of the step and its algorithmic bytes
+    names = ["dedup", "records", "join_count", "join_write", "degrees", "fill", "row_sort"]
+    phase_ms = {nm: statistics.mean(s["ms_phase"][i] for s in stats) for i, nm in enumerate(names)}
+    if is_tile:
+        phase_ms = {"count_pass": statistics.mean(s["ms_count"] for s in stats),
+                    "write_pass": statistics.mean(s["ms_write"] for s in stats),
+                    "row_sort": statistics.mean(s["ms_sort"] for s in stats)}
+    dom = max(phase_ms, key=phase_ms.get)
+    nnz = st0["nnz"]
+    U, R, E = st0["n_unique"], st0["n_records"], st0["unique_edges"]
+    alg_bytes = 1 if is_tile else {
+        "row_sort": 8 * nnz + 8 * (n + 1),                 # read + write cols, read offsets
+        "fill": 4 * nnz + 4 * n + 8 * (n + 1) + 8 * E,     # write cols, read members/offsets/edges
+        "join_count": 4 * R + 32 * U,                      # read records and distinct strings
+        "join_write": 4 * R + 32 * U + 8 * E,              # + write edges
+        "records": 32 * U + 8 * R,                         # read strings, count + scatter records
+        "dedup": 32 * n + 32 * U + 8 * n,
+        "degrees": 8 * E + 8 * n + 8 * (n + 1),
+    }[dom]
+    achieved = alg_bytes / (phase_ms[dom] / 1e3) / 1e9
+    if is_tile:
+        ops, _ = tile_ops_per_pair(rep.lengths())
+        peak_ops = SMS * INT_LANES_PER_SM * sm_max_nominal * 1e6
+        ach = ops / (phase_ms[dom] / 1e3)
+        roofline_tile = {"bound": "alu", "kernel_phase": dom, "achieved": ach / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "Tops/s", "frac": ach / peak_ops, "traffic": None, "ms_per_launch": phase_ms[dom]}
+    roofline = {"bound": "hbm", "kernel_phase": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs",
+                "alg_bytes_per_launch": alg_bytes, "ms_per_launch": phase_ms[dom]}
+    if is_tile:
+        roofline = roofline_tile
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": workload_config(args, "deletion" if st0["method"] == 2 else "tile"),
+        "edges_per_s": edges_per_s, "edges_per_build": edges, "nnz": nnz,
+        "wall_s_timed_region": wall, "phases_ms": phase_ms, "roofline": roofline,
+        "gpu_launches": launches, "clocks": clocks,
+    }
+
+    if rank == 0 and not args.no_extras:
+        # --- tile kernel: candidate pair tests per second vs the integer ALU roofline
+        lens = rep.lengths()
+        ops, pairs = tile_ops_per_pair(lens)
+        tstats = []
+        build(method="tile").free()
+        for _ in range(args.tile_steps):
+            flush.fill_(1)
+            g = build(method="tile")
+            tstats.append(g.stats())
+            g.free()
+        cnt_ms = statistics.mean(s["ms_count"] for s in tstats)
+        tot_ms = statistics.mean(s["ms_total"] for s in tstats)
+        cand = tstats[0]["candidate_pairs"]
+        clk = (clocks or {}).get("sm_mhz") or sm_max_nominal
+        peak_ops = SMS * INT_LANES_PER_SM * sm_max_nominal * 1e6
+        peak_ops_clk = SMS * INT_LANES_PER_SM * clk * 1e6
+        ach_ops = ops / (cnt_ms / 1e3)
+        line["tile"] = {
+            "candidate_pairs": cand, "count_pass_ms": cnt_ms, "build_ms": tot_ms,
+            "candidate_pairs_per_s": cand / (cnt_ms / 1e3),
+            "all_pairs_per_s_build": pairs_per_build / (tot_ms / 1e3),
+            "roofline": {"bound": "alu", "achieved": ach_ops / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+                         "frac": ach_ops / peak_ops, "frac_at_sampled_clock": ach_ops / peak_ops_clk,
+                         "ops_per_launch": ops, "peak_basis": f"{SMS} SMs x {INT_LANES_PER_SM} int32 lanes x "
+                                                               f"{sm_max_nominal:.0f} MHz"},
+        }
+        # --- queries against the resident repertoire (host in, host out)
+        from synthgen import generate_config2
+
+        qsrc = generate_config2(200_000, seed=1000 + rank)
+        qstr_off = qsrc.offsets
+        rng = np.random.default_rng(7)
+        resident = build(profile=False)
+        lat, qn = [], []
+        for b in range(args.query_batches + 2):
+            m = int(round(math.exp(rng.uniform(0, math.log(50_000)))))
+            start = int(rng.integers(0, qsrc.n - m))
+            qo = (qstr_off[start:start + m + 1] - qstr_off[start]).astype(np.int64)
+            qc = qsrc.chars[qstr_off[start]:qstr_off[start + m]]
+            t = time.perf_counter()
+            r = resident.query_flat(qc, qo)
+            r.copy_csr()
+            dt = time.perf_counter() - t
+            r.free()
+            if b >= 2:
+                lat.append(dt * 1e3)
+                qn.append(m)
+        resident.free()
+        line["query"] = {"batches": len(lat), "batch_size": "log-uniform 1..50000", "p50_ms": float(np.percentile(lat, 50)),
+                         "p99_ms": float(np.percentile(lat, 99)), "queries_per_s": sum(qn) / (sum(lat) / 1e3),
+                         "method": "tile kernel against buckets L-1, L, L+1"}
+        # --- end to end: pinned host inputs in, CSR back in pinned host memory
+        hc = torch.from_numpy(rep.chars).pin_memory()
+        ho = torch.from_numpy(rep.offsets).pin_memory()
+        off_h = torch.empty(n + 1, dtype=torch.int32).pin_memory()
+        cols_h = torch.empty(max(nnz, 1), dtype=torch.int32).pin_memory()
+        deg_h = torch.empty(n, dtype=torch.int32).pin_memory()
+        e2e_ms = []
+        for k in range(args.e2e_steps + 2):
+            flush.fill_(2)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            g = tn.tcrnet_build_flat(hc, ho, 1, method=args.method, stream=stream)
+            g.copy_csr(out=(off_h, cols_h, deg_h))
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t
+            g.free()
+            if k >= 2:
+                e2e_ms.append(dt * 1e3)
+        e_ms = statistics.mean(e2e_ms)
+        line["e2e"] = {"value": pairs_per_build / (e_ms / 1e3), "unit": UNIT, "ms_per_step": e_ms,
+                       "h2d_bytes_per_step": int(rep.chars.nbytes + rep.offsets.nbytes),
+                       "d2h_bytes_per_step": int(4 * (n + 1) + 4 * nnz + 4 * n)}
+        # --- CPU oracle on a bounded sample (rank 0, one GPU only)
+        if world == 1 and args.cpu_seconds > 0:
+            rate, cores, rows, el = oracle_rate(rep, args.cpu_seconds)
+            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                    "sample": f"{rows} seeded rows of the N={n} network, each the full "
+                                              f"Wagner-Fischer scan against all {n} strings ({el:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

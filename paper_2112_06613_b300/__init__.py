@@ -54,6 +54,7 @@ class tcrnet_stats(ctypes.Structure):
         ("n_records", ctypes.c_int64),
         ("unique_edges", ctypes.c_int64),
         ("n_fallback", ctypes.c_int64),
+        ("kernel_launches", ctypes.c_int64),
         ("ms_upload", ctypes.c_double),
         ("ms_pack", ctypes.c_double),
         ("ms_count", ctypes.c_double),

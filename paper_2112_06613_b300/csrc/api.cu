@@ -35,6 +35,10 @@ struct tcrnet_graph {
 namespace tcr {
 
 static thread_local int64_t t_last_bad = -1;
+static thread_local int64_t t_launches = 0;
+
+void note_launch() { ++t_launches; }
+int64_t launches_so_far() { return t_launches; }
 static thread_local char t_last_cuda[256] = {0};
 
 void note_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
@@ -264,6 +268,7 @@ tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n
     h->stats.n = n;
 
     Phases ph(opt.profile != 0, s);
+    const int64_t launches0 = launches_so_far();
     auto fail = [&](tcrnet_status st) {
         cudaStreamSynchronize(s);
         free_handle_memory(h);
@@ -323,6 +328,7 @@ tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n
     const int p3 = ph.mark();
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(TCRNET_EDEVICE);
     h->stats.nnz = h->nnz;
+    h->stats.kernel_launches = launches_so_far() - launches0;
     h->stats.ms_upload = ph.ms(p0, p1);
     h->stats.ms_pack = ph.ms(p1, p2);
     h->stats.ms_total = ph.ms(p0, p3);
@@ -419,6 +425,7 @@ tcrnet_status tcrnet_query_flat(tcrnet_handle h, const uint8_t* chars, const int
         return st;
     };
     Phases ph(false, s);
+    const int64_t launches0 = launches_so_far();
     Inputs in;
     tcrnet_status st = stage_inputs(chars, offsets, m, mem, in, s);
     if (st != TCRNET_OK) return fail(st);
@@ -444,6 +451,7 @@ tcrnet_status tcrnet_query_flat(tcrnet_handle h, const uint8_t* chars, const int
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(TCRNET_EDEVICE);
     r->stats.nnz = r->nnz;
+    r->stats.kernel_launches = launches_so_far() - launches0;
     *out = r;
     return TCRNET_OK;
 }

@@ -91,7 +91,15 @@ inline tcrnet_status status_of(cudaError_t e) {
         if (s_ != TCRNET_OK) return s_;                                 \
     } while (0)
 
-#define TCR_LAUNCH_CHECK() TCR_CUDA(cudaGetLastError())
+// Counts kernel launches of the calling thread (reported in tcrnet_stats).
+void note_launch();
+int64_t launches_so_far();
+
+#define TCR_LAUNCH_CHECK()      \
+    do {                        \
+        ::tcr::note_launch();   \
+        TCR_CUDA(cudaGetLastError()); \
+    } while (0)
 
 // Stream-ordered device buffer (cudaMallocAsync / cudaFreeAsync). Freed when it
 // goes out of scope unless released.
