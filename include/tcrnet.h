@@ -59,7 +59,8 @@ typedef enum tcrnet_status {
     TCRNET_ENOMEM = 5,    /* device or host allocation failed; nothing leaked */
     TCRNET_EDEVICE = 6,   /* a CUDA error; the handle is poisoned */
     TCRNET_ETIMEOUT = 7,  /* a bounded device wait ran out; the handle is poisoned */
-    TCRNET_ESTATE = 8     /* the handle cannot serve this call (e.g. query on a query result) */
+    TCRNET_ESTATE = 8,    /* the handle cannot serve this call (e.g. query on a query result) */
+    TCRNET_ECAPACITY = 9  /* input larger than a fixed-capacity entry point accepts */
 } tcrnet_status;
 
 typedef enum tcrnet_method {
@@ -183,6 +184,41 @@ const char *tcrnet_version(void);
 
 /* Text of the calling thread's last failing CUDA call (diagnostics; "" if none). */
 const char *tcrnet_last_cuda_error(void);
+
+/* Largest n tcrnet_degree_noalloc accepts. */
+#define TCRNET_NOALLOC_MAX_N 16384
+
+/*
+ * Node degrees of the network of at most TCRNET_NOALLOC_MAX_N strings, without
+ * allocating any memory. The paper has no counterpart: this entry point exists
+ * for callers that cannot call cudaMalloc (code running while a CUDA graph is
+ * being captured, programs whose device memory is fully reserved up front by
+ * another allocator, hosts that forbid allocation after start-up).
+ *
+ * d_chars / d_offsets: the flat string layout of tcrnet_build_flat, in device
+ * memory of the calling thread's current device. d_degree: device output of n
+ * int32, overwritten with d(i) = number of j != i with lev(s_i, s_j) <=
+ * threshold (threshold 0 or 1); equal to tcrnet_copy_csr's degree for the same
+ * input. stream: cudaStream_t (NULL = legacy default stream). bad_index
+ * (optional host pointer) receives the offending input index on
+ * EBADCHAR / ETOOLONG / EINVAL, else -1. The call returns when the result is
+ * complete.
+ *
+ * Errors: TCRNET_ECAPACITY if n > TCRNET_NOALLOC_MAX_N (nothing runs);
+ * EINVAL / ENOTSUP for bad arguments; EBADCHAR / ETOOLONG / EINVAL for bad
+ * strings; EDEVICE for a CUDA error.
+ *
+ * Working memory is one fixed file-scope device array of about 0.5 MB that
+ * every device loading the library keeps until the process exits. The first
+ * call on each device looks up that array's device address (a one-time set-up
+ * step), so make the first call on a device before any stream capture. All
+ * calls share the array and it keeps the previous call's contents (each call
+ * clears what must start at zero), so calls that overlap on the GPU, from
+ * different streams or host threads, race: serialise them.
+ */
+tcrnet_status tcrnet_degree_noalloc(const uint8_t *d_chars, const int64_t *d_offsets, int64_t n,
+                                    int32_t threshold, int32_t *d_degree, void *stream,
+                                    int64_t *bad_index);
 
 #ifdef __cplusplus
 }

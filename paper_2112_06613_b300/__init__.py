@@ -24,8 +24,10 @@ HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "tcrnet.h")
 
 MAX_LEN = 48
 
-OK, EINVAL, EBADCHAR, ETOOLONG, ENOTSUP, ENOMEM, EDEVICE, ETIMEOUT, ESTATE = range(9)
-STATUS_NAMES = ["OK", "EINVAL", "EBADCHAR", "ETOOLONG", "ENOTSUP", "ENOMEM", "EDEVICE", "ETIMEOUT", "ESTATE"]
+OK, EINVAL, EBADCHAR, ETOOLONG, ENOTSUP, ENOMEM, EDEVICE, ETIMEOUT, ESTATE, ECAPACITY = range(10)
+STATUS_NAMES = ["OK", "EINVAL", "EBADCHAR", "ETOOLONG", "ENOTSUP", "ENOMEM", "EDEVICE", "ETIMEOUT", "ESTATE",
+                "ECAPACITY"]
+NOALLOC_MAX_N = 16384
 METHOD_AUTO, METHOD_TILE, METHOD_DELETION = 0, 1, 2
 METHODS = {"auto": METHOD_AUTO, "tile": METHOD_TILE, "deletion": METHOD_DELETION}
 HOST, DEVICE = 0, 1
@@ -92,6 +94,7 @@ SYMBOLS = [
     "tcrnet_options_init", "tcrnet_build", "tcrnet_build_flat", "tcrnet_info", "tcrnet_copy_csr",
     "tcrnet_csr_device", "tcrnet_query_flat", "tcrnet_query", "tcrnet_stats_get", "tcrnet_free",
     "tcrnet_strerror", "tcrnet_last_error_index", "tcrnet_version", "tcrnet_last_cuda_error",
+    "tcrnet_degree_noalloc",
 ]
 
 
@@ -138,6 +141,8 @@ def load_library(path: str = LIB_PATH):
         lib.tcrnet_version.restype = ctypes.c_char_p
         lib.tcrnet_last_cuda_error.argtypes = []
         lib.tcrnet_last_cuda_error.restype = ctypes.c_char_p
+        lib.tcrnet_degree_noalloc.argtypes = [vp, vp, i64, i32, vp, vp, ctypes.POINTER(i64)]
+        lib.tcrnet_degree_noalloc.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -324,3 +329,19 @@ def tcrnet_strerror(status: int) -> str:
 
 def tcrnet_version() -> str:
     return load_library().tcrnet_version().decode()
+
+
+def tcrnet_degree_noalloc(chars, offsets, degree, threshold: int = 1, stream=None) -> None:
+    """Node degrees into the preallocated device tensor `degree` (int32, n), for
+    callers that cannot allocate: torch CUDA tensors in, nothing allocated by
+    the library (see include/tcrnet.h). At most NOALLOC_MAX_N strings."""
+    import torch
+
+    assert chars.is_cuda and offsets.is_cuda and degree.is_cuda
+    assert chars.dtype == torch.uint8 and offsets.dtype == torch.int64 and degree.dtype == torch.int32
+    n = offsets.numel() - 1
+    bad = ctypes.c_int64(-1)
+    st = load_library().tcrnet_degree_noalloc(chars.data_ptr(), offsets.data_ptr(), n, int(threshold),
+                                              degree.data_ptr(), _stream_ptr(stream), ctypes.byref(bad))
+    if st != OK:
+        raise TcrnetError(st, "tcrnet_degree_noalloc", int(bad.value))

@@ -492,6 +492,7 @@ const char* tcrnet_strerror(tcrnet_status s) {
         case TCRNET_EDEVICE: return "CUDA device error";
         case TCRNET_ETIMEOUT: return "bounded device wait timed out";
         case TCRNET_ESTATE: return "handle cannot serve this call";
+        case TCRNET_ECAPACITY: return "input larger than this fixed-capacity entry point accepts";
         default: return "unknown status";
     }
 }
