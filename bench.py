@@ -305,7 +305,7 @@ def run_ours(args):
 
     is_tile = st0["method"] == 1
     # dominant phase of the step and its algorithmic bytes
-    names = ["dedup", "records", "join_count", "join_write", "degrees", "fill", "row_sort"]
+    names = ["dedup", "records", "join_count", "join_write", "closed_fill", "closed_sort", "expand"]
     phase_ms = {nm: statistics.mean(s["ms_phase"][i] for s in stats) for i, nm in enumerate(names)}
     if is_tile:
         phase_ms = {"count_pass": statistics.mean(s["ms_count"] for s in stats),
@@ -313,15 +313,15 @@ def run_ours(args):
                     "row_sort": statistics.mean(s["ms_sort"] for s in stats)}
     dom = max(phase_ms, key=phase_ms.get)
     nnz = st0["nnz"]
-    U, R, E = st0["n_unique"], st0["n_records"], st0["unique_edges"]
+    U, R, E, SD = st0["n_unique"], st0["n_records"], st0["unique_edges"], st0["closed_total"]
     alg_bytes = 1 if is_tile else {
-        "row_sort": 8 * nnz + 8 * (n + 1),                 # read + write cols, read offsets
-        "fill": 4 * nnz + 4 * n + 8 * (n + 1) + 8 * E,     # write cols, read members/offsets/edges
-        "join_count": 4 * R + 32 * U,                      # read records and distinct strings
-        "join_write": 4 * R + 32 * U + 8 * E,              # + write edges
-        "records": 32 * U + 8 * R,                         # read strings, count + scatter records
+        "expand": 4 * nnz + 4 * SD + 8 * (n + 1) + 4 * n,  # write cols; read lists, offsets, ids
+        "closed_sort": 8 * SD + 8 * (U + 1),              # read + write lists, read offsets
+        "closed_fill": 16 * E + 8 * SD + 8 * (U + 1),     # read edges (x2), members; write lists
+        "join_count": 8 * R,                              # read records
+        "join_write": 8 * R + 8 * E,                      # + write edges
+        "records": 32 * U + 8 * R,                        # read strings, scatter records
         "dedup": 32 * n + 32 * U + 8 * n,
-        "degrees": 8 * E + 8 * n + 8 * (n + 1),
     }[dom]
     achieved = alg_bytes / (phase_ms[dom] / 1e3) / 1e9
     if is_tile:

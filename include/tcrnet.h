@@ -101,6 +101,7 @@ typedef struct tcrnet_stats {
     int64_t unique_edges;     /* edges among distinct strings (deletion path) */
     int64_t n_fallback;       /* deletion-join partitions joined by the exact fallback */
     int64_t kernel_launches;  /* CUDA kernels this call launched */
+    int64_t closed_total;     /* deletion path: sum over distinct strings of |closed neighbourhood| */
     double ms_upload;         /* host -> device copy of the input (host inputs only) */
     double ms_pack;           /* validate, encode, bucket */
     double ms_count;          /* tile count pass / deletion join count */

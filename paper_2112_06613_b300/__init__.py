@@ -57,6 +57,7 @@ class tcrnet_stats(ctypes.Structure):
         ("unique_edges", ctypes.c_int64),
         ("n_fallback", ctypes.c_int64),
         ("kernel_launches", ctypes.c_int64),
+        ("closed_total", ctypes.c_int64),
         ("ms_upload", ctypes.c_double),
         ("ms_pack", ctypes.c_double),
         ("ms_count", ctypes.c_double),

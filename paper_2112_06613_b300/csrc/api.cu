@@ -314,6 +314,7 @@ tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n
         h->stats.n_records = dr.n_records;
         h->stats.unique_edges = dr.unique_edges;
         h->stats.n_fallback = dr.n_fallback;
+        h->stats.closed_total = dr.closed_total;
         h->stats.ms_count = dr.ms_join;
         h->stats.ms_scan = dr.ms_scan;
         h->stats.ms_write = dr.ms_fill;

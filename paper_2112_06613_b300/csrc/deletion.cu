@@ -21,21 +21,27 @@
 //  1. dedup: open-addressing hash table of the packed strings (slot claimed by
 //     atomicCAS, exact comparison on probe) -> distinct-string ids u,
 //     multiplicities m_u, member lists M_u.
-//  2. records: per distinct string one full-string record F (tag 63) and one
-//     record per deletion position p (with a run-start flag), each a 32-bit
-//     word (u << 7 | runstart << 6 | p); they are hash-partitioned by the
-//     content they stand for (two passes: count, scatter).
-//  3. join: one block per partition loads its records into shared memory,
-//     keys each by (56-bit content hash | p), sorts (bitonic), checks that
-//     equal hashes are equal contents (exact), and emits edges between
-//     distinct strings: every pair inside a run of equal keys (equal length,
-//     one substitution), and each run-start deletion record with the full
-//     record of the same content (one indel). Count pass, exclusive scan,
-//     write pass (a block prefix sum gives each thread its slots). Partitions
-//     over capacity or with a hash collision take an exact quadratic fallback.
-//  4. degrees: deg(i) = m_u - 1 + sum over distinct neighbours v of m_v.
-//  5. fill: all members of u share one row layout (self clique first, then
-//     one cursor per distinct string), then rows are sorted (rowsort.cu).
+//  2. records: per distinct string one full-string record (tag p = 63) and one
+//     record per deletion position p; each is one 64-bit word
+//       bits 63..32  low 32 bits of the content hash
+//       bits 31..26  p (63: the full string)
+//       bit  25      p starts a run of equal letters
+//       bits 24..0   u
+//     hash-partitioned (high hash bits, ~32 records per partition) in two
+//     passes (count, scatter).
+//  3. join: one warp per partition sorts its words in registers (bitonic
+//     network), confirms that equal hashes are equal contents (exact), and
+//     emits edges between distinct strings: every pair inside a run of equal
+//     (hash, p) (equal length, one substitution), and each run-start deletion
+//     record with the full record of the same content (one indel). Count pass,
+//     exclusive scan, write pass (warp prefix sums give each lane its slots).
+//     Partitions over capacity or with a hash collision take an exact
+//     quadratic fallback.
+//  4. closed neighbourhoods: D_u = m_u + sum over distinct neighbours v of
+//     m_v; S_u = M_u followed by every M_v, written once per distinct string
+//     and sorted (rowsort.cu). A node i of u has degree D_u - 1.
+//  5. expand: row i of the CSR is S_u without i (a streaming copy), so the
+//     long rows of frequent strings are sorted once, not once per copy.
 #include <algorithm>
 #include <vector>
 
@@ -45,10 +51,15 @@ namespace tcr {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kCap = 2048;        // records per partition joined in shared memory
-constexpr int kTargetPart = 256;  // mean records per partition
+constexpr int kWarps = kThreads / 32;
+constexpr int kWarpCap = 128;     // records per partition joined by one warp
+constexpr int kTargetPart = 32;   // mean records per partition
 constexpr uint32_t kTagF = 63;    // position tag of a full-string record
-constexpr int kHeavy = 32;        // m_u * m_v above this: a warp fills the edge
+constexpr uint64_t kUMask = (1ull << 25) - 1;
+
+__device__ __forceinline__ uint32_t rec_u(uint64_t r) { return (uint32_t)(r & kUMask); }
+__device__ __forceinline__ uint32_t rec_p(uint64_t r) { return (uint32_t)(r >> 26) & 63u; }
+__device__ __forceinline__ bool rec_runstart(uint64_t r) { return (r >> 25) & 1ull; }
 
 // 64-bit finaliser of MurmurHash3 (public domain).
 __device__ __forceinline__ uint64_t fmix64(uint64_t x) {
@@ -97,20 +108,14 @@ __device__ __forceinline__ bool run_start(const Canon& c, int p) {
     return p == 0 || code_at(c, p) != code_at(c, p - 1);
 }
 
-__device__ __forceinline__ Canon record_content(uint32_t rec, const Canon* __restrict__ ucanon) {
-    const Canon c = load_canon(ucanon + (rec >> 7));
-    const int p = (int)(rec & 63u);
-    return p == (int)kTagF ? c : delete_at(c, p);
+__device__ __forceinline__ Canon record_content(uint64_t rec, const Canon* __restrict__ ucanon) {
+    const Canon c = load_canon(ucanon + rec_u(rec));
+    const uint32_t p = rec_p(rec);
+    return p == kTagF ? c : delete_at(c, (int)p);
 }
 
 __device__ __forceinline__ uint32_t part_of(uint64_t h, uint32_t P) {
     return (uint32_t)(((h >> 32) * (uint64_t)P) >> 32);
-}
-
-__device__ __forceinline__ int next_pow2(int x) {
-    int p = 1;
-    while (p < x) p <<= 1;
-    return p;
 }
 
 inline unsigned grid_for(int64_t n, int threads = kThreads) {
@@ -130,19 +135,31 @@ __device__ __forceinline__ int64_t block_scan(int64_t v, int64_t& excl, int64_t*
     if (lane == 31) wtot[warp] = x;
     __syncthreads();
     if (warp == 0) {
-        int64_t t = lane < kThreads / 32 ? wtot[lane] : 0;
+        int64_t t = lane < kWarps ? wtot[lane] : 0;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const int64_t y = __shfl_up_sync(kFull, t, d);
             if (lane >= d) t += y;
         }
-        if (lane < kThreads / 32) wtot[lane] = t;
+        if (lane < kWarps) wtot[lane] = t;
     }
     __syncthreads();
     excl = (warp ? wtot[warp - 1] : 0) + x - v;
-    const int64_t total = wtot[kThreads / 32 - 1];
+    const int64_t total = wtot[kWarps - 1];
     __syncthreads();
     return total;
+}
+
+// Warp-wide exclusive scan of one int64 per lane; returns the warp total.
+__device__ __forceinline__ int64_t warp_scan(int64_t v, int64_t& excl, int lane) {
+    int64_t x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int64_t y = __shfl_up_sync(kFull, x, d);
+        if (lane >= d) x += y;
+    }
+    excl = x - v;
+    return __shfl_sync(kFull, x, 31);
 }
 
 // ---- 1. dedup -------------------------------------------------------------
@@ -194,63 +211,110 @@ __global__ void k_uid(const int32_t* __restrict__ slot_of, const int64_t* __rest
     }
 }
 
+// Member lists M_u (arrival order) and each node's position inside its list.
 __global__ void k_members(const int32_t* __restrict__ uid, int64_t n, const int64_t* __restrict__ mem_off,
-                          int32_t* __restrict__ mcur, int32_t* __restrict__ members) {
+                          int32_t* __restrict__ mcur, int32_t* __restrict__ members, int32_t* __restrict__ mpos) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int32_t u = uid[i];
-    members[mem_off[u] + atomicAdd(&mcur[u], 1)] = (int32_t)i;
+    const int32_t k = atomicAdd(&mcur[u], 1);
+    members[mem_off[u] + k] = (int32_t)i;
+    mpos[i] = k;
 }
 
 // ---- 2. records -----------------------------------------------------------
 
 template <bool SCATTER>
 __global__ void k_records(const Canon* __restrict__ ucanon, const uint8_t* __restrict__ ulen, int64_t U, uint32_t P,
-                          int32_t* __restrict__ pcnt, const int64_t* __restrict__ poff, uint32_t* __restrict__ recs) {
+                          int32_t* __restrict__ pcnt, const int64_t* __restrict__ poff, uint64_t* __restrict__ recs) {
     const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= U) return;
     const Canon c = load_canon(ucanon + u);
     const int L = ulen[u];
     for (int p = -1; p < L; ++p) {
         const bool full = p < 0;
-        const Canon d = full ? c : delete_at(c, p);
-        const uint32_t pid = part_of(hash_canon(d), P);
+        const uint64_t h = hash_canon(full ? c : delete_at(c, p));
+        const uint32_t pid = part_of(h, P);
         if (!SCATTER) {
             atomicAdd(&pcnt[pid], 1);
         } else {
-            const uint32_t tag = full ? kTagF : ((run_start(c, p) ? 64u : 0u) | (uint32_t)p);
+            const uint64_t tag = full ? ((uint64_t)kTagF << 26)
+                                      : (((uint64_t)p << 26) | (run_start(c, p) ? (1ull << 25) : 0ull));
             const int32_t slot = atomicAdd(&pcnt[pid], 1);
-            recs[poff[pid] + slot] = ((uint32_t)u << 7) | tag;
+            recs[poff[pid] + slot] = (h << 32) | tag | (uint64_t)u;
         }
     }
 }
 
 // ---- 3. join --------------------------------------------------------------
 
-struct JoinSmem {
-    uint64_t key[kCap];
-    uint32_t rec[kCap];
-    int64_t wtot[kThreads / 32];
-    int flag;
-};
+// Bitonic sort of 32*K words held K per lane (network position lane*K + r).
+template <int K>
+__device__ __forceinline__ void warp_sort_u64(uint64_t (&v)[K], int lane) {
+    constexpr int P = 32 * K;
+#pragma unroll
+    for (int k = 2; k <= P; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j < K) {
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    if ((r & j) == 0) {
+                        const int r2 = r | j;
+                        const bool up = ((lane * K + r) & k) == 0;
+                        const uint64_t a = v[r], b = v[r2];
+                        const bool sw = (a > b) == up;
+                        v[r] = sw ? b : a;
+                        v[r2] = sw ? a : b;
+                    }
+                }
+            } else {
+                const int jl = j / K;
+                const bool lower = (lane & jl) == 0;
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    const uint64_t p = __shfl_xor_sync(kFull, v[r], jl);
+                    const bool up = ((lane * K + r) & k) == 0;
+                    const uint64_t mn = v[r] < p ? v[r] : p;
+                    const uint64_t mx = v[r] < p ? p : v[r];
+                    v[r] = (lower == up) ? mn : mx;
+                }
+            }
+        }
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void load_sort_store(const uint64_t* __restrict__ src, int s, uint64_t* buf, int lane) {
+    uint64_t v[K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const int e = r * 32 + lane;
+        v[r] = e < s ? src[e] : ~0ull;  // ~0 is never a record (full records have no run-start bit)
+    }
+    warp_sort_u64<K>(v, lane);
+#pragma unroll
+    for (int r = 0; r < K; ++r) buf[lane * K + r] = v[r];
+}
 
 // Edges initiated by sorted record k (see the file comment); calls emit(a, b).
 template <typename Emit>
-__device__ __forceinline__ int64_t record_edges(const JoinSmem& sm, int k, int s, int T, Emit emit) {
-    const uint64_t key = sm.key[k];
-    if ((key & 0xffu) == kTagF) return 0;
-    const int32_t u = (int32_t)(sm.rec[k] >> 7);
+__device__ __forceinline__ int64_t record_edges(const uint64_t* buf, int k, int s, int T, Emit emit) {
+    const uint64_t key = buf[k];
+    if (rec_p(key) == kTagF) return 0;
+    const uint32_t u = rec_u(key);
     int64_t cnt = 0;
     int k2 = k + 1;
-    for (; k2 < s && sm.key[k2] == key; ++k2) {  // same content, same deleted position
-        emit(u, (int32_t)(sm.rec[k2] >> 7));
+    for (; k2 < s && (buf[k2] >> 26) == (key >> 26); ++k2) {  // same content, same deleted position
+        emit((int32_t)u, (int32_t)rec_u(buf[k2]));
         ++cnt;
     }
-    if (T >= 1 && ((sm.rec[k] >> 6) & 1u)) {  // run-start deletion: look for the full record
+    if (T >= 1 && rec_runstart(key)) {  // run-start deletion: look for the full record
         int g = k2;
-        while (g < s && (sm.key[g] >> 8) == (key >> 8)) ++g;
-        if ((sm.key[g - 1] & 0xffu) == kTagF) {
-            emit((int32_t)(sm.rec[g - 1] >> 7), u);
+        while (g < s && (buf[g] >> 32) == (key >> 32)) ++g;
+        const uint64_t last = buf[g - 1];
+        if (rec_p(last) == kTagF) {
+            emit((int32_t)rec_u(last), (int32_t)u);
             ++cnt;
         }
     }
@@ -259,17 +323,19 @@ __device__ __forceinline__ int64_t record_edges(const JoinSmem& sm, int k, int s
 
 template <bool WRITE>
 __global__ void __launch_bounds__(kThreads)
-k_join(const int64_t* __restrict__ poff, int64_t P, const uint32_t* __restrict__ recs,
+k_join(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __restrict__ recs,
        const Canon* __restrict__ ucanon, int cap, int T, int64_t* __restrict__ pedges,
        const int64_t* __restrict__ eoff, int2* __restrict__ edges, int32_t* __restrict__ fb_list,
        int* __restrict__ fb_count) {
-    __shared__ JoinSmem sm;
-    const int tid = threadIdx.x;
-    for (int64_t pid = blockIdx.x; pid < P; pid += gridDim.x) {
+    __shared__ uint64_t sbuf[kWarps][kWarpCap];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t* buf = sbuf[warp];
+    const int64_t stride = (int64_t)gridDim.x * kWarps;
+    for (int64_t pid = (int64_t)blockIdx.x * kWarps + warp; pid < P; pid += stride) {
         const int64_t base = poff[pid];
         const int64_t s64 = poff[pid + 1] - base;
         if (s64 > cap) {
-            if (!WRITE && tid == 0) {
+            if (!WRITE && lane == 0) {
                 fb_list[atomicAdd(fb_count, 1)] = (int32_t)pid;
                 pedges[pid] = 0;
             }
@@ -277,69 +343,40 @@ k_join(const int64_t* __restrict__ poff, int64_t P, const uint32_t* __restrict__
         }
         const int s = (int)s64;
         if (s < 2) {
-            if (!WRITE && tid == 0) pedges[pid] = 0;
+            if (!WRITE && lane == 0) pedges[pid] = 0;
             continue;
         }
-        const int Pp = next_pow2(s);
-        for (int k = tid; k < Pp; k += kThreads) {
-            if (k < s) {
-                const uint32_t r = recs[base + k];
-                const uint64_t h = hash_canon(record_content(r, ucanon));
-                sm.key[k] = (h & ~0xffull) | (r & 63u);
-                sm.rec[k] = r;
-            } else {
-                sm.key[k] = ~0ull;
-                sm.rec[k] = 0;
-            }
+        if (s <= 32) load_sort_store<1>(recs + base, s, buf, lane);
+        else if (s <= 64) load_sort_store<2>(recs + base, s, buf, lane);
+        else load_sort_store<4>(recs + base, s, buf, lane);
+        __syncwarp();
+        // equal 32-bit hashes must be equal contents; otherwise the exact fallback
+        bool bad = false;
+        for (int k = lane + 1; k < s; k += 32) {
+            if ((buf[k] >> 32) == (buf[k - 1] >> 32) &&
+                !canon_eq(record_content(buf[k], ucanon), record_content(buf[k - 1], ucanon)))
+                bad = true;
         }
-        if (tid == 0) sm.flag = 0;
-        __syncthreads();
-        // bitonic sort of (key, rec) ascending by key
-        for (int kk = 2; kk <= Pp; kk <<= 1) {
-            for (int j = kk >> 1; j > 0; j >>= 1) {
-                for (int i = tid; i < (Pp >> 1); i += kThreads) {
-                    const int lo = 2 * j * (i / j) + (i % j);
-                    const int hi = lo + j;
-                    const bool up = (lo & kk) == 0;
-                    const uint64_t x = sm.key[lo], y = sm.key[hi];
-                    if ((x > y) == up) {
-                        sm.key[lo] = y;
-                        sm.key[hi] = x;
-                        const uint32_t t = sm.rec[lo];
-                        sm.rec[lo] = sm.rec[hi];
-                        sm.rec[hi] = t;
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        // equal 56-bit hashes must be equal contents; otherwise the exact fallback
-        for (int k = tid + 1; k < s; k += kThreads) {
-            if ((sm.key[k] >> 8) == (sm.key[k - 1] >> 8) &&
-                !canon_eq(record_content(sm.rec[k], ucanon), record_content(sm.rec[k - 1], ucanon)))
-                sm.flag = 1;
-        }
-        __syncthreads();
-        if (sm.flag) {
-            if (!WRITE && tid == 0) {
+        if (__any_sync(kFull, bad)) {
+            if (!WRITE && lane == 0) {
                 fb_list[atomicAdd(fb_count, 1)] = (int32_t)pid;
                 pedges[pid] = 0;
             }
-            __syncthreads();
+            __syncwarp();
             continue;
         }
         int64_t mine = 0;
-        for (int k = tid; k < s; k += kThreads) mine += record_edges(sm, k, s, T, [](int32_t, int32_t) {});
+        for (int k = lane; k < s; k += 32) mine += record_edges(buf, k, s, T, [](int32_t, int32_t) {});
         int64_t excl;
-        const int64_t total = block_scan(mine, excl, sm.wtot);
+        const int64_t total = warp_scan(mine, excl, lane);
         if (!WRITE) {
-            if (tid == 0) pedges[pid] = total;
+            if (lane == 0) pedges[pid] = total;
         } else {
             int64_t pos = eoff[pid] + excl;
-            for (int k = tid; k < s; k += kThreads)
-                record_edges(sm, k, s, T, [&](int32_t a, int32_t b) { edges[pos++] = make_int2(a, b); });
+            for (int k = lane; k < s; k += 32)
+                record_edges(buf, k, s, T, [&](int32_t a, int32_t b) { edges[pos++] = make_int2(a, b); });
         }
-        __syncthreads();
+        __syncwarp();
     }
 }
 
@@ -347,9 +384,9 @@ k_join(const int64_t* __restrict__ poff, int64_t P, const uint32_t* __restrict__
 template <bool WRITE>
 __global__ void __launch_bounds__(kThreads)
 k_join_fallback(const int32_t* __restrict__ fb_list, int nfb, const int64_t* __restrict__ poff,
-                const uint32_t* __restrict__ recs, const Canon* __restrict__ ucanon, int T,
+                const uint64_t* __restrict__ recs, const Canon* __restrict__ ucanon, int T,
                 int64_t* __restrict__ pedges, const int64_t* __restrict__ eoff, int2* __restrict__ edges) {
-    __shared__ int64_t wtot[kThreads / 32];
+    __shared__ int64_t wtot[kWarps];
     for (int f = blockIdx.x; f < nfb; f += gridDim.x) {
         const int64_t pid = fb_list[f];
         const int64_t base = poff[pid];
@@ -357,21 +394,21 @@ k_join_fallback(const int32_t* __restrict__ fb_list, int nfb, const int64_t* __r
         auto scan_pairs = [&](auto emit) {
             int64_t cnt = 0;
             for (int64_t k1 = threadIdx.x; k1 < s; k1 += kThreads) {
-                const uint32_t r1 = recs[base + k1];
-                const uint32_t p1 = r1 & 63u;
+                const uint64_t r1 = recs[base + k1];
+                const uint32_t p1 = rec_p(r1);
                 if (p1 == kTagF) continue;  // deletion records initiate every edge
                 const Canon c1 = record_content(r1, ucanon);
-                const bool rs1 = (r1 >> 6) & 1u;
+                const bool rs1 = rec_runstart(r1);
                 for (int64_t k2 = 0; k2 < s; ++k2) {
                     if (k2 == k1) continue;
-                    const uint32_t r2 = recs[base + k2];
-                    const uint32_t p2 = r2 & 63u;
+                    const uint64_t r2 = recs[base + k2];
+                    const uint32_t p2 = rec_p(r2);
                     const bool same = (p2 == p1) && (k2 > k1);
                     const bool indel = (T >= 1) && rs1 && (p2 == kTagF);
                     if (!same && !indel) continue;
                     if (!canon_eq(c1, record_content(r2, ucanon))) continue;
-                    if (same) emit((int32_t)(r1 >> 7), (int32_t)(r2 >> 7));
-                    else emit((int32_t)(r2 >> 7), (int32_t)(r1 >> 7));
+                    if (same) emit((int32_t)rec_u(r1), (int32_t)rec_u(r2));
+                    else emit((int32_t)rec_u(r2), (int32_t)rec_u(r1));
                     ++cnt;
                 }
             }
@@ -390,7 +427,7 @@ k_join_fallback(const int32_t* __restrict__ fb_list, int nfb, const int64_t* __r
     }
 }
 
-// ---- 4. degrees -----------------------------------------------------------
+// ---- 4. closed neighbourhoods ---------------------------------------------
 
 __global__ void k_weighted_degree(const int2* __restrict__ edges, int64_t E, const int32_t* __restrict__ umult,
                                   int32_t* __restrict__ wsum) {
@@ -401,93 +438,69 @@ __global__ void k_weighted_degree(const int2* __restrict__ edges, int64_t E, con
     atomicAdd(&wsum[uv.y], umult[uv.x]);
 }
 
-__global__ void k_node_degree(const int32_t* __restrict__ uid, int64_t n, const int32_t* __restrict__ umult,
-                              const int32_t* __restrict__ wsum, int32_t* __restrict__ deg) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int32_t u = uid[i];
-    deg[i] = umult[u] - 1 + wsum[u];
-}
-
-// ---- 5. fill --------------------------------------------------------------
-
-__global__ void k_cursor_init(const int32_t* __restrict__ umult, int64_t U, int32_t* __restrict__ cur) {
+// D_u = m_u + W_u (written into wsum in place); cursor starts after M_u.
+__global__ void k_closed_size(const int32_t* __restrict__ umult, int64_t U, int32_t* __restrict__ wsum,
+                              int32_t* __restrict__ ucur) {
     const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (u < U) cur[u] = umult[u] - 1;
+    if (u >= U) return;
+    wsum[u] += umult[u];
+    ucur[u] = umult[u];
 }
 
-__global__ void k_fill_self(const int32_t* __restrict__ uid, int64_t n, const int32_t* __restrict__ umult,
-                            const int64_t* __restrict__ mem_off, const int32_t* __restrict__ members,
-                            const int64_t* __restrict__ off, int32_t* __restrict__ cols) {
+__global__ void k_node_degree(const int32_t* __restrict__ uid, int64_t n, const int32_t* __restrict__ dsize,
+                              int32_t* __restrict__ deg) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int32_t u = uid[i];
-    const int32_t m = umult[u];
-    if (m < 2) return;
-    const int64_t b = off[i];
-    const int32_t* mem = members + mem_off[u];
-    int32_t pos = 0;
-    for (int32_t k = 0; k < m; ++k) {
-        const int32_t j = mem[k];
-        if (j != (int32_t)i) cols[b + pos++] = j;
-    }
+    if (i < n) deg[i] = dsize[uid[i]] - 1;
 }
 
-__global__ void k_fill_edges(const int2* __restrict__ edges, int64_t E, const int32_t* __restrict__ umult,
-                             const int64_t* __restrict__ mem_off, const int32_t* __restrict__ members,
-                             const int64_t* __restrict__ off, int32_t* __restrict__ cur, int32_t* __restrict__ cols,
-                             int64_t* __restrict__ heavy, int* __restrict__ nheavy, int* __restrict__ err) {
+__global__ void k_closed_self(const int32_t* __restrict__ uid, const int32_t* __restrict__ mpos, int64_t n,
+                              const int64_t* __restrict__ uoff, int32_t* __restrict__ S) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) S[uoff[uid[i]] + mpos[i]] = (int32_t)i;
+}
+
+__global__ void k_closed_edges(const int2* __restrict__ edges, int64_t E, const int32_t* __restrict__ umult,
+                               const int64_t* __restrict__ mem_off, const int32_t* __restrict__ members,
+                               const int64_t* __restrict__ uoff, int32_t* __restrict__ ucur,
+                               int32_t* __restrict__ S, int* __restrict__ err) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 2 * E) return;
     const int2 uv = edges[t >> 1];
-    const int32_t a = (t & 1) ? uv.y : uv.x;  // row side
-    const int32_t b = (t & 1) ? uv.x : uv.y;  // neighbour side
-    const int32_t ma = umult[a], mb = umult[b];
-    if ((int64_t)ma * mb > kHeavy) {
-        heavy[atomicAdd(nheavy, 1)] = t;
+    const int32_t a = (t & 1) ? uv.y : uv.x;  // list owner
+    const int32_t b = (t & 1) ? uv.x : uv.y;  // neighbour whose members are appended
+    const int32_t mb = umult[b];
+    const int32_t slot = atomicAdd(&ucur[a], mb);
+    const int64_t o = uoff[a] + slot;
+    if (o + mb > uoff[a + 1]) {
+        atomicExch(err, 1);
         return;
     }
-    const int32_t slot = atomicAdd(&cur[a], mb);
-    const int32_t* ra = members + mem_off[a];
     const int32_t* rb = members + mem_off[b];
-    for (int32_t x = 0; x < ma; ++x) {
-        const int32_t i = ra[x];
-        const int64_t o = off[i] + slot;
-        if (o + mb > off[i + 1]) {
-            atomicExch(err, 1);
-            continue;
-        }
-        for (int32_t y = 0; y < mb; ++y) cols[o + y] = rb[y];
-    }
+    for (int32_t y = 0; y < mb; ++y) S[o + y] = rb[y];
 }
 
-__global__ void k_fill_heavy(const int64_t* __restrict__ heavy, const int* __restrict__ nheavy,
-                             const int2* __restrict__ edges, const int32_t* __restrict__ umult,
-                             const int64_t* __restrict__ mem_off, const int32_t* __restrict__ members,
-                             const int64_t* __restrict__ off, int32_t* __restrict__ cur, int32_t* __restrict__ cols,
-                             int* __restrict__ err) {
+// ---- 5. expand --------------------------------------------------------------
+
+// Row i = sorted S_u without i; one warp per row, lanes along the row.
+__global__ void k_expand(const int32_t* __restrict__ uid, int64_t n, const int64_t* __restrict__ uoff,
+                         const int32_t* __restrict__ S, const int64_t* __restrict__ off, int32_t* __restrict__ cols) {
     const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int nh = *nheavy;
-    for (int64_t w = w0; w < nh; w += nw) {
-        const int64_t t = heavy[w];
-        const int2 uv = edges[t >> 1];
-        const int32_t a = (t & 1) ? uv.y : uv.x;
-        const int32_t b = (t & 1) ? uv.x : uv.y;
-        const int32_t ma = umult[a], mb = umult[b];
-        int32_t slot = 0;
-        if (lane == 0) slot = atomicAdd(&cur[a], mb);
-        slot = __shfl_sync(kFull, slot, 0);
-        const int32_t* ra = members + mem_off[a];
-        const int32_t* rb = members + mem_off[b];
-        const int64_t total = (int64_t)ma * mb;
-        for (int64_t idx = lane; idx < total; idx += 32) {
-            const int32_t i = ra[idx / mb];
-            const int32_t y = (int32_t)(idx % mb);
-            const int64_t o = off[i] + slot + y;
-            if (o < off[i + 1]) cols[o] = rb[y];
-            else atomicExch(err, 1);
+    const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += stride) {
+        const int32_t u = uid[i];
+        const int64_t s0 = uoff[u];
+        const int64_t D = uoff[u + 1] - s0;
+        if (D <= 1) continue;
+        const int32_t* su = S + s0;
+        int64_t lo = 0, hi = D;  // position of i in S_u
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (su[mid] < (int32_t)i) lo = mid + 1; else hi = mid;
+        }
+        const int64_t o = off[i];
+        for (int64_t k = lane; k < D; k += 32) {
+            const int32_t x = su[k];
+            if (k != lo) cols[o + k - (k > lo ? 1 : 0)] = x;
         }
     }
 }
@@ -526,7 +539,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
                              int partition_cap) {
     const int64_t n = pk.n;
     if (n > kDeletionMaxN) return TCRNET_ENOTSUP;
-    const int cap = (partition_cap > 0 && partition_cap < kCap) ? partition_cap : kCap;
+    const int cap = (partition_cap > 0 && partition_cap < kWarpCap) ? partition_cap : kWarpCap;
     Timer tm(profile, s);
     const int t0 = tm.mark();
 
@@ -539,7 +552,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     TCR_CHECK(scount.alloc(sizeof(int32_t) * S, s));
     TCR_CHECK(flag.alloc(sizeof(int32_t) * S, s));
     TCR_CHECK(ubase.alloc(sizeof(int64_t) * (S + 1), s));
-    TCR_CHECK(errb.alloc(sizeof(int) * 4, s));  // [0] dedup, [1] fill, [2] fallback count, [3] heavy count
+    TCR_CHECK(errb.alloc(sizeof(int) * 4, s));  // [0] dedup, [1] fill, [2] fallback count
     TCR_CUDA(cudaMemsetAsync(table.as<void>(), 0xff, sizeof(int32_t) * S, s));
     TCR_CUDA(cudaMemsetAsync(scount.as<void>(), 0, sizeof(int32_t) * S, s));
     TCR_CUDA(cudaMemsetAsync(errb.as<void>(), 0, sizeof(int) * 4, s));
@@ -554,7 +567,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     int64_t U = 0;
     TCR_CUDA(cudaMemcpyAsync(&U, ubase.as<int64_t>() + S, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TCR_CUDA(cudaStreamSynchronize(s));
-    DevBuf ucanon, ulen, umult, uid, mem_off, mcur, members;
+    DevBuf ucanon, ulen, umult, uid, mem_off, mcur, members, mpos;
     TCR_CHECK(ucanon.alloc(sizeof(Canon) * U, s));
     TCR_CHECK(ulen.alloc(U, s));
     TCR_CHECK(umult.alloc(sizeof(int32_t) * U, s));
@@ -562,6 +575,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     TCR_CHECK(mem_off.alloc(sizeof(int64_t) * (U + 1), s));
     TCR_CHECK(mcur.alloc(sizeof(int32_t) * U, s));
     TCR_CHECK(members.alloc(sizeof(int32_t) * n, s));
+    TCR_CHECK(mpos.alloc(sizeof(int32_t) * n, s));
     k_unique_compact<<<grid_for(S), kThreads, 0, s>>>(scount.as<int32_t>(), table.as<int32_t>(), ubase.as<int64_t>(),
                                                       S, pk.canon_in.as<Canon>(), pk.lens.as<uint8_t>(),
                                                       ucanon.as<Canon>(), ulen.as<uint8_t>(), umult.as<int32_t>());
@@ -576,9 +590,8 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     TCR_CHECK(scan_exclusive_i32_to_i64(umult.as<int32_t>(), mem_off.as<int64_t>(), U, s));
     TCR_CUDA(cudaMemsetAsync(mcur.as<void>(), 0, sizeof(int32_t) * U, s));
     k_members<<<grid_for(n), kThreads, 0, s>>>(uid.as<int32_t>(), n, mem_off.as<int64_t>(), mcur.as<int32_t>(),
-                                               members.as<int32_t>());
+                                               members.as<int32_t>(), mpos.as<int32_t>());
     TCR_LAUNCH_CHECK();
-    mcur.reset();
     const int t1 = tm.mark();
 
     // ---- 2. records and 3. join (l_max >= 1 only; l_max = 0 keeps duplicates only)
@@ -601,18 +614,18 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         TCR_CHECK(scan_exclusive_i32_to_i64(pcnt.as<int32_t>(), poff.as<int64_t>(), P, s));
         TCR_CUDA(cudaMemcpyAsync(&R, poff.as<int64_t>() + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         TCR_CUDA(cudaStreamSynchronize(s));
-        TCR_CHECK(recs.alloc(sizeof(uint32_t) * R, s));
+        TCR_CHECK(recs.alloc(sizeof(uint64_t) * R, s));
         TCR_CUDA(cudaMemsetAsync(pcnt.as<void>(), 0, sizeof(int32_t) * P, s));
         k_records<true><<<grid_for(U), kThreads, 0, s>>>(ucanon.as<Canon>(), ulen.as<uint8_t>(), U, (uint32_t)P,
-                                                         pcnt.as<int32_t>(), poff.as<int64_t>(), recs.as<uint32_t>());
+                                                         pcnt.as<int32_t>(), poff.as<int64_t>(), recs.as<uint64_t>());
         TCR_LAUNCH_CHECK();
         pcnt.reset();
         t2 = tm.mark();
         TCR_CHECK(pedges.alloc(sizeof(int64_t) * P, s));
         TCR_CHECK(eoff.alloc(sizeof(int64_t) * (P + 1), s));
         TCR_CHECK(fb_list.alloc(sizeof(int32_t) * P, s));
-        const int jgrid = (int)std::min<int64_t>(P, (int64_t)num_sms * 8);
-        k_join<false><<<jgrid, kThreads, 0, s>>>(poff.as<int64_t>(), P, recs.as<uint32_t>(), ucanon.as<Canon>(), cap,
+        const int jgrid = (int)std::min<int64_t>(ceil_div(P, kWarps), (int64_t)num_sms * 16);
+        k_join<false><<<jgrid, kThreads, 0, s>>>(poff.as<int64_t>(), P, recs.as<uint64_t>(), ucanon.as<Canon>(), cap,
                                                  T, pedges.as<int64_t>(), nullptr, nullptr, fb_list.as<int32_t>(),
                                                  d_err + 2);
         TCR_LAUNCH_CHECK();
@@ -622,7 +635,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         nfb = h_nfb;
         if (h_nfb > 0) {
             k_join_fallback<false><<<std::min(h_nfb, num_sms * 4), kThreads, 0, s>>>(
-                fb_list.as<int32_t>(), h_nfb, poff.as<int64_t>(), recs.as<uint32_t>(), ucanon.as<Canon>(), T,
+                fb_list.as<int32_t>(), h_nfb, poff.as<int64_t>(), recs.as<uint64_t>(), ucanon.as<Canon>(), T,
                 pedges.as<int64_t>(), nullptr, nullptr);
             TCR_LAUNCH_CHECK();
         }
@@ -632,13 +645,13 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         t3 = tm.mark();
         TCR_CHECK(edges.alloc(sizeof(int2) * E, s));
         if (E > 0) {
-            k_join<true><<<jgrid, kThreads, 0, s>>>(poff.as<int64_t>(), P, recs.as<uint32_t>(), ucanon.as<Canon>(),
+            k_join<true><<<jgrid, kThreads, 0, s>>>(poff.as<int64_t>(), P, recs.as<uint64_t>(), ucanon.as<Canon>(),
                                                     cap, T, nullptr, eoff.as<int64_t>(), edges.as<int2>(), nullptr,
                                                     nullptr);
             TCR_LAUNCH_CHECK();
             if (h_nfb > 0) {
                 k_join_fallback<true><<<std::min(h_nfb, num_sms * 4), kThreads, 0, s>>>(
-                    fb_list.as<int32_t>(), h_nfb, poff.as<int64_t>(), recs.as<uint32_t>(), ucanon.as<Canon>(), T,
+                    fb_list.as<int32_t>(), h_nfb, poff.as<int64_t>(), recs.as<uint64_t>(), ucanon.as<Canon>(), T,
                     nullptr, eoff.as<int64_t>(), edges.as<int2>());
                 TCR_LAUNCH_CHECK();
             }
@@ -646,51 +659,53 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         t4 = tm.mark();
     }
 
-    // ---- 4. degrees
-    DevBuf wsum, deg, off64;
-    TCR_CHECK(wsum.alloc(sizeof(int32_t) * U, s));
+    // ---- 4. closed neighbourhoods and node degrees
+    DevBuf dsize, ucur, uoff, deg, off64, Sbuf;
+    TCR_CHECK(dsize.alloc(sizeof(int32_t) * U, s));
+    TCR_CHECK(ucur.alloc(sizeof(int32_t) * U, s));
+    TCR_CHECK(uoff.alloc(sizeof(int64_t) * (U + 1), s));
     TCR_CHECK(deg.alloc(sizeof(int32_t) * n, s));
     TCR_CHECK(off64.alloc(sizeof(int64_t) * (n + 1), s));
-    TCR_CUDA(cudaMemsetAsync(wsum.as<void>(), 0, sizeof(int32_t) * U, s));
+    TCR_CUDA(cudaMemsetAsync(dsize.as<void>(), 0, sizeof(int32_t) * U, s));
     if (E > 0) {
         k_weighted_degree<<<grid_for(E), kThreads, 0, s>>>(edges.as<int2>(), E, umult.as<int32_t>(),
-                                                           wsum.as<int32_t>());
+                                                           dsize.as<int32_t>());
         TCR_LAUNCH_CHECK();
     }
-    k_node_degree<<<grid_for(n), kThreads, 0, s>>>(uid.as<int32_t>(), n, umult.as<int32_t>(), wsum.as<int32_t>(),
-                                                   deg.as<int32_t>());
+    k_closed_size<<<grid_for(U), kThreads, 0, s>>>(umult.as<int32_t>(), U, dsize.as<int32_t>(), ucur.as<int32_t>());
+    TCR_LAUNCH_CHECK();
+    TCR_CHECK(scan_exclusive_i32_to_i64(dsize.as<int32_t>(), uoff.as<int64_t>(), U, s));
+    k_node_degree<<<grid_for(n), kThreads, 0, s>>>(uid.as<int32_t>(), n, dsize.as<int32_t>(), deg.as<int32_t>());
     TCR_LAUNCH_CHECK();
     TCR_CHECK(scan_exclusive_i32_to_i64(deg.as<int32_t>(), off64.as<int64_t>(), n, s));
-    int64_t nnz = 0;
-    TCR_CUDA(cudaMemcpyAsync(&nnz, off64.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    int64_t sizes[2] = {0, 0};  // sum of D_u, nnz
+    TCR_CUDA(cudaMemcpyAsync(&sizes[0], uoff.as<int64_t>() + U, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaMemcpyAsync(&sizes[1], off64.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TCR_CUDA(cudaStreamSynchronize(s));
-    wsum.reset();
-    const int t5 = tm.mark();
-
-    // ---- 5. fill
-    DevBuf cols, cur, heavy;
-    TCR_CHECK(cols.alloc(sizeof(int32_t) * nnz, s));
-    TCR_CHECK(cur.alloc(sizeof(int32_t) * U, s));
-    k_cursor_init<<<grid_for(U), kThreads, 0, s>>>(umult.as<int32_t>(), U, cur.as<int32_t>());
-    TCR_LAUNCH_CHECK();
-    k_fill_self<<<grid_for(n), kThreads, 0, s>>>(uid.as<int32_t>(), n, umult.as<int32_t>(), mem_off.as<int64_t>(),
-                                                 members.as<int32_t>(), off64.as<int64_t>(), cols.as<int32_t>());
+    const int64_t SD = sizes[0], nnz = sizes[1];
+    dsize.reset();
+    TCR_CHECK(Sbuf.alloc(sizeof(int32_t) * SD, s));
+    k_closed_self<<<grid_for(n), kThreads, 0, s>>>(uid.as<int32_t>(), mpos.as<int32_t>(), n, uoff.as<int64_t>(),
+                                                   Sbuf.as<int32_t>());
     TCR_LAUNCH_CHECK();
     if (E > 0) {
-        TCR_CHECK(heavy.alloc(sizeof(int64_t) * 2 * E, s));
-        k_fill_edges<<<grid_for(2 * E), kThreads, 0, s>>>(edges.as<int2>(), E, umult.as<int32_t>(),
-                                                          mem_off.as<int64_t>(), members.as<int32_t>(),
-                                                          off64.as<int64_t>(), cur.as<int32_t>(), cols.as<int32_t>(),
-                                                          heavy.as<int64_t>(), d_err + 3, d_err + 1);
-        TCR_LAUNCH_CHECK();
-        k_fill_heavy<<<num_sms * 8, kThreads, 0, s>>>(heavy.as<int64_t>(), d_err + 3, edges.as<int2>(),
-                                                      umult.as<int32_t>(), mem_off.as<int64_t>(),
-                                                      members.as<int32_t>(), off64.as<int64_t>(), cur.as<int32_t>(),
-                                                      cols.as<int32_t>(), d_err + 1);
+        k_closed_edges<<<grid_for(2 * E), kThreads, 0, s>>>(edges.as<int2>(), E, umult.as<int32_t>(),
+                                                            mem_off.as<int64_t>(), members.as<int32_t>(),
+                                                            uoff.as<int64_t>(), ucur.as<int32_t>(),
+                                                            Sbuf.as<int32_t>(), d_err + 1);
         TCR_LAUNCH_CHECK();
     }
+    edges.reset();
+    const int t5 = tm.mark();
+    TCR_CHECK(sort_rows(uoff.as<int64_t>(), Sbuf.as<int32_t>(), U, s, num_sms));
     const int t6 = tm.mark();
-    TCR_CHECK(sort_rows(off64.as<int64_t>(), cols.as<int32_t>(), n, s, num_sms));
+
+    // ---- 5. expand
+    DevBuf cols;
+    TCR_CHECK(cols.alloc(sizeof(int32_t) * nnz, s));
+    k_expand<<<(unsigned)std::min<int64_t>(ceil_div(n, kWarps), (int64_t)num_sms * 32), kThreads, 0, s>>>(
+        uid.as<int32_t>(), n, uoff.as<int64_t>(), Sbuf.as<int32_t>(), off64.as<int64_t>(), cols.as<int32_t>());
+    TCR_LAUNCH_CHECK();
     const int t7 = tm.mark();
     int h_err[4] = {0, 0, 0, 0};
     TCR_CUDA(cudaMemcpyAsync(h_err, d_err, sizeof(h_err), cudaMemcpyDeviceToHost, s));
@@ -705,6 +720,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     out.n_records = R;
     out.unique_edges = E;
     out.n_fallback = nfb;
+    out.closed_total = SD;
     out.ms_phase[0] = tm.ms(t0, t1);
     out.ms_phase[1] = tm.ms(t1, t2);
     out.ms_phase[2] = tm.ms(t2, t3);
@@ -714,9 +730,9 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     out.ms_phase[6] = tm.ms(t6, t7);
     out.ms_phase[7] = tm.ms(t0, t7);
     out.ms_join = tm.ms(t2, t3) + tm.ms(t3, t4);
-    out.ms_scan = tm.ms(t4, t5);
-    out.ms_fill = tm.ms(t5, t6);
-    out.ms_sort = tm.ms(t6, t7);
+    out.ms_scan = 0.0;
+    out.ms_fill = tm.ms(t4, t5);
+    out.ms_sort = tm.ms(t5, t6) + tm.ms(t6, t7);
     return TCRNET_OK;
 }
 

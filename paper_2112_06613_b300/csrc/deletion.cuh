@@ -19,9 +19,11 @@ struct DeletionResult {
     int64_t n_unique = 0;
     int64_t n_records = 0;
     int64_t unique_edges = 0;
-    int64_t n_fallback = 0;  // partitions joined by the exact quadratic fallback
+    int64_t n_fallback = 0;    // partitions joined by the exact quadratic fallback
+    int64_t closed_total = 0;  // sum over distinct strings of closed-neighbourhood sizes
     double ms_join = 0, ms_scan = 0, ms_fill = 0, ms_sort = 0;
-    double ms_phase[8] = {0};  // dedup, records, join count, join write, degrees, fill, sort, total
+    // dedup, records, join count, join write, closed fill, closed sort, expand, total
+    double ms_phase[8] = {0};
 };
 
 // Test knob: partitions larger than `partition_cap` (<= the shared-memory

@@ -5,9 +5,10 @@
 // scheduling, i.e. bit-exact and deterministic. Values inside a row are
 // distinct node ids.
 //
-//   len <= 32:          one warp, one value per lane, register bitonic network
-//                       (shuffle exchanges).
-//   33 <= len <= 1024:  one warp, shared-memory bitonic network (4 KB per warp).
+//   len <= 1024:        one warp, values in registers (K = 1..32 per lane,
+//                       network position lane * K + r), bitonic network:
+//                       stages with partner distance < K exchange registers,
+//                       longer ones exchange lanes by shuffle.
 //   1025 .. 16384:      one 1024-thread block, shared-memory bitonic network.
 //   > 16384:            one block; 16384-value chunks sorted in shared memory,
 //                       then pairwise merges through a scratch buffer where each
@@ -34,13 +35,15 @@ __device__ __forceinline__ int next_pow2(int x) {
 }
 
 // Bitonic network over s[0, P) by `nthreads` cooperating threads with index t;
-// `sync` orders the stages.
+// `sync` orders the stages. P and j are powers of two, so the pair index
+// arithmetic is shifts and masks.
 template <typename Sync>
 __device__ __forceinline__ void bitonic_smem(int32_t* s, int P, int t, int nthreads, Sync sync) {
     for (int k = 2; k <= P; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
+            const int lj = __ffs(j) - 1;
             for (int i = t; i < (P >> 1); i += nthreads) {
-                const int lo = 2 * j * (i / j) + (i % j);
+                const int lo = ((i >> lj) << (lj + 1)) | (i & (j - 1));
                 const int hi = lo + j;
                 const bool up = (lo & k) == 0;
                 const int32_t x = s[lo], y = s[hi];
@@ -54,10 +57,55 @@ __device__ __forceinline__ void bitonic_smem(int32_t* s, int P, int t, int nthre
     }
 }
 
+// Sort one row of len <= 32 * K values held K per lane (see the file comment).
+template <int K>
+__device__ __forceinline__ void warp_sort_regs(int32_t* __restrict__ row, int len, int lane) {
+    constexpr int P = 32 * K;
+    int32_t v[K];
+    // coalesced load; which value sits at which network position is irrelevant
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const int e = r * 32 + lane;
+        v[r] = e < len ? row[e] : kInf;
+    }
+#pragma unroll
+    for (int k = 2; k <= P; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j < K) {
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    if ((r & j) == 0) {
+                        const int r2 = r | j;
+                        const bool up = ((lane * K + r) & k) == 0;
+                        const int32_t a = v[r], b = v[r2];
+                        const int32_t mn = min(a, b), mx = max(a, b);
+                        v[r] = up ? mn : mx;
+                        v[r2] = up ? mx : mn;
+                    }
+                }
+            } else {
+                const int jl = j / K;
+                const bool lower = (lane & jl) == 0;
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    const int32_t p = __shfl_xor_sync(kFull, v[r], jl);
+                    const bool up = ((lane * K + r) & k) == 0;
+                    v[r] = (lower == up) ? min(v[r], p) : max(v[r], p);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const int e = lane * K + r;
+        if (e < len) row[e] = v[r];
+    }
+}
+
 __global__ void __launch_bounds__(kSortWarps * 32)
 k_sort_warp(const int64_t* __restrict__ off, int32_t* __restrict__ cols, int64_t n,
-            int32_t* __restrict__ big, int* __restrict__ nbig) {
-    __shared__ int32_t buf[kSortWarps][kWarpCap];
+            int32_t* __restrict__ mid, int* __restrict__ nmid, int32_t* __restrict__ big, int* __restrict__ nbig) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t gw = (int64_t)blockIdx.x * kSortWarps + warp;
     const int64_t stride = (int64_t)gridDim.x * kSortWarps;
@@ -66,37 +114,39 @@ k_sort_warp(const int64_t* __restrict__ off, int32_t* __restrict__ cols, int64_t
         const int64_t len64 = off[r + 1] - base;
         const int len = len64 > (int64_t)kInf ? kInf : (int)len64;
         if (len <= 1) continue;
-        if (len <= 32) {
-            int32_t v = lane < len ? cols[base + lane] : kInf;
-#pragma unroll
-            for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-                for (int j = k >> 1; j > 0; j >>= 1) {
-                    const int32_t p = __shfl_xor_sync(kFull, v, j);
-                    const bool up = (lane & k) == 0;
-                    const bool lower = (lane & j) == 0;
-                    v = (lower == up) ? min(v, p) : max(v, p);
-                }
-            }
-            if (lane < len) cols[base + lane] = v;
-        } else if (len <= kWarpCap) {
-            const int P = next_pow2(len);
-            int32_t* s = buf[warp];
-            for (int i = lane; i < P; i += 32) s[i] = i < len ? cols[base + i] : kInf;
-            __syncwarp();
-            bitonic_smem(s, P, lane, 32, [] __device__() { __syncwarp(); });
-            for (int i = lane; i < len; i += 32) cols[base + i] = s[i];
-            __syncwarp();
-        } else if (lane == 0) {
-            big[atomicAdd(nbig, 1)] = (int32_t)r;
+        int32_t* row = cols + base;
+        if (len <= 32) warp_sort_regs<1>(row, len, lane);
+        else if (len <= 64) warp_sort_regs<2>(row, len, lane);
+        else if (len <= 128) warp_sort_regs<4>(row, len, lane);
+        else if (len <= 256) warp_sort_regs<8>(row, len, lane);
+        else if (lane == 0) {
+            if (len <= kWarpCap) mid[atomicAdd(nmid, 1)] = (int32_t)r;
+            else big[atomicAdd(nbig, 1)] = (int32_t)r;
         }
+    }
+}
+
+// Rows of 257..1024 values (listed by k_sort_warp); a separate kernel so the
+// wide register arrays do not lower the occupancy of the short-row kernel.
+__global__ void __launch_bounds__(kSortWarps * 32)
+k_sort_warp_mid(const int64_t* __restrict__ off, int32_t* __restrict__ cols, const int32_t* __restrict__ mid,
+                const int* __restrict__ nmid) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int count = *nmid;
+    for (int64_t k = (int64_t)blockIdx.x * kSortWarps + warp; k < count; k += (int64_t)gridDim.x * kSortWarps) {
+        const int64_t r = mid[k];
+        const int64_t base = off[r];
+        const int len = (int)(off[r + 1] - base);
+        if (len <= 512) warp_sort_regs<16>(cols + base, len, lane);
+        else warp_sort_regs<32>(cols + base, len, lane);
     }
 }
 
 __global__ void __launch_bounds__(kBlockThreads)
 k_sort_block(const int64_t* __restrict__ off, int32_t* __restrict__ cols, const int32_t* __restrict__ rows,
-             int nrows, int32_t* __restrict__ huge, int* __restrict__ nhuge) {
+             const int* __restrict__ nrows_ptr, int32_t* __restrict__ huge, int* __restrict__ nhuge) {
     extern __shared__ int32_t sbuf[];
+    const int nrows = *nrows_ptr;
     for (int k = blockIdx.x; k < nrows; k += gridDim.x) {
         const int64_t r = rows[k];
         const int64_t base = off[r];
@@ -153,31 +203,32 @@ __global__ void k_merge_runs(const int32_t* __restrict__ src, int32_t* __restric
 
 tcrnet_status sort_rows(const int64_t* off, int32_t* cols, int64_t n, cudaStream_t s, int num_sms) {
     if (n <= 0) return TCRNET_OK;
-    DevBuf big, counts;
-    TCR_CHECK(big.alloc(sizeof(int32_t) * 2 * n, s));  // big rows, then huge rows
-    TCR_CHECK(counts.alloc(sizeof(int) * 2, s));
-    TCR_CUDA(cudaMemsetAsync(counts.as<void>(), 0, sizeof(int) * 2, s));
+    // lists: [0, n) rows of 257..1024, [n, 2n) rows above 1024, [2n, 3n) rows above kBlockCap
+    DevBuf lists, counts;
+    TCR_CHECK(lists.alloc(sizeof(int32_t) * 3 * n, s));
+    TCR_CHECK(counts.alloc(sizeof(int) * 3, s));
+    TCR_CUDA(cudaMemsetAsync(counts.as<void>(), 0, sizeof(int) * 3, s));
+    int32_t* mid = lists.as<int32_t>();
+    int32_t* big = mid + n;
+    int32_t* huge_list = big + n;
+    int* cnt = counts.as<int>();
     const int64_t blocks = std::min<int64_t>(ceil_div(n, kSortWarps), (int64_t)num_sms * 64);
-    k_sort_warp<<<(unsigned)blocks, kSortWarps * 32, 0, s>>>(off, cols, n, big.as<int32_t>(), counts.as<int>());
+    k_sort_warp<<<(unsigned)blocks, kSortWarps * 32, 0, s>>>(off, cols, n, mid, cnt, big, cnt + 1);
     TCR_LAUNCH_CHECK();
-    int h_counts[2] = {0, 0};
-    TCR_CUDA(cudaMemcpyAsync(h_counts, counts.as<void>(), sizeof(h_counts), cudaMemcpyDeviceToHost, s));
-    TCR_CUDA(cudaStreamSynchronize(s));
-    if (h_counts[0] == 0) return TCRNET_OK;
+    k_sort_warp_mid<<<num_sms * 4, kSortWarps * 32, 0, s>>>(off, cols, mid, cnt);
+    TCR_LAUNCH_CHECK();
     const size_t smem = sizeof(int32_t) * kBlockCap;
     TCR_CUDA(cudaFuncSetAttribute(k_sort_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     TCR_CUDA(cudaFuncSetAttribute(k_sort_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = std::min(h_counts[0], num_sms * 2);
-    k_sort_block<<<grid, kBlockThreads, smem, s>>>(off, cols, big.as<int32_t>(), h_counts[0],
-                                                   big.as<int32_t>() + h_counts[0], counts.as<int>() + 1);
+    k_sort_block<<<num_sms * 2, kBlockThreads, smem, s>>>(off, cols, big, cnt + 1, huge_list, cnt + 2);
     TCR_LAUNCH_CHECK();
-    TCR_CUDA(cudaMemcpyAsync(h_counts, counts.as<void>(), sizeof(h_counts), cudaMemcpyDeviceToHost, s));
+    int h_huge = 0;
+    TCR_CUDA(cudaMemcpyAsync(&h_huge, cnt + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
     TCR_CUDA(cudaStreamSynchronize(s));
-    if (h_counts[1] == 0) return TCRNET_OK;
+    if (h_huge == 0) return TCRNET_OK;
     // Rare: rows longer than one shared-memory block.
-    std::vector<int32_t> huge(h_counts[1]);
-    TCR_CUDA(cudaMemcpyAsync(huge.data(), big.as<int32_t>() + h_counts[0], sizeof(int32_t) * huge.size(),
-                             cudaMemcpyDeviceToHost, s));
+    std::vector<int32_t> huge(h_huge);
+    TCR_CUDA(cudaMemcpyAsync(huge.data(), huge_list, sizeof(int32_t) * huge.size(), cudaMemcpyDeviceToHost, s));
     std::vector<int64_t> hoff(2);
     TCR_CUDA(cudaStreamSynchronize(s));
     for (int32_t r : huge) {
