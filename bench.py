@@ -305,8 +305,8 @@ def run_ours(args):
 
     is_tile = st0["method"] == 1
     # dominant phase of the step and its algorithmic bytes
-    names = ["dedup", "records", "join_count", "join_write", "closed_fill", "closed_sort", "expand"]
-    phase_ms = {nm: statistics.mean(s["ms_phase"][i] for s in stats) for i, nm in enumerate(names)}
+    names = ["dedup", "records", "join_weigh", "join_fill", "unused", "list_sort", "expand"]
+    phase_ms = {nm: statistics.mean(s["ms_phase"][i] for s in stats) for i, nm in enumerate(names) if nm != "unused"}
     if is_tile:
         phase_ms = {"count_pass": statistics.mean(s["ms_count"] for s in stats),
                     "write_pass": statistics.mean(s["ms_write"] for s in stats),
@@ -316,10 +316,9 @@ def run_ours(args):
     U, R, E, SD = st0["n_unique"], st0["n_records"], st0["unique_edges"], st0["closed_total"]
     alg_bytes = 1 if is_tile else {
         "expand": 4 * nnz + 4 * SD + 8 * (n + 1) + 4 * n,  # write cols; read lists, offsets, ids
-        "closed_sort": 8 * SD + 8 * (U + 1),              # read + write lists, read offsets
-        "closed_fill": 16 * E + 8 * SD + 8 * (U + 1),     # read edges (x2), members; write lists
-        "join_count": 8 * R,                              # read records
-        "join_write": 8 * R + 8 * E,                      # + write edges
+        "list_sort": 8 * SD + 8 * (U + 1),                # read + write lists, read offsets
+        "join_fill": 8 * R + 8 * SD,                      # read records; read members, write lists
+        "join_weigh": 8 * R,                              # read records
         "records": 32 * U + 8 * R,                        # read strings, scatter records
         "dedup": 32 * n + 32 * U + 8 * n,
     }[dom]

@@ -31,15 +31,17 @@
 //     passes (count, scatter).
 //  3. join: one warp per partition sorts its words in registers (bitonic
 //     network), confirms that equal hashes are equal contents (exact), and
-//     emits edges between distinct strings: every pair inside a run of equal
-//     (hash, p) (equal length, one substitution), and each run-start deletion
-//     record with the full record of the same content (one indel). Count pass,
-//     exclusive scan, write pass (warp prefix sums give each lane its slots).
+//     finds the edges between distinct strings: every pair inside a run of
+//     equal (hash, p) (equal length, one substitution), and each run-start
+//     deletion record with the full record of the same content (one indel).
 //     Partitions over capacity or with a hash collision take an exact
-//     quadratic fallback.
-//  4. closed neighbourhoods: D_u = m_u + sum over distinct neighbours v of
-//     m_v; S_u = M_u followed by every M_v, written once per distinct string
-//     and sorted (rowsort.cu). A node i of u has degree D_u - 1.
+//     quadratic fallback. The join runs twice: the first pass adds m_v to
+//     W_u (and m_u to W_v) for every edge {u, v} and counts the edges of each
+//     partition; the second writes the edges at scanned positions.
+//  4. closed neighbourhoods: D_u = m_u + W_u; S_u = M_u followed by every
+//     M_v (appended at a slot taken from a per-string cursor; long member
+//     lists are copied by a whole warp), written once per distinct string and
+//     sorted (rowsort.cu). A node i of u has degree D_u - 1.
 //  5. expand: row i of the CSR is S_u without i (a streaming copy), so the
 //     long rows of frequent strings are sorted once, not once per copy.
 #include <algorithm>
@@ -225,10 +227,11 @@ __global__ void k_members(const int32_t* __restrict__ uid, int64_t n, const int6
 // ---- 2. records -----------------------------------------------------------
 
 template <bool SCATTER>
-__global__ void k_records(const Canon* __restrict__ ucanon, const uint8_t* __restrict__ ulen, int64_t U, uint32_t P,
-                          int32_t* __restrict__ pcnt, const int64_t* __restrict__ poff, uint64_t* __restrict__ recs) {
+__global__ void k_records(const Canon* __restrict__ ucanon, const uint8_t* __restrict__ ulen,
+                          const int64_t* __restrict__ U_ptr, int64_t n, uint32_t P, int32_t* __restrict__ pcnt,
+                          const int64_t* __restrict__ poff, uint64_t* __restrict__ recs) {
     const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= U) return;
+    if (u >= n || u >= *U_ptr) return;
     const Canon c = load_canon(ucanon + u);
     const int L = ulen[u];
     for (int p = -1; p < L; ++p) {
@@ -321,10 +324,20 @@ __device__ __forceinline__ int64_t record_edges(const uint64_t* buf, int k, int 
     return cnt;
 }
 
+// Pass 1 of the join: W_u += m_v and W_v += m_u for an edge {u, v}.
+struct Weigh {
+    const int32_t* umult;
+    int32_t* wsum;
+    __device__ __forceinline__ void operator()(int32_t a, int32_t b) const {
+        atomicAdd(&wsum[a], umult[b]);
+        atomicAdd(&wsum[b], umult[a]);
+    }
+};
+
 template <bool WRITE>
 __global__ void __launch_bounds__(kThreads)
 k_join(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __restrict__ recs,
-       const Canon* __restrict__ ucanon, int cap, int T, int64_t* __restrict__ pedges,
+       const Canon* __restrict__ ucanon, int cap, int T, Weigh weigh, int64_t* __restrict__ pedges,
        const int64_t* __restrict__ eoff, int2* __restrict__ edges, int32_t* __restrict__ fb_list,
        int* __restrict__ fb_count) {
     __shared__ uint64_t sbuf[kWarps][kWarpCap];
@@ -365,13 +378,17 @@ k_join(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __restrict__
             __syncwarp();
             continue;
         }
-        int64_t mine = 0;
-        for (int k = lane; k < s; k += 32) mine += record_edges(buf, k, s, T, [](int32_t, int32_t) {});
-        int64_t excl;
-        const int64_t total = warp_scan(mine, excl, lane);
         if (!WRITE) {
+            int64_t mine = 0;
+            for (int k = lane; k < s; k += 32) mine += record_edges(buf, k, s, T, weigh);
+            int64_t excl;
+            const int64_t total = warp_scan(mine, excl, lane);
             if (lane == 0) pedges[pid] = total;
         } else {
+            int64_t mine = 0;
+            for (int k = lane; k < s; k += 32) mine += record_edges(buf, k, s, T, [](int32_t, int32_t) {});
+            int64_t excl;
+            warp_scan(mine, excl, lane);
             int64_t pos = eoff[pid] + excl;
             for (int k = lane; k < s; k += 32)
                 record_edges(buf, k, s, T, [&](int32_t a, int32_t b) { edges[pos++] = make_int2(a, b); });
@@ -383,10 +400,11 @@ k_join(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __restrict__
 // Exact quadratic join of one partition (over capacity or with a hash collision).
 template <bool WRITE>
 __global__ void __launch_bounds__(kThreads)
-k_join_fallback(const int32_t* __restrict__ fb_list, int nfb, const int64_t* __restrict__ poff,
-                const uint64_t* __restrict__ recs, const Canon* __restrict__ ucanon, int T,
+k_join_fallback(const int32_t* __restrict__ fb_list, const int* __restrict__ fb_count, const int64_t* __restrict__ poff,
+                const uint64_t* __restrict__ recs, const Canon* __restrict__ ucanon, int T, Weigh weigh,
                 int64_t* __restrict__ pedges, const int64_t* __restrict__ eoff, int2* __restrict__ edges) {
     __shared__ int64_t wtot[kWarps];
+    const int nfb = *fb_count;
     for (int f = blockIdx.x; f < nfb; f += gridDim.x) {
         const int64_t pid = fb_list[f];
         const int64_t base = poff[pid];
@@ -414,12 +432,15 @@ k_join_fallback(const int32_t* __restrict__ fb_list, int nfb, const int64_t* __r
             }
             return cnt;
         };
-        const int64_t mine = scan_pairs([](int32_t, int32_t) {});
-        int64_t excl;
-        const int64_t total = block_scan(mine, excl, wtot);
         if (!WRITE) {
+            const int64_t mine = scan_pairs(weigh);
+            int64_t excl;
+            const int64_t total = block_scan(mine, excl, wtot);
             if (threadIdx.x == 0) pedges[pid] = total;
         } else {
+            const int64_t mine = scan_pairs([](int32_t, int32_t) {});
+            int64_t excl;
+            block_scan(mine, excl, wtot);
             int64_t pos = eoff[pid] + excl;
             scan_pairs([&](int32_t a, int32_t b) { edges[pos++] = make_int2(a, b); });
         }
@@ -428,15 +449,6 @@ k_join_fallback(const int32_t* __restrict__ fb_list, int nfb, const int64_t* __r
 }
 
 // ---- 4. closed neighbourhoods ---------------------------------------------
-
-__global__ void k_weighted_degree(const int2* __restrict__ edges, int64_t E, const int32_t* __restrict__ umult,
-                                  int32_t* __restrict__ wsum) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= E) return;
-    const int2 uv = edges[e];
-    atomicAdd(&wsum[uv.x], umult[uv.y]);
-    atomicAdd(&wsum[uv.y], umult[uv.x]);
-}
 
 // D_u = m_u + W_u (written into wsum in place); cursor starts after M_u.
 __global__ void k_closed_size(const int32_t* __restrict__ umult, int64_t U, int32_t* __restrict__ wsum,
@@ -459,24 +471,44 @@ __global__ void k_closed_self(const int32_t* __restrict__ uid, const int32_t* __
     if (i < n) S[uoff[uid[i]] + mpos[i]] = (int32_t)i;
 }
 
-__global__ void k_closed_edges(const int2* __restrict__ edges, int64_t E, const int32_t* __restrict__ umult,
-                               const int64_t* __restrict__ mem_off, const int32_t* __restrict__ members,
-                               const int64_t* __restrict__ uoff, int32_t* __restrict__ ucur,
-                               int32_t* __restrict__ S, int* __restrict__ err) {
+// Append M_b to the list of a for both directions of every edge. Lanes copy
+// short member lists themselves; long ones are copied by the whole warp.
+__global__ void __launch_bounds__(kThreads)
+k_closed_edges(const int2* __restrict__ edges, int64_t E, const int32_t* __restrict__ umult,
+               const int64_t* __restrict__ mem_off, const int32_t* __restrict__ members,
+               const int64_t* __restrict__ uoff, int32_t* __restrict__ ucur, int32_t* __restrict__ S,
+               int* __restrict__ err) {
+    constexpr int kShort = 4;
+    const int lane = threadIdx.x & 31;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 2 * E) return;
-    const int2 uv = edges[t >> 1];
-    const int32_t a = (t & 1) ? uv.y : uv.x;  // list owner
-    const int32_t b = (t & 1) ? uv.x : uv.y;  // neighbour whose members are appended
-    const int32_t mb = umult[b];
-    const int32_t slot = atomicAdd(&ucur[a], mb);
-    const int64_t o = uoff[a] + slot;
-    if (o + mb > uoff[a + 1]) {
-        atomicExch(err, 1);
-        return;
+    const bool have = t < 2 * E;
+    int32_t a = 0, b = 0, mb = 0;
+    int64_t o = 0;
+    if (have) {
+        const int2 uv = edges[t >> 1];
+        a = (t & 1) ? uv.y : uv.x;  // list owner
+        b = (t & 1) ? uv.x : uv.y;  // neighbour whose members are appended
+        mb = umult[b];
+        o = uoff[a] + atomicAdd(&ucur[a], mb);
+        if (o + mb > uoff[a + 1]) {
+            atomicExch(err, 1);
+            mb = 0;
+        }
+        if (mb <= kShort) {
+            const int32_t* rb = members + mem_off[b];
+            for (int32_t y = 0; y < mb; ++y) S[o + y] = rb[y];
+        }
     }
-    const int32_t* rb = members + mem_off[b];
-    for (int32_t y = 0; y < mb; ++y) S[o + y] = rb[y];
+    unsigned longs = __ballot_sync(kFull, have && mb > kShort);
+    while (longs) {
+        const int src = __ffs(longs) - 1;
+        longs &= longs - 1;
+        const int32_t lb = __shfl_sync(kFull, b, src);
+        const int32_t lm = __shfl_sync(kFull, mb, src);
+        const int64_t lo = __shfl_sync(kFull, o, src);
+        const int32_t* rb = members + mem_off[lb];
+        for (int32_t y = lane; y < lm; y += 32) S[lo + y] = rb[y];
+    }
 }
 
 // ---- 5. expand --------------------------------------------------------------
@@ -542,21 +574,30 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     const int cap = (partition_cap > 0 && partition_cap < kWarpCap) ? partition_cap : kWarpCap;
     Timer tm(profile, s);
     const int t0 = tm.mark();
+    // Arrays over distinct strings are sized by n (an upper bound) and the
+    // record array by n + total length, so no host round trip is needed until
+    // the output sizes are known.
+    int64_t lensum = 0;
+    for (int L = 1; L <= kMaxLen; ++L) lensum += (int64_t)L * (pk.bucket_off[L + 1] - pk.bucket_off[L]);
+    const int64_t R_max = n + lensum;
+
+    // device counters: [0] dedup error, [1] fill error, [2] fallback partitions
+    DevBuf errb;
+    TCR_CHECK(errb.alloc(sizeof(int) * 4, s));
+    TCR_CUDA(cudaMemsetAsync(errb.as<void>(), 0, sizeof(int) * 4, s));
+    int* d_err = errb.as<int>();
 
     // ---- 1. dedup
     int64_t S = 1024;
     while (S < 2 * n) S <<= 1;
-    DevBuf table, slot_of, scount, flag, ubase, errb;
+    DevBuf table, slot_of, scount, flag, ubase;
     TCR_CHECK(table.alloc(sizeof(int32_t) * S, s));
     TCR_CHECK(slot_of.alloc(sizeof(int32_t) * n, s));
     TCR_CHECK(scount.alloc(sizeof(int32_t) * S, s));
     TCR_CHECK(flag.alloc(sizeof(int32_t) * S, s));
     TCR_CHECK(ubase.alloc(sizeof(int64_t) * (S + 1), s));
-    TCR_CHECK(errb.alloc(sizeof(int) * 4, s));  // [0] dedup, [1] fill, [2] fallback count
     TCR_CUDA(cudaMemsetAsync(table.as<void>(), 0xff, sizeof(int32_t) * S, s));
     TCR_CUDA(cudaMemsetAsync(scount.as<void>(), 0, sizeof(int32_t) * S, s));
-    TCR_CUDA(cudaMemsetAsync(errb.as<void>(), 0, sizeof(int) * 4, s));
-    int* d_err = errb.as<int>();
     k_dedup_insert<<<grid_for(n), kThreads, 0, s>>>(pk.canon_in.as<Canon>(), n, table.as<int32_t>(),
                                                     (uint32_t)(S - 1), slot_of.as<int32_t>(), scount.as<int32_t>(),
                                                     d_err);
@@ -564,141 +605,118 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     k_occupied<<<grid_for(S), kThreads, 0, s>>>(scount.as<int32_t>(), S, flag.as<int32_t>());
     TCR_LAUNCH_CHECK();
     TCR_CHECK(scan_exclusive_i32_to_i64(flag.as<int32_t>(), ubase.as<int64_t>(), S, s));
-    int64_t U = 0;
-    TCR_CUDA(cudaMemcpyAsync(&U, ubase.as<int64_t>() + S, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    TCR_CUDA(cudaStreamSynchronize(s));
+    const int64_t* d_U = ubase.as<int64_t>() + S;  // number of distinct strings, on the device
     DevBuf ucanon, ulen, umult, uid, mem_off, mcur, members, mpos;
-    TCR_CHECK(ucanon.alloc(sizeof(Canon) * U, s));
-    TCR_CHECK(ulen.alloc(U, s));
-    TCR_CHECK(umult.alloc(sizeof(int32_t) * U, s));
+    TCR_CHECK(ucanon.alloc(sizeof(Canon) * n, s));
+    TCR_CHECK(ulen.alloc(n, s));
+    TCR_CHECK(umult.alloc(sizeof(int32_t) * n, s));
     TCR_CHECK(uid.alloc(sizeof(int32_t) * n, s));
-    TCR_CHECK(mem_off.alloc(sizeof(int64_t) * (U + 1), s));
-    TCR_CHECK(mcur.alloc(sizeof(int32_t) * U, s));
+    TCR_CHECK(mem_off.alloc(sizeof(int64_t) * (n + 1), s));
+    TCR_CHECK(mcur.alloc(sizeof(int32_t) * n, s));
     TCR_CHECK(members.alloc(sizeof(int32_t) * n, s));
     TCR_CHECK(mpos.alloc(sizeof(int32_t) * n, s));
+    TCR_CUDA(cudaMemsetAsync(umult.as<void>(), 0, sizeof(int32_t) * n, s));  // ids >= U stay 0
     k_unique_compact<<<grid_for(S), kThreads, 0, s>>>(scount.as<int32_t>(), table.as<int32_t>(), ubase.as<int64_t>(),
                                                       S, pk.canon_in.as<Canon>(), pk.lens.as<uint8_t>(),
                                                       ucanon.as<Canon>(), ulen.as<uint8_t>(), umult.as<int32_t>());
     TCR_LAUNCH_CHECK();
     k_uid<<<grid_for(n), kThreads, 0, s>>>(slot_of.as<int32_t>(), ubase.as<int64_t>(), n, uid.as<int32_t>());
     TCR_LAUNCH_CHECK();
-    table.reset();
-    slot_of.reset();
-    scount.reset();
-    flag.reset();
-    ubase.reset();
-    TCR_CHECK(scan_exclusive_i32_to_i64(umult.as<int32_t>(), mem_off.as<int64_t>(), U, s));
-    TCR_CUDA(cudaMemsetAsync(mcur.as<void>(), 0, sizeof(int32_t) * U, s));
+    TCR_CHECK(scan_exclusive_i32_to_i64(umult.as<int32_t>(), mem_off.as<int64_t>(), n, s));
+    TCR_CUDA(cudaMemsetAsync(mcur.as<void>(), 0, sizeof(int32_t) * n, s));
     k_members<<<grid_for(n), kThreads, 0, s>>>(uid.as<int32_t>(), n, mem_off.as<int64_t>(), mcur.as<int32_t>(),
                                                members.as<int32_t>(), mpos.as<int32_t>());
     TCR_LAUNCH_CHECK();
     const int t1 = tm.mark();
 
-    // ---- 2. records and 3. join (l_max >= 1 only; l_max = 0 keeps duplicates only)
-    DevBuf edges;
-    int64_t E = 0, R = 0, nfb = 0;
-    int t2 = t1, t3 = t1, t4 = t1;
-    if (T >= 1 && U > 0) {
-        int64_t lensum = 0;
-        for (int L = 1; L <= kMaxLen; ++L) lensum += (int64_t)L * (pk.bucket_off[L + 1] - pk.bucket_off[L]);
-        const double mean_len = n > 0 ? (double)lensum / (double)n : 1.0;
-        const int64_t R_est = (int64_t)((double)U * (mean_len + 1.0)) + 1;
-        const int64_t P = std::max<int64_t>(1, std::min<int64_t>(R_est / kTargetPart + 1, 1LL << 30));
-        DevBuf pcnt, poff, recs, pedges, eoff, fb_list;
+    // ---- 2. records
+    DevBuf pcnt, poff, recs, fb_list, pedges, eoff, wsum, ucur, uoff;
+    TCR_CHECK(wsum.alloc(sizeof(int32_t) * n, s));
+    TCR_CHECK(ucur.alloc(sizeof(int32_t) * n, s));
+    TCR_CHECK(uoff.alloc(sizeof(int64_t) * (n + 1), s));
+    TCR_CUDA(cudaMemsetAsync(wsum.as<void>(), 0, sizeof(int32_t) * n, s));
+    const Weigh weigh{umult.as<int32_t>(), wsum.as<int32_t>()};
+    const bool join = T >= 1;
+    int64_t P = 1;
+    int jgrid = 1;
+    int t2 = t1, t3 = t1;
+    if (join) {
+        P = std::max<int64_t>(1, std::min<int64_t>(R_max / kTargetPart + 1, 1LL << 30));
         TCR_CHECK(pcnt.alloc(sizeof(int32_t) * P, s));
         TCR_CHECK(poff.alloc(sizeof(int64_t) * (P + 1), s));
-        TCR_CUDA(cudaMemsetAsync(pcnt.as<void>(), 0, sizeof(int32_t) * P, s));
-        k_records<false><<<grid_for(U), kThreads, 0, s>>>(ucanon.as<Canon>(), ulen.as<uint8_t>(), U, (uint32_t)P,
-                                                          pcnt.as<int32_t>(), nullptr, nullptr);
-        TCR_LAUNCH_CHECK();
-        TCR_CHECK(scan_exclusive_i32_to_i64(pcnt.as<int32_t>(), poff.as<int64_t>(), P, s));
-        TCR_CUDA(cudaMemcpyAsync(&R, poff.as<int64_t>() + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        TCR_CUDA(cudaStreamSynchronize(s));
-        TCR_CHECK(recs.alloc(sizeof(uint64_t) * R, s));
-        TCR_CUDA(cudaMemsetAsync(pcnt.as<void>(), 0, sizeof(int32_t) * P, s));
-        k_records<true><<<grid_for(U), kThreads, 0, s>>>(ucanon.as<Canon>(), ulen.as<uint8_t>(), U, (uint32_t)P,
-                                                         pcnt.as<int32_t>(), poff.as<int64_t>(), recs.as<uint64_t>());
-        TCR_LAUNCH_CHECK();
-        pcnt.reset();
-        t2 = tm.mark();
+        TCR_CHECK(recs.alloc(sizeof(uint64_t) * R_max, s));
+        TCR_CHECK(fb_list.alloc(sizeof(int32_t) * P, s));
         TCR_CHECK(pedges.alloc(sizeof(int64_t) * P, s));
         TCR_CHECK(eoff.alloc(sizeof(int64_t) * (P + 1), s));
-        TCR_CHECK(fb_list.alloc(sizeof(int32_t) * P, s));
-        const int jgrid = (int)std::min<int64_t>(ceil_div(P, kWarps), (int64_t)num_sms * 16);
-        k_join<false><<<jgrid, kThreads, 0, s>>>(poff.as<int64_t>(), P, recs.as<uint64_t>(), ucanon.as<Canon>(), cap,
-                                                 T, pedges.as<int64_t>(), nullptr, nullptr, fb_list.as<int32_t>(),
-                                                 d_err + 2);
+        TCR_CUDA(cudaMemsetAsync(pcnt.as<void>(), 0, sizeof(int32_t) * P, s));
+        k_records<false><<<grid_for(n), kThreads, 0, s>>>(ucanon.as<Canon>(), ulen.as<uint8_t>(), d_U, n,
+                                                          (uint32_t)P, pcnt.as<int32_t>(), nullptr, nullptr);
         TCR_LAUNCH_CHECK();
-        int h_nfb = 0;
-        TCR_CUDA(cudaMemcpyAsync(&h_nfb, d_err + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
-        TCR_CUDA(cudaStreamSynchronize(s));
-        nfb = h_nfb;
-        if (h_nfb > 0) {
-            k_join_fallback<false><<<std::min(h_nfb, num_sms * 4), kThreads, 0, s>>>(
-                fb_list.as<int32_t>(), h_nfb, poff.as<int64_t>(), recs.as<uint64_t>(), ucanon.as<Canon>(), T,
-                pedges.as<int64_t>(), nullptr, nullptr);
-            TCR_LAUNCH_CHECK();
-        }
+        TCR_CHECK(scan_exclusive_i32_to_i64(pcnt.as<int32_t>(), poff.as<int64_t>(), P, s));
+        TCR_CUDA(cudaMemsetAsync(pcnt.as<void>(), 0, sizeof(int32_t) * P, s));
+        k_records<true><<<grid_for(n), kThreads, 0, s>>>(ucanon.as<Canon>(), ulen.as<uint8_t>(), d_U, n,
+                                                         (uint32_t)P, pcnt.as<int32_t>(), poff.as<int64_t>(),
+                                                         recs.as<uint64_t>());
+        TCR_LAUNCH_CHECK();
+        t2 = tm.mark();
+        // ---- 3a. join, pass 1: weighted degrees W_u
+        jgrid = (int)std::min<int64_t>(ceil_div(P, kWarps), (int64_t)num_sms * 16);
+        k_join<false><<<jgrid, kThreads, 0, s>>>(poff.as<int64_t>(), P, recs.as<uint64_t>(), ucanon.as<Canon>(), cap,
+                                                 T, weigh, pedges.as<int64_t>(), nullptr, nullptr,
+                                                 fb_list.as<int32_t>(), d_err + 2);
+        TCR_LAUNCH_CHECK();
+        k_join_fallback<false><<<num_sms * 2, kThreads, 0, s>>>(fb_list.as<int32_t>(), d_err + 2, poff.as<int64_t>(),
+                                                                recs.as<uint64_t>(), ucanon.as<Canon>(), T, weigh,
+                                                                pedges.as<int64_t>(), nullptr, nullptr);
+        TCR_LAUNCH_CHECK();
         TCR_CHECK(scan_exclusive_i64(pedges.as<int64_t>(), eoff.as<int64_t>(), P, s));
-        TCR_CUDA(cudaMemcpyAsync(&E, eoff.as<int64_t>() + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        TCR_CUDA(cudaStreamSynchronize(s));
         t3 = tm.mark();
-        TCR_CHECK(edges.alloc(sizeof(int2) * E, s));
-        if (E > 0) {
-            k_join<true><<<jgrid, kThreads, 0, s>>>(poff.as<int64_t>(), P, recs.as<uint64_t>(), ucanon.as<Canon>(),
-                                                    cap, T, nullptr, eoff.as<int64_t>(), edges.as<int2>(), nullptr,
-                                                    nullptr);
-            TCR_LAUNCH_CHECK();
-            if (h_nfb > 0) {
-                k_join_fallback<true><<<std::min(h_nfb, num_sms * 4), kThreads, 0, s>>>(
-                    fb_list.as<int32_t>(), h_nfb, poff.as<int64_t>(), recs.as<uint64_t>(), ucanon.as<Canon>(), T,
-                    nullptr, eoff.as<int64_t>(), edges.as<int2>());
-                TCR_LAUNCH_CHECK();
-            }
-        }
-        t4 = tm.mark();
     }
 
-    // ---- 4. closed neighbourhoods and node degrees
-    DevBuf dsize, ucur, uoff, deg, off64, Sbuf;
-    TCR_CHECK(dsize.alloc(sizeof(int32_t) * U, s));
-    TCR_CHECK(ucur.alloc(sizeof(int32_t) * U, s));
-    TCR_CHECK(uoff.alloc(sizeof(int64_t) * (U + 1), s));
+    // ---- 4. list sizes D_u = m_u + W_u, list offsets, node degrees
+    DevBuf deg, off64;
     TCR_CHECK(deg.alloc(sizeof(int32_t) * n, s));
     TCR_CHECK(off64.alloc(sizeof(int64_t) * (n + 1), s));
-    TCR_CUDA(cudaMemsetAsync(dsize.as<void>(), 0, sizeof(int32_t) * U, s));
-    if (E > 0) {
-        k_weighted_degree<<<grid_for(E), kThreads, 0, s>>>(edges.as<int2>(), E, umult.as<int32_t>(),
-                                                           dsize.as<int32_t>());
-        TCR_LAUNCH_CHECK();
-    }
-    k_closed_size<<<grid_for(U), kThreads, 0, s>>>(umult.as<int32_t>(), U, dsize.as<int32_t>(), ucur.as<int32_t>());
+    k_closed_size<<<grid_for(n), kThreads, 0, s>>>(umult.as<int32_t>(), n, wsum.as<int32_t>(), ucur.as<int32_t>());
     TCR_LAUNCH_CHECK();
-    TCR_CHECK(scan_exclusive_i32_to_i64(dsize.as<int32_t>(), uoff.as<int64_t>(), U, s));
-    k_node_degree<<<grid_for(n), kThreads, 0, s>>>(uid.as<int32_t>(), n, dsize.as<int32_t>(), deg.as<int32_t>());
+    TCR_CHECK(scan_exclusive_i32_to_i64(wsum.as<int32_t>(), uoff.as<int64_t>(), n, s));
+    k_node_degree<<<grid_for(n), kThreads, 0, s>>>(uid.as<int32_t>(), n, wsum.as<int32_t>(), deg.as<int32_t>());
     TCR_LAUNCH_CHECK();
     TCR_CHECK(scan_exclusive_i32_to_i64(deg.as<int32_t>(), off64.as<int64_t>(), n, s));
-    int64_t sizes[2] = {0, 0};  // sum of D_u, nnz
-    TCR_CUDA(cudaMemcpyAsync(&sizes[0], uoff.as<int64_t>() + U, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    int64_t sizes[3] = {0, 0, 0};  // sum of D_u, nnz, unique edges
+    TCR_CUDA(cudaMemcpyAsync(&sizes[0], uoff.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TCR_CUDA(cudaMemcpyAsync(&sizes[1], off64.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    if (join) TCR_CUDA(cudaMemcpyAsync(&sizes[2], eoff.as<int64_t>() + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TCR_CUDA(cudaStreamSynchronize(s));
-    const int64_t SD = sizes[0], nnz = sizes[1];
-    dsize.reset();
+    const int64_t SD = sizes[0], nnz = sizes[1], E = sizes[2];
+    DevBuf Sbuf, edges;
     TCR_CHECK(Sbuf.alloc(sizeof(int32_t) * SD, s));
     k_closed_self<<<grid_for(n), kThreads, 0, s>>>(uid.as<int32_t>(), mpos.as<int32_t>(), n, uoff.as<int64_t>(),
                                                    Sbuf.as<int32_t>());
     TCR_LAUNCH_CHECK();
-    if (E > 0) {
+    // ---- 3b. join, pass 2: write the edges; then append neighbour member lists
+    if (join && E > 0) {
+        TCR_CHECK(edges.alloc(sizeof(int2) * E, s));
+        k_join<true><<<jgrid, kThreads, 0, s>>>(poff.as<int64_t>(), P, recs.as<uint64_t>(), ucanon.as<Canon>(), cap,
+                                                T, weigh, nullptr, eoff.as<int64_t>(), edges.as<int2>(), nullptr,
+                                                nullptr);
+        TCR_LAUNCH_CHECK();
+        k_join_fallback<true><<<num_sms * 2, kThreads, 0, s>>>(fb_list.as<int32_t>(), d_err + 2, poff.as<int64_t>(),
+                                                               recs.as<uint64_t>(), ucanon.as<Canon>(), T, weigh,
+                                                               nullptr, eoff.as<int64_t>(), edges.as<int2>());
+        TCR_LAUNCH_CHECK();
+        recs.reset();
         k_closed_edges<<<grid_for(2 * E), kThreads, 0, s>>>(edges.as<int2>(), E, umult.as<int32_t>(),
                                                             mem_off.as<int64_t>(), members.as<int32_t>(),
                                                             uoff.as<int64_t>(), ucur.as<int32_t>(),
                                                             Sbuf.as<int32_t>(), d_err + 1);
         TCR_LAUNCH_CHECK();
     }
+    const int t4 = tm.mark();
+    recs.reset();
     edges.reset();
+    TCR_CHECK(sort_rows(uoff.as<int64_t>(), Sbuf.as<int32_t>(), n, s, num_sms));
     const int t5 = tm.mark();
-    TCR_CHECK(sort_rows(uoff.as<int64_t>(), Sbuf.as<int32_t>(), U, s, num_sms));
-    const int t6 = tm.mark();
 
     // ---- 5. expand
     DevBuf cols;
@@ -706,9 +724,12 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     k_expand<<<(unsigned)std::min<int64_t>(ceil_div(n, kWarps), (int64_t)num_sms * 32), kThreads, 0, s>>>(
         uid.as<int32_t>(), n, uoff.as<int64_t>(), Sbuf.as<int32_t>(), off64.as<int64_t>(), cols.as<int32_t>());
     TCR_LAUNCH_CHECK();
-    const int t7 = tm.mark();
+    const int t6 = tm.mark();
     int h_err[4] = {0, 0, 0, 0};
+    int64_t h_U = 0, h_R = 0;
     TCR_CUDA(cudaMemcpyAsync(h_err, d_err, sizeof(h_err), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaMemcpyAsync(&h_U, d_U, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    if (join) TCR_CUDA(cudaMemcpyAsync(&h_R, poff.as<int64_t>() + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TCR_CUDA(cudaStreamSynchronize(s));
     if (h_err[0] || h_err[1]) return TCRNET_EDEVICE;
 
@@ -716,23 +737,23 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     out.cols = std::move(cols);
     out.degree = std::move(deg);
     out.nnz = nnz;
-    out.n_unique = U;
-    out.n_records = R;
+    out.n_unique = h_U;
+    out.n_records = h_R;
     out.unique_edges = E;
-    out.n_fallback = nfb;
+    out.n_fallback = h_err[2];
     out.closed_total = SD;
-    out.ms_phase[0] = tm.ms(t0, t1);
-    out.ms_phase[1] = tm.ms(t1, t2);
-    out.ms_phase[2] = tm.ms(t2, t3);
-    out.ms_phase[3] = tm.ms(t3, t4);
-    out.ms_phase[4] = tm.ms(t4, t5);
-    out.ms_phase[5] = tm.ms(t5, t6);
-    out.ms_phase[6] = tm.ms(t6, t7);
-    out.ms_phase[7] = tm.ms(t0, t7);
-    out.ms_join = tm.ms(t2, t3) + tm.ms(t3, t4);
+    out.ms_phase[0] = tm.ms(t0, t1);  // dedup
+    out.ms_phase[1] = tm.ms(t1, t2);  // records
+    out.ms_phase[2] = tm.ms(t2, t3);  // join pass 1 (weighted degrees)
+    out.ms_phase[3] = tm.ms(t3, t4);  // list sizes, join pass 2 (edges), list fill
+    out.ms_phase[4] = 0.0;
+    out.ms_phase[5] = tm.ms(t4, t5);  // list sort
+    out.ms_phase[6] = tm.ms(t5, t6);  // expand
+    out.ms_phase[7] = tm.ms(t0, t6);
+    out.ms_join = tm.ms(t2, t4);
     out.ms_scan = 0.0;
-    out.ms_fill = tm.ms(t4, t5);
-    out.ms_sort = tm.ms(t5, t6) + tm.ms(t6, t7);
+    out.ms_fill = tm.ms(t3, t4);
+    out.ms_sort = tm.ms(t4, t6);
     return TCRNET_OK;
 }
 

@@ -223,3 +223,55 @@ def test_deletion_counts_distinct_strings():
     assert st["n_unique"] == len(set(strs))
     assert st["n_records"] == sum(len(s) + 1 for s in set(strs))
     assert st["n_fallback"] == 0
+
+
+def _device_build(rep, method, **kw):
+    import torch
+
+    chars = torch.from_numpy(rep.chars).cuda()
+    offs = torch.from_numpy(rep.offsets).cuda()
+    g = tn.tcrnet_build_flat(chars, offs, 1, method=method, stream=torch.cuda.current_stream(), **kw)
+    return g
+
+
+def test_full_size_8e5_sampled_rows_and_invariants():
+    # the configuration bench.py times: N = 800,000 (config 2, seed 0), default method
+    from synthgen import generate_config2
+
+    rep = generate_config2(800_000, seed=0)
+    with _device_build(rep, "auto") as g:
+        off, cols, deg = g.copy_csr()
+        st = g.stats()
+    assert st["method"] == tn.METHOD_DELETION
+    off = np.asarray(off, dtype=np.int64)
+    check_invariants(off, cols, deg, rep.n)
+    rows = sample_rows(deg, 300, seed=3, top=40)
+    roff, rcols = oracle.rows(rep.chars, rep.offsets, rows)
+    assert_rows_equal(off, cols, rows, roff, rcols, "8e5 sampled rows")
+    # the all-pairs tile path builds the identical network
+    with _device_build(rep, "tile") as g:
+        o2, c2, d2 = g.copy_csr()
+    assert_csr_equal(off, cols, o2, c2, "tile vs deletion at 8e5")
+
+
+def test_full_size_8e6_sampled_rows_int64_offsets():
+    # config 3: N = 8,000,000, insertion 0-9 aa, nnz > 2^31 -> int64 offsets
+    from synthgen import generate_config3
+
+    rep = generate_config3(8_000_000, seed=0)
+    with _device_build(rep, "auto") as g:
+        n, nnz, o64 = g.info()
+        assert o64 and nnz > 2**31
+        import torch
+
+        off_d, cols_d, deg_d = g.copy_csr_device()
+    deg = deg_d.cpu().numpy()
+    off_h = off_d.cpu().numpy()
+    assert off_h[0] == 0 and off_h[-1] == nnz and np.array_equal(np.diff(off_h), deg)
+    assert int(deg.sum()) == nnz and nnz % 2 == 0
+    rows = sample_rows(deg, 40, seed=4, top=8)
+    roff, rcols = oracle.rows(rep.chars, rep.offsets, rows)
+    for k, i in enumerate(rows):
+        got = cols_d[int(off_h[i]):int(off_h[i + 1])].cpu().numpy()
+        want = rcols[roff[k]:roff[k + 1]]
+        assert np.array_equal(got, want), f"row {i}"
