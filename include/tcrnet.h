@@ -102,6 +102,7 @@ typedef struct tcrnet_stats {
     int64_t n_fallback;       /* deletion-join partitions joined by the exact fallback */
     int64_t kernel_launches;  /* CUDA kernels this call launched */
     int64_t closed_total;     /* deletion path: sum over distinct strings of |closed neighbourhood| */
+    int64_t two_pass_join;    /* deletion path: 1 if the edges overflowed the one-pass buffer */
     double ms_upload;         /* host -> device copy of the input (host inputs only) */
     double ms_pack;           /* validate, encode, bucket */
     double ms_count;          /* tile count pass / deletion join count */

@@ -58,6 +58,7 @@ class tcrnet_stats(ctypes.Structure):
         ("n_fallback", ctypes.c_int64),
         ("kernel_launches", ctypes.c_int64),
         ("closed_total", ctypes.c_int64),
+        ("two_pass_join", ctypes.c_int64),
         ("ms_upload", ctypes.c_double),
         ("ms_pack", ctypes.c_double),
         ("ms_count", ctypes.c_double),

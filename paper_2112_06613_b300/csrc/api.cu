@@ -5,6 +5,7 @@
 // deletion: deletion.cu) -> export (int32 or int64 offsets, degree). The
 // result stays in device memory owned by the handle; host copies happen only
 // in tcrnet_copy_csr.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -39,6 +40,74 @@ static thread_local int64_t t_launches = 0;
 
 void note_launch() { ++t_launches; }
 int64_t launches_so_far() { return t_launches; }
+
+// ---- build workspace arena (see common.cuh) ----
+namespace {
+constexpr size_t kArenaAlign = 256;
+constexpr size_t kMinChunk = 64ull << 20;
+struct Chunk {
+    char* p;
+    size_t size;
+};
+struct DeviceArena {
+    std::mutex mu;
+    std::vector<Chunk> chunks;
+    size_t cur = 0;   // chunk being carved
+    size_t used = 0;  // bytes used in chunks[cur]
+};
+DeviceArena g_arenas[64];
+thread_local DeviceArena* t_arena = nullptr;
+}  // namespace
+
+bool arena_active() { return t_arena != nullptr; }
+
+void* arena_carve(size_t bytes, cudaError_t* err) {
+    DeviceArena* a = t_arena;
+    if (!a) return nullptr;
+    bytes = (bytes + kArenaAlign - 1) & ~(kArenaAlign - 1);
+    while (a->cur < a->chunks.size()) {
+        Chunk& c = a->chunks[a->cur];
+        if (a->used + bytes <= c.size) {
+            void* p = c.p + a->used;
+            a->used += bytes;
+            return p;
+        }
+        ++a->cur;
+        a->used = 0;
+    }
+    // grow: a new chunk, kept for later calls
+    size_t sz = kMinChunk;
+    if (!a->chunks.empty()) sz = std::max(sz, a->chunks.back().size * 2);
+    sz = std::max(sz, bytes);
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, sz);
+    if (e != cudaSuccess) {
+        *err = e;
+        return nullptr;
+    }
+    a->chunks.push_back(Chunk{static_cast<char*>(p), sz});
+    a->cur = a->chunks.size() - 1;
+    a->used = bytes;
+    return p;
+}
+
+ArenaLease::ArenaLease(int device, cudaStream_t s) : dev_(device), s_(s) {
+    if (device < 0 || device >= 64 || t_arena) return;
+    DeviceArena& a = g_arenas[device];
+    if (!a.mu.try_lock()) return;  // another host thread is building on this device
+    held_ = true;
+    a.cur = 0;
+    a.used = 0;
+    t_arena = &a;
+}
+
+ArenaLease::~ArenaLease() {
+    if (!held_) return;
+    // the next lease reuses this memory: the call's work must be complete
+    cudaStreamSynchronize(s_);
+    t_arena = nullptr;
+    g_arenas[dev_].mu.unlock();
+}
 static thread_local char t_last_cuda[256] = {0};
 
 void note_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
@@ -136,12 +205,13 @@ tcrnet_status export_csr(tcrnet_graph* h, DevBuf& off64, DevBuf& cols, DevBuf& d
         h->d_offsets = off64.release();
     } else {
         DevBuf off32;
-        TCR_CHECK(off32.alloc(sizeof(int32_t) * (n + 1), s));
+        TCR_CHECK(off32.alloc_owned(sizeof(int32_t) * (n + 1), s));
         TCR_CHECK(narrow_offsets(off64.as<int64_t>(), off32.as<int32_t>(), n + 1, s));
         h->d_offsets = off32.release();
     }
     h->d_cols = static_cast<int32_t*>(cols.release());
     h->d_degree = static_cast<int32_t*>(degree.release());
+    if (!h->d_offsets || !h->d_cols || !h->d_degree) return TCRNET_EDEVICE;  // scratch cannot be exported
     return TCRNET_OK;
 }
 
@@ -150,19 +220,19 @@ tcrnet_status tile_method(tcrnet_graph* h, const TileSide& rows, const TileSide&
                           int T, bool force64, Phases& ph, cudaStream_t s, int sms) {
     tcrnet_stats& st = h->stats;
     DevBuf count, off64, out_cols, cursor;
-    TCR_CHECK(count.alloc(sizeof(int32_t) * n_rows, s));
+    TCR_CHECK(count.alloc_owned(sizeof(int32_t) * n_rows, s));
     TCR_CUDA(cudaMemsetAsync(count.as<void>(), 0, sizeof(int32_t) * n_rows, s));
     const int e0 = ph.mark();
     int64_t pairs = 0;
     TCR_CHECK(tile_pass(rows, cols, sym, T, false, count.as<int32_t>(), nullptr, nullptr, nullptr, &pairs, s, sms));
     const int e1 = ph.mark();
-    TCR_CHECK(off64.alloc(sizeof(int64_t) * (n_rows + 1), s));
+    TCR_CHECK(off64.alloc_owned(sizeof(int64_t) * (n_rows + 1), s));
     TCR_CHECK(scan_exclusive_i32_to_i64(count.as<int32_t>(), off64.as<int64_t>(), n_rows, s));
     int64_t nnz = 0;
     TCR_CUDA(cudaMemcpyAsync(&nnz, off64.as<int64_t>() + n_rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TCR_CUDA(cudaStreamSynchronize(s));
     const int e2 = ph.mark();
-    TCR_CHECK(out_cols.alloc(sizeof(int32_t) * nnz, s));
+    TCR_CHECK(out_cols.alloc_owned(sizeof(int32_t) * nnz, s));
     TCR_CHECK(cursor.alloc(sizeof(int32_t) * n_rows, s));
     TCR_CUDA(cudaMemsetAsync(cursor.as<void>(), 0, sizeof(int32_t) * n_rows, s));
     if (nnz > 0)
@@ -267,6 +337,7 @@ tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n
     h->stats.threshold = T;
     h->stats.n = n;
 
+    ArenaLease lease(dev, s);
     Phases ph(opt.profile != 0, s);
     const int64_t launches0 = launches_so_far();
     auto fail = [&](tcrnet_status st) {
@@ -297,10 +368,10 @@ tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n
     for (int L = 0; L < kMaxLen + 2; ++L) h->bucket_off[L] = pk.bucket_off[L];
     if (n == 0) {
         DevBuf off64, cols, deg;
-        if ((st = off64.alloc(sizeof(int64_t), s)) != TCRNET_OK) return fail(st);
+        if ((st = off64.alloc_owned(sizeof(int64_t), s)) != TCRNET_OK) return fail(st);
         if (cudaMemsetAsync(off64.as<void>(), 0, sizeof(int64_t), s) != cudaSuccess) return fail(TCRNET_EDEVICE);
-        if ((st = cols.alloc(0, s)) != TCRNET_OK) return fail(st);
-        if ((st = deg.alloc(0, s)) != TCRNET_OK) return fail(st);
+        if ((st = cols.alloc_owned(0, s)) != TCRNET_OK) return fail(st);
+        if ((st = deg.alloc_owned(0, s)) != TCRNET_OK) return fail(st);
         if ((st = export_csr(h, off64, cols, deg, 0, 0, opt.force_offsets64 != 0, s)) != TCRNET_OK) return fail(st);
     } else if (method == TCRNET_METHOD_TILE) {
         TileSide side{pk.canon.as<Canon>(), pk.perm.as<int32_t>(), pk.bucket_off};
@@ -315,6 +386,7 @@ tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n
         h->stats.unique_edges = dr.unique_edges;
         h->stats.n_fallback = dr.n_fallback;
         h->stats.closed_total = dr.closed_total;
+        h->stats.two_pass_join = dr.two_pass_join;
         h->stats.ms_count = dr.ms_join;
         h->stats.ms_scan = dr.ms_scan;
         h->stats.ms_write = dr.ms_fill;
@@ -425,6 +497,7 @@ tcrnet_status tcrnet_query_flat(tcrnet_handle h, const uint8_t* chars, const int
         delete r;
         return st;
     };
+    ArenaLease lease(h->device, s);
     Phases ph(false, s);
     const int64_t launches0 = launches_so_far();
     Inputs in;
@@ -432,10 +505,10 @@ tcrnet_status tcrnet_query_flat(tcrnet_handle h, const uint8_t* chars, const int
     if (st != TCRNET_OK) return fail(st);
     if (m == 0) {
         DevBuf off64, cols, deg;
-        if ((st = off64.alloc(sizeof(int64_t), s)) != TCRNET_OK) return fail(st);
+        if ((st = off64.alloc_owned(sizeof(int64_t), s)) != TCRNET_OK) return fail(st);
         if (cudaMemsetAsync(off64.as<void>(), 0, sizeof(int64_t), s) != cudaSuccess) return fail(TCRNET_EDEVICE);
-        if ((st = cols.alloc(0, s)) != TCRNET_OK) return fail(st);
-        if ((st = deg.alloc(0, s)) != TCRNET_OK) return fail(st);
+        if ((st = cols.alloc_owned(0, s)) != TCRNET_OK) return fail(st);
+        if ((st = deg.alloc_owned(0, s)) != TCRNET_OK) return fail(st);
         if ((st = export_csr(r, off64, cols, deg, 0, 0, false, s)) != TCRNET_OK) return fail(st);
     } else {
         Packed pk;

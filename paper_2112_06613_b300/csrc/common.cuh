@@ -101,20 +101,48 @@ int64_t launches_so_far();
         TCR_CUDA(cudaGetLastError()); \
     } while (0)
 
-// Stream-ordered device buffer (cudaMallocAsync / cudaFreeAsync). Freed when it
-// goes out of scope unless released.
+// Build workspace: scratch memory of a build or query is carved from a
+// per-device arena of cached chunks (a bump allocator reset at the start of
+// every call), so a call in steady state makes no allocator calls for its
+// scratch. A call leases the arena for its duration (ArenaLease); if another
+// host thread holds it, the call falls back to stream-ordered allocations.
+// Buffers handed to a handle are never carved from the arena.
+void* arena_carve(size_t bytes, cudaError_t* err);  // nullptr: no lease on this thread
+bool arena_active();
+
+class ArenaLease {
+public:
+    ArenaLease(int device, cudaStream_t s);
+    ~ArenaLease();
+    ArenaLease(const ArenaLease&) = delete;
+    ArenaLease& operator=(const ArenaLease&) = delete;
+
+private:
+    int dev_ = -1;
+    cudaStream_t s_ = 0;
+    bool held_ = false;
+};
+
+// Device buffer: arena scratch while a lease is active on this thread
+// (alloc), otherwise stream-ordered cudaMallocAsync / cudaFreeAsync; alloc_owned
+// always allocates (for results a handle keeps). Freed when it goes out of
+// scope unless released.
 class DevBuf {
 public:
     DevBuf() = default;
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
-    DevBuf(DevBuf&& o) noexcept : p_(o.p_), bytes_(o.bytes_), s_(o.s_) { o.p_ = nullptr; o.bytes_ = 0; }
+    DevBuf(DevBuf&& o) noexcept : p_(o.p_), bytes_(o.bytes_), s_(o.s_), arena_(o.arena_) {
+        o.p_ = nullptr;
+        o.bytes_ = 0;
+    }
     DevBuf& operator=(DevBuf&& o) noexcept {
         if (this != &o) {
             reset();
             p_ = o.p_;
             bytes_ = o.bytes_;
             s_ = o.s_;
+            arena_ = o.arena_;
             o.p_ = nullptr;
             o.bytes_ = 0;
         }
@@ -122,9 +150,28 @@ public:
     }
     ~DevBuf() { reset(); }
     tcrnet_status alloc(size_t bytes, cudaStream_t s) {
+        if (arena_active()) {
+            reset();
+            cudaError_t e = cudaSuccess;
+            void* p = arena_carve(bytes == 0 ? 16 : bytes, &e);
+            if (!p) {
+                note_cuda_error(e, "arena chunk", __FILE__, __LINE__);
+                (void)cudaGetLastError();
+                return status_of(e == cudaSuccess ? cudaErrorMemoryAllocation : e);
+            }
+            p_ = p;
+            bytes_ = bytes;
+            s_ = s;
+            arena_ = true;
+            return TCRNET_OK;
+        }
+        return alloc_owned(bytes, s);
+    }
+    tcrnet_status alloc_owned(size_t bytes, cudaStream_t s) {
         reset();
         s_ = s;
         bytes_ = bytes;
+        arena_ = false;
         if (bytes == 0) bytes = 16;
         cudaError_t e = cudaMallocAsync(&p_, bytes, s);
         if (e != cudaSuccess) {
@@ -137,11 +184,14 @@ public:
         return TCRNET_OK;
     }
     void reset() {
-        if (p_) cudaFreeAsync(p_, s_);
+        if (p_ && !arena_) cudaFreeAsync(p_, s_);
         p_ = nullptr;
         bytes_ = 0;
+        arena_ = false;
     }
+    // Hand the allocation to its new owner; arena scratch cannot be handed out.
     void* release() {
+        if (arena_) return nullptr;
         void* p = p_;
         p_ = nullptr;
         bytes_ = 0;
@@ -155,6 +205,7 @@ private:
     void* p_ = nullptr;
     size_t bytes_ = 0;
     cudaStream_t s_ = 0;
+    bool arena_ = false;
 };
 
 }  // namespace tcr

@@ -35,9 +35,10 @@
 //     equal (hash, p) (equal length, one substitution), and each run-start
 //     deletion record with the full record of the same content (one indel).
 //     Partitions over capacity or with a hash collision take an exact
-//     quadratic fallback. The join runs twice: the first pass adds m_v to
-//     W_u (and m_u to W_v) for every edge {u, v} and counts the edges of each
-//     partition; the second writes the edges at scanned positions.
+//     quadratic fallback. The join adds m_v to W_u (and m_u to W_v) for every
+//     edge {u, v} and writes the edges into a buffer of 2 x (records bound)
+//     entries (one atomic per partition); if they do not fit, a second pass
+//     writes them at positions scanned from the per-partition counts.
 //  4. closed neighbourhoods: D_u = m_u + W_u; S_u = M_u followed by every
 //     M_v (appended at a slot taken from a per-string cursor; long member
 //     lists are copied by a whole warp), written once per distinct string and
@@ -73,11 +74,13 @@ __device__ __forceinline__ uint64_t fmix64(uint64_t x) {
     return x;
 }
 
+// Content hash: odd-multiplier combination of the four words, then one
+// finaliser. Only the partition choice and the in-partition order depend on
+// it; equal hashes are always confirmed by comparing contents.
 __device__ __forceinline__ uint64_t hash_canon(const Canon& c) {
-    uint64_t h = 0x243f6a8885a308d3ULL;
-#pragma unroll
-    for (int w = 0; w < kCanonWords; ++w) h = fmix64(h ^ (c.w[w] + 0x9e3779b97f4a7c15ULL * (uint64_t)(w + 1)));
-    return h;
+    const uint64_t x = c.w[0] + 0x9e3779b97f4a7c15ULL * c.w[1] + 0xc2b2ae3d27d4eb4fULL * c.w[2] +
+                       0x165667b19e3779f9ULL * c.w[3];
+    return fmix64(x ^ 0x243f6a8885a308d3ULL);
 }
 
 __device__ __forceinline__ bool canon_eq(const Canon& a, const Canon& b) {
@@ -338,15 +341,25 @@ template <bool WRITE>
 __global__ void __launch_bounds__(kThreads)
 k_join(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __restrict__ recs,
        const Canon* __restrict__ ucanon, int cap, int T, Weigh weigh, int64_t* __restrict__ pedges,
-       const int64_t* __restrict__ eoff, int2* __restrict__ edges, int32_t* __restrict__ fb_list,
-       int* __restrict__ fb_count) {
+       const int64_t* __restrict__ eoff, int2* __restrict__ edges, unsigned long long* __restrict__ ecur,
+       int64_t ecap, int32_t* __restrict__ fb_list, int* __restrict__ fb_count) {
     __shared__ uint64_t sbuf[kWarps][kWarpCap];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint64_t* buf = sbuf[warp];
-    const int64_t stride = (int64_t)gridDim.x * kWarps;
-    for (int64_t pid = (int64_t)blockIdx.x * kWarps + warp; pid < P; pid += stride) {
-        const int64_t base = poff[pid];
-        const int64_t s64 = poff[pid + 1] - base;
+    // a warp takes 32 consecutive partitions; lane j fetches the bounds of the j-th
+    const int64_t wid = (int64_t)blockIdx.x * kWarps + warp;
+    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+    for (int64_t p0 = wid * 32; p0 < P; p0 += nwarps * 32) {
+      int64_t my_base = 0, my_size = 0;
+      if (p0 + lane < P) {
+          my_base = poff[p0 + lane];
+          my_size = poff[p0 + lane + 1] - my_base;
+      }
+      const int pcount = (P - p0) < 32 ? (int)(P - p0) : 32;
+      for (int j = 0; j < pcount; ++j) {
+        const int64_t pid = p0 + j;
+        const int64_t base = __shfl_sync(kFull, my_base, j);
+        const int64_t s64 = __shfl_sync(kFull, my_size, j);
         if (s64 > cap) {
             if (!WRITE && lane == 0) {
                 fb_list[atomicAdd(fb_count, 1)] = (int32_t)pid;
@@ -379,11 +392,22 @@ k_join(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __restrict__
             continue;
         }
         if (!WRITE) {
+            // weigh, count, and write the edges into the capped buffer when they fit
             int64_t mine = 0;
             for (int k = lane; k < s; k += 32) mine += record_edges(buf, k, s, T, weigh);
             int64_t excl;
             const int64_t total = warp_scan(mine, excl, lane);
             if (lane == 0) pedges[pid] = total;
+            if (total) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(ecur, (unsigned long long)total);
+                base = __shfl_sync(kFull, base, 0);
+                if ((int64_t)(base + total) <= ecap) {
+                    int64_t pos = (int64_t)base + excl;
+                    for (int k = lane; k < s; k += 32)
+                        record_edges(buf, k, s, T, [&](int32_t a, int32_t b) { edges[pos++] = make_int2(a, b); });
+                }
+            }
         } else {
             int64_t mine = 0;
             for (int k = lane; k < s; k += 32) mine += record_edges(buf, k, s, T, [](int32_t, int32_t) {});
@@ -394,6 +418,7 @@ k_join(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __restrict__
                 record_edges(buf, k, s, T, [&](int32_t a, int32_t b) { edges[pos++] = make_int2(a, b); });
         }
         __syncwarp();
+      }
     }
 }
 
@@ -402,7 +427,8 @@ template <bool WRITE>
 __global__ void __launch_bounds__(kThreads)
 k_join_fallback(const int32_t* __restrict__ fb_list, const int* __restrict__ fb_count, const int64_t* __restrict__ poff,
                 const uint64_t* __restrict__ recs, const Canon* __restrict__ ucanon, int T, Weigh weigh,
-                int64_t* __restrict__ pedges, const int64_t* __restrict__ eoff, int2* __restrict__ edges) {
+                int64_t* __restrict__ pedges, const int64_t* __restrict__ eoff, int2* __restrict__ edges,
+                unsigned long long* __restrict__ ecur, int64_t ecap) {
     __shared__ int64_t wtot[kWarps];
     const int nfb = *fb_count;
     for (int f = blockIdx.x; f < nfb; f += gridDim.x) {
@@ -437,6 +463,15 @@ k_join_fallback(const int32_t* __restrict__ fb_list, const int* __restrict__ fb_
             int64_t excl;
             const int64_t total = block_scan(mine, excl, wtot);
             if (threadIdx.x == 0) pedges[pid] = total;
+            if (total) {
+                __shared__ unsigned long long base;
+                if (threadIdx.x == 0) base = atomicAdd(ecur, (unsigned long long)total);
+                __syncthreads();
+                if ((int64_t)(base + total) <= ecap) {
+                    int64_t pos = (int64_t)base + excl;
+                    scan_pairs([&](int32_t a, int32_t b) { edges[pos++] = make_int2(a, b); });
+                }
+            }
         } else {
             const int64_t mine = scan_pairs([](int32_t, int32_t) {});
             int64_t excl;
@@ -513,26 +548,37 @@ k_closed_edges(const int2* __restrict__ edges, int64_t E, const int32_t* __restr
 
 // ---- 5. expand --------------------------------------------------------------
 
-// Row i = sorted S_u without i; one warp per row, lanes along the row.
+// Row i = sorted S_u without i. A warp takes 32 rows: each lane fetches one
+// row's list bounds (independent loads in parallel), then the warp copies the
+// rows one after another, lanes along the row. S_u is sorted and contains i
+// once, so element x at position k goes to k - (x > i).
 __global__ void k_expand(const int32_t* __restrict__ uid, int64_t n, const int64_t* __restrict__ uoff,
                          const int32_t* __restrict__ S, const int64_t* __restrict__ off, int32_t* __restrict__ cols) {
     const int lane = threadIdx.x & 31;
-    const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += stride) {
-        const int32_t u = uid[i];
-        const int64_t s0 = uoff[u];
-        const int64_t D = uoff[u + 1] - s0;
-        if (D <= 1) continue;
-        const int32_t* su = S + s0;
-        int64_t lo = 0, hi = D;  // position of i in S_u
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (su[mid] < (int32_t)i) lo = mid + 1; else hi = mid;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r0 = w0 * 32; r0 < n; r0 += nw * 32) {
+        const int64_t my = r0 + lane;
+        int64_t s0 = 0, D = 0, o = 0;
+        if (my < n) {
+            const int32_t u = uid[my];
+            s0 = uoff[u];
+            D = uoff[u + 1] - s0;
+            o = off[my];
         }
-        const int64_t o = off[i];
-        for (int64_t k = lane; k < D; k += 32) {
-            const int32_t x = su[k];
-            if (k != lo) cols[o + k - (k > lo ? 1 : 0)] = x;
+        const int cnt = (n - r0) < 32 ? (int)(n - r0) : 32;
+        for (int j = 0; j < cnt; ++j) {
+            const int64_t js0 = __shfl_sync(kFull, s0, j);
+            const int64_t jD = __shfl_sync(kFull, D, j);
+            const int64_t jo = __shfl_sync(kFull, o, j);
+            const int32_t me = (int32_t)(r0 + j);
+            const int32_t* su = S + js0;
+            int32_t* row = cols + jo;
+            for (int64_t k = lane; k < jD; k += 32) {
+                const int32_t x = su[k];
+                const int64_t q = k - (x > me ? 1 : 0);
+                if (x != me && q < jD - 1) row[q] = x;  // q < D - 1 always holds when i is in S_u
+            }
         }
     }
 }
@@ -581,11 +627,16 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     for (int L = 1; L <= kMaxLen; ++L) lensum += (int64_t)L * (pk.bucket_off[L + 1] - pk.bucket_off[L]);
     const int64_t R_max = n + lensum;
 
-    // device counters: [0] dedup error, [1] fill error, [2] fallback partitions
-    DevBuf errb;
+    // device counters: [0] dedup error, [1] fill error, [2] fallback partitions;
+    // edge cursor
+    DevBuf errb, ecur_b;
     TCR_CHECK(errb.alloc(sizeof(int) * 4, s));
+    TCR_CHECK(ecur_b.alloc(sizeof(unsigned long long), s));
     TCR_CUDA(cudaMemsetAsync(errb.as<void>(), 0, sizeof(int) * 4, s));
+    TCR_CUDA(cudaMemsetAsync(ecur_b.as<void>(), 0, sizeof(unsigned long long), s));
     int* d_err = errb.as<int>();
+    unsigned long long* d_ecur = ecur_b.as<unsigned long long>();
+    const int64_t ecap = 2 * R_max + 64;  // edges of the one-pass join
 
     // ---- 1. dedup
     int64_t S = 1024;
@@ -630,7 +681,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     const int t1 = tm.mark();
 
     // ---- 2. records
-    DevBuf pcnt, poff, recs, fb_list, pedges, eoff, wsum, ucur, uoff;
+    DevBuf pcnt, poff, recs, fb_list, pedges, eoff, wsum, ucur, uoff, edges;
     TCR_CHECK(wsum.alloc(sizeof(int32_t) * n, s));
     TCR_CHECK(ucur.alloc(sizeof(int32_t) * n, s));
     TCR_CHECK(uoff.alloc(sizeof(int64_t) * (n + 1), s));
@@ -648,35 +699,37 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         TCR_CHECK(fb_list.alloc(sizeof(int32_t) * P, s));
         TCR_CHECK(pedges.alloc(sizeof(int64_t) * P, s));
         TCR_CHECK(eoff.alloc(sizeof(int64_t) * (P + 1), s));
+        TCR_CHECK(edges.alloc(sizeof(int2) * ecap, s));
         TCR_CUDA(cudaMemsetAsync(pcnt.as<void>(), 0, sizeof(int32_t) * P, s));
-        k_records<false><<<grid_for(n), kThreads, 0, s>>>(ucanon.as<Canon>(), ulen.as<uint8_t>(), d_U, n,
+        const unsigned rgrid = grid_for(n);
+        k_records<false><<<rgrid, kThreads, 0, s>>>(ucanon.as<Canon>(), ulen.as<uint8_t>(), d_U, n,
                                                           (uint32_t)P, pcnt.as<int32_t>(), nullptr, nullptr);
         TCR_LAUNCH_CHECK();
         TCR_CHECK(scan_exclusive_i32_to_i64(pcnt.as<int32_t>(), poff.as<int64_t>(), P, s));
         TCR_CUDA(cudaMemsetAsync(pcnt.as<void>(), 0, sizeof(int32_t) * P, s));
-        k_records<true><<<grid_for(n), kThreads, 0, s>>>(ucanon.as<Canon>(), ulen.as<uint8_t>(), d_U, n,
+        k_records<true><<<rgrid, kThreads, 0, s>>>(ucanon.as<Canon>(), ulen.as<uint8_t>(), d_U, n,
                                                          (uint32_t)P, pcnt.as<int32_t>(), poff.as<int64_t>(),
                                                          recs.as<uint64_t>());
         TCR_LAUNCH_CHECK();
         t2 = tm.mark();
         // ---- 3a. join, pass 1: weighted degrees W_u
-        jgrid = (int)std::min<int64_t>(ceil_div(P, kWarps), (int64_t)num_sms * 16);
+        jgrid = (int)std::min<int64_t>(ceil_div(P, 32 * kWarps), (int64_t)num_sms * 16);
         k_join<false><<<jgrid, kThreads, 0, s>>>(poff.as<int64_t>(), P, recs.as<uint64_t>(), ucanon.as<Canon>(), cap,
-                                                 T, weigh, pedges.as<int64_t>(), nullptr, nullptr,
-                                                 fb_list.as<int32_t>(), d_err + 2);
+                                                 T, weigh, pedges.as<int64_t>(), nullptr, edges.as<int2>(), d_ecur,
+                                                 ecap, fb_list.as<int32_t>(), d_err + 2);
         TCR_LAUNCH_CHECK();
         k_join_fallback<false><<<num_sms * 2, kThreads, 0, s>>>(fb_list.as<int32_t>(), d_err + 2, poff.as<int64_t>(),
                                                                 recs.as<uint64_t>(), ucanon.as<Canon>(), T, weigh,
-                                                                pedges.as<int64_t>(), nullptr, nullptr);
+                                                                pedges.as<int64_t>(), nullptr, edges.as<int2>(),
+                                                                d_ecur, ecap);
         TCR_LAUNCH_CHECK();
-        TCR_CHECK(scan_exclusive_i64(pedges.as<int64_t>(), eoff.as<int64_t>(), P, s));
         t3 = tm.mark();
     }
 
     // ---- 4. list sizes D_u = m_u + W_u, list offsets, node degrees
     DevBuf deg, off64;
-    TCR_CHECK(deg.alloc(sizeof(int32_t) * n, s));
-    TCR_CHECK(off64.alloc(sizeof(int64_t) * (n + 1), s));
+    TCR_CHECK(deg.alloc_owned(sizeof(int32_t) * n, s));  // results are handed to the handle
+    TCR_CHECK(off64.alloc_owned(sizeof(int64_t) * (n + 1), s));
     k_closed_size<<<grid_for(n), kThreads, 0, s>>>(umult.as<int32_t>(), n, wsum.as<int32_t>(), ucur.as<int32_t>());
     TCR_LAUNCH_CHECK();
     TCR_CHECK(scan_exclusive_i32_to_i64(wsum.as<int32_t>(), uoff.as<int64_t>(), n, s));
@@ -686,25 +739,33 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     int64_t sizes[3] = {0, 0, 0};  // sum of D_u, nnz, unique edges
     TCR_CUDA(cudaMemcpyAsync(&sizes[0], uoff.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TCR_CUDA(cudaMemcpyAsync(&sizes[1], off64.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    if (join) TCR_CUDA(cudaMemcpyAsync(&sizes[2], eoff.as<int64_t>() + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaMemcpyAsync(&sizes[2], d_ecur, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TCR_CUDA(cudaStreamSynchronize(s));
     const int64_t SD = sizes[0], nnz = sizes[1], E = sizes[2];
-    DevBuf Sbuf, edges;
+    int n_two_pass = 0;
+    DevBuf Sbuf;
     TCR_CHECK(Sbuf.alloc(sizeof(int32_t) * SD, s));
     k_closed_self<<<grid_for(n), kThreads, 0, s>>>(uid.as<int32_t>(), mpos.as<int32_t>(), n, uoff.as<int64_t>(),
                                                    Sbuf.as<int32_t>());
     TCR_LAUNCH_CHECK();
-    // ---- 3b. join, pass 2: write the edges; then append neighbour member lists
-    if (join && E > 0) {
+    // ---- 3b. edges that did not fit: second join pass at scanned positions;
+    // then append neighbour member lists
+    if (join && E > ecap) {
+        edges.reset();
         TCR_CHECK(edges.alloc(sizeof(int2) * E, s));
+        TCR_CHECK(scan_exclusive_i64(pedges.as<int64_t>(), eoff.as<int64_t>(), P, s));
         k_join<true><<<jgrid, kThreads, 0, s>>>(poff.as<int64_t>(), P, recs.as<uint64_t>(), ucanon.as<Canon>(), cap,
-                                                T, weigh, nullptr, eoff.as<int64_t>(), edges.as<int2>(), nullptr,
-                                                nullptr);
+                                                T, weigh, nullptr, eoff.as<int64_t>(), edges.as<int2>(), nullptr, 0,
+                                                nullptr, nullptr);
         TCR_LAUNCH_CHECK();
         k_join_fallback<true><<<num_sms * 2, kThreads, 0, s>>>(fb_list.as<int32_t>(), d_err + 2, poff.as<int64_t>(),
                                                                recs.as<uint64_t>(), ucanon.as<Canon>(), T, weigh,
-                                                               nullptr, eoff.as<int64_t>(), edges.as<int2>());
+                                                               nullptr, eoff.as<int64_t>(), edges.as<int2>(),
+                                                               nullptr, 0);
         TCR_LAUNCH_CHECK();
+        n_two_pass = 1;
+    }
+    if (join && E > 0) {
         recs.reset();
         k_closed_edges<<<grid_for(2 * E), kThreads, 0, s>>>(edges.as<int2>(), E, umult.as<int32_t>(),
                                                             mem_off.as<int64_t>(), members.as<int32_t>(),
@@ -720,8 +781,8 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
 
     // ---- 5. expand
     DevBuf cols;
-    TCR_CHECK(cols.alloc(sizeof(int32_t) * nnz, s));
-    k_expand<<<(unsigned)std::min<int64_t>(ceil_div(n, kWarps), (int64_t)num_sms * 32), kThreads, 0, s>>>(
+    TCR_CHECK(cols.alloc_owned(sizeof(int32_t) * nnz, s));
+    k_expand<<<(unsigned)std::min<int64_t>(ceil_div(n, 32 * kWarps), (int64_t)num_sms * 16), kThreads, 0, s>>>(
         uid.as<int32_t>(), n, uoff.as<int64_t>(), Sbuf.as<int32_t>(), off64.as<int64_t>(), cols.as<int32_t>());
     TCR_LAUNCH_CHECK();
     const int t6 = tm.mark();
@@ -742,6 +803,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     out.unique_edges = E;
     out.n_fallback = h_err[2];
     out.closed_total = SD;
+    out.two_pass_join = n_two_pass;
     out.ms_phase[0] = tm.ms(t0, t1);  // dedup
     out.ms_phase[1] = tm.ms(t1, t2);  // records
     out.ms_phase[2] = tm.ms(t2, t3);  // join pass 1 (weighted degrees)

@@ -21,6 +21,7 @@ struct DeletionResult {
     int64_t unique_edges = 0;
     int64_t n_fallback = 0;    // partitions joined by the exact quadratic fallback
     int64_t closed_total = 0;  // sum over distinct strings of closed-neighbourhood sizes
+    int two_pass_join = 0;     // 1 when the edges overflowed the one-pass buffer
     double ms_join = 0, ms_scan = 0, ms_fill = 0, ms_sort = 0;
     // dedup, records, join count, join write, closed fill, closed sort, expand, total
     double ms_phase[8] = {0};

@@ -107,8 +107,8 @@ tcrnet_status pack_strings(const uint8_t* d_chars, const int64_t* d_offsets, int
     const int nblocks = (int)ceil_div(n, kPackThreads);
     TCR_CHECK(out.canon_in.alloc(sizeof(Canon) * n, s));
     TCR_CHECK(out.lens.alloc(n, s));
-    TCR_CHECK(out.canon.alloc(sizeof(Canon) * n, s));
-    TCR_CHECK(out.perm.alloc(sizeof(int32_t) * n, s));
+    TCR_CHECK(out.canon.alloc_owned(sizeof(Canon) * n, s));  // kept by the handle
+    TCR_CHECK(out.perm.alloc_owned(sizeof(int32_t) * n, s));
     const int64_t ncnt = (int64_t)kBins * nblocks;
     DevBuf blockcnt, blockoff, err, bounds;
     TCR_CHECK(blockcnt.alloc(sizeof(int32_t) * ncnt, s));

@@ -275,3 +275,18 @@ def test_full_size_8e6_sampled_rows_int64_offsets():
         got = cols_d[int(off_h[i]):int(off_h[i + 1])].cpu().numpy()
         want = rcols[roff[k]:roff[k + 1]]
         assert np.array_equal(got, want), f"row {i}"
+
+
+def test_deletion_dense_unique_graph_takes_two_pass_join():
+    # every 1- and 2-letter string: far more edges between distinct strings than
+    # records, so the one-pass edge buffer overflows and the exact second pass runs
+    letters = list(ALPHABET)
+    strs = letters + [a + b for a in letters for b in letters] + ["AA", "C", "CAS"]
+    rep = from_strings(strs)
+    off, cols, deg, st = gpu_csr(rep, 1, "deletion")
+    assert st["two_pass_join"] == 1
+    ro, rc, _ = oracle_csr(rep, 1)
+    assert_csr_equal(off, cols, ro, rc, "dense unique graph")
+    # the generator workload fits in one pass
+    _, _, _, st = gpu_csr(generate_config1(5000, seed=3), 1, "deletion")
+    assert st["two_pass_join"] == 0
