@@ -59,6 +59,7 @@ constexpr int kWarpCap = 128;     // records per partition joined by one warp
 constexpr int kTargetPart = 32;   // mean records per partition
 constexpr uint32_t kTagF = 63;    // position tag of a full-string record
 constexpr uint64_t kUMask = (1ull << 25) - 1;
+constexpr int kEdgeSegs = 64;     // edge buffer segments (one cursor each), by partition id
 
 __device__ __forceinline__ uint32_t rec_u(uint64_t r) { return (uint32_t)(r & kUMask); }
 __device__ __forceinline__ uint32_t rec_p(uint64_t r) { return (uint32_t)(r >> 26) & 63u; }
@@ -337,12 +338,48 @@ struct Weigh {
     }
 };
 
+// Counting traversal with exactness check: every pair that would become an
+// edge is confirmed by comparing contents. A failed comparison means two
+// different contents share a 32-bit hash in this partition (bad = true); the
+// partition then goes to the exact fallback. A collision that could hide or
+// fake an edge always puts two different contents into some attempted pair
+// (same run of (hash, p), or a deletion record and the group's last full
+// record), so checking only attempted pairs is enough.
+__device__ __forceinline__ int64_t record_edges_checked(const uint64_t* buf, int k, int s, int T,
+                                                        const Canon* __restrict__ ucanon, bool& bad) {
+    const uint64_t key = buf[k];
+    if (rec_p(key) == kTagF) return 0;
+    int64_t cnt = 0;
+    int k2 = k + 1;
+    bool have = false;
+    Canon ck;
+    for (; k2 < s && (buf[k2] >> 26) == (key >> 26); ++k2) {
+        if (!have) {
+            ck = record_content(key, ucanon);
+            have = true;
+        }
+        if (canon_eq(ck, record_content(buf[k2], ucanon))) ++cnt;
+        else bad = true;
+    }
+    if (T >= 1 && rec_runstart(key)) {
+        int g = k2;
+        while (g < s && (buf[g] >> 32) == (key >> 32)) ++g;
+        const uint64_t last = buf[g - 1];
+        if (rec_p(last) == kTagF) {
+            if (!have) ck = record_content(key, ucanon);
+            if (canon_eq(ck, record_content(last, ucanon))) ++cnt;
+            else bad = true;
+        }
+    }
+    return cnt;
+}
+
 template <bool WRITE>
 __global__ void __launch_bounds__(kThreads)
 k_join(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __restrict__ recs,
        const Canon* __restrict__ ucanon, int cap, int T, Weigh weigh, int64_t* __restrict__ pedges,
        const int64_t* __restrict__ eoff, int2* __restrict__ edges, unsigned long long* __restrict__ ecur,
-       int64_t ecap, int32_t* __restrict__ fb_list, int* __restrict__ fb_count) {
+       int64_t seg_cap, int32_t* __restrict__ fb_list, int* __restrict__ fb_count) {
     __shared__ uint64_t sbuf[kWarps][kWarpCap];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint64_t* buf = sbuf[warp];
@@ -376,13 +413,10 @@ k_join(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __restrict__
         else if (s <= 64) load_sort_store<2>(recs + base, s, buf, lane);
         else load_sort_store<4>(recs + base, s, buf, lane);
         __syncwarp();
-        // equal 32-bit hashes must be equal contents; otherwise the exact fallback
+        // count the edges, confirming each one's contents (exact)
         bool bad = false;
-        for (int k = lane + 1; k < s; k += 32) {
-            if ((buf[k] >> 32) == (buf[k - 1] >> 32) &&
-                !canon_eq(record_content(buf[k], ucanon), record_content(buf[k - 1], ucanon)))
-                bad = true;
-        }
+        int64_t mine = 0;
+        for (int k = lane; k < s; k += 32) mine += record_edges_checked(buf, k, s, T, ucanon, bad);
         if (__any_sync(kFull, bad)) {
             if (!WRITE && lane == 0) {
                 fb_list[atomicAdd(fb_count, 1)] = (int32_t)pid;
@@ -391,28 +425,25 @@ k_join(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __restrict__
             __syncwarp();
             continue;
         }
+        int64_t excl;
+        const int64_t total = warp_scan(mine, excl, lane);
         if (!WRITE) {
-            // weigh, count, and write the edges into the capped buffer when they fit
-            int64_t mine = 0;
-            for (int k = lane; k < s; k += 32) mine += record_edges(buf, k, s, T, weigh);
-            int64_t excl;
-            const int64_t total = warp_scan(mine, excl, lane);
+            // weigh every edge and write it into the capped buffer when it fits
             if (lane == 0) pedges[pid] = total;
             if (total) {
+                const int seg = (int)(pid & (kEdgeSegs - 1));
                 unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(ecur, (unsigned long long)total);
+                if (lane == 0) base = atomicAdd(&ecur[seg], (unsigned long long)total);
                 base = __shfl_sync(kFull, base, 0);
-                if ((int64_t)(base + total) <= ecap) {
-                    int64_t pos = (int64_t)base + excl;
-                    for (int k = lane; k < s; k += 32)
-                        record_edges(buf, k, s, T, [&](int32_t a, int32_t b) { edges[pos++] = make_int2(a, b); });
-                }
+                const bool fits = (int64_t)(base + total) <= seg_cap;
+                int64_t pos = seg * seg_cap + (int64_t)base + excl;
+                for (int k = lane; k < s; k += 32)
+                    record_edges(buf, k, s, T, [&](int32_t a, int32_t b) {
+                        weigh(a, b);
+                        if (fits) edges[pos++] = make_int2(a, b);
+                    });
             }
         } else {
-            int64_t mine = 0;
-            for (int k = lane; k < s; k += 32) mine += record_edges(buf, k, s, T, [](int32_t, int32_t) {});
-            int64_t excl;
-            warp_scan(mine, excl, lane);
             int64_t pos = eoff[pid] + excl;
             for (int k = lane; k < s; k += 32)
                 record_edges(buf, k, s, T, [&](int32_t a, int32_t b) { edges[pos++] = make_int2(a, b); });
@@ -428,7 +459,7 @@ __global__ void __launch_bounds__(kThreads)
 k_join_fallback(const int32_t* __restrict__ fb_list, const int* __restrict__ fb_count, const int64_t* __restrict__ poff,
                 const uint64_t* __restrict__ recs, const Canon* __restrict__ ucanon, int T, Weigh weigh,
                 int64_t* __restrict__ pedges, const int64_t* __restrict__ eoff, int2* __restrict__ edges,
-                unsigned long long* __restrict__ ecur, int64_t ecap) {
+                unsigned long long* __restrict__ ecur, int64_t seg_cap) {
     __shared__ int64_t wtot[kWarps];
     const int nfb = *fb_count;
     for (int f = blockIdx.x; f < nfb; f += gridDim.x) {
@@ -464,11 +495,12 @@ k_join_fallback(const int32_t* __restrict__ fb_list, const int* __restrict__ fb_
             const int64_t total = block_scan(mine, excl, wtot);
             if (threadIdx.x == 0) pedges[pid] = total;
             if (total) {
+                const int seg = (int)(pid & (kEdgeSegs - 1));
                 __shared__ unsigned long long base;
-                if (threadIdx.x == 0) base = atomicAdd(ecur, (unsigned long long)total);
+                if (threadIdx.x == 0) base = atomicAdd(&ecur[seg], (unsigned long long)total);
                 __syncthreads();
-                if ((int64_t)(base + total) <= ecap) {
-                    int64_t pos = (int64_t)base + excl;
+                if ((int64_t)(base + total) <= seg_cap) {
+                    int64_t pos = seg * seg_cap + (int64_t)base + excl;
                     scan_pairs([&](int32_t a, int32_t b) { edges[pos++] = make_int2(a, b); });
                 }
             }
@@ -509,18 +541,21 @@ __global__ void k_closed_self(const int32_t* __restrict__ uid, const int32_t* __
 // Append M_b to the list of a for both directions of every edge. Lanes copy
 // short member lists themselves; long ones are copied by the whole warp.
 __global__ void __launch_bounds__(kThreads)
-k_closed_edges(const int2* __restrict__ edges, int64_t E, const int32_t* __restrict__ umult,
+k_closed_edges(const int2* __restrict__ edges, int64_t seg_cap, const unsigned long long* __restrict__ seg_count,
+               const int32_t* __restrict__ umult,
                const int64_t* __restrict__ mem_off, const int32_t* __restrict__ members,
                const int64_t* __restrict__ uoff, int32_t* __restrict__ ucur, int32_t* __restrict__ S,
                int* __restrict__ err) {
     constexpr int kShort = 4;
     const int lane = threadIdx.x & 31;
+    // grid.y = edge segment; t = direction-expanded index inside the segment
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t E = (int64_t)seg_count[blockIdx.y];
     const bool have = t < 2 * E;
     int32_t a = 0, b = 0, mb = 0;
     int64_t o = 0;
     if (have) {
-        const int2 uv = edges[t >> 1];
+        const int2 uv = edges[blockIdx.y * seg_cap + (t >> 1)];
         a = (t & 1) ? uv.y : uv.x;  // list owner
         b = (t & 1) ? uv.x : uv.y;  // neighbour whose members are appended
         mb = umult[b];
@@ -631,12 +666,14 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     // edge cursor
     DevBuf errb, ecur_b;
     TCR_CHECK(errb.alloc(sizeof(int) * 4, s));
-    TCR_CHECK(ecur_b.alloc(sizeof(unsigned long long), s));
+    TCR_CHECK(ecur_b.alloc(sizeof(unsigned long long) * (kEdgeSegs + 1), s));
     TCR_CUDA(cudaMemsetAsync(errb.as<void>(), 0, sizeof(int) * 4, s));
-    TCR_CUDA(cudaMemsetAsync(ecur_b.as<void>(), 0, sizeof(unsigned long long), s));
+    TCR_CUDA(cudaMemsetAsync(ecur_b.as<void>(), 0, sizeof(unsigned long long) * (kEdgeSegs + 1), s));
     int* d_err = errb.as<int>();
-    unsigned long long* d_ecur = ecur_b.as<unsigned long long>();
-    const int64_t ecap = 2 * R_max + 64;  // edges of the one-pass join
+    unsigned long long* d_ecur = ecur_b.as<unsigned long long>();  // [kEdgeSegs]: single-segment count
+    // edges of the one-pass join: 2 x (records bound), split in kEdgeSegs segments
+    const int64_t seg_cap = ceil_div(2 * R_max + 64, kEdgeSegs);
+    const int64_t ecap = seg_cap * kEdgeSegs;
 
     // ---- 1. dedup
     int64_t S = 1024;
@@ -716,12 +753,12 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         jgrid = (int)std::min<int64_t>(ceil_div(P, 32 * kWarps), (int64_t)num_sms * 16);
         k_join<false><<<jgrid, kThreads, 0, s>>>(poff.as<int64_t>(), P, recs.as<uint64_t>(), ucanon.as<Canon>(), cap,
                                                  T, weigh, pedges.as<int64_t>(), nullptr, edges.as<int2>(), d_ecur,
-                                                 ecap, fb_list.as<int32_t>(), d_err + 2);
+                                                 seg_cap, fb_list.as<int32_t>(), d_err + 2);
         TCR_LAUNCH_CHECK();
         k_join_fallback<false><<<num_sms * 2, kThreads, 0, s>>>(fb_list.as<int32_t>(), d_err + 2, poff.as<int64_t>(),
                                                                 recs.as<uint64_t>(), ucanon.as<Canon>(), T, weigh,
                                                                 pedges.as<int64_t>(), nullptr, edges.as<int2>(),
-                                                                d_ecur, ecap);
+                                                                d_ecur, seg_cap);
         TCR_LAUNCH_CHECK();
         t3 = tm.mark();
     }
@@ -736,12 +773,20 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     k_node_degree<<<grid_for(n), kThreads, 0, s>>>(uid.as<int32_t>(), n, wsum.as<int32_t>(), deg.as<int32_t>());
     TCR_LAUNCH_CHECK();
     TCR_CHECK(scan_exclusive_i32_to_i64(deg.as<int32_t>(), off64.as<int64_t>(), n, s));
-    int64_t sizes[3] = {0, 0, 0};  // sum of D_u, nnz, unique edges
+    int64_t sizes[2] = {0, 0};  // sum of D_u, nnz
+    unsigned long long segs[kEdgeSegs];
     TCR_CUDA(cudaMemcpyAsync(&sizes[0], uoff.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TCR_CUDA(cudaMemcpyAsync(&sizes[1], off64.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    TCR_CUDA(cudaMemcpyAsync(&sizes[2], d_ecur, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaMemcpyAsync(segs, d_ecur, sizeof(segs), cudaMemcpyDeviceToHost, s));
     TCR_CUDA(cudaStreamSynchronize(s));
-    const int64_t SD = sizes[0], nnz = sizes[1], E = sizes[2];
+    const int64_t SD = sizes[0], nnz = sizes[1];
+    int64_t E = 0, seg_max = 0;
+    bool overflow = false;
+    for (int g = 0; g < kEdgeSegs; ++g) {
+        E += (int64_t)segs[g];
+        seg_max = std::max<int64_t>(seg_max, (int64_t)segs[g]);
+        overflow = overflow || (int64_t)segs[g] > seg_cap;
+    }
     int n_two_pass = 0;
     DevBuf Sbuf;
     TCR_CHECK(Sbuf.alloc(sizeof(int32_t) * SD, s));
@@ -750,7 +795,9 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     TCR_LAUNCH_CHECK();
     // ---- 3b. edges that did not fit: second join pass at scanned positions;
     // then append neighbour member lists
-    if (join && E > ecap) {
+    int64_t fill_segs = kEdgeSegs, fill_cap = seg_cap;
+    const unsigned long long* fill_counts = d_ecur;
+    if (join && overflow) {
         edges.reset();
         TCR_CHECK(edges.alloc(sizeof(int2) * E, s));
         TCR_CHECK(scan_exclusive_i64(pedges.as<int64_t>(), eoff.as<int64_t>(), P, s));
@@ -764,10 +811,18 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
                                                                nullptr, 0);
         TCR_LAUNCH_CHECK();
         n_two_pass = 1;
+        // the edges are now contiguous: one segment of E
+        const unsigned long long e64 = (unsigned long long)E;
+        TCR_CUDA(cudaMemcpyAsync(d_ecur + kEdgeSegs, &e64, sizeof(e64), cudaMemcpyHostToDevice, s));
+        fill_segs = 1;
+        fill_cap = E;
+        fill_counts = d_ecur + kEdgeSegs;
+        seg_max = E;
     }
     if (join && E > 0) {
         recs.reset();
-        k_closed_edges<<<grid_for(2 * E), kThreads, 0, s>>>(edges.as<int2>(), E, umult.as<int32_t>(),
+        const dim3 fgrid(grid_for(2 * seg_max), (unsigned)fill_segs);
+        k_closed_edges<<<fgrid, kThreads, 0, s>>>(edges.as<int2>(), fill_cap, fill_counts, umult.as<int32_t>(),
                                                             mem_off.as<int64_t>(), members.as<int32_t>(),
                                                             uoff.as<int64_t>(), ucur.as<int32_t>(),
                                                             Sbuf.as<int32_t>(), d_err + 1);
