@@ -18,7 +18,8 @@
 // sets bit 4 of each non-zero field: t = (((x | HI) - LOW) | x) & HI. Shifting
 // word w's result right by (4 - w) puts position W*f + w at bit 5*f + w, so the
 // OR over the W words is a 32-bit mask with one bit per position, in position
-// order (W <= 5, strings up to 30). Then
+// order (W <= 5, strings up to 30; for W <= 3 the shift is a left shift done
+// as a multiply-add, see posmask_fma). Then
 //   equal length: adjacent <=> (m & (m - 1)) == 0;
 //   L vs L+1:     m1 = mask(a, b), m2 = mask(a, b >> one position);
 //                 adjacent <=> (m2 & (m1 | -m1)) == 0  (no m2 bit at or above
@@ -91,9 +92,38 @@ __device__ __forceinline__ uint32_t field_mismatch(uint32_t x) {
     return (((x | kHI) - kLOW) | x) & kHI;
 }
 
+// x * m + c on the integer multiply-add unit (the FMA pipe), leaving the
+// ALU pipe to the logic operations.
+__device__ __forceinline__ uint32_t imad(uint32_t x, uint32_t m, uint32_t c) {
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(m), "r"(c));
+    return r;
+}
+
+// Up to three words (strings of at most 18): the same mask with position
+// W*f + w at bit 5*f + 4 + w (still increasing with the position), built with
+// three logic operations and two multiply-adds per word. The multipliers carry
+// an extra 2^31 term so they are not powers of two; it only reaches bit 31,
+// which is masked off (y) or never set (t has no bit 0).
+template <int W>
+__device__ __forceinline__ uint32_t posmask_fma(const uint32_t (&a)[W], const uint32_t (&b)[W]) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const uint32_t x = a[w] ^ b[w];
+        const uint32_t z = x | kHI;
+        const uint32_t y = imad(z, 0x80000001u, 0u - kLOW);  // z - LOW
+        const uint32_t t = (y | x) & kHI;
+        m = imad(t, (1u << w) | 0x80000000u, m);  // m + (t << w)
+    }
+    return m;
+}
+
 template <int W>
 __device__ __forceinline__ Mask<W> posmask(const uint32_t (&a)[W], const uint32_t (&b)[W]) {
-    if constexpr (W <= 5) {
+    if constexpr (W <= 3) {
+        return posmask_fma<W>(a, b);
+    } else if constexpr (W <= 5) {
         uint32_t m = 0;
 #pragma unroll
         for (int w = 0; w < W; ++w) m |= field_mismatch(a[w] ^ b[w]) >> (4 - w);
@@ -113,7 +143,12 @@ __device__ __forceinline__ Mask<W> posmask(const uint32_t (&a)[W], const uint32_
 template <int W>
 __device__ __forceinline__ bool same_len_adjacent(const uint32_t (&a)[W], const uint32_t (&b)[W], int T) {
     const Mask<W> m = posmask<W>(a, b);
-    return T == 0 ? (m == 0) : ((m & (m - 1)) == 0);
+    if constexpr (W <= 3) {
+        // m - 1 as a multiply-add (bit 0 of m is never set, so the 2^31 term cancels out of the test)
+        return T == 0 ? (m == 0) : ((m & imad(m, 0x80000001u, 0xffffffffu)) == 0);
+    } else {
+        return T == 0 ? (m == 0) : ((m & (m - 1)) == 0);
+    }
 }
 
 // a shorter (length L), b longer (L + 1), bs = b shifted down by one position.
@@ -122,7 +157,11 @@ __device__ __forceinline__ bool indel_adjacent(const uint32_t (&a)[W], const uin
                                                const uint32_t (&bs)[W]) {
     const Mask<W> m1 = posmask<W>(a, b);
     const Mask<W> m2 = posmask<W>(a, bs);
-    return (m2 & (m1 | (Mask<W>)(Mask<W>(0) - m1))) == 0;
+    if constexpr (W <= 3) {
+        return (m2 & (m1 | imad(m1, 0xffffffffu, 0u))) == 0;  // -m1 on the multiply-add unit
+    } else {
+        return (m2 & (m1 | (Mask<W>)(Mask<W>(0) - m1))) == 0;
+    }
 }
 
 template <int W>
