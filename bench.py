@@ -217,6 +217,25 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# cross-rank aggregation (weak scaling: every rank builds its own repertoire)
+
+def aggregate_ranks(ms_local, pairs_per_build, edges_per_build, world, dist_mod=None, device="cpu"):
+    """Max step time over ranks and whole-job throughputs.
+
+    value = world x pairs per build / max step time (all ranks' units over the
+    slowest rank's time). With dist_mod (torch.distributed, any backend) the max
+    is an all-reduce; without it the local time is used."""
+    ms = float(ms_local)
+    if dist_mod is not None and world > 1:
+        import torch
+
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * pairs_per_build / (ms / 1e3), world * edges_per_build / (ms / 1e3)
+
+
+# ---------------------------------------------------------------------------
 # ours
 
 def tile_ops_per_pair(lengths):
@@ -293,17 +312,11 @@ def run_ours(args):
     wall = time.perf_counter() - t0
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    ms = statistics.mean(step_ms)
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     st0 = stats[-1]
     n = args.n
     pairs_per_build = n * (n - 1) / 2
     edges = st0["nnz"] / 2
-    value = world * pairs_per_build / (ms / 1e3)
-    edges_per_s = world * edges / (ms / 1e3)
+    ms, value, edges_per_s = aggregate_ranks(statistics.mean(step_ms), pairs_per_build, edges, world, dist, dev)
     launches = int(sum(s["kernel_launches"] for s in stats))
 
     is_tile = st0["method"] == 1
