@@ -412,7 +412,7 @@ def run_ours(args):
         resident.free()
         line["query"] = {"batches": len(lat), "batch_size": "log-uniform 1..50000", "p50_ms": float(np.percentile(lat, 50)),
                          "p99_ms": float(np.percentile(lat, 99)), "queries_per_s": sum(qn) / (sum(lat) / 1e3),
-                         "method": "tile kernel against buckets L-1, L, L+1"}
+                         "method": "deletion index of the resident build (probe of the query strings own records)"}
         # --- end to end: pinned host inputs in, CSR back in pinned host memory
         hc = torch.from_numpy(rep.chars).pin_memory()
         ho = torch.from_numpy(rep.offsets).pin_memory()

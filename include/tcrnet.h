@@ -164,6 +164,14 @@ tcrnet_status tcrnet_csr_device(tcrnet_handle h, const void **offsets, const int
 tcrnet_status tcrnet_query_flat(tcrnet_handle h, const uint8_t *chars, const int64_t *offsets,
                                 int64_t m, int32_t mem, tcrnet_handle *out);
 
+/* tcrnet_query_flat with options: opt->stream orders the call (NULL options or
+ * stream: the build's stream); opt->method selects the search: AUTO (the
+ * deletion index when the build kept one, i.e. a deletion-method build with
+ * l_max >= 1, else the tile kernel), TILE, or DELETION (ENOTSUP without an
+ * index). Both searches return identical lists. */
+tcrnet_status tcrnet_query_ex(tcrnet_handle h, const uint8_t *chars, const int64_t *offsets, int64_t m,
+                              int32_t mem, const tcrnet_options *opt, tcrnet_handle *out);
+
 /* Same as tcrnet_query_flat for NUL-terminated host strings. */
 tcrnet_status tcrnet_query(tcrnet_handle h, const char *const *queries, int64_t m,
                            tcrnet_handle *out);

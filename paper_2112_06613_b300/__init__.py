@@ -96,7 +96,7 @@ SYMBOLS = [
     "tcrnet_options_init", "tcrnet_build", "tcrnet_build_flat", "tcrnet_info", "tcrnet_copy_csr",
     "tcrnet_csr_device", "tcrnet_query_flat", "tcrnet_query", "tcrnet_stats_get", "tcrnet_free",
     "tcrnet_strerror", "tcrnet_last_error_index", "tcrnet_version", "tcrnet_last_cuda_error",
-    "tcrnet_degree_noalloc",
+    "tcrnet_degree_noalloc", "tcrnet_query_ex",
 ]
 
 
@@ -129,6 +129,8 @@ def load_library(path: str = LIB_PATH):
         lib.tcrnet_csr_device.restype = ctypes.c_int
         lib.tcrnet_query_flat.argtypes = [H, vp, vp, i64, i32, HP]
         lib.tcrnet_query_flat.restype = ctypes.c_int
+        lib.tcrnet_query_ex.argtypes = [H, vp, vp, i64, i32, optp, HP]
+        lib.tcrnet_query_ex.restype = ctypes.c_int
         lib.tcrnet_query.argtypes = [H, ctypes.POINTER(ctypes.c_char_p), i64, HP]
         lib.tcrnet_query.restype = ctypes.c_int
         lib.tcrnet_stats_get.argtypes = [H, ctypes.POINTER(tcrnet_stats)]
@@ -252,8 +254,10 @@ class Graph:
     def query(self, queries):
         return tcrnet_query(self, queries)
 
-    def query_flat(self, chars, offsets):
-        return tcrnet_query_flat(self, chars, offsets)
+    def query_flat(self, chars, offsets, method="auto", stream=None):
+        if method == "auto" and stream is None:
+            return tcrnet_query_flat(self, chars, offsets)
+        return tcrnet_query_ex(self, chars, offsets, method=method, stream=stream)
 
 
 def _ptr(a):
@@ -322,6 +326,17 @@ def tcrnet_query_flat(graph: Graph, chars, offsets) -> Graph:
     st = lib.tcrnet_query_flat(graph.handle, cp, op, m, mem, ctypes.byref(h))
     del keep
     _check(st, "tcrnet_query_flat")
+    return Graph(h.value)
+
+
+def tcrnet_query_ex(graph: Graph, chars, offsets, method="auto", stream=None) -> Graph:
+    lib = load_library()
+    cp, op, m, mem, keep = _flat_args(chars, offsets)
+    opt = make_options(method, None, stream)
+    h = ctypes.c_void_p()
+    st = lib.tcrnet_query_ex(graph.handle, cp, op, m, mem, ctypes.byref(opt), ctypes.byref(h))
+    del keep
+    _check(st, "tcrnet_query_ex")
     return Graph(h.value)
 
 

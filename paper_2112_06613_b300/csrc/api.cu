@@ -30,6 +30,7 @@ struct tcrnet_graph {
     tcr::Canon* d_bcanon = nullptr;
     int32_t* d_bperm = nullptr;
     int64_t bucket_off[tcr::kMaxLen + 2] = {0};
+    tcr::DeletionIndex ix;  // query index of a deletion build (l_max >= 1)
     tcrnet_stats stats;
 };
 
@@ -184,9 +185,11 @@ int sm_count(int dev) {
 }
 
 void free_handle_memory(tcrnet_graph* h) {
-    void* ptrs[] = {h->d_offsets, h->d_cols, h->d_degree, h->d_bcanon, h->d_bperm};
+    void* ptrs[] = {h->d_offsets, h->d_cols, h->d_degree, h->d_bcanon, h->d_bperm, h->ix.ucanon, h->ix.umult,
+                    h->ix.mem_off, h->ix.members, h->ix.recs, h->ix.poff};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    h->ix = DeletionIndex();
     h->d_offsets = nullptr;
     h->d_cols = nullptr;
     h->d_degree = nullptr;
@@ -379,7 +382,7 @@ tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n
         if (st != TCRNET_OK) return fail(st);
     } else {
         DeletionResult dr;
-        st = deletion_build(pk, T, dr, s, sms, opt.profile != 0, opt.partition_cap);
+        st = deletion_build(pk, T, dr, s, sms, opt.profile != 0, opt.partition_cap, /*keep_index=*/true);
         if (st != TCRNET_OK) return fail(st);
         h->stats.n_unique = dr.n_unique;
         h->stats.n_records = dr.n_records;
@@ -392,6 +395,8 @@ tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n
         h->stats.ms_write = dr.ms_fill;
         h->stats.ms_sort = dr.ms_sort;
         for (int k = 0; k < 8; ++k) h->stats.ms_phase[k] = dr.ms_phase[k];
+        h->ix = dr.index;  // owned by the handle from here on
+        dr.index = DeletionIndex();
         st = export_csr(h, dr.off64, dr.cols, dr.degree, n, dr.nnz, opt.force_offsets64 != 0, s);
         if (st != TCRNET_OK) return fail(st);
     }
@@ -470,16 +475,20 @@ tcrnet_status tcrnet_csr_device(tcrnet_handle h, const void** offsets, const int
     return TCRNET_OK;
 }
 
-tcrnet_status tcrnet_query_flat(tcrnet_handle h, const uint8_t* chars, const int64_t* offsets, int64_t m,
-                                int32_t mem, tcrnet_handle* out) {
+tcrnet_status tcrnet_query_ex(tcrnet_handle h, const uint8_t* chars, const int64_t* offsets, int64_t m, int32_t mem,
+                              const tcrnet_options* opt, tcrnet_handle* out) {
     if (!out) return TCRNET_EINVAL;
     *out = nullptr;
     t_last_bad = -1;
     if (!h || m < 0 || m > 0x7fffffffLL) return TCRNET_EINVAL;
     if (h->query_result) return TCRNET_ESTATE;
+    int method = opt ? opt->method : TCRNET_METHOD_AUTO;
+    if (method < TCRNET_METHOD_AUTO || method > TCRNET_METHOD_DELETION) return TCRNET_EINVAL;
+    if (method == TCRNET_METHOD_AUTO) method = h->ix.valid() ? TCRNET_METHOD_DELETION : TCRNET_METHOD_TILE;
+    if (method == TCRNET_METHOD_DELETION && !h->ix.valid()) return TCRNET_ENOTSUP;
     DeviceGuard dg;
     TCR_CHECK(dg.set(h->device));
-    cudaStream_t s = h->stream;
+    cudaStream_t s = (opt && opt->stream) ? (cudaStream_t)opt->stream : h->stream;
     const int sms = sm_count(h->device);
     tcrnet_graph* r = new (std::nothrow) tcrnet_graph();
     if (!r) return TCRNET_ENOMEM;
@@ -490,7 +499,7 @@ tcrnet_status tcrnet_query_flat(tcrnet_handle h, const uint8_t* chars, const int
     r->threshold = h->threshold;
     r->stats.threshold = h->threshold;
     r->stats.n = m;
-    r->stats.method = TCRNET_METHOD_TILE;
+    r->stats.method = method;
     auto fail = [&](tcrnet_status st) {
         cudaStreamSynchronize(s);
         free_handle_memory(r);
@@ -518,16 +527,30 @@ tcrnet_status tcrnet_query_flat(tcrnet_handle h, const uint8_t* chars, const int
             t_last_bad = bad;
             return fail(st);
         }
-        TileSide qs{pk.canon.as<Canon>(), pk.perm.as<int32_t>(), pk.bucket_off};
-        TileSide rs{h->d_bcanon, h->d_bperm, h->bucket_off};
-        st = tile_method(r, qs, rs, m, false, h->threshold, false, ph, s, sms);
-        if (st != TCRNET_OK) return fail(st);
+        if (method == TCRNET_METHOD_DELETION) {
+            DevBuf off64, cols, cnt;
+            int64_t nnz = 0;
+            st = deletion_query(h->ix, pk, h->threshold, off64, cols, cnt, &nnz, s, sms);
+            if (st != TCRNET_OK) return fail(st);
+            st = export_csr(r, off64, cols, cnt, m, nnz, false, s);
+            if (st != TCRNET_OK) return fail(st);
+        } else {
+            TileSide qs{pk.canon.as<Canon>(), pk.perm.as<int32_t>(), pk.bucket_off};
+            TileSide rs{h->d_bcanon, h->d_bperm, h->bucket_off};
+            st = tile_method(r, qs, rs, m, false, h->threshold, false, ph, s, sms);
+            if (st != TCRNET_OK) return fail(st);
+        }
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(TCRNET_EDEVICE);
     r->stats.nnz = r->nnz;
     r->stats.kernel_launches = launches_so_far() - launches0;
     *out = r;
     return TCRNET_OK;
+}
+
+tcrnet_status tcrnet_query_flat(tcrnet_handle h, const uint8_t* chars, const int64_t* offsets, int64_t m,
+                                int32_t mem, tcrnet_handle* out) {
+    return tcrnet_query_ex(h, chars, offsets, m, mem, nullptr, out);
 }
 
 tcrnet_status tcrnet_query(tcrnet_handle h, const char* const* queries, int64_t m, tcrnet_handle* out) {

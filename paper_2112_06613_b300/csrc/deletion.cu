@@ -649,7 +649,7 @@ private:
 }  // namespace
 
 tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaStream_t s, int num_sms, bool profile,
-                             int partition_cap) {
+                             int partition_cap, bool keep_index) {
     const int64_t n = pk.n;
     if (n > kDeletionMaxN) return TCRNET_ENOTSUP;
     const int cap = (partition_cap > 0 && partition_cap < kWarpCap) ? partition_cap : kWarpCap;
@@ -695,13 +695,17 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     TCR_CHECK(scan_exclusive_i32_to_i64(flag.as<int32_t>(), ubase.as<int64_t>(), S, s));
     const int64_t* d_U = ubase.as<int64_t>() + S;  // number of distinct strings, on the device
     DevBuf ucanon, ulen, umult, uid, mem_off, mcur, members, mpos;
-    TCR_CHECK(ucanon.alloc(sizeof(Canon) * n, s));
+    if (keep_index) TCR_CHECK(ucanon.alloc_owned(sizeof(Canon) * n, s));
+    else TCR_CHECK(ucanon.alloc(sizeof(Canon) * n, s));
     TCR_CHECK(ulen.alloc(n, s));
-    TCR_CHECK(umult.alloc(sizeof(int32_t) * n, s));
+    if (keep_index) TCR_CHECK(umult.alloc_owned(sizeof(int32_t) * n, s));
+    else TCR_CHECK(umult.alloc(sizeof(int32_t) * n, s));
     TCR_CHECK(uid.alloc(sizeof(int32_t) * n, s));
-    TCR_CHECK(mem_off.alloc(sizeof(int64_t) * (n + 1), s));
+    if (keep_index) TCR_CHECK(mem_off.alloc_owned(sizeof(int64_t) * (n + 1), s));
+    else TCR_CHECK(mem_off.alloc(sizeof(int64_t) * (n + 1), s));
     TCR_CHECK(mcur.alloc(sizeof(int32_t) * n, s));
-    TCR_CHECK(members.alloc(sizeof(int32_t) * n, s));
+    if (keep_index) TCR_CHECK(members.alloc_owned(sizeof(int32_t) * n, s));
+    else TCR_CHECK(members.alloc(sizeof(int32_t) * n, s));
     TCR_CHECK(mpos.alloc(sizeof(int32_t) * n, s));
     TCR_CUDA(cudaMemsetAsync(umult.as<void>(), 0, sizeof(int32_t) * n, s));  // ids >= U stay 0
     k_unique_compact<<<grid_for(S), kThreads, 0, s>>>(scount.as<int32_t>(), table.as<int32_t>(), ubase.as<int64_t>(),
@@ -731,8 +735,10 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     if (join) {
         P = std::max<int64_t>(1, std::min<int64_t>(R_max / kTargetPart + 1, 1LL << 30));
         TCR_CHECK(pcnt.alloc(sizeof(int32_t) * P, s));
-        TCR_CHECK(poff.alloc(sizeof(int64_t) * (P + 1), s));
-        TCR_CHECK(recs.alloc(sizeof(uint64_t) * R_max, s));
+        if (keep_index) TCR_CHECK(poff.alloc_owned(sizeof(int64_t) * (P + 1), s));
+        else TCR_CHECK(poff.alloc(sizeof(int64_t) * (P + 1), s));
+        if (keep_index) TCR_CHECK(recs.alloc_owned(sizeof(uint64_t) * R_max, s));
+        else TCR_CHECK(recs.alloc(sizeof(uint64_t) * R_max, s));
         TCR_CHECK(fb_list.alloc(sizeof(int32_t) * P, s));
         TCR_CHECK(pedges.alloc(sizeof(int64_t) * P, s));
         TCR_CHECK(eoff.alloc(sizeof(int64_t) * (P + 1), s));
@@ -820,7 +826,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         seg_max = E;
     }
     if (join && E > 0) {
-        recs.reset();
+        if (!keep_index) recs.reset();
         const dim3 fgrid(grid_for(2 * seg_max), (unsigned)fill_segs);
         k_closed_edges<<<fgrid, kThreads, 0, s>>>(edges.as<int2>(), fill_cap, fill_counts, umult.as<int32_t>(),
                                                             mem_off.as<int64_t>(), members.as<int32_t>(),
@@ -829,7 +835,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         TCR_LAUNCH_CHECK();
     }
     const int t4 = tm.mark();
-    recs.reset();
+    if (!keep_index) recs.reset();
     edges.reset();
     TCR_CHECK(sort_rows(uoff.as<int64_t>(), Sbuf.as<int32_t>(), n, s, num_sms));
     const int t5 = tm.mark();
@@ -859,6 +865,17 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     out.n_fallback = h_err[2];
     out.closed_total = SD;
     out.two_pass_join = n_two_pass;
+    if (keep_index && join) {
+        out.index.ucanon = static_cast<Canon*>(ucanon.release());
+        out.index.umult = static_cast<int32_t*>(umult.release());
+        out.index.mem_off = static_cast<int64_t*>(mem_off.release());
+        out.index.members = static_cast<int32_t*>(members.release());
+        out.index.recs = static_cast<uint64_t*>(recs.release());
+        out.index.poff = static_cast<int64_t*>(poff.release());
+        out.index.U = h_U;
+        out.index.P = P;
+        out.index.n = n;
+    }
     out.ms_phase[0] = tm.ms(t0, t1);  // dedup
     out.ms_phase[1] = tm.ms(t1, t2);  // records
     out.ms_phase[2] = tm.ms(t2, t3);  // join pass 1 (weighted degrees)
@@ -871,6 +888,114 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     out.ms_scan = 0.0;
     out.ms_fill = tm.ms(t3, t4);
     out.ms_sort = tm.ms(t4, t6);
+    return TCRNET_OK;
+}
+
+// ---- queries against the resident index -----------------------------------
+
+namespace {
+
+struct IndexView {
+    const Canon* ucanon;
+    const int32_t* umult;
+    const int64_t* mem_off;
+    const int32_t* members;
+    const uint64_t* recs;
+    const int64_t* poff;
+    uint32_t P;
+};
+
+// Neighbours of query string q among the distinct resident strings, found
+// through q's own records (full string and every deletion) in the resident
+// partitions; each match is confirmed by content and each neighbour is found
+// exactly once (see the file comment; an identical resident string matches
+// full-to-full only, its deletion matches are skipped). Calls emit(u).
+template <typename Emit>
+__device__ __forceinline__ int64_t query_record(const IndexView& ix, const Canon& qc, int Lq, int p, int T,
+                                                Emit emit) {
+    const bool full = p < 0;
+    const Canon cq = full ? qc : delete_at(qc, p);
+    const bool q_rs = !full && run_start(qc, p);
+    if (!full && T < 1) return 0;
+    const uint64_t h = hash_canon(cq);
+    const uint32_t h32 = (uint32_t)h;
+    const uint32_t pid = part_of(h, ix.P);
+    const int64_t b0 = ix.poff[pid], b1 = ix.poff[pid + 1];
+    int64_t cnt = 0;
+    for (int64_t k = b0; k < b1; ++k) {
+        const uint64_t r = ix.recs[k];
+        if ((uint32_t)(r >> 32) != h32) continue;
+        const uint32_t rp = rec_p(r);
+        bool cand;
+        if (full) cand = (rp == kTagF) || (T >= 1 && rec_runstart(r));   // identical / q one shorter
+        else cand = (rp == kTagF) ? q_rs : (rp == (uint32_t)p);           // q one longer / one substitution
+        if (!cand) continue;
+        if (!canon_eq(cq, record_content(r, ix.ucanon))) continue;       // hash collision
+        const uint32_t u = rec_u(r);
+        if (!full && rp != kTagF && canon_eq(qc, load_canon(ix.ucanon + u))) continue;  // identical: counted once
+        emit(u);
+        ++cnt;
+    }
+    return cnt;
+}
+
+template <bool WRITE>
+__global__ void __launch_bounds__(kThreads)
+k_query(IndexView ix, const Canon* __restrict__ qcanon, const uint8_t* __restrict__ qlen, int64_t m, int T,
+        int64_t* __restrict__ qcount, const int64_t* __restrict__ qoff, int32_t* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < m; q += stride) {
+        const Canon qc = load_canon(qcanon + q);
+        const int Lq = qlen[q];
+        int64_t mine = 0;  // members this lane contributes
+        for (int p = lane - 1; p < Lq; p += 32)
+            query_record(ix, qc, Lq, p, T, [&](uint32_t u) { mine += ix.umult[u]; });
+        int64_t excl;
+        const int64_t total = warp_scan(mine, excl, lane);
+        if (!WRITE) {
+            if (lane == 0) qcount[q] = total;
+        } else {
+            int64_t pos = qoff[q] + excl;
+            for (int p = lane - 1; p < Lq; p += 32)
+                query_record(ix, qc, Lq, p, T, [&](uint32_t u) {
+                    const int32_t* mb = ix.members + ix.mem_off[u];
+                    const int32_t mu = ix.umult[u];
+                    for (int32_t y = 0; y < mu; ++y) out[pos++] = mb[y];
+                });
+        }
+    }
+}
+
+}  // namespace
+
+tcrnet_status deletion_query(const DeletionIndex& ix, const Packed& q, int T, DevBuf& off64, DevBuf& cols,
+                             DevBuf& count, int64_t* nnz_out, cudaStream_t s, int num_sms) {
+    const int64_t m = q.n;
+    *nnz_out = 0;
+    if (!ix.valid()) return TCRNET_ESTATE;
+    IndexView v{ix.ucanon, ix.umult, ix.mem_off, ix.members, ix.recs, ix.poff, (uint32_t)ix.P};
+    DevBuf qcnt;
+    TCR_CHECK(qcnt.alloc(sizeof(int64_t) * m, s));
+    TCR_CHECK(off64.alloc_owned(sizeof(int64_t) * (m + 1), s));
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(m, kWarps), (int64_t)num_sms * 32);
+    k_query<false><<<grid, kThreads, 0, s>>>(v, q.canon_in.as<Canon>(), q.lens.as<uint8_t>(), m, T,
+                                             qcnt.as<int64_t>(), nullptr, nullptr);
+    TCR_LAUNCH_CHECK();
+    TCR_CHECK(scan_exclusive_i64(qcnt.as<int64_t>(), off64.as<int64_t>(), m, s));
+    int64_t nnz = 0;
+    TCR_CUDA(cudaMemcpyAsync(&nnz, off64.as<int64_t>() + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaStreamSynchronize(s));
+    TCR_CHECK(cols.alloc_owned(sizeof(int32_t) * nnz, s));
+    TCR_CHECK(count.alloc_owned(sizeof(int32_t) * m, s));
+    if (nnz > 0) {
+        k_query<true><<<grid, kThreads, 0, s>>>(v, q.canon_in.as<Canon>(), q.lens.as<uint8_t>(), m, T, nullptr,
+                                                off64.as<int64_t>(), cols.as<int32_t>());
+        TCR_LAUNCH_CHECK();
+        TCR_CHECK(sort_rows(off64.as<int64_t>(), cols.as<int32_t>(), m, s, num_sms));
+    }
+    TCR_CHECK(degree_from_offsets(off64.as<int64_t>(), count.as<int32_t>(), m, s));
+    *nnz_out = nnz;
     return TCRNET_OK;
 }
 

@@ -11,6 +11,20 @@ constexpr int64_t kAutoDeletionMinN = 2048;
 // Largest input the deletion records can address (distinct-string ids use 25 bits).
 constexpr int64_t kDeletionMaxN = 1LL << 25;
 
+// Resident query index of a deletion build (device pointers; owned by the
+// handle, freed with cudaFree): distinct strings, their multiplicities and
+// member lists, and the hash-partitioned records.
+struct DeletionIndex {
+    Canon* ucanon = nullptr;
+    int32_t* umult = nullptr;
+    int64_t* mem_off = nullptr;
+    int32_t* members = nullptr;
+    uint64_t* recs = nullptr;
+    int64_t* poff = nullptr;
+    int64_t U = 0, P = 0, n = 0;
+    bool valid() const { return recs != nullptr; }
+};
+
 struct DeletionResult {
     DevBuf off64;   // int64[n + 1]
     DevBuf cols;    // int32[nnz]
@@ -25,11 +39,17 @@ struct DeletionResult {
     double ms_join = 0, ms_scan = 0, ms_fill = 0, ms_sort = 0;
     // dedup, records, join count, join write, closed fill, closed sort, expand, total
     double ms_phase[8] = {0};
+    DeletionIndex index;  // filled when the build keeps its index
 };
 
 // Test knob: partitions larger than `partition_cap` (<= the shared-memory
 // capacity; 0 = default) take the quadratic fallback.
 tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaStream_t s, int num_sms,
-                             bool profile, int partition_cap = 0);
+                             bool profile, int partition_cap = 0, bool keep_index = false);
+
+// Neighbour lists (l_max = T) of packed query strings against a resident
+// index: CSR with int64 offsets (m + 1), columns, per-query counts.
+tcrnet_status deletion_query(const DeletionIndex& ix, const Packed& q, int T, DevBuf& off64, DevBuf& cols,
+                             DevBuf& count, int64_t* nnz, cudaStream_t s, int num_sms);
 
 }  // namespace tcr

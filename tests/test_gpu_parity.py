@@ -290,3 +290,40 @@ def test_deletion_dense_unique_graph_takes_two_pass_join():
     # the generator workload fits in one pass
     _, _, _, st = gpu_csr(generate_config1(5000, seed=3), 1, "deletion")
     assert st["two_pass_join"] == 0
+
+
+@pytest.mark.parametrize("qmethod", ["auto", "tile", "deletion"])
+def test_index_queries_match_oracle(qmethod):
+    rep = generate_config1(20_000, seed=17)
+    strs = rep.strings()
+    rng = np.random.default_rng(8)
+    qs = [strs[i] for i in rng.choice(len(strs), 300, replace=False)]
+    qs += [q[:-1] for q in qs[:40]] + [q + "A" for q in qs[40:80]] + [q[:2] + q[3:] for q in qs[80:120]]
+    qs += [q[:5] + "Y" + q[6:] for q in qs[120:160]] + ["A", "W" * 48, "CASSLGQF", "CAAAF", "CAAF"]
+    q = from_strings(qs)
+    with tn.tcrnet_build_flat(rep.chars, rep.offsets, 1, method="deletion") as g:
+        with g.query_flat(q.chars, q.offsets, method=qmethod) as r:
+            qo, qc, _ = r.copy_csr()
+            st = r.stats()
+    assert st["method"] == (tn.METHOD_TILE if qmethod == "tile" else tn.METHOD_DELETION)
+    ro, rc = oracle.neighbors(rep.chars, rep.offsets, q.chars, q.offsets, max_dist=1)
+    assert_csr_equal(qo, qc, ro, rc, f"queries via {qmethod}")
+
+
+def test_index_queries_on_edge_strings():
+    strs = edge_strings()
+    rep = from_strings(strs)
+    qrep = from_strings(strs + ["AAAAA", "AC", "CA", "A" * 47, "Y" * 48])
+    with tn.tcrnet_build_flat(rep.chars, rep.offsets, 1, method="deletion") as g:
+        with g.query_flat(qrep.chars, qrep.offsets) as r:
+            qo, qc, _ = r.copy_csr()
+    ro, rc = oracle.neighbors(rep.chars, rep.offsets, qrep.chars, qrep.offsets, max_dist=1)
+    assert_csr_equal(qo, qc, ro, rc, "edge-string queries")
+
+
+def test_query_without_index_rejects_deletion_search():
+    rep = generate_config1(1000, seed=1)
+    with tn.tcrnet_build_flat(rep.chars, rep.offsets, 1, method="tile") as g:
+        with pytest.raises(tn.TcrnetError) as e:
+            g.query_flat(rep.chars, rep.offsets, method="deletion")
+        assert e.value.status == tn.ENOTSUP
