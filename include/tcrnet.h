@@ -176,10 +176,33 @@ tcrnet_status tcrnet_query_ex(tcrnet_handle h, const uint8_t *chars, const int64
 tcrnet_status tcrnet_query(tcrnet_handle h, const char *const *queries, int64_t m,
                            tcrnet_handle *out);
 
+/*
+ * Append m strings to a build handle as nodes n .. n+m-1 (flat layout as in
+ * tcrnet_build_flat). On success the handle's CSR, degree, resident repertoire
+ * and query index describe the grown repertoire, exactly as a fresh build of
+ * the concatenated input would (node ids of existing strings are unchanged);
+ * previously returned device pointers (tcrnet_csr_device) become invalid. The
+ * update is computed on the device from the handle's packed strings. On failure
+ * (bad string: its index within the new batch is reported) the handle keeps its
+ * previous network. Not for query-result handles (ESTATE). Callers must not use
+ * the handle from another thread during the call.
+ */
+tcrnet_status tcrnet_insert_flat(tcrnet_handle h, const uint8_t *chars, const int64_t *offsets, int64_t m,
+                                 int32_t mem);
+
+/* tcrnet_insert_flat with options (opt->stream orders the call; opt->profile). */
+tcrnet_status tcrnet_insert_ex(tcrnet_handle h, const uint8_t *chars, const int64_t *offsets, int64_t m,
+                               int32_t mem, const tcrnet_options *opt);
+
+/* tcrnet_insert_flat for NUL-terminated host strings. */
+tcrnet_status tcrnet_insert(tcrnet_handle h, const char *const *seqs, int64_t m);
+
 /* Counters and phase times of the call that produced the handle. */
 tcrnet_status tcrnet_stats_get(tcrnet_handle h, tcrnet_stats *out);
 
-/* Release a handle and all device memory it owns. NULL is a no-op. */
+/* Release a handle and all device memory it owns. NULL is a no-op. The memory
+ * is returned stream-ordered without waiting for the device; finish any work of
+ * your own that reads the handle's device pointers before freeing it. */
 void tcrnet_free(tcrnet_handle h);
 
 /* Static description of a status code. */

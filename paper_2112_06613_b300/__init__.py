@@ -96,7 +96,7 @@ SYMBOLS = [
     "tcrnet_options_init", "tcrnet_build", "tcrnet_build_flat", "tcrnet_info", "tcrnet_copy_csr",
     "tcrnet_csr_device", "tcrnet_query_flat", "tcrnet_query", "tcrnet_stats_get", "tcrnet_free",
     "tcrnet_strerror", "tcrnet_last_error_index", "tcrnet_version", "tcrnet_last_cuda_error",
-    "tcrnet_degree_noalloc", "tcrnet_query_ex",
+    "tcrnet_degree_noalloc", "tcrnet_query_ex", "tcrnet_insert_flat", "tcrnet_insert_ex", "tcrnet_insert",
 ]
 
 
@@ -129,6 +129,12 @@ def load_library(path: str = LIB_PATH):
         lib.tcrnet_csr_device.restype = ctypes.c_int
         lib.tcrnet_query_flat.argtypes = [H, vp, vp, i64, i32, HP]
         lib.tcrnet_query_flat.restype = ctypes.c_int
+        lib.tcrnet_insert_flat.argtypes = [H, vp, vp, i64, i32]
+        lib.tcrnet_insert_flat.restype = ctypes.c_int
+        lib.tcrnet_insert_ex.argtypes = [H, vp, vp, i64, i32, optp]
+        lib.tcrnet_insert_ex.restype = ctypes.c_int
+        lib.tcrnet_insert.argtypes = [H, ctypes.POINTER(ctypes.c_char_p), i64]
+        lib.tcrnet_insert.restype = ctypes.c_int
         lib.tcrnet_query_ex.argtypes = [H, vp, vp, i64, i32, optp, HP]
         lib.tcrnet_query_ex.restype = ctypes.c_int
         lib.tcrnet_query.argtypes = [H, ctypes.POINTER(ctypes.c_char_p), i64, HP]
@@ -253,6 +259,22 @@ class Graph:
 
     def query(self, queries):
         return tcrnet_query(self, queries)
+
+    def insert(self, seqs):
+        """Append host strings as new nodes (tcrnet_insert)."""
+        lib = load_library()
+        enc = [s.encode("ascii") if isinstance(s, str) else bytes(s) for s in seqs]
+        arr = (ctypes.c_char_p * max(len(enc), 1))(*enc)
+        _check(lib.tcrnet_insert(self._h, arr, len(enc)), "tcrnet_insert")
+
+    def insert_flat(self, chars, offsets, stream=None, profile=False):
+        """Append strings in flat layout (numpy or torch, host or device) as new nodes."""
+        lib = load_library()
+        cp, op, m, mem, keep = _flat_args(chars, offsets)
+        opt = make_options(stream=stream, profile=profile)
+        st = lib.tcrnet_insert_ex(self._h, cp, op, m, mem, ctypes.byref(opt))
+        del keep
+        _check(st, "tcrnet_insert_ex")
 
     def query_flat(self, chars, offsets, method="auto", stream=None):
         if method == "auto" and stream is None:

@@ -184,11 +184,25 @@ int sm_count(int dev) {
     return v;
 }
 
+// Per-device non-blocking stream on which handle memory is returned to the
+// pool. Every call that touches a handle's memory synchronizes its stream before
+// returning, so nothing is pending on it at free time, and a free does not
+// serialize work running on other streams (cudaFree would synchronize the device).
+cudaStream_t free_stream(int dev) {
+    static std::mutex mu;
+    static cudaStream_t st[64] = {nullptr};
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= 64) return 0;
+    if (!st[dev] && cudaStreamCreateWithFlags(&st[dev], cudaStreamNonBlocking) != cudaSuccess) st[dev] = 0;
+    return st[dev];
+}
+
 void free_handle_memory(tcrnet_graph* h) {
     void* ptrs[] = {h->d_offsets, h->d_cols, h->d_degree, h->d_bcanon, h->d_bperm, h->ix.ucanon, h->ix.umult,
                     h->ix.mem_off, h->ix.members, h->ix.recs, h->ix.poff};
+    const cudaStream_t fs = free_stream(h->device);
     for (void* p : ptrs)
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, fs);
     h->ix = DeletionIndex();
     h->d_offsets = nullptr;
     h->d_cols = nullptr;
@@ -311,6 +325,53 @@ tcrnet_status flatten(const char* const* seqs, int64_t n, std::vector<uint8_t>& 
     return TCRNET_OK;
 }
 
+// Network of an encoded, bucketed repertoire (pk) into handle h by the method
+// the options select: CSR, degree, resident repertoire and, for the deletion
+// method, the query index.
+tcrnet_status build_from_packed(tcrnet_graph* h, Packed& pk, int64_t n, int32_t T, const tcrnet_options& opt,
+                                Phases& ph, cudaStream_t s, int sms) {
+    tcrnet_status st = TCRNET_OK;
+    int method = opt.method;
+    if (method == TCRNET_METHOD_AUTO) method = (n >= kAutoDeletionMinN) ? TCRNET_METHOD_DELETION : TCRNET_METHOD_TILE;
+    h->stats.method = method;
+    for (int L = 0; L < kMaxLen + 2; ++L) h->bucket_off[L] = pk.bucket_off[L];
+    if (n == 0) {
+        DevBuf off64, cols, deg;
+        if ((st = off64.alloc_owned(sizeof(int64_t), s)) != TCRNET_OK) return st;
+        if (cudaMemsetAsync(off64.as<void>(), 0, sizeof(int64_t), s) != cudaSuccess) return TCRNET_EDEVICE;
+        if ((st = cols.alloc_owned(0, s)) != TCRNET_OK) return st;
+        if ((st = deg.alloc_owned(0, s)) != TCRNET_OK) return st;
+        if ((st = export_csr(h, off64, cols, deg, 0, 0, opt.force_offsets64 != 0, s)) != TCRNET_OK) return st;
+    } else if (method == TCRNET_METHOD_TILE) {
+        TileSide side{pk.canon.as<Canon>(), pk.perm.as<int32_t>(), pk.bucket_off};
+        st = tile_method(h, side, side, n, true, T, opt.force_offsets64 != 0, ph, s, sms);
+        if (st != TCRNET_OK) return st;
+    } else {
+        DeletionResult dr;
+        st = deletion_build(pk, T, dr, s, sms, opt.profile != 0, opt.partition_cap, /*keep_index=*/true);
+        if (st != TCRNET_OK) return st;
+        h->stats.n_unique = dr.n_unique;
+        h->stats.n_records = dr.n_records;
+        h->stats.unique_edges = dr.unique_edges;
+        h->stats.n_fallback = dr.n_fallback;
+        h->stats.closed_total = dr.closed_total;
+        h->stats.two_pass_join = dr.two_pass_join;
+        h->stats.ms_count = dr.ms_join;
+        h->stats.ms_scan = dr.ms_scan;
+        h->stats.ms_write = dr.ms_fill;
+        h->stats.ms_sort = dr.ms_sort;
+        for (int k = 0; k < 8; ++k) h->stats.ms_phase[k] = dr.ms_phase[k];
+        h->ix = dr.index;  // owned by the handle from here on
+        dr.index = DeletionIndex();
+        st = export_csr(h, dr.off64, dr.cols, dr.degree, n, dr.nnz, opt.force_offsets64 != 0, s);
+        if (st != TCRNET_OK) return st;
+    }
+    // keep the bucketed repertoire resident for queries
+    h->d_bcanon = static_cast<Canon*>(pk.canon.release());
+    h->d_bperm = static_cast<int32_t*>(pk.perm.release());
+    return TCRNET_OK;
+}
+
 tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n, int mem, int32_t T,
                          const tcrnet_options* opt_in, tcrnet_handle* out) {
     if (!out) return TCRNET_EINVAL;
@@ -365,44 +426,8 @@ tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n
         }
     }
     const int p2 = ph.mark();
-    int method = opt.method;
-    if (method == TCRNET_METHOD_AUTO) method = (n >= kAutoDeletionMinN) ? TCRNET_METHOD_DELETION : TCRNET_METHOD_TILE;
-    h->stats.method = method;
-    for (int L = 0; L < kMaxLen + 2; ++L) h->bucket_off[L] = pk.bucket_off[L];
-    if (n == 0) {
-        DevBuf off64, cols, deg;
-        if ((st = off64.alloc_owned(sizeof(int64_t), s)) != TCRNET_OK) return fail(st);
-        if (cudaMemsetAsync(off64.as<void>(), 0, sizeof(int64_t), s) != cudaSuccess) return fail(TCRNET_EDEVICE);
-        if ((st = cols.alloc_owned(0, s)) != TCRNET_OK) return fail(st);
-        if ((st = deg.alloc_owned(0, s)) != TCRNET_OK) return fail(st);
-        if ((st = export_csr(h, off64, cols, deg, 0, 0, opt.force_offsets64 != 0, s)) != TCRNET_OK) return fail(st);
-    } else if (method == TCRNET_METHOD_TILE) {
-        TileSide side{pk.canon.as<Canon>(), pk.perm.as<int32_t>(), pk.bucket_off};
-        st = tile_method(h, side, side, n, true, T, opt.force_offsets64 != 0, ph, s, sms);
-        if (st != TCRNET_OK) return fail(st);
-    } else {
-        DeletionResult dr;
-        st = deletion_build(pk, T, dr, s, sms, opt.profile != 0, opt.partition_cap, /*keep_index=*/true);
-        if (st != TCRNET_OK) return fail(st);
-        h->stats.n_unique = dr.n_unique;
-        h->stats.n_records = dr.n_records;
-        h->stats.unique_edges = dr.unique_edges;
-        h->stats.n_fallback = dr.n_fallback;
-        h->stats.closed_total = dr.closed_total;
-        h->stats.two_pass_join = dr.two_pass_join;
-        h->stats.ms_count = dr.ms_join;
-        h->stats.ms_scan = dr.ms_scan;
-        h->stats.ms_write = dr.ms_fill;
-        h->stats.ms_sort = dr.ms_sort;
-        for (int k = 0; k < 8; ++k) h->stats.ms_phase[k] = dr.ms_phase[k];
-        h->ix = dr.index;  // owned by the handle from here on
-        dr.index = DeletionIndex();
-        st = export_csr(h, dr.off64, dr.cols, dr.degree, n, dr.nnz, opt.force_offsets64 != 0, s);
-        if (st != TCRNET_OK) return fail(st);
-    }
-    // keep the bucketed repertoire resident for queries
-    h->d_bcanon = static_cast<Canon*>(pk.canon.release());
-    h->d_bperm = static_cast<int32_t*>(pk.perm.release());
+    st = build_from_packed(h, pk, n, T, opt, ph, s, sms);
+    if (st != TCRNET_OK) return fail(st);
     const int p3 = ph.mark();
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(TCRNET_EDEVICE);
     h->stats.nnz = h->nnz;
@@ -563,6 +588,89 @@ tcrnet_status tcrnet_query(tcrnet_handle h, const char* const* queries, int64_t 
     return tcrnet_query_flat(h, chars.data(), offs.data(), m, TCRNET_HOST, out);
 }
 
+tcrnet_status tcrnet_insert_ex(tcrnet_handle h, const uint8_t* chars, const int64_t* offsets, int64_t m, int32_t mem,
+                               const tcrnet_options* opt_in) {
+    t_last_bad = -1;
+    if (!h || m < 0) return TCRNET_EINVAL;
+    if (h->query_result) return TCRNET_ESTATE;
+    if (m == 0) return TCRNET_OK;
+    const int64_t n_old = h->n;
+    const int64_t N = n_old + m;
+    if (N > 0x7fffffffLL) return TCRNET_EINVAL;
+    tcrnet_options opt;
+    tcrnet_options_init(&opt);
+    opt.method = h->stats.method;  // the grown repertoire is built the way the handle was
+    opt.force_offsets64 = (h->offsets64 && h->nnz <= 0x7fffffffLL) ? 1 : 0;
+    if (opt_in) {
+        opt.stream = opt_in->stream;
+        opt.profile = opt_in->profile;
+    }
+    DeviceGuard dg;
+    TCR_CHECK(dg.set(h->device));
+    cudaStream_t s = opt.stream ? (cudaStream_t)opt.stream : h->stream;
+    opt.stream = s;
+    const int sms = sm_count(h->device);
+    ArenaLease lease(h->device, s);
+    Phases ph(opt.profile != 0, s);
+    const int64_t launches0 = launches_so_far();
+    Inputs in;
+    TCR_CHECK(stage_inputs(chars, offsets, m, mem, in, s));
+    Packed pn;
+    int64_t bad = -1;
+    tcrnet_status st = pack_strings(in.d_chars - in.base, in.d_offs, m, pn, &bad, s);
+    if (st != TCRNET_OK) {
+        t_last_bad = bad;
+        return st;
+    }
+    // the grown repertoire: resident strings (input order restored) then the new ones
+    Packed pk;
+    pk.n = N;
+    TCR_CHECK(pk.canon_in.alloc(sizeof(Canon) * N, s));
+    TCR_CHECK(pk.lens.alloc(N, s));
+    TCR_CHECK(unbucket_strings(h->d_bcanon, h->d_bperm, h->bucket_off, n_old, pk.canon_in.as<Canon>(),
+                               pk.lens.as<uint8_t>(), s));
+    TCR_CUDA(cudaMemcpyAsync(pk.canon_in.as<Canon>() + n_old, pn.canon_in.as<Canon>(), sizeof(Canon) * m,
+                             cudaMemcpyDeviceToDevice, s));
+    TCR_CUDA(cudaMemcpyAsync(pk.lens.as<uint8_t>() + n_old, pn.lens.as<uint8_t>(), m, cudaMemcpyDeviceToDevice, s));
+    TCR_CHECK(bucket_strings(pk, s));
+    tcrnet_graph* g = new (std::nothrow) tcrnet_graph();
+    if (!g) return TCRNET_ENOMEM;
+    std::memset(&g->stats, 0, sizeof(g->stats));
+    g->device = h->device;
+    g->stream = h->stream;
+    g->threshold = h->threshold;
+    g->stats.threshold = h->threshold;
+    g->stats.n = N;
+    st = build_from_packed(g, pk, N, h->threshold, opt, ph, s, sms);
+    if (st == TCRNET_OK && cudaStreamSynchronize(s) != cudaSuccess) st = TCRNET_EDEVICE;
+    if (st != TCRNET_OK) {
+        cudaStreamSynchronize(s);
+        free_handle_memory(g);
+        delete g;
+        return st;  // the handle keeps its previous network
+    }
+    free_handle_memory(h);
+    g->stats.nnz = g->nnz;
+    g->stats.kernel_launches = launches_so_far() - launches0;
+    *h = *g;  // plain pointers and sizes: the handle now owns g's memory
+    delete g;
+    return TCRNET_OK;
+}
+
+tcrnet_status tcrnet_insert_flat(tcrnet_handle h, const uint8_t* chars, const int64_t* offsets, int64_t m,
+                                 int32_t mem) {
+    return tcrnet_insert_ex(h, chars, offsets, m, mem, nullptr);
+}
+
+tcrnet_status tcrnet_insert(tcrnet_handle h, const char* const* seqs, int64_t m) {
+    t_last_bad = -1;
+    if (m < 0) return TCRNET_EINVAL;
+    std::vector<uint8_t> chars;
+    std::vector<int64_t> offs;
+    TCR_CHECK(flatten(seqs, m, chars, offs));
+    return tcrnet_insert_ex(h, chars.data(), offs.data(), m, TCRNET_HOST, nullptr);
+}
+
 tcrnet_status tcrnet_stats_get(tcrnet_handle h, tcrnet_stats* out) {
     if (!h || !out) return TCRNET_EINVAL;
     *out = h->stats;
@@ -573,8 +681,7 @@ void tcrnet_free(tcrnet_handle h) {
     if (!h) return;
     DeviceGuard dg;
     dg.set(h->device);
-    cudaStreamSynchronize(h->stream);
-    free_handle_memory(h);
+    free_handle_memory(h);  // every call on h already completed; see free_stream
     delete h;
 }
 

@@ -29,6 +29,12 @@ struct Packed {
 tcrnet_status pack_strings(const uint8_t* d_chars, const int64_t* d_offsets, int64_t n, Packed& out,
                            int64_t* bad_index, cudaStream_t s);
 
+// Bucket already encoded strings (out.canon_in, out.lens, out.n set).
+tcrnet_status bucket_strings(Packed& out, cudaStream_t s);
+// Inverse of the bucketing: input-order canon and lengths from bucket order.
+tcrnet_status unbucket_strings(const Canon* canon, const int32_t* perm, const int64_t* bucket_off_host, int64_t n,
+                               Canon* canon_in, uint8_t* lens, cudaStream_t s);
+
 // ---- tile.cu --------------------------------------------------------------
 struct TileSide {
     const Canon* canon;  // bucket order

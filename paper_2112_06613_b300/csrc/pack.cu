@@ -91,12 +91,75 @@ k_bucket_scatter(const Canon* __restrict__ canon_in, const uint8_t* __restrict__
     }
 }
 
+// Length counts per block of already encoded strings (lens).
+__global__ void __launch_bounds__(kPackThreads)
+k_count_lengths(const uint8_t* __restrict__ lens, int64_t n, int32_t* __restrict__ blockcnt, int nblocks) {
+    __shared__ int cnt[kBins];
+    for (int t = threadIdx.x; t < kBins; t += blockDim.x) cnt[t] = 0;
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * kPackThreads + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[lens[i]], 1);
+    __syncthreads();
+    for (int t = threadIdx.x; t < kBins; t += blockDim.x) blockcnt[(int64_t)t * nblocks + blockIdx.x] = cnt[t];
+}
+
+// Input order from bucket order: canon_in[perm[pos]] = canon[pos], lens from the bucket bounds.
+__global__ void k_unbucket(const Canon* __restrict__ canon, const int32_t* __restrict__ perm, int64_t n,
+                           const int64_t* __restrict__ bounds, Canon* __restrict__ canon_in, uint8_t* __restrict__ lens) {
+    const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= n) return;
+    int L = 0;
+    while (L < kMaxLen && bounds[L + 1] <= pos) ++L;
+    const int32_t i = perm[pos];
+    store_canon(canon_in + i, load_canon(canon + pos));
+    lens[i] = (uint8_t)L;
+}
+
 __global__ void k_bucket_bounds(const int64_t* __restrict__ blockoff, int nblocks, int64_t* __restrict__ bounds) {
     const int t = threadIdx.x;
     if (t <= kBins) bounds[t] = blockoff[(int64_t)t * nblocks];  // t == kBins: the grand total
 }
 
 }  // namespace
+
+tcrnet_status bucket_strings(Packed& out, cudaStream_t s) {
+    const int64_t n = out.n;
+    for (int L = 0; L < kMaxLen + 2; ++L) out.bucket_off[L] = 0;
+    if (n == 0) return TCRNET_OK;
+    const int nblocks = (int)ceil_div(n, kPackThreads);
+    TCR_CHECK(out.canon.alloc_owned(sizeof(Canon) * n, s));
+    TCR_CHECK(out.perm.alloc_owned(sizeof(int32_t) * n, s));
+    const int64_t ncnt = (int64_t)kBins * nblocks;
+    DevBuf blockcnt, blockoff, bounds;
+    TCR_CHECK(blockcnt.alloc(sizeof(int32_t) * ncnt, s));
+    TCR_CHECK(blockoff.alloc(sizeof(int64_t) * (ncnt + 1), s));
+    TCR_CHECK(bounds.alloc(sizeof(int64_t) * (kBins + 1), s));
+    k_count_lengths<<<nblocks, kPackThreads, 0, s>>>(out.lens.as<uint8_t>(), n, blockcnt.as<int32_t>(), nblocks);
+    TCR_LAUNCH_CHECK();
+    TCR_CHECK(scan_exclusive_i32_to_i64(blockcnt.as<int32_t>(), blockoff.as<int64_t>(), ncnt, s));
+    k_bucket_bounds<<<1, 64, 0, s>>>(blockoff.as<int64_t>(), nblocks, bounds.as<int64_t>());
+    TCR_LAUNCH_CHECK();
+    int64_t h_bounds[kBins + 1];
+    TCR_CUDA(cudaMemcpyAsync(h_bounds, bounds.as<void>(), sizeof(h_bounds), cudaMemcpyDeviceToHost, s));
+    k_bucket_scatter<<<nblocks, kPackThreads, 0, s>>>(out.canon_in.as<Canon>(), out.lens.as<uint8_t>(), n,
+                                                      blockoff.as<int64_t>(), nblocks, out.canon.as<Canon>(),
+                                                      out.perm.as<int32_t>());
+    TCR_LAUNCH_CHECK();
+    TCR_CUDA(cudaStreamSynchronize(s));
+    for (int L = 0; L <= kBins; ++L) out.bucket_off[L] = h_bounds[L];
+    return TCRNET_OK;
+}
+
+tcrnet_status unbucket_strings(const Canon* canon, const int32_t* perm, const int64_t* bucket_off_host, int64_t n,
+                               Canon* canon_in, uint8_t* lens, cudaStream_t s) {
+    if (n == 0) return TCRNET_OK;
+    DevBuf bounds;
+    TCR_CHECK(bounds.alloc(sizeof(int64_t) * (kBins + 1), s));
+    TCR_CUDA(cudaMemcpyAsync(bounds.as<void>(), bucket_off_host, sizeof(int64_t) * (kBins + 1), cudaMemcpyHostToDevice, s));
+    k_unbucket<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(canon, perm, n, bounds.as<int64_t>(), canon_in, lens);
+    TCR_LAUNCH_CHECK();
+    return TCRNET_OK;
+}
 
 tcrnet_status pack_strings(const uint8_t* d_chars, const int64_t* d_offsets, int64_t n, Packed& out,
                            int64_t* bad_index, cudaStream_t s) {

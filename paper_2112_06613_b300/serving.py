@@ -1,0 +1,281 @@
+"""Serving loop over a resident TCR network (host-side scheduler).
+
+A resident build handle answers neighbour queries and absorbs inserts while
+requests keep arriving:
+
+- continuous batching: when a worker slot frees up it takes every queued query
+  request at the head of the queue (up to `max_batch_strings` strings) and runs
+  them as one device call (`tcrnet_query_ex`); the result rows are split back
+  per request;
+- slots: `slots` worker threads, each with its own CUDA stream, so admitted
+  queries overlap on the device (the C library releases the GIL);
+- inserts (`tcrnet_insert_ex`) take the handle exclusively (reader-writer
+  lock); queries admitted before an insert see the previous repertoire, later
+  ones the grown one; each request records the repertoire version it ran on;
+- admission by memory: a request starts only when its estimated device memory
+  fits in the free HBM reported by the driver minus a reserve (otherwise it
+  waits until running requests release theirs).
+
+All computation happens in the CUDA library; this module only schedules calls.
+"""
+
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import Graph
+
+
+class RWLock:
+    """Many readers or one writer; a waiting writer blocks new readers."""
+
+    def __init__(self):
+        self._cv = threading.Condition()
+        self._readers = 0
+        self._writer = False
+        self._writers_waiting = 0
+
+    def acquire_read(self):
+        with self._cv:
+            while self._writer or self._writers_waiting:
+                self._cv.wait()
+            self._readers += 1
+
+    def release_read(self):
+        with self._cv:
+            self._readers -= 1
+            if self._readers == 0:
+                self._cv.notify_all()
+
+    def acquire_write(self):
+        with self._cv:
+            self._writers_waiting += 1
+            while self._writer or self._readers:
+                self._cv.wait()
+            self._writers_waiting -= 1
+            self._writer = True
+
+    def release_write(self):
+        with self._cv:
+            self._writer = False
+            self._cv.notify_all()
+
+
+@dataclass
+class Request:
+    kind: str  # "query" or "insert"
+    chars: np.ndarray
+    offsets: np.ndarray
+    t_arrival: float = 0.0
+    t_start: float = 0.0
+    t_done: float = 0.0
+    version: int = -1  # inserts applied before this request ran
+    batch_id: int = -1  # device call that served it
+    offsets_out: np.ndarray | None = None
+    cols_out: np.ndarray | None = None
+    error: BaseException | None = None
+    done: threading.Event = field(default_factory=threading.Event)
+
+    @property
+    def n_strings(self) -> int:
+        return int(self.offsets.shape[0] - 1)
+
+    @property
+    def latency_s(self) -> float:
+        return self.t_done - self.t_arrival
+
+
+class ServingEngine:
+    def __init__(self, graph: Graph, slots: int = 4, max_batch_strings: int = 200_000,
+                 hbm_reserve_bytes: int = 4 << 30, device: int = 0):
+        import torch
+
+        self.graph = graph
+        self.slots = slots
+        self.max_batch_strings = max_batch_strings
+        self.reserve = hbm_reserve_bytes
+        self.device = device
+        self._torch = torch
+        self._streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
+        self._queue: collections.deque[Request] = collections.deque()
+        self._cv = threading.Condition()
+        self._rw = RWLock()
+        self._inflight_bytes = 0
+        self._inflight = 0
+        self._stop = False
+        self._version = 0
+        self._batches = 0
+        self._workers = [threading.Thread(target=self._run, args=(k,), daemon=True) for k in range(slots)]
+        self.completed: list[Request] = []
+
+    # ---- lifecycle -----------------------------------------------------
+    def start(self):
+        for w in self._workers:
+            w.start()
+        return self
+
+    def shutdown(self, wait: bool = True):
+        with self._cv:
+            self._stop = True
+            self._cv.notify_all()
+        if wait:
+            for w in self._workers:
+                w.join()
+
+    def __enter__(self):
+        return self.start()
+
+    def __exit__(self, *exc):
+        self.shutdown()
+
+    # ---- requests ------------------------------------------------------
+    def submit(self, req: Request) -> Request:
+        req.t_arrival = time.perf_counter()
+        with self._cv:
+            self._queue.append(req)
+            self._cv.notify_all()
+        return req
+
+    def query(self, chars, offsets) -> Request:
+        return self.submit(Request("query", np.ascontiguousarray(chars, np.uint8),
+                                   np.ascontiguousarray(offsets, np.int64)))
+
+    def insert(self, chars, offsets) -> Request:
+        return self.submit(Request("insert", np.ascontiguousarray(chars, np.uint8),
+                                   np.ascontiguousarray(offsets, np.int64)))
+
+    # ---- admission -----------------------------------------------------
+    def _estimate_bytes(self, kind: str, strings: int) -> int:
+        n, nnz, _ = self.graph.info()
+        mean_deg = nnz / max(n, 1)
+        if kind == "query":
+            # packed strings, records, counts, offsets, and the result lists (x4 margin)
+            return int(strings * (96 + 4 * 4 * (mean_deg + 1)))
+        # an insert rebuilds the grown repertoire: scratch about 600 B per string
+        # plus the new CSR
+        return int((n + strings) * 600 + 4 * (nnz * (n + strings) / max(n, 1)))
+
+    def _admissible(self, need: int) -> bool:
+        if self._inflight == 0:
+            return True  # never starve: one request may always run
+        free, _ = self._torch.cuda.mem_get_info(self.device)
+        return need + self.reserve <= free
+
+    def _take(self):
+        with self._cv:
+            while True:
+                if self._stop and not self._queue:
+                    return None, 0
+                if self._queue:
+                    head = self._queue[0]
+                    if head.kind == "insert":
+                        batch = [head]
+                        strings = head.n_strings
+                    else:
+                        batch, strings = [], 0
+                        for r in self._queue:
+                            if r.kind != "query":
+                                break
+                            if batch and strings + r.n_strings > self.max_batch_strings:
+                                break
+                            batch.append(r)
+                            strings += r.n_strings
+                    need = self._estimate_bytes(head.kind, strings)
+                    if self._admissible(need):
+                        for _ in batch:
+                            self._queue.popleft()
+                        self._inflight += 1
+                        self._inflight_bytes += need
+                        return batch, need
+                self._cv.wait(timeout=0.05)
+
+    def _release(self, need: int):
+        with self._cv:
+            self._inflight -= 1
+            self._inflight_bytes -= need
+            self._cv.notify_all()
+
+    # ---- workers -------------------------------------------------------
+    def _run(self, slot: int):
+        stream = self._streams[slot]
+        while True:
+            batch, need = self._take()
+            if batch is None:
+                return
+            t0 = time.perf_counter()
+            for r in batch:
+                r.t_start = t0
+            try:
+                if batch[0].kind == "insert":
+                    self._do_insert(batch[0], stream)
+                else:
+                    self._do_queries(batch, stream)
+            except BaseException as e:  # reported per request
+                for r in batch:
+                    r.error = e
+            finally:
+                t1 = time.perf_counter()
+                for r in batch:
+                    r.t_done = t1
+                    r.done.set()
+                with self._cv:
+                    self.completed.extend(batch)
+                self._release(need)
+
+    def _do_insert(self, req: Request, stream):
+        self._rw.acquire_write()
+        try:
+            with self._cv:
+                req.version = self._version
+                req.batch_id = self._batches
+                self._batches += 1
+            self.graph.insert_flat(req.chars, req.offsets, stream=stream)
+            with self._cv:
+                self._version += 1
+        finally:
+            self._rw.release_write()
+
+    def _do_queries(self, batch: list[Request], stream):
+        if len(batch) == 1:
+            chars, offsets = batch[0].chars, batch[0].offsets
+        else:
+            chars = np.concatenate([r.chars[r.offsets[0]:r.offsets[-1]] for r in batch])
+            lens = np.concatenate([np.diff(r.offsets) for r in batch])
+            offsets = np.zeros(lens.shape[0] + 1, dtype=np.int64)
+            np.cumsum(lens, out=offsets[1:])
+        self._rw.acquire_read()
+        try:
+            with self._cv:
+                version = self._version
+                bid = self._batches
+                self._batches += 1
+            res = self.graph.query_flat(chars, offsets, method="auto", stream=stream)
+            try:
+                off, cols, _ = res.copy_csr()
+            finally:
+                res.free()
+        finally:
+            self._rw.release_read()
+        off = np.asarray(off, dtype=np.int64)
+        row = 0
+        for r in batch:
+            k = r.n_strings
+            o = off[row:row + k + 1]
+            r.offsets_out = o - o[0]
+            r.cols_out = cols[o[0]:o[-1]].copy()
+            r.version = version
+            r.batch_id = bid
+            row += k
+
+
+def latency_summary(reqs, kind: str):
+    lat = [1e3 * r.latency_s for r in reqs if r.kind == kind and r.error is None]
+    if not lat:
+        return None
+    return {"count": len(lat), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(np.mean(lat))}
