@@ -66,6 +66,8 @@ def parse_args():
     ap.add_argument("--query-batches", type=int, default=30)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--serve-seconds", type=float, default=5.0, help="0 skips the serving leg")
+    ap.add_argument("--serve-n", type=int, default=2_000_000)
     ap.add_argument("--no-extras", action="store_true", help="skip tile/query/e2e/cpu legs")
     return ap.parse_args()
 
@@ -260,6 +262,72 @@ def tile_ops_per_pair(lengths):
     return ops, pairs
 
 
+def serve_leg(args, tn, torch, stream):
+    """Serving: resident repertoire of args.serve_n strings, open-loop Poisson
+    arrivals (200/s) of queries (90%, log-uniform 1..50,000 strings) and inserts
+    (10%, log-uniform 1,000..100,000 strings) for args.serve_seconds."""
+    from paper_2112_06613_b300.serving import ServingEngine, latency_summary
+    from synthgen import generate_config2
+
+    rng = np.random.default_rng(11)
+    base = generate_config2(args.serve_n, seed=100)
+    qpool = generate_config2(400_000, seed=101)
+    ipool = generate_config2(3_000_000, seed=102)
+    rate = 200.0
+    arrivals, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > args.serve_seconds:
+            break
+        if rng.random() < 0.1:
+            arrivals.append((t, "insert", int(round(math.exp(rng.uniform(math.log(1e3), math.log(1e5)))))))
+        else:
+            arrivals.append((t, "query", int(round(math.exp(rng.uniform(0, math.log(5e4)))))))
+    chars = torch.from_numpy(base.chars).to("cuda")
+    offs = torch.from_numpy(base.offsets).to("cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = tn.tcrnet_build_flat(chars, offs, 1, stream=stream)
+    torch.cuda.synchronize()
+    plain_build_ms = 1e3 * (time.perf_counter() - t0)
+    reqs = []
+    ip = 0
+    with ServingEngine(g, slots=4, max_batch_strings=200_000) as eng:
+        start = time.perf_counter()
+        for at, kind, size in arrivals:
+            now = time.perf_counter() - start
+            if at > now:
+                time.sleep(at - now)
+            if kind == "query":
+                k0 = int(rng.integers(0, qpool.n - size))
+                o = qpool.offsets[k0:k0 + size + 1]
+                reqs.append(eng.query(qpool.chars[o[0]:o[-1]], o - o[0]))
+            else:
+                size = min(size, ipool.n - ip)
+                o = ipool.offsets[ip:ip + size + 1]
+                reqs.append(eng.insert(ipool.chars[o[0]:o[-1]], o - o[0]))
+                ip += size
+        for r in reqs:
+            r.done.wait()
+        wall = time.perf_counter() - start
+    n_final, nnz_final, _ = g.info()
+    g.free()
+    errors = sum(r.error is not None for r in reqs)
+    qs = [r for r in reqs if r.kind == "query"]
+    return {
+        "resident_strings_start": args.serve_n, "resident_strings_end": n_final, "nnz_end": nnz_final,
+        "arrival_rate_per_s": rate, "duration_s": args.serve_seconds, "wall_s": wall,
+        "requests": len(reqs), "errors": errors,
+        "query": latency_summary(reqs, "query"), "insert": latency_summary(reqs, "insert"),
+        "throughput_requests_per_s": len(reqs) / wall,
+        "query_strings_per_s": sum(r.n_strings for r in qs) / wall,
+        "device_calls": len({r.batch_id for r in reqs}),
+        "plain_build_ms_at_start": plain_build_ms,
+        "engine": "4 slots (streams), queued queries merged up to 200,000 strings per call, inserts exclusive, "
+                  "admission by free HBM",
+    }
+
+
 def run_ours(args):
     import torch
 
@@ -435,6 +503,9 @@ def run_ours(args):
         line["e2e"] = {"value": pairs_per_build / (e_ms / 1e3), "unit": UNIT, "ms_per_step": e_ms,
                        "h2d_bytes_per_step": int(rep.chars.nbytes + rep.offsets.nbytes),
                        "d2h_bytes_per_step": int(4 * (n + 1) + 4 * nnz + 4 * n)}
+        # --- serving: resident repertoire, Poisson queries and inserts
+        if args.serve_seconds > 0:
+            line["serving"] = serve_leg(args, tn, torch, stream)
         # --- CPU oracle on a bounded sample (rank 0, one GPU only)
         if world == 1 and args.cpu_seconds > 0:
             rate, cores, rows, el = oracle_rate(rep, args.cpu_seconds)
