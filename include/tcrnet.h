@@ -23,9 +23,11 @@
  *  - Node id = input position. Duplicate strings are distinct nodes and are
  *    adjacent to each other (distance 0).
  *  - Inputs are borrowed for the duration of the call and never retained.
- *  - Supported thresholds: 0 and 1 (the paper's network-construction setting,
- *    Fig. performance). Thresholds >= 2 return TCRNET_ENOTSUP; negative ones
- *    TCRNET_EINVAL.
+ *  - Thresholds: any l_max >= 0 (negative: TCRNET_EINVAL). 0 and 1 (the paper's
+ *    network-construction setting, Fig. performance) use closed-form tests or
+ *    the deletion join; l_max >= 2 (the paper's analyses use 2 and 6) computes
+ *    the distance bit-parallel on the tile path (TCRNET_METHOD_DELETION with
+ *    l_max >= 2: TCRNET_ENOTSUP).
  *  - Work is ordered on the CUDA stream given in tcrnet_options (NULL: the
  *    legacy default stream). Calls return after the result is complete on the
  *    device unless stated otherwise.
@@ -55,7 +57,7 @@ typedef enum tcrnet_status {
     TCRNET_EINVAL = 1,    /* bad argument, empty string or non-monotone offsets */
     TCRNET_EBADCHAR = 2,  /* a character outside the 20-letter alphabet */
     TCRNET_ETOOLONG = 3,  /* a string longer than TCRNET_MAX_LEN */
-    TCRNET_ENOTSUP = 4,   /* threshold >= 2, or an option this build lacks */
+    TCRNET_ENOTSUP = 4,   /* combination not supported (deletion method with l_max >= 2, ...) */
     TCRNET_ENOMEM = 5,    /* device or host allocation failed; nothing leaked */
     TCRNET_EDEVICE = 6,   /* a CUDA error; the handle is poisoned */
     TCRNET_ETIMEOUT = 7,  /* a bounded device wait ran out; the handle is poisoned */

@@ -332,7 +332,8 @@ tcrnet_status build_from_packed(tcrnet_graph* h, Packed& pk, int64_t n, int32_t 
                                 Phases& ph, cudaStream_t s, int sms) {
     tcrnet_status st = TCRNET_OK;
     int method = opt.method;
-    if (method == TCRNET_METHOD_AUTO) method = (n >= kAutoDeletionMinN) ? TCRNET_METHOD_DELETION : TCRNET_METHOD_TILE;
+    if (method == TCRNET_METHOD_AUTO)
+        method = (n >= kAutoDeletionMinN && T <= 1) ? TCRNET_METHOD_DELETION : TCRNET_METHOD_TILE;
     h->stats.method = method;
     for (int L = 0; L < kMaxLen + 2; ++L) h->bucket_off[L] = pk.bucket_off[L];
     if (n == 0) {
@@ -382,8 +383,8 @@ tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n
     if (opt_in) opt = *opt_in;
     if (n < 0 || n > 0x7fffffffLL) return TCRNET_EINVAL;
     if (T < 0) return TCRNET_EINVAL;
-    if (T > 1) return TCRNET_ENOTSUP;
     if (opt.method < TCRNET_METHOD_AUTO || opt.method > TCRNET_METHOD_DELETION) return TCRNET_EINVAL;
+    if (T > 1 && opt.method == TCRNET_METHOD_DELETION) return TCRNET_ENOTSUP;  // deletion join: l_max <= 1
     DeviceGuard dg;
     TCR_CHECK(dg.set(opt.device));
     int dev = 0;
@@ -691,7 +692,7 @@ const char* tcrnet_strerror(tcrnet_status s) {
         case TCRNET_EINVAL: return "invalid argument (empty string, bad offsets or parameter)";
         case TCRNET_EBADCHAR: return "character outside the 20 standard amino acids";
         case TCRNET_ETOOLONG: return "string longer than TCRNET_MAX_LEN";
-        case TCRNET_ENOTSUP: return "not supported (threshold >= 2 or option)";
+        case TCRNET_ENOTSUP: return "not supported (deletion method with threshold >= 2, or option)";
         case TCRNET_ENOMEM: return "out of memory";
         case TCRNET_EDEVICE: return "CUDA device error";
         case TCRNET_ETIMEOUT: return "bounded device wait timed out";

@@ -51,6 +51,12 @@ tcrnet_status tile_pass(const TileSide& rows, const TileSide& cols, bool sym, in
                         int32_t* count, const int64_t* off, int32_t* cursor, int32_t* cols_out,
                         int64_t* pairs, cudaStream_t s, int num_sms);
 
+// ---- dp.cu ----------------------------------------------------------------
+// Same contract as tile_pass for l_max >= 2 (bit-parallel Levenshtein distance).
+tcrnet_status dp_pass(const TileSide& rows, const TileSide& cols, bool sym, int threshold, bool write,
+                      int32_t* count, const int64_t* off, int32_t* cursor, int32_t* cols_out, int64_t* pairs,
+                      cudaStream_t s, int num_sms);
+
 // ---- rowsort.cu -----------------------------------------------------------
 // Sort every row segment cols[off[i] .. off[i+1]) ascending (values distinct).
 tcrnet_status sort_rows(const int64_t* off, int32_t* cols, int64_t n, cudaStream_t s, int num_sms);

@@ -382,6 +382,9 @@ void add_triangle(std::vector<Item>& v, int64_t s, int64_t e, int W, int64_t& pa
 tcrnet_status tile_pass(const TileSide& rows, const TileSide& cols, bool sym, int threshold, bool write,
                         int32_t* count, const int64_t* off, int32_t* cursor, int32_t* cols_out,
                         int64_t* pairs, cudaStream_t s, int num_sms) {
+    if (threshold >= 2)
+        return dp_pass(rows, cols, sym, std::min(threshold, kMaxLen), write, count, off, cursor, cols_out, pairs, s,
+                       num_sms);
     std::vector<Item> items;
     int64_t np = 0;
     for (int L = 1; L <= kMaxLen; ++L) {

@@ -327,3 +327,45 @@ def test_query_without_index_rejects_deletion_search():
         with pytest.raises(tn.TcrnetError) as e:
             g.query_flat(rep.chars, rep.offsets, method="deletion")
         assert e.value.status == tn.ENOTSUP
+
+
+def _all_strings(alphabet, max_len):
+    import itertools
+
+    out = []
+    for L in range(1, max_len + 1):
+        out += ["".join(t) for t in itertools.product(alphabet, repeat=L)]
+    return out
+
+
+@pytest.mark.parametrize("threshold", [2, 3])
+def test_larger_threshold_exhaustive_tiny_alphabet(threshold):
+    rep = from_strings(_all_strings("AC", 6) + _all_strings("ACD", 3))
+    off, cols, deg, st = gpu_csr(rep, threshold, "auto")
+    assert st["method"] == tn.METHOD_TILE
+    ro, rc, _ = oracle_csr(rep, threshold)
+    assert_csr_equal(off, cols, ro, rc, f"tiny alphabet T={threshold}")
+
+
+@pytest.mark.parametrize("threshold", [2, 3, 6])
+def test_larger_threshold_generator_strings(threshold):
+    # the paper's analyses use l_max = 2 (assortativity), a sweep, and 6 (LCC drawings)
+    rep = generate_config1(3000, seed=60 + threshold)
+    off, cols, deg, _ = gpu_csr(rep, threshold, "tile")
+    ro, rc, _ = oracle_csr(rep, threshold)
+    assert_csr_equal(off, cols, ro, rc, f"generator T={threshold}")
+    check_invariants(off, cols, deg, rep.n)
+
+
+def test_larger_threshold_edge_strings_and_queries():
+    rep = from_strings(edge_strings())
+    off, cols, _, _ = gpu_csr(rep, 2, "tile")
+    ro, rc, _ = oracle_csr(rep, 2)
+    assert_csr_equal(off, cols, ro, rc, "edge strings T=2")
+    base = generate_config1(4000, seed=71)
+    qs = from_strings(base.strings()[:100] + ["CASSF", "A", "W" * 48] + [s[:-2] for s in base.strings()[100:150]])
+    with tn.tcrnet_build_flat(base.chars, base.offsets, 2) as g:
+        with g.query_flat(qs.chars, qs.offsets) as r:
+            qo, qc, _ = r.copy_csr()
+    ro, rc = oracle.neighbors(base.chars, base.offsets, qs.chars, qs.offsets, max_dist=2)
+    assert_csr_equal(qo, qc, ro, rc, "queries T=2")
