@@ -199,6 +199,24 @@ tcrnet_status tcrnet_insert_ex(tcrnet_handle h, const uint8_t *chars, const int6
 /* tcrnet_insert_flat for NUL-terminated host strings. */
 tcrnet_status tcrnet_insert(tcrnet_handle h, const char *const *seqs, int64_t m);
 
+/*
+ * Connected components of the network restricted to the nodes with keep[i] != 0
+ * (keep == NULL keeps every node): node removal of the robustness analysis
+ * (Methods "Computing LCC"; the caller draws which nodes are removed). labels
+ * (n int32, may be NULL) receives the smallest node id of each node's component,
+ * -1 for removed nodes; *n_components the number of components among kept
+ * nodes; *largest the size of the largest one (LCC). keep and labels live in
+ * memory space `mem`. TCRNET_ETIMEOUT if the bounded union retry loop ran out
+ * (not expected; the handle stays usable).
+ */
+tcrnet_status tcrnet_components(tcrnet_handle h, const uint8_t *keep, int32_t *labels, int32_t mem,
+                                int64_t *n_components, int64_t *largest);
+
+/* Average neighbour degree (Methods "Overview of network theory concepts",
+ * <d_nn>): knn[i] = (sum over neighbours j of d(j)) / d(i), 0 for isolated nodes;
+ * n doubles in memory space `mem`. */
+tcrnet_status tcrnet_neighbor_degree(tcrnet_handle h, double *knn, int32_t mem);
+
 /* Counters and phase times of the call that produced the handle. */
 tcrnet_status tcrnet_stats_get(tcrnet_handle h, tcrnet_stats *out);
 

@@ -97,6 +97,7 @@ SYMBOLS = [
     "tcrnet_csr_device", "tcrnet_query_flat", "tcrnet_query", "tcrnet_stats_get", "tcrnet_free",
     "tcrnet_strerror", "tcrnet_last_error_index", "tcrnet_version", "tcrnet_last_cuda_error",
     "tcrnet_degree_noalloc", "tcrnet_query_ex", "tcrnet_insert_flat", "tcrnet_insert_ex", "tcrnet_insert",
+    "tcrnet_components", "tcrnet_neighbor_degree",
 ]
 
 
@@ -129,6 +130,10 @@ def load_library(path: str = LIB_PATH):
         lib.tcrnet_csr_device.restype = ctypes.c_int
         lib.tcrnet_query_flat.argtypes = [H, vp, vp, i64, i32, HP]
         lib.tcrnet_query_flat.restype = ctypes.c_int
+        lib.tcrnet_components.argtypes = [H, vp, vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        lib.tcrnet_components.restype = ctypes.c_int
+        lib.tcrnet_neighbor_degree.argtypes = [H, vp, i32]
+        lib.tcrnet_neighbor_degree.restype = ctypes.c_int
         lib.tcrnet_insert_flat.argtypes = [H, vp, vp, i64, i32]
         lib.tcrnet_insert_flat.restype = ctypes.c_int
         lib.tcrnet_insert_ex.argtypes = [H, vp, vp, i64, i32, optp]
@@ -259,6 +264,28 @@ class Graph:
 
     def query(self, queries):
         return tcrnet_query(self, queries)
+
+    def components(self, keep=None):
+        """Connected components (host arrays): (labels int32 [n], n_components, largest).
+        keep: optional uint8 mask of the nodes that stay (node removal)."""
+        n, _, _ = self.info()
+        labels = np.empty(max(n, 1), dtype=np.int32)
+        kp = None
+        if keep is not None:
+            keep = np.ascontiguousarray(keep, dtype=np.uint8)
+            assert keep.shape[0] == n
+            kp = keep.ctypes.data
+        nc, lc = ctypes.c_int64(), ctypes.c_int64()
+        _check(load_library().tcrnet_components(self._h, kp, labels.ctypes.data, HOST, ctypes.byref(nc),
+                                                ctypes.byref(lc)), "tcrnet_components")
+        return labels[:n], nc.value, lc.value
+
+    def neighbor_degree(self):
+        """Average neighbour degree per node (host float64 array)."""
+        n, _, _ = self.info()
+        knn = np.empty(max(n, 1), dtype=np.float64)
+        _check(load_library().tcrnet_neighbor_degree(self._h, knn.ctypes.data, HOST), "tcrnet_neighbor_degree")
+        return knn[:n]
 
     def insert(self, seqs):
         """Append host strings as new nodes (tcrnet_insert)."""

@@ -1,0 +1,183 @@
+// Network analytics on the device CSR (the analyses of the paper's Results that
+// consume the network): connected components under node removal (Methods
+// "Computing LCC": the largest connected component, LCC(p) after removing a
+// fraction p of the nodes) and the average neighbour degree d_nn (Methods
+// "Overview of network theory concepts").
+//
+// Components: lock-free union-find over the undirected edges {i, j}, i < j,
+// both kept. A union links the larger root below the smaller one (compare-and-
+// swap on the root's parent, retried when another thread moved it), so every
+// parent pointer only decreases and points to a node of the same set; `find`
+// walks strictly decreasing ids (terminates) and halves the path as it goes.
+// Each final root is the smallest node id of its component, which makes the
+// labels deterministic. Component sizes by atomic counting; the number of
+// components and the largest size by a grid reduction.
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace tcr {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxLinkRetries = 1 << 20;
+
+__device__ __forceinline__ int32_t find_root(int32_t* parent, int32_t x) {
+    volatile int32_t* vp = parent;
+    int32_t p = vp[x];
+    while (p != x) {
+        const int32_t gp = vp[p];
+        if (gp != p) vp[x] = gp;  // path halving (benign: gp is an ancestor of x)
+        x = p;
+        p = gp;
+    }
+    return x;
+}
+
+__global__ void k_cc_init(const uint8_t* __restrict__ keep, int64_t n, int32_t* __restrict__ parent,
+                          int32_t* __restrict__ size) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    parent[i] = (keep == nullptr || keep[i]) ? (int32_t)i : -1;
+    size[i] = 0;
+}
+
+template <typename Off>
+__global__ void __launch_bounds__(kThreads)
+k_cc_link(const Off* __restrict__ off, const int32_t* __restrict__ cols, int64_t n, int32_t* parent,
+          int* __restrict__ err) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += stride) {
+        if (parent[i] < 0) continue;  // removed (set before this kernel; uniform per warp)
+        const int64_t b = off[i], e = off[i + 1];
+        for (int64_t k = b + lane; k < e; k += 32) {
+            const int32_t j = cols[k];
+            if (j <= i || ((volatile int32_t*)parent)[j] < 0) continue;
+            int32_t a = (int32_t)i, c = j;
+            int it = 0;
+            for (; it < kMaxLinkRetries; ++it) {
+                int32_t ra = find_root(parent, a), rc = find_root(parent, c);
+                if (ra == rc) break;
+                if (ra > rc) {
+                    const int32_t t = ra;
+                    ra = rc;
+                    rc = t;
+                }
+                if (atomicCAS(&parent[rc], rc, ra) == rc) break;
+                a = ra;
+                c = rc;
+            }
+            if (it == kMaxLinkRetries) atomicExch(err, 1);
+        }
+    }
+}
+
+__global__ void k_cc_label(int64_t n, int32_t* parent, int32_t* __restrict__ labels, int32_t* __restrict__ size) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (parent[i] < 0) {
+        labels[i] = -1;
+        return;
+    }
+    const int32_t r = find_root(parent, (int32_t)i);
+    labels[i] = r;
+    atomicAdd(&size[r], 1);
+}
+
+__global__ void k_cc_reduce(int64_t n, const int32_t* __restrict__ labels, const int32_t* __restrict__ size,
+                            unsigned long long* __restrict__ out /* [0] components, [1] largest */) {
+    unsigned long long roots = 0, largest = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (labels[i] == (int32_t)i) {
+            ++roots;
+            largest = largest > (unsigned long long)size[i] ? largest : (unsigned long long)size[i];
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        roots += __shfl_down_sync(kFull, roots, d);
+        const unsigned long long o = __shfl_down_sync(kFull, largest, d);
+        largest = largest > o ? largest : o;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&out[0], roots);
+        atomicMax(&out[1], largest);
+    }
+}
+
+template <typename Off>
+__global__ void __launch_bounds__(kThreads)
+k_neighbor_degree(const Off* __restrict__ off, const int32_t* __restrict__ cols, int64_t n,
+                  double* __restrict__ knn) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += stride) {
+        const int64_t b = off[i], e = off[i + 1];
+        long long s = 0;
+        for (int64_t k = b + lane; k < e; k += 32) {
+            const int32_t j = cols[k];
+            s += (long long)(off[j + 1] - off[j]);
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(kFull, s, d);
+        if (lane == 0) knn[i] = (e > b) ? (double)s / (double)(e - b) : 0.0;
+    }
+}
+
+inline unsigned blocks_for(int64_t n, int per_block, int num_sms) {
+    const int64_t b = ceil_div(n, per_block);
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms * 32));
+}
+
+}  // namespace
+
+tcrnet_status components(const void* off, bool off64, const int32_t* cols, int64_t n, const uint8_t* keep,
+                         int32_t* labels, int64_t* n_components, int64_t* largest, cudaStream_t s, int num_sms) {
+    *n_components = 0;
+    *largest = 0;
+    if (n == 0) return TCRNET_OK;
+    DevBuf parent, size, red;
+    TCR_CHECK(parent.alloc(sizeof(int32_t) * n, s));
+    TCR_CHECK(size.alloc(sizeof(int32_t) * n, s));
+    TCR_CHECK(red.alloc(sizeof(unsigned long long) * 2 + sizeof(int), s));
+    TCR_CUDA(cudaMemsetAsync(red.as<void>(), 0, sizeof(unsigned long long) * 2 + sizeof(int), s));
+    int* err = reinterpret_cast<int*>(red.as<unsigned long long>() + 2);
+    k_cc_init<<<(unsigned)ceil_div(n, kThreads), kThreads, 0, s>>>(keep, n, parent.as<int32_t>(), size.as<int32_t>());
+    TCR_LAUNCH_CHECK();
+    const unsigned wb = blocks_for(n, kWarps, num_sms);
+    if (off64)
+        k_cc_link<int64_t><<<wb, kThreads, 0, s>>>(static_cast<const int64_t*>(off), cols, n, parent.as<int32_t>(), err);
+    else
+        k_cc_link<int32_t><<<wb, kThreads, 0, s>>>(static_cast<const int32_t*>(off), cols, n, parent.as<int32_t>(), err);
+    TCR_LAUNCH_CHECK();
+    k_cc_label<<<(unsigned)ceil_div(n, kThreads), kThreads, 0, s>>>(n, parent.as<int32_t>(), labels, size.as<int32_t>());
+    TCR_LAUNCH_CHECK();
+    k_cc_reduce<<<blocks_for(n, kThreads, num_sms), kThreads, 0, s>>>(n, labels, size.as<int32_t>(),
+                                                                       red.as<unsigned long long>());
+    TCR_LAUNCH_CHECK();
+    unsigned long long h[2] = {0, 0};
+    int h_err = 0;
+    TCR_CUDA(cudaMemcpyAsync(h, red.as<void>(), sizeof(h), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaStreamSynchronize(s));
+    if (h_err) return TCRNET_ETIMEOUT;
+    *n_components = (int64_t)h[0];
+    *largest = (int64_t)h[1];
+    return TCRNET_OK;
+}
+
+tcrnet_status neighbor_degree(const void* off, bool off64, const int32_t* cols, int64_t n, double* knn,
+                              cudaStream_t s, int num_sms) {
+    if (n == 0) return TCRNET_OK;
+    const unsigned wb = blocks_for(n, kWarps, num_sms);
+    if (off64)
+        k_neighbor_degree<int64_t><<<wb, kThreads, 0, s>>>(static_cast<const int64_t*>(off), cols, n, knn);
+    else
+        k_neighbor_degree<int32_t><<<wb, kThreads, 0, s>>>(static_cast<const int32_t*>(off), cols, n, knn);
+    TCR_LAUNCH_CHECK();
+    return TCRNET_OK;
+}
+
+}  // namespace tcr

@@ -672,6 +672,61 @@ tcrnet_status tcrnet_insert(tcrnet_handle h, const char* const* seqs, int64_t m)
     return tcrnet_insert_ex(h, chars.data(), offs.data(), m, TCRNET_HOST, nullptr);
 }
 
+tcrnet_status tcrnet_components(tcrnet_handle h, const uint8_t* keep, int32_t* labels, int32_t mem,
+                                int64_t* n_components, int64_t* largest) {
+    if (!h || (mem != TCRNET_HOST && mem != TCRNET_DEVICE)) return TCRNET_EINVAL;
+    DeviceGuard dg;
+    TCR_CHECK(dg.set(h->device));
+    cudaStream_t s = h->stream;
+    const int64_t n = h->n;
+    int64_t nc = 0, lc = 0;
+    if (n > 0) {
+        ArenaLease lease(h->device, s);
+        DevBuf dkeep, dlab;
+        const uint8_t* k = keep;
+        int32_t* lab = labels;
+        if (mem == TCRNET_HOST) {
+            if (keep) {
+                TCR_CHECK(dkeep.alloc(n, s));
+                TCR_CUDA(cudaMemcpyAsync(dkeep.as<void>(), keep, n, cudaMemcpyHostToDevice, s));
+                k = dkeep.as<uint8_t>();
+            }
+            TCR_CHECK(dlab.alloc(sizeof(int32_t) * n, s));
+            lab = dlab.as<int32_t>();
+        } else if (!lab) {
+            TCR_CHECK(dlab.alloc(sizeof(int32_t) * n, s));
+            lab = dlab.as<int32_t>();
+        }
+        TCR_CHECK(components(h->d_offsets, h->offsets64 != 0, h->d_cols, n, k, lab, &nc, &lc, s, sm_count(h->device)));
+        if (mem == TCRNET_HOST && labels)
+            TCR_CUDA(cudaMemcpyAsync(labels, lab, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+        TCR_CUDA(cudaStreamSynchronize(s));
+    }
+    if (n_components) *n_components = nc;
+    if (largest) *largest = lc;
+    return TCRNET_OK;
+}
+
+tcrnet_status tcrnet_neighbor_degree(tcrnet_handle h, double* knn, int32_t mem) {
+    if (!h || !knn || (mem != TCRNET_HOST && mem != TCRNET_DEVICE)) return TCRNET_EINVAL;
+    DeviceGuard dg;
+    TCR_CHECK(dg.set(h->device));
+    cudaStream_t s = h->stream;
+    const int64_t n = h->n;
+    if (n == 0) return TCRNET_OK;
+    ArenaLease lease(h->device, s);
+    DevBuf dk;
+    double* out = knn;
+    if (mem == TCRNET_HOST) {
+        TCR_CHECK(dk.alloc(sizeof(double) * n, s));
+        out = dk.as<double>();
+    }
+    TCR_CHECK(neighbor_degree(h->d_offsets, h->offsets64 != 0, h->d_cols, n, out, s, sm_count(h->device)));
+    if (mem == TCRNET_HOST) TCR_CUDA(cudaMemcpyAsync(knn, out, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaStreamSynchronize(s));
+    return TCRNET_OK;
+}
+
 tcrnet_status tcrnet_stats_get(tcrnet_handle h, tcrnet_stats* out) {
     if (!h || !out) return TCRNET_EINVAL;
     *out = h->stats;

@@ -57,6 +57,15 @@ tcrnet_status dp_pass(const TileSide& rows, const TileSide& cols, bool sym, int 
                       int32_t* count, const int64_t* off, int32_t* cursor, int32_t* cols_out, int64_t* pairs,
                       cudaStream_t s, int num_sms);
 
+// ---- analytics.cu ---------------------------------------------------------
+// Connected components of the CSR restricted to keep[i] != 0 (keep may be null):
+// labels[i] = smallest node id of the component, -1 for removed nodes.
+tcrnet_status components(const void* off, bool off64, const int32_t* cols, int64_t n, const uint8_t* keep,
+                         int32_t* labels, int64_t* n_components, int64_t* largest, cudaStream_t s, int num_sms);
+// knn[i] = mean degree of i's neighbours (0 for isolated nodes).
+tcrnet_status neighbor_degree(const void* off, bool off64, const int32_t* cols, int64_t n, double* knn,
+                              cudaStream_t s, int num_sms);
+
 // ---- rowsort.cu -----------------------------------------------------------
 // Sort every row segment cols[off[i] .. off[i+1]) ascending (values distinct).
 tcrnet_status sort_rows(const int64_t* off, int32_t* cols, int64_t n, cudaStream_t s, int num_sms);
