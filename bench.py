@@ -328,6 +328,18 @@ def serve_leg(args, tn, torch, stream):
     }
 
 
+def _components_device(g, keep_dev, tn):
+    """tcrnet_components with a device-resident removal mask; labels stay on the device."""
+    import ctypes
+
+    nc, lc = ctypes.c_int64(), ctypes.c_int64()
+    st = tn.load_library().tcrnet_components(g.handle, keep_dev.data_ptr(), None, tn.DEVICE, ctypes.byref(nc),
+                                             ctypes.byref(lc))
+    if st != tn.OK:
+        raise tn.TcrnetError(st, "tcrnet_components")
+    return None, nc.value, lc.value
+
+
 def run_ours(args):
     import torch
 
@@ -503,6 +515,47 @@ def run_ours(args):
         line["e2e"] = {"value": pairs_per_build / (e_ms / 1e3), "unit": UNIT, "ms_per_step": e_ms,
                        "h2d_bytes_per_step": int(rep.chars.nbytes + rep.offsets.nbytes),
                        "d2h_bytes_per_step": int(4 * (n + 1) + 4 * nnz + 4 * n)}
+        # --- analytics on the N = 8e5 network: LCC under random node removal
+        #     (normalisations of Methods "Computing LCC"), average neighbour degree
+        with build() as g:
+            ps = [0.0, 0.01, 0.1, 0.3, 0.49, 0.7, 0.89, 0.95, 0.98]
+            rng = np.random.default_rng(2024)
+            curve, t_cc = [], []
+            lcc0 = None
+            for p in ps:
+                keep = (rng.random(n) >= p).astype(np.uint8)
+                kt = torch.from_numpy(keep).to(dev)
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                _, nc, lcc = _components_device(g, kt, tn)
+                t_cc.append(1e3 * (time.perf_counter() - t))
+                lcc0 = lcc if p == 0.0 else lcc0
+                norm1 = lcc / ((1 - p) * n)
+                curve.append({"p": p, "lcc": lcc, "components": nc, "lcc_norm1": norm1,
+                              "lcc_norm2": norm1 / (lcc0 / n)})
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            knn = g.neighbor_degree()
+            t_knn = 1e3 * (time.perf_counter() - t)
+        line["analytics"] = {"lcc_under_removal": curve, "components_ms_median": statistics.median(t_cc),
+                             "neighbor_degree_ms": t_knn, "mean_neighbor_degree": float(knn.mean())}
+        # --- l_max = 2 (bit-parallel distance): the paper's assortativity setting of
+        #     4 x 8,000 sequences, and N = 1e5
+        from synthgen import generate_config1
+
+        lm2 = {}
+        for n2 in (32_000, 100_000):
+            r2 = generate_config1(n2, seed=7)
+            c2 = torch.from_numpy(r2.chars).to(dev)
+            o2 = torch.from_numpy(r2.offsets).to(dev)
+            tn.tcrnet_build_flat(c2, o2, 2, stream=stream).free()
+            g2 = tn.tcrnet_build_flat(c2, o2, 2, stream=stream, profile=True)
+            st2 = g2.stats()
+            g2.free()
+            lm2[str(n2)] = {"build_ms": st2["ms_total"], "count_pass_ms": st2["ms_count"],
+                            "candidate_pairs": st2["candidate_pairs"], "nnz": st2["nnz"],
+                            "candidate_pairs_per_s": st2["candidate_pairs"] / (st2["ms_count"] / 1e3)}
+        line["lmax2"] = lm2
         # --- serving: resident repertoire, Poisson queries and inserts
         if args.serve_seconds > 0:
             line["serving"] = serve_leg(args, tn, torch, stream)
