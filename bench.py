@@ -68,6 +68,7 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="0 skips the serving leg")
     ap.add_argument("--serve-n", type=int, default=2_000_000)
+    ap.add_argument("--batched-reps", type=int, default=256, help="0 skips the batched leg")
     ap.add_argument("--no-extras", action="store_true", help="skip tile/query/e2e/cpu legs")
     return ap.parse_args()
 
@@ -328,6 +329,67 @@ def serve_leg(args, tn, torch, stream):
     }
 
 
+def batched_leg(args, tn, torch, stream, flush, reps_steps=3):
+    """Repertoires with log-uniform sizes in [1e3, 2e5]: one batched build of all of
+    them against one plain build per repertoire (device inputs, CUDA events)."""
+    from synthgen import generate_batched
+
+    reps = generate_batched(args.batched_reps, seed=0)
+    sizes = np.array([r.n for r in reps], dtype=np.int64)
+    bounds = np.zeros(len(reps) + 1, dtype=np.int64)
+    np.cumsum(sizes, out=bounds[1:])
+    chars = np.concatenate([r.chars for r in reps])
+    lens = np.concatenate([np.diff(r.offsets) for r in reps])
+    offs = np.zeros(lens.shape[0] + 1, dtype=np.int64)
+    np.cumsum(lens, out=offs[1:])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    dc, do = torch.from_numpy(chars).to(dev), torch.from_numpy(offs).to(dev)
+    per = [(torch.from_numpy(r.chars).to(dev), torch.from_numpy(r.offsets).to(dev)) for r in reps]
+    pairs = float((sizes * (sizes - 1) // 2).sum())
+
+    def timed(fn):
+        out = []
+        for k in range(reps_steps + 1):
+            flush.fill_(3)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            extra = fn()
+            b.record(stream)
+            b.synchronize()
+            if k > 0:
+                out.append((a.elapsed_time(b), extra))
+        return out
+
+    def batched():
+        g = tn.tcrnet_build_batched(dc, do, bounds, 1, stream=stream, profile=False)
+        st = g.stats()
+        g.free()
+        return st
+
+    def sequential():
+        nnz, launches = 0, 0
+        for c, o in per:
+            g = tn.tcrnet_build_flat(c, o, 1, stream=stream)
+            st = g.stats()
+            nnz += st["nnz"]
+            launches += st["kernel_launches"]
+            g.free()
+        return {"nnz": nnz, "kernel_launches": launches}
+
+    tb = timed(batched)
+    ts = timed(sequential)
+    mb = statistics.mean(t for t, _ in tb)
+    ms = statistics.mean(t for t, _ in ts)
+    assert tb[0][1]["nnz"] == ts[0][1]["nnz"]
+    return {"repertoires": len(reps), "strings": int(sizes.sum()), "size_range": "log-uniform [1e3, 2e5]",
+            "pairs": pairs, "nnz": int(tb[0][1]["nnz"]),
+            "batched_ms": mb, "batched_pairs_per_s": pairs / (mb / 1e3),
+            "batched_kernel_launches": int(tb[0][1]["kernel_launches"]),
+            "sequential_ms": ms, "sequential_pairs_per_s": pairs / (ms / 1e3),
+            "sequential_kernel_launches": int(ts[0][1]["kernel_launches"]),
+            "speedup": ms / mb, "timing": f"CUDA events, mean of {reps_steps} after 1 warm-up, L2 flushed"}
+
+
 def _components_device(g, keep_dev, tn):
     """tcrnet_components with a device-resident removal mask; labels stay on the device."""
     import ctypes
@@ -556,6 +618,9 @@ def run_ours(args):
                             "candidate_pairs": st2["candidate_pairs"], "nnz": st2["nnz"],
                             "candidate_pairs_per_s": st2["candidate_pairs"] / (st2["ms_count"] / 1e3)}
         line["lmax2"] = lm2
+        # --- batched: uneven repertoires in one pass vs one plain build each
+        if args.batched_reps > 0:
+            line["batched"] = batched_leg(args, tn, torch, stream, flush)
         # --- serving: resident repertoire, Poisson queries and inserts
         if args.serve_seconds > 0:
             line["serving"] = serve_leg(args, tn, torch, stream)

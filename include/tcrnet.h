@@ -137,6 +137,22 @@ tcrnet_status tcrnet_build_flat(const uint8_t *chars, const int64_t *offsets, in
                                 int32_t mem, int32_t threshold, const tcrnet_options *opt,
                                 tcrnet_handle *out);
 
+/*
+ * Batched build: the networks of nrep independent repertoires in one pass.
+ * The n strings (flat layout in memory space `mem`) are the repertoires back to
+ * back; repertoire r is strings rep_offsets[r] .. rep_offsets[r+1]
+ * (rep_offsets: nrep + 1 int64 in HOST memory, rep_offsets[0] = 0,
+ * rep_offsets[nrep] = n, non-decreasing, nrep <= 65536). The handle holds one
+ * block-diagonal CSR: row i of repertoire r lists the global ids of i's
+ * neighbours within r, so rows rep_offsets[r] .. rep_offsets[r+1] minus
+ * rep_offsets[r] are exactly the network tcrnet_build_flat would return for
+ * that repertoire alone. l_max <= 1 (deletion join; ENOTSUP otherwise or with
+ * TCRNET_METHOD_TILE). Batched handles answer no queries or inserts (ESTATE).
+ */
+tcrnet_status tcrnet_build_batched(const uint8_t *chars, const int64_t *offsets, int64_t n,
+                                   const int64_t *rep_offsets, int64_t nrep, int32_t mem, int32_t threshold,
+                                   const tcrnet_options *opt, tcrnet_handle *out);
+
 /* Size of a handle's CSR: rows, directed entries (nnz = sum of degrees) and
  * whether exported offsets are int64 (nnz >= 2^31 or force_offsets64). Any
  * pointer may be NULL. */

@@ -97,7 +97,7 @@ SYMBOLS = [
     "tcrnet_csr_device", "tcrnet_query_flat", "tcrnet_query", "tcrnet_stats_get", "tcrnet_free",
     "tcrnet_strerror", "tcrnet_last_error_index", "tcrnet_version", "tcrnet_last_cuda_error",
     "tcrnet_degree_noalloc", "tcrnet_query_ex", "tcrnet_insert_flat", "tcrnet_insert_ex", "tcrnet_insert",
-    "tcrnet_components", "tcrnet_neighbor_degree",
+    "tcrnet_components", "tcrnet_neighbor_degree", "tcrnet_build_batched",
 ]
 
 
@@ -130,6 +130,8 @@ def load_library(path: str = LIB_PATH):
         lib.tcrnet_csr_device.restype = ctypes.c_int
         lib.tcrnet_query_flat.argtypes = [H, vp, vp, i64, i32, HP]
         lib.tcrnet_query_flat.restype = ctypes.c_int
+        lib.tcrnet_build_batched.argtypes = [vp, vp, i64, vp, i64, i32, i32, optp, HP]
+        lib.tcrnet_build_batched.restype = ctypes.c_int
         lib.tcrnet_components.argtypes = [H, vp, vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]
         lib.tcrnet_components.restype = ctypes.c_int
         lib.tcrnet_neighbor_degree.argtypes = [H, vp, i32]
@@ -357,6 +359,32 @@ def tcrnet_build_flat(chars, offsets, threshold: int = 1, method="auto", device=
     del keep
     _check(st, "tcrnet_build_flat")
     return Graph(h.value)
+
+
+def tcrnet_build_batched(chars, offsets, rep_offsets, threshold: int = 1, stream=None, profile=False) -> Graph:
+    """Block-diagonal network of several repertoires in one pass (see include/tcrnet.h).
+    rep_offsets: host int64 array of nrep + 1 string-index bounds."""
+    lib = load_library()
+    cp, op, n, mem, keep = _flat_args(chars, offsets)
+    ro = np.ascontiguousarray(rep_offsets, dtype=np.int64)
+    opt = make_options("deletion", None, stream, profile)
+    h = ctypes.c_void_p()
+    st = lib.tcrnet_build_batched(cp, op, n, ro.ctypes.data, ro.shape[0] - 1, mem, int(threshold),
+                                  ctypes.byref(opt), ctypes.byref(h))
+    del keep
+    _check(st, "tcrnet_build_batched")
+    return Graph(h.value)
+
+
+def split_block_diagonal(offsets, cols, rep_offsets):
+    """Per-repertoire (offsets, cols) of a batched build's CSR, ids local to the repertoire."""
+    off = np.asarray(offsets, dtype=np.int64)
+    out = []
+    for r in range(len(rep_offsets) - 1):
+        a, b = int(rep_offsets[r]), int(rep_offsets[r + 1])
+        o = off[a:b + 1]
+        out.append((o - o[0], cols[o[0]:o[-1]] - a))
+    return out
 
 
 def tcrnet_query(graph: Graph, queries) -> Graph:

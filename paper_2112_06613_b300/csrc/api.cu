@@ -19,6 +19,7 @@ struct tcrnet_graph {
     int device = 0;
     cudaStream_t stream = 0;
     bool query_result = false;
+    bool batched = false;  // block-diagonal network of several repertoires
     int32_t threshold = 1;
     int64_t n = 0;
     int64_t nnz = 0;
@@ -329,7 +330,7 @@ tcrnet_status flatten(const char* const* seqs, int64_t n, std::vector<uint8_t>& 
 // the options select: CSR, degree, resident repertoire and, for the deletion
 // method, the query index.
 tcrnet_status build_from_packed(tcrnet_graph* h, Packed& pk, int64_t n, int32_t T, const tcrnet_options& opt,
-                                Phases& ph, cudaStream_t s, int sms) {
+                                Phases& ph, cudaStream_t s, int sms, bool keep_index = true) {
     tcrnet_status st = TCRNET_OK;
     int method = opt.method;
     if (method == TCRNET_METHOD_AUTO)
@@ -349,7 +350,7 @@ tcrnet_status build_from_packed(tcrnet_graph* h, Packed& pk, int64_t n, int32_t 
         if (st != TCRNET_OK) return st;
     } else {
         DeletionResult dr;
-        st = deletion_build(pk, T, dr, s, sms, opt.profile != 0, opt.partition_cap, /*keep_index=*/true);
+        st = deletion_build(pk, T, dr, s, sms, opt.profile != 0, opt.partition_cap, keep_index);
         if (st != TCRNET_OK) return st;
         h->stats.n_unique = dr.n_unique;
         h->stats.n_records = dr.n_records;
@@ -374,7 +375,8 @@ tcrnet_status build_from_packed(tcrnet_graph* h, Packed& pk, int64_t n, int32_t 
 }
 
 tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n, int mem, int32_t T,
-                         const tcrnet_options* opt_in, tcrnet_handle* out) {
+                         const tcrnet_options* opt_in, tcrnet_handle* out, const int64_t* rep_off = nullptr,
+                         int64_t nrep = 0) {
     if (!out) return TCRNET_EINVAL;
     *out = nullptr;
     t_last_bad = -1;
@@ -385,6 +387,14 @@ tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n
     if (T < 0) return TCRNET_EINVAL;
     if (opt.method < TCRNET_METHOD_AUTO || opt.method > TCRNET_METHOD_DELETION) return TCRNET_EINVAL;
     if (T > 1 && opt.method == TCRNET_METHOD_DELETION) return TCRNET_ENOTSUP;  // deletion join: l_max <= 1
+    if (rep_off) {
+        // batched: one deletion-method pass over all repertoires
+        if (T > 1 || opt.method == TCRNET_METHOD_TILE) return TCRNET_ENOTSUP;
+        if (nrep < 1 || nrep > 65536 || rep_off[0] != 0 || rep_off[nrep] != n) return TCRNET_EINVAL;
+        for (int64_t r = 0; r < nrep; ++r)
+            if (rep_off[r + 1] < rep_off[r]) return TCRNET_EINVAL;
+        opt.method = TCRNET_METHOD_DELETION;
+    }
     DeviceGuard dg;
     TCR_CHECK(dg.set(opt.device));
     int dev = 0;
@@ -426,8 +436,13 @@ tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n
             return fail(st);
         }
     }
+    if (rep_off && n > 0) {
+        st = tag_repertoires(pk.canon_in.as<Canon>(), n, rep_off, nrep, s);
+        if (st != TCRNET_OK) return fail(st);
+        h->batched = true;
+    }
     const int p2 = ph.mark();
-    st = build_from_packed(h, pk, n, T, opt, ph, s, sms);
+    st = build_from_packed(h, pk, n, T, opt, ph, s, sms, /*keep_index=*/rep_off == nullptr);
     if (st != TCRNET_OK) return fail(st);
     const int p3 = ph.mark();
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(TCRNET_EDEVICE);
@@ -457,6 +472,13 @@ void tcrnet_options_init(tcrnet_options* opt) {
 tcrnet_status tcrnet_build_flat(const uint8_t* chars, const int64_t* offsets, int64_t n, int32_t mem,
                                 int32_t threshold, const tcrnet_options* opt, tcrnet_handle* out) {
     return build_impl(chars, offsets, n, mem, threshold, opt, out);
+}
+
+tcrnet_status tcrnet_build_batched(const uint8_t* chars, const int64_t* offsets, int64_t n,
+                                   const int64_t* rep_offsets, int64_t nrep, int32_t mem, int32_t threshold,
+                                   const tcrnet_options* opt, tcrnet_handle* out) {
+    if (!rep_offsets) return TCRNET_EINVAL;
+    return build_impl(chars, offsets, n, mem, threshold, opt, out, rep_offsets, nrep);
 }
 
 tcrnet_status tcrnet_build(const char* const* seqs, int64_t n, int32_t threshold, const tcrnet_options* opt,
@@ -507,7 +529,7 @@ tcrnet_status tcrnet_query_ex(tcrnet_handle h, const uint8_t* chars, const int64
     *out = nullptr;
     t_last_bad = -1;
     if (!h || m < 0 || m > 0x7fffffffLL) return TCRNET_EINVAL;
-    if (h->query_result) return TCRNET_ESTATE;
+    if (h->query_result || h->batched) return TCRNET_ESTATE;
     int method = opt ? opt->method : TCRNET_METHOD_AUTO;
     if (method < TCRNET_METHOD_AUTO || method > TCRNET_METHOD_DELETION) return TCRNET_EINVAL;
     if (method == TCRNET_METHOD_AUTO) method = h->ix.valid() ? TCRNET_METHOD_DELETION : TCRNET_METHOD_TILE;
@@ -593,7 +615,7 @@ tcrnet_status tcrnet_insert_ex(tcrnet_handle h, const uint8_t* chars, const int6
                                const tcrnet_options* opt_in) {
     t_last_bad = -1;
     if (!h || m < 0) return TCRNET_EINVAL;
-    if (h->query_result) return TCRNET_ESTATE;
+    if (h->query_result || h->batched) return TCRNET_ESTATE;
     if (m == 0) return TCRNET_OK;
     const int64_t n_old = h->n;
     const int64_t N = n_old + m;

@@ -27,6 +27,11 @@ struct __align__(16) Canon {
     uint64_t w[kCanonWords];
 };
 
+// Bits 60..63 of the four words hold no code. A batched build stores the
+// repertoire number there (16 bits, nibble k in word k), so strings of
+// different repertoires never compare equal and never hash alike on purpose.
+constexpr uint64_t kTagBits = 0xF000000000000000ULL;
+
 // ASCII -> code (0 = not in the alphabet).
 __host__ __device__ inline uint32_t aa_code(uint32_t c) {
     switch (c) {

@@ -78,9 +78,16 @@ __device__ __forceinline__ uint64_t fmix64(uint64_t x) {
 // Content hash: odd-multiplier combination of the four words, then one
 // finaliser. Only the partition choice and the in-partition order depend on
 // it; equal hashes are always confirmed by comparing contents.
+// The repertoire tag (top nibble of each word) enters through its own term:
+// in the word combination a top-nibble difference only reaches bits 60..63 of
+// x, so strings equal up to their tag would collide for 1 in 16 tag pairs.
+// The gathered 16-bit tag times an odd constant keeps its lowest set bit below
+// bit 16, so a pure tag difference can never cancel.
 __device__ __forceinline__ uint64_t hash_canon(const Canon& c) {
+    const uint64_t tag = (c.w[0] >> 60) | ((c.w[1] >> 56) & 0xF0ull) | ((c.w[2] >> 52) & 0xF00ull) |
+                         ((c.w[3] >> 48) & 0xF000ull);
     const uint64_t x = c.w[0] + 0x9e3779b97f4a7c15ULL * c.w[1] + 0xc2b2ae3d27d4eb4fULL * c.w[2] +
-                       0x165667b19e3779f9ULL * c.w[3];
+                       0x165667b19e3779f9ULL * c.w[3] + 0xd6e8feb86659fd93ULL * tag;
     return fmix64(x ^ 0x243f6a8885a308d3ULL);
 }
 
@@ -96,16 +103,18 @@ __device__ __forceinline__ uint32_t code_at(const Canon& c, int k) {
     return (uint32_t)(word_at(c, k / kCodesPerWord) >> (5 * (k % kCodesPerWord))) & 31u;
 }
 
-// The string with position p removed (later positions move down by one).
+// The string with position p removed (later positions move down by one); the
+// repertoire tag bits stay where they are.
 __device__ __forceinline__ Canon delete_at(const Canon& c, int p) {
     const int wp = p / kCodesPerWord;
     const uint64_t low = (1ull << (5 * (p % kCodesPerWord))) - 1ull;
     Canon o;
 #pragma unroll
     for (int w = 0; w < kCanonWords; ++w) {
+        const uint64_t cw = c.w[w] & ~kTagBits;
         const uint64_t next = (w + 1 < kCanonWords) ? (c.w[w + 1] & 31ull) : 0ull;
-        const uint64_t down = (c.w[w] >> 5) | (next << 55);
-        o.w[w] = w < wp ? c.w[w] : (w > wp ? down : ((c.w[w] & low) | (down & ~low)));
+        const uint64_t down = (cw >> 5) | (next << 55);
+        o.w[w] = (w < wp ? cw : (w > wp ? down : ((cw & low) | (down & ~low)))) | (c.w[w] & kTagBits);
     }
     return o;
 }

@@ -29,6 +29,9 @@ struct Packed {
 tcrnet_status pack_strings(const uint8_t* d_chars, const int64_t* d_offsets, int64_t n, Packed& out,
                            int64_t* bad_index, cudaStream_t s);
 
+// Write repertoire numbers into the spare bits of input-order canon
+// (repertoire r = strings rep_off[r] .. rep_off[r+1]).
+tcrnet_status tag_repertoires(Canon* canon, int64_t n, const int64_t* rep_off_host, int64_t nrep, cudaStream_t s);
 // Bucket already encoded strings (out.canon_in, out.lens, out.n set).
 tcrnet_status bucket_strings(Packed& out, cudaStream_t s);
 // Inverse of the bucketing: input-order canon and lengths from bucket order.

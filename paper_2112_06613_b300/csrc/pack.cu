@@ -91,6 +91,23 @@ k_bucket_scatter(const Canon* __restrict__ canon_in, const uint8_t* __restrict__
     }
 }
 
+// Repertoire tags of a batched build: string i of repertoire r gets r in the
+// spare bits (nibble k of r in bits 60..63 of word k).
+__global__ void k_tag(Canon* __restrict__ canon, int64_t n, const int64_t* __restrict__ rep_off, int64_t nrep) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t lo = 0, hi = nrep;  // largest r with rep_off[r] <= i
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (rep_off[mid] <= i) lo = mid; else hi = mid;
+    }
+    const uint64_t r = (uint64_t)lo;
+    Canon c = load_canon(canon + i);
+#pragma unroll
+    for (int k = 0; k < kCanonWords; ++k) c.w[k] = (c.w[k] & ~kTagBits) | (((r >> (4 * k)) & 0xFull) << 60);
+    store_canon(canon + i, c);
+}
+
 // Length counts per block of already encoded strings (lens).
 __global__ void __launch_bounds__(kPackThreads)
 k_count_lengths(const uint8_t* __restrict__ lens, int64_t n, int32_t* __restrict__ blockcnt, int nblocks) {
@@ -121,6 +138,17 @@ __global__ void k_bucket_bounds(const int64_t* __restrict__ blockoff, int nblock
 }
 
 }  // namespace
+
+tcrnet_status tag_repertoires(Canon* canon, int64_t n, const int64_t* rep_off_host, int64_t nrep, cudaStream_t s) {
+    if (n == 0) return TCRNET_OK;
+    DevBuf d;
+    TCR_CHECK(d.alloc(sizeof(int64_t) * (nrep + 1), s));
+    TCR_CUDA(cudaMemcpyAsync(d.as<void>(), rep_off_host, sizeof(int64_t) * (nrep + 1), cudaMemcpyHostToDevice, s));
+    k_tag<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(canon, n, d.as<int64_t>(), nrep);
+    TCR_LAUNCH_CHECK();
+    TCR_CUDA(cudaStreamSynchronize(s));  // rep_off_host may go away
+    return TCRNET_OK;
+}
 
 tcrnet_status bucket_strings(Packed& out, cudaStream_t s) {
     const int64_t n = out.n;

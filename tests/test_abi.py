@@ -4,6 +4,7 @@ declares; argument checks that precede any device work answer on the CPU."""
 import ctypes
 import re
 
+import numpy as np
 import pytest
 
 import paper_2112_06613_b300 as tn
@@ -62,3 +63,36 @@ def test_bad_method_rejected():
     with pytest.raises(tn.TcrnetError) as e:
         tn.tcrnet_build(["CASSF"], method=7)
     assert e.value.status == tn.EINVAL
+
+
+@pytest.mark.parametrize("rep_offsets,threshold,status", [
+    ([0, 1], 1, tn.EINVAL),          # does not end at n
+    ([1, 2], 1, tn.EINVAL),          # does not start at 0
+    ([0, 2, 1, 2], 1, tn.EINVAL),    # decreasing
+    ([0, 2], 2, tn.ENOTSUP),         # batched builds use the l_max <= 1 deletion join
+    ([0], 1, tn.EINVAL),             # no repertoire
+])
+def test_batched_bounds_rejected_before_device_work(rep_offsets, threshold, status):
+    chars = np.frombuffer(b"CASSFCASSG", dtype=np.uint8)
+    offsets = np.array([0, 5, 10], dtype=np.int64)
+    with pytest.raises(tn.TcrnetError) as e:
+        tn.tcrnet_build_batched(chars, offsets, np.array(rep_offsets, dtype=np.int64), threshold=threshold)
+    assert e.value.status == status
+
+
+def test_batched_repertoire_limit_and_tile_method_rejected():
+    lib = tn.load_library()
+    chars = np.frombuffer(b"CASSF", dtype=np.uint8)
+    offsets = np.array([0, 5], dtype=np.int64)
+    too_many = np.zeros(65538, dtype=np.int64)
+    too_many[-1] = 1
+    h = ctypes.c_void_p()
+    assert lib.tcrnet_build_batched(chars.ctypes.data, offsets.ctypes.data, 1, too_many.ctypes.data, 65537,
+                                    tn.HOST, 1, None, ctypes.byref(h)) == tn.EINVAL
+    ro = np.array([0, 1], dtype=np.int64)
+    opt = tn.make_options("tile")
+    assert lib.tcrnet_build_batched(chars.ctypes.data, offsets.ctypes.data, 1, ro.ctypes.data, 1,
+                                    tn.HOST, 1, ctypes.byref(opt), ctypes.byref(h)) == tn.ENOTSUP
+    assert lib.tcrnet_build_batched(chars.ctypes.data, offsets.ctypes.data, 1, None, 1,
+                                    tn.HOST, 1, None, ctypes.byref(h)) == tn.EINVAL
+    assert h.value is None
