@@ -54,6 +54,9 @@ SMS = 148
 INT_LANES_PER_SM = 128
 
 
+LEGS = ("tile", "query", "e2e", "analytics", "lmax2", "batched", "serving", "cpu")
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -69,7 +72,9 @@ def parse_args():
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="0 skips the serving leg")
     ap.add_argument("--serve-n", type=int, default=2_000_000)
     ap.add_argument("--batched-reps", type=int, default=256, help="0 skips the batched leg")
-    ap.add_argument("--no-extras", action="store_true", help="skip tile/query/e2e/cpu legs")
+    ap.add_argument("--no-extras", action="store_true", help="skip every leg after the timed step")
+    ap.add_argument("--legs", default=",".join(LEGS),
+                    help="comma list of the legs run after the timed step (default: all)")
     return ap.parse_args()
 
 
@@ -503,133 +508,142 @@ def run_ours(args):
         "gpu_launches": launches, "clocks": clocks,
     }
 
+    legs = set(args.legs.split(",")) - {""}
     if rank == 0 and not args.no_extras:
-        # --- tile kernel: candidate pair tests per second vs the integer ALU roofline
-        lens = rep.lengths()
-        ops, pairs = tile_ops_per_pair(lens)
-        tstats = []
-        build(method="tile").free()
-        for _ in range(args.tile_steps):
-            flush.fill_(1)
-            g = build(method="tile")
-            tstats.append(g.stats())
-            g.free()
-        cnt_ms = statistics.mean(s["ms_count"] for s in tstats)
-        tot_ms = statistics.mean(s["ms_total"] for s in tstats)
-        cand = tstats[0]["candidate_pairs"]
-        clk = (clocks or {}).get("sm_mhz") or sm_max_nominal
-        peak_ops = SMS * INT_LANES_PER_SM * sm_max_nominal * 1e6
-        peak_ops_clk = SMS * INT_LANES_PER_SM * clk * 1e6
-        ach_ops = ops / (cnt_ms / 1e3)
-        line["tile"] = {
-            "candidate_pairs": cand, "count_pass_ms": cnt_ms, "build_ms": tot_ms,
-            "candidate_pairs_per_s": cand / (cnt_ms / 1e3),
-            "all_pairs_per_s_build": pairs_per_build / (tot_ms / 1e3),
-            "roofline": {"bound": "alu", "achieved": ach_ops / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-                         "frac": ach_ops / peak_ops, "frac_at_sampled_clock": ach_ops / peak_ops_clk,
-                         "ops_per_launch": ops, "peak_basis": f"{SMS} SMs x {INT_LANES_PER_SM} int32 issue lanes x "
-                                                               f"{sm_max_nominal:.0f} MHz (issue ceiling)"},
-        }
-        # --- queries against the resident repertoire (host in, host out)
-        from synthgen import generate_config2
+        if "tile" in legs:
+            # --- tile kernel: candidate pair tests per second vs the integer ALU roofline
+            lens = rep.lengths()
+            ops, pairs = tile_ops_per_pair(lens)
+            tstats = []
+            build(method="tile").free()
+            for _ in range(args.tile_steps):
+                flush.fill_(1)
+                g = build(method="tile")
+                tstats.append(g.stats())
+                g.free()
+            cnt_ms = statistics.mean(s["ms_count"] for s in tstats)
+            tot_ms = statistics.mean(s["ms_total"] for s in tstats)
+            cand = tstats[0]["candidate_pairs"]
+            clk = (clocks or {}).get("sm_mhz") or sm_max_nominal
+            peak_ops = SMS * INT_LANES_PER_SM * sm_max_nominal * 1e6
+            peak_ops_clk = SMS * INT_LANES_PER_SM * clk * 1e6
+            ach_ops = ops / (cnt_ms / 1e3)
+            line["tile"] = {
+                "candidate_pairs": cand, "count_pass_ms": cnt_ms, "build_ms": tot_ms,
+                "candidate_pairs_per_s": cand / (cnt_ms / 1e3),
+                "all_pairs_per_s_build": pairs_per_build / (tot_ms / 1e3),
+                "roofline": {"bound": "alu", "achieved": ach_ops / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+                             "frac": ach_ops / peak_ops, "frac_at_sampled_clock": ach_ops / peak_ops_clk,
+                             "ops_per_launch": ops, "peak_basis": f"{SMS} SMs x {INT_LANES_PER_SM} int32 issue lanes x "
+                                                                   f"{sm_max_nominal:.0f} MHz (issue ceiling)"},
+            }
+        if "query" in legs:
+            # --- queries against the resident repertoire (host in, host out)
+            from synthgen import generate_config2
 
-        qsrc = generate_config2(200_000, seed=1000 + rank)
-        qstr_off = qsrc.offsets
-        rng = np.random.default_rng(7)
-        resident = build(profile=False)
-        lat, qn = [], []
-        for b in range(args.query_batches + 2):
-            m = int(round(math.exp(rng.uniform(0, math.log(50_000)))))
-            start = int(rng.integers(0, qsrc.n - m))
-            qo = (qstr_off[start:start + m + 1] - qstr_off[start]).astype(np.int64)
-            qc = qsrc.chars[qstr_off[start]:qstr_off[start + m]]
-            t = time.perf_counter()
-            r = resident.query_flat(qc, qo)
-            r.copy_csr()
-            dt = time.perf_counter() - t
-            r.free()
-            if b >= 2:
-                lat.append(dt * 1e3)
-                qn.append(m)
-        resident.free()
-        line["query"] = {"batches": len(lat), "batch_size": "log-uniform 1..50000", "p50_ms": float(np.percentile(lat, 50)),
-                         "p99_ms": float(np.percentile(lat, 99)), "queries_per_s": sum(qn) / (sum(lat) / 1e3),
-                         "method": "deletion index of the resident build (probe of the query strings own records)"}
-        # --- end to end: pinned host inputs in, CSR back in pinned host memory
-        hc = torch.from_numpy(rep.chars).pin_memory()
-        ho = torch.from_numpy(rep.offsets).pin_memory()
-        off_h = torch.empty(n + 1, dtype=torch.int32).pin_memory()
-        cols_h = torch.empty(max(nnz, 1), dtype=torch.int32).pin_memory()
-        deg_h = torch.empty(n, dtype=torch.int32).pin_memory()
-        e2e_ms = []
-        for k in range(args.e2e_steps + 2):
-            flush.fill_(2)
-            torch.cuda.synchronize()
-            t = time.perf_counter()
-            g = tn.tcrnet_build_flat(hc, ho, 1, method=args.method, stream=stream)
-            g.copy_csr(out=(off_h, cols_h, deg_h))
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t
-            g.free()
-            if k >= 2:
-                e2e_ms.append(dt * 1e3)
-        e_ms = statistics.mean(e2e_ms)
-        line["e2e"] = {"value": pairs_per_build / (e_ms / 1e3), "unit": UNIT, "ms_per_step": e_ms,
-                       "h2d_bytes_per_step": int(rep.chars.nbytes + rep.offsets.nbytes),
-                       "d2h_bytes_per_step": int(4 * (n + 1) + 4 * nnz + 4 * n)}
-        # --- analytics on the N = 8e5 network: LCC under random node removal
-        #     (normalisations of Methods "Computing LCC"), average neighbour degree
-        with build() as g:
-            ps = [0.0, 0.01, 0.1, 0.3, 0.49, 0.7, 0.89, 0.95, 0.98]
-            rng = np.random.default_rng(2024)
-            curve, t_cc = [], []
-            lcc0 = None
-            for p in ps:
-                keep = (rng.random(n) >= p).astype(np.uint8)
-                kt = torch.from_numpy(keep).to(dev)
+            qsrc = generate_config2(200_000, seed=1000 + rank)
+            qstr_off = qsrc.offsets
+            rng = np.random.default_rng(7)
+            resident = build(profile=False)
+            lat, qn = [], []
+            for b in range(args.query_batches + 2):
+                m = int(round(math.exp(rng.uniform(0, math.log(50_000)))))
+                start = int(rng.integers(0, qsrc.n - m))
+                qo = (qstr_off[start:start + m + 1] - qstr_off[start]).astype(np.int64)
+                qc = qsrc.chars[qstr_off[start]:qstr_off[start + m]]
+                t = time.perf_counter()
+                r = resident.query_flat(qc, qo)
+                r.copy_csr()
+                dt = time.perf_counter() - t
+                r.free()
+                if b >= 2:
+                    lat.append(dt * 1e3)
+                    qn.append(m)
+            resident.free()
+            line["query"] = {"batches": len(lat), "batch_size": "log-uniform 1..50000", "p50_ms": float(np.percentile(lat, 50)),
+                             "p99_ms": float(np.percentile(lat, 99)), "queries_per_s": sum(qn) / (sum(lat) / 1e3),
+                             "method": "deletion index of the resident build (probe of the query strings own records)"}
+        if "e2e" in legs:
+            # --- end to end: pinned host inputs in, CSR back in pinned host memory
+            hc = torch.from_numpy(rep.chars).pin_memory()
+            ho = torch.from_numpy(rep.offsets).pin_memory()
+            off_h = torch.empty(n + 1, dtype=torch.int32).pin_memory()
+            cols_h = torch.empty(max(nnz, 1), dtype=torch.int32).pin_memory()
+            deg_h = torch.empty(n, dtype=torch.int32).pin_memory()
+            e2e_ms = []
+            for k in range(args.e2e_steps + 2):
+                flush.fill_(2)
                 torch.cuda.synchronize()
                 t = time.perf_counter()
-                _, nc, lcc = _components_device(g, kt, tn)
-                t_cc.append(1e3 * (time.perf_counter() - t))
-                lcc0 = lcc if p == 0.0 else lcc0
-                norm1 = lcc / ((1 - p) * n)
-                curve.append({"p": p, "lcc": lcc, "components": nc, "lcc_norm1": norm1,
-                              "lcc_norm2": norm1 / (lcc0 / n)})
-            torch.cuda.synchronize()
-            t = time.perf_counter()
-            knn = g.neighbor_degree()
-            t_knn = 1e3 * (time.perf_counter() - t)
-        line["analytics"] = {"lcc_under_removal": curve, "components_ms_median": statistics.median(t_cc),
-                             "neighbor_degree_ms": t_knn, "mean_neighbor_degree": float(knn.mean())}
-        # --- l_max = 2 (bit-parallel distance): the paper's assortativity setting of
-        #     4 x 8,000 sequences, and N = 1e5
-        from synthgen import generate_config1
+                g = tn.tcrnet_build_flat(hc, ho, 1, method=args.method, stream=stream)
+                g.copy_csr(out=(off_h, cols_h, deg_h))
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t
+                g.free()
+                if k >= 2:
+                    e2e_ms.append(dt * 1e3)
+            e_ms = statistics.mean(e2e_ms)
+            line["e2e"] = {"value": pairs_per_build / (e_ms / 1e3), "unit": UNIT, "ms_per_step": e_ms,
+                           "h2d_bytes_per_step": int(rep.chars.nbytes + rep.offsets.nbytes),
+                           "d2h_bytes_per_step": int(4 * (n + 1) + 4 * nnz + 4 * n)}
+        if "analytics" in legs:
+            # --- analytics on the N = 8e5 network: LCC under random node removal
+            #     (normalisations of Methods "Computing LCC"), average neighbour degree
+            with build() as g:
+                ps = [0.0, 0.01, 0.1, 0.3, 0.49, 0.7, 0.89, 0.95, 0.98]
+                rng = np.random.default_rng(2024)
+                curve, t_cc = [], []
+                lcc0 = None
+                for p in ps:
+                    keep = (rng.random(n) >= p).astype(np.uint8)
+                    kt = torch.from_numpy(keep).to(dev)
+                    torch.cuda.synchronize()
+                    t = time.perf_counter()
+                    _, nc, lcc = _components_device(g, kt, tn)
+                    t_cc.append(1e3 * (time.perf_counter() - t))
+                    lcc0 = lcc if p == 0.0 else lcc0
+                    norm1 = lcc / ((1 - p) * n)
+                    curve.append({"p": p, "lcc": lcc, "components": nc, "lcc_norm1": norm1,
+                                  "lcc_norm2": norm1 / (lcc0 / n)})
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                knn = g.neighbor_degree()
+                t_knn = 1e3 * (time.perf_counter() - t)
+            line["analytics"] = {"lcc_under_removal": curve, "components_ms_median": statistics.median(t_cc),
+                                 "neighbor_degree_ms": t_knn, "mean_neighbor_degree": float(knn.mean())}
+        if "lmax2" in legs:
+            # --- l_max = 2 (bit-parallel distance): the paper's assortativity setting of
+            #     4 x 8,000 sequences, and N = 1e5
+            from synthgen import generate_config1
 
-        lm2 = {}
-        for n2 in (32_000, 100_000):
-            r2 = generate_config1(n2, seed=7)
-            c2 = torch.from_numpy(r2.chars).to(dev)
-            o2 = torch.from_numpy(r2.offsets).to(dev)
-            tn.tcrnet_build_flat(c2, o2, 2, stream=stream).free()
-            g2 = tn.tcrnet_build_flat(c2, o2, 2, stream=stream, profile=True)
-            st2 = g2.stats()
-            g2.free()
-            lm2[str(n2)] = {"build_ms": st2["ms_total"], "count_pass_ms": st2["ms_count"],
-                            "candidate_pairs": st2["candidate_pairs"], "nnz": st2["nnz"],
-                            "candidate_pairs_per_s": st2["candidate_pairs"] / (st2["ms_count"] / 1e3)}
-        line["lmax2"] = lm2
-        # --- batched: uneven repertoires in one pass vs one plain build each
-        if args.batched_reps > 0:
-            line["batched"] = batched_leg(args, tn, torch, stream, flush)
-        # --- serving: resident repertoire, Poisson queries and inserts
-        if args.serve_seconds > 0:
-            line["serving"] = serve_leg(args, tn, torch, stream)
-        # --- CPU oracle on a bounded sample (rank 0, one GPU only)
-        if world == 1 and args.cpu_seconds > 0:
-            rate, cores, rows, el = oracle_rate(rep, args.cpu_seconds)
-            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                    "sample": f"{rows} seeded rows of the N={n} network, each the full "
-                                              f"Wagner-Fischer scan against all {n} strings ({el:.1f} s)"}
+            lm2 = {}
+            for n2 in (32_000, 100_000):
+                r2 = generate_config1(n2, seed=7)
+                c2 = torch.from_numpy(r2.chars).to(dev)
+                o2 = torch.from_numpy(r2.offsets).to(dev)
+                tn.tcrnet_build_flat(c2, o2, 2, stream=stream).free()
+                g2 = tn.tcrnet_build_flat(c2, o2, 2, stream=stream, profile=True)
+                st2 = g2.stats()
+                g2.free()
+                lm2[str(n2)] = {"build_ms": st2["ms_total"], "count_pass_ms": st2["ms_count"],
+                                "candidate_pairs": st2["candidate_pairs"], "nnz": st2["nnz"],
+                                "candidate_pairs_per_s": st2["candidate_pairs"] / (st2["ms_count"] / 1e3)}
+            line["lmax2"] = lm2
+        if "batched" in legs:
+            # --- batched: uneven repertoires in one pass vs one plain build each
+            if args.batched_reps > 0:
+                line["batched"] = batched_leg(args, tn, torch, stream, flush)
+        if "serving" in legs:
+            # --- serving: resident repertoire, Poisson queries and inserts
+            if args.serve_seconds > 0:
+                line["serving"] = serve_leg(args, tn, torch, stream)
+        if "cpu" in legs:
+            # --- CPU oracle on a bounded sample (rank 0, one GPU only)
+            if world == 1 and args.cpu_seconds > 0:
+                rate, cores, rows, el = oracle_rate(rep, args.cpu_seconds)
+                line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                        "sample": f"{rows} seeded rows of the N={n} network, each the full "
+                                                  f"Wagner-Fischer scan against all {n} strings ({el:.1f} s)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -233,6 +233,14 @@ tcrnet_status tcrnet_components(tcrnet_handle h, const uint8_t *keep, int32_t *l
  * n doubles in memory space `mem`. */
 tcrnet_status tcrnet_neighbor_degree(tcrnet_handle h, double *knn, int32_t mem);
 
+/* Degree distribution (Results, degree distributions of the networks; d(u) of
+ * Methods "Overview of network theory concepts"): hist[d] = number of nodes of
+ * degree d for d < nbins - 1; hist[nbins - 1] counts every node of degree >=
+ * nbins - 1. nbins >= 1 int64 counters in memory space `mem`. *max_degree (may
+ * be NULL) receives the largest degree, so a caller can size the bins exactly. */
+tcrnet_status tcrnet_degree_histogram(tcrnet_handle h, int64_t *hist, int64_t nbins, int32_t mem,
+                                      int64_t *max_degree);
+
 /* Counters and phase times of the call that produced the handle. */
 tcrnet_status tcrnet_stats_get(tcrnet_handle h, tcrnet_stats *out);
 

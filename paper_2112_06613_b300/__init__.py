@@ -98,6 +98,7 @@ SYMBOLS = [
     "tcrnet_strerror", "tcrnet_last_error_index", "tcrnet_version", "tcrnet_last_cuda_error",
     "tcrnet_degree_noalloc", "tcrnet_query_ex", "tcrnet_insert_flat", "tcrnet_insert_ex", "tcrnet_insert",
     "tcrnet_components", "tcrnet_neighbor_degree", "tcrnet_build_batched",
+    "tcrnet_degree_histogram",
 ]
 
 
@@ -130,6 +131,8 @@ def load_library(path: str = LIB_PATH):
         lib.tcrnet_csr_device.restype = ctypes.c_int
         lib.tcrnet_query_flat.argtypes = [H, vp, vp, i64, i32, HP]
         lib.tcrnet_query_flat.restype = ctypes.c_int
+        lib.tcrnet_degree_histogram.argtypes = [H, vp, i64, i32, ctypes.POINTER(i64)]
+        lib.tcrnet_degree_histogram.restype = ctypes.c_int
         lib.tcrnet_build_batched.argtypes = [vp, vp, i64, vp, i64, i32, i32, optp, HP]
         lib.tcrnet_build_batched.restype = ctypes.c_int
         lib.tcrnet_components.argtypes = [H, vp, vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]
@@ -281,6 +284,21 @@ class Graph:
         _check(load_library().tcrnet_components(self._h, kp, labels.ctypes.data, HOST, ctypes.byref(nc),
                                                 ctypes.byref(lc)), "tcrnet_components")
         return labels[:n], nc.value, lc.value
+
+    def degree_histogram(self, nbins=None):
+        """Nodes per degree (host int64 array); the last bin collects larger degrees.
+        nbins=None sizes the bins to the largest degree + 1."""
+        lib = load_library()
+        mx = ctypes.c_int64()
+        if nbins is None:
+            one = np.empty(1, dtype=np.int64)
+            _check(lib.tcrnet_degree_histogram(self._h, one.ctypes.data, 1, HOST, ctypes.byref(mx)),
+                   "tcrnet_degree_histogram")
+            nbins = int(mx.value) + 1
+        hist = np.empty(int(nbins), dtype=np.int64)
+        _check(lib.tcrnet_degree_histogram(self._h, hist.ctypes.data, int(nbins), HOST, ctypes.byref(mx)),
+               "tcrnet_degree_histogram")
+        return hist
 
     def neighbor_degree(self):
         """Average neighbour degree per node (host float64 array)."""

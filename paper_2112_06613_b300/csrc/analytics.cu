@@ -126,6 +126,38 @@ k_neighbor_degree(const Off* __restrict__ off, const int32_t* __restrict__ cols,
     }
 }
 
+// Degree histogram: bins in shared memory per block when they fit, global
+// atomics otherwise; the last bin collects every larger degree.
+constexpr int kSmemBins = 4096;
+
+__global__ void __launch_bounds__(kThreads)
+k_degree_hist(const int32_t* __restrict__ deg, int64_t n, unsigned long long* __restrict__ hist, int64_t nbins,
+              int* __restrict__ dmax) {
+    __shared__ unsigned int bins[kSmemBins];
+    const bool local = nbins <= kSmemBins;
+    if (local)
+        for (int b = threadIdx.x; b < nbins; b += blockDim.x) bins[b] = 0;
+    __syncthreads();
+    int mymax = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int d = deg[i];
+        mymax = d > mymax ? d : mymax;
+        const int64_t b = (int64_t)d < nbins - 1 ? (int64_t)d : nbins - 1;
+        if (local) atomicAdd(&bins[b], 1u);
+        else atomicAdd(&hist[b], 1ull);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const int t = __shfl_down_sync(kFull, mymax, o);
+        mymax = t > mymax ? t : mymax;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(dmax, mymax);
+    __syncthreads();
+    if (local)
+        for (int b = threadIdx.x; b < nbins; b += blockDim.x)
+            if (bins[b]) atomicAdd(&hist[b], (unsigned long long)bins[b]);
+}
+
 inline unsigned blocks_for(int64_t n, int per_block, int num_sms) {
     const int64_t b = ceil_div(n, per_block);
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms * 32));
@@ -177,6 +209,25 @@ tcrnet_status neighbor_degree(const void* off, bool off64, const int32_t* cols, 
     else
         k_neighbor_degree<int32_t><<<wb, kThreads, 0, s>>>(static_cast<const int32_t*>(off), cols, n, knn);
     TCR_LAUNCH_CHECK();
+    return TCRNET_OK;
+}
+
+tcrnet_status degree_histogram(const int32_t* deg, int64_t n, int64_t* hist, int64_t nbins, int64_t* max_degree,
+                               cudaStream_t s, int num_sms) {
+    DevBuf dm;
+    TCR_CHECK(dm.alloc(sizeof(int), s));
+    TCR_CUDA(cudaMemsetAsync(dm.as<void>(), 0, sizeof(int), s));
+    TCR_CUDA(cudaMemsetAsync(hist, 0, sizeof(int64_t) * nbins, s));
+    if (n > 0) {
+        const unsigned grid = std::min(blocks_for(n, kThreads, num_sms), (unsigned)num_sms * 2);
+        k_degree_hist<<<grid, kThreads, 0, s>>>(deg, n, reinterpret_cast<unsigned long long*>(hist), nbins,
+                                                dm.as<int>());
+        TCR_LAUNCH_CHECK();
+    }
+    int h_max = 0;
+    TCR_CUDA(cudaMemcpyAsync(&h_max, dm.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaStreamSynchronize(s));
+    if (max_degree) *max_degree = h_max;
     return TCRNET_OK;
 }
 

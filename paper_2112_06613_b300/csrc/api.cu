@@ -749,6 +749,27 @@ tcrnet_status tcrnet_neighbor_degree(tcrnet_handle h, double* knn, int32_t mem) 
     return TCRNET_OK;
 }
 
+tcrnet_status tcrnet_degree_histogram(tcrnet_handle h, int64_t* hist, int64_t nbins, int32_t mem,
+                                      int64_t* max_degree) {
+    if (!h || !hist || nbins < 1 || (mem != TCRNET_HOST && mem != TCRNET_DEVICE)) return TCRNET_EINVAL;
+    DeviceGuard dg;
+    TCR_CHECK(dg.set(h->device));
+    cudaStream_t s = h->stream;
+    ArenaLease lease(h->device, s);
+    DevBuf dh;
+    int64_t* out = hist;
+    if (mem == TCRNET_HOST) {
+        TCR_CHECK(dh.alloc(sizeof(int64_t) * nbins, s));
+        out = dh.as<int64_t>();
+    }
+    TCR_CHECK(degree_histogram(h->d_degree, h->n, out, nbins, max_degree, s, sm_count(h->device)));
+    if (mem == TCRNET_HOST) {
+        TCR_CUDA(cudaMemcpyAsync(hist, out, sizeof(int64_t) * nbins, cudaMemcpyDeviceToHost, s));
+        TCR_CUDA(cudaStreamSynchronize(s));
+    }
+    return TCRNET_OK;
+}
+
 tcrnet_status tcrnet_stats_get(tcrnet_handle h, tcrnet_stats* out) {
     if (!h || !out) return TCRNET_EINVAL;
     *out = h->stats;

@@ -66,6 +66,8 @@ tcrnet_status dp_pass(const TileSide& rows, const TileSide& cols, bool sym, int 
 tcrnet_status components(const void* off, bool off64, const int32_t* cols, int64_t n, const uint8_t* keep,
                          int32_t* labels, int64_t* n_components, int64_t* largest, cudaStream_t s, int num_sms);
 // knn[i] = mean degree of i's neighbours (0 for isolated nodes).
+tcrnet_status degree_histogram(const int32_t* deg, int64_t n, int64_t* hist, int64_t nbins, int64_t* max_degree,
+                               cudaStream_t s, int num_sms);
 tcrnet_status neighbor_degree(const void* off, bool off64, const int32_t* cols, int64_t n, double* knn,
                               cudaStream_t s, int num_sms);
 

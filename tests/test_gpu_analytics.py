@@ -49,3 +49,33 @@ def test_neighbor_degree():
         knn = g.neighbor_degree()
     ref = analytics.neighbor_degree(np.asarray(off, dtype=np.int64), cols)
     assert np.allclose(knn, ref, rtol=0, atol=1e-12)
+
+
+@pytest.fixture(scope="module")
+def hist_case():
+    rep = generate_config1(12_000, seed=83)
+    _, _, odeg = oracle.network(rep.chars, rep.offsets, max_dist=1)
+    return rep, np.bincount(np.asarray(odeg, dtype=np.int64))
+
+
+@pytest.mark.parametrize("nbins", [None, 1, 7, 5000, 70_000])
+def test_degree_histogram_against_oracle_degrees(hist_case, nbins):
+    rep, full = hist_case
+    with tn.tcrnet_build_flat(rep.chars, rep.offsets, 1, method="deletion") as g:
+        hist = g.degree_histogram(nbins)
+    if nbins is None:
+        assert np.array_equal(hist, full)
+        return
+    want = np.zeros(nbins, dtype=np.int64)
+    k = min(nbins - 1, full.shape[0])
+    want[:k] = full[:k]
+    want[nbins - 1] += full[nbins - 1:].sum()
+    assert np.array_equal(hist, want)
+    assert hist.sum() == rep.n
+
+
+def test_degree_histogram_empty_and_isolated():
+    with tn.tcrnet_build([], 1) as g:
+        assert list(g.degree_histogram(3)) == [0, 0, 0]
+    with tn.tcrnet_build(["W", "CASSF", "CASSG", "CASSG"], 1) as g:
+        assert list(g.degree_histogram()) == [1, 0, 3]
