@@ -365,8 +365,13 @@ def batched_leg(args, tn, torch, stream, flush, reps_steps=3):
                 out.append((a.elapsed_time(b), extra))
         return out
 
+    from paper_2112_06613_b300.autotune import PartitionTuner
+
+    tuner = PartitionTuner(trials=1)
+    target = tuner.tune(dc, do, rep_offsets=bounds, stream=stream)  # untimed
+
     def batched():
-        g = tn.tcrnet_build_batched(dc, do, bounds, 1, stream=stream, profile=False)
+        g = tn.tcrnet_build_batched(dc, do, bounds, 1, stream=stream, profile=False, partition_target=target)
         st = g.stats()
         g.free()
         return st
@@ -392,7 +397,9 @@ def batched_leg(args, tn, torch, stream, flush, reps_steps=3):
             "batched_kernel_launches": int(tb[0][1]["kernel_launches"]),
             "sequential_ms": ms, "sequential_pairs_per_s": pairs / (ms / 1e3),
             "sequential_kernel_launches": int(ts[0][1]["kernel_launches"]),
-            "speedup": ms / mb, "timing": f"CUDA events, mean of {reps_steps} after 1 warm-up, L2 flushed"}
+            "speedup": ms / mb, "timing": f"CUDA events, mean of {reps_steps} after 1 warm-up, L2 flushed",
+            "partition_target": target, "autotune_ms": {str(k): v for k, v in tuner.last_timings.items()},
+            "autotune": "records per partition chosen by timing the candidates once on this input (untimed)"}
 
 
 def _components_device(g, keep_dev, tn):

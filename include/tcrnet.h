@@ -84,7 +84,10 @@ typedef struct tcrnet_options {
     int32_t profile;          /* 1: record per-phase CUDA-event times (tcrnet_stats) */
     int32_t partition_cap;    /* testing: deletion-join partitions larger than this
                                  take the exact quadratic fallback; 0 = default */
-    int32_t reserved[7];      /* must be zero */
+    int32_t partition_target; /* tuning: mean records per deletion-join partition,
+                                 4 .. 128; 0 = default (24 up to 2^25 records,
+                                 else 32). Any value gives the same network. */
+    int32_t reserved[6];      /* must be zero */
 } tcrnet_options;
 
 /* Defaults: AUTO method, current device, legacy default stream, no profiling. */

@@ -41,7 +41,8 @@ class tcrnet_options(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("profile", ctypes.c_int32),
         ("partition_cap", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 7),
+        ("partition_target", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 6),
     ]
 
 
@@ -188,7 +189,7 @@ def _stream_ptr(stream):
 
 
 def make_options(method="auto", device=None, stream=None, profile=False, force_offsets64=False,
-                 partition_cap=0):
+                 partition_cap=0, partition_target=0):
     lib = load_library()
     o = tcrnet_options()
     lib.tcrnet_options_init(ctypes.byref(o))
@@ -199,6 +200,7 @@ def make_options(method="auto", device=None, stream=None, profile=False, force_o
     o.profile = 1 if profile else 0
     o.force_offsets64 = 1 if force_offsets64 else 0
     o.partition_cap = int(partition_cap)
+    o.partition_target = int(partition_target)
     return o
 
 
@@ -367,11 +369,11 @@ def tcrnet_build(seqs, threshold: int = 1, method="auto", device=None, stream=No
 
 
 def tcrnet_build_flat(chars, offsets, threshold: int = 1, method="auto", device=None, stream=None,
-                      profile=False, force_offsets64=False, partition_cap=0) -> Graph:
+                      profile=False, force_offsets64=False, partition_cap=0, partition_target=0) -> Graph:
     """Network of strings in flat layout (numpy arrays, or torch tensors on host or device)."""
     lib = load_library()
     cp, op, n, mem, keep = _flat_args(chars, offsets)
-    opt = make_options(method, device, stream, profile, force_offsets64, partition_cap)
+    opt = make_options(method, device, stream, profile, force_offsets64, partition_cap, partition_target)
     h = ctypes.c_void_p()
     st = lib.tcrnet_build_flat(cp, op, n, mem, int(threshold), ctypes.byref(opt), ctypes.byref(h))
     del keep
@@ -379,13 +381,14 @@ def tcrnet_build_flat(chars, offsets, threshold: int = 1, method="auto", device=
     return Graph(h.value)
 
 
-def tcrnet_build_batched(chars, offsets, rep_offsets, threshold: int = 1, stream=None, profile=False) -> Graph:
+def tcrnet_build_batched(chars, offsets, rep_offsets, threshold: int = 1, stream=None, profile=False,
+                         partition_target=0) -> Graph:
     """Block-diagonal network of several repertoires in one pass (see include/tcrnet.h).
     rep_offsets: host int64 array of nrep + 1 string-index bounds."""
     lib = load_library()
     cp, op, n, mem, keep = _flat_args(chars, offsets)
     ro = np.ascontiguousarray(rep_offsets, dtype=np.int64)
-    opt = make_options("deletion", None, stream, profile)
+    opt = make_options("deletion", None, stream, profile, partition_target=partition_target)
     h = ctypes.c_void_p()
     st = lib.tcrnet_build_batched(cp, op, n, ro.ctypes.data, ro.shape[0] - 1, mem, int(threshold),
                                   ctypes.byref(opt), ctypes.byref(h))

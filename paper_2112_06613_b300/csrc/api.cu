@@ -350,7 +350,8 @@ tcrnet_status build_from_packed(tcrnet_graph* h, Packed& pk, int64_t n, int32_t 
         if (st != TCRNET_OK) return st;
     } else {
         DeletionResult dr;
-        st = deletion_build(pk, T, dr, s, sms, opt.profile != 0, opt.partition_cap, keep_index);
+        st = deletion_build(pk, T, dr, s, sms, opt.profile != 0, opt.partition_cap, keep_index,
+                            opt.partition_target);
         if (st != TCRNET_OK) return st;
         h->stats.n_unique = dr.n_unique;
         h->stats.n_records = dr.n_records;
@@ -386,6 +387,7 @@ tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n
     if (n < 0 || n > 0x7fffffffLL) return TCRNET_EINVAL;
     if (T < 0) return TCRNET_EINVAL;
     if (opt.method < TCRNET_METHOD_AUTO || opt.method > TCRNET_METHOD_DELETION) return TCRNET_EINVAL;
+    if (opt.partition_target != 0 && (opt.partition_target < 4 || opt.partition_target > 128)) return TCRNET_EINVAL;
     if (T > 1 && opt.method == TCRNET_METHOD_DELETION) return TCRNET_ENOTSUP;  // deletion join: l_max <= 1
     if (rep_off) {
         // batched: one deletion-method pass over all repertoires

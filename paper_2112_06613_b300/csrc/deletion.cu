@@ -56,7 +56,13 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kWarpCap = 128;     // records per partition joined by one warp
-constexpr int kTargetPart = 32;   // mean records per partition
+// Default mean records per partition. Fewer records per partition make more of
+// them fit one warp's match step (<= 32); more partitions make the counters of
+// the record scatter colder. Measured on one B300 (8e5 strings: 24 best, 1.47 vs
+// 1.50 ms at 32; 8.9e6 strings: 32 best, 14.5 vs 14.8 ms at 24).
+constexpr int kTargetPartSmall = 24;
+constexpr int kTargetPartLarge = 32;
+constexpr int64_t kTargetSwitchRecords = 1LL << 25;
 constexpr uint32_t kTagF = 63;    // position tag of a full-string record
 constexpr uint64_t kUMask = (1ull << 25) - 1;
 constexpr int kEdgeSegs = 64;     // edge buffer segments (one cursor each), by partition id
@@ -383,43 +389,211 @@ __device__ __forceinline__ int64_t record_edges_checked(const uint64_t* buf, int
     return cnt;
 }
 
+// Join of the partitions of at most 32 records, without sorting. Lane k holds
+// record k; __match_any_sync on the 32-bit hash gives each lane its hash group
+// G, on (hash, p) its run M. Same-position partners are the lanes of M above
+// this one (each pair once); a run-start deletion pairs with the group's full
+// record. Exactness as in the sorted path: every attempted pair is confirmed
+// by content, a group with two full records (two different contents under one
+// hash, since the strings are distinct) is a collision, and a collision sends
+// the partition to the exact fallback. Larger partitions are listed for
+// k_join_sorted (first pass) and skipped here; both passes take the same
+// decisions, so their counts agree.
+// First pass (WRITE = false): per-partition edge counts, weighted degrees
+// W_u += m_v, W_v += m_u, and every edge written into the capped segmented
+// buffer when it fits; a warp gathers its edges in shared memory and moves
+// them out kStage at a time (one cursor update per flush, coalesced stores).
+// Second pass (WRITE = true, only after an overflow): edges written at the
+// scanned positions eoff. The records of the next partition are loaded while
+// the current one is joined.
+constexpr int kStage = 256;
+
+template <bool WRITE>
+__global__ void __launch_bounds__(kThreads, 6)
+k_join_small(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __restrict__ recs,
+             const Canon* __restrict__ ucanon, const int32_t* __restrict__ umult, int cap, int T,
+             int32_t* __restrict__ wsum, int64_t* __restrict__ pedges, const int64_t* __restrict__ eoff,
+             int2* __restrict__ edges, unsigned long long* __restrict__ ecur, int64_t seg_cap,
+             int32_t* __restrict__ big_list, int* __restrict__ big_count, int32_t* __restrict__ fb_list,
+             int* __restrict__ fb_count) {
+    __shared__ uint64_t sbuf[kWarps][32];
+    __shared__ int32_t smul[kWarps][32];
+    __shared__ int2 sstage[WRITE ? 1 : kWarps][WRITE ? 1 : kStage];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t* buf = sbuf[warp];
+    int32_t* mul = smul[warp];
+    int2* stage = sstage[WRITE ? 0 : warp];
+    const uint32_t above = lane == 31 ? 0u : ~((2u << lane) - 1u);
+    const int64_t wid = (int64_t)blockIdx.x * kWarps + warp;
+    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+    const int seg = (int)(wid & (kEdgeSegs - 1));
+    int fillc = 0;  // staged edges of this warp
+    auto flush = [&]() {
+        __syncwarp();
+        if (fillc) {
+            unsigned long long eb = 0;
+            if (lane == 0) eb = atomicAdd(&ecur[seg], (unsigned long long)fillc);
+            eb = __shfl_sync(kFull, eb, 0);
+            if ((int64_t)(eb + fillc) <= seg_cap) {
+                int2* dst = edges + seg * seg_cap + (int64_t)eb;
+                for (int k = lane; k < fillc; k += 32) dst[k] = stage[k];
+            }
+            fillc = 0;
+        }
+        __syncwarp();
+    };
+    for (int64_t p0 = wid * 32; p0 < P; p0 += nwarps * 32) {
+        int64_t my_base = 0;
+        int my_size = 0;
+        if (p0 + lane < P) {
+            my_base = poff[p0 + lane];
+            const int64_t sz = poff[p0 + lane + 1] - my_base;
+            my_size = sz > 0x7fffffff ? 0x7fffffff : (int)sz;
+        }
+        const int small_max = cap < 32 ? cap : 32;
+        if (!WRITE && p0 + lane < P) {  // lane-parallel hand-off of the other partitions
+            if (my_size > cap) {
+                fb_list[atomicAdd(fb_count, 1)] = (int32_t)(p0 + lane);
+                pedges[p0 + lane] = 0;
+            } else if (my_size > 32) {
+                big_list[atomicAdd(big_count, 1)] = (int32_t)(p0 + lane);
+            } else if (my_size < 2) {
+                pedges[p0 + lane] = 0;
+            }
+        }
+        uint32_t todo = __ballot_sync(kFull, my_size >= 2 && my_size <= small_max);
+        int jn = todo ? __ffs(todo) - 1 : -1;
+        uint64_t rec_next = ~0ull;
+        int s_next = 0;
+        if (jn >= 0) {
+            const int64_t b = __shfl_sync(kFull, my_base, jn);
+            s_next = __shfl_sync(kFull, my_size, jn);
+            if (lane < s_next) rec_next = recs[b + lane];
+        }
+        while (jn >= 0) {
+            const int j = jn;
+            const int s = s_next;
+            const uint64_t rec = rec_next;
+            todo &= todo - 1;
+            jn = todo ? __ffs(todo) - 1 : -1;
+            if (jn >= 0) {  // prefetch the next partition's records
+                const int64_t b = __shfl_sync(kFull, my_base, jn);
+                s_next = __shfl_sync(kFull, my_size, jn);
+                rec_next = lane < s_next ? recs[b + lane] : ~0ull;
+            }
+            const int64_t pid = p0 + j;
+            const bool act = lane < s;
+            buf[lane] = rec;
+            const uint32_t amask = (s >= 32) ? kFull : ((1u << s) - 1u);
+            const uint32_t G = __match_any_sync(kFull, (uint32_t)(rec >> 32)) & amask;
+            const uint32_t M = __match_any_sync(kFull, (unsigned long long)(rec >> 26)) & amask;
+            const bool isF = rec_p(rec) == kTagF;
+            const uint32_t Gf = G & __ballot_sync(kFull, act && isF);
+            bool bad = act && __popc(Gf) > 1;
+            const uint32_t partners = (act && !isF) ? (M & above) : 0u;
+            const bool indel = act && !isF && T >= 1 && rec_runstart(rec) && Gf != 0;
+            const bool grouped = act && __popc(G) > 1;
+            if (__any_sync(kFull, grouped)) {
+                Canon c;
+                c.w[0] = c.w[1] = c.w[2] = c.w[3] = 0;
+                if (grouped) {
+                    if (!WRITE) mul[lane] = umult[rec_u(rec)];
+                    c = record_content(rec, ucanon);
+                }
+                const int lead = M ? __ffs(M) - 1 : lane;
+                const int fl = Gf ? __ffs(Gf) - 1 : lane;
+                uint64_t d1 = 0, d2 = 0;
+#pragma unroll
+                for (int w = 0; w < kCanonWords; ++w) {
+                    d1 |= __shfl_sync(kFull, c.w[w], lead) ^ c.w[w];
+                    d2 |= __shfl_sync(kFull, c.w[w], fl) ^ c.w[w];
+                }
+                if (act && !isF && __popc(M) > 1 && d1) bad = true;
+                if (indel && d2) bad = true;
+            }
+            __syncwarp();
+            if (__any_sync(kFull, bad)) {
+                if (!WRITE && lane == 0) {
+                    fb_list[atomicAdd(fb_count, 1)] = (int32_t)pid;
+                    pedges[pid] = 0;
+                }
+                __syncwarp();
+                continue;
+            }
+            const int mine = __popc(partners) + (indel ? 1 : 0);
+            int x = mine;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(kFull, x, d);
+                if (lane >= d) x += y;
+            }
+            const int total = __shfl_sync(kFull, x, 31);
+            const int excl = x - mine;
+            const int32_t u = (int32_t)rec_u(rec);
+            if (!WRITE) {
+                if (lane == 0) pedges[pid] = total;
+                if (total) {
+                    // staged (total <= kStage) or written directly with its own cursor update
+                    if (fillc + total > kStage) flush();
+                    int2* dst = stage + fillc + excl;
+                    bool fits = true;
+                    if (total > kStage) {
+                        unsigned long long eb = 0;
+                        if (lane == 0) eb = atomicAdd(&ecur[seg], (unsigned long long)total);
+                        eb = __shfl_sync(kFull, eb, 0);
+                        fits = (int64_t)(eb + total) <= seg_cap;
+                        dst = edges + seg * seg_cap + (int64_t)eb + excl;
+                    } else {
+                        fillc += total;
+                    }
+                    if (mine) {
+                        const int32_t mu = mul[lane];
+                        for (uint32_t m = partners; m; m &= m - 1) {
+                            const int k = __ffs(m) - 1;
+                            const int32_t v = (int32_t)rec_u(buf[k]);
+                            atomicAdd(&wsum[u], mul[k]);
+                            atomicAdd(&wsum[v], mu);
+                            if (fits) *dst++ = make_int2(u, v);
+                        }
+                        if (indel) {
+                            const int k = __ffs(Gf) - 1;
+                            const int32_t v = (int32_t)rec_u(buf[k]);
+                            atomicAdd(&wsum[u], mul[k]);
+                            atomicAdd(&wsum[v], mu);
+                            if (fits) *dst++ = make_int2(v, u);
+                        }
+                    }
+                }
+            } else if (mine) {
+                int64_t pos = eoff[pid] + excl;
+                for (uint32_t m = partners; m; m &= m - 1) edges[pos++] = make_int2(u, (int32_t)rec_u(buf[__ffs(m) - 1]));
+                if (indel) edges[pos++] = make_int2((int32_t)rec_u(buf[__ffs(Gf) - 1]), u);
+            }
+            __syncwarp();
+        }
+    }
+    if (!WRITE) flush();
+}
+
+// Join of the listed partitions of 33 .. cap records: warp per partition,
+// register bitonic sort, runs of equal (hash, p) and hash groups scanned in
+// order (see record_edges / record_edges_checked).
 template <bool WRITE>
 __global__ void __launch_bounds__(kThreads)
-k_join(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __restrict__ recs,
-       const Canon* __restrict__ ucanon, int cap, int T, Weigh weigh, int64_t* __restrict__ pedges,
-       const int64_t* __restrict__ eoff, int2* __restrict__ edges, unsigned long long* __restrict__ ecur,
-       int64_t seg_cap, int32_t* __restrict__ fb_list, int* __restrict__ fb_count) {
+k_join_sorted(const int32_t* __restrict__ list, const int* __restrict__ count, const int64_t* __restrict__ poff,
+              const uint64_t* __restrict__ recs, const Canon* __restrict__ ucanon, int T, Weigh weigh,
+              int64_t* __restrict__ pedges, const int64_t* __restrict__ eoff, int2* __restrict__ edges,
+              unsigned long long* __restrict__ ecur, int64_t seg_cap, int32_t* __restrict__ fb_list,
+              int* __restrict__ fb_count) {
     __shared__ uint64_t sbuf[kWarps][kWarpCap];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint64_t* buf = sbuf[warp];
-    // a warp takes 32 consecutive partitions; lane j fetches the bounds of the j-th
-    const int64_t wid = (int64_t)blockIdx.x * kWarps + warp;
-    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
-    for (int64_t p0 = wid * 32; p0 < P; p0 += nwarps * 32) {
-      int64_t my_base = 0, my_size = 0;
-      if (p0 + lane < P) {
-          my_base = poff[p0 + lane];
-          my_size = poff[p0 + lane + 1] - my_base;
-      }
-      const int pcount = (P - p0) < 32 ? (int)(P - p0) : 32;
-      for (int j = 0; j < pcount; ++j) {
-        const int64_t pid = p0 + j;
-        const int64_t base = __shfl_sync(kFull, my_base, j);
-        const int64_t s64 = __shfl_sync(kFull, my_size, j);
-        if (s64 > cap) {
-            if (!WRITE && lane == 0) {
-                fb_list[atomicAdd(fb_count, 1)] = (int32_t)pid;
-                pedges[pid] = 0;
-            }
-            continue;
-        }
-        const int s = (int)s64;
-        if (s < 2) {
-            if (!WRITE && lane == 0) pedges[pid] = 0;
-            continue;
-        }
-        if (s <= 32) load_sort_store<1>(recs + base, s, buf, lane);
-        else if (s <= 64) load_sort_store<2>(recs + base, s, buf, lane);
+    const int nlist = *count;
+    for (int f = blockIdx.x * kWarps + warp; f < nlist; f += gridDim.x * kWarps) {
+        const int64_t pid = list[f];
+        const int64_t base = poff[pid];
+        const int s = (int)(poff[pid + 1] - base);
+        if (s <= 64) load_sort_store<2>(recs + base, s, buf, lane);
         else load_sort_store<4>(recs + base, s, buf, lane);
         __syncwarp();
         // count the edges, confirming each one's contents (exact)
@@ -437,15 +611,14 @@ k_join(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __restrict__
         int64_t excl;
         const int64_t total = warp_scan(mine, excl, lane);
         if (!WRITE) {
-            // weigh every edge and write it into the capped buffer when it fits
             if (lane == 0) pedges[pid] = total;
             if (total) {
                 const int seg = (int)(pid & (kEdgeSegs - 1));
-                unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(&ecur[seg], (unsigned long long)total);
-                base = __shfl_sync(kFull, base, 0);
-                const bool fits = (int64_t)(base + total) <= seg_cap;
-                int64_t pos = seg * seg_cap + (int64_t)base + excl;
+                unsigned long long eb = 0;
+                if (lane == 0) eb = atomicAdd(&ecur[seg], (unsigned long long)total);
+                eb = __shfl_sync(kFull, eb, 0);
+                const bool fits = (int64_t)(eb + total) <= seg_cap;
+                int64_t pos = seg * seg_cap + (int64_t)eb + excl;
                 for (int k = lane; k < s; k += 32)
                     record_edges(buf, k, s, T, [&](int32_t a, int32_t b) {
                         weigh(a, b);
@@ -458,7 +631,6 @@ k_join(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __restrict__
                 record_edges(buf, k, s, T, [&](int32_t a, int32_t b) { edges[pos++] = make_int2(a, b); });
         }
         __syncwarp();
-      }
     }
 }
 
@@ -658,7 +830,7 @@ private:
 }  // namespace
 
 tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaStream_t s, int num_sms, bool profile,
-                             int partition_cap, bool keep_index) {
+                             int partition_cap, bool keep_index, int partition_target) {
     const int64_t n = pk.n;
     if (n > kDeletionMaxN) return TCRNET_ENOTSUP;
     const int cap = (partition_cap > 0 && partition_cap < kWarpCap) ? partition_cap : kWarpCap;
@@ -731,7 +903,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     const int t1 = tm.mark();
 
     // ---- 2. records
-    DevBuf pcnt, poff, recs, fb_list, pedges, eoff, wsum, ucur, uoff, edges;
+    DevBuf pcnt, poff, recs, fb_list, big_list, pedges, eoff, wsum, ucur, uoff, edges;
     TCR_CHECK(wsum.alloc(sizeof(int32_t) * n, s));
     TCR_CHECK(ucur.alloc(sizeof(int32_t) * n, s));
     TCR_CHECK(uoff.alloc(sizeof(int64_t) * (n + 1), s));
@@ -742,13 +914,16 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     int jgrid = 1;
     int t2 = t1, t3 = t1;
     if (join) {
-        P = std::max<int64_t>(1, std::min<int64_t>(R_max / kTargetPart + 1, 1LL << 30));
+        const int target = partition_target > 0 ? partition_target
+                                                 : (R_max <= kTargetSwitchRecords ? kTargetPartSmall : kTargetPartLarge);
+        P = std::max<int64_t>(1, std::min<int64_t>(R_max / target + 1, 1LL << 30));
         TCR_CHECK(pcnt.alloc(sizeof(int32_t) * P, s));
         if (keep_index) TCR_CHECK(poff.alloc_owned(sizeof(int64_t) * (P + 1), s));
         else TCR_CHECK(poff.alloc(sizeof(int64_t) * (P + 1), s));
         if (keep_index) TCR_CHECK(recs.alloc_owned(sizeof(uint64_t) * R_max, s));
         else TCR_CHECK(recs.alloc(sizeof(uint64_t) * R_max, s));
         TCR_CHECK(fb_list.alloc(sizeof(int32_t) * P, s));
+        TCR_CHECK(big_list.alloc(sizeof(int32_t) * P, s));
         TCR_CHECK(pedges.alloc(sizeof(int64_t) * P, s));
         TCR_CHECK(eoff.alloc(sizeof(int64_t) * (P + 1), s));
         TCR_CHECK(edges.alloc(sizeof(int2) * ecap, s));
@@ -766,9 +941,15 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         t2 = tm.mark();
         // ---- 3a. join, pass 1: weighted degrees W_u
         jgrid = (int)std::min<int64_t>(ceil_div(P, 32 * kWarps), (int64_t)num_sms * 16);
-        k_join<false><<<jgrid, kThreads, 0, s>>>(poff.as<int64_t>(), P, recs.as<uint64_t>(), ucanon.as<Canon>(), cap,
-                                                 T, weigh, pedges.as<int64_t>(), nullptr, edges.as<int2>(), d_ecur,
-                                                 seg_cap, fb_list.as<int32_t>(), d_err + 2);
+        k_join_small<false><<<jgrid, kThreads, 0, s>>>(
+            poff.as<int64_t>(), P, recs.as<uint64_t>(), ucanon.as<Canon>(), umult.as<int32_t>(), cap, T,
+            wsum.as<int32_t>(), pedges.as<int64_t>(), nullptr, edges.as<int2>(), d_ecur, seg_cap,
+            big_list.as<int32_t>(), d_err + 3, fb_list.as<int32_t>(), d_err + 2);
+        TCR_LAUNCH_CHECK();
+        k_join_sorted<false><<<num_sms * 4, kThreads, 0, s>>>(big_list.as<int32_t>(), d_err + 3, poff.as<int64_t>(),
+                                                              recs.as<uint64_t>(), ucanon.as<Canon>(), T, weigh,
+                                                              pedges.as<int64_t>(), nullptr, edges.as<int2>(), d_ecur,
+                                                              seg_cap, fb_list.as<int32_t>(), d_err + 2);
         TCR_LAUNCH_CHECK();
         k_join_fallback<false><<<num_sms * 2, kThreads, 0, s>>>(fb_list.as<int32_t>(), d_err + 2, poff.as<int64_t>(),
                                                                 recs.as<uint64_t>(), ucanon.as<Canon>(), T, weigh,
@@ -816,9 +997,14 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         edges.reset();
         TCR_CHECK(edges.alloc(sizeof(int2) * E, s));
         TCR_CHECK(scan_exclusive_i64(pedges.as<int64_t>(), eoff.as<int64_t>(), P, s));
-        k_join<true><<<jgrid, kThreads, 0, s>>>(poff.as<int64_t>(), P, recs.as<uint64_t>(), ucanon.as<Canon>(), cap,
-                                                T, weigh, nullptr, eoff.as<int64_t>(), edges.as<int2>(), nullptr, 0,
-                                                nullptr, nullptr);
+        k_join_small<true><<<jgrid, kThreads, 0, s>>>(
+            poff.as<int64_t>(), P, recs.as<uint64_t>(), ucanon.as<Canon>(), umult.as<int32_t>(), cap, T, nullptr,
+            nullptr, eoff.as<int64_t>(), edges.as<int2>(), nullptr, 0, nullptr, nullptr, nullptr, nullptr);
+        TCR_LAUNCH_CHECK();
+        k_join_sorted<true><<<num_sms * 4, kThreads, 0, s>>>(big_list.as<int32_t>(), d_err + 3, poff.as<int64_t>(),
+                                                             recs.as<uint64_t>(), ucanon.as<Canon>(), T, weigh,
+                                                             nullptr, eoff.as<int64_t>(), edges.as<int2>(), nullptr,
+                                                             0, nullptr, nullptr);
         TCR_LAUNCH_CHECK();
         k_join_fallback<true><<<num_sms * 2, kThreads, 0, s>>>(fb_list.as<int32_t>(), d_err + 2, poff.as<int64_t>(),
                                                                recs.as<uint64_t>(), ucanon.as<Canon>(), T, weigh,

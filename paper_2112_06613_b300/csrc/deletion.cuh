@@ -45,7 +45,8 @@ struct DeletionResult {
 // Test knob: partitions larger than `partition_cap` (<= the shared-memory
 // capacity; 0 = default) take the quadratic fallback.
 tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaStream_t s, int num_sms,
-                             bool profile, int partition_cap = 0, bool keep_index = false);
+                             bool profile, int partition_cap = 0, bool keep_index = false,
+                             int partition_target = 0);
 
 // Neighbour lists (l_max = T) of packed query strings against a resident
 // index: CSR with int64 offsets (m + 1), columns, per-query counts.

@@ -96,3 +96,15 @@ def test_batched_repertoire_limit_and_tile_method_rejected():
     assert lib.tcrnet_build_batched(chars.ctypes.data, offsets.ctypes.data, 1, None, 1,
                                     tn.HOST, 1, None, ctypes.byref(h)) == tn.EINVAL
     assert h.value is None
+
+
+@pytest.mark.parametrize("target", [1, 3, 129, -2])
+def test_partition_target_out_of_range_rejected(target):
+    lib = tn.load_library()
+    chars = np.frombuffer(b"CASSF", dtype=np.uint8)
+    offsets = np.array([0, 5], dtype=np.int64)
+    opt = tn.make_options("deletion", partition_target=target)
+    h = ctypes.c_void_p()
+    assert lib.tcrnet_build_flat(chars.ctypes.data, offsets.ctypes.data, 1, tn.HOST, 1, ctypes.byref(opt),
+                                 ctypes.byref(h)) == tn.EINVAL
+    assert h.value is None

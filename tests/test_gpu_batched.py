@@ -111,3 +111,24 @@ def test_batched_many_repertoires_on_device_inputs():
     rep_of = np.repeat(np.arange(len(reps)), np.diff(bounds))
     rows = np.repeat(np.arange(flat.n), np.diff(np.asarray(off, dtype=np.int64)))
     assert np.array_equal(rep_of[rows], rep_of[np.asarray(cols, dtype=np.int64)])
+
+
+def test_autotuned_builds_equal_default_builds():
+    from paper_2112_06613_b300.autotune import PartitionTuner
+
+    reps = generate_batched(12, seed=13, lo=200, hi=20_000)
+    flat, bounds = concat(reps)
+    tuner = PartitionTuner(candidates=(12, 24, 40), trials=1)
+    with tn.tcrnet_build_batched(flat.chars, flat.offsets, bounds, 1) as g:
+        ref = g.copy_csr()
+    with tuner.build(flat.chars, flat.offsets, 1, rep_offsets=bounds) as g:
+        got = g.copy_csr()
+    assert set(tuner.last_timings) == {12, 24, 40}
+    assert_csr_equal(got[0], got[1], ref[0], ref[1], "tuned batched vs default")
+    one = reps[0]
+    with tn.tcrnet_build_flat(one.chars, one.offsets, 1, method="deletion") as g:
+        ref = g.copy_csr()
+    for t in (4, 7, 128):
+        with tn.tcrnet_build_flat(one.chars, one.offsets, 1, method="deletion", partition_target=t) as g:
+            got = g.copy_csr()
+        assert_csr_equal(got[0], got[1], ref[0], ref[1], f"partition_target {t}")
