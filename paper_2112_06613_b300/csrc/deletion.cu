@@ -27,18 +27,21 @@
 //       bits 31..26  p (63: the full string)
 //       bit  25      p starts a run of equal letters
 //       bits 24..0   u
-//     hash-partitioned (high hash bits, ~32 records per partition) in two
-//     passes (count, scatter).
-//  3. join: one warp per partition sorts its words in registers (bitonic
-//     network), confirms that equal hashes are equal contents (exact), and
-//     finds the edges between distinct strings: every pair inside a run of
-//     equal (hash, p) (equal length, one substitution), and each run-start
-//     deletion record with the full record of the same content (one indel).
-//     Partitions over capacity or with a hash collision take an exact
-//     quadratic fallback. The join adds m_v to W_u (and m_u to W_v) for every
-//     edge {u, v} and writes the edges into a buffer of 2 x (records bound)
-//     entries (one atomic per partition); if they do not fit, a second pass
-//     writes them at positions scanned from the per-partition counts.
+//     hash-partitioned (high hash bits, 24 or 32 records per partition on
+//     average) in two passes (count, scatter).
+//  3. join: a partition of at most 32 records is joined by one warp step
+//     without sorting (lane k holds record k; warp match on the hash gives
+//     each record its group, on (hash, p) its run); larger ones by a warp that
+//     sorts its words in registers (bitonic network). Either way equal hashes
+//     are confirmed to be equal contents (exact), and the edges between
+//     distinct strings are every pair inside a run of equal (hash, p) (equal
+//     length, one substitution) and each run-start deletion record with the
+//     full record of the same content (one indel). Partitions over capacity
+//     or with a hash collision take an exact quadratic fallback. The join adds
+//     m_v to W_u (and m_u to W_v) for every edge {u, v} and writes the edges
+//     into a buffer of 2 x (records bound) entries (staged per warp in shared
+//     memory); if they do not fit, a second pass writes them at positions
+//     scanned from the per-partition counts.
 //  4. closed neighbourhoods: D_u = m_u + W_u; S_u = M_u followed by every
 //     M_v (appended at a slot taken from a per-string cursor; long member
 //     lists are copied by a whole warp), written once per distinct string and
