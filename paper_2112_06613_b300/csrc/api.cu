@@ -215,12 +215,14 @@ void free_handle_memory(tcrnet_graph* h) {
 // Move a finished CSR (int64 offsets, cols, degree) into the handle, narrowing
 // offsets to int32 when they fit.
 tcrnet_status export_csr(tcrnet_graph* h, DevBuf& off64, DevBuf& cols, DevBuf& degree, int64_t n, int64_t nnz,
-                         bool force64, cudaStream_t s) {
+                         bool force64, cudaStream_t s, DevBuf* off32_ready = nullptr) {
     h->n = n;
     h->nnz = nnz;
     h->offsets64 = (force64 || nnz > 0x7fffffffLL) ? 1 : 0;
     if (h->offsets64) {
         h->d_offsets = off64.release();
+    } else if (off32_ready && off32_ready->as<void>()) {
+        h->d_offsets = off32_ready->release();
     } else {
         DevBuf off32;
         TCR_CHECK(off32.alloc_owned(sizeof(int32_t) * (n + 1), s));
@@ -351,7 +353,7 @@ tcrnet_status build_from_packed(tcrnet_graph* h, Packed& pk, int64_t n, int32_t 
     } else {
         DeletionResult dr;
         st = deletion_build(pk, T, dr, s, sms, opt.profile != 0, opt.partition_cap, keep_index,
-                            opt.partition_target);
+                            opt.partition_target, opt.force_offsets64 != 0);
         if (st != TCRNET_OK) return st;
         h->stats.n_unique = dr.n_unique;
         h->stats.n_records = dr.n_records;
@@ -366,7 +368,7 @@ tcrnet_status build_from_packed(tcrnet_graph* h, Packed& pk, int64_t n, int32_t 
         for (int k = 0; k < 8; ++k) h->stats.ms_phase[k] = dr.ms_phase[k];
         h->ix = dr.index;  // owned by the handle from here on
         dr.index = DeletionIndex();
-        st = export_csr(h, dr.off64, dr.cols, dr.degree, n, dr.nnz, opt.force_offsets64 != 0, s);
+        st = export_csr(h, dr.off64, dr.cols, dr.degree, n, dr.nnz, opt.force_offsets64 != 0, s, &dr.off32);
         if (st != TCRNET_OK) return st;
     }
     // keep the bucketed repertoire resident for queries

@@ -57,6 +57,17 @@ __device__ __forceinline__ Canon load_canon(const Canon* p) {
     return c;
 }
 
+// Plain (coherent, any state space) load, e.g. from shared memory; load_canon
+// above is for read-only global data only.
+__device__ __forceinline__ Canon load_canon_plain(const Canon* p) {
+    const ulonglong2* q = reinterpret_cast<const ulonglong2*>(p);
+    const ulonglong2 x = q[0];
+    const ulonglong2 y = q[1];
+    Canon c;
+    c.w[0] = x.x; c.w[1] = x.y; c.w[2] = y.x; c.w[3] = y.y;
+    return c;
+}
+
 __device__ __forceinline__ void store_canon(Canon* p, const Canon& c) {
     ulonglong2* q = reinterpret_cast<ulonglong2*>(p);
     q[0] = make_ulonglong2(c.w[0], c.w[1]);

@@ -248,6 +248,8 @@ __global__ void k_members(const int32_t* __restrict__ uid, int64_t n, const int6
 
 // ---- 2. records -----------------------------------------------------------
 
+constexpr int kRecBatch = 4;
+
 template <bool SCATTER>
 __global__ void k_records(const Canon* __restrict__ ucanon, const uint8_t* __restrict__ ulen,
                           const int64_t* __restrict__ U_ptr, int64_t n, uint32_t P, int32_t* __restrict__ pcnt,
@@ -256,18 +258,40 @@ __global__ void k_records(const Canon* __restrict__ ucanon, const uint8_t* __res
     if (u >= n || u >= *U_ptr) return;
     const Canon c = load_canon(ucanon + u);
     const int L = ulen[u];
-    for (int p = -1; p < L; ++p) {
-        const bool full = p < 0;
-        const uint64_t h = hash_canon(full ? c : delete_at(c, p));
-        const uint32_t pid = part_of(h, P);
-        if (!SCATTER) {
-            atomicAdd(&pcnt[pid], 1);
-        } else {
-            const uint64_t tag = full ? ((uint64_t)kTagF << 26)
-                                      : (((uint64_t)p << 26) | (run_start(c, p) ? (1ull << 25) : 0ull));
-            const int32_t slot = atomicAdd(&pcnt[pid], 1);
-            recs[poff[pid] + slot] = (h << 32) | tag | (uint64_t)u;
+    if constexpr (!SCATTER) {
+        for (int p = -1; p < L; ++p) {
+            const uint64_t h = hash_canon(p < 0 ? c : delete_at(c, p));
+            atomicAdd(&pcnt[part_of(h, P)], 1);
         }
+    } else {
+    // kRecBatch records at a time: their slot atomics and offset loads are
+    // independent, so they are in flight together rather than one round trip each
+    for (int p0 = -1; p0 < L; p0 += kRecBatch) {
+        uint64_t rec[kRecBatch];
+        uint32_t pid[kRecBatch];
+        int32_t slot[kRecBatch];
+        int64_t base[kRecBatch];
+#pragma unroll
+        for (int t = 0; t < kRecBatch; ++t) {
+            const int p = p0 + t;
+            const bool full = p < 0;
+            const uint64_t h = hash_canon(full ? c : delete_at(c, p < L ? p : 0));
+            pid[t] = part_of(h, P);
+            const uint64_t tag = full ? ((uint64_t)kTagF << 26)
+                                      : (((uint64_t)p << 26) | (run_start(c, p < L ? p : 0) ? (1ull << 25) : 0ull));
+            rec[t] = (h << 32) | tag | (uint64_t)u;
+        }
+#pragma unroll
+        for (int t = 0; t < kRecBatch; ++t) {
+            if (p0 + t < L) {
+                slot[t] = atomicAdd(&pcnt[pid[t]], 1);
+                base[t] = poff[pid[t]];
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < kRecBatch; ++t)
+            if (p0 + t < L) recs[base[t] + slot[t]] = rec[t];
+    }
     }
 }
 
@@ -422,7 +446,9 @@ k_join_small(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __rest
     __shared__ uint64_t sbuf[kWarps][32];
     __shared__ int32_t smul[kWarps][32];
     __shared__ int2 sstage[WRITE ? 1 : kWarps][WRITE ? 1 : kStage];
+    __shared__ Canon scanon[kWarps][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    Canon* cbuf = scanon[warp];
     uint64_t* buf = sbuf[warp];
     int32_t* mul = smul[warp];
     int2* stage = sstage[WRITE ? 0 : warp];
@@ -497,22 +523,17 @@ k_join_small(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __rest
             const bool indel = act && !isF && T >= 1 && rec_runstart(rec) && Gf != 0;
             const bool grouped = act && __popc(G) > 1;
             if (__any_sync(kFull, grouped)) {
+                // contents through shared memory (fewer shared-memory-pipe
+                // instructions than shuffling four words from two lanes)
                 Canon c;
-                c.w[0] = c.w[1] = c.w[2] = c.w[3] = 0;
                 if (grouped) {
                     if (!WRITE) mul[lane] = umult[rec_u(rec)];
                     c = record_content(rec, ucanon);
+                    store_canon(cbuf + lane, c);
                 }
-                const int lead = M ? __ffs(M) - 1 : lane;
-                const int fl = Gf ? __ffs(Gf) - 1 : lane;
-                uint64_t d1 = 0, d2 = 0;
-#pragma unroll
-                for (int w = 0; w < kCanonWords; ++w) {
-                    d1 |= __shfl_sync(kFull, c.w[w], lead) ^ c.w[w];
-                    d2 |= __shfl_sync(kFull, c.w[w], fl) ^ c.w[w];
-                }
-                if (act && !isF && __popc(M) > 1 && d1) bad = true;
-                if (indel && d2) bad = true;
+                __syncwarp();
+                if (act && !isF && __popc(M) > 1 && !canon_eq(c, load_canon_plain(cbuf + (__ffs(M) - 1)))) bad = true;
+                if (indel && !canon_eq(c, load_canon_plain(cbuf + (__ffs(Gf) - 1)))) bad = true;
             }
             __syncwarp();
             if (__any_sync(kFull, bad)) {
@@ -523,15 +544,17 @@ k_join_small(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __rest
                 __syncwarp();
                 continue;
             }
+            // prefix sum of the per-lane counts (<= 32) by bit planes: votes and
+            // population counts instead of shuffles
             const int mine = __popc(partners) + (indel ? 1 : 0);
-            int x = mine;
+            const uint32_t below = (1u << lane) - 1u;
+            int excl = 0, total = 0;
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int y = __shfl_up_sync(kFull, x, d);
-                if (lane >= d) x += y;
+            for (int b = 0; b < 6; ++b) {
+                const uint32_t plane = __ballot_sync(kFull, (mine >> b) & 1);
+                excl += __popc(plane & below) << b;
+                total += __popc(plane) << b;
             }
-            const int total = __shfl_sync(kFull, x, 31);
-            const int excl = x - mine;
             const int32_t u = (int32_t)rec_u(rec);
             if (!WRITE) {
                 if (lane == 0) pedges[pid] = total;
@@ -701,13 +724,29 @@ k_join_fallback(const int32_t* __restrict__ fb_list, const int* __restrict__ fb_
 
 // ---- 4. closed neighbourhoods ---------------------------------------------
 
-// D_u = m_u + W_u (written into wsum in place); cursor starts after M_u.
+// D_u = m_u + W_u (written into wsum in place); cursor starts after M_u;
+// the largest D_u into *dmax.
 __global__ void k_closed_size(const int32_t* __restrict__ umult, int64_t U, int32_t* __restrict__ wsum,
-                              int32_t* __restrict__ ucur) {
+                              int32_t* __restrict__ ucur, int* __restrict__ dmax) {
     const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= U) return;
-    wsum[u] += umult[u];
-    ucur[u] = umult[u];
+    int d = 0;
+    if (u < U) {
+        d = wsum[u] + umult[u];
+        wsum[u] = d;
+        ucur[u] = umult[u];
+    }
+    // block maximum, then one atomic per block
+    __shared__ int wmax[kWarps];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d = max(d, __shfl_xor_sync(kFull, d, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = d;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        d = threadIdx.x < kWarps ? wmax[threadIdx.x] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d = max(d, __shfl_xor_sync(kFull, d, o));
+        if (threadIdx.x == 0 && d > 0) atomicMax(dmax, d);
+    }
 }
 
 __global__ void k_node_degree(const int32_t* __restrict__ uid, int64_t n, const int32_t* __restrict__ dsize,
@@ -833,7 +872,7 @@ private:
 }  // namespace
 
 tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaStream_t s, int num_sms, bool profile,
-                             int partition_cap, bool keep_index, int partition_target) {
+                             int partition_cap, bool keep_index, int partition_target, bool force_off64) {
     const int64_t n = pk.n;
     if (n > kDeletionMaxN) return TCRNET_ENOTSUP;
     const int cap = (partition_cap > 0 && partition_cap < kWarpCap) ? partition_cap : kWarpCap;
@@ -846,12 +885,12 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     for (int L = 1; L <= kMaxLen; ++L) lensum += (int64_t)L * (pk.bucket_off[L + 1] - pk.bucket_off[L]);
     const int64_t R_max = n + lensum;
 
-    // device counters: [0] dedup error, [1] fill error, [2] fallback partitions;
-    // edge cursor
+    // device counters: [0] dedup error, [1] fill error, [2] fallback partitions,
+    // [3] partitions for the sorted join, [4] largest closed list; edge cursor
     DevBuf errb, ecur_b;
-    TCR_CHECK(errb.alloc(sizeof(int) * 4, s));
+    TCR_CHECK(errb.alloc(sizeof(int) * 8, s));
     TCR_CHECK(ecur_b.alloc(sizeof(unsigned long long) * (kEdgeSegs + 1), s));
-    TCR_CUDA(cudaMemsetAsync(errb.as<void>(), 0, sizeof(int) * 4, s));
+    TCR_CUDA(cudaMemsetAsync(errb.as<void>(), 0, sizeof(int) * 8, s));
     TCR_CUDA(cudaMemsetAsync(ecur_b.as<void>(), 0, sizeof(unsigned long long) * (kEdgeSegs + 1), s));
     int* d_err = errb.as<int>();
     unsigned long long* d_ecur = ecur_b.as<unsigned long long>();  // [kEdgeSegs]: single-segment count
@@ -966,7 +1005,8 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     DevBuf deg, off64;
     TCR_CHECK(deg.alloc_owned(sizeof(int32_t) * n, s));  // results are handed to the handle
     TCR_CHECK(off64.alloc_owned(sizeof(int64_t) * (n + 1), s));
-    k_closed_size<<<grid_for(n), kThreads, 0, s>>>(umult.as<int32_t>(), n, wsum.as<int32_t>(), ucur.as<int32_t>());
+    k_closed_size<<<grid_for(n), kThreads, 0, s>>>(umult.as<int32_t>(), n, wsum.as<int32_t>(), ucur.as<int32_t>(),
+                                                   d_err + 4);
     TCR_LAUNCH_CHECK();
     TCR_CHECK(scan_exclusive_i32_to_i64(wsum.as<int32_t>(), uoff.as<int64_t>(), n, s));
     k_node_degree<<<grid_for(n), kThreads, 0, s>>>(uid.as<int32_t>(), n, wsum.as<int32_t>(), deg.as<int32_t>());
@@ -974,9 +1014,11 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     TCR_CHECK(scan_exclusive_i32_to_i64(deg.as<int32_t>(), off64.as<int64_t>(), n, s));
     int64_t sizes[2] = {0, 0};  // sum of D_u, nnz
     unsigned long long segs[kEdgeSegs];
+    int h_dmax = 0;
     TCR_CUDA(cudaMemcpyAsync(&sizes[0], uoff.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TCR_CUDA(cudaMemcpyAsync(&sizes[1], off64.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TCR_CUDA(cudaMemcpyAsync(segs, d_ecur, sizeof(segs), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaMemcpyAsync(&h_dmax, d_err + 4, sizeof(int), cudaMemcpyDeviceToHost, s));
     TCR_CUDA(cudaStreamSynchronize(s));
     const int64_t SD = sizes[0], nnz = sizes[1];
     int64_t E = 0, seg_max = 0;
@@ -1035,7 +1077,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     const int t4 = tm.mark();
     if (!keep_index) recs.reset();
     edges.reset();
-    TCR_CHECK(sort_rows(uoff.as<int64_t>(), Sbuf.as<int32_t>(), n, s, num_sms));
+    TCR_CHECK(sort_rows(uoff.as<int64_t>(), Sbuf.as<int32_t>(), n, s, num_sms, h_dmax));
     const int t5 = tm.mark();
 
     // ---- 5. expand
@@ -1044,8 +1086,15 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     k_expand<<<(unsigned)std::min<int64_t>(ceil_div(n, 32 * kWarps), (int64_t)num_sms * 16), kThreads, 0, s>>>(
         uid.as<int32_t>(), n, uoff.as<int64_t>(), Sbuf.as<int32_t>(), off64.as<int64_t>(), cols.as<int32_t>());
     TCR_LAUNCH_CHECK();
+    // int32 row offsets for the handle, queued behind the expansion so that no
+    // kernel follows the final read-back
+    DevBuf off32;
+    if (!force_off64 && nnz <= 0x7fffffffLL) {
+        TCR_CHECK(off32.alloc_owned(sizeof(int32_t) * (n + 1), s));
+        TCR_CHECK(narrow_offsets(off64.as<int64_t>(), off32.as<int32_t>(), n + 1, s));
+    }
     const int t6 = tm.mark();
-    int h_err[4] = {0, 0, 0, 0};
+    int h_err[4] = {0, 0, 0, 0};  // the first four device counters
     int64_t h_U = 0, h_R = 0;
     TCR_CUDA(cudaMemcpyAsync(h_err, d_err, sizeof(h_err), cudaMemcpyDeviceToHost, s));
     TCR_CUDA(cudaMemcpyAsync(&h_U, d_U, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -1054,6 +1103,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     if (h_err[0] || h_err[1]) return TCRNET_EDEVICE;
 
     out.off64 = std::move(off64);
+    out.off32 = std::move(off32);
     out.cols = std::move(cols);
     out.degree = std::move(deg);
     out.nnz = nnz;

@@ -27,6 +27,7 @@ struct DeletionIndex {
 
 struct DeletionResult {
     DevBuf off64;   // int64[n + 1]
+    DevBuf off32;   // int32[n + 1] when nnz < 2^31 and int32 offsets were not refused
     DevBuf cols;    // int32[nnz]
     DevBuf degree;  // int32[n]
     int64_t nnz = 0;
@@ -46,7 +47,7 @@ struct DeletionResult {
 // capacity; 0 = default) take the quadratic fallback.
 tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaStream_t s, int num_sms,
                              bool profile, int partition_cap = 0, bool keep_index = false,
-                             int partition_target = 0);
+                             int partition_target = 0, bool force_off64 = false);
 
 // Neighbour lists (l_max = T) of packed query strings against a resident
 // index: CSR with int64 offsets (m + 1), columns, per-query counts.

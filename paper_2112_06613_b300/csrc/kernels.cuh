@@ -73,6 +73,10 @@ tcrnet_status neighbor_degree(const void* off, bool off64, const int32_t* cols, 
 
 // ---- rowsort.cu -----------------------------------------------------------
 // Sort every row segment cols[off[i] .. off[i+1]) ascending (values distinct).
-tcrnet_status sort_rows(const int64_t* off, int32_t* cols, int64_t n, cudaStream_t s, int num_sms);
+// max_len: an upper bound of the row lengths when the caller knows one (-1:
+// unknown; then the kernels of every class run and the host reads back how many
+// rows exceed a block's shared memory).
+tcrnet_status sort_rows(const int64_t* off, int32_t* cols, int64_t n, cudaStream_t s, int num_sms,
+                        int64_t max_len = -1);
 
 }  // namespace tcr

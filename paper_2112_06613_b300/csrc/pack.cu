@@ -102,7 +102,7 @@ __global__ void k_tag(Canon* __restrict__ canon, int64_t n, const int64_t* __res
         if (rep_off[mid] <= i) lo = mid; else hi = mid;
     }
     const uint64_t r = (uint64_t)lo;
-    Canon c = load_canon(canon + i);
+    Canon c = load_canon_plain(canon + i);  // read and rewritten here: no read-only path
 #pragma unroll
     for (int k = 0; k < kCanonWords; ++k) c.w[k] = (c.w[k] & ~kTagBits) | (((r >> (4 * k)) & 0xFull) << 60);
     store_canon(canon + i, c);

@@ -5,10 +5,17 @@
 // scheduling, i.e. bit-exact and deterministic. Values inside a row are
 // distinct node ids.
 //
-//   len <= 1024:        one warp, values in registers (K = 1..32 per lane,
+//   len <= 8:           one lane, values in registers, Batcher's odd-even
+//                       merge network for 8 (19 comparators); a warp takes 32
+//                       consecutive rows at once.
+//   9 .. 1024:          one warp, values in registers (K = 1..32 per lane,
 //                       network position lane * K + r), bitonic network:
 //                       stages with partner distance < K exchange registers,
-//                       longer ones exchange lanes by shuffle.
+//                       longer ones exchange lanes by shuffle. K = 1 stops at
+//                       the next power of two above the row length. Rows of
+//                       65..256 and 257..1024 are listed and sorted by their own
+//                       kernels, so wide register arrays do not lower the
+//                       occupancy of the kernel that sorts the many short rows.
 //   1025 .. 16384:      one 1024-thread block, shared-memory bitonic network.
 //   > 16384:            one block; 16384-value chunks sorted in shared memory,
 //                       then pairwise merges through a scratch buffer where each
@@ -22,6 +29,9 @@
 namespace tcr {
 namespace {
 
+constexpr int kLaneMax = 8;
+constexpr int kShortMax = 64;
+constexpr int kWideMax = 256;
 constexpr int kWarpCap = 1024;
 constexpr int kBlockThreads = 1024;
 constexpr int kBlockCap = 16384;
@@ -57,6 +67,28 @@ __device__ __forceinline__ void bitonic_smem(int32_t* s, int P, int t, int nthre
     }
 }
 
+__device__ __forceinline__ void cmp_swap(int32_t& a, int32_t& b) {
+    const int32_t lo = min(a, b), hi = max(a, b);
+    a = lo;
+    b = hi;
+}
+
+// Sort len <= 8 values held by one thread (Batcher's odd-even merge sort, n = 8).
+__device__ __forceinline__ void lane_sort8(int32_t* __restrict__ row, int len) {
+    int32_t v[kLaneMax];
+#pragma unroll
+    for (int t = 0; t < kLaneMax; ++t) v[t] = t < len ? row[t] : kInf;
+    cmp_swap(v[0], v[1]); cmp_swap(v[2], v[3]); cmp_swap(v[4], v[5]); cmp_swap(v[6], v[7]);
+    cmp_swap(v[0], v[2]); cmp_swap(v[1], v[3]); cmp_swap(v[4], v[6]); cmp_swap(v[5], v[7]);
+    cmp_swap(v[1], v[2]); cmp_swap(v[5], v[6]);
+    cmp_swap(v[0], v[4]); cmp_swap(v[1], v[5]); cmp_swap(v[2], v[6]); cmp_swap(v[3], v[7]);
+    cmp_swap(v[2], v[4]); cmp_swap(v[3], v[5]);
+    cmp_swap(v[1], v[2]); cmp_swap(v[3], v[4]); cmp_swap(v[5], v[6]);
+#pragma unroll
+    for (int t = 0; t < kLaneMax; ++t)
+        if (t < len) row[t] = v[t];
+}
+
 // Sort one row of len <= 32 * K values held K per lane (see the file comment).
 template <int K>
 __device__ __forceinline__ void warp_sort_regs(int32_t* __restrict__ row, int len, int lane) {
@@ -68,8 +100,12 @@ __device__ __forceinline__ void warp_sort_regs(int32_t* __restrict__ row, int le
         const int e = r * 32 + lane;
         v[r] = e < len ? row[e] : kInf;
     }
+    // K = 1: value e sits at position e, so positions >= len hold kInf and a
+    // network over the next power of two above len sorts the row
+    const int pmax = K == 1 ? next_pow2(len) : P;
 #pragma unroll
     for (int k = 2; k <= P; k <<= 1) {
+        if (k > pmax) break;
 #pragma unroll
         for (int j = k >> 1; j > 0; j >>= 1) {
             if (j < K) {
@@ -103,26 +139,53 @@ __device__ __forceinline__ void warp_sort_regs(int32_t* __restrict__ row, int le
     }
 }
 
+// Rows of at most 64 values; longer rows are listed for the kernels below.
+// A warp takes 32 consecutive rows: each lane sorts its own row when it has at
+// most 8 values, then the warp sorts the rows of 9..64 values one by one.
 __global__ void __launch_bounds__(kSortWarps * 32)
-k_sort_warp(const int64_t* __restrict__ off, int32_t* __restrict__ cols, int64_t n,
-            int32_t* __restrict__ mid, int* __restrict__ nmid, int32_t* __restrict__ big, int* __restrict__ nbig) {
+k_sort_warp(const int64_t* __restrict__ off, int32_t* __restrict__ cols, int64_t n, int32_t* __restrict__ wide,
+            int* __restrict__ nwide, int32_t* __restrict__ mid, int* __restrict__ nmid, int32_t* __restrict__ big,
+            int* __restrict__ nbig) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t gw = (int64_t)blockIdx.x * kSortWarps + warp;
     const int64_t stride = (int64_t)gridDim.x * kSortWarps;
-    for (int64_t r = gw; r < n; r += stride) {
-        const int64_t base = off[r];
-        const int64_t len64 = off[r + 1] - base;
-        const int len = len64 > (int64_t)kInf ? kInf : (int)len64;
-        if (len <= 1) continue;
-        int32_t* row = cols + base;
-        if (len <= 32) warp_sort_regs<1>(row, len, lane);
-        else if (len <= 64) warp_sort_regs<2>(row, len, lane);
-        else if (len <= 128) warp_sort_regs<4>(row, len, lane);
-        else if (len <= 256) warp_sort_regs<8>(row, len, lane);
-        else if (lane == 0) {
-            if (len <= kWarpCap) mid[atomicAdd(nmid, 1)] = (int32_t)r;
-            else big[atomicAdd(nbig, 1)] = (int32_t)r;
+    for (int64_t r0 = gw * 32; r0 < n; r0 += stride * 32) {
+        const int64_t r = r0 + lane;
+        int64_t base = 0;
+        int len = 0;
+        if (r < n) {
+            base = off[r];
+            const int64_t len64 = off[r + 1] - base;
+            len = len64 > (int64_t)kInf ? kInf : (int)len64;
         }
+        if (len >= 2 && len <= kLaneMax) lane_sort8(cols + base, len);
+        else if (len > kWarpCap) big[atomicAdd(nbig, 1)] = (int32_t)r;
+        else if (len > kWideMax) mid[atomicAdd(nmid, 1)] = (int32_t)r;
+        else if (len > kShortMax) wide[atomicAdd(nwide, 1)] = (int32_t)r;
+        uint32_t todo = __ballot_sync(kFull, len > kLaneMax && len <= kShortMax);
+        while (todo) {
+            const int j = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t b = __shfl_sync(kFull, base, j);
+            const int l = __shfl_sync(kFull, len, j);
+            if (l <= 32) warp_sort_regs<1>(cols + b, l, lane);
+            else warp_sort_regs<2>(cols + b, l, lane);
+        }
+    }
+}
+
+// Rows of 65..256 values (listed by k_sort_warp).
+__global__ void __launch_bounds__(kSortWarps * 32)
+k_sort_warp_wide(const int64_t* __restrict__ off, int32_t* __restrict__ cols, const int32_t* __restrict__ rows,
+                 const int* __restrict__ nrows) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int count = *nrows;
+    for (int64_t k = (int64_t)blockIdx.x * kSortWarps + warp; k < count; k += (int64_t)gridDim.x * kSortWarps) {
+        const int64_t r = rows[k];
+        const int64_t base = off[r];
+        const int len = (int)(off[r + 1] - base);
+        if (len <= 128) warp_sort_regs<4>(cols + base, len, lane);
+        else warp_sort_regs<8>(cols + base, len, lane);
     }
 }
 
@@ -201,27 +264,38 @@ __global__ void k_merge_runs(const int32_t* __restrict__ src, int32_t* __restric
 
 }  // namespace
 
-tcrnet_status sort_rows(const int64_t* off, int32_t* cols, int64_t n, cudaStream_t s, int num_sms) {
+tcrnet_status sort_rows(const int64_t* off, int32_t* cols, int64_t n, cudaStream_t s, int num_sms, int64_t max_len) {
     if (n <= 0) return TCRNET_OK;
-    // lists: [0, n) rows of 257..1024, [n, 2n) rows above 1024, [2n, 3n) rows above kBlockCap
+    // lists: [0, n) rows of 257..1024, [n, 2n) rows above 1024, [2n, 3n) rows
+    // above kBlockCap, [3n, 4n) rows of 65..256; counts in the same order
     DevBuf lists, counts;
-    TCR_CHECK(lists.alloc(sizeof(int32_t) * 3 * n, s));
-    TCR_CHECK(counts.alloc(sizeof(int) * 3, s));
-    TCR_CUDA(cudaMemsetAsync(counts.as<void>(), 0, sizeof(int) * 3, s));
+    TCR_CHECK(lists.alloc(sizeof(int32_t) * 4 * n, s));
+    TCR_CHECK(counts.alloc(sizeof(int) * 4, s));
+    TCR_CUDA(cudaMemsetAsync(counts.as<void>(), 0, sizeof(int) * 4, s));
     int32_t* mid = lists.as<int32_t>();
     int32_t* big = mid + n;
     int32_t* huge_list = big + n;
+    int32_t* wide = huge_list + n;
     int* cnt = counts.as<int>();
-    const int64_t blocks = std::min<int64_t>(ceil_div(n, kSortWarps), (int64_t)num_sms * 64);
-    k_sort_warp<<<(unsigned)blocks, kSortWarps * 32, 0, s>>>(off, cols, n, mid, cnt, big, cnt + 1);
+    const int64_t blocks = std::min<int64_t>(ceil_div(n, 32 * kSortWarps), (int64_t)num_sms * 16);
+    k_sort_warp<<<(unsigned)blocks, kSortWarps * 32, 0, s>>>(off, cols, n, wide, cnt + 3, mid, cnt, big, cnt + 1);
     TCR_LAUNCH_CHECK();
-    k_sort_warp_mid<<<num_sms * 4, kSortWarps * 32, 0, s>>>(off, cols, mid, cnt);
-    TCR_LAUNCH_CHECK();
+    const bool known = max_len >= 0;  // a known bound skips the kernels of longer classes
+    if (!known || max_len > kShortMax) {
+        k_sort_warp_wide<<<num_sms * 8, kSortWarps * 32, 0, s>>>(off, cols, wide, cnt + 3);
+        TCR_LAUNCH_CHECK();
+    }
+    if (!known || max_len > kWideMax) {
+        k_sort_warp_mid<<<num_sms * 4, kSortWarps * 32, 0, s>>>(off, cols, mid, cnt);
+        TCR_LAUNCH_CHECK();
+    }
+    if (known && max_len <= kWarpCap) return TCRNET_OK;
     const size_t smem = sizeof(int32_t) * kBlockCap;
     TCR_CUDA(cudaFuncSetAttribute(k_sort_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     TCR_CUDA(cudaFuncSetAttribute(k_sort_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_sort_block<<<num_sms * 2, kBlockThreads, smem, s>>>(off, cols, big, cnt + 1, huge_list, cnt + 2);
     TCR_LAUNCH_CHECK();
+    if (known && max_len <= kBlockCap) return TCRNET_OK;  // no row can be listed as huge
     int h_huge = 0;
     TCR_CUDA(cudaMemcpyAsync(&h_huge, cnt + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
     TCR_CUDA(cudaStreamSynchronize(s));
