@@ -19,7 +19,8 @@
 //
 // Pipeline:
 //  1. dedup: open-addressing hash table of the packed strings (slot claimed by
-//     atomicCAS, exact comparison on probe) -> distinct-string ids u,
+//     atomicCAS, exact comparison on probe; the claiming thread numbers the
+//     new distinct string) -> distinct-string ids u,
 //     multiplicities m_u, member lists M_u.
 //  2. records: per distinct string one full-string record (tag p = 63) and one
 //     record per deletion position p; each is one 64-bit word
@@ -188,18 +189,29 @@ __device__ __forceinline__ int64_t warp_scan(int64_t v, int64_t& excl, int lane)
 
 // ---- 1. dedup -------------------------------------------------------------
 
-__global__ void k_dedup_insert(const Canon* __restrict__ canon, int64_t n, int32_t* __restrict__ table,
-                               uint32_t mask, int32_t* __restrict__ slot_of, int32_t* __restrict__ scount,
-                               int* __restrict__ err) {
+// Claim or find the table slot of each string. The claiming thread numbers
+// the new distinct string (u = running count; the numbering depends on the
+// schedule, the network does not) and copies it to ucanon/ulen.
+__global__ void k_dedup_insert(const Canon* __restrict__ canon, const uint8_t* __restrict__ lens, int64_t n,
+                               int32_t* __restrict__ table, uint32_t mask, int32_t* __restrict__ slot_of,
+                               int32_t* __restrict__ slot_u, unsigned long long* __restrict__ U,
+                               Canon* __restrict__ ucanon, uint8_t* __restrict__ ulen, int* __restrict__ err) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const Canon c = load_canon(canon + i);
     uint32_t slot = (uint32_t)hash_canon(c) & mask;
     for (uint32_t probe = 0; probe <= mask; ++probe) {
         const int32_t r = atomicCAS(&table[slot], -1, (int32_t)i);
-        if (r == -1 || canon_eq(load_canon(canon + r), c)) {
+        if (r == -1) {
+            const int32_t u = (int32_t)atomicAdd(U, 1ull);
+            slot_u[slot] = u;
+            store_canon(ucanon + u, c);
+            ulen[u] = lens[i];
             slot_of[i] = (int32_t)slot;
-            atomicAdd(&scount[slot], 1);
+            return;
+        }
+        if (canon_eq(load_canon(canon + r), c)) {
+            slot_of[i] = (int32_t)slot;
             return;
         }
         slot = (slot + 1) & mask;
@@ -208,30 +220,15 @@ __global__ void k_dedup_insert(const Canon* __restrict__ canon, int64_t n, int32
     slot_of[i] = -1;
 }
 
-__global__ void k_occupied(const int32_t* __restrict__ scount, int64_t S, int32_t* __restrict__ flag) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < S) flag[k] = scount[k] > 0 ? 1 : 0;
-}
-
-__global__ void k_unique_compact(const int32_t* __restrict__ scount, const int32_t* __restrict__ table,
-                                 const int64_t* __restrict__ ubase, int64_t S, const Canon* __restrict__ canon,
-                                 const uint8_t* __restrict__ lens, Canon* __restrict__ ucanon,
-                                 uint8_t* __restrict__ ulen, int32_t* __restrict__ umult) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= S || scount[k] == 0) return;
-    const int64_t u = ubase[k];
-    const int32_t rep = table[k];
-    store_canon(ucanon + u, load_canon(canon + rep));
-    ulen[u] = lens[rep];
-    umult[u] = scount[k];
-}
-
-__global__ void k_uid(const int32_t* __restrict__ slot_of, const int64_t* __restrict__ ubase, int64_t n,
-                      int32_t* __restrict__ uid) {
+// Distinct-string id of every node and the multiplicities m_u.
+__global__ void k_uid(const int32_t* __restrict__ slot_of, const int32_t* __restrict__ slot_u, int64_t n,
+                      int32_t* __restrict__ uid, int32_t* __restrict__ umult) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         const int32_t slot = slot_of[i];
-        uid[i] = slot >= 0 ? (int32_t)ubase[slot] : 0;  // slot < 0 only with the dedup error flag set
+        const int32_t u = slot >= 0 ? slot_u[slot] : 0;  // slot < 0 only with the dedup error flag set
+        uid[i] = u;
+        atomicAdd(&umult[u], 1);
     }
 }
 
@@ -807,9 +804,12 @@ k_closed_edges(const int2* __restrict__ edges, int64_t seg_cap, const unsigned l
 // ---- 5. expand --------------------------------------------------------------
 
 // Row i = sorted S_u without i. A warp takes 32 rows: each lane fetches one
-// row's list bounds (independent loads in parallel), then the warp copies the
-// rows one after another, lanes along the row. S_u is sorted and contains i
-// once, so element x at position k goes to k - (x > i).
+// row's list bounds (independent loads in parallel); rows of at most
+// kLaneRow entries are copied by their own lane, longer ones by the whole warp
+// one after another, lanes along the row. S_u is sorted and contains i once,
+// so element x at position k goes to k - (x > i).
+constexpr int kLaneRow = 16;
+
 __global__ void k_expand(const int32_t* __restrict__ uid, int64_t n, const int64_t* __restrict__ uoff,
                          const int32_t* __restrict__ S, const int64_t* __restrict__ off, int32_t* __restrict__ cols) {
     const int lane = threadIdx.x & 31;
@@ -824,8 +824,20 @@ __global__ void k_expand(const int32_t* __restrict__ uid, int64_t n, const int64
             D = uoff[u + 1] - s0;
             o = off[my];
         }
-        const int cnt = (n - r0) < 32 ? (int)(n - r0) : 32;
-        for (int j = 0; j < cnt; ++j) {
+        if (D >= 2 && D <= kLaneRow + 1) {
+            const int32_t me = (int32_t)my;
+            const int32_t* su = S + s0;
+            int32_t* row = cols + o;
+            int q = 0;
+            for (int k = 0; k < (int)D; ++k) {
+                const int32_t x = su[k];
+                if (x != me && q < (int)D - 1) row[q++] = x;
+            }
+        }
+        uint32_t todo = __ballot_sync(kFull, D > kLaneRow + 1);
+        while (todo) {
+            const int j = __ffs(todo) - 1;
+            todo &= todo - 1;
             const int64_t js0 = __shfl_sync(kFull, s0, j);
             const int64_t jD = __shfl_sync(kFull, D, j);
             const int64_t jo = __shfl_sync(kFull, o, j);
@@ -901,22 +913,14 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     // ---- 1. dedup
     int64_t S = 1024;
     while (S < 2 * n) S <<= 1;
-    DevBuf table, slot_of, scount, flag, ubase;
+    DevBuf table, slot_of, slot_u, ucount;
     TCR_CHECK(table.alloc(sizeof(int32_t) * S, s));
     TCR_CHECK(slot_of.alloc(sizeof(int32_t) * n, s));
-    TCR_CHECK(scount.alloc(sizeof(int32_t) * S, s));
-    TCR_CHECK(flag.alloc(sizeof(int32_t) * S, s));
-    TCR_CHECK(ubase.alloc(sizeof(int64_t) * (S + 1), s));
+    TCR_CHECK(slot_u.alloc(sizeof(int32_t) * S, s));
+    TCR_CHECK(ucount.alloc(sizeof(int64_t), s));
     TCR_CUDA(cudaMemsetAsync(table.as<void>(), 0xff, sizeof(int32_t) * S, s));
-    TCR_CUDA(cudaMemsetAsync(scount.as<void>(), 0, sizeof(int32_t) * S, s));
-    k_dedup_insert<<<grid_for(n), kThreads, 0, s>>>(pk.canon_in.as<Canon>(), n, table.as<int32_t>(),
-                                                    (uint32_t)(S - 1), slot_of.as<int32_t>(), scount.as<int32_t>(),
-                                                    d_err);
-    TCR_LAUNCH_CHECK();
-    k_occupied<<<grid_for(S), kThreads, 0, s>>>(scount.as<int32_t>(), S, flag.as<int32_t>());
-    TCR_LAUNCH_CHECK();
-    TCR_CHECK(scan_exclusive_i32_to_i64(flag.as<int32_t>(), ubase.as<int64_t>(), S, s));
-    const int64_t* d_U = ubase.as<int64_t>() + S;  // number of distinct strings, on the device
+    TCR_CUDA(cudaMemsetAsync(ucount.as<void>(), 0, sizeof(int64_t), s));
+    const int64_t* d_U = ucount.as<int64_t>();  // number of distinct strings, on the device
     DevBuf ucanon, ulen, umult, uid, mem_off, mcur, members, mpos;
     if (keep_index) TCR_CHECK(ucanon.alloc_owned(sizeof(Canon) * n, s));
     else TCR_CHECK(ucanon.alloc(sizeof(Canon) * n, s));
@@ -931,11 +935,13 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     else TCR_CHECK(members.alloc(sizeof(int32_t) * n, s));
     TCR_CHECK(mpos.alloc(sizeof(int32_t) * n, s));
     TCR_CUDA(cudaMemsetAsync(umult.as<void>(), 0, sizeof(int32_t) * n, s));  // ids >= U stay 0
-    k_unique_compact<<<grid_for(S), kThreads, 0, s>>>(scount.as<int32_t>(), table.as<int32_t>(), ubase.as<int64_t>(),
-                                                      S, pk.canon_in.as<Canon>(), pk.lens.as<uint8_t>(),
-                                                      ucanon.as<Canon>(), ulen.as<uint8_t>(), umult.as<int32_t>());
+    k_dedup_insert<<<grid_for(n), kThreads, 0, s>>>(
+        pk.canon_in.as<Canon>(), pk.lens.as<uint8_t>(), n, table.as<int32_t>(), (uint32_t)(S - 1),
+        slot_of.as<int32_t>(), slot_u.as<int32_t>(), reinterpret_cast<unsigned long long*>(ucount.as<int64_t>()),
+        ucanon.as<Canon>(), ulen.as<uint8_t>(), d_err);
     TCR_LAUNCH_CHECK();
-    k_uid<<<grid_for(n), kThreads, 0, s>>>(slot_of.as<int32_t>(), ubase.as<int64_t>(), n, uid.as<int32_t>());
+    k_uid<<<grid_for(n), kThreads, 0, s>>>(slot_of.as<int32_t>(), slot_u.as<int32_t>(), n, uid.as<int32_t>(),
+                                           umult.as<int32_t>());
     TCR_LAUNCH_CHECK();
     TCR_CHECK(scan_exclusive_i32_to_i64(umult.as<int32_t>(), mem_off.as<int64_t>(), n, s));
     TCR_CUDA(cudaMemsetAsync(mcur.as<void>(), 0, sizeof(int32_t) * n, s));
