@@ -415,7 +415,8 @@ __device__ __forceinline__ int64_t record_edges_checked(const uint64_t* buf, int
 
 // Join of the partitions of at most 32 records, without sorting. Lane k holds
 // record k; __match_any_sync on the 32-bit hash gives each lane its hash group
-// G, on (hash, p) its run M. Same-position partners are the lanes of M above
+// G, and G intersected with a match on p its run M of equal (hash, p) (two
+// 32-bit matches cost less than one on the 38-bit pair, measured). Same-position partners are the lanes of M above
 // this one (each pair once); a run-start deletion pairs with the group's full
 // record. Exactness as in the sorted path: every attempted pair is confirmed
 // by content, a group with two full records (two different contents under one
@@ -512,7 +513,7 @@ k_join_small(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __rest
             buf[lane] = rec;
             const uint32_t amask = (s >= 32) ? kFull : ((1u << s) - 1u);
             const uint32_t G = __match_any_sync(kFull, (uint32_t)(rec >> 32)) & amask;
-            const uint32_t M = __match_any_sync(kFull, (unsigned long long)(rec >> 26)) & amask;
+            const uint32_t M = G & __match_any_sync(kFull, rec_p(rec));  // same hash and same p
             const bool isF = rec_p(rec) == kTagF;
             const uint32_t Gf = G & __ballot_sync(kFull, act && isF);
             bool bad = act && __popc(Gf) > 1;
