@@ -66,6 +66,8 @@ def parse_args():
     ap.add_argument("--n", type=int, default=800_000)
     ap.add_argument("--method", default="auto", choices=["auto", "deletion", "tile"])
     ap.add_argument("--tile-steps", type=int, default=2)
+    ap.add_argument("--phase-steps", type=int, default=20,
+                    help="profiled builds after the timed region, for the per-phase times")
     ap.add_argument("--query-batches", type=int, default=30)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -456,7 +458,7 @@ def run_ours(args):
     for k in range(args.steps):
         flush.fill_(k & 0xff)
         evs[k][0].record(stream)
-        g = build()
+        g = build(profile=False)
         evs[k][1].record(stream)
         stats.append(g.stats())
         g.free()
@@ -472,15 +474,26 @@ def run_ours(args):
     edges = st0["nnz"] / 2
     ms, value, edges_per_s = aggregate_ranks(statistics.mean(step_ms), pairs_per_build, edges, world, dist, dev)
     launches = int(sum(s["kernel_launches"] for s in stats))
+    # per-phase times: the same build with CUDA-event marks between its phases,
+    # run after the timed region (the marks cost ~45 us per build, so the timed
+    # builds run without them)
+    pstats = []
+    for k in range(max(args.phase_steps, 1)):
+        flush.fill_(k & 0xff)
+        g = build(profile=True)
+        pstats.append(g.stats())
+        g.free()
+    torch.cuda.synchronize()
 
     is_tile = st0["method"] == 1
     # dominant phase of the step and its algorithmic bytes
     names = ["dedup", "records", "join_weigh", "join_fill", "unused", "list_sort", "expand"]
-    phase_ms = {nm: statistics.mean(s["ms_phase"][i] for s in stats) for i, nm in enumerate(names) if nm != "unused"}
+    phase_ms = {nm: statistics.mean(s["ms_phase"][i] for s in pstats) for i, nm in enumerate(names) if nm != "unused"}
+    phase_ms["pack"] = statistics.mean(s["ms_pack"] for s in pstats)
     if is_tile:
-        phase_ms = {"count_pass": statistics.mean(s["ms_count"] for s in stats),
-                    "write_pass": statistics.mean(s["ms_write"] for s in stats),
-                    "row_sort": statistics.mean(s["ms_sort"] for s in stats)}
+        phase_ms = {"count_pass": statistics.mean(s["ms_count"] for s in pstats),
+                    "write_pass": statistics.mean(s["ms_write"] for s in pstats),
+                    "row_sort": statistics.mean(s["ms_sort"] for s in pstats)}
     dom = max(phase_ms, key=phase_ms.get)
     nnz = st0["nnz"]
     U, R, E, SD = st0["n_unique"], st0["n_records"], st0["unique_edges"], st0["closed_total"]
@@ -491,6 +504,8 @@ def run_ours(args):
         "join_weigh": 8 * R,                              # read records
         "records": 32 * U + 8 * R,                        # read strings, scatter records
         "dedup": 32 * n + 32 * U + 8 * n,
+        # read chars and offsets; write codes and lengths; bucketed copy (read, write codes + order)
+        "pack": int(rep.chars.nbytes) + 8 * (n + 1) + 33 * n + 33 * n + 36 * n,
     }[dom]
     achieved = alg_bytes / (phase_ms[dom] / 1e3) / 1e9
     if is_tile:

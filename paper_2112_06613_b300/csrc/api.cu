@@ -63,6 +63,37 @@ thread_local DeviceArena* t_arena = nullptr;
 
 bool arena_active() { return t_arena != nullptr; }
 
+namespace {
+std::mutex g_event_mu;
+std::vector<cudaEvent_t> g_event_pool[64];
+}  // namespace
+
+cudaEvent_t event_acquire() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_event_mu);
+        if (!g_event_pool[dev].empty()) {
+            cudaEvent_t e = g_event_pool[dev].back();
+            g_event_pool[dev].pop_back();
+            return e;
+        }
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+void event_release(cudaEvent_t e) {
+    int dev = 0;
+    if (!e || cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        if (e) cudaEventDestroy(e);
+        return;
+    }
+    std::lock_guard<std::mutex> lk(g_event_mu);
+    g_event_pool[dev].push_back(e);
+}
+
 void* arena_carve(size_t bytes, cudaError_t* err) {
     DeviceArena* a = t_arena;
     if (!a) return nullptr;
@@ -151,33 +182,7 @@ void configure_pool(int dev) {
 }
 
 // CUDA-event phase timer (active only with options.profile).
-class Phases {
-public:
-    Phases(bool on, cudaStream_t s) : on_(on), s_(s) {}
-    ~Phases() {
-        for (auto e : ev_) cudaEventDestroy(e);
-    }
-    int mark() {
-        if (!on_) return -1;
-        cudaEvent_t e;
-        if (cudaEventCreate(&e) != cudaSuccess) return -1;
-        cudaEventRecord(e, s_);
-        ev_.push_back(e);
-        return (int)ev_.size() - 1;
-    }
-    double ms(int a, int b) {
-        if (!on_ || a < 0 || b < 0) return 0.0;
-        cudaEventSynchronize(ev_[b]);
-        float t = 0.f;
-        cudaEventElapsedTime(&t, ev_[a], ev_[b]);
-        return (double)t;
-    }
-
-private:
-    bool on_;
-    cudaStream_t s_;
-    std::vector<cudaEvent_t> ev_;
-};
+using Phases = EventMarks;
 
 int sm_count(int dev) {
     int v = 148;

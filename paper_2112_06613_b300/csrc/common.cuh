@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 #include <cstdio>
 
 #include "tcrnet.h"
@@ -125,6 +126,42 @@ int64_t launches_so_far();
 // Buffers handed to a handle are never carved from the arena.
 void* arena_carve(size_t bytes, cudaError_t* err);  // nullptr: no lease on this thread
 bool arena_active();
+
+// Events for the optional phase timing, recycled through a per-device pool so
+// that a profiled build does not create and destroy events on its critical path.
+cudaEvent_t event_acquire();          // an event of the current device
+void event_release(cudaEvent_t e);    // back to the current device's pool
+
+// CUDA-event marks on one stream (no-op when off); ms(a, b) waits for mark b.
+class EventMarks {
+public:
+    EventMarks(bool on, cudaStream_t s) : on_(on), s_(s) {}
+    ~EventMarks() {
+        for (auto e : ev_) event_release(e);
+    }
+    EventMarks(const EventMarks&) = delete;
+    EventMarks& operator=(const EventMarks&) = delete;
+    int mark() {
+        if (!on_) return -1;
+        cudaEvent_t e = event_acquire();
+        if (!e) return -1;
+        cudaEventRecord(e, s_);
+        ev_.push_back(e);
+        return (int)ev_.size() - 1;
+    }
+    double ms(int a, int b) {
+        if (!on_ || a < 0 || b < 0) return 0.0;
+        cudaEventSynchronize(ev_[b]);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, ev_[a], ev_[b]);
+        return (double)t;
+    }
+
+private:
+    bool on_;
+    cudaStream_t s_;
+    std::vector<cudaEvent_t> ev_;
+};
 
 class ArenaLease {
 public:

@@ -854,33 +854,7 @@ __global__ void k_expand(const int32_t* __restrict__ uid, int64_t n, const int64
     }
 }
 
-class Timer {
-public:
-    Timer(bool on, cudaStream_t s) : on_(on), s_(s) {}
-    ~Timer() {
-        for (auto e : ev_) cudaEventDestroy(e);
-    }
-    int mark() {
-        if (!on_) return -1;
-        cudaEvent_t e;
-        if (cudaEventCreate(&e) != cudaSuccess) return -1;
-        cudaEventRecord(e, s_);
-        ev_.push_back(e);
-        return (int)ev_.size() - 1;
-    }
-    double ms(int a, int b) {
-        if (!on_ || a < 0 || b < 0) return 0.0;
-        cudaEventSynchronize(ev_[b]);
-        float t = 0.f;
-        cudaEventElapsedTime(&t, ev_[a], ev_[b]);
-        return (double)t;
-    }
-
-private:
-    bool on_;
-    cudaStream_t s_;
-    std::vector<cudaEvent_t> ev_;
-};
+using Timer = EventMarks;
 
 }  // namespace
 
