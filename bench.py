@@ -54,6 +54,15 @@ SMS = 148
 INT_LANES_PER_SM = 128
 
 
+# DRAM bytes (read + write) per build of the phase's kernels at N = 800,000,
+# from one ncu capture of the current kernels (profiles/k_join_small_n800000.md,
+# profiles/k_records_expand_n800000.md); None where no capture covers the phase.
+PHASE_TRAFFIC_N800000 = {
+    "join_weigh": 100.30e6 + 5.87e6 + 21.84e6 + 0.03e6,
+    "records": 21.91e6 + 86.57e6 + 105.64e6,
+    "expand": 84.27e6 + 199.98e6,
+}
+
 LEGS = ("tile", "query", "e2e", "analytics", "lmax2", "batched", "serving", "cpu")
 
 
@@ -514,9 +523,11 @@ def run_ours(args):
         ach = ops / (phase_ms[dom] / 1e3)
         roofline_tile = {"bound": "alu", "kernel_phase": dom, "achieved": ach / 1e12, "peak": peak_ops / 1e12,
                          "unit": "Tops/s", "frac": ach / peak_ops, "traffic": None, "ms_per_launch": phase_ms[dom]}
+    traffic = PHASE_TRAFFIC_N800000.get(dom) if (n == 800_000 and not is_tile) else None
     roofline = {"bound": "hbm", "kernel_phase": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs",
-                "alg_bytes_per_launch": alg_bytes, "ms_per_launch": phase_ms[dom]}
+                "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": f"{peak_kind} hbm_gbs",
+                "alg_bytes_per_launch": alg_bytes, "ms_per_launch": phase_ms[dom],
+                "traffic_source": "ncu DRAM bytes of the phase's kernels, one capture (profiles/)" if traffic else None}
     if is_tile:
         roofline = roofline_tile
 
