@@ -340,7 +340,7 @@ def serve_leg(args, tn, torch, stream):
         "query_strings_per_s": sum(r.n_strings for r in qs) / wall,
         "device_calls": len({r.batch_id for r in reqs}),
         "plain_build_ms_at_start": plain_build_ms,
-        "engine": "4 slots (streams), queued queries merged up to 200,000 strings per call, inserts exclusive, "
+        "engine": "4 slots (streams), queued queries merged up to 200,000 strings per call, inserts copy-on-write on low-priority streams, "
                   "admission by free HBM",
     }
 

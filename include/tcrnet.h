@@ -219,6 +219,18 @@ tcrnet_status tcrnet_insert_ex(tcrnet_handle h, const uint8_t *chars, const int6
 tcrnet_status tcrnet_insert(tcrnet_handle h, const char *const *seqs, int64_t m);
 
 /*
+ * Copy-on-write insert: a NEW handle whose network is that of h's strings
+ * followed by the m new strings (ids n, n+1, ... as with tcrnet_insert); h is
+ * not modified and only read, so queries on h may continue on other host
+ * threads and streams while the new network is built (h's reads are of memory
+ * that no call modifies). The caller swaps handles when it returns and frees
+ * the old one after its last query. Same arguments and errors as
+ * tcrnet_insert_ex; on error *out = NULL. m = 0 gives a rebuilt copy.
+ */
+tcrnet_status tcrnet_extend(tcrnet_handle h, const uint8_t *chars, const int64_t *offsets, int64_t m, int32_t mem,
+                            const tcrnet_options *opt, tcrnet_handle *out);
+
+/*
  * Connected components of the network restricted to the nodes with keep[i] != 0
  * (keep == NULL keeps every node): node removal of the robustness analysis
  * (Methods "Computing LCC"; the caller draws which nodes are removed). labels

@@ -99,7 +99,7 @@ SYMBOLS = [
     "tcrnet_strerror", "tcrnet_last_error_index", "tcrnet_version", "tcrnet_last_cuda_error",
     "tcrnet_degree_noalloc", "tcrnet_query_ex", "tcrnet_insert_flat", "tcrnet_insert_ex", "tcrnet_insert",
     "tcrnet_components", "tcrnet_neighbor_degree", "tcrnet_build_batched",
-    "tcrnet_degree_histogram",
+    "tcrnet_degree_histogram", "tcrnet_extend",
 ]
 
 
@@ -132,6 +132,8 @@ def load_library(path: str = LIB_PATH):
         lib.tcrnet_csr_device.restype = ctypes.c_int
         lib.tcrnet_query_flat.argtypes = [H, vp, vp, i64, i32, HP]
         lib.tcrnet_query_flat.restype = ctypes.c_int
+        lib.tcrnet_extend.argtypes = [H, vp, vp, i64, i32, optp, HP]
+        lib.tcrnet_extend.restype = ctypes.c_int
         lib.tcrnet_degree_histogram.argtypes = [H, vp, i64, i32, ctypes.POINTER(i64)]
         lib.tcrnet_degree_histogram.restype = ctypes.c_int
         lib.tcrnet_build_batched.argtypes = [vp, vp, i64, vp, i64, i32, i32, optp, HP]
@@ -207,15 +209,34 @@ def make_options(method="auto", device=None, stream=None, profile=False, force_o
 class Graph:
     """Owns one tcrnet handle: a CSR (n rows) in device memory."""
 
-    def __init__(self, handle: int):
+    def __init__(self, handle: int, owned: bool = True):
         self._h = ctypes.c_void_p(handle)
+        self._owned = owned
+
+    @classmethod
+    def borrowed(cls, handle: int) -> "Graph":
+        """A view of a handle owned elsewhere (free() leaves it alone)."""
+        return cls(handle, owned=False)
 
     @property
     def handle(self):
         return self._h
 
+    def release(self) -> int:
+        """Give up ownership; returns the raw handle (the caller frees it with tcrnet_free)."""
+        h = self._h.value if self._h is not None else None
+        self._h = None
+        return h
+
+    def adopt(self, handle: int) -> int | None:
+        """Take ownership of `handle`; returns the previously held raw handle, not freed."""
+        old = self._h.value if (self._h is not None and self._owned) else None
+        self._h = ctypes.c_void_p(handle)
+        self._owned = True
+        return old
+
     def free(self):
-        if self._h is not None and self._h.value:
+        if self._owned and self._h is not None and self._h.value:
             load_library().tcrnet_free(self._h)
         self._h = None
 
@@ -324,6 +345,18 @@ class Graph:
         st = lib.tcrnet_insert_ex(self._h, cp, op, m, mem, ctypes.byref(opt))
         del keep
         _check(st, "tcrnet_insert_ex")
+
+    def extend_flat(self, chars, offsets, stream=None, profile=False) -> "Graph":
+        """Copy-on-write insert: a new Graph of this one's strings plus the new ones;
+        this Graph is unchanged and may keep serving queries meanwhile."""
+        lib = load_library()
+        cp, op, m, mem, keep = _flat_args(chars, offsets)
+        opt = make_options(stream=stream, profile=profile)
+        h = ctypes.c_void_p()
+        st = lib.tcrnet_extend(self._h, cp, op, m, mem, ctypes.byref(opt), ctypes.byref(h))
+        del keep
+        _check(st, "tcrnet_extend")
+        return Graph(h.value)
 
     def query_flat(self, chars, offsets, method="auto", stream=None):
         if method == "auto" and stream is None:

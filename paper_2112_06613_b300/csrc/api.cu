@@ -620,12 +620,16 @@ tcrnet_status tcrnet_query(tcrnet_handle h, const char* const* queries, int64_t 
     return tcrnet_query_flat(h, chars.data(), offs.data(), m, TCRNET_HOST, out);
 }
 
-tcrnet_status tcrnet_insert_ex(tcrnet_handle h, const uint8_t* chars, const int64_t* offsets, int64_t m, int32_t mem,
-                               const tcrnet_options* opt_in) {
-    t_last_bad = -1;
-    if (!h || m < 0) return TCRNET_EINVAL;
-    if (h->query_result || h->batched) return TCRNET_ESTATE;
-    if (m == 0) return TCRNET_OK;
+}  // extern "C"
+
+namespace tcr {
+namespace {
+
+// The network of h's strings followed by m new ones, as a new graph; h is only
+// read (its resident strings), so queries on h may run meanwhile on other streams.
+tcrnet_status extend_impl(tcrnet_handle h, const uint8_t* chars, const int64_t* offsets, int64_t m, int32_t mem,
+                          const tcrnet_options* opt_in, tcrnet_graph** out) {
+    *out = nullptr;
     const int64_t n_old = h->n;
     const int64_t N = n_old + m;
     if (N > 0x7fffffffLL) return TCRNET_EINVAL;
@@ -681,11 +685,47 @@ tcrnet_status tcrnet_insert_ex(tcrnet_handle h, const uint8_t* chars, const int6
         delete g;
         return st;  // the handle keeps its previous network
     }
-    free_handle_memory(h);
     g->stats.nnz = g->nnz;
     g->stats.kernel_launches = launches_so_far() - launches0;
+    *out = g;
+    return TCRNET_OK;
+}
+
+}  // namespace
+}  // namespace tcr
+
+extern "C" {
+
+tcrnet_status tcrnet_insert_ex(tcrnet_handle h, const uint8_t* chars, const int64_t* offsets, int64_t m, int32_t mem,
+                               const tcrnet_options* opt_in) {
+    t_last_bad = -1;
+    if (!h || m < 0) return TCRNET_EINVAL;
+    if (h->query_result || h->batched) return TCRNET_ESTATE;
+    if (m == 0) return TCRNET_OK;
+    tcrnet_graph* g = nullptr;
+    const tcrnet_status st = extend_impl(h, chars, offsets, m, mem, opt_in, &g);
+    if (st != TCRNET_OK) return st;  // the handle keeps its previous network
+    {
+        DeviceGuard dg;
+        TCR_CHECK(dg.set(h->device));
+        free_handle_memory(h);
+    }
     *h = *g;  // plain pointers and sizes: the handle now owns g's memory
     delete g;
+    return TCRNET_OK;
+}
+
+tcrnet_status tcrnet_extend(tcrnet_handle h, const uint8_t* chars, const int64_t* offsets, int64_t m, int32_t mem,
+                            const tcrnet_options* opt, tcrnet_handle* out) {
+    t_last_bad = -1;
+    if (!out) return TCRNET_EINVAL;
+    *out = nullptr;
+    if (!h || m < 0) return TCRNET_EINVAL;
+    if (h->query_result || h->batched) return TCRNET_ESTATE;
+    tcrnet_graph* g = nullptr;  // m == 0: a rebuilt copy, a handle of its own
+    const tcrnet_status st = extend_impl(h, chars, offsets, m, mem, opt, &g);
+    if (st != TCRNET_OK) return st;
+    *out = g;
     return TCRNET_OK;
 }
 

@@ -7,11 +7,16 @@ requests keep arriving:
   request at the head of the queue (up to `max_batch_strings` strings) and runs
   them as one device call (`tcrnet_query_ex`); the result rows are split back
   per request;
-- slots: `slots` worker threads, each with its own CUDA stream, so admitted
-  queries overlap on the device (the C library releases the GIL);
-- inserts (`tcrnet_insert_ex`) take the handle exclusively (reader-writer
-  lock); queries admitted before an insert see the previous repertoire, later
-  ones the grown one; each request records the repertoire version it ran on;
+- slots: `slots` worker threads, each with its own CUDA streams (queries on a
+  high-priority stream, inserts on a low-priority one), so admitted requests
+  overlap on the device (the C library releases the GIL);
+- inserts are copy-on-write (`tcrnet_extend`): the grown repertoire is built
+  into a new handle while queries keep running on the current one; the new
+  handle then replaces it (the caller's Graph adopts it) and the old one is
+  freed after its last running query. Inserts apply one at a time in arrival
+  order; queries that start before an insert's swap see the previous
+  repertoire, later ones the grown one; each request records the repertoire
+  version it ran on;
 - admission by memory: a request starts only when its estimated device memory
   fits in the free HBM reported by the driver minus a reserve (otherwise it
   waits until running requests release theirs).
@@ -28,42 +33,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import Graph
-
-
-class RWLock:
-    """Many readers or one writer; a waiting writer blocks new readers."""
-
-    def __init__(self):
-        self._cv = threading.Condition()
-        self._readers = 0
-        self._writer = False
-        self._writers_waiting = 0
-
-    def acquire_read(self):
-        with self._cv:
-            while self._writer or self._writers_waiting:
-                self._cv.wait()
-            self._readers += 1
-
-    def release_read(self):
-        with self._cv:
-            self._readers -= 1
-            if self._readers == 0:
-                self._cv.notify_all()
-
-    def acquire_write(self):
-        with self._cv:
-            self._writers_waiting += 1
-            while self._writer or self._readers:
-                self._cv.wait()
-            self._writers_waiting -= 1
-            self._writer = True
-
-    def release_write(self):
-        with self._cv:
-            self._writer = False
-            self._cv.notify_all()
+from . import Graph, load_library
 
 
 @dataclass
@@ -75,6 +45,7 @@ class Request:
     t_start: float = 0.0
     t_done: float = 0.0
     version: int = -1  # inserts applied before this request ran
+    ticket: int = -1  # arrival order among inserts
     batch_id: int = -1  # device call that served it
     offsets_out: np.ndarray | None = None
     cols_out: np.ndarray | None = None
@@ -101,10 +72,18 @@ class ServingEngine:
         self.reserve = hbm_reserve_bytes
         self.device = device
         self._torch = torch
-        self._streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
+        # per slot: a high-priority stream for queries, a low-priority one for
+        # inserts, so query blocks are scheduled first while a rebuild runs
+        lo, hi = torch.cuda.Stream.priority_range()
+        self._streams = [torch.cuda.Stream(device=device, priority=hi) for _ in range(slots)]
+        self._insert_streams = [torch.cuda.Stream(device=device, priority=lo) for _ in range(slots)]
         self._queue: collections.deque[Request] = collections.deque()
         self._cv = threading.Condition()
-        self._rw = RWLock()
+        self._cur = graph.handle.value  # raw handle of the current version
+        self._refs: collections.Counter = collections.Counter()  # raw handle -> running calls
+        self._retired: set = set()  # replaced handles waiting for their last query
+        self._tickets = 0  # inserts taken
+        self._turn = 0  # next insert to apply
         self._inflight_bytes = 0
         self._inflight = 0
         self._stop = False
@@ -189,6 +168,9 @@ class ServingEngine:
                     if self._admissible(need):
                         for _ in batch:
                             self._queue.popleft()
+                        if head.kind == "insert":
+                            head.ticket = self._tickets
+                            self._tickets += 1
                         self._inflight += 1
                         self._inflight_bytes += need
                         return batch, need
@@ -203,6 +185,7 @@ class ServingEngine:
     # ---- workers -------------------------------------------------------
     def _run(self, slot: int):
         stream = self._streams[slot]
+        insert_stream = self._insert_streams[slot]
         while True:
             batch, need = self._take()
             if batch is None:
@@ -212,7 +195,7 @@ class ServingEngine:
                 r.t_start = t0
             try:
                 if batch[0].kind == "insert":
-                    self._do_insert(batch[0], stream)
+                    self._do_insert(batch[0], insert_stream)
                 else:
                     self._do_queries(batch, stream)
             except BaseException as e:  # reported per request
@@ -227,18 +210,45 @@ class ServingEngine:
                     self.completed.extend(batch)
                 self._release(need)
 
+    def _acquire(self):
+        with self._cv:
+            h = self._cur
+            self._refs[h] += 1
+            return h, self._version
+
+    def _drop(self, h):
+        with self._cv:
+            self._refs[h] -= 1
+            if h in self._retired and self._refs[h] == 0:
+                self._retired.discard(h)
+                load_library().tcrnet_free(h)
+
     def _do_insert(self, req: Request, stream):
-        self._rw.acquire_write()
+        with self._cv:
+            while self._turn != req.ticket:  # inserts apply in arrival order
+                self._cv.wait()
         try:
+            h, version = self._acquire()
+            try:
+                new = Graph.borrowed(h).extend_flat(req.chars, req.offsets, stream=stream)
+            finally:
+                self._drop(h)
             with self._cv:
-                req.version = self._version
+                req.version = version
                 req.batch_id = self._batches
                 self._batches += 1
-            self.graph.insert_flat(req.chars, req.offsets, stream=stream)
-            with self._cv:
+                old = self.graph.adopt(new.release())
+                self._cur = self.graph.handle.value
                 self._version += 1
+                if old is not None:
+                    if self._refs[old] == 0:
+                        load_library().tcrnet_free(old)
+                    else:
+                        self._retired.add(old)
         finally:
-            self._rw.release_write()
+            with self._cv:
+                self._turn += 1
+                self._cv.notify_all()
 
     def _do_queries(self, batch: list[Request], stream):
         if len(batch) == 1:
@@ -248,19 +258,18 @@ class ServingEngine:
             lens = np.concatenate([np.diff(r.offsets) for r in batch])
             offsets = np.zeros(lens.shape[0] + 1, dtype=np.int64)
             np.cumsum(lens, out=offsets[1:])
-        self._rw.acquire_read()
+        h, version = self._acquire()
         try:
             with self._cv:
-                version = self._version
                 bid = self._batches
                 self._batches += 1
-            res = self.graph.query_flat(chars, offsets, method="auto", stream=stream)
+            res = Graph.borrowed(h).query_flat(chars, offsets, method="auto", stream=stream)
             try:
                 off, cols, _ = res.copy_csr()
             finally:
                 res.free()
         finally:
-            self._rw.release_read()
+            self._drop(h)
         off = np.asarray(off, dtype=np.int64)
         row = 0
         for r in batch:

@@ -131,3 +131,26 @@ def test_engine_mixed_queries_and_inserts_versions():
         final = versions[-1]
         ro, rc, _ = oracle.network(final.chars, final.offsets, max_dist=1)
         assert_csr_equal(off, cols, ro, rc, "final network")
+
+
+def test_extend_is_copy_on_write():
+    base = generate_config1(5000, seed=71)
+    add = generate_config1(1200, seed=72)
+    with tn.tcrnet_build_flat(base.chars, base.offsets, 1, method="deletion") as g:
+        before = csr_of(g)
+        with g.extend_flat(add.chars, add.offsets) as g2:
+            # the original handle is untouched and still answers queries
+            after = csr_of(g)
+            assert_csr_equal(after[0], after[1], before[0], before[1], "original after extend")
+            full = concat(base, add)
+            ro, rc, _ = oracle.network(full.chars, full.offsets, max_dist=1)
+            eo, ec, _ = csr_of(g2)
+            assert_csr_equal(eo, ec, ro, rc, "extended vs oracle")
+            q = from_strings(add.strings()[:40])
+            with g2.query_flat(q.chars, q.offsets) as r:
+                qo, qc, _ = csr_of(r)
+            ro, rc = oracle.neighbors(full.chars, full.offsets, q.chars, q.offsets, max_dist=1)
+            assert_csr_equal(qo, qc, ro, rc, "queries on the extended handle")
+        with g.extend_flat(np.zeros(0, np.uint8), np.zeros(1, np.int64)) as g3:
+            co, cc, _ = csr_of(g3)
+            assert_csr_equal(co, cc, before[0], before[1], "empty extension is a copy")
