@@ -27,10 +27,14 @@ struct tcrnet_graph {
     void* d_offsets = nullptr;
     int32_t* d_cols = nullptr;
     int32_t* d_degree = nullptr;
-    // resident repertoire (build handles only)
+    // resident repertoire (build handles only): the bucketed copy (tile
+    // builds) or the input-order copy (deletion builds), and the total length
     tcr::Canon* d_bcanon = nullptr;
     int32_t* d_bperm = nullptr;
     int64_t bucket_off[tcr::kMaxLen + 2] = {0};
+    tcr::Canon* d_canon_in = nullptr;
+    uint8_t* d_lens = nullptr;
+    int64_t lensum = 0;
     tcr::DeletionIndex ix;  // query index of a deletion build (l_max >= 1)
     tcrnet_stats stats;
 };
@@ -204,8 +208,8 @@ cudaStream_t free_stream(int dev) {
 }
 
 void free_handle_memory(tcrnet_graph* h) {
-    void* ptrs[] = {h->d_offsets, h->d_cols, h->d_degree, h->d_bcanon, h->d_bperm, h->ix.ucanon, h->ix.umult,
-                    h->ix.mem_off, h->ix.members, h->ix.recs, h->ix.poff};
+    void* ptrs[] = {h->d_offsets, h->d_cols, h->d_degree, h->d_bcanon, h->d_bperm, h->d_canon_in, h->d_lens,
+                    h->ix.ucanon, h->ix.umult, h->ix.mem_off, h->ix.members, h->ix.recs, h->ix.poff};
     const cudaStream_t fs = free_stream(h->device);
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, fs);
@@ -215,6 +219,8 @@ void free_handle_memory(tcrnet_graph* h) {
     h->d_degree = nullptr;
     h->d_bcanon = nullptr;
     h->d_bperm = nullptr;
+    h->d_canon_in = nullptr;
+    h->d_lens = nullptr;
 }
 
 // Move a finished CSR (int64 offsets, cols, degree) into the handle, narrowing
@@ -376,9 +382,16 @@ tcrnet_status build_from_packed(tcrnet_graph* h, Packed& pk, int64_t n, int32_t 
         st = export_csr(h, dr.off64, dr.cols, dr.degree, n, dr.nnz, opt.force_offsets64 != 0, s, &dr.off32);
         if (st != TCRNET_OK) return st;
     }
-    // keep the bucketed repertoire resident for queries
-    h->d_bcanon = static_cast<Canon*>(pk.canon.release());
-    h->d_bperm = static_cast<int32_t*>(pk.perm.release());
+    // keep the repertoire resident for queries and inserts: the bucketed copy
+    // of a tile build, the input-order copy of a deletion build
+    h->lensum = pk.lensum;
+    if (pk.canon.as<void>()) {
+        h->d_bcanon = static_cast<Canon*>(pk.canon.release());
+        h->d_bperm = static_cast<int32_t*>(pk.perm.release());
+    } else if (keep_index) {
+        h->d_canon_in = static_cast<Canon*>(pk.canon_in.release());
+        h->d_lens = static_cast<uint8_t*>(pk.lens.release());
+    }
     return TCRNET_OK;
 }
 
@@ -404,6 +417,8 @@ tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n
             if (rep_off[r + 1] < rep_off[r]) return TCRNET_EINVAL;
         opt.method = TCRNET_METHOD_DELETION;
     }
+    if (opt.method == TCRNET_METHOD_AUTO)  // decided before packing: only the tile method buckets
+        opt.method = (n >= kAutoDeletionMinN && T <= 1) ? TCRNET_METHOD_DELETION : TCRNET_METHOD_TILE;
     DeviceGuard dg;
     TCR_CHECK(dg.set(opt.device));
     int dev = 0;
@@ -439,7 +454,8 @@ tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n
     int64_t bad = -1;
     if (n > 0) {
         // chars are addressed as d_chars + (offsets[i] - base)
-        st = pack_strings(in.d_chars - in.base, in.d_offs, n, pk, &bad, s);
+        st = pack_strings(in.d_chars - in.base, in.d_offs, n, pk, &bad, s, opt.method == TCRNET_METHOD_TILE,
+                          opt.method != TCRNET_METHOD_TILE && !rep_off);
         if (st != TCRNET_OK) {
             t_last_bad = bad;
             return fail(st);
@@ -579,7 +595,7 @@ tcrnet_status tcrnet_query_ex(tcrnet_handle h, const uint8_t* chars, const int64
     } else {
         Packed pk;
         int64_t bad = -1;
-        st = pack_strings(in.d_chars - in.base, in.d_offs, m, pk, &bad, s);
+        st = pack_strings(in.d_chars - in.base, in.d_offs, m, pk, &bad, s, method != TCRNET_METHOD_DELETION);
         if (st != TCRNET_OK) {
             t_last_bad = bad;
             return fail(st);
@@ -594,6 +610,12 @@ tcrnet_status tcrnet_query_ex(tcrnet_handle h, const uint8_t* chars, const int64
         } else {
             TileSide qs{pk.canon.as<Canon>(), pk.perm.as<int32_t>(), pk.bucket_off};
             TileSide rs{h->d_bcanon, h->d_bperm, h->bucket_off};
+            Packed rb;  // a deletion build keeps its strings in input order: bucket them for this call
+            if (!h->d_bcanon && h->n > 0) {
+                st = bucket_from(h->d_canon_in, h->d_lens, h->n, rb, s);
+                if (st != TCRNET_OK) return fail(st);
+                rs = TileSide{rb.canon.as<Canon>(), rb.perm.as<int32_t>(), rb.bucket_off};
+            }
             st = tile_method(r, qs, rs, m, false, h->threshold, false, ph, s, sms);
             if (st != TCRNET_OK) return fail(st);
         }
@@ -653,22 +675,41 @@ tcrnet_status extend_impl(tcrnet_handle h, const uint8_t* chars, const int64_t* 
     TCR_CHECK(stage_inputs(chars, offsets, m, mem, in, s));
     Packed pn;
     int64_t bad = -1;
-    tcrnet_status st = pack_strings(in.d_chars - in.base, in.d_offs, m, pn, &bad, s);
+    tcrnet_status st = pack_strings(in.d_chars - in.base, in.d_offs, m, pn, &bad, s, /*bucket=*/false);
     if (st != TCRNET_OK) {
         t_last_bad = bad;
         return st;
     }
-    // the grown repertoire: resident strings (input order restored) then the new ones
+    // the grown repertoire: resident strings (input order) then the new ones;
+    // a deletion rebuild keeps this input-order copy, a tile rebuild buckets it
+    const bool tile = opt.method == TCRNET_METHOD_TILE;
     Packed pk;
     pk.n = N;
-    TCR_CHECK(pk.canon_in.alloc(sizeof(Canon) * N, s));
-    TCR_CHECK(pk.lens.alloc(N, s));
-    TCR_CHECK(unbucket_strings(h->d_bcanon, h->d_bperm, h->bucket_off, n_old, pk.canon_in.as<Canon>(),
-                               pk.lens.as<uint8_t>(), s));
-    TCR_CUDA(cudaMemcpyAsync(pk.canon_in.as<Canon>() + n_old, pn.canon_in.as<Canon>(), sizeof(Canon) * m,
-                             cudaMemcpyDeviceToDevice, s));
-    TCR_CUDA(cudaMemcpyAsync(pk.lens.as<uint8_t>() + n_old, pn.lens.as<uint8_t>(), m, cudaMemcpyDeviceToDevice, s));
-    TCR_CHECK(bucket_strings(pk, s));
+    pk.lensum = h->lensum + pn.lensum;
+    if (tile) {
+        TCR_CHECK(pk.canon_in.alloc(sizeof(Canon) * N, s));
+        TCR_CHECK(pk.lens.alloc(N, s));
+    } else {
+        TCR_CHECK(pk.canon_in.alloc_owned(sizeof(Canon) * N, s));
+        TCR_CHECK(pk.lens.alloc_owned(N, s));
+    }
+    if (h->d_canon_in) {
+        if (n_old > 0) {
+            TCR_CUDA(cudaMemcpyAsync(pk.canon_in.as<Canon>(), h->d_canon_in, sizeof(Canon) * n_old,
+                                     cudaMemcpyDeviceToDevice, s));
+            TCR_CUDA(cudaMemcpyAsync(pk.lens.as<uint8_t>(), h->d_lens, n_old, cudaMemcpyDeviceToDevice, s));
+        }
+    } else {
+        TCR_CHECK(unbucket_strings(h->d_bcanon, h->d_bperm, h->bucket_off, n_old, pk.canon_in.as<Canon>(),
+                                   pk.lens.as<uint8_t>(), s));
+    }
+    if (m > 0) {
+        TCR_CUDA(cudaMemcpyAsync(pk.canon_in.as<Canon>() + n_old, pn.canon_in.as<Canon>(), sizeof(Canon) * m,
+                                 cudaMemcpyDeviceToDevice, s));
+        TCR_CUDA(cudaMemcpyAsync(pk.lens.as<uint8_t>() + n_old, pn.lens.as<uint8_t>(), m,
+                                 cudaMemcpyDeviceToDevice, s));
+    }
+    if (tile) TCR_CHECK(bucket_strings(pk, s));
     tcrnet_graph* g = new (std::nothrow) tcrnet_graph();
     if (!g) return TCRNET_ENOMEM;
     std::memset(&g->stats, 0, sizeof(g->stats));

@@ -868,9 +868,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     // Arrays over distinct strings are sized by n (an upper bound) and the
     // record array by n + total length, so no host round trip is needed until
     // the output sizes are known.
-    int64_t lensum = 0;
-    for (int L = 1; L <= kMaxLen; ++L) lensum += (int64_t)L * (pk.bucket_off[L + 1] - pk.bucket_off[L]);
-    const int64_t R_max = n + lensum;
+    const int64_t R_max = n + pk.lensum;
 
     // device counters: [0] dedup error, [1] fill error, [2] fallback partitions,
     // [3] partitions for the sorted join, [4] largest closed list; edge cursor

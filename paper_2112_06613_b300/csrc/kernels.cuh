@@ -23,17 +23,24 @@ struct Packed {
     DevBuf lens;     // uint8[n], input order
     DevBuf canon_in; // Canon[n], input order
     int64_t bucket_off[kMaxLen + 2] = {0};  // bucket L = [bucket_off[L], bucket_off[L+1])
+    int64_t lensum = 0;                     // total length of the strings
 };
 // Encodes chars/offsets (device memory) into `out`. On a bad input returns the
-// status and sets *bad_index to the lowest offending input index.
+// status and sets *bad_index to the lowest offending input index. With
+// bucket = false only the input-order copy is made (no bucketed copy,
+// bucket_off left zero); keep_input_order allocates that copy for a handle to
+// keep (outside the call's workspace).
 tcrnet_status pack_strings(const uint8_t* d_chars, const int64_t* d_offsets, int64_t n, Packed& out,
-                           int64_t* bad_index, cudaStream_t s);
+                           int64_t* bad_index, cudaStream_t s, bool bucket = true, bool keep_input_order = false);
 
 // Write repertoire numbers into the spare bits of input-order canon
 // (repertoire r = strings rep_off[r] .. rep_off[r+1]).
 tcrnet_status tag_repertoires(Canon* canon, int64_t n, const int64_t* rep_off_host, int64_t nrep, cudaStream_t s);
 // Bucket already encoded strings (out.canon_in, out.lens, out.n set).
 tcrnet_status bucket_strings(Packed& out, cudaStream_t s);
+// Bucketed copy (out.canon, out.perm, out.bucket_off) of input-order strings
+// owned elsewhere.
+tcrnet_status bucket_from(const Canon* canon_in, const uint8_t* lens, int64_t n, Packed& out, cudaStream_t s);
 // Inverse of the bucketing: input-order canon and lengths from bucket order.
 tcrnet_status unbucket_strings(const Canon* canon, const int32_t* perm, const int64_t* bucket_off_host, int64_t n,
                                Canon* canon_in, uint8_t* lens, cudaStream_t s);

@@ -27,7 +27,7 @@ constexpr int kBins = kMaxLen + 1;
 __global__ void __launch_bounds__(kPackThreads)
 k_encode(const uint8_t* __restrict__ chars, const int64_t* __restrict__ offs, int64_t n,
          Canon* __restrict__ canon, uint8_t* __restrict__ lens, int32_t* __restrict__ blockcnt,
-         int nblocks, unsigned long long* __restrict__ err) {
+         int nblocks, unsigned long long* __restrict__ err, unsigned long long* __restrict__ lensum) {
     __shared__ uint8_t lut[256];
     __shared__ int cnt[kBins];
     for (int t = threadIdx.x; t < 256; t += blockDim.x) lut[t] = (uint8_t)aa_code((uint32_t)t);
@@ -65,7 +65,13 @@ k_encode(const uint8_t* __restrict__ chars, const int64_t* __restrict__ offs, in
         }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < kBins; t += blockDim.x) blockcnt[(int64_t)t * nblocks + blockIdx.x] = cnt[t];
+    if (blockcnt)
+        for (int t = threadIdx.x; t < kBins; t += blockDim.x) blockcnt[(int64_t)t * nblocks + blockIdx.x] = cnt[t];
+    if (threadIdx.x == 0) {
+        unsigned long long total = 0;
+        for (int t = 1; t < kBins; ++t) total += (unsigned long long)t * (unsigned long long)cnt[t];
+        if (total) atomicAdd(lensum, total);
+    }
 }
 
 __global__ void __launch_bounds__(kPackThreads)
@@ -150,8 +156,7 @@ tcrnet_status tag_repertoires(Canon* canon, int64_t n, const int64_t* rep_off_ho
     return TCRNET_OK;
 }
 
-tcrnet_status bucket_strings(Packed& out, cudaStream_t s) {
-    const int64_t n = out.n;
+tcrnet_status bucket_from(const Canon* canon_in, const uint8_t* lens, int64_t n, Packed& out, cudaStream_t s) {
     for (int L = 0; L < kMaxLen + 2; ++L) out.bucket_off[L] = 0;
     if (n == 0) return TCRNET_OK;
     const int nblocks = (int)ceil_div(n, kPackThreads);
@@ -162,20 +167,23 @@ tcrnet_status bucket_strings(Packed& out, cudaStream_t s) {
     TCR_CHECK(blockcnt.alloc(sizeof(int32_t) * ncnt, s));
     TCR_CHECK(blockoff.alloc(sizeof(int64_t) * (ncnt + 1), s));
     TCR_CHECK(bounds.alloc(sizeof(int64_t) * (kBins + 1), s));
-    k_count_lengths<<<nblocks, kPackThreads, 0, s>>>(out.lens.as<uint8_t>(), n, blockcnt.as<int32_t>(), nblocks);
+    k_count_lengths<<<nblocks, kPackThreads, 0, s>>>(lens, n, blockcnt.as<int32_t>(), nblocks);
     TCR_LAUNCH_CHECK();
     TCR_CHECK(scan_exclusive_i32_to_i64(blockcnt.as<int32_t>(), blockoff.as<int64_t>(), ncnt, s));
     k_bucket_bounds<<<1, 64, 0, s>>>(blockoff.as<int64_t>(), nblocks, bounds.as<int64_t>());
     TCR_LAUNCH_CHECK();
     int64_t h_bounds[kBins + 1];
     TCR_CUDA(cudaMemcpyAsync(h_bounds, bounds.as<void>(), sizeof(h_bounds), cudaMemcpyDeviceToHost, s));
-    k_bucket_scatter<<<nblocks, kPackThreads, 0, s>>>(out.canon_in.as<Canon>(), out.lens.as<uint8_t>(), n,
-                                                      blockoff.as<int64_t>(), nblocks, out.canon.as<Canon>(),
-                                                      out.perm.as<int32_t>());
+    k_bucket_scatter<<<nblocks, kPackThreads, 0, s>>>(canon_in, lens, n, blockoff.as<int64_t>(), nblocks,
+                                                      out.canon.as<Canon>(), out.perm.as<int32_t>());
     TCR_LAUNCH_CHECK();
     TCR_CUDA(cudaStreamSynchronize(s));
     for (int L = 0; L <= kBins; ++L) out.bucket_off[L] = h_bounds[L];
     return TCRNET_OK;
+}
+
+tcrnet_status bucket_strings(Packed& out, cudaStream_t s) {
+    return bucket_from(out.canon_in.as<Canon>(), out.lens.as<uint8_t>(), out.n, out, s);
 }
 
 tcrnet_status unbucket_strings(const Canon* canon, const int32_t* perm, const int64_t* bucket_off_host, int64_t n,
@@ -190,39 +198,55 @@ tcrnet_status unbucket_strings(const Canon* canon, const int32_t* perm, const in
 }
 
 tcrnet_status pack_strings(const uint8_t* d_chars, const int64_t* d_offsets, int64_t n, Packed& out,
-                           int64_t* bad_index, cudaStream_t s) {
+                           int64_t* bad_index, cudaStream_t s, bool bucket, bool keep_input_order) {
     out.n = n;
+    out.lensum = 0;
     *bad_index = -1;
     for (int L = 0; L < kMaxLen + 2; ++L) out.bucket_off[L] = 0;
     if (n == 0) return TCRNET_OK;
     const int nblocks = (int)ceil_div(n, kPackThreads);
-    TCR_CHECK(out.canon_in.alloc(sizeof(Canon) * n, s));
-    TCR_CHECK(out.lens.alloc(n, s));
-    TCR_CHECK(out.canon.alloc_owned(sizeof(Canon) * n, s));  // kept by the handle
-    TCR_CHECK(out.perm.alloc_owned(sizeof(int32_t) * n, s));
-    const int64_t ncnt = (int64_t)kBins * nblocks;
-    DevBuf blockcnt, blockoff, err, bounds;
-    TCR_CHECK(blockcnt.alloc(sizeof(int32_t) * ncnt, s));
-    TCR_CHECK(blockoff.alloc(sizeof(int64_t) * (ncnt + 1), s));
-    TCR_CHECK(err.alloc(sizeof(unsigned long long), s));
-    TCR_CHECK(bounds.alloc(sizeof(int64_t) * (kBins + 1), s));
-    TCR_CUDA(cudaMemsetAsync(err.as<void>(), 0xff, sizeof(unsigned long long), s));
-    k_encode<<<nblocks, kPackThreads, 0, s>>>(d_chars, d_offsets, n, out.canon_in.as<Canon>(),
-                                              out.lens.as<uint8_t>(), blockcnt.as<int32_t>(), nblocks,
-                                              err.as<unsigned long long>());
-    TCR_LAUNCH_CHECK();
-    unsigned long long h_err = ~0ull;
-    TCR_CUDA(cudaMemcpyAsync(&h_err, err.as<void>(), sizeof(h_err), cudaMemcpyDeviceToHost, s));
-    TCR_CHECK(scan_exclusive_i32_to_i64(blockcnt.as<int32_t>(), blockoff.as<int64_t>(), ncnt, s));
-    k_bucket_bounds<<<1, 64, 0, s>>>(blockoff.as<int64_t>(), nblocks, bounds.as<int64_t>());
-    TCR_LAUNCH_CHECK();
-    int64_t h_bounds[kBins + 1];
-    TCR_CUDA(cudaMemcpyAsync(h_bounds, bounds.as<void>(), sizeof(h_bounds), cudaMemcpyDeviceToHost, s));
-    TCR_CUDA(cudaStreamSynchronize(s));
-    if (h_err != ~0ull) {
-        *bad_index = (int64_t)(h_err >> 8);
-        return (tcrnet_status)(h_err & 0xff);
+    if (keep_input_order) {
+        TCR_CHECK(out.canon_in.alloc_owned(sizeof(Canon) * n, s));  // kept by the handle
+        TCR_CHECK(out.lens.alloc_owned(n, s));
+    } else {
+        TCR_CHECK(out.canon_in.alloc(sizeof(Canon) * n, s));
+        TCR_CHECK(out.lens.alloc(n, s));
     }
+    if (bucket) {
+        TCR_CHECK(out.canon.alloc_owned(sizeof(Canon) * n, s));  // kept by the handle
+        TCR_CHECK(out.perm.alloc_owned(sizeof(int32_t) * n, s));
+    }
+    const int64_t ncnt = (int64_t)kBins * nblocks;
+    DevBuf blockcnt, blockoff, flags, bounds;
+    if (bucket) {
+        TCR_CHECK(blockcnt.alloc(sizeof(int32_t) * ncnt, s));
+        TCR_CHECK(blockoff.alloc(sizeof(int64_t) * (ncnt + 1), s));
+        TCR_CHECK(bounds.alloc(sizeof(int64_t) * (kBins + 1), s));
+    }
+    TCR_CHECK(flags.alloc(sizeof(unsigned long long) * 2, s));  // [0] first error, [1] total length
+    unsigned long long* d_flags = flags.as<unsigned long long>();
+    TCR_CUDA(cudaMemsetAsync(d_flags, 0xff, sizeof(unsigned long long), s));
+    TCR_CUDA(cudaMemsetAsync(d_flags + 1, 0, sizeof(unsigned long long), s));
+    k_encode<<<nblocks, kPackThreads, 0, s>>>(d_chars, d_offsets, n, out.canon_in.as<Canon>(),
+                                              out.lens.as<uint8_t>(), bucket ? blockcnt.as<int32_t>() : nullptr,
+                                              nblocks, d_flags, d_flags + 1);
+    TCR_LAUNCH_CHECK();
+    unsigned long long h_flags[2] = {~0ull, 0};
+    TCR_CUDA(cudaMemcpyAsync(h_flags, d_flags, sizeof(h_flags), cudaMemcpyDeviceToHost, s));
+    int64_t h_bounds[kBins + 1];
+    if (bucket) {
+        TCR_CHECK(scan_exclusive_i32_to_i64(blockcnt.as<int32_t>(), blockoff.as<int64_t>(), ncnt, s));
+        k_bucket_bounds<<<1, 64, 0, s>>>(blockoff.as<int64_t>(), nblocks, bounds.as<int64_t>());
+        TCR_LAUNCH_CHECK();
+        TCR_CUDA(cudaMemcpyAsync(h_bounds, bounds.as<void>(), sizeof(h_bounds), cudaMemcpyDeviceToHost, s));
+    }
+    TCR_CUDA(cudaStreamSynchronize(s));
+    if (h_flags[0] != ~0ull) {
+        *bad_index = (int64_t)(h_flags[0] >> 8);
+        return (tcrnet_status)(h_flags[0] & 0xff);
+    }
+    out.lensum = (int64_t)h_flags[1];
+    if (!bucket) return TCRNET_OK;
     for (int L = 0; L <= kBins; ++L) out.bucket_off[L] = h_bounds[L];
     k_bucket_scatter<<<nblocks, kPackThreads, 0, s>>>(out.canon_in.as<Canon>(), out.lens.as<uint8_t>(), n,
                                                       blockoff.as<int64_t>(), nblocks, out.canon.as<Canon>(),
