@@ -13,7 +13,9 @@
 // score follows the last row. lev <= l_max is then score <= l_max. Only bucket
 // pairs with |len a - len b| <= l_max are visited (lev >= |len a - len b|).
 //
-// Strings are at most 48 long, so one 64-bit word holds a column. One row string
+// Strings are at most 48 long, so one 64-bit word holds a column; bucket pairs
+// whose column strings have at most 32 letters (most CDR3s) run the same
+// recurrence on 32-bit words, half the integer work per step. One row string
 // per thread (256 rows per item), columns staged 256 at a time.
 #include <algorithm>
 #include <vector>
@@ -52,29 +54,33 @@ struct DpArgs {
     int T;
 };
 
+template <typename Word>
 struct DpSmem {
-    uint64_t peq[kChunk][kLetters];
+    Word peq[kChunk][kLetters];
     int32_t id[kChunk];
     int item;
 };
 
-// lev(a, b) by the bit-vector recurrence; peq = position masks of b (length Lb >= 1).
-__device__ __forceinline__ int myers_distance(const uint64_t* __restrict__ peq, int Lb, const Canon& a, int La) {
-    uint64_t vp = ~0ull, vn = 0ull;
-    const uint64_t top = 1ull << (Lb - 1);
+// lev(a, b) by the bit-vector recurrence; peq = position masks of b (length
+// 1 <= Lb <= bits of Word). Bits above Lb - 1 never reach the ones below
+// (carries and shifts move up only), so they need no masking.
+template <typename Word>
+__device__ __forceinline__ int myers_distance(const Word* __restrict__ peq, int Lb, const Canon& a, int La) {
+    Word vp = ~Word(0), vn = Word(0);
+    const Word top = Word(1) << (Lb - 1);
     int score = Lb;
 #pragma unroll
     for (int j = 0; j < kMaxLen; ++j) {
         if (j < La) {
             const uint32_t c = (uint32_t)(a.w[j / kCodesPerWord] >> (5 * (j % kCodesPerWord))) & 31u;
-            const uint64_t eq = peq[c - 1];
-            const uint64_t xv = eq | vn;
-            const uint64_t xh = (((eq & vp) + vp) ^ vp) | eq;
-            uint64_t hp = vn | ~(xh | vp);
-            uint64_t hn = vp & xh;
+            const Word eq = peq[c - 1];
+            const Word xv = eq | vn;
+            const Word xh = (((eq & vp) + vp) ^ vp) | eq;
+            Word hp = vn | ~(xh | vp);
+            Word hn = vp & xh;
             score += (hp & top) ? 1 : 0;
             score -= (hn & top) ? 1 : 0;
-            hp = (hp << 1) | 1ull;
+            hp = (hp << 1) | Word(1);
             hn = hn << 1;
             vp = hn | ~(xv | hp);
             vn = hp & xv;
@@ -83,9 +89,43 @@ __device__ __forceinline__ int myers_distance(const uint64_t* __restrict__ peq, 
     return score;
 }
 
-template <bool WRITE>
+// Two columns against one row at once: two independent recurrences in one loop
+// over the row's letters, so each step has two dependency chains to overlap.
+template <typename Word>
+__device__ __forceinline__ void myers_distance2(const Word* __restrict__ peq0, const Word* __restrict__ peq1, int Lb,
+                                                const Canon& a, int La, int& d0, int& d1) {
+    Word vp0 = ~Word(0), vn0 = Word(0), vp1 = ~Word(0), vn1 = Word(0);
+    const Word top = Word(1) << (Lb - 1);
+    int s0 = Lb, s1 = Lb;
+#pragma unroll
+    for (int j = 0; j < kMaxLen; ++j) {
+        if (j < La) {
+            const uint32_t c = (uint32_t)(a.w[j / kCodesPerWord] >> (5 * (j % kCodesPerWord))) & 31u;
+            const Word e0 = peq0[c - 1], e1 = peq1[c - 1];
+            const Word xv0 = e0 | vn0, xv1 = e1 | vn1;
+            const Word xh0 = (((e0 & vp0) + vp0) ^ vp0) | e0;
+            const Word xh1 = (((e1 & vp1) + vp1) ^ vp1) | e1;
+            Word hp0 = vn0 | ~(xh0 | vp0), hp1 = vn1 | ~(xh1 | vp1);
+            Word hn0 = vp0 & xh0, hn1 = vp1 & xh1;
+            s0 += ((hp0 & top) ? 1 : 0) - ((hn0 & top) ? 1 : 0);
+            s1 += ((hp1 & top) ? 1 : 0) - ((hn1 & top) ? 1 : 0);
+            hp0 = (hp0 << 1) | Word(1);
+            hp1 = (hp1 << 1) | Word(1);
+            hn0 <<= 1;
+            hn1 <<= 1;
+            vp0 = hn0 | ~(xv0 | hp0);
+            vp1 = hn1 | ~(xv1 | hp1);
+            vn0 = hp0 & xv0;
+            vn1 = hp1 & xv1;
+        }
+    }
+    d0 = s0;
+    d1 = s1;
+}
+
+template <bool WRITE, typename Word>
 __global__ void __launch_bounds__(kThreads) k_dp(DpArgs g) {
-    __shared__ DpSmem sm;
+    __shared__ DpSmem<Word> sm;
     const int tid = threadIdx.x;
     for (;;) {
         __syncthreads();
@@ -108,16 +148,16 @@ __global__ void __launch_bounds__(kThreads) k_dp(DpArgs g) {
             __syncthreads();
             for (int t = tid; t < kChunk; t += kThreads) {
                 const int pos = c0 + t;
-                uint64_t* pq = sm.peq[t];
+                Word* pq = sm.peq[t];
 #pragma unroll
-                for (int c = 0; c < kLetters; ++c) pq[c] = 0ull;
+                for (int c = 0; c < kLetters; ++c) pq[c] = Word(0);
                 if (pos < it.b1) {
                     const Canon b = load_canon(g.colc + pos);
 #pragma unroll
                     for (int k = 0; k < kMaxLen; ++k) {
                         if (k < it.Lb) {
                             const uint32_t c = (uint32_t)(b.w[k / kCodesPerWord] >> (5 * (k % kCodesPerWord))) & 31u;
-                            pq[c - 1] |= 1ull << k;
+                            pq[c - 1] |= Word(1) << k;
                         }
                     }
                     sm.id[t] = g.col_id[pos];
@@ -128,10 +168,17 @@ __global__ void __launch_bounds__(kThreads) k_dp(DpArgs g) {
             __syncthreads();
             const int nb = min(kChunk, it.b1 - c0);
             if (valid) {
-                for (int jj = 0; jj < nb; ++jj) {
-                    if (it.diag && c0 + jj <= row) continue;
-                    const int d = myers_distance(sm.peq[jj], it.Lb, a, it.La);
-                    if (d > g.T) continue;
+                for (int j2 = 0; j2 < nb; j2 += 2) {
+                    const bool has1 = j2 + 1 < nb;
+                    const bool use0 = !(it.diag && c0 + j2 <= row);
+                    const bool use1 = has1 && !(it.diag && c0 + j2 + 1 <= row);
+                    if (!use0 && !use1) continue;
+                    int dd[2];
+                    myers_distance2<Word>(sm.peq[j2], sm.peq[has1 ? j2 + 1 : j2], it.Lb, a, it.La, dd[0], dd[1]);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                    const int jj = j2 + h;
+                    if (!(h == 0 ? use0 : use1) || dd[h] > g.T) continue;
                     const int32_t bid = sm.id[jj];
                     if constexpr (!WRITE) {
                         ++cnt;
@@ -145,6 +192,7 @@ __global__ void __launch_bounds__(kThreads) k_dp(DpArgs g) {
                             if (g.off[bid] + sb < g.off[bid + 1]) g.out[g.off[bid] + sb] = aid;
                             else atomicExch(g.err, 1);
                         }
+                    }
                     }
                 }
             }
@@ -191,32 +239,45 @@ tcrnet_status dp_pass(const TileSide& rows, const TileSide& cols, bool sym, int 
     }
     if (pairs) *pairs = np;
     if (items.empty()) return TCRNET_OK;
+    // column strings of <= 32 letters first (32-bit words), then the rest;
+    // heaviest items first within each group
     std::stable_sort(items.begin(), items.end(), [](const DpItem& x, const DpItem& y) {
+        const bool nx = x.Lb <= 32, ny = y.Lb <= 32;
+        if (nx != ny) return nx;
         return (int64_t)(x.a1 - x.a0) * (x.b1 - x.b0) * x.La > (int64_t)(y.a1 - y.a0) * (y.b1 - y.b0) * y.La;
     });
+    const int n_narrow = (int)(std::partition_point(items.begin(), items.end(),
+                                                    [](const DpItem& x) { return x.Lb <= 32; }) -
+                               items.begin());
+    const int n_wide = (int)items.size() - n_narrow;
     DevBuf d_items, d_counter;
     TCR_CHECK(d_items.alloc(sizeof(DpItem) * items.size(), s));
-    TCR_CHECK(d_counter.alloc(sizeof(int) * 2, s));
+    TCR_CHECK(d_counter.alloc(sizeof(int) * 3, s));  // [0] narrow items taken, [1] error, [2] wide items taken
     TCR_CUDA(cudaMemcpyAsync(d_items.as<void>(), items.data(), sizeof(DpItem) * items.size(),
                              cudaMemcpyHostToDevice, s));
-    TCR_CUDA(cudaMemsetAsync(d_counter.as<void>(), 0, sizeof(int) * 2, s));
-    DpArgs g{d_items.as<DpItem>(), (int)items.size(), d_counter.as<int>(), rows.canon, rows.id, cols.canon, cols.id,
-             count, off, cursor, cols_out, d_counter.as<int>() + 1, sym ? 1 : 0, threshold};
-    int per_sm = 0;
+    TCR_CUDA(cudaMemsetAsync(d_counter.as<void>(), 0, sizeof(int) * 3, s));
+    auto launch = [&](auto kernel, const DpItem* list, int nitems, int* counter) -> tcrnet_status {
+        if (nitems == 0) return TCRNET_OK;
+        DpArgs g{list, nitems, counter, rows.canon, rows.id, cols.canon, cols.id,
+                 count, off, cursor, cols_out, d_counter.as<int>() + 1, sym ? 1 : 0, threshold};
+        int per_sm = 0;
+        TCR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0));
+        const int grid = (int)std::min<int64_t>((int64_t)nitems, (int64_t)num_sms * std::max(per_sm, 1));
+        kernel<<<grid, kThreads, 0, s>>>(g);
+        TCR_LAUNCH_CHECK();
+        return TCRNET_OK;
+    };
+    const DpItem* d0 = d_items.as<DpItem>();
     if (write) {
-        TCR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dp<true>, kThreads, 0));
+        TCR_CHECK(launch(k_dp<true, uint32_t>, d0, n_narrow, d_counter.as<int>()));
+        TCR_CHECK(launch(k_dp<true, uint64_t>, d0 + n_narrow, n_wide, d_counter.as<int>() + 2));
     } else {
-        TCR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dp<false>, kThreads, 0));
+        TCR_CHECK(launch(k_dp<false, uint32_t>, d0, n_narrow, d_counter.as<int>()));
+        TCR_CHECK(launch(k_dp<false, uint64_t>, d0 + n_narrow, n_wide, d_counter.as<int>() + 2));
     }
-    const int grid = (int)std::min<int64_t>((int64_t)items.size(), (int64_t)num_sms * std::max(per_sm, 1));
-    if (write)
-        k_dp<true><<<grid, kThreads, 0, s>>>(g);
-    else
-        k_dp<false><<<grid, kThreads, 0, s>>>(g);
-    TCR_LAUNCH_CHECK();
     if (write) {
         int h_err = 0;
-        TCR_CUDA(cudaMemcpyAsync(&h_err, g.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        TCR_CUDA(cudaMemcpyAsync(&h_err, d_counter.as<int>() + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
         TCR_CUDA(cudaStreamSynchronize(s));
         if (h_err) return TCRNET_EDEVICE;
     }

@@ -369,3 +369,34 @@ def test_larger_threshold_edge_strings_and_queries():
             qo, qc, _ = r.copy_csr()
     ro, rc = oracle.neighbors(base.chars, base.offsets, qs.chars, qs.offsets, max_dist=2)
     assert_csr_equal(qo, qc, ro, rc, "queries T=2")
+
+
+@pytest.mark.parametrize("threshold", [2, 3])
+def test_larger_threshold_across_the_32_letter_word_boundary(threshold):
+    # column strings of <= 32 letters run on 32-bit words, longer ones on 64-bit
+    rng = np.random.default_rng(90 + threshold)
+    alpha = np.array(list("ACDEFG"))
+    strs = []
+    for _ in range(300):
+        L = int(rng.integers(28, 41))
+        s = list(alpha[rng.integers(0, len(alpha), L)])
+        strs.append("".join(s))
+        for _ in range(3):  # near copies: substitutions, deletions, insertions
+            t = list(s)
+            for _ in range(int(rng.integers(1, threshold + 2))):
+                k = int(rng.integers(0, len(t)))
+                op = int(rng.integers(0, 3))
+                if op == 0:
+                    t[k] = alpha[rng.integers(0, len(alpha))]
+                elif op == 1 and len(t) > 1:
+                    del t[k]
+                elif len(t) < 48:
+                    t.insert(k, alpha[rng.integers(0, len(alpha))])
+            strs.append("".join(t))
+    rep = from_strings(strs)
+    lens = np.diff(rep.offsets)
+    assert (lens <= 32).any() and (lens > 32).any()
+    off, cols, deg, _ = gpu_csr(rep, threshold, "tile")
+    ro, rc, _ = oracle_csr(rep, threshold)
+    assert_csr_equal(off, cols, ro, rc, f"lengths 26..44, T={threshold}")
+    check_invariants(off, cols, deg, rep.n)
