@@ -253,22 +253,50 @@ tcrnet_status tile_method(tcrnet_graph* h, const TileSide& rows, const TileSide&
     DevBuf count, off64, out_cols, cursor;
     TCR_CHECK(count.alloc_owned(sizeof(int32_t) * n_rows, s));
     TCR_CUDA(cudaMemsetAsync(count.as<void>(), 0, sizeof(int32_t) * n_rows, s));
+    // The count pass keeps its hits (up to kPairsPerRow per row on average); when
+    // they all fit, a scatter replaces the write pass, which would test every
+    // candidate pair again.
+    constexpr int64_t kPairsPerRow = 64;
+    const int64_t pcap = std::max<int64_t>(1 << 20, std::min<int64_t>(kPairsPerRow * n_rows, 1LL << 28));
+    DevBuf pairbuf, pcur;
+    PairSink sink;
+    if (pairbuf.alloc(sizeof(int2) * pcap, s) == TCRNET_OK && pcur.alloc(sizeof(unsigned long long) * 2, s) == TCRNET_OK) {
+        TCR_CUDA(cudaMemsetAsync(pcur.as<void>(), 0, sizeof(unsigned long long) * 2, s));
+        sink.pairs = pairbuf.as<int2>();
+        sink.cursor = pcur.as<unsigned long long>();
+        sink.cap = pcap;
+    }
     const int e0 = ph.mark();
     int64_t pairs = 0;
-    TCR_CHECK(tile_pass(rows, cols, sym, T, false, count.as<int32_t>(), nullptr, nullptr, nullptr, &pairs, s, sms));
+    TCR_CHECK(tile_pass(rows, cols, sym, T, false, count.as<int32_t>(), nullptr, nullptr, nullptr, &pairs, s, sms,
+                        &sink));
     const int e1 = ph.mark();
     TCR_CHECK(off64.alloc_owned(sizeof(int64_t) * (n_rows + 1), s));
     TCR_CHECK(scan_exclusive_i32_to_i64(count.as<int32_t>(), off64.as<int64_t>(), n_rows, s));
     int64_t nnz = 0;
+    unsigned long long kept = ~0ull;
     TCR_CUDA(cudaMemcpyAsync(&nnz, off64.as<int64_t>() + n_rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    if (sink.cursor)
+        TCR_CUDA(cudaMemcpyAsync(&kept, sink.cursor, sizeof(kept), cudaMemcpyDeviceToHost, s));
     TCR_CUDA(cudaStreamSynchronize(s));
     const int e2 = ph.mark();
     TCR_CHECK(out_cols.alloc_owned(sizeof(int32_t) * nnz, s));
     TCR_CHECK(cursor.alloc(sizeof(int32_t) * n_rows, s));
     TCR_CUDA(cudaMemsetAsync(cursor.as<void>(), 0, sizeof(int32_t) * n_rows, s));
-    if (nnz > 0)
-        TCR_CHECK(tile_pass(rows, cols, sym, T, true, nullptr, off64.as<int64_t>(), cursor.as<int32_t>(),
-                            out_cols.as<int32_t>(), nullptr, s, sms));
+    if (nnz > 0) {
+        if (sink.cursor && (int64_t)kept <= pcap) {
+            int* err = reinterpret_cast<int*>(sink.cursor + 1);
+            TCR_CHECK(scatter_pairs(sink.pairs, (int64_t)kept, sym, off64.as<int64_t>(), cursor.as<int32_t>(),
+                                    out_cols.as<int32_t>(), err, s));
+            int h_err = 0;
+            TCR_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+            TCR_CUDA(cudaStreamSynchronize(s));
+            if (h_err) return TCRNET_EDEVICE;
+        } else {
+            TCR_CHECK(tile_pass(rows, cols, sym, T, true, nullptr, off64.as<int64_t>(), cursor.as<int32_t>(),
+                                out_cols.as<int32_t>(), nullptr, s, sms));
+        }
+    }
     const int e3 = ph.mark();
     TCR_CHECK(sort_rows(off64.as<int64_t>(), out_cols.as<int32_t>(), n_rows, s, sms));
     const int e4 = ph.mark();

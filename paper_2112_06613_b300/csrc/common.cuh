@@ -81,6 +81,28 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
+// Append this lane's `k` hits (pairs (a, row_b[0..k)) given by emit) to a pair
+// sink with one atomic per warp: every lane of the warp must call it (k may
+// be 0). emit(slot_base) writes the lane's pairs at slots slot_base ..
+// slot_base + k - 1 when they are below cap.
+template <typename Emit>
+__device__ __forceinline__ void warp_append_pairs(unsigned long long* cursor, int k, Emit emit) {
+    const unsigned any = __ballot_sync(0xffffffffu, k > 0);
+    if (!any) return;
+    const int lane = threadIdx.x & 31;
+    int x = k;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, x, 31);
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(cursor, (unsigned long long)total);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (k > 0) emit((long long)(base + (unsigned long long)(x - k)));
+}
+
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // Error record of the last failing CUDA call (diagnostics only).

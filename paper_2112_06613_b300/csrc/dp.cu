@@ -52,6 +52,9 @@ struct DpArgs {
     int* err;
     int sym;
     int T;
+    int2* pairs;  // count pass: hits kept for the scatter (null: none)
+    unsigned long long* pcur;
+    int64_t pcap;
 };
 
 template <typename Word>
@@ -167,14 +170,29 @@ __global__ void __launch_bounds__(kThreads) k_dp(DpArgs g) {
             }
             __syncthreads();
             const int nb = min(kChunk, it.b1 - c0);
-            if (valid) {
+            {
+                // every lane runs the loop (rows past the item's end compute and
+                // discard), so the count pass can keep its hits warp by warp
                 for (int j2 = 0; j2 < nb; j2 += 2) {
                     const bool has1 = j2 + 1 < nb;
-                    const bool use0 = !(it.diag && c0 + j2 <= row);
-                    const bool use1 = has1 && !(it.diag && c0 + j2 + 1 <= row);
+                    const bool use0 = valid && !(it.diag && c0 + j2 <= row);
+                    const bool use1 = valid && has1 && !(it.diag && c0 + j2 + 1 <= row);
+                    int dd[2] = {g.T + 1, g.T + 1};
+                    if (use0 || use1)
+                        myers_distance2<Word>(sm.peq[j2], sm.peq[has1 ? j2 + 1 : j2], it.Lb, a, it.La, dd[0], dd[1]);
+                    if constexpr (!WRITE) {
+                        if (g.pcur) {
+                            const bool k0 = use0 && dd[0] <= g.T, k1 = use1 && dd[1] <= g.T;
+                            warp_append_pairs(g.pcur, (int)k0 + (int)k1, [&](long long base) {
+                                if (k0) {
+                                    if (base < g.pcap) g.pairs[base] = make_int2(aid, sm.id[j2]);
+                                    ++base;
+                                }
+                                if (k1 && base < g.pcap) g.pairs[base] = make_int2(aid, sm.id[j2 + 1]);
+                            });
+                        }
+                    }
                     if (!use0 && !use1) continue;
-                    int dd[2];
-                    myers_distance2<Word>(sm.peq[j2], sm.peq[has1 ? j2 + 1 : j2], it.Lb, a, it.La, dd[0], dd[1]);
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                     const int jj = j2 + h;
@@ -222,7 +240,7 @@ void add_block(std::vector<DpItem>& v, int64_t r0, int64_t r1, int64_t c0, int64
 
 tcrnet_status dp_pass(const TileSide& rows, const TileSide& cols, bool sym, int threshold, bool write,
                       int32_t* count, const int64_t* off, int32_t* cursor, int32_t* cols_out, int64_t* pairs,
-                      cudaStream_t s, int num_sms) {
+                      cudaStream_t s, int num_sms, const PairSink* sink) {
     std::vector<DpItem> items;
     int64_t np = 0;
     for (int La = 1; La <= kMaxLen; ++La) {
@@ -258,8 +276,10 @@ tcrnet_status dp_pass(const TileSide& rows, const TileSide& cols, bool sym, int 
     TCR_CUDA(cudaMemsetAsync(d_counter.as<void>(), 0, sizeof(int) * 3, s));
     auto launch = [&](auto kernel, const DpItem* list, int nitems, int* counter) -> tcrnet_status {
         if (nitems == 0) return TCRNET_OK;
+        const bool keep = !write && sink && sink->pairs;
         DpArgs g{list, nitems, counter, rows.canon, rows.id, cols.canon, cols.id,
-                 count, off, cursor, cols_out, d_counter.as<int>() + 1, sym ? 1 : 0, threshold};
+                 count, off, cursor, cols_out, d_counter.as<int>() + 1, sym ? 1 : 0, threshold,
+                 keep ? sink->pairs : nullptr, keep ? sink->cursor : nullptr, keep ? sink->cap : 0};
         int per_sm = 0;
         TCR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0));
         const int grid = (int)std::min<int64_t>((int64_t)nitems, (int64_t)num_sms * std::max(per_sm, 1));

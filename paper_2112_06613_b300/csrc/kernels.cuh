@@ -51,6 +51,19 @@ struct TileSide {
     const int32_t* id;   // bucket position -> output id
     const int64_t* bucket_off;  // host copy, kMaxLen + 2 entries
 };
+// Hits of a count pass, kept so that the write pass can be skipped: each hit
+// (row id, column id) goes to pairs[slot], slot from one warp-level atomic on
+// *cursor; slots at or above cap are not written (the caller then runs the
+// write pass instead).
+struct PairSink {
+    int2* pairs = nullptr;
+    unsigned long long* cursor = nullptr;
+    int64_t cap = 0;
+};
+// Rows of the hits (both directions when sym) at slots from per-row cursors,
+// then the caller sorts the rows. Errors (a row fuller than its count) set *err.
+tcrnet_status scatter_pairs(const int2* pairs, int64_t npairs, bool sym, const int64_t* off, int32_t* cursor,
+                            int32_t* cols_out, int* err, cudaStream_t s);
 // Count (write == false) or write (write == true) every adjacent pair.
 //  graph mode (rows == cols, sym == true): tests (L, L) upper triangles and
 //   (L, L+1) rectangles; count[] gets both endpoints, writes go both ways.
@@ -59,13 +72,13 @@ struct TileSide {
 // Returns the number of candidate pairs tested in *pairs.
 tcrnet_status tile_pass(const TileSide& rows, const TileSide& cols, bool sym, int threshold, bool write,
                         int32_t* count, const int64_t* off, int32_t* cursor, int32_t* cols_out,
-                        int64_t* pairs, cudaStream_t s, int num_sms);
+                        int64_t* pairs, cudaStream_t s, int num_sms, const PairSink* sink = nullptr);
 
 // ---- dp.cu ----------------------------------------------------------------
 // Same contract as tile_pass for l_max >= 2 (bit-parallel Levenshtein distance).
 tcrnet_status dp_pass(const TileSide& rows, const TileSide& cols, bool sym, int threshold, bool write,
                       int32_t* count, const int64_t* off, int32_t* cursor, int32_t* cols_out, int64_t* pairs,
-                      cudaStream_t s, int num_sms);
+                      cudaStream_t s, int num_sms, const PairSink* sink = nullptr);
 
 // ---- analytics.cu ---------------------------------------------------------
 // Connected components of the CSR restricted to keep[i] != 0 (keep may be null):

@@ -202,6 +202,9 @@ struct Args {
     int* err;
     int sym;
     int T;
+    int2* pairs;                // count pass: hits kept for the scatter (null: none)
+    unsigned long long* pcur;
+    int64_t pcap;
 };
 
 template <int W, int KIND, bool WRITE>
@@ -279,6 +282,20 @@ __device__ __forceinline__ void process_item(const Args& g, const Item& it, Smem
                     if constexpr (KIND == kDiag) h = h && (jj > lim[r]);
                 }
                 hit |= (unsigned)h << r;
+            }
+            if constexpr (!WRITE) {
+                if (g.pcur) {  // uniform: every lane of the warp takes part
+                    warp_append_pairs(g.pcur, __popc(hit), [&](long long base) {
+                        const int32_t bid = sm.id[jj];
+#pragma unroll
+                        for (int r = 0; r < R; ++r) {
+                            if ((hit >> r) & 1u) {
+                                if (base < g.pcap) g.pairs[base] = make_int2(rid[r], bid);
+                                ++base;
+                            }
+                        }
+                    });
+                }
             }
             if (hit) {
                 const int32_t bid = sm.id[jj];
@@ -379,12 +396,40 @@ void add_triangle(std::vector<Item>& v, int64_t s, int64_t e, int W, int64_t& pa
 
 }  // namespace
 
+namespace {
+__global__ void k_scatter_pairs(const int2* __restrict__ pairs, int64_t npairs, int sym,
+                                const int64_t* __restrict__ off, int32_t* __restrict__ cursor,
+                                int32_t* __restrict__ out, int* __restrict__ err) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < npairs;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int2 p = pairs[k];
+        const int32_t sa = atomicAdd(&cursor[p.x], 1);
+        if (off[p.x] + sa < off[p.x + 1]) out[off[p.x] + sa] = p.y;
+        else atomicExch(err, 1);
+        if (sym) {
+            const int32_t sb = atomicAdd(&cursor[p.y], 1);
+            if (off[p.y] + sb < off[p.y + 1]) out[off[p.y] + sb] = p.x;
+            else atomicExch(err, 1);
+        }
+    }
+}
+}  // namespace
+
+tcrnet_status scatter_pairs(const int2* pairs, int64_t npairs, bool sym, const int64_t* off, int32_t* cursor,
+                            int32_t* cols_out, int* err, cudaStream_t s) {
+    if (npairs <= 0) return TCRNET_OK;
+    const int64_t blocks = std::min<int64_t>(ceil_div(npairs, 256), 148LL * 64);
+    k_scatter_pairs<<<(unsigned)blocks, 256, 0, s>>>(pairs, npairs, sym ? 1 : 0, off, cursor, cols_out, err);
+    TCR_LAUNCH_CHECK();
+    return TCRNET_OK;
+}
+
 tcrnet_status tile_pass(const TileSide& rows, const TileSide& cols, bool sym, int threshold, bool write,
                         int32_t* count, const int64_t* off, int32_t* cursor, int32_t* cols_out,
-                        int64_t* pairs, cudaStream_t s, int num_sms) {
+                        int64_t* pairs, cudaStream_t s, int num_sms, const PairSink* sink) {
     if (threshold >= 2)
         return dp_pass(rows, cols, sym, std::min(threshold, kMaxLen), write, count, off, cursor, cols_out, pairs, s,
-                       num_sms);
+                       num_sms, sink);
     std::vector<Item> items;
     int64_t np = 0;
     for (int L = 1; L <= kMaxLen; ++L) {
@@ -435,6 +480,10 @@ tcrnet_status tile_pass(const TileSide& rows, const TileSide& cols, bool sym, in
     g.err = d_counter.as<int>() + 1;
     g.sym = sym ? 1 : 0;
     g.T = threshold;
+    const bool keep = !write && sink && sink->pairs;
+    g.pairs = keep ? sink->pairs : nullptr;
+    g.pcur = keep ? sink->cursor : nullptr;
+    g.pcap = keep ? sink->cap : 0;
     int per_sm = 0;
     if (write) {
         TCR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile<true>, kThreads, 0));

@@ -400,3 +400,15 @@ def test_larger_threshold_across_the_32_letter_word_boundary(threshold):
     ro, rc, _ = oracle_csr(rep, threshold)
     assert_csr_equal(off, cols, ro, rc, f"lengths 26..44, T={threshold}")
     check_invariants(off, cols, deg, rep.n)
+
+
+@pytest.mark.parametrize("threshold", [1, 2])
+def test_tile_write_pass_when_hits_overflow_the_kept_pairs(threshold):
+    # 3.1 million adjacent pairs among 2,500 strings: more than the count pass
+    # keeps (at least 2^20 pairs, 64 per row), so the write pass runs instead
+    strs = ["CASSLGQETQYF"] * 2000 + ["CASSLGQETQYW"] * 300 + ["CASSLGETQYF"] * 200 + ["CASSPGQETQYF"]
+    rep = from_strings(strs)
+    off, cols, deg, _ = gpu_csr(rep, threshold, "tile")
+    ro, rc, _ = oracle_csr(rep, threshold)
+    assert_csr_equal(off, cols, ro, rc, f"dense tile build T={threshold}")
+    check_invariants(off, cols, deg, rep.n)
