@@ -180,11 +180,15 @@ __device__ __forceinline__ void load_words(const uint32_t* p, uint32_t (&o)[W]) 
     }
 }
 
+constexpr int kHitBuf = 128;  // kept hits staged per warp and column chunk
+
 struct Smem {
     uint32_t b[kChunk][8];   // column strings (W words, padded to 4 or 8)
     uint32_t bs[kChunk][8];  // column strings shifted by one position (kShortRows)
     int32_t id[kChunk];
     int item;
+    int2 hits[kThreads / 32][kHitBuf];  // count pass: hits of the current chunk, per warp
+    int nhits[kThreads / 32];
 };
 
 struct Args {
@@ -283,23 +287,24 @@ __device__ __forceinline__ void process_item(const Args& g, const Item& it, Smem
                 }
                 hit |= (unsigned)h << r;
             }
-            if constexpr (!WRITE) {
-                if (g.pcur) {  // uniform: every lane of the warp takes part
-                    warp_append_pairs(g.pcur, __popc(hit), [&](long long base) {
-                        const int32_t bid = sm.id[jj];
-#pragma unroll
-                        for (int r = 0; r < R; ++r) {
-                            if ((hit >> r) & 1u) {
-                                if (base < g.pcap) g.pairs[base] = make_int2(rid[r], bid);
-                                ++base;
-                            }
-                        }
-                    });
-                }
-            }
             if (hit) {
                 const int32_t bid = sm.id[jj];
                 if constexpr (!WRITE) {
+                    if (g.pcur) {  // keep the hits: staged per warp, moved out at the chunk's end
+                        const int wq = tid >> 5;
+#pragma unroll
+                        for (int r = 0; r < R; ++r) {
+                            if ((hit >> r) & 1u) {
+                                const int slot = atomicAdd(&sm.nhits[wq], 1);
+                                if (slot < kHitBuf) {
+                                    sm.hits[wq][slot] = make_int2(rid[r], bid);
+                                } else {
+                                    const unsigned long long pos = atomicAdd(g.pcur, 1ull);
+                                    if ((long long)pos < g.pcap) g.pairs[pos] = make_int2(rid[r], bid);
+                                }
+                            }
+                        }
+                    }
 #pragma unroll
                     for (int r = 0; r < R; ++r) rc[r] += (hit >> r) & 1u;
                     if (g.sym) atomicAdd(&g.count[bid], __popc(hit));
@@ -321,6 +326,23 @@ __device__ __forceinline__ void process_item(const Args& g, const Item& it, Smem
                         }
                     }
                 }
+            }
+        }
+        if constexpr (!WRITE) {
+            if (g.pcur) {  // move this warp's staged hits out: one cursor update
+                __syncwarp();
+                const int wq = tid >> 5, lane = tid & 31;
+                const int k = min(sm.nhits[wq], kHitBuf);
+                if (k > 0) {
+                    unsigned long long base = 0;
+                    if (lane == 0) base = atomicAdd(g.pcur, (unsigned long long)k);
+                    base = __shfl_sync(kFull, base, 0);
+                    for (int t = lane; t < k; t += 32)
+                        if ((long long)(base + t) < g.pcap) g.pairs[base + t] = sm.hits[wq][t];
+                }
+                __syncwarp();
+                if (lane == 0) sm.nhits[wq] = 0;
+                __syncwarp();
             }
         }
     }
@@ -348,6 +370,7 @@ __device__ __forceinline__ void dispatch_w(const Args& g, const Item& it, Smem& 
 template <bool WRITE>
 __global__ void __launch_bounds__(kThreads, 2) k_tile(Args g) {
     __shared__ Smem sm;
+    if (threadIdx.x < kThreads / 32) sm.nhits[threadIdx.x] = 0;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) sm.item = atomicAdd(g.counter, 1);
