@@ -87,7 +87,11 @@ typedef struct tcrnet_options {
     int32_t partition_target; /* tuning: mean records per deletion-join partition,
                                  4 .. 128; 0 = default (24 up to 2^25 records,
                                  else 32). Any value gives the same network. */
-    int32_t reserved[6];      /* must be zero */
+    int32_t fail_alloc_at;    /* testing (host-side fault injection): the k-th device
+                                 allocation of this call fails and the call returns
+                                 TCRNET_ENOMEM after releasing what it holds;
+                                 0 = off */
+    int32_t reserved[5];      /* must be zero */
 } tcrnet_options;
 
 /* Defaults: AUTO method, current device, legacy default stream, no profiling. */

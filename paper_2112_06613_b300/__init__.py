@@ -42,7 +42,8 @@ class tcrnet_options(ctypes.Structure):
         ("profile", ctypes.c_int32),
         ("partition_cap", ctypes.c_int32),
         ("partition_target", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 6),
+        ("fail_alloc_at", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 5),
     ]
 
 
@@ -191,7 +192,7 @@ def _stream_ptr(stream):
 
 
 def make_options(method="auto", device=None, stream=None, profile=False, force_offsets64=False,
-                 partition_cap=0, partition_target=0):
+                 partition_cap=0, partition_target=0, fail_alloc_at=0):
     lib = load_library()
     o = tcrnet_options()
     lib.tcrnet_options_init(ctypes.byref(o))
@@ -203,6 +204,7 @@ def make_options(method="auto", device=None, stream=None, profile=False, force_o
     o.force_offsets64 = 1 if force_offsets64 else 0
     o.partition_cap = int(partition_cap)
     o.partition_target = int(partition_target)
+    o.fail_alloc_at = int(fail_alloc_at)
     return o
 
 

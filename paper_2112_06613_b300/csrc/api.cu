@@ -45,6 +45,21 @@ static thread_local int64_t t_last_bad = -1;
 static thread_local int64_t t_launches = 0;
 
 void note_launch() { ++t_launches; }
+
+static thread_local int64_t t_alloc_countdown = -1;  // -1: fault injection off
+
+bool alloc_fault_tick() {
+    if (t_alloc_countdown < 0) return false;
+    if (t_alloc_countdown == 0) return true;  // stays armed: later allocations fail too
+    --t_alloc_countdown;
+    return t_alloc_countdown == 0;
+}
+
+AllocFaultScope::AllocFaultScope(int32_t fail_at) : saved_(t_alloc_countdown) {
+    t_alloc_countdown = fail_at > 0 ? (int64_t)fail_at : -1;
+}
+
+AllocFaultScope::~AllocFaultScope() { t_alloc_countdown = saved_; }
 int64_t launches_so_far() { return t_launches; }
 
 // ---- build workspace arena (see common.cuh) ----
@@ -432,6 +447,7 @@ tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n
     tcrnet_options opt;
     tcrnet_options_init(&opt);
     if (opt_in) opt = *opt_in;
+    AllocFaultScope fault_scope(opt.fail_alloc_at);
     if (n < 0 || n > 0x7fffffffLL) return TCRNET_EINVAL;
     if (T < 0) return TCRNET_EINVAL;
     if (opt.method < TCRNET_METHOD_AUTO || opt.method > TCRNET_METHOD_DELETION) return TCRNET_EINVAL;
@@ -587,6 +603,7 @@ tcrnet_status tcrnet_query_ex(tcrnet_handle h, const uint8_t* chars, const int64
     if (method < TCRNET_METHOD_AUTO || method > TCRNET_METHOD_DELETION) return TCRNET_EINVAL;
     if (method == TCRNET_METHOD_AUTO) method = h->ix.valid() ? TCRNET_METHOD_DELETION : TCRNET_METHOD_TILE;
     if (method == TCRNET_METHOD_DELETION && !h->ix.valid()) return TCRNET_ENOTSUP;
+    AllocFaultScope fault_scope(opt ? opt->fail_alloc_at : 0);
     DeviceGuard dg;
     TCR_CHECK(dg.set(h->device));
     cudaStream_t s = (opt && opt->stream) ? (cudaStream_t)opt->stream : h->stream;
@@ -690,7 +707,9 @@ tcrnet_status extend_impl(tcrnet_handle h, const uint8_t* chars, const int64_t* 
     if (opt_in) {
         opt.stream = opt_in->stream;
         opt.profile = opt_in->profile;
+        opt.fail_alloc_at = opt_in->fail_alloc_at;
     }
+    AllocFaultScope fault_scope(opt.fail_alloc_at);
     DeviceGuard dg;
     TCR_CHECK(dg.set(h->device));
     cudaStream_t s = opt.stream ? (cudaStream_t)opt.stream : h->stream;

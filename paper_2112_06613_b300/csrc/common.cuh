@@ -202,6 +202,21 @@ private:
 // (alloc), otherwise stream-ordered cudaMallocAsync / cudaFreeAsync; alloc_owned
 // always allocates (for results a handle keeps). Freed when it goes out of
 // scope unless released.
+// Host-side fault injection (options.fail_alloc_at): when armed, the k-th
+// allocation of the calling thread's current call fails with ENOMEM.
+bool alloc_fault_tick();  // true: fail this allocation
+
+class AllocFaultScope {
+public:
+    explicit AllocFaultScope(int32_t fail_at);
+    ~AllocFaultScope();
+    AllocFaultScope(const AllocFaultScope&) = delete;
+    AllocFaultScope& operator=(const AllocFaultScope&) = delete;
+
+private:
+    int64_t saved_;
+};
+
 class DevBuf {
 public:
     DevBuf() = default;
@@ -225,6 +240,10 @@ public:
     }
     ~DevBuf() { reset(); }
     tcrnet_status alloc(size_t bytes, cudaStream_t s) {
+        if (alloc_fault_tick()) {
+            reset();
+            return TCRNET_ENOMEM;
+        }
         if (arena_active()) {
             reset();
             cudaError_t e = cudaSuccess;
@@ -240,9 +259,14 @@ public:
             arena_ = true;
             return TCRNET_OK;
         }
-        return alloc_owned(bytes, s);
+        return owned_alloc(bytes, s);
     }
     tcrnet_status alloc_owned(size_t bytes, cudaStream_t s) {
+        reset();
+        if (alloc_fault_tick()) return TCRNET_ENOMEM;
+        return owned_alloc(bytes, s);
+    }
+    tcrnet_status owned_alloc(size_t bytes, cudaStream_t s) {
         reset();
         s_ = s;
         bytes_ = bytes;
