@@ -160,6 +160,19 @@ tcrnet_status tcrnet_build_batched(const uint8_t *chars, const int64_t *offsets,
                                    const int64_t *rep_offsets, int64_t nrep, int32_t mem, int32_t threshold,
                                    const tcrnet_options *opt, tcrnet_handle *out);
 
+/*
+ * Checkpoint / resume of a serving state. tcrnet_save writes a build handle
+ * (network, resident strings and, for deletion builds, the query index) to the
+ * file `path` (host byte order, format version 1); tcrnet_load makes a new
+ * handle from such a file on opt->device / opt->stream (opt may be NULL) that
+ * answers queries and inserts like the saved one. Errors: TCRNET_EINVAL (NULL
+ * argument, unreadable or unwritable file, bad magic, version or sizes; the
+ * header is checked before any device work), TCRNET_ESTATE (query results are
+ * not saved), TCRNET_ENOMEM / TCRNET_EDEVICE.
+ */
+tcrnet_status tcrnet_save(tcrnet_handle h, const char *path);
+tcrnet_status tcrnet_load(const char *path, const tcrnet_options *opt, tcrnet_handle *out);
+
 /* Size of a handle's CSR: rows, directed entries (nnz = sum of degrees) and
  * whether exported offsets are int64 (nnz >= 2^31 or force_offsets64). Any
  * pointer may be NULL. */

@@ -100,7 +100,7 @@ SYMBOLS = [
     "tcrnet_strerror", "tcrnet_last_error_index", "tcrnet_version", "tcrnet_last_cuda_error",
     "tcrnet_degree_noalloc", "tcrnet_query_ex", "tcrnet_insert_flat", "tcrnet_insert_ex", "tcrnet_insert",
     "tcrnet_components", "tcrnet_neighbor_degree", "tcrnet_build_batched",
-    "tcrnet_degree_histogram", "tcrnet_extend",
+    "tcrnet_degree_histogram", "tcrnet_extend", "tcrnet_save", "tcrnet_load",
 ]
 
 
@@ -133,6 +133,10 @@ def load_library(path: str = LIB_PATH):
         lib.tcrnet_csr_device.restype = ctypes.c_int
         lib.tcrnet_query_flat.argtypes = [H, vp, vp, i64, i32, HP]
         lib.tcrnet_query_flat.restype = ctypes.c_int
+        lib.tcrnet_save.argtypes = [H, ctypes.c_char_p]
+        lib.tcrnet_save.restype = ctypes.c_int
+        lib.tcrnet_load.argtypes = [ctypes.c_char_p, optp, HP]
+        lib.tcrnet_load.restype = ctypes.c_int
         lib.tcrnet_extend.argtypes = [H, vp, vp, i64, i32, optp, HP]
         lib.tcrnet_extend.restype = ctypes.c_int
         lib.tcrnet_degree_histogram.argtypes = [H, vp, i64, i32, ctypes.POINTER(i64)]
@@ -348,6 +352,10 @@ class Graph:
         del keep
         _check(st, "tcrnet_insert_ex")
 
+    def save(self, path: str):
+        """Checkpoint this handle (network, resident strings, query index) to a file."""
+        _check(load_library().tcrnet_save(self._h, os.fsencode(path)), "tcrnet_save")
+
     def extend_flat(self, chars, offsets, stream=None, profile=False) -> "Graph":
         """Copy-on-write insert: a new Graph of this one's strings plus the new ones;
         this Graph is unchanged and may keep serving queries meanwhile."""
@@ -413,6 +421,15 @@ def tcrnet_build_flat(chars, offsets, threshold: int = 1, method="auto", device=
     st = lib.tcrnet_build_flat(cp, op, n, mem, int(threshold), ctypes.byref(opt), ctypes.byref(h))
     del keep
     _check(st, "tcrnet_build_flat")
+    return Graph(h.value)
+
+
+def tcrnet_load(path: str, device=None, stream=None) -> Graph:
+    """A handle restored from a tcrnet_save checkpoint."""
+    lib = load_library()
+    opt = make_options("auto", device, stream)
+    h = ctypes.c_void_p()
+    _check(lib.tcrnet_load(os.fsencode(path), ctypes.byref(opt), ctypes.byref(h)), "tcrnet_load")
     return Graph(h.value)
 
 

@@ -907,6 +907,215 @@ tcrnet_status tcrnet_degree_histogram(tcrnet_handle h, int64_t* hist, int64_t nb
     return TCRNET_OK;
 }
 
+}  // extern "C"
+
+namespace tcr {
+namespace {
+
+// ---- checkpoint file -------------------------------------------------------
+// Header (fixed layout, host byte order) then the device arrays, each as a u64
+// byte count followed by the bytes. Arrays: offsets, cols, degree, then the
+// resident strings (bucketed copy + order, or input-order copy + lengths),
+// then the deletion index when present.
+constexpr char kMagic[8] = {'T', 'C', 'R', 'N', 'E', 'T', 'C', 'K'};
+constexpr uint32_t kFileVersion = 1;
+
+struct FileHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t header_bytes;
+    int32_t threshold, offsets64, batched, has_bucketed, has_input_order, has_index;
+    int64_t n, nnz, lensum, ix_U, ix_P, ix_R;
+    int64_t bucket_off[kMaxLen + 2];
+    tcrnet_stats stats;
+};
+
+bool write_array(std::FILE* f, const void* dev, uint64_t bytes, cudaStream_t s, std::vector<char>& staging) {
+    if (std::fwrite(&bytes, sizeof(bytes), 1, f) != 1) return false;
+    if (bytes == 0) return true;
+    staging.resize(bytes);
+    if (cudaMemcpyAsync(staging.data(), dev, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return false;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return false;
+    return std::fwrite(staging.data(), 1, bytes, f) == bytes;
+}
+
+tcrnet_status read_array(std::FILE* f, uint64_t expect, void** dev, cudaStream_t s, std::vector<char>& staging) {
+    uint64_t bytes = 0;
+    if (std::fread(&bytes, sizeof(bytes), 1, f) != 1 || bytes != expect) return TCRNET_EINVAL;
+    DevBuf b;
+    TCR_CHECK(b.alloc_owned(bytes, s));
+    if (bytes > 0) {
+        staging.resize(bytes);
+        if (std::fread(staging.data(), 1, bytes, f) != bytes) return TCRNET_EINVAL;
+        TCR_CUDA(cudaMemcpyAsync(b.as<void>(), staging.data(), bytes, cudaMemcpyHostToDevice, s));
+        TCR_CUDA(cudaStreamSynchronize(s));
+    }
+    *dev = b.release();
+    return TCRNET_OK;
+}
+
+}  // namespace
+}  // namespace tcr
+
+extern "C" {
+
+tcrnet_status tcrnet_save(tcrnet_handle h, const char* path) {
+    if (!h || !path) return TCRNET_EINVAL;
+    if (h->query_result) return TCRNET_ESTATE;
+    DeviceGuard dg;
+    TCR_CHECK(dg.set(h->device));
+    FileHeader hd;
+    std::memset(&hd, 0, sizeof(hd));
+    std::memcpy(hd.magic, kMagic, sizeof(kMagic));
+    hd.version = kFileVersion;
+    hd.header_bytes = (uint32_t)sizeof(FileHeader);
+    hd.threshold = h->threshold;
+    hd.offsets64 = h->offsets64;
+    hd.batched = h->batched ? 1 : 0;
+    hd.has_bucketed = h->d_bcanon ? 1 : 0;
+    hd.has_input_order = h->d_canon_in ? 1 : 0;
+    hd.has_index = h->ix.valid() ? 1 : 0;
+    hd.n = h->n;
+    hd.nnz = h->nnz;
+    hd.lensum = h->lensum;
+    for (int L = 0; L < kMaxLen + 2; ++L) hd.bucket_off[L] = h->bucket_off[L];
+    hd.stats = h->stats;
+    cudaStream_t s = h->stream;
+    if (hd.has_index) {
+        hd.ix_U = h->ix.U;
+        hd.ix_P = h->ix.P;
+        TCR_CUDA(cudaMemcpyAsync(&hd.ix_R, h->ix.poff + h->ix.P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        TCR_CUDA(cudaStreamSynchronize(s));
+    }
+    std::FILE* f = std::fopen(path, "wb");
+    if (!f) return TCRNET_EINVAL;
+    std::vector<char> st;
+    const uint64_t n = (uint64_t)h->n;
+    bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1;
+    ok = ok && write_array(f, h->d_offsets, (n + 1) * (h->offsets64 ? 8 : 4), s, st);
+    ok = ok && write_array(f, h->d_cols, (uint64_t)h->nnz * 4, s, st);
+    ok = ok && write_array(f, h->d_degree, n * 4, s, st);
+    if (hd.has_bucketed) {
+        ok = ok && write_array(f, h->d_bcanon, n * sizeof(Canon), s, st);
+        ok = ok && write_array(f, h->d_bperm, n * 4, s, st);
+    }
+    if (hd.has_input_order) {
+        ok = ok && write_array(f, h->d_canon_in, n * sizeof(Canon), s, st);
+        ok = ok && write_array(f, h->d_lens, n, s, st);
+    }
+    if (hd.has_index) {
+        ok = ok && write_array(f, h->ix.ucanon, (uint64_t)h->ix.U * sizeof(Canon), s, st);
+        ok = ok && write_array(f, h->ix.umult, n * 4, s, st);
+        ok = ok && write_array(f, h->ix.mem_off, (n + 1) * 8, s, st);
+        ok = ok && write_array(f, h->ix.members, n * 4, s, st);
+        ok = ok && write_array(f, h->ix.recs, (uint64_t)hd.ix_R * 8, s, st);
+        ok = ok && write_array(f, h->ix.poff, ((uint64_t)h->ix.P + 1) * 8, s, st);
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? TCRNET_OK : TCRNET_EINVAL;
+}
+
+tcrnet_status tcrnet_load(const char* path, const tcrnet_options* opt_in, tcrnet_handle* out) {
+    if (!out) return TCRNET_EINVAL;
+    *out = nullptr;
+    if (!path) return TCRNET_EINVAL;
+    tcrnet_options opt;
+    tcrnet_options_init(&opt);
+    if (opt_in) opt = *opt_in;
+    std::FILE* f = std::fopen(path, "rb");
+    if (!f) return TCRNET_EINVAL;
+    FileHeader hd;
+    // the header is checked before any device work
+    const bool head_ok = std::fread(&hd, sizeof(hd), 1, f) == 1 && std::memcmp(hd.magic, kMagic, 8) == 0 &&
+                         hd.version == kFileVersion && hd.header_bytes == sizeof(FileHeader) && hd.n >= 0 &&
+                         hd.n <= 0x7fffffffLL && hd.nnz >= 0 && hd.threshold >= 0 &&
+                         (hd.offsets64 == 0 || hd.offsets64 == 1) && (hd.has_index == 0 || hd.has_index == 1) &&
+                         hd.ix_U >= 0 && hd.ix_U <= hd.n && hd.ix_P >= 0 && hd.ix_R >= 0 &&
+                         (hd.offsets64 || hd.nnz <= 0x7fffffffLL);
+    if (!head_ok) {
+        std::fclose(f);
+        return TCRNET_EINVAL;
+    }
+    DeviceGuard dg;
+    tcrnet_status st = dg.set(opt.device);
+    if (st != TCRNET_OK) {
+        std::fclose(f);
+        return st;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    configure_pool(dev);
+    cudaStream_t s = (cudaStream_t)opt.stream;
+    tcrnet_graph* h = new (std::nothrow) tcrnet_graph();
+    if (!h) {
+        std::fclose(f);
+        return TCRNET_ENOMEM;
+    }
+    h->device = dev;
+    h->stream = s;
+    h->threshold = hd.threshold;
+    h->batched = hd.batched != 0;
+    h->n = hd.n;
+    h->nnz = hd.nnz;
+    h->offsets64 = hd.offsets64;
+    h->lensum = hd.lensum;
+    for (int L = 0; L < kMaxLen + 2; ++L) h->bucket_off[L] = hd.bucket_off[L];
+    h->stats = hd.stats;
+    const uint64_t n = (uint64_t)hd.n;
+    std::vector<char> buf;
+    void* p = nullptr;
+    auto rd = [&](uint64_t bytes) {
+        p = nullptr;
+        return st == TCRNET_OK ? (st = read_array(f, bytes, &p, s, buf)) : st;
+    };
+    if (rd((n + 1) * (hd.offsets64 ? 8 : 4)) == TCRNET_OK) h->d_offsets = p;
+    if (rd((uint64_t)hd.nnz * 4) == TCRNET_OK) h->d_cols = static_cast<int32_t*>(p);
+    if (rd(n * 4) == TCRNET_OK) h->d_degree = static_cast<int32_t*>(p);
+    if (hd.has_bucketed) {
+        if (rd(n * sizeof(Canon)) == TCRNET_OK) h->d_bcanon = static_cast<Canon*>(p);
+        if (rd(n * 4) == TCRNET_OK) h->d_bperm = static_cast<int32_t*>(p);
+    }
+    if (hd.has_input_order) {
+        if (rd(n * sizeof(Canon)) == TCRNET_OK) h->d_canon_in = static_cast<Canon*>(p);
+        if (rd(n) == TCRNET_OK) h->d_lens = static_cast<uint8_t*>(p);
+    }
+    if (hd.has_index) {
+        // the index arrays are sized for n strings (ids >= U unused)
+        DevBuf uc;
+        if (st == TCRNET_OK) st = uc.alloc_owned(sizeof(Canon) * (n > 0 ? n : 1), s);
+        if (st == TCRNET_OK) {
+            uint64_t bytes = 0;
+            const uint64_t want = (uint64_t)hd.ix_U * sizeof(Canon);
+            if (std::fread(&bytes, sizeof(bytes), 1, f) != 1 || bytes != want) st = TCRNET_EINVAL;
+            if (st == TCRNET_OK && bytes > 0) {
+                buf.resize(bytes);
+                if (std::fread(buf.data(), 1, bytes, f) != bytes) st = TCRNET_EINVAL;
+                else if (cudaMemcpyAsync(uc.as<void>(), buf.data(), bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                         cudaStreamSynchronize(s) != cudaSuccess)
+                    st = TCRNET_EDEVICE;
+            }
+            if (st == TCRNET_OK) h->ix.ucanon = static_cast<Canon*>(uc.release());
+        }
+        if (rd(n * 4) == TCRNET_OK) h->ix.umult = static_cast<int32_t*>(p);
+        if (rd((n + 1) * 8) == TCRNET_OK) h->ix.mem_off = static_cast<int64_t*>(p);
+        if (rd(n * 4) == TCRNET_OK) h->ix.members = static_cast<int32_t*>(p);
+        if (rd((uint64_t)hd.ix_R * 8) == TCRNET_OK) h->ix.recs = static_cast<uint64_t*>(p);
+        if (rd(((uint64_t)hd.ix_P + 1) * 8) == TCRNET_OK) h->ix.poff = static_cast<int64_t*>(p);
+        h->ix.U = hd.ix_U;
+        h->ix.P = hd.ix_P;
+        h->ix.n = hd.n;
+    }
+    std::fclose(f);
+    if (st != TCRNET_OK) {
+        cudaStreamSynchronize(s);
+        free_handle_memory(h);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return TCRNET_OK;
+}
+
 tcrnet_status tcrnet_stats_get(tcrnet_handle h, tcrnet_stats* out) {
     if (!h || !out) return TCRNET_EINVAL;
     *out = h->stats;

@@ -108,3 +108,18 @@ def test_partition_target_out_of_range_rejected(target):
     assert lib.tcrnet_build_flat(chars.ctypes.data, offsets.ctypes.data, 1, tn.HOST, 1, ctypes.byref(opt),
                                  ctypes.byref(h)) == tn.EINVAL
     assert h.value is None
+
+
+def test_load_rejects_bad_files_before_device_work(tmp_path):
+    lib = tn.load_library()
+    h = ctypes.c_void_p()
+    bad = tmp_path / "bad.tcr"
+    bad.write_bytes(b"not a checkpoint" * 20)
+    assert lib.tcrnet_load(str(bad).encode(), None, ctypes.byref(h)) == tn.EINVAL
+    short = tmp_path / "short.tcr"
+    short.write_bytes(b"TCRNETCK")
+    assert lib.tcrnet_load(str(short).encode(), None, ctypes.byref(h)) == tn.EINVAL
+    assert lib.tcrnet_load(str(tmp_path / "missing.tcr").encode(), None, ctypes.byref(h)) == tn.EINVAL
+    assert lib.tcrnet_load(None, None, ctypes.byref(h)) == tn.EINVAL
+    assert h.value is None
+    assert lib.tcrnet_save(None, str(tmp_path / "x.tcr").encode()) == tn.EINVAL
