@@ -43,8 +43,10 @@ def records_estimate(offsets) -> int:
     return n + total
 
 
-def size_class(records: int, batched: bool) -> str:
-    return f"{'batched' if batched else 'single'}:{int(math.log2(max(records, 1)))}"
+def size_class(records: int, batched: bool, device_name: str = "") -> str:
+    """Cache key: GPU model, batched or not, log2 of the record count."""
+    prefix = f"{device_name}|" if device_name else ""
+    return f"{prefix}{'batched' if batched else 'single'}:{int(math.log2(max(records, 1)))}"
 
 
 class PartitionTuner:
@@ -86,7 +88,7 @@ class PartitionTuner:
         import torch
 
         batched = rep_offsets is not None
-        key = size_class(records_estimate(offsets), batched)
+        key = size_class(records_estimate(offsets), batched, torch.cuda.get_device_name())
         s = stream if stream is not None else torch.cuda.current_stream()
 
         def timer(target):

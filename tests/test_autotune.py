@@ -34,3 +34,8 @@ def test_choice_is_fastest_and_cached(tmp_path):
     assert json.loads(path.read_text()) == {"single:23": 24}
     again = PartitionTuner(candidates=(16, 24, 32), cache_path=str(path))
     assert again.choose("single:23", lambda t: 1 / 0) == 24  # loaded from the file
+
+
+def test_size_class_keys_the_gpu_model():
+    assert size_class(1 << 20, False, "GPU A") != size_class(1 << 20, False, "GPU B")
+    assert size_class(1 << 20, False, "GPU A").startswith("GPU A|")

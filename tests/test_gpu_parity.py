@@ -412,3 +412,41 @@ def test_tile_write_pass_when_hits_overflow_the_kept_pairs(threshold):
     ro, rc, _ = oracle_csr(rep, threshold)
     assert_csr_equal(off, cols, ro, rc, f"dense tile build T={threshold}")
     check_invariants(off, cols, deg, rep.n)
+
+
+@pytest.mark.parametrize("method", ["deletion", "tile"])
+def test_repeat_builds_are_bit_identical(method):
+    # slots come from atomics in every write, yet rows are sorted: the result
+    # may not depend on scheduling
+    rep = generate_config1(30_000 if method == "deletion" else 6000, seed=111)
+    first = None
+    for k in range(4):
+        opts = {"partition_target": (12, 24, 40, 0)[k]} if method == "deletion" else {}
+        with tn.tcrnet_build_flat(rep.chars, rep.offsets, 1, method=method, **opts) as g:
+            off, cols, deg = g.copy_csr()
+        if first is None:
+            first = (np.asarray(off).copy(), cols.copy(), deg.copy())
+        else:
+            assert np.array_equal(off, first[0]) and np.array_equal(cols, first[1]) and np.array_equal(deg, first[2])
+
+
+def test_device_copy_leaves_guard_bytes_untouched():
+    import torch
+
+    rep = generate_config1(4000, seed=112)
+    with tn.tcrnet_build_flat(rep.chars, rep.offsets, 1, method="deletion") as g:
+        n, nnz, o64 = g.info()
+        guard = 4096
+        sentinel = -123456789
+        off = torch.full((guard + n + 1 + guard,), sentinel, dtype=torch.int64 if o64 else torch.int32, device="cuda")
+        cols = torch.full((guard + nnz + guard,), sentinel, dtype=torch.int32, device="cuda")
+        deg = torch.full((guard + n + guard,), sentinel, dtype=torch.int32, device="cuda")
+        st = tn.load_library().tcrnet_copy_csr(g.handle, off[guard:].data_ptr(), cols[guard:].data_ptr(),
+                                               deg[guard:].data_ptr(), tn.DEVICE)
+        assert st == tn.OK
+        torch.cuda.synchronize()
+        for t, inner in ((off, n + 1), (cols, nnz), (deg, n)):
+            assert (t[:guard] == sentinel).all() and (t[guard + inner:] == sentinel).all()
+        ho, hc, hd = g.copy_csr()
+        assert np.array_equal(off[guard:guard + n + 1].cpu().numpy(), ho)
+        assert np.array_equal(cols[guard:guard + nnz].cpu().numpy(), hc)
