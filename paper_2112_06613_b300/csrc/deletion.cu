@@ -388,24 +388,27 @@ __device__ __forceinline__ int64_t record_edges_checked(const uint64_t* buf, int
                                                         const Canon* __restrict__ ucanon, bool& bad) {
     const uint64_t key = buf[k];
     if (rec_p(key) == kTagF) return 0;
-    int64_t cnt = 0;
-    int k2 = k + 1;
-    bool have = false;
-    Canon ck;
-    for (; k2 < s && (buf[k2] >> 26) == (key >> 26); ++k2) {
-        if (!have) {
-            ck = record_content(key, ucanon);
-            have = true;
-        }
-        if (canon_eq(ck, record_content(buf[k2], ucanon))) ++cnt;
-        else bad = true;
-    }
-    if (T >= 1 && rec_runstart(key)) {
-        int g = k2;
+    // the run [r0, r1) of equal (hash, p) around k: every member is compared
+    // with the run's first record once (all equal to it => pairwise equal),
+    // instead of each member loading every later one (hot runs of a shared
+    // deletion variant made that a chain of dependent loads)
+    int r1 = k + 1;
+    while (r1 < s && (buf[r1] >> 26) == (key >> 26)) ++r1;
+    int r0 = k;
+    while (r0 > 0 && (buf[r0 - 1] >> 26) == (key >> 26)) --r0;
+    int64_t cnt = r1 - k - 1;
+    const bool indel_try = T >= 1 && rec_runstart(key);
+    uint64_t last = 0;
+    if (indel_try) {
+        int g = r1;
         while (g < s && (buf[g] >> 32) == (key >> 32)) ++g;
-        const uint64_t last = buf[g - 1];
-        if (rec_p(last) == kTagF) {
-            if (!have) ck = record_content(key, ucanon);
+        last = buf[g - 1];
+    }
+    const bool indel = indel_try && rec_p(last) == kTagF;
+    if (r1 - r0 > 1 || indel) {
+        const Canon ck = record_content(key, ucanon);
+        if (k != r0 && !canon_eq(ck, record_content(buf[r0], ucanon))) bad = true;
+        if (indel) {
             if (canon_eq(ck, record_content(last, ucanon))) ++cnt;
             else bad = true;
         }
