@@ -75,12 +75,26 @@ struct DeviceArena {
     std::vector<Chunk> chunks;
     size_t cur = 0;   // chunk being carved
     size_t used = 0;  // bytes used in chunks[cur]
+    SideStream side;  // created on first use, kept for the process
+    bool side_ok = false;
 };
 DeviceArena g_arenas[64];
 thread_local DeviceArena* t_arena = nullptr;
 }  // namespace
 
 bool arena_active() { return t_arena != nullptr; }
+
+const SideStream* leased_side_stream() {
+    DeviceArena* a = t_arena;
+    if (!a) return nullptr;
+    if (!a->side_ok) {
+        if (cudaStreamCreateWithFlags(&a->side.stream, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+        for (auto& e : a->side.ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        a->side_ok = true;
+    }
+    return &a->side;
+}
 
 namespace {
 std::mutex g_event_mu;
@@ -155,8 +169,11 @@ ArenaLease::ArenaLease(int device, cudaStream_t s) : dev_(device), s_(s) {
 
 ArenaLease::~ArenaLease() {
     if (!held_) return;
-    // the next lease reuses this memory: the call's work must be complete
+    // the next lease reuses this memory: the call's work must be complete,
+    // on its stream and on the side stream (an early error return may leave
+    // forked work there)
     cudaStreamSynchronize(s_);
+    if (g_arenas[dev_].side_ok) cudaStreamSynchronize(g_arenas[dev_].side.stream);
     t_arena = nullptr;
     g_arenas[dev_].mu.unlock();
 }

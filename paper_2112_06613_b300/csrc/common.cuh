@@ -148,6 +148,14 @@ int64_t launches_so_far();
 // Buffers handed to a handle are never carved from the arena.
 void* arena_carve(size_t bytes, cudaError_t* err);  // nullptr: no lease on this thread
 bool arena_active();
+// While the calling thread holds its device's workspace lease: a second stream
+// of that device and `count` (<= 4) events for forking independent work off the
+// call's stream and joining it back (null: no lease; run everything in order).
+struct SideStream {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+const SideStream* leased_side_stream();
 
 // Events for the optional phase timing, recycled through a per-device pool so
 // that a profiled build does not create and destroy events on its critical path.

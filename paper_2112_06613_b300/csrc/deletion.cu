@@ -919,11 +919,21 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     k_uid<<<grid_for(n), kThreads, 0, s>>>(slot_of.as<int32_t>(), slot_u.as<int32_t>(), n, uid.as<int32_t>(),
                                            umult.as<int32_t>());
     TCR_LAUNCH_CHECK();
-    TCR_CHECK(scan_exclusive_i32_to_i64(umult.as<int32_t>(), mem_off.as<int64_t>(), n, s));
-    TCR_CUDA(cudaMemsetAsync(mcur.as<void>(), 0, sizeof(int32_t) * n, s));
-    k_members<<<grid_for(n), kThreads, 0, s>>>(uid.as<int32_t>(), n, mem_off.as<int64_t>(), mcur.as<int32_t>(),
-                                               members.as<int32_t>(), mpos.as<int32_t>());
+    // member lists M_u are first needed when the closed lists are filled: build
+    // them on the side stream while the records and the join run
+    const SideStream* side = leased_side_stream();
+    cudaStream_t ms = s;
+    if (side) {
+        TCR_CUDA(cudaEventRecord(side->ev[0], s));
+        TCR_CUDA(cudaStreamWaitEvent(side->stream, side->ev[0], 0));
+        ms = side->stream;
+    }
+    TCR_CHECK(scan_exclusive_i32_to_i64(umult.as<int32_t>(), mem_off.as<int64_t>(), n, ms));
+    TCR_CUDA(cudaMemsetAsync(mcur.as<void>(), 0, sizeof(int32_t) * n, ms));
+    k_members<<<grid_for(n), kThreads, 0, ms>>>(uid.as<int32_t>(), n, mem_off.as<int64_t>(), mcur.as<int32_t>(),
+                                                members.as<int32_t>(), mpos.as<int32_t>());
     TCR_LAUNCH_CHECK();
+    if (side) TCR_CUDA(cudaEventRecord(side->ev[1], ms));
     const int t1 = tm.mark();
 
     // ---- 2. records
@@ -1013,6 +1023,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     int n_two_pass = 0;
     DevBuf Sbuf;
     TCR_CHECK(Sbuf.alloc(sizeof(int32_t) * SD, s));
+    if (side) TCR_CUDA(cudaStreamWaitEvent(s, side->ev[1], 0));  // member lists ready
     k_closed_self<<<grid_for(n), kThreads, 0, s>>>(uid.as<int32_t>(), mpos.as<int32_t>(), n, uoff.as<int64_t>(),
                                                    Sbuf.as<int32_t>());
     TCR_LAUNCH_CHECK();
