@@ -1023,10 +1023,23 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     int n_two_pass = 0;
     DevBuf Sbuf;
     TCR_CHECK(Sbuf.alloc(sizeof(int32_t) * SD, s));
-    if (side) TCR_CUDA(cudaStreamWaitEvent(s, side->ev[1], 0));  // member lists ready
-    k_closed_self<<<grid_for(n), kThreads, 0, s>>>(uid.as<int32_t>(), mpos.as<int32_t>(), n, uoff.as<int64_t>(),
-                                                   Sbuf.as<int32_t>());
+    // int32 row offsets for the handle
+    DevBuf off32;
+    if (!force_off64 && nnz <= 0x7fffffffLL) TCR_CHECK(off32.alloc_owned(sizeof(int32_t) * (n + 1), s));
+    // each list's own members (after its member list exists) and the narrowed
+    // offsets go to the side stream, next to the neighbour appends on this one
+    cudaStream_t fs = s;
+    if (side) {
+        TCR_CUDA(cudaEventRecord(side->ev[2], s));
+        TCR_CUDA(cudaStreamWaitEvent(side->stream, side->ev[2], 0));
+        TCR_CUDA(cudaStreamWaitEvent(s, side->ev[1], 0));  // member lists ready for the appends
+        fs = side->stream;
+    }
+    k_closed_self<<<grid_for(n), kThreads, 0, fs>>>(uid.as<int32_t>(), mpos.as<int32_t>(), n, uoff.as<int64_t>(),
+                                                    Sbuf.as<int32_t>());
     TCR_LAUNCH_CHECK();
+    if (off32.as<void>()) TCR_CHECK(narrow_offsets(off64.as<int64_t>(), off32.as<int32_t>(), n + 1, fs));
+    if (side) TCR_CUDA(cudaEventRecord(side->ev[3], fs));
     // ---- 3b. edges that did not fit: second join pass at scanned positions;
     // then append neighbour member lists
     int64_t fill_segs = kEdgeSegs, fill_cap = seg_cap;
@@ -1067,6 +1080,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
                                                             Sbuf.as<int32_t>(), d_err + 1);
         TCR_LAUNCH_CHECK();
     }
+    if (side) TCR_CUDA(cudaStreamWaitEvent(s, side->ev[3], 0));  // own members and offsets written
     const int t4 = tm.mark();
     if (!keep_index) recs.reset();
     edges.reset();
@@ -1079,13 +1093,6 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     k_expand<<<(unsigned)std::min<int64_t>(ceil_div(n, 32 * kWarps), (int64_t)num_sms * 16), kThreads, 0, s>>>(
         uid.as<int32_t>(), n, uoff.as<int64_t>(), Sbuf.as<int32_t>(), off64.as<int64_t>(), cols.as<int32_t>());
     TCR_LAUNCH_CHECK();
-    // int32 row offsets for the handle, queued behind the expansion so that no
-    // kernel follows the final read-back
-    DevBuf off32;
-    if (!force_off64 && nnz <= 0x7fffffffLL) {
-        TCR_CHECK(off32.alloc_owned(sizeof(int32_t) * (n + 1), s));
-        TCR_CHECK(narrow_offsets(off64.as<int64_t>(), off32.as<int32_t>(), n + 1, s));
-    }
     const int t6 = tm.mark();
     int h_err[4] = {0, 0, 0, 0};  // the first four device counters
     int64_t h_U = 0, h_R = 0;
