@@ -848,10 +848,21 @@ __global__ void k_expand(const int32_t* __restrict__ uid, int64_t n, const int64
             const int32_t me = (int32_t)(r0 + j);
             const int32_t* su = S + js0;
             int32_t* row = cols + jo;
-            for (int64_t k = lane; k < jD; k += 32) {
-                const int32_t x = su[k];
-                const int64_t q = k - (x > me ? 1 : 0);
-                if (x != me && q < jD - 1) row[q] = x;  // q < D - 1 always holds when i is in S_u
+            // four loads per lane in flight before their stores
+            const int iD = (int)jD;
+            for (int k0 = 0; k0 < iD; k0 += 128) {
+                int32_t x[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int k = k0 + lane + 32 * t;
+                    x[t] = k < iD ? su[k] : me;
+                }
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int k = k0 + lane + 32 * t;
+                    const int q = k - (x[t] > me ? 1 : 0);
+                    if (x[t] != me && q < iD - 1) row[q] = x[t];  // q < D - 1 always holds when i is in S_u
+                }
             }
         }
     }
