@@ -158,6 +158,130 @@ k_degree_hist(const int32_t* __restrict__ deg, int64_t n, unsigned long long* __
             if (bins[b]) atomicAdd(&hist[b], (unsigned long long)bins[b]);
 }
 
+// ---- the same analyses on the graph of distinct strings --------------------
+// A deletion build keeps node -> distinct string (uid) and the edges between
+// distinct strings, each once. The members of a distinct string are a clique,
+// so with node removal a string is present iff one of its members is kept,
+// the network's components are those of the string graph restricted to
+// present strings, and a kept node's component is its string's. Work is
+// proportional to the U strings and E edges instead of the nnz entries.
+
+__global__ void k_dcc_init(const int32_t* __restrict__ uid, const uint8_t* __restrict__ keep, int64_t n,
+                           int32_t* __restrict__ present) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && (keep == nullptr || keep[i])) present[uid[i]] = 1;
+}
+
+__global__ void k_dcc_parent(const int32_t* __restrict__ present, int64_t U, int32_t* __restrict__ parent,
+                             int32_t* __restrict__ cmin, int32_t* __restrict__ size) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= U) return;
+    parent[u] = present[u] ? (int32_t)u : -1;
+    cmin[u] = 0x7fffffff;
+    size[u] = 0;
+}
+
+__global__ void k_dcc_link(const int2* __restrict__ edges, int64_t E, int32_t* parent, int* __restrict__ err) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x) {
+        const int2 e = edges[k];
+        if (((volatile int32_t*)parent)[e.x] < 0 || ((volatile int32_t*)parent)[e.y] < 0) continue;
+        int32_t a = e.x, c = e.y;
+        int it = 0;
+        for (; it < kMaxLinkRetries; ++it) {
+            int32_t ra = find_root(parent, a), rc = find_root(parent, c);
+            if (ra == rc) break;
+            if (ra > rc) {
+                const int32_t t = ra;
+                ra = rc;
+                rc = t;
+            }
+            if (atomicCAS(&parent[rc], rc, ra) == rc) break;
+            a = ra;
+            c = rc;
+        }
+        if (it == kMaxLinkRetries) atomicExch(err, 1);
+    }
+}
+
+// per kept node: its string's root collects the smallest kept node id and the size
+__global__ void k_dcc_members(const int32_t* __restrict__ uid, const uint8_t* __restrict__ keep, int64_t n,
+                              int32_t* parent, int32_t* __restrict__ cmin, int32_t* __restrict__ size) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || (keep != nullptr && !keep[i])) return;
+    const int32_t r = find_root(parent, uid[i]);
+    atomicMin(&cmin[r], (int32_t)i);
+    atomicAdd(&size[r], 1);
+}
+
+__global__ void k_dcc_label(const int32_t* __restrict__ uid, const uint8_t* __restrict__ keep, int64_t n,
+                            int32_t* parent, const int32_t* __restrict__ cmin, int32_t* __restrict__ labels) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    labels[i] = (keep != nullptr && !keep[i]) ? -1 : cmin[find_root(parent, uid[i])];
+}
+
+__global__ void k_dcc_reduce(const int32_t* __restrict__ parent, const int32_t* __restrict__ size, int64_t U,
+                             unsigned long long* __restrict__ out /* [0] components, [1] largest */) {
+    unsigned long long roots = 0, largest = 0;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < U; u += (int64_t)gridDim.x * blockDim.x) {
+        if (parent[u] == (int32_t)u) {
+            ++roots;
+            largest = largest > (unsigned long long)size[u] ? largest : (unsigned long long)size[u];
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        roots += __shfl_down_sync(kFull, roots, d);
+        const unsigned long long o = __shfl_down_sync(kFull, largest, d);
+        largest = largest > o ? largest : o;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&out[0], roots);
+        atomicMax(&out[1], largest);
+    }
+}
+
+// d_nn per distinct string u: the members of u other than i (m_u - 1 nodes of
+// degree D_u - 1) and the members of each neighbour string v (m_v nodes of
+// degree D_v - 1), over the degree D_u - 1 of each member of u.
+__global__ void k_dknn_self(const int32_t* __restrict__ umult, const int64_t* __restrict__ dsize, int64_t U,
+                            double* __restrict__ acc) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < U) acc[u] = (double)(umult[u] - 1) * (double)(dsize[u] - 1);
+}
+
+__global__ void k_dknn_edges(const int2* __restrict__ edges, int64_t E, const int32_t* __restrict__ umult,
+                             const int64_t* __restrict__ dsize, double* __restrict__ acc) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x) {
+        const int2 e = edges[k];
+        atomicAdd(&acc[e.x], (double)umult[e.y] * (double)(dsize[e.y] - 1));
+        atomicAdd(&acc[e.y], (double)umult[e.x] * (double)(dsize[e.x] - 1));
+    }
+}
+
+__global__ void k_dsize_edges(const int2* __restrict__ edges, int64_t E, const int32_t* __restrict__ umult,
+                              unsigned long long* __restrict__ dsize) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x) {
+        const int2 e = edges[k];
+        atomicAdd(&dsize[e.x], (unsigned long long)umult[e.y]);
+        atomicAdd(&dsize[e.y], (unsigned long long)umult[e.x]);
+    }
+}
+
+__global__ void k_dsize_self(const int32_t* __restrict__ umult, int64_t U, unsigned long long* __restrict__ dsize) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < U) dsize[u] = (unsigned long long)umult[u];
+}
+
+__global__ void k_dknn_nodes(const int32_t* __restrict__ uid, int64_t n, const int64_t* __restrict__ dsize,
+                             const double* __restrict__ acc, double* __restrict__ knn) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t u = uid[i];
+    const int64_t d = dsize[u] - 1;
+    knn[i] = d > 0 ? acc[u] / (double)d : 0.0;
+}
+
 inline unsigned blocks_for(int64_t n, int per_block, int num_sms) {
     const int64_t b = ceil_div(n, per_block);
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms * 32));
@@ -197,6 +321,79 @@ tcrnet_status components(const void* off, bool off64, const int32_t* cols, int64
     if (h_err) return TCRNET_ETIMEOUT;
     *n_components = (int64_t)h[0];
     *largest = (int64_t)h[1];
+    return TCRNET_OK;
+}
+
+tcrnet_status components_distinct(const int32_t* uid, int64_t n, const int2* edges, int64_t E, int64_t U,
+                                  const uint8_t* keep, int32_t* labels, int64_t* n_components, int64_t* largest,
+                                  cudaStream_t s, int num_sms) {
+    *n_components = 0;
+    *largest = 0;
+    if (n == 0) return TCRNET_OK;
+    DevBuf present, parent, cmin, size, red;
+    TCR_CHECK(present.alloc(sizeof(int32_t) * U, s));
+    TCR_CHECK(parent.alloc(sizeof(int32_t) * U, s));
+    TCR_CHECK(cmin.alloc(sizeof(int32_t) * U, s));
+    TCR_CHECK(size.alloc(sizeof(int32_t) * U, s));
+    TCR_CHECK(red.alloc(sizeof(unsigned long long) * 2 + sizeof(int), s));
+    TCR_CUDA(cudaMemsetAsync(present.as<void>(), 0, sizeof(int32_t) * U, s));
+    TCR_CUDA(cudaMemsetAsync(red.as<void>(), 0, sizeof(unsigned long long) * 2 + sizeof(int), s));
+    int* err = reinterpret_cast<int*>(red.as<unsigned long long>() + 2);
+    const unsigned gn = (unsigned)ceil_div(n, kThreads), gu = (unsigned)ceil_div(U, kThreads);
+    k_dcc_init<<<gn, kThreads, 0, s>>>(uid, keep, n, present.as<int32_t>());
+    TCR_LAUNCH_CHECK();
+    k_dcc_parent<<<gu, kThreads, 0, s>>>(present.as<int32_t>(), U, parent.as<int32_t>(), cmin.as<int32_t>(),
+                                         size.as<int32_t>());
+    TCR_LAUNCH_CHECK();
+    if (E > 0) {
+        k_dcc_link<<<blocks_for(E, kThreads, num_sms), kThreads, 0, s>>>(edges, E, parent.as<int32_t>(), err);
+        TCR_LAUNCH_CHECK();
+    }
+    k_dcc_members<<<gn, kThreads, 0, s>>>(uid, keep, n, parent.as<int32_t>(), cmin.as<int32_t>(),
+                                          size.as<int32_t>());
+    TCR_LAUNCH_CHECK();
+    if (labels) {
+        k_dcc_label<<<gn, kThreads, 0, s>>>(uid, keep, n, parent.as<int32_t>(), cmin.as<int32_t>(), labels);
+        TCR_LAUNCH_CHECK();
+    }
+    k_dcc_reduce<<<blocks_for(U, kThreads, num_sms), kThreads, 0, s>>>(parent.as<int32_t>(), size.as<int32_t>(), U,
+                                                                       red.as<unsigned long long>());
+    TCR_LAUNCH_CHECK();
+    unsigned long long h[2] = {0, 0};
+    int h_err = 0;
+    TCR_CUDA(cudaMemcpyAsync(h, red.as<void>(), sizeof(h), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaStreamSynchronize(s));
+    if (h_err) return TCRNET_ETIMEOUT;
+    *n_components = (int64_t)h[0];
+    *largest = (int64_t)h[1];
+    return TCRNET_OK;
+}
+
+tcrnet_status neighbor_degree_distinct(const int32_t* uid, int64_t n, const int2* edges, int64_t E,
+                                       const int32_t* umult, int64_t U, double* knn, cudaStream_t s, int num_sms) {
+    if (n == 0) return TCRNET_OK;
+    DevBuf dsize, acc;
+    TCR_CHECK(dsize.alloc(sizeof(int64_t) * U, s));
+    TCR_CHECK(acc.alloc(sizeof(double) * U, s));
+    const unsigned gu = (unsigned)ceil_div(U, kThreads);
+    auto* ds = reinterpret_cast<unsigned long long*>(dsize.as<int64_t>());
+    k_dsize_self<<<gu, kThreads, 0, s>>>(umult, U, ds);
+    TCR_LAUNCH_CHECK();
+    if (E > 0) {
+        k_dsize_edges<<<blocks_for(E, kThreads, num_sms), kThreads, 0, s>>>(edges, E, umult, ds);
+        TCR_LAUNCH_CHECK();
+    }
+    k_dknn_self<<<gu, kThreads, 0, s>>>(umult, dsize.as<int64_t>(), U, acc.as<double>());
+    TCR_LAUNCH_CHECK();
+    if (E > 0) {
+        k_dknn_edges<<<blocks_for(E, kThreads, num_sms), kThreads, 0, s>>>(edges, E, umult, dsize.as<int64_t>(),
+                                                                           acc.as<double>());
+        TCR_LAUNCH_CHECK();
+    }
+    k_dknn_nodes<<<(unsigned)ceil_div(n, kThreads), kThreads, 0, s>>>(uid, n, dsize.as<int64_t>(), acc.as<double>(),
+                                                                     knn);
+    TCR_LAUNCH_CHECK();
     return TCRNET_OK;
 }
 

@@ -241,7 +241,8 @@ cudaStream_t free_stream(int dev) {
 
 void free_handle_memory(tcrnet_graph* h) {
     void* ptrs[] = {h->d_offsets, h->d_cols, h->d_degree, h->d_bcanon, h->d_bperm, h->d_canon_in, h->d_lens,
-                    h->ix.ucanon, h->ix.umult, h->ix.mem_off, h->ix.members, h->ix.recs, h->ix.poff};
+                    h->ix.ucanon, h->ix.umult, h->ix.mem_off, h->ix.members, h->ix.recs, h->ix.poff,
+                    h->ix.uid, h->ix.uedges};
     const cudaStream_t fs = free_stream(h->device);
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, fs);
@@ -873,7 +874,13 @@ tcrnet_status tcrnet_components(tcrnet_handle h, const uint8_t* keep, int32_t* l
             TCR_CHECK(dlab.alloc(sizeof(int32_t) * n, s));
             lab = dlab.as<int32_t>();
         }
-        TCR_CHECK(components(h->d_offsets, h->offsets64 != 0, h->d_cols, n, k, lab, &nc, &lc, s, sm_count(h->device)));
+        if (h->ix.uid) {  // a deletion build: the graph of distinct strings gives the same components
+            TCR_CHECK(components_distinct(h->ix.uid, n, h->ix.uedges, h->ix.E, h->ix.U, k, labels ? lab : nullptr, &nc,
+                                          &lc, s, sm_count(h->device)));
+        } else {
+            TCR_CHECK(components(h->d_offsets, h->offsets64 != 0, h->d_cols, n, k, lab, &nc, &lc, s,
+                                 sm_count(h->device)));
+        }
         if (mem == TCRNET_HOST && labels)
             TCR_CUDA(cudaMemcpyAsync(labels, lab, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
         TCR_CUDA(cudaStreamSynchronize(s));
@@ -897,7 +904,12 @@ tcrnet_status tcrnet_neighbor_degree(tcrnet_handle h, double* knn, int32_t mem) 
         TCR_CHECK(dk.alloc(sizeof(double) * n, s));
         out = dk.as<double>();
     }
-    TCR_CHECK(neighbor_degree(h->d_offsets, h->offsets64 != 0, h->d_cols, n, out, s, sm_count(h->device)));
+    if (h->ix.uid) {
+        TCR_CHECK(neighbor_degree_distinct(h->ix.uid, n, h->ix.uedges, h->ix.E, h->ix.umult, h->ix.U, out, s,
+                                           sm_count(h->device)));
+    } else {
+        TCR_CHECK(neighbor_degree(h->d_offsets, h->offsets64 != 0, h->d_cols, n, out, s, sm_count(h->device)));
+    }
     if (mem == TCRNET_HOST) TCR_CUDA(cudaMemcpyAsync(knn, out, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     TCR_CUDA(cudaStreamSynchronize(s));
     return TCRNET_OK;
@@ -935,14 +947,14 @@ namespace {
 // resident strings (bucketed copy + order, or input-order copy + lengths),
 // then the deletion index when present.
 constexpr char kMagic[8] = {'T', 'C', 'R', 'N', 'E', 'T', 'C', 'K'};
-constexpr uint32_t kFileVersion = 1;
+constexpr uint32_t kFileVersion = 2;
 
 struct FileHeader {
     char magic[8];
     uint32_t version;
     uint32_t header_bytes;
     int32_t threshold, offsets64, batched, has_bucketed, has_input_order, has_index;
-    int64_t n, nnz, lensum, ix_U, ix_P, ix_R;
+    int64_t n, nnz, lensum, ix_U, ix_P, ix_R, ix_E;
     int64_t bucket_off[kMaxLen + 2];
     tcrnet_stats stats;
 };
@@ -1001,6 +1013,7 @@ tcrnet_status tcrnet_save(tcrnet_handle h, const char* path) {
     if (hd.has_index) {
         hd.ix_U = h->ix.U;
         hd.ix_P = h->ix.P;
+        hd.ix_E = h->ix.uid ? h->ix.E : -1;
         TCR_CUDA(cudaMemcpyAsync(&hd.ix_R, h->ix.poff + h->ix.P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         TCR_CUDA(cudaStreamSynchronize(s));
     }
@@ -1027,6 +1040,10 @@ tcrnet_status tcrnet_save(tcrnet_handle h, const char* path) {
         ok = ok && write_array(f, h->ix.members, n * 4, s, st);
         ok = ok && write_array(f, h->ix.recs, (uint64_t)hd.ix_R * 8, s, st);
         ok = ok && write_array(f, h->ix.poff, ((uint64_t)h->ix.P + 1) * 8, s, st);
+        if (hd.ix_E >= 0) {
+            ok = ok && write_array(f, h->ix.uid, n * 4, s, st);
+            ok = ok && write_array(f, h->ix.uedges, (uint64_t)hd.ix_E * 8, s, st);
+        }
     }
     ok = (std::fclose(f) == 0) && ok;
     return ok ? TCRNET_OK : TCRNET_EINVAL;
@@ -1047,7 +1064,7 @@ tcrnet_status tcrnet_load(const char* path, const tcrnet_options* opt_in, tcrnet
                          hd.version == kFileVersion && hd.header_bytes == sizeof(FileHeader) && hd.n >= 0 &&
                          hd.n <= 0x7fffffffLL && hd.nnz >= 0 && hd.threshold >= 0 &&
                          (hd.offsets64 == 0 || hd.offsets64 == 1) && (hd.has_index == 0 || hd.has_index == 1) &&
-                         hd.ix_U >= 0 && hd.ix_U <= hd.n && hd.ix_P >= 0 && hd.ix_R >= 0 &&
+                         hd.ix_U >= 0 && hd.ix_U <= hd.n && hd.ix_P >= 0 && hd.ix_R >= 0 && hd.ix_E >= -1 &&
                          (hd.offsets64 || hd.nnz <= 0x7fffffffLL);
     if (!head_ok) {
         std::fclose(f);
@@ -1118,6 +1135,11 @@ tcrnet_status tcrnet_load(const char* path, const tcrnet_options* opt_in, tcrnet
         if (rd(n * 4) == TCRNET_OK) h->ix.members = static_cast<int32_t*>(p);
         if (rd((uint64_t)hd.ix_R * 8) == TCRNET_OK) h->ix.recs = static_cast<uint64_t*>(p);
         if (rd(((uint64_t)hd.ix_P + 1) * 8) == TCRNET_OK) h->ix.poff = static_cast<int64_t*>(p);
+        if (hd.ix_E >= 0) {
+            if (rd(n * 4) == TCRNET_OK) h->ix.uid = static_cast<int32_t*>(p);
+            if (rd((uint64_t)hd.ix_E * 8) == TCRNET_OK) h->ix.uedges = static_cast<int2*>(p);
+            h->ix.E = hd.ix_E;
+        }
         h->ix.U = hd.ix_U;
         h->ix.P = hd.ix_P;
         h->ix.n = hd.n;

@@ -756,6 +756,18 @@ __global__ void k_node_degree(const int32_t* __restrict__ uid, int64_t n, const 
     if (i < n) deg[i] = dsize[uid[i]] - 1;
 }
 
+// Edges of the segmented join buffer moved next to each other (kept by a
+// build handle: the network of distinct strings).
+struct SegBases {
+    int64_t base[kEdgeSegs + 1];
+};
+
+__global__ void k_compact_edges(const int2* __restrict__ edges, int64_t seg_cap, SegBases b, int2* __restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = blockIdx.y;
+    if (t < b.base[g + 1] - b.base[g]) out[b.base[g] + t] = edges[(int64_t)g * seg_cap + t];
+}
+
 __global__ void k_closed_self(const int32_t* __restrict__ uid, const int32_t* __restrict__ mpos, int64_t n,
                               const int64_t* __restrict__ uoff, int32_t* __restrict__ S) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -914,7 +926,8 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     TCR_CHECK(ulen.alloc(n, s));
     if (keep_index) TCR_CHECK(umult.alloc_owned(sizeof(int32_t) * n, s));
     else TCR_CHECK(umult.alloc(sizeof(int32_t) * n, s));
-    TCR_CHECK(uid.alloc(sizeof(int32_t) * n, s));
+    if (keep_index) TCR_CHECK(uid.alloc_owned(sizeof(int32_t) * n, s));
+    else TCR_CHECK(uid.alloc(sizeof(int32_t) * n, s));
     if (keep_index) TCR_CHECK(mem_off.alloc_owned(sizeof(int64_t) * (n + 1), s));
     else TCR_CHECK(mem_off.alloc(sizeof(int64_t) * (n + 1), s));
     TCR_CHECK(mcur.alloc(sizeof(int32_t) * n, s));
@@ -1091,6 +1104,22 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
                                                             Sbuf.as<int32_t>(), d_err + 1);
         TCR_LAUNCH_CHECK();
     }
+    // a build handle keeps the edges between distinct strings (analytics run on
+    // that graph of U nodes instead of the n-node network)
+    DevBuf uedges;
+    if (keep_index && join && E > 0) {
+        TCR_CHECK(uedges.alloc_owned(sizeof(int2) * E, s));
+        SegBases sb;
+        sb.base[0] = 0;
+        if (fill_segs == 1) {
+            for (int g = 1; g <= kEdgeSegs; ++g) sb.base[g] = E;
+        } else {
+            for (int g = 0; g < kEdgeSegs; ++g) sb.base[g + 1] = sb.base[g] + (int64_t)segs[g];
+        }
+        const dim3 cgrid(grid_for(seg_max), (unsigned)fill_segs);
+        k_compact_edges<<<cgrid, kThreads, 0, s>>>(edges.as<int2>(), fill_cap, sb, uedges.as<int2>());
+        TCR_LAUNCH_CHECK();
+    }
     if (side) TCR_CUDA(cudaStreamWaitEvent(s, side->ev[3], 0));  // own members and offsets written
     const int t4 = tm.mark();
     if (!keep_index) recs.reset();
@@ -1131,6 +1160,9 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         out.index.members = static_cast<int32_t*>(members.release());
         out.index.recs = static_cast<uint64_t*>(recs.release());
         out.index.poff = static_cast<int64_t*>(poff.release());
+        out.index.uid = static_cast<int32_t*>(uid.release());
+        out.index.uedges = static_cast<int2*>(uedges.release());
+        out.index.E = out.index.uedges ? E : 0;
         out.index.U = h_U;
         out.index.P = P;
         out.index.n = n;

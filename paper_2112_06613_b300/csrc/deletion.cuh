@@ -21,7 +21,9 @@ struct DeletionIndex {
     int32_t* members = nullptr;
     uint64_t* recs = nullptr;
     int64_t* poff = nullptr;
-    int64_t U = 0, P = 0, n = 0;
+    int32_t* uid = nullptr;    // node -> distinct string
+    int2* uedges = nullptr;    // edges between distinct strings, each once
+    int64_t U = 0, P = 0, n = 0, E = 0;
     bool valid() const { return recs != nullptr; }
 };
 

@@ -88,6 +88,14 @@ tcrnet_status components(const void* off, bool off64, const int32_t* cols, int64
 // knn[i] = mean degree of i's neighbours (0 for isolated nodes).
 tcrnet_status degree_histogram(const int32_t* deg, int64_t n, int64_t* hist, int64_t nbins, int64_t* max_degree,
                                cudaStream_t s, int num_sms);
+// The same analyses on the graph of distinct strings of a deletion build
+// (uid: node -> string, edges: each pair of adjacent strings once, umult:
+// members per string); identical results, work ~ U + E instead of nnz.
+tcrnet_status components_distinct(const int32_t* uid, int64_t n, const int2* edges, int64_t E, int64_t U,
+                                  const uint8_t* keep, int32_t* labels, int64_t* n_components, int64_t* largest,
+                                  cudaStream_t s, int num_sms);
+tcrnet_status neighbor_degree_distinct(const int32_t* uid, int64_t n, const int2* edges, int64_t E,
+                                       const int32_t* umult, int64_t U, double* knn, cudaStream_t s, int num_sms);
 tcrnet_status neighbor_degree(const void* off, bool off64, const int32_t* cols, int64_t n, double* knn,
                               cudaStream_t s, int num_sms);
 

@@ -26,6 +26,10 @@ def test_save_load_round_trip(tmp_path, method, n, threshold):
         ref = g.copy_csr()
         with g.query_flat(q.chars, q.offsets) as r:
             qref = r.copy_csr()
+        keep = (np.random.default_rng(5).random(n) >= 0.3).astype(np.uint8)
+        labels, nc, lc = g.components(keep)
+        comps = (nc, lc)
+        knn = g.neighbor_degree()
         g.save(path)
     with tn.tcrnet_load(path) as h:
         got = h.copy_csr()
@@ -35,6 +39,10 @@ def test_save_load_round_trip(tmp_path, method, n, threshold):
         with h.query_flat(q.chars, q.offsets) as r:
             qgot = r.copy_csr()
         assert_csr_equal(qgot[0], qgot[1], qref[0], qref[1], "queries on the restored handle")
+        keep = (np.random.default_rng(5).random(n) >= 0.3).astype(np.uint8)
+        assert h.components(keep)[1:] == comps
+        assert np.array_equal(h.components(keep)[0], labels)
+        assert np.array_equal(h.neighbor_degree(), knn)
         h.insert_flat(add.chars, add.offsets)
         full = from_strings(rep.strings() + add.strings())
         fo, fc, _ = h.copy_csr()
