@@ -203,21 +203,39 @@ __global__ void k_dcc_link(const int2* __restrict__ edges, int64_t E, int32_t* p
     }
 }
 
-// per kept node: its string's root collects the smallest kept node id and the size
+// every present string points at its root afterwards (one find per string)
+__global__ void k_dcc_flatten(int64_t U, int32_t* parent, int32_t* __restrict__ root) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= U) return;
+    root[u] = parent[u] < 0 ? -1 : find_root(parent, (int32_t)u);
+}
+
+// per kept node: its string's root collects the smallest kept node id and the
+// size. Lanes of a warp with the same root combine first (the largest
+// component's root would otherwise take one atomic per member).
 __global__ void k_dcc_members(const int32_t* __restrict__ uid, const uint8_t* __restrict__ keep, int64_t n,
-                              int32_t* parent, int32_t* __restrict__ cmin, int32_t* __restrict__ size) {
+                              const int32_t* __restrict__ root, int32_t* __restrict__ cmin,
+                              int32_t* __restrict__ size) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || (keep != nullptr && !keep[i])) return;
-    const int32_t r = find_root(parent, uid[i]);
-    atomicMin(&cmin[r], (int32_t)i);
-    atomicAdd(&size[r], 1);
+    const bool kept = i < n && (keep == nullptr || keep[i]);
+    const int32_t r = kept ? root[uid[i]] : -1;
+    const unsigned peers = __match_any_sync(kFull, r);
+    if (!kept) return;
+    const int lane = threadIdx.x & 31;
+    // node ids grow with the lane, so the lowest peer holds the smallest id
+    const int leader = __ffs(peers) - 1;
+    if (lane == leader) {
+        atomicMin(&cmin[r], (int32_t)i);
+        atomicAdd(&size[r], __popc(peers));
+    }
 }
 
 __global__ void k_dcc_label(const int32_t* __restrict__ uid, const uint8_t* __restrict__ keep, int64_t n,
-                            int32_t* parent, const int32_t* __restrict__ cmin, int32_t* __restrict__ labels) {
+                            const int32_t* __restrict__ root, const int32_t* __restrict__ cmin,
+                            int32_t* __restrict__ labels) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    labels[i] = (keep != nullptr && !keep[i]) ? -1 : cmin[find_root(parent, uid[i])];
+    labels[i] = (keep != nullptr && !keep[i]) ? -1 : cmin[root[uid[i]]];
 }
 
 __global__ void k_dcc_reduce(const int32_t* __restrict__ parent, const int32_t* __restrict__ size, int64_t U,
@@ -330,8 +348,9 @@ tcrnet_status components_distinct(const int32_t* uid, int64_t n, const int2* edg
     *n_components = 0;
     *largest = 0;
     if (n == 0) return TCRNET_OK;
-    DevBuf present, parent, cmin, size, red;
+    DevBuf present, parent, cmin, size, red, root;
     TCR_CHECK(present.alloc(sizeof(int32_t) * U, s));
+    TCR_CHECK(root.alloc(sizeof(int32_t) * U, s));
     TCR_CHECK(parent.alloc(sizeof(int32_t) * U, s));
     TCR_CHECK(cmin.alloc(sizeof(int32_t) * U, s));
     TCR_CHECK(size.alloc(sizeof(int32_t) * U, s));
@@ -349,11 +368,12 @@ tcrnet_status components_distinct(const int32_t* uid, int64_t n, const int2* edg
         k_dcc_link<<<blocks_for(E, kThreads, num_sms), kThreads, 0, s>>>(edges, E, parent.as<int32_t>(), err);
         TCR_LAUNCH_CHECK();
     }
-    k_dcc_members<<<gn, kThreads, 0, s>>>(uid, keep, n, parent.as<int32_t>(), cmin.as<int32_t>(),
-                                          size.as<int32_t>());
+    k_dcc_flatten<<<gu, kThreads, 0, s>>>(U, parent.as<int32_t>(), root.as<int32_t>());
+    TCR_LAUNCH_CHECK();
+    k_dcc_members<<<gn, kThreads, 0, s>>>(uid, keep, n, root.as<int32_t>(), cmin.as<int32_t>(), size.as<int32_t>());
     TCR_LAUNCH_CHECK();
     if (labels) {
-        k_dcc_label<<<gn, kThreads, 0, s>>>(uid, keep, n, parent.as<int32_t>(), cmin.as<int32_t>(), labels);
+        k_dcc_label<<<gn, kThreads, 0, s>>>(uid, keep, n, root.as<int32_t>(), cmin.as<int32_t>(), labels);
         TCR_LAUNCH_CHECK();
     }
     k_dcc_reduce<<<blocks_for(U, kThreads, num_sms), kThreads, 0, s>>>(parent.as<int32_t>(), size.as<int32_t>(), U,
