@@ -347,6 +347,7 @@ struct Inputs {
     const uint8_t* d_chars = nullptr;
     const int64_t* d_offs = nullptr;
     int64_t base = 0;
+    int64_t lo = INT64_MIN, hi = INT64_MAX;  // byte offsets the strings must stay in (host inputs)
 };
 
 // Device views of flat inputs; host inputs are uploaded on the stream.
@@ -361,14 +362,8 @@ tcrnet_status stage_inputs(const uint8_t* chars, const int64_t* offsets, int64_t
         return TCRNET_OK;
     }
     if (mem != TCRNET_HOST) return TCRNET_EINVAL;
-    // Every string must lie inside [offsets[0], offsets[n]) before anything is
-    // uploaded: offsets must not decrease.
-    for (int64_t i = 0; i < n; ++i) {
-        if (offsets[i + 1] < offsets[i]) {
-            t_last_bad = i;
-            return TCRNET_EINVAL;
-        }
-    }
+    // Bytes [offsets[0], offsets[n]) are uploaded; the encoder checks that every
+    // string lies inside them (and that offsets do not decrease), per string.
     const int64_t base = offsets[0];
     const int64_t total = offsets[n] - base;
     if (base < 0 || total < 0) return TCRNET_EINVAL;
@@ -380,6 +375,8 @@ tcrnet_status stage_inputs(const uint8_t* chars, const int64_t* offsets, int64_t
     in.d_chars = in.chars.as<uint8_t>();
     in.d_offs = in.offs.as<int64_t>();
     in.base = base;
+    in.lo = base;
+    in.hi = base + total;
     return TCRNET_OK;
 }
 
@@ -517,7 +514,7 @@ tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n
     if (n > 0) {
         // chars are addressed as d_chars + (offsets[i] - base)
         st = pack_strings(in.d_chars - in.base, in.d_offs, n, pk, &bad, s, opt.method == TCRNET_METHOD_TILE,
-                          opt.method != TCRNET_METHOD_TILE && !rep_off);
+                          opt.method != TCRNET_METHOD_TILE && !rep_off, in.lo, in.hi);
         if (st != TCRNET_OK) {
             t_last_bad = bad;
             return fail(st);
@@ -658,7 +655,8 @@ tcrnet_status tcrnet_query_ex(tcrnet_handle h, const uint8_t* chars, const int64
     } else {
         Packed pk;
         int64_t bad = -1;
-        st = pack_strings(in.d_chars - in.base, in.d_offs, m, pk, &bad, s, method != TCRNET_METHOD_DELETION);
+        st = pack_strings(in.d_chars - in.base, in.d_offs, m, pk, &bad, s, method != TCRNET_METHOD_DELETION, false,
+                          in.lo, in.hi);
         if (st != TCRNET_OK) {
             t_last_bad = bad;
             return fail(st);
@@ -740,7 +738,8 @@ tcrnet_status extend_impl(tcrnet_handle h, const uint8_t* chars, const int64_t* 
     TCR_CHECK(stage_inputs(chars, offsets, m, mem, in, s));
     Packed pn;
     int64_t bad = -1;
-    tcrnet_status st = pack_strings(in.d_chars - in.base, in.d_offs, m, pn, &bad, s, /*bucket=*/false);
+    tcrnet_status st = pack_strings(in.d_chars - in.base, in.d_offs, m, pn, &bad, s, /*bucket=*/false, false, in.lo,
+                                    in.hi);
     if (st != TCRNET_OK) {
         t_last_bad = bad;
         return st;

@@ -1050,8 +1050,15 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     // int32 row offsets for the handle
     DevBuf off32;
     if (!force_off64 && nnz <= 0x7fffffffLL) TCR_CHECK(off32.alloc_owned(sizeof(int32_t) * (n + 1), s));
-    // each list's own members (after its member list exists) and the narrowed
-    // offsets go to the side stream, next to the neighbour appends on this one
+    // a build handle keeps the edges between distinct strings (analytics run on
+    // that graph of U nodes instead of the n-node network); allocated before
+    // the fork so the side stream may write it
+    DevBuf uedges;
+    const bool keep_edges = keep_index && join && E > 0;
+    if (keep_edges) TCR_CHECK(uedges.alloc_owned(sizeof(int2) * E, s));
+    // each list's own members (after its member list exists), the narrowed
+    // offsets and the kept edges go to the side stream, next to the neighbour
+    // appends on this one
     cudaStream_t fs = s;
     if (side) {
         TCR_CUDA(cudaEventRecord(side->ev[2], s));
@@ -1063,6 +1070,14 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
                                                     Sbuf.as<int32_t>());
     TCR_LAUNCH_CHECK();
     if (off32.as<void>()) TCR_CHECK(narrow_offsets(off64.as<int64_t>(), off32.as<int32_t>(), n + 1, fs));
+    if (keep_edges && !overflow) {  // the one-pass buffer holds every edge: segments to one array
+        SegBases sb;
+        sb.base[0] = 0;
+        for (int g = 0; g < kEdgeSegs; ++g) sb.base[g + 1] = sb.base[g] + (int64_t)segs[g];
+        const dim3 cgrid(grid_for(std::max<int64_t>(seg_max, 1)), (unsigned)kEdgeSegs);
+        k_compact_edges<<<cgrid, kThreads, 0, fs>>>(edges.as<int2>(), seg_cap, sb, uedges.as<int2>());
+        TCR_LAUNCH_CHECK();
+    }
     if (side) TCR_CUDA(cudaEventRecord(side->ev[3], fs));
     // ---- 3b. edges that did not fit: second join pass at scanned positions;
     // then append neighbour member lists
@@ -1094,6 +1109,8 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         fill_cap = E;
         fill_counts = d_ecur + kEdgeSegs;
         seg_max = E;
+        if (keep_edges)  // the second pass wrote them contiguously
+            TCR_CUDA(cudaMemcpyAsync(uedges.as<void>(), edges.as<void>(), sizeof(int2) * E, cudaMemcpyDeviceToDevice, s));
     }
     if (join && E > 0) {
         if (!keep_index) recs.reset();
@@ -1102,22 +1119,6 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
                                                             mem_off.as<int64_t>(), members.as<int32_t>(),
                                                             uoff.as<int64_t>(), ucur.as<int32_t>(),
                                                             Sbuf.as<int32_t>(), d_err + 1);
-        TCR_LAUNCH_CHECK();
-    }
-    // a build handle keeps the edges between distinct strings (analytics run on
-    // that graph of U nodes instead of the n-node network)
-    DevBuf uedges;
-    if (keep_index && join && E > 0) {
-        TCR_CHECK(uedges.alloc_owned(sizeof(int2) * E, s));
-        SegBases sb;
-        sb.base[0] = 0;
-        if (fill_segs == 1) {
-            for (int g = 1; g <= kEdgeSegs; ++g) sb.base[g] = E;
-        } else {
-            for (int g = 0; g < kEdgeSegs; ++g) sb.base[g + 1] = sb.base[g] + (int64_t)segs[g];
-        }
-        const dim3 cgrid(grid_for(seg_max), (unsigned)fill_segs);
-        k_compact_edges<<<cgrid, kThreads, 0, s>>>(edges.as<int2>(), fill_cap, sb, uedges.as<int2>());
         TCR_LAUNCH_CHECK();
     }
     if (side) TCR_CUDA(cudaStreamWaitEvent(s, side->ev[3], 0));  // own members and offsets written

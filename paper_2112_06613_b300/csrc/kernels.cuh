@@ -29,9 +29,12 @@ struct Packed {
 // status and sets *bad_index to the lowest offending input index. With
 // bucket = false only the input-order copy is made (no bucketed copy,
 // bucket_off left zero); keep_input_order allocates that copy for a handle to
-// keep (outside the call's workspace).
+// keep (outside the call's workspace). Strings must lie in byte offsets
+// [lo, hi) of d_chars (TCRNET_EINVAL with the index otherwise; offsets that
+// decrease give an empty or negative length and fail the same way).
 tcrnet_status pack_strings(const uint8_t* d_chars, const int64_t* d_offsets, int64_t n, Packed& out,
-                           int64_t* bad_index, cudaStream_t s, bool bucket = true, bool keep_input_order = false);
+                           int64_t* bad_index, cudaStream_t s, bool bucket = true, bool keep_input_order = false,
+                           int64_t lo = INT64_MIN, int64_t hi = INT64_MAX);
 
 // Write repertoire numbers into the spare bits of input-order canon
 // (repertoire r = strings rep_off[r] .. rep_off[r+1]).

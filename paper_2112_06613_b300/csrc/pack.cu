@@ -25,7 +25,7 @@ constexpr int kPackWarps = kPackThreads / 32;
 constexpr int kBins = kMaxLen + 1;
 
 __global__ void __launch_bounds__(kPackThreads)
-k_encode(const uint8_t* __restrict__ chars, const int64_t* __restrict__ offs, int64_t n,
+k_encode(const uint8_t* __restrict__ chars, const int64_t* __restrict__ offs, int64_t n, int64_t lo, int64_t hi,
          Canon* __restrict__ canon, uint8_t* __restrict__ lens, int32_t* __restrict__ blockcnt,
          int nblocks, unsigned long long* __restrict__ err, unsigned long long* __restrict__ lensum) {
     __shared__ uint8_t lut[256];
@@ -40,7 +40,10 @@ k_encode(const uint8_t* __restrict__ chars, const int64_t* __restrict__ offs, in
         unsigned code_err = 0;
         Canon c;
         c.w[0] = c.w[1] = c.w[2] = c.w[3] = 0;
-        if (len <= 0) {
+        // empty, decreasing offsets, or outside the uploaded bytes (host inputs:
+        // lo = first byte, hi = one past the last; device inputs: no bounds)
+        const bool outside = lo != INT64_MIN && (s < lo || s > hi || len > hi - s);
+        if (len <= 0 || outside) {
             code_err = TCRNET_EINVAL;
         } else if (len > kMaxLen) {
             code_err = TCRNET_ETOOLONG;
@@ -198,7 +201,8 @@ tcrnet_status unbucket_strings(const Canon* canon, const int32_t* perm, const in
 }
 
 tcrnet_status pack_strings(const uint8_t* d_chars, const int64_t* d_offsets, int64_t n, Packed& out,
-                           int64_t* bad_index, cudaStream_t s, bool bucket, bool keep_input_order) {
+                           int64_t* bad_index, cudaStream_t s, bool bucket, bool keep_input_order, int64_t lo,
+                           int64_t hi) {
     out.n = n;
     out.lensum = 0;
     *bad_index = -1;
@@ -227,7 +231,7 @@ tcrnet_status pack_strings(const uint8_t* d_chars, const int64_t* d_offsets, int
     unsigned long long* d_flags = flags.as<unsigned long long>();
     TCR_CUDA(cudaMemsetAsync(d_flags, 0xff, sizeof(unsigned long long), s));
     TCR_CUDA(cudaMemsetAsync(d_flags + 1, 0, sizeof(unsigned long long), s));
-    k_encode<<<nblocks, kPackThreads, 0, s>>>(d_chars, d_offsets, n, out.canon_in.as<Canon>(),
+    k_encode<<<nblocks, kPackThreads, 0, s>>>(d_chars, d_offsets, n, lo, hi, out.canon_in.as<Canon>(),
                                               out.lens.as<uint8_t>(), bucket ? blockcnt.as<int32_t>() : nullptr,
                                               nblocks, d_flags, d_flags + 1);
     TCR_LAUNCH_CHECK();

@@ -450,3 +450,21 @@ def test_device_copy_leaves_guard_bytes_untouched():
         ho, hc, hd = g.copy_csr()
         assert np.array_equal(off[guard:guard + n + 1].cpu().numpy(), ho)
         assert np.array_equal(cols[guard:guard + nnz].cpu().numpy(), hc)
+
+
+@pytest.mark.parametrize("method", ["deletion", "tile"])
+def test_flat_offsets_checked_on_the_device(method):
+    chars = np.frombuffer(b"XXCASSFCASSGCASF", dtype=np.uint8)
+    cases = [
+        (np.array([2, 7, 5, 16], np.int64), tn.EINVAL, 1),   # decreasing: negative length
+        (np.array([2, 18, 16, 16], np.int64), tn.EINVAL, 0),  # string 0 reaches past offsets[n]
+        (np.array([2, 7, 7, 16], np.int64), tn.EINVAL, 1),   # empty string
+    ]
+    for off, status, idx in cases:
+        with pytest.raises(tn.TcrnetError) as e:
+            tn.tcrnet_build_flat(chars, off, 1, method=method)
+        assert e.value.status == status and e.value.index == idx, (off, e.value.status, e.value.index)
+    # a base offset above zero: CASSF, CASSG, CASF
+    with tn.tcrnet_build_flat(chars, np.array([2, 7, 12, 16], np.int64), 1, method=method) as g:
+        off, cols, _ = g.copy_csr()
+    assert list(np.asarray(off)) == [0, 2, 3, 4] and list(cols) == [1, 2, 0, 0]
