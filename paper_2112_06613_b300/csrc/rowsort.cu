@@ -8,15 +8,17 @@
 //   len <= 8:           one lane, values in registers, Batcher's odd-even
 //                       merge network for 8 (19 comparators); a warp takes 32
 //                       consecutive rows at once.
-//   9 .. 1024:          one warp, values in registers (K = 1..32 per lane,
+//   9 .. 512:           one warp, values in registers (K = 1..16 per lane,
 //                       network position lane * K + r), bitonic network:
 //                       stages with partner distance < K exchange registers,
 //                       longer ones exchange lanes by shuffle. K = 1 stops at
 //                       the next power of two above the row length. Rows of
-//                       65..256 and 257..1024 are listed and sorted by their own
+//                       65..256 and 257..512 are listed and sorted by their own
 //                       kernels, so wide register arrays do not lower the
 //                       occupancy of the kernel that sorts the many short rows.
-//   1025 .. 16384:      one 1024-thread block, shared-memory bitonic network.
+//   513 .. 16384:       one 1024-thread block, shared-memory bitonic network
+//                       (such rows are few; one warp per row was the slowest
+//                       part of the sort).
 //   > 16384:            one block; 16384-value chunks sorted in shared memory,
 //                       then pairwise merges through a scratch buffer where each
 //                       value finds its output slot by binary search in the
@@ -32,7 +34,6 @@ namespace {
 constexpr int kLaneMax = 8;
 constexpr int kShortMax = 64;
 constexpr int kWideMax = 256;
-constexpr int kWarpCap = 1024;
 constexpr int kBlockThreads = 1024;
 constexpr int kBlockCap = 16384;
 constexpr int kSortWarps = 8;
@@ -144,8 +145,8 @@ __device__ __forceinline__ void warp_sort_regs(int32_t* __restrict__ row, int le
 // most 8 values, then the warp sorts the rows of 9..64 values one by one.
 __global__ void __launch_bounds__(kSortWarps * 32)
 k_sort_warp(const int64_t* __restrict__ off, int32_t* __restrict__ cols, int64_t n, int32_t* __restrict__ wide,
-            int* __restrict__ nwide, int32_t* __restrict__ mid, int* __restrict__ nmid, int32_t* __restrict__ mid32,
-            int* __restrict__ nmid32, int32_t* __restrict__ big, int* __restrict__ nbig) {
+            int* __restrict__ nwide, int32_t* __restrict__ mid, int* __restrict__ nmid, int32_t* __restrict__ big,
+            int* __restrict__ nbig) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t gw = (int64_t)blockIdx.x * kSortWarps + warp;
     const int64_t stride = (int64_t)gridDim.x * kSortWarps;
@@ -159,8 +160,7 @@ k_sort_warp(const int64_t* __restrict__ off, int32_t* __restrict__ cols, int64_t
             len = len64 > (int64_t)kInf ? kInf : (int)len64;
         }
         if (len >= 2 && len <= kLaneMax) lane_sort8(cols + base, len);
-        else if (len > kWarpCap) big[atomicAdd(nbig, 1)] = (int32_t)r;
-        else if (len > 2 * kWideMax) mid32[atomicAdd(nmid32, 1)] = (int32_t)r;
+        else if (len > 2 * kWideMax) big[atomicAdd(nbig, 1)] = (int32_t)r;  // few, long: a block each
         else if (len > kWideMax) mid[atomicAdd(nmid, 1)] = (int32_t)r;
         else if (len > kShortMax) wide[atomicAdd(nwide, 1)] = (int32_t)r;
         uint32_t todo = __ballot_sync(kFull, len > kLaneMax && len <= kShortMax);
@@ -267,22 +267,19 @@ __global__ void k_merge_runs(const int32_t* __restrict__ src, int32_t* __restric
 
 tcrnet_status sort_rows(const int64_t* off, int32_t* cols, int64_t n, cudaStream_t s, int num_sms, int64_t max_len) {
     if (n <= 0) return TCRNET_OK;
-    // lists: [0, n) rows of 257..512, [n, 2n) rows above 1024, [2n, 3n) rows
-    // above kBlockCap, [3n, 4n) rows of 65..256, [4n, 5n) rows of 513..1024;
-    // counts in the same order
+    // lists: [0, n) rows of 257..512, [n, 2n) rows above 512, [2n, 3n) rows
+    // above kBlockCap, [3n, 4n) rows of 65..256; counts in the same order
     DevBuf lists, counts;
-    TCR_CHECK(lists.alloc(sizeof(int32_t) * 5 * n, s));
-    TCR_CHECK(counts.alloc(sizeof(int) * 5, s));
-    TCR_CUDA(cudaMemsetAsync(counts.as<void>(), 0, sizeof(int) * 5, s));
+    TCR_CHECK(lists.alloc(sizeof(int32_t) * 4 * n, s));
+    TCR_CHECK(counts.alloc(sizeof(int) * 4, s));
+    TCR_CUDA(cudaMemsetAsync(counts.as<void>(), 0, sizeof(int) * 4, s));
     int32_t* mid = lists.as<int32_t>();
     int32_t* big = mid + n;
     int32_t* huge_list = big + n;
     int32_t* wide = huge_list + n;
-    int32_t* mid32 = wide + n;
     int* cnt = counts.as<int>();
     const int64_t blocks = std::min<int64_t>(ceil_div(n, 32 * kSortWarps), (int64_t)num_sms * 16);
-    k_sort_warp<<<(unsigned)blocks, kSortWarps * 32, 0, s>>>(off, cols, n, wide, cnt + 3, mid, cnt, mid32, cnt + 4,
-                                                              big, cnt + 1);
+    k_sort_warp<<<(unsigned)blocks, kSortWarps * 32, 0, s>>>(off, cols, n, wide, cnt + 3, mid, cnt, big, cnt + 1);
     TCR_LAUNCH_CHECK();
     const bool known = max_len >= 0;  // a known bound skips the kernels of longer classes
     if (!known || max_len > kShortMax) {
@@ -293,11 +290,7 @@ tcrnet_status sort_rows(const int64_t* off, int32_t* cols, int64_t n, cudaStream
         k_sort_warp_mid<16><<<num_sms * 4, kSortWarps * 32, 0, s>>>(off, cols, mid, cnt);
         TCR_LAUNCH_CHECK();
     }
-    if (!known || max_len > 2 * kWideMax) {
-        k_sort_warp_mid<32><<<num_sms * 2, kSortWarps * 32, 0, s>>>(off, cols, mid32, cnt + 4);
-        TCR_LAUNCH_CHECK();
-    }
-    if (known && max_len <= kWarpCap) return TCRNET_OK;
+    if (known && max_len <= 2 * kWideMax) return TCRNET_OK;
     const size_t smem = sizeof(int32_t) * kBlockCap;
     TCR_CUDA(cudaFuncSetAttribute(k_sort_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     TCR_CUDA(cudaFuncSetAttribute(k_sort_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
