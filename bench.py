@@ -58,9 +58,9 @@ INT_LANES_PER_SM = 128
 # from one ncu capture of the current kernels (profiles/k_join_small_n800000.md,
 # profiles/k_records_expand_n800000.md); None where no capture covers the phase.
 PHASE_TRAFFIC_N800000 = {
-    "join_weigh": 100.30e6 + 5.87e6 + 21.84e6 + 0.03e6,
-    "records": 21.91e6 + 86.57e6 + 105.64e6,
-    "expand": 84.27e6 + 199.98e6,
+    "join_weigh": 100.13e6 + 5.81e6 + 21.85e6 + 0.03e6,
+    "records": 21.91e6 + 86.58e6 + 105.56e6,
+    "expand": 83.94e6 + 200.01e6,
 }
 
 LEGS = ("tile", "query", "e2e", "analytics", "lmax2", "batched", "serving", "cpu")
