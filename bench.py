@@ -530,13 +530,21 @@ def run_ours(args):
                 "traffic_source": "ncu DRAM bytes of the phase's kernels, one capture (profiles/)" if traffic else None}
     if is_tile:
         roofline = roofline_tile
+    # edge write: the CSR columns (4 B per directed entry) the expansion writes, over
+    # the expansion phase, against the HBM peak
+    edge_write = None
+    if not is_tile and phase_ms.get("expand"):
+        ew = 4 * nnz / (phase_ms["expand"] / 1e3) / 1e9
+        edge_write = {"bound": "hbm", "kernel_phase": "expand", "achieved": ew, "peak": hbm_peak, "unit": "GB/s",
+                      "frac": ew / hbm_peak, "bytes_per_launch": 4 * nnz, "ms_per_launch": phase_ms["expand"],
+                      "traffic": PHASE_TRAFFIC_N800000.get("expand") if n == 800_000 else None}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": workload_config(args, "deletion" if st0["method"] == 2 else "tile"),
-        "edges_per_s": edges_per_s, "edges_per_build": edges, "nnz": nnz,
+        "edges_per_s": edges_per_s, "edges_per_build": edges, "nnz": nnz, "edge_write": edge_write,
         "wall_s_timed_region": wall, "phases_ms": phase_ms, "roofline": roofline,
         "gpu_launches": launches, "clocks": clocks,
     }
