@@ -91,7 +91,12 @@ typedef struct tcrnet_options {
                                  allocation of this call fails and the call returns
                                  TCRNET_ENOMEM after releasing what it holds;
                                  0 = off */
-    int32_t reserved[5];      /* must be zero */
+    int32_t insert_rebuild;   /* inserts (tcrnet_insert_ex, tcrnet_extend): 1 = rebuild
+                                 the grown repertoire from scratch; 0 (default) =
+                                 merge the new strings into the handle's network and
+                                 index where the handle allows it (deletion builds
+                                 with l_max = 1), which gives the same network */
+    int32_t reserved[4];      /* must be zero */
 } tcrnet_options;
 
 /* Defaults: AUTO method, current device, legacy default stream, no profiling. */
@@ -119,7 +124,11 @@ typedef struct tcrnet_stats {
     double ms_write;          /* tile write pass / deletion fill */
     double ms_sort;           /* per-row ordering */
     double ms_total;          /* whole call on the stream */
-    double ms_phase[8];       /* method-specific sub-phases (see DESIGN notes) */
+    double ms_phase[8];       /* deletion path sub-phases: dedup, records, join (weighted
+                                 degrees), list sizes + fill, unused, list sort, expand,
+                                 total */
+    int64_t merged_inserts;   /* inserts merged into this network since its last
+                                 full build (0 after a build or a rebuild) */
 } tcrnet_stats;
 
 /* Opaque handle: a CSR (n rows) owned by the library in device memory, plus,
@@ -163,7 +172,7 @@ tcrnet_status tcrnet_build_batched(const uint8_t *chars, const int64_t *offsets,
 /*
  * Checkpoint / resume of a serving state. tcrnet_save writes a build handle
  * (network, resident strings and, for deletion builds, the query index) to the
- * file `path` (host byte order, format version 1); tcrnet_load makes a new
+ * file `path` (host byte order, format version 3); tcrnet_load makes a new
  * handle from such a file on opt->device / opt->stream (opt may be NULL) that
  * answers queries and inserts like the saved one. Errors: TCRNET_EINVAL (NULL
  * argument, unreadable or unwritable file, bad magic, version or sizes; the

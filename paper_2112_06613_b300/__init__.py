@@ -43,7 +43,8 @@ class tcrnet_options(ctypes.Structure):
         ("partition_cap", ctypes.c_int32),
         ("partition_target", ctypes.c_int32),
         ("fail_alloc_at", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 5),
+        ("insert_rebuild", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
     ]
 
 
@@ -69,6 +70,7 @@ class tcrnet_stats(ctypes.Structure):
         ("ms_sort", ctypes.c_double),
         ("ms_total", ctypes.c_double),
         ("ms_phase", ctypes.c_double * 8),
+        ("merged_inserts", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -196,7 +198,7 @@ def _stream_ptr(stream):
 
 
 def make_options(method="auto", device=None, stream=None, profile=False, force_offsets64=False,
-                 partition_cap=0, partition_target=0, fail_alloc_at=0):
+                 partition_cap=0, partition_target=0, fail_alloc_at=0, insert_rebuild=False):
     lib = load_library()
     o = tcrnet_options()
     lib.tcrnet_options_init(ctypes.byref(o))
@@ -209,6 +211,7 @@ def make_options(method="auto", device=None, stream=None, profile=False, force_o
     o.partition_cap = int(partition_cap)
     o.partition_target = int(partition_target)
     o.fail_alloc_at = int(fail_alloc_at)
+    o.insert_rebuild = 1 if insert_rebuild else 0
     return o
 
 
@@ -343,11 +346,13 @@ class Graph:
         arr = (ctypes.c_char_p * max(len(enc), 1))(*enc)
         _check(lib.tcrnet_insert(self._h, arr, len(enc)), "tcrnet_insert")
 
-    def insert_flat(self, chars, offsets, stream=None, profile=False):
-        """Append strings in flat layout (numpy or torch, host or device) as new nodes."""
+    def insert_flat(self, chars, offsets, stream=None, profile=False, rebuild=False, fail_alloc_at=0):
+        """Append strings in flat layout (numpy or torch, host or device) as new nodes.
+        A deletion build merges them into its network and index; rebuild=True
+        rebuilds the grown repertoire instead (same network)."""
         lib = load_library()
         cp, op, m, mem, keep = _flat_args(chars, offsets)
-        opt = make_options(stream=stream, profile=profile)
+        opt = make_options(stream=stream, profile=profile, insert_rebuild=rebuild, fail_alloc_at=fail_alloc_at)
         st = lib.tcrnet_insert_ex(self._h, cp, op, m, mem, ctypes.byref(opt))
         del keep
         _check(st, "tcrnet_insert_ex")
@@ -356,12 +361,13 @@ class Graph:
         """Checkpoint this handle (network, resident strings, query index) to a file."""
         _check(load_library().tcrnet_save(self._h, os.fsencode(path)), "tcrnet_save")
 
-    def extend_flat(self, chars, offsets, stream=None, profile=False) -> "Graph":
+    def extend_flat(self, chars, offsets, stream=None, profile=False, rebuild=False, fail_alloc_at=0) -> "Graph":
         """Copy-on-write insert: a new Graph of this one's strings plus the new ones;
-        this Graph is unchanged and may keep serving queries meanwhile."""
+        this Graph is unchanged and may keep serving queries meanwhile. rebuild as
+        for insert_flat."""
         lib = load_library()
         cp, op, m, mem, keep = _flat_args(chars, offsets)
-        opt = make_options(stream=stream, profile=profile)
+        opt = make_options(stream=stream, profile=profile, insert_rebuild=rebuild, fail_alloc_at=fail_alloc_at)
         h = ctypes.c_void_p()
         st = lib.tcrnet_extend(self._h, cp, op, m, mem, ctypes.byref(opt), ctypes.byref(h))
         del keep

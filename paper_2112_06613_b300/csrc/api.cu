@@ -708,8 +708,13 @@ tcrnet_status tcrnet_query(tcrnet_handle h, const char* const* queries, int64_t 
 namespace tcr {
 namespace {
 
+// Largest mean records per partition that a merged insert may leave behind
+// (builds aim at 24 or 32).
+constexpr int64_t kMergeMaxPartitionFill = 48;
+
 // The network of h's strings followed by m new ones, as a new graph; h is only
-// read (its resident strings), so queries on h may run meanwhile on other streams.
+// read (its resident strings, network and index), so queries on h may run
+// meanwhile on other streams.
 tcrnet_status extend_impl(tcrnet_handle h, const uint8_t* chars, const int64_t* offsets, int64_t m, int32_t mem,
                           const tcrnet_options* opt_in, tcrnet_graph** out) {
     *out = nullptr;
@@ -724,6 +729,7 @@ tcrnet_status extend_impl(tcrnet_handle h, const uint8_t* chars, const int64_t* 
         opt.stream = opt_in->stream;
         opt.profile = opt_in->profile;
         opt.fail_alloc_at = opt_in->fail_alloc_at;
+        opt.insert_rebuild = opt_in->insert_rebuild;
     }
     AllocFaultScope fault_scope(opt.fail_alloc_at);
     DeviceGuard dg;
@@ -774,6 +780,14 @@ tcrnet_status extend_impl(tcrnet_handle h, const uint8_t* chars, const int64_t* 
                                  cudaMemcpyDeviceToDevice, s));
     }
     if (tile) TCR_CHECK(bucket_strings(pk, s));
+    // A deletion build's network and index can take the new strings without a
+    // rebuild, while its partitions stay small (they were sized for the
+    // original record count; a rebuild re-sizes them) and the insert is small
+    // next to the repertoire.
+    const DeletionIndex& ix = h->ix;
+    const bool merge = !tile && opt.insert_rebuild == 0 && m > 0 && m <= n_old && ix.valid() && ix.uid &&
+                       ix.n == n_old && h->threshold >= 1 && N <= kDeletionMaxN &&
+                       ix.R + m + pn.lensum <= kMergeMaxPartitionFill * ix.P;
     tcrnet_graph* g = new (std::nothrow) tcrnet_graph();
     if (!g) return TCRNET_ENOMEM;
     std::memset(&g->stats, 0, sizeof(g->stats));
@@ -782,7 +796,34 @@ tcrnet_status extend_impl(tcrnet_handle h, const uint8_t* chars, const int64_t* 
     g->threshold = h->threshold;
     g->stats.threshold = h->threshold;
     g->stats.n = N;
-    st = build_from_packed(g, pk, N, h->threshold, opt, ph, s, sms);
+    if (merge) {
+        CsrView gv;
+        gv.offsets = h->d_offsets;
+        gv.off64 = h->offsets64 != 0;
+        gv.cols = h->d_cols;
+        gv.degree = h->d_degree;
+        gv.n = n_old;
+        gv.nnz = h->nnz;
+        InsertResult ir;
+        st = deletion_insert(ix, gv, pn, h->threshold, ir, s, sms);
+        if (st == TCRNET_OK) {
+            g->ix = ir.index;  // owned by g from here on (freed with it on a later error)
+            ir.index = DeletionIndex();
+            g->stats.method = TCRNET_METHOD_DELETION;
+            g->stats.n_unique = g->ix.U;
+            g->stats.n_records = g->ix.R;
+            g->stats.unique_edges = g->ix.E;
+            g->stats.merged_inserts = h->stats.merged_inserts + 1;
+            st = export_csr(g, ir.off64, ir.cols, ir.degree, N, ir.nnz, opt.force_offsets64 != 0, s);
+        }
+        if (st == TCRNET_OK) {
+            g->lensum = pk.lensum;
+            g->d_canon_in = static_cast<Canon*>(pk.canon_in.release());
+            g->d_lens = static_cast<uint8_t*>(pk.lens.release());
+        }
+    } else {
+        st = build_from_packed(g, pk, N, h->threshold, opt, ph, s, sms);
+    }
     if (st == TCRNET_OK && cudaStreamSynchronize(s) != cudaSuccess) st = TCRNET_EDEVICE;
     if (st != TCRNET_OK) {
         cudaStreamSynchronize(s);
@@ -946,7 +987,7 @@ namespace {
 // resident strings (bucketed copy + order, or input-order copy + lengths),
 // then the deletion index when present.
 constexpr char kMagic[8] = {'T', 'C', 'R', 'N', 'E', 'T', 'C', 'K'};
-constexpr uint32_t kFileVersion = 2;
+constexpr uint32_t kFileVersion = 3;
 
 struct FileHeader {
     char magic[8];
@@ -1141,6 +1182,7 @@ tcrnet_status tcrnet_load(const char* path, const tcrnet_options* opt_in, tcrnet
         }
         h->ix.U = hd.ix_U;
         h->ix.P = hd.ix_P;
+        h->ix.R = hd.ix_R;
         h->ix.n = hd.n;
     }
     std::fclose(f);

@@ -250,7 +250,7 @@ constexpr int kRecBatch = 4;
 template <bool SCATTER>
 __global__ void k_records(const Canon* __restrict__ ucanon, const uint8_t* __restrict__ ulen,
                           const int64_t* __restrict__ U_ptr, int64_t n, uint32_t P, int32_t* __restrict__ pcnt,
-                          const int64_t* __restrict__ poff, uint64_t* __restrict__ recs) {
+                          const int64_t* __restrict__ poff, uint64_t* __restrict__ recs, uint32_t u0 = 0) {
     const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= n || u >= *U_ptr) return;
     const Canon c = load_canon(ucanon + u);
@@ -276,7 +276,7 @@ __global__ void k_records(const Canon* __restrict__ ucanon, const uint8_t* __res
             pid[t] = part_of(h, P);
             const uint64_t tag = full ? ((uint64_t)kTagF << 26)
                                       : (((uint64_t)p << 26) | (run_start(c, p < L ? p : 0) ? (1ull << 25) : 0ull));
-            rec[t] = (h << 32) | tag | (uint64_t)u;
+            rec[t] = (h << 32) | tag | (uint64_t)(u0 + (uint32_t)u);  // ids of a slice start at u0
         }
 #pragma unroll
         for (int t = 0; t < kRecBatch; ++t) {
@@ -1166,6 +1166,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         out.index.E = out.index.uedges ? E : 0;
         out.index.U = h_U;
         out.index.P = P;
+        out.index.R = h_R;
         out.index.n = n;
     }
     out.ms_phase[0] = tm.ms(t0, t1);  // dedup
@@ -1288,6 +1289,502 @@ tcrnet_status deletion_query(const DeletionIndex& ix, const Packed& q, int T, De
     }
     TCR_CHECK(degree_from_offsets(off64.as<int64_t>(), count.as<int32_t>(), m, s));
     *nnz_out = nnz;
+    return TCRNET_OK;
+}
+
+// ---- merging new strings into a resident network ----------------------------
+//
+// The network of a repertoire grown by m strings differs from the old one by
+// the rows of the new nodes and by new entries appended to old rows (new ids
+// are larger than every old id, so an old row stays sorted when they are
+// appended in ascending order). Every edge that involves a new string joins it
+// either to an old string (the query of the new strings against the resident
+// index) or to another new string (the network of the new strings alone).
+// The index is grown the same way: a new string equal to a resident distinct
+// string joins its member list; the others become fresh distinct strings whose
+// records are added to the same hash partitions.
+
+namespace {
+
+// Distinct id of each new string: the resident distinct string it equals
+// (found through the full-string record of its partition), else a slot of a
+// table of the new strings; the string that claims a slot numbers a fresh
+// distinct string (u0 + running count) and is its representative.
+__global__ void k_ins_dedup(IndexView ix, const Canon* __restrict__ qcanon, const uint8_t* __restrict__ qlen,
+                            int64_t m, int32_t* __restrict__ table, uint32_t mask, int32_t* __restrict__ slot_of,
+                            int32_t* __restrict__ slot_u, unsigned long long* __restrict__ fresh, uint32_t u0,
+                            Canon* __restrict__ ucanon_new, uint8_t* __restrict__ flen, int32_t* __restrict__ nuid,
+                            uint8_t* __restrict__ is_rep, int* __restrict__ err) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const Canon c = load_canon(qcanon + j);
+    const uint64_t h = hash_canon(c);
+    const uint32_t pid = part_of(h, ix.P);
+    for (int64_t k = ix.poff[pid], k1 = ix.poff[pid + 1]; k < k1; ++k) {
+        const uint64_t r = ix.recs[k];
+        if ((uint32_t)(r >> 32) == (uint32_t)h && rec_p(r) == kTagF && canon_eq(c, load_canon(ix.ucanon + rec_u(r)))) {
+            nuid[j] = (int32_t)rec_u(r);
+            slot_of[j] = -1;
+            is_rep[j] = 0;
+            return;
+        }
+    }
+    uint32_t slot = (uint32_t)h & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const int32_t r = atomicCAS(&table[slot], -1, (int32_t)j);
+        if (r == -1) {
+            const uint32_t f = (uint32_t)atomicAdd(fresh, 1ull);
+            slot_u[slot] = (int32_t)(u0 + f);
+            store_canon(ucanon_new + u0 + f, c);
+            flen[f] = qlen[j];
+            slot_of[j] = (int32_t)slot;
+            is_rep[j] = 1;
+            return;
+        }
+        if (canon_eq(load_canon(qcanon + r), c)) {
+            slot_of[j] = (int32_t)slot;
+            is_rep[j] = 0;
+            return;
+        }
+        slot = (slot + 1) & mask;
+    }
+    atomicExch(err, 1);  // unreachable: the table has at least 2m slots
+    slot_of[j] = -1;
+    nuid[j] = 0;
+    is_rep[j] = 0;
+}
+
+// Fresh ids resolved (their slots are all numbered now); node ids and
+// multiplicities of the grown repertoire.
+__global__ void k_ins_uid(const int32_t* __restrict__ slot_of, const int32_t* __restrict__ slot_u, int64_t m,
+                          int64_t n0, int32_t* __restrict__ nuid, int32_t* __restrict__ uid_new,
+                          int32_t* __restrict__ umult_new) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int32_t sl = slot_of[j];
+    const int32_t u = sl >= 0 ? slot_u[sl] : nuid[j];
+    nuid[j] = u;
+    uid_new[n0 + j] = u;
+    atomicAdd(&umult_new[u], 1);
+}
+
+// Partition starts after the new records (poff_new = poff + exclusive counts of
+// the new records) and the slot cursor of each partition (its old size).
+__global__ void k_ins_part_base(const int64_t* __restrict__ poff, const int64_t* __restrict__ pscan, int64_t P,
+                                int64_t* __restrict__ poff_new, int32_t* __restrict__ pcur) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > P) return;
+    poff_new[p] = poff[p] + pscan[p];
+    if (p < P) pcur[p] = (int32_t)(poff[p + 1] - poff[p]);
+}
+
+// Segments (rows, partitions) that grow: flag[i] = grow[i] > 0.
+__global__ void k_ins_flags(const int32_t* __restrict__ grow, int64_t R, int32_t* __restrict__ flag) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < R) flag[i] = grow[i] > 0 ? 1 : 0;
+}
+
+// Cuts of a segmented array whose segments grow at their ends: the old
+// elements after the end of the k-th growing segment move by shifts[k + 1]
+// (shifts[0] = 0: elements before the first cut stay).
+template <typename OffT>
+__global__ void k_ins_cuts(const int32_t* __restrict__ grow, const OffT* __restrict__ old_off,
+                           const int64_t* __restrict__ new_off, int64_t R, const int64_t* __restrict__ pos,
+                           int64_t* __restrict__ cuts, int64_t* __restrict__ shifts) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= R || grow[i] <= 0) return;
+    const int64_t k = pos[i];
+    const int64_t end = (int64_t)old_off[i + 1];
+    cuts[k] = end;
+    shifts[k + 1] = new_off[i + 1] - end;
+}
+
+// dst[t + shifts[k(t)]] = src[t], k(t) = number of cuts <= t. Each block moves
+// one contiguous range, finds the piece of its first element by a block-wide
+// 256-ary search and advances through the (sorted) cuts with its elements.
+template <typename T>
+__global__ void __launch_bounds__(256) k_shifted_copy(const T* __restrict__ src, T* __restrict__ dst, int64_t count,
+                                                      const int64_t* __restrict__ cuts,
+                                                      const int64_t* __restrict__ shifts,
+                                                      const int64_t* __restrict__ K_ptr) {
+    constexpr int kUnroll = 8;
+    const int64_t K = *K_ptr;
+    const int64_t nb = (int64_t)blockDim.x;
+    const int64_t per = ((count + gridDim.x - 1) / gridDim.x + nb - 1) / nb * nb;
+    const int64_t b0 = (int64_t)blockIdx.x * per;
+    const int64_t b1 = b0 + per < count ? b0 + per : count;
+    if (b0 >= b1) return;
+    // first index k with cuts[k] > b0, in [lo, hi]
+    int64_t lo = 0, hi = K;
+    while (hi > lo) {
+        const int64_t span = hi - lo;
+        const int64_t step = span <= nb ? 1 : (span + nb - 1) / nb;
+        const int64_t idx = lo + (int64_t)threadIdx.x * step;
+        const bool le = idx < hi && cuts[idx] <= b0;
+        const int c = __syncthreads_count(le);  // probes at or below b0 form a prefix
+        if (c == 0) break;                      // cuts[lo] > b0: the answer is lo
+        const int64_t nlo = lo + (int64_t)(c - 1) * step + 1;
+        hi = lo + (int64_t)c * step < hi ? lo + (int64_t)c * step : hi;
+        lo = nlo;
+        if (step == 1) break;  // every index in the span was probed
+    }
+    int64_t k = lo;
+    for (int64_t t0 = b0 + threadIdx.x; t0 < b1; t0 += (int64_t)kUnroll * blockDim.x) {
+        T v[kUnroll];
+#pragma unroll
+        for (int r = 0; r < kUnroll; ++r) {
+            const int64_t t = t0 + (int64_t)r * blockDim.x;
+            if (t < b1) v[r] = src[t];
+        }
+#pragma unroll
+        for (int r = 0; r < kUnroll; ++r) {
+            const int64_t t = t0 + (int64_t)r * blockDim.x;
+            if (t < b1) {
+                while (k < K && cuts[k] <= t) ++k;
+                dst[t + shifts[k]] = v[r];
+            }
+        }
+    }
+}
+
+// Edges between a fresh distinct string and a resident one: for the
+// representative of each fresh string, every resident distinct string among
+// its query neighbours (all members of a neighbour are listed; its first
+// member stands for it).
+__global__ void k_ins_edges_old(const int64_t* __restrict__ qoff, const int32_t* __restrict__ qcols, int64_t m,
+                                const uint8_t* __restrict__ is_rep, const int32_t* __restrict__ nuid,
+                                const int32_t* __restrict__ uid_old, const int64_t* __restrict__ mem_off_old,
+                                const int32_t* __restrict__ members_old, int2* __restrict__ out,
+                                unsigned long long* __restrict__ cur, int64_t cap, int* __restrict__ err) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < m; j += nw) {
+        if (!is_rep[j]) continue;
+        const int32_t w = nuid[j];
+        for (int64_t e = qoff[j] + lane; e < qoff[j + 1]; e += 32) {
+            const int32_t i = qcols[e];
+            const int32_t x = uid_old[i];
+            if (members_old[mem_off_old[x]] != i) continue;
+            const unsigned long long slot = atomicAdd(cur, 1ull);
+            if ((int64_t)slot < cap) out[slot] = make_int2(w, x);
+            else atomicExch(err, 1);
+        }
+    }
+}
+
+// Edges between two fresh distinct strings: pairs of representatives j < k
+// adjacent in the network of the new strings.
+__global__ void k_ins_edges_new(const int64_t* __restrict__ noff, const int32_t* __restrict__ ncols, int64_t m,
+                                const uint8_t* __restrict__ is_rep, const int32_t* __restrict__ nuid,
+                                int2* __restrict__ out, unsigned long long* __restrict__ cur, int64_t cap,
+                                int* __restrict__ err) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < m; j += nw) {
+        if (!is_rep[j]) continue;
+        for (int64_t e = noff[j] + lane; e < noff[j + 1]; e += 32) {
+            const int32_t k = ncols[e];
+            if (k <= j || !is_rep[k]) continue;
+            const unsigned long long slot = atomicAdd(cur, 1ull);
+            if ((int64_t)slot < cap) out[slot] = make_int2(nuid[j], nuid[k]);
+            else atomicExch(err, 1);
+        }
+    }
+}
+
+// New entries of old rows: delta[i] = number of new strings adjacent to old node i.
+__global__ void k_ins_delta(const int32_t* __restrict__ qcols, int64_t nq, int32_t* __restrict__ delta) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nq; e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&delta[qcols[e]], 1);
+}
+
+// Degrees of the grown network.
+__global__ void k_ins_degree(const int32_t* __restrict__ deg_old, const int32_t* __restrict__ delta, int64_t n0,
+                             const int32_t* __restrict__ qcnt, const int32_t* __restrict__ ndeg, int64_t m,
+                             int32_t* __restrict__ deg) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n0) deg[i] = deg_old[i] + delta[i];
+    else if (i < n0 + m) deg[i] = qcnt[i - n0] + ndeg[i - n0];
+}
+
+// Transpose of the query rows: old node i receives n0 + j for every new string
+// j adjacent to it, at a slot of its tail list (sorted afterwards).
+__global__ void k_ins_tails(const int64_t* __restrict__ qoff, const int32_t* __restrict__ qcols, int64_t m,
+                            int64_t n0, const int64_t* __restrict__ toff, int32_t* __restrict__ tcur,
+                            int32_t* __restrict__ tcols) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < m; j += nw)
+        for (int64_t e = qoff[j] + lane; e < qoff[j + 1]; e += 32) {
+            const int32_t i = qcols[e];
+            tcols[toff[i] + atomicAdd(&tcur[i], 1)] = (int32_t)(n0 + j);
+        }
+}
+
+// Tail lists of the old rows after their old entries.
+template <typename OffT>
+__global__ void k_ins_fill_tails(const OffT* __restrict__ old_off, const int64_t* __restrict__ new_off,
+                                 const int64_t* __restrict__ toff, const int32_t* __restrict__ tcols, int64_t n0,
+                                 int32_t* __restrict__ cols) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n0) return;
+    const int64_t a = toff[i], b = toff[i + 1];
+    if (a == b) return;
+    int32_t* row = cols + new_off[i] + ((int64_t)old_off[i + 1] - (int64_t)old_off[i]);
+    for (int64_t e = a; e < b; ++e) row[e - a] = tcols[e];
+}
+
+// Rows of the new strings: old neighbours (ascending), then new ones.
+__global__ void k_ins_fill_new(const int64_t* __restrict__ qoff, const int32_t* __restrict__ qcols,
+                               const int64_t* __restrict__ noff, const int32_t* __restrict__ ncols, int64_t m,
+                               int64_t n0, const int64_t* __restrict__ new_off, int32_t* __restrict__ cols) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < m; j += nw) {
+        int32_t* row = cols + new_off[n0 + j];
+        const int64_t q0 = qoff[j], nq = qoff[j + 1] - q0;
+        for (int64_t e = lane; e < nq; e += 32) row[e] = qcols[q0 + e];
+        const int64_t a = noff[j], nn = noff[j + 1] - a;
+        for (int64_t e = lane; e < nn; e += 32) row[nq + e] = (int32_t)(n0 + ncols[a + e]);
+    }
+}
+
+// Cuts of a segmented array (segment i = [old_off[i], old_off[i+1]) grows by
+// grow[i] at its end; new_off = the grown offsets): K (on the device), cuts
+// and shifts for k_shifted_copy.
+template <typename OffT>
+tcrnet_status growth_cuts(const int32_t* grow, const OffT* old_off, const int64_t* new_off, int64_t R,
+                          int64_t max_cuts, DevBuf& cuts, DevBuf& shifts, DevBuf& pos, cudaStream_t s) {
+    DevBuf flag;
+    TCR_CHECK(flag.alloc(sizeof(int32_t) * (R > 0 ? R : 1), s));
+    TCR_CHECK(pos.alloc(sizeof(int64_t) * (R + 1), s));
+    TCR_CHECK(cuts.alloc(sizeof(int64_t) * (max_cuts > 0 ? max_cuts : 1), s));
+    TCR_CHECK(shifts.alloc(sizeof(int64_t) * (max_cuts + 1), s));
+    TCR_CUDA(cudaMemsetAsync(shifts.as<void>(), 0, sizeof(int64_t), s));
+    if (R == 0) {
+        TCR_CUDA(cudaMemsetAsync(pos.as<void>(), 0, sizeof(int64_t), s));
+        return TCRNET_OK;
+    }
+    k_ins_flags<<<grid_for(R), kThreads, 0, s>>>(grow, R, flag.as<int32_t>());
+    TCR_LAUNCH_CHECK();
+    TCR_CHECK(scan_exclusive_i32_to_i64(flag.as<int32_t>(), pos.as<int64_t>(), R, s));
+    k_ins_cuts<OffT><<<grid_for(R), kThreads, 0, s>>>(grow, old_off, new_off, R, pos.as<int64_t>(),
+                                                       cuts.as<int64_t>(), shifts.as<int64_t>());
+    TCR_LAUNCH_CHECK();
+    return TCRNET_OK;
+}
+
+template <typename T>
+tcrnet_status shifted_copy(const T* src, T* dst, int64_t count, const DevBuf& cuts, const DevBuf& shifts,
+                           const int64_t* K_dev, cudaStream_t s, int num_sms) {
+    if (count <= 0) return TCRNET_OK;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(count, 256 * 16), (int64_t)num_sms * 8));
+    k_shifted_copy<T><<<(unsigned)blocks, 256, 0, s>>>(src, dst, count, cuts.as<int64_t>(), shifts.as<int64_t>(),
+                                                       K_dev);
+    TCR_LAUNCH_CHECK();
+    return TCRNET_OK;
+}
+
+template <typename OffT>
+tcrnet_status csr_merge(const CsrView& g, const OffT* old_off, const int32_t* delta, const int64_t* new_off,
+                        const int64_t* toff, const int32_t* tcols, int64_t nq, const int64_t* qoff,
+                        const int32_t* qcols, const int64_t* noff, const int32_t* ncols, int64_t m, int32_t* cols,
+                        cudaStream_t s, int num_sms) {
+    const int64_t n0 = g.n;
+    DevBuf cuts, shifts, pos;
+    TCR_CHECK(growth_cuts<OffT>(delta, old_off, new_off, n0, std::min<int64_t>(n0, nq), cuts, shifts, pos, s));
+    TCR_CHECK(shifted_copy<int32_t>(g.cols, cols, g.nnz, cuts, shifts, pos.as<int64_t>() + n0, s, num_sms));
+    if (nq > 0 && n0 > 0) {
+        k_ins_fill_tails<OffT><<<grid_for(n0), kThreads, 0, s>>>(old_off, new_off, toff, tcols, n0, cols);
+        TCR_LAUNCH_CHECK();
+    }
+    const unsigned wgrid = (unsigned)std::min<int64_t>(ceil_div(m, kWarps), (int64_t)num_sms * 16);
+    k_ins_fill_new<<<wgrid, kThreads, 0, s>>>(qoff, qcols, noff, ncols, m, n0, new_off, cols);
+    TCR_LAUNCH_CHECK();
+    return TCRNET_OK;
+}
+
+}  // namespace
+
+tcrnet_status deletion_insert(const DeletionIndex& ix, const CsrView& g, const Packed& q, int T, InsertResult& out,
+                              cudaStream_t s, int num_sms) {
+    const int64_t m = q.n, n0 = g.n, N = n0 + m;
+    const int64_t U0 = ix.U, P = ix.P, R0 = ix.R, E0 = ix.E;
+    if (!ix.valid() || !ix.uid || ix.n != n0 || m <= 0 || N > kDeletionMaxN || T < 1) return TCRNET_ESTATE;
+    IndexView v{ix.ucanon, ix.umult, ix.mem_off, ix.members, ix.recs, ix.poff, (uint32_t)P};
+
+    // 1. neighbours of the new strings among the resident nodes, and among
+    //    the new strings themselves
+    DevBuf qoff, qcols, qcnt;
+    int64_t nq = 0;
+    TCR_CHECK(deletion_query(ix, q, T, qoff, qcols, qcnt, &nq, s, num_sms));
+    DeletionResult dn;
+    TCR_CHECK(deletion_build(q, T, dn, s, num_sms, false, 0, false, 0, true));
+    const int64_t nn = dn.nnz;
+
+    // 2. distinct ids of the new strings; fresh distinct strings
+    DevBuf errb, counters;
+    TCR_CHECK(errb.alloc(sizeof(int) * 4, s));
+    TCR_CHECK(counters.alloc(sizeof(unsigned long long) * 2, s));  // [0] fresh strings, [1] new edges
+    TCR_CUDA(cudaMemsetAsync(errb.as<void>(), 0, sizeof(int) * 4, s));
+    TCR_CUDA(cudaMemsetAsync(counters.as<void>(), 0, sizeof(unsigned long long) * 2, s));
+    int* d_err = errb.as<int>();
+    unsigned long long* d_fresh = counters.as<unsigned long long>();
+    unsigned long long* d_ecur = d_fresh + 1;
+    int64_t S = 1024;
+    while (S < 2 * m) S <<= 1;
+    DevBuf table, slot_of, slot_u, flen, nuid, is_rep;
+    TCR_CHECK(table.alloc(sizeof(int32_t) * S, s));
+    TCR_CHECK(slot_u.alloc(sizeof(int32_t) * S, s));
+    TCR_CHECK(slot_of.alloc(sizeof(int32_t) * m, s));
+    TCR_CHECK(flen.alloc(m, s));
+    TCR_CHECK(nuid.alloc(sizeof(int32_t) * m, s));
+    TCR_CHECK(is_rep.alloc(m, s));
+    TCR_CUDA(cudaMemsetAsync(table.as<void>(), 0xff, sizeof(int32_t) * S, s));
+    // index arrays of the grown repertoire, sized for N strings like a build's
+    DevBuf ucanon, umult, uid, mem_off, members, mcur, mpos;
+    TCR_CHECK(ucanon.alloc_owned(sizeof(Canon) * N, s));
+    TCR_CHECK(umult.alloc_owned(sizeof(int32_t) * N, s));
+    TCR_CHECK(uid.alloc_owned(sizeof(int32_t) * N, s));
+    TCR_CHECK(mem_off.alloc_owned(sizeof(int64_t) * (N + 1), s));
+    TCR_CHECK(members.alloc_owned(sizeof(int32_t) * N, s));
+    TCR_CHECK(mcur.alloc(sizeof(int32_t) * N, s));
+    TCR_CHECK(mpos.alloc(sizeof(int32_t) * N, s));
+    if (U0 > 0)
+        TCR_CUDA(cudaMemcpyAsync(ucanon.as<void>(), ix.ucanon, sizeof(Canon) * U0, cudaMemcpyDeviceToDevice, s));
+    TCR_CUDA(cudaMemcpyAsync(umult.as<void>(), ix.umult, sizeof(int32_t) * n0, cudaMemcpyDeviceToDevice, s));
+    TCR_CUDA(cudaMemsetAsync(umult.as<int32_t>() + n0, 0, sizeof(int32_t) * m, s));
+    TCR_CUDA(cudaMemcpyAsync(uid.as<void>(), ix.uid, sizeof(int32_t) * n0, cudaMemcpyDeviceToDevice, s));
+    k_ins_dedup<<<grid_for(m), kThreads, 0, s>>>(v, q.canon_in.as<Canon>(), q.lens.as<uint8_t>(), m,
+                                                 table.as<int32_t>(), (uint32_t)(S - 1), slot_of.as<int32_t>(),
+                                                 slot_u.as<int32_t>(), d_fresh, (uint32_t)U0, ucanon.as<Canon>(),
+                                                 flen.as<uint8_t>(), nuid.as<int32_t>(), is_rep.as<uint8_t>(), d_err);
+    TCR_LAUNCH_CHECK();
+    k_ins_uid<<<grid_for(m), kThreads, 0, s>>>(slot_of.as<int32_t>(), slot_u.as<int32_t>(), m, n0,
+                                               nuid.as<int32_t>(), uid.as<int32_t>(), umult.as<int32_t>());
+    TCR_LAUNCH_CHECK();
+    TCR_CHECK(scan_exclusive_i32_to_i64(umult.as<int32_t>(), mem_off.as<int64_t>(), N, s));
+    TCR_CUDA(cudaMemsetAsync(mcur.as<void>(), 0, sizeof(int32_t) * N, s));
+    k_members<<<grid_for(N), kThreads, 0, s>>>(uid.as<int32_t>(), N, mem_off.as<int64_t>(), mcur.as<int32_t>(),
+                                               members.as<int32_t>(), mpos.as<int32_t>());
+    TCR_LAUNCH_CHECK();
+
+    // 3. records of the fresh strings into the same partitions
+    const int64_t R_bound = R0 + m + q.lensum;
+    DevBuf pcnt, pscan, poff, recs;
+    TCR_CHECK(pcnt.alloc(sizeof(int32_t) * P, s));
+    TCR_CHECK(pscan.alloc(sizeof(int64_t) * (P + 1), s));
+    TCR_CHECK(poff.alloc_owned(sizeof(int64_t) * (P + 1), s));
+    TCR_CHECK(recs.alloc_owned(sizeof(uint64_t) * R_bound, s));
+    TCR_CUDA(cudaMemsetAsync(pcnt.as<void>(), 0, sizeof(int32_t) * P, s));
+    const int64_t* d_F = reinterpret_cast<const int64_t*>(d_fresh);
+    k_records<false><<<grid_for(m), kThreads, 0, s>>>(ucanon.as<Canon>() + U0, flen.as<uint8_t>(), d_F, m,
+                                                      (uint32_t)P, pcnt.as<int32_t>(), nullptr, nullptr, (uint32_t)U0);
+    TCR_LAUNCH_CHECK();
+    TCR_CHECK(scan_exclusive_i32_to_i64(pcnt.as<int32_t>(), pscan.as<int64_t>(), P, s));
+    DevBuf pcur;
+    TCR_CHECK(pcur.alloc(sizeof(int32_t) * P, s));
+    k_ins_part_base<<<grid_for(P + 1), kThreads, 0, s>>>(ix.poff, pscan.as<int64_t>(), P, poff.as<int64_t>(),
+                                                         pcur.as<int32_t>());
+    TCR_LAUNCH_CHECK();
+    {
+        DevBuf cuts, shifts, pos;
+        TCR_CHECK(growth_cuts<int64_t>(pcnt.as<int32_t>(), ix.poff, poff.as<int64_t>(), P,
+                                       std::min<int64_t>(P, m + q.lensum), cuts, shifts, pos, s));
+        TCR_CHECK(shifted_copy<uint64_t>(ix.recs, recs.as<uint64_t>(), R0, cuts, shifts, pos.as<int64_t>() + P, s,
+                                         num_sms));
+    }
+    k_records<true><<<grid_for(m), kThreads, 0, s>>>(ucanon.as<Canon>() + U0, flen.as<uint8_t>(), d_F, m,
+                                                     (uint32_t)P, pcur.as<int32_t>(), poff.as<int64_t>(),
+                                                     recs.as<uint64_t>(), (uint32_t)U0);
+    TCR_LAUNCH_CHECK();
+
+    // 4. edges between distinct strings: the resident ones, then those of the
+    //    fresh strings (to resident strings, to each other)
+    const int64_t E_cap = E0 + nq + nn;
+    DevBuf uedges;
+    TCR_CHECK(uedges.alloc_owned(sizeof(int2) * (E_cap > 0 ? E_cap : 1), s));
+    if (E0 > 0)
+        TCR_CUDA(cudaMemcpyAsync(uedges.as<void>(), ix.uedges, sizeof(int2) * E0, cudaMemcpyDeviceToDevice, s));
+    const unsigned wgrid = (unsigned)std::min<int64_t>(ceil_div(m, kWarps), (int64_t)num_sms * 16);
+    k_ins_edges_old<<<wgrid, kThreads, 0, s>>>(qoff.as<int64_t>(), qcols.as<int32_t>(), m, is_rep.as<uint8_t>(),
+                                               nuid.as<int32_t>(), ix.uid, ix.mem_off, ix.members,
+                                               uedges.as<int2>() + E0, d_ecur, E_cap - E0, d_err + 1);
+    TCR_LAUNCH_CHECK();
+    k_ins_edges_new<<<wgrid, kThreads, 0, s>>>(dn.off64.as<int64_t>(), dn.cols.as<int32_t>(), m,
+                                               is_rep.as<uint8_t>(), nuid.as<int32_t>(), uedges.as<int2>() + E0,
+                                               d_ecur, E_cap - E0, d_err + 1);
+    TCR_LAUNCH_CHECK();
+
+    // 5. the grown CSR: degrees, offsets, old rows moved with their tails, new rows
+    DevBuf delta, deg, off64, toff, tcur, tcols, cols;
+    TCR_CHECK(delta.alloc(sizeof(int32_t) * (n0 > 0 ? n0 : 1), s));
+    TCR_CHECK(deg.alloc_owned(sizeof(int32_t) * N, s));
+    TCR_CHECK(off64.alloc_owned(sizeof(int64_t) * (N + 1), s));
+    TCR_CHECK(toff.alloc(sizeof(int64_t) * (n0 + 1), s));
+    TCR_CHECK(tcur.alloc(sizeof(int32_t) * (n0 > 0 ? n0 : 1), s));
+    TCR_CHECK(tcols.alloc(sizeof(int32_t) * (nq > 0 ? nq : 1), s));
+    const int64_t nnz = g.nnz + 2 * nq + nn;
+    TCR_CHECK(cols.alloc_owned(sizeof(int32_t) * nnz, s));
+    TCR_CUDA(cudaMemsetAsync(delta.as<void>(), 0, sizeof(int32_t) * n0, s));
+    TCR_CUDA(cudaMemsetAsync(tcur.as<void>(), 0, sizeof(int32_t) * n0, s));
+    if (nq > 0) {
+        k_ins_delta<<<(unsigned)std::min<int64_t>(grid_for(nq), (int64_t)num_sms * 16), kThreads, 0, s>>>(
+            qcols.as<int32_t>(), nq, delta.as<int32_t>());
+        TCR_LAUNCH_CHECK();
+    }
+    k_ins_degree<<<grid_for(N), kThreads, 0, s>>>(g.degree, delta.as<int32_t>(), n0, qcnt.as<int32_t>(),
+                                                  dn.degree.as<int32_t>(), m, deg.as<int32_t>());
+    TCR_LAUNCH_CHECK();
+    TCR_CHECK(scan_exclusive_i32_to_i64(deg.as<int32_t>(), off64.as<int64_t>(), N, s));
+    TCR_CHECK(scan_exclusive_i32_to_i64(delta.as<int32_t>(), toff.as<int64_t>(), n0, s));
+    if (nq > 0) {
+        k_ins_tails<<<wgrid, kThreads, 0, s>>>(qoff.as<int64_t>(), qcols.as<int32_t>(), m, n0, toff.as<int64_t>(),
+                                               tcur.as<int32_t>(), tcols.as<int32_t>());
+        TCR_LAUNCH_CHECK();
+        TCR_CHECK(sort_rows(toff.as<int64_t>(), tcols.as<int32_t>(), n0, s, num_sms));
+    }
+    if (g.off64)
+        TCR_CHECK(csr_merge<int64_t>(g, static_cast<const int64_t*>(g.offsets), delta.as<int32_t>(),
+                                     off64.as<int64_t>(), toff.as<int64_t>(), tcols.as<int32_t>(), nq,
+                                     qoff.as<int64_t>(), qcols.as<int32_t>(), dn.off64.as<int64_t>(),
+                                     dn.cols.as<int32_t>(), m, cols.as<int32_t>(), s, num_sms));
+    else
+        TCR_CHECK(csr_merge<int32_t>(g, static_cast<const int32_t*>(g.offsets), delta.as<int32_t>(),
+                                     off64.as<int64_t>(), toff.as<int64_t>(), tcols.as<int32_t>(), nq,
+                                     qoff.as<int64_t>(), qcols.as<int32_t>(), dn.off64.as<int64_t>(),
+                                     dn.cols.as<int32_t>(), m, cols.as<int32_t>(), s, num_sms));
+
+    // 6. sizes and error flags
+    unsigned long long h_cnt[2] = {0, 0};
+    int h_err[2] = {0, 0};
+    int64_t h_R = 0, h_nnz = 0;
+    TCR_CUDA(cudaMemcpyAsync(h_cnt, d_fresh, sizeof(h_cnt), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaMemcpyAsync(h_err, d_err, sizeof(h_err), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaMemcpyAsync(&h_R, poff.as<int64_t>() + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaMemcpyAsync(&h_nnz, off64.as<int64_t>() + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaStreamSynchronize(s));
+    if (h_err[0] || h_err[1] || h_nnz != nnz || h_R > R_bound) return TCRNET_EDEVICE;
+
+    out.off64 = std::move(off64);
+    out.cols = std::move(cols);
+    out.degree = std::move(deg);
+    out.nnz = nnz;
+    out.fresh = (int64_t)h_cnt[0];
+    out.new_edges = (int64_t)h_cnt[1];
+    out.index.ucanon = static_cast<Canon*>(ucanon.release());
+    out.index.umult = static_cast<int32_t*>(umult.release());
+    out.index.mem_off = static_cast<int64_t*>(mem_off.release());
+    out.index.members = static_cast<int32_t*>(members.release());
+    out.index.recs = static_cast<uint64_t*>(recs.release());
+    out.index.poff = static_cast<int64_t*>(poff.release());
+    out.index.uid = static_cast<int32_t*>(uid.release());
+    out.index.uedges = static_cast<int2*>(uedges.release());
+    out.index.U = U0 + out.fresh;
+    out.index.P = P;
+    out.index.R = h_R;
+    out.index.n = N;
+    out.index.E = E0 + out.new_edges;
     return TCRNET_OK;
 }
 

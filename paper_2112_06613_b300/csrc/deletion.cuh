@@ -24,6 +24,7 @@ struct DeletionIndex {
     int32_t* uid = nullptr;    // node -> distinct string
     int2* uedges = nullptr;    // edges between distinct strings, each once
     int64_t U = 0, P = 0, n = 0, E = 0;
+    int64_t R = 0;             // records (poff[P])
     bool valid() const { return recs != nullptr; }
 };
 
@@ -55,5 +56,34 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
 // index: CSR with int64 offsets (m + 1), columns, per-query counts.
 tcrnet_status deletion_query(const DeletionIndex& ix, const Packed& q, int T, DevBuf& off64, DevBuf& cols,
                              DevBuf& count, int64_t* nnz, cudaStream_t s, int num_sms);
+
+// A resident network (device views of a handle's CSR).
+struct CsrView {
+    const void* offsets = nullptr;  // int32 or int64 [n + 1]
+    bool off64 = false;
+    const int32_t* cols = nullptr;  // [nnz], rows ascending
+    const int32_t* degree = nullptr;
+    int64_t n = 0, nnz = 0;
+};
+
+struct InsertResult {
+    DevBuf off64;   // int64[N + 1]
+    DevBuf cols;    // int32[nnz]
+    DevBuf degree;  // int32[N]
+    int64_t nnz = 0;
+    int64_t fresh = 0;      // new distinct strings
+    int64_t new_edges = 0;  // new edges between distinct strings
+    DeletionIndex index;    // index of the grown repertoire; the caller owns it
+};
+
+// Network and index of a deletion build's repertoire (ix, g: n0 strings,
+// l_max = T >= 1) grown by the m strings of q (input order, not bucketed), as
+// nodes n0 .. n0+m-1, merged instead of rebuilt: the rows of the new strings
+// come from their query against ix and from the network of the new strings
+// alone; old rows gain the new neighbours at their ends; the index gains the
+// new distinct strings and their records in the same partitions. ix and g are
+// only read. The CSR equals that of a fresh build of the concatenation.
+tcrnet_status deletion_insert(const DeletionIndex& ix, const CsrView& g, const Packed& q, int T, InsertResult& out,
+                              cudaStream_t s, int num_sms);
 
 }  // namespace tcr

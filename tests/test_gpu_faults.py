@@ -74,7 +74,7 @@ def test_query_and_insert_allocation_failures_keep_the_handle():
                 assert_csr_equal(got[0], got[1], qref[0], qref[1], f"query fail_alloc_at={k}")
                 break
             assert st == tn.ENOMEM and h.value is None
-        for k in range(1, 80):
+        for k in range(1, 400):
             opt = tn.make_options(fail_alloc_at=k)
             st = lib.tcrnet_insert_ex(g.handle, add.chars.ctypes.data, add.offsets.ctypes.data, add.n, tn.HOST,
                                       ctypes.byref(opt))
