@@ -63,7 +63,7 @@ PHASE_TRAFFIC_N800000 = {
     "expand": 83.94e6 + 200.01e6,
 }
 
-LEGS = ("tile", "query", "e2e", "analytics", "lmax2", "batched", "serving", "cpu")
+LEGS = ("tile", "query", "e2e", "insert", "analytics", "lmax2", "batched", "serving", "cpu")
 
 
 def parse_args():
@@ -627,6 +627,41 @@ def run_ours(args):
             line["e2e"] = {"value": pairs_per_build / (e_ms / 1e3), "unit": UNIT, "ms_per_step": e_ms,
                            "h2d_bytes_per_step": int(rep.chars.nbytes + rep.offsets.nbytes),
                            "d2h_bytes_per_step": int(4 * (n + 1) + 4 * nnz + 4 * n)}
+        if "insert" in legs:
+            # --- inserts into the resident N = 8e5 network: merged (query + network
+            #     of the new strings, grown rows and index) vs rebuilt; copy-on-write
+            #     (tcrnet_extend), new strings in device memory
+            from synthgen import generate_config2
+
+            ipool = generate_config2(100_000, seed=2000 + rank)
+            ic = torch.from_numpy(ipool.chars).to(dev)
+            io = torch.from_numpy(ipool.offsets).to(dev)
+            ins = {}
+            with build() as g:
+                for m_ins in (100, 1_000, 10_000, 100_000):
+                    row = {}
+                    for mode, rebuild in (("merged", False), ("rebuilt", True)):
+                        ts = []
+                        for k in range(4):
+                            torch.cuda.synchronize()
+                            t = time.perf_counter()
+                            g2 = g.extend_flat(ic, io[:m_ins + 1], stream=stream, rebuild=rebuild)
+                            torch.cuda.synchronize()
+                            dt = 1e3 * (time.perf_counter() - t)
+                            if k == 0:
+                                st2 = g2.stats()
+                            g2.free()
+                            if k >= 1:
+                                ts.append(dt)
+                        row[f"{mode}_ms"] = statistics.median(ts)
+                        if mode == "merged":
+                            row["merged"] = st2["merged_inserts"] == 1
+                            row["nnz_after"] = st2["nnz"]
+                    row["speedup"] = row["rebuilt_ms"] / row["merged_ms"]
+                    ins[str(m_ins)] = row
+            line["insert"] = {"resident_strings": n, "sizes": ins,
+                              "timing": "host time of tcrnet_extend (copy-on-write insert) with a stream sync, median of 3 "
+                                        "after 1 warm-up; new strings already in device memory"}
         if "analytics" in legs:
             # --- analytics on the N = 8e5 network: LCC under random node removal
             #     (normalisations of Methods "Computing LCC"), average neighbour degree

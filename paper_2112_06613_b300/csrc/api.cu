@@ -805,7 +805,7 @@ tcrnet_status extend_impl(tcrnet_handle h, const uint8_t* chars, const int64_t* 
         gv.n = n_old;
         gv.nnz = h->nnz;
         InsertResult ir;
-        st = deletion_insert(ix, gv, pn, h->threshold, ir, s, sms);
+        st = deletion_insert(ix, gv, pn, h->threshold, ir, s, sms, opt.profile != 0);
         if (st == TCRNET_OK) {
             g->ix = ir.index;  // owned by g from here on (freed with it on a later error)
             ir.index = DeletionIndex();
@@ -814,6 +814,8 @@ tcrnet_status extend_impl(tcrnet_handle h, const uint8_t* chars, const int64_t* 
             g->stats.n_records = g->ix.R;
             g->stats.unique_edges = g->ix.E;
             g->stats.merged_inserts = h->stats.merged_inserts + 1;
+            for (int k = 0; k < 8; ++k) g->stats.ms_phase[k] = ir.ms_phase[k];
+            g->stats.ms_total = ir.ms_phase[7];
             st = export_csr(g, ir.off64, ir.cols, ir.degree, N, ir.nnz, opt.force_offsets64 != 0, s);
         }
         if (st == TCRNET_OK) {

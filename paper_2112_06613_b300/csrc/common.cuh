@@ -227,6 +227,17 @@ private:
 
 class DevBuf {
 public:
+    // Large blocks are requested in size classes (multiples of an eighth of
+    // their power of two, at most 12.5% over): a network that grows by small
+    // inserts then gets a block of the size that its previous version freed,
+    // which the stream-ordered pool reuses, instead of a slightly larger one
+    // that would map new memory on every insert.
+    static size_t size_class(size_t bytes) {
+        if (bytes < (size_t(32) << 20)) return bytes;
+        int top = 63 - __builtin_clzll((unsigned long long)bytes);
+        const size_t step = size_t(1) << (top - 3);
+        return (bytes + step - 1) / step * step;
+    }
     DevBuf() = default;
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
@@ -280,7 +291,7 @@ public:
         bytes_ = bytes;
         arena_ = false;
         if (bytes == 0) bytes = 16;
-        cudaError_t e = cudaMallocAsync(&p_, bytes, s);
+        cudaError_t e = cudaMallocAsync(&p_, size_class(bytes), s);
         if (e != cudaSuccess) {
             p_ = nullptr;
             bytes_ = 0;

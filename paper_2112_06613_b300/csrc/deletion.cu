@@ -1246,16 +1246,44 @@ k_query(IndexView ix, const Canon* __restrict__ qcanon, const uint8_t* __restric
             query_record(ix, qc, Lq, p, T, [&](uint32_t u) { mine += ix.umult[u]; });
         int64_t excl;
         const int64_t total = warp_scan(mine, excl, lane);
-        if (!WRITE) {
+        if constexpr (!WRITE) {
             if (lane == 0) qcount[q] = total;
         } else {
+            // a lane copies short member lists itself and queues long ones
+            // (strings with many copies), which the whole warp copies after
+            constexpr int kLaneCopyMax = 8, kQueued = 16;
+            __shared__ int64_t big_src[kWarps][kQueued], big_dst[kWarps][kQueued];
+            __shared__ int32_t big_len[kWarps][kQueued];
+            __shared__ int big_n[kWarps];
+            const int w = threadIdx.x >> 5;
+            if (lane == 0) big_n[w] = 0;
+            __syncwarp();
             int64_t pos = qoff[q] + excl;
             for (int p = lane - 1; p < Lq; p += 32)
                 query_record(ix, qc, Lq, p, T, [&](uint32_t u) {
-                    const int32_t* mb = ix.members + ix.mem_off[u];
+                    const int64_t src = ix.mem_off[u];
                     const int32_t mu = ix.umult[u];
-                    for (int32_t y = 0; y < mu; ++y) out[pos++] = mb[y];
+                    int slot = kQueued;
+                    if (mu > kLaneCopyMax) {
+                        slot = atomicAdd(&big_n[w], 1);
+                        if (slot < kQueued) {
+                            big_src[w][slot] = src;
+                            big_dst[w][slot] = pos;
+                            big_len[w][slot] = mu;
+                        }
+                    }
+                    if (slot >= kQueued)
+                        for (int32_t y = 0; y < mu; ++y) out[pos + y] = ix.members[src + y];
+                    pos += mu;
                 });
+            __syncwarp();
+            const int nb = big_n[w] < kQueued ? big_n[w] : kQueued;
+            for (int t = 0; t < nb; ++t) {
+                const int64_t src = big_src[w][t], dst = big_dst[w][t];
+                const int32_t len = big_len[w][t];
+                for (int32_t y = lane; y < len; y += 32) out[dst + y] = ix.members[src + y];
+            }
+            __syncwarp();
         }
     }
 }
@@ -1297,12 +1325,11 @@ tcrnet_status deletion_query(const DeletionIndex& ix, const Packed& q, int T, De
 // The network of a repertoire grown by m strings differs from the old one by
 // the rows of the new nodes and by new entries appended to old rows (new ids
 // are larger than every old id, so an old row stays sorted when they are
-// appended in ascending order). Every edge that involves a new string joins it
-// either to an old string (the query of the new strings against the resident
-// index) or to another new string (the network of the new strings alone).
-// The index is grown the same way: a new string equal to a resident distinct
-// string joins its member list; the others become fresh distinct strings whose
-// records are added to the same hash partitions.
+// appended in ascending order). The index is grown first: a new string equal
+// to a resident distinct string joins its member list; the others become
+// fresh distinct strings whose records are added to the same hash partitions.
+// Every edge that involves a new string is then found by the query of the new
+// strings against the grown index (a row lists the string itself as well).
 
 namespace {
 
@@ -1447,24 +1474,65 @@ __global__ void __launch_bounds__(256) k_shifted_copy(const T* __restrict__ src,
     }
 }
 
-// Edges between a fresh distinct string and a resident one: for the
-// representative of each fresh string, every resident distinct string among
-// its query neighbours (all members of a neighbour are listed; its first
-// member stands for it).
-__global__ void k_ins_edges_old(const int64_t* __restrict__ qoff, const int32_t* __restrict__ qcols, int64_t m,
-                                const uint8_t* __restrict__ is_rep, const int32_t* __restrict__ nuid,
-                                const int32_t* __restrict__ uid_old, const int64_t* __restrict__ mem_off_old,
-                                const int32_t* __restrict__ members_old, int2* __restrict__ out,
-                                unsigned long long* __restrict__ cur, int64_t cap, int* __restrict__ err) {
+// Distinct strings that the new strings take: the first new string of each
+// (first[u] = smallest j) represents it.
+__global__ void k_ins_first(const int32_t* __restrict__ nuid, int64_t m, unsigned* __restrict__ first) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < m) atomicMin(&first[nuid[j]], (unsigned)j);
+}
+
+__global__ void k_ins_rep_flags(const int32_t* __restrict__ nuid, int64_t m, const unsigned* __restrict__ first,
+                                int32_t* __restrict__ flag) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < m) flag[j] = first[nuid[j]] == (unsigned)j ? 1 : 0;
+}
+
+// Representatives in new-string order: their strings (the query input), their
+// distinct ids and the row index of each represented distinct string.
+__global__ void k_ins_reps(const int32_t* __restrict__ nuid, int64_t m, const unsigned* __restrict__ first,
+                           const int64_t* __restrict__ rpos, const Canon* __restrict__ qcanon,
+                           const uint8_t* __restrict__ qlen, Canon* __restrict__ rcanon, uint8_t* __restrict__ rlen,
+                           int32_t* __restrict__ rep_u, int32_t* __restrict__ ridx) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int32_t u = nuid[j];
+    if (first[u] != (unsigned)j) return;
+    const int64_t r = rpos[j];
+    store_canon(rcanon + r, load_canon(qcanon + j));
+    rlen[r] = qlen[j];
+    rep_u[r] = u;
+    ridx[u] = (int32_t)r;
+}
+
+// New members of each represented distinct string (new-string ids j).
+__global__ void k_ins_new_members(const int32_t* __restrict__ nuid, int64_t m, const int32_t* __restrict__ ridx,
+                                  const int64_t* __restrict__ nm_off, int32_t* __restrict__ nm_cur,
+                                  int32_t* __restrict__ nm_list, int32_t* __restrict__ nm_cnt, bool place) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int32_t r = ridx[nuid[j]];
+    if (!place) atomicAdd(&nm_cnt[r], 1);
+    else nm_list[nm_off[r] + atomicAdd(&nm_cur[r], 1)] = (int32_t)j;
+}
+
+// Edges between distinct strings that involve a fresh one: for each fresh
+// distinct string w (a row of its closed neighbourhood), every other distinct
+// string x in the row (all members of a neighbour are listed; its first member
+// stands for it); a pair of fresh strings is taken from the smaller id's side.
+__global__ void k_ins_edges(const int64_t* __restrict__ roff, const int32_t* __restrict__ rcols, int64_t nrep,
+                            const int32_t* __restrict__ rep_u, const int32_t* __restrict__ uid,
+                            const int64_t* __restrict__ mem_off, const int32_t* __restrict__ members, int64_t U0,
+                            int2* __restrict__ out, unsigned long long* __restrict__ cur, int64_t cap,
+                            int* __restrict__ err) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < m; j += nw) {
-        if (!is_rep[j]) continue;
-        const int32_t w = nuid[j];
-        for (int64_t e = qoff[j] + lane; e < qoff[j + 1]; e += 32) {
-            const int32_t i = qcols[e];
-            const int32_t x = uid_old[i];
-            if (members_old[mem_off_old[x]] != i) continue;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrep; r += nw) {
+        const int32_t w = rep_u[r];
+        if (w < U0) continue;  // a resident string: its edges are known
+        for (int64_t e = roff[r] + lane; e < roff[r + 1]; e += 32) {
+            const int32_t i = rcols[e];
+            const int32_t x = uid[i];
+            if (x == w || (x >= U0 && x < w) || members[mem_off[x]] != i) continue;
             const unsigned long long slot = atomicAdd(cur, 1ull);
             if ((int64_t)slot < cap) out[slot] = make_int2(w, x);
             else atomicExch(err, 1);
@@ -1472,80 +1540,101 @@ __global__ void k_ins_edges_old(const int64_t* __restrict__ qoff, const int32_t*
     }
 }
 
-// Edges between two fresh distinct strings: pairs of representatives j < k
-// adjacent in the network of the new strings.
-__global__ void k_ins_edges_new(const int64_t* __restrict__ noff, const int32_t* __restrict__ ncols, int64_t m,
-                                const uint8_t* __restrict__ is_rep, const int32_t* __restrict__ nuid,
-                                int2* __restrict__ out, unsigned long long* __restrict__ cur, int64_t cap,
-                                int* __restrict__ err) {
+// New entries of old rows: old node i gains every new member of every
+// represented string whose closed row lists i.
+__global__ void k_ins_delta(const int64_t* __restrict__ roff, const int32_t* __restrict__ rcols, int64_t nrep,
+                            const int32_t* __restrict__ nm_cnt, int64_t n0, int32_t* __restrict__ delta) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < m; j += nw) {
-        if (!is_rep[j]) continue;
-        for (int64_t e = noff[j] + lane; e < noff[j + 1]; e += 32) {
-            const int32_t k = ncols[e];
-            if (k <= j || !is_rep[k]) continue;
-            const unsigned long long slot = atomicAdd(cur, 1ull);
-            if ((int64_t)slot < cap) out[slot] = make_int2(nuid[j], nuid[k]);
-            else atomicExch(err, 1);
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrep; r += nw) {
+        const int32_t c = nm_cnt[r];
+        for (int64_t e = roff[r] + lane; e < roff[r + 1]; e += 32) {
+            const int32_t i = rcols[e];
+            if (i < n0) atomicAdd(&delta[i], c);
         }
     }
 }
 
-// New entries of old rows: delta[i] = number of new strings adjacent to old node i.
-__global__ void k_ins_delta(const int32_t* __restrict__ qcols, int64_t nq, int32_t* __restrict__ delta) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nq; e += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&delta[qcols[e]], 1);
-}
-
-// Degrees of the grown network.
+// Degrees of the grown network: a new node has its closed row minus itself.
 __global__ void k_ins_degree(const int32_t* __restrict__ deg_old, const int32_t* __restrict__ delta, int64_t n0,
-                             const int32_t* __restrict__ qcnt, const int32_t* __restrict__ ndeg, int64_t m,
-                             int32_t* __restrict__ deg) {
+                             const int32_t* __restrict__ nuid, const int32_t* __restrict__ ridx,
+                             const int32_t* __restrict__ rcnt, int64_t m, int32_t* __restrict__ deg) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n0) deg[i] = deg_old[i] + delta[i];
-    else if (i < n0 + m) deg[i] = qcnt[i - n0] + ndeg[i - n0];
+    else if (i < n0 + m) deg[i] = rcnt[ridx[nuid[i - n0]]] - 1;
 }
 
-// Transpose of the query rows: old node i receives n0 + j for every new string
-// j adjacent to it, at a slot of its tail list (sorted afterwards).
-__global__ void k_ins_tails(const int64_t* __restrict__ qoff, const int32_t* __restrict__ qcols, int64_t m,
-                            int64_t n0, const int64_t* __restrict__ toff, int32_t* __restrict__ tcur,
-                            int32_t* __restrict__ tcols) {
+// Tail lists of the old rows: old node i takes n0 + j for the new members j of
+// every closed row that lists it, at slots of its tail (sorted afterwards);
+// trow keeps the row of each slot. Few new members: a lane per row entry;
+// many: the whole warp per entry.
+__global__ void k_ins_tails(const int64_t* __restrict__ roff, const int32_t* __restrict__ rcols, int64_t nrep,
+                            const int64_t* __restrict__ nm_off, const int32_t* __restrict__ nm_list, int64_t n0,
+                            const int64_t* __restrict__ toff, int32_t* __restrict__ tcur, int32_t* __restrict__ tcols,
+                            int32_t* __restrict__ trow) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < m; j += nw)
-        for (int64_t e = qoff[j] + lane; e < qoff[j + 1]; e += 32) {
-            const int32_t i = qcols[e];
-            tcols[toff[i] + atomicAdd(&tcur[i], 1)] = (int32_t)(n0 + j);
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrep; r += nw) {
+        const int64_t a = nm_off[r];
+        const int32_t c = (int32_t)(nm_off[r + 1] - a);
+        const int64_t e0 = roff[r], e1 = roff[r + 1];
+        if (c <= 4) {
+            for (int64_t e = e0 + lane; e < e1; e += 32) {
+                const int32_t i = rcols[e];
+                if (i >= n0) continue;
+                const int64_t base = toff[i] + atomicAdd(&tcur[i], c);
+                for (int32_t k = 0; k < c; ++k) {
+                    tcols[base + k] = (int32_t)(n0 + nm_list[a + k]);
+                    trow[base + k] = i;
+                }
+            }
+        } else {
+            for (int64_t e = e0; e < e1; ++e) {
+                const int32_t i = rcols[e];
+                if (i >= n0) continue;
+                int64_t base = 0;
+                if (lane == 0) base = toff[i] + atomicAdd(&tcur[i], c);
+                base = __shfl_sync(kFull, base, 0);
+                for (int32_t k = lane; k < c; k += 32) {
+                    tcols[base + k] = (int32_t)(n0 + nm_list[a + k]);
+                    trow[base + k] = i;
+                }
+            }
         }
+    }
 }
 
-// Tail lists of the old rows after their old entries.
+// Tail lists of the old rows after their old entries, one thread per entry
+// (a row next to many new strings has a long tail).
 template <typename OffT>
 __global__ void k_ins_fill_tails(const OffT* __restrict__ old_off, const int64_t* __restrict__ new_off,
-                                 const int64_t* __restrict__ toff, const int32_t* __restrict__ tcols, int64_t n0,
-                                 int32_t* __restrict__ cols) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n0) return;
-    const int64_t a = toff[i], b = toff[i + 1];
-    if (a == b) return;
-    int32_t* row = cols + new_off[i] + ((int64_t)old_off[i + 1] - (int64_t)old_off[i]);
-    for (int64_t e = a; e < b; ++e) row[e - a] = tcols[e];
+                                 const int64_t* __restrict__ toff, const int32_t* __restrict__ tcols,
+                                 const int32_t* __restrict__ trow, int64_t n0, int32_t* __restrict__ cols) {
+    const int64_t nt = toff[n0];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nt; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = trow[e];
+        const int64_t at = new_off[i] + ((int64_t)old_off[i + 1] - (int64_t)old_off[i]) + (e - toff[i]);
+        cols[at] = tcols[e];
+    }
 }
 
-// Rows of the new strings: old neighbours (ascending), then new ones.
-__global__ void k_ins_fill_new(const int64_t* __restrict__ qoff, const int32_t* __restrict__ qcols,
-                               const int64_t* __restrict__ noff, const int32_t* __restrict__ ncols, int64_t m,
+// Rows of the new nodes: the closed row of their distinct string (ascending)
+// without the node itself, a warp per node.
+__global__ void k_ins_fill_new(const int64_t* __restrict__ roff, const int32_t* __restrict__ rcols,
+                               const int32_t* __restrict__ nuid, const int32_t* __restrict__ ridx, int64_t m,
                                int64_t n0, const int64_t* __restrict__ new_off, int32_t* __restrict__ cols) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < m; j += nw) {
+        const int32_t self = (int32_t)(n0 + j);
+        const int32_t r = ridx[nuid[j]];
         int32_t* row = cols + new_off[n0 + j];
-        const int64_t q0 = qoff[j], nq = qoff[j + 1] - q0;
-        for (int64_t e = lane; e < nq; e += 32) row[e] = qcols[q0 + e];
-        const int64_t a = noff[j], nn = noff[j + 1] - a;
-        for (int64_t e = lane; e < nn; e += 32) row[nq + e] = (int32_t)(n0 + ncols[a + e]);
+        const int64_t q0 = roff[r], len = roff[r + 1] - q0;
+        for (int64_t e = lane; e < len; e += 32) {
+            const int32_t v = rcols[q0 + e];
+            const int64_t at = e - (v > self ? 1 : 0);
+            if (v != self && at < len - 1) row[at] = v;
+        }
     }
 }
 
@@ -1586,20 +1675,21 @@ tcrnet_status shifted_copy(const T* src, T* dst, int64_t count, const DevBuf& cu
 }
 
 template <typename OffT>
-tcrnet_status csr_merge(const CsrView& g, const OffT* old_off, const int32_t* delta, const int64_t* new_off,
-                        const int64_t* toff, const int32_t* tcols, int64_t nq, const int64_t* qoff,
-                        const int32_t* qcols, const int64_t* noff, const int32_t* ncols, int64_t m, int32_t* cols,
-                        cudaStream_t s, int num_sms) {
+tcrnet_status csr_merge(const CsrView& g, const OffT* old_off, const int32_t* delta, int64_t n_tail,
+                        const int64_t* new_off, const int64_t* toff, const int32_t* tcols, const int32_t* trow,
+                        const int64_t* roff, const int32_t* rcols, const int32_t* nuid, const int32_t* ridx,
+                        int64_t m, int32_t* cols, cudaStream_t s, int num_sms) {
     const int64_t n0 = g.n;
     DevBuf cuts, shifts, pos;
-    TCR_CHECK(growth_cuts<OffT>(delta, old_off, new_off, n0, std::min<int64_t>(n0, nq), cuts, shifts, pos, s));
+    TCR_CHECK(growth_cuts<OffT>(delta, old_off, new_off, n0, std::min<int64_t>(n0, n_tail), cuts, shifts, pos, s));
     TCR_CHECK(shifted_copy<int32_t>(g.cols, cols, g.nnz, cuts, shifts, pos.as<int64_t>() + n0, s, num_sms));
-    if (nq > 0 && n0 > 0) {
-        k_ins_fill_tails<OffT><<<grid_for(n0), kThreads, 0, s>>>(old_off, new_off, toff, tcols, n0, cols);
+    if (n_tail > 0) {
+        k_ins_fill_tails<OffT><<<(unsigned)std::min<int64_t>(grid_for(n_tail), (int64_t)num_sms * 16), kThreads, 0,
+                                 s>>>(old_off, new_off, toff, tcols, trow, n0, cols);
         TCR_LAUNCH_CHECK();
     }
     const unsigned wgrid = (unsigned)std::min<int64_t>(ceil_div(m, kWarps), (int64_t)num_sms * 16);
-    k_ins_fill_new<<<wgrid, kThreads, 0, s>>>(qoff, qcols, noff, ncols, m, n0, new_off, cols);
+    k_ins_fill_new<<<wgrid, kThreads, 0, s>>>(roff, rcols, nuid, ridx, m, n0, new_off, cols);
     TCR_LAUNCH_CHECK();
     return TCRNET_OK;
 }
@@ -1607,22 +1697,16 @@ tcrnet_status csr_merge(const CsrView& g, const OffT* old_off, const int32_t* de
 }  // namespace
 
 tcrnet_status deletion_insert(const DeletionIndex& ix, const CsrView& g, const Packed& q, int T, InsertResult& out,
-                              cudaStream_t s, int num_sms) {
+                              cudaStream_t s, int num_sms, bool profile) {
     const int64_t m = q.n, n0 = g.n, N = n0 + m;
     const int64_t U0 = ix.U, P = ix.P, R0 = ix.R, E0 = ix.E;
     if (!ix.valid() || !ix.uid || ix.n != n0 || m <= 0 || N > kDeletionMaxN || T < 1) return TCRNET_ESTATE;
+    Timer tm(profile, s);
+    const int t0 = tm.mark();
     IndexView v{ix.ucanon, ix.umult, ix.mem_off, ix.members, ix.recs, ix.poff, (uint32_t)P};
 
-    // 1. neighbours of the new strings among the resident nodes, and among
-    //    the new strings themselves
-    DevBuf qoff, qcols, qcnt;
-    int64_t nq = 0;
-    TCR_CHECK(deletion_query(ix, q, T, qoff, qcols, qcnt, &nq, s, num_sms));
-    DeletionResult dn;
-    TCR_CHECK(deletion_build(q, T, dn, s, num_sms, false, 0, false, 0, true));
-    const int64_t nn = dn.nnz;
-
-    // 2. distinct ids of the new strings; fresh distinct strings
+    // 1. distinct ids of the new strings (resident or fresh); ids,
+    //    multiplicities and member lists of the grown repertoire
     DevBuf errb, counters;
     TCR_CHECK(errb.alloc(sizeof(int) * 4, s));
     TCR_CHECK(counters.alloc(sizeof(unsigned long long) * 2, s));  // [0] fresh strings, [1] new edges
@@ -1668,8 +1752,9 @@ tcrnet_status deletion_insert(const DeletionIndex& ix, const CsrView& g, const P
     k_members<<<grid_for(N), kThreads, 0, s>>>(uid.as<int32_t>(), N, mem_off.as<int64_t>(), mcur.as<int32_t>(),
                                                members.as<int32_t>(), mpos.as<int32_t>());
     TCR_LAUNCH_CHECK();
+    const int t1 = tm.mark();
 
-    // 3. records of the fresh strings into the same partitions
+    // 2. records of the fresh strings into the same partitions
     const int64_t R_bound = R0 + m + q.lensum;
     DevBuf pcnt, pscan, poff, recs;
     TCR_CHECK(pcnt.alloc(sizeof(int32_t) * P, s));
@@ -1698,62 +1783,124 @@ tcrnet_status deletion_insert(const DeletionIndex& ix, const CsrView& g, const P
                                                      (uint32_t)P, pcur.as<int32_t>(), poff.as<int64_t>(),
                                                      recs.as<uint64_t>(), (uint32_t)U0);
     TCR_LAUNCH_CHECK();
+    const int t2 = tm.mark();
+
+    // 3. closed rows of the distinct strings that the new strings take (each
+    //    once, by its first new string): their query against the grown index
+    DevBuf first, rflag, rpos;
+    TCR_CHECK(first.alloc(sizeof(unsigned) * N, s));  // indexed by distinct id (< N)
+    TCR_CHECK(rflag.alloc(sizeof(int32_t) * m, s));
+    TCR_CHECK(rpos.alloc(sizeof(int64_t) * (m + 1), s));
+    TCR_CUDA(cudaMemsetAsync(first.as<void>(), 0xff, sizeof(unsigned) * N, s));
+    k_ins_first<<<grid_for(m), kThreads, 0, s>>>(nuid.as<int32_t>(), m, first.as<unsigned>());
+    TCR_LAUNCH_CHECK();
+    k_ins_rep_flags<<<grid_for(m), kThreads, 0, s>>>(nuid.as<int32_t>(), m, first.as<unsigned>(),
+                                                     rflag.as<int32_t>());
+    TCR_LAUNCH_CHECK();
+    TCR_CHECK(scan_exclusive_i32_to_i64(rflag.as<int32_t>(), rpos.as<int64_t>(), m, s));
+    int64_t nrep = 0;
+    TCR_CUDA(cudaMemcpyAsync(&nrep, rpos.as<int64_t>() + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaStreamSynchronize(s));
+    if (nrep <= 0 || nrep > m) return TCRNET_EDEVICE;
+    Packed qr;  // the representatives' strings, input order
+    qr.n = nrep;
+    DevBuf rep_u, ridx, nm_cnt, nm_off, nm_cur, nm_list;
+    TCR_CHECK(qr.canon_in.alloc(sizeof(Canon) * nrep, s));
+    TCR_CHECK(qr.lens.alloc(nrep, s));
+    TCR_CHECK(rep_u.alloc(sizeof(int32_t) * nrep, s));
+    TCR_CHECK(ridx.alloc(sizeof(int32_t) * N, s));
+    TCR_CHECK(nm_cnt.alloc(sizeof(int32_t) * nrep, s));
+    TCR_CHECK(nm_off.alloc(sizeof(int64_t) * (nrep + 1), s));
+    TCR_CHECK(nm_cur.alloc(sizeof(int32_t) * nrep, s));
+    TCR_CHECK(nm_list.alloc(sizeof(int32_t) * m, s));
+    k_ins_reps<<<grid_for(m), kThreads, 0, s>>>(nuid.as<int32_t>(), m, first.as<unsigned>(), rpos.as<int64_t>(),
+                                                q.canon_in.as<Canon>(), q.lens.as<uint8_t>(), qr.canon_in.as<Canon>(),
+                                                qr.lens.as<uint8_t>(), rep_u.as<int32_t>(), ridx.as<int32_t>());
+    TCR_LAUNCH_CHECK();
+    TCR_CUDA(cudaMemsetAsync(nm_cnt.as<void>(), 0, sizeof(int32_t) * nrep, s));
+    TCR_CUDA(cudaMemsetAsync(nm_cur.as<void>(), 0, sizeof(int32_t) * nrep, s));
+    k_ins_new_members<<<grid_for(m), kThreads, 0, s>>>(nuid.as<int32_t>(), m, ridx.as<int32_t>(), nullptr, nullptr,
+                                                       nullptr, nm_cnt.as<int32_t>(), false);
+    TCR_LAUNCH_CHECK();
+    TCR_CHECK(scan_exclusive_i32_to_i64(nm_cnt.as<int32_t>(), nm_off.as<int64_t>(), nrep, s));
+    k_ins_new_members<<<grid_for(m), kThreads, 0, s>>>(nuid.as<int32_t>(), m, ridx.as<int32_t>(),
+                                                       nm_off.as<int64_t>(), nm_cur.as<int32_t>(),
+                                                       nm_list.as<int32_t>(), nullptr, true);
+    TCR_LAUNCH_CHECK();
+    DeletionIndex gx;  // a view of the grown index (not owned)
+    gx.ucanon = ucanon.as<Canon>();
+    gx.umult = umult.as<int32_t>();
+    gx.mem_off = mem_off.as<int64_t>();
+    gx.members = members.as<int32_t>();
+    gx.recs = recs.as<uint64_t>();
+    gx.poff = poff.as<int64_t>();
+    gx.P = P;
+    gx.n = N;
+    DevBuf roff, rcols, rcnt;  // closed rows: every member of every neighbour, the string's own included
+    int64_t nr = 0;
+    TCR_CHECK(deletion_query(gx, qr, T, roff, rcols, rcnt, &nr, s, num_sms));
+    const int t3 = tm.mark();
 
     // 4. edges between distinct strings: the resident ones, then those of the
-    //    fresh strings (to resident strings, to each other)
-    const int64_t E_cap = E0 + nq + nn;
+    //    fresh strings
+    const int64_t E_cap = E0 + nr;
     DevBuf uedges;
     TCR_CHECK(uedges.alloc_owned(sizeof(int2) * (E_cap > 0 ? E_cap : 1), s));
     if (E0 > 0)
         TCR_CUDA(cudaMemcpyAsync(uedges.as<void>(), ix.uedges, sizeof(int2) * E0, cudaMemcpyDeviceToDevice, s));
-    const unsigned wgrid = (unsigned)std::min<int64_t>(ceil_div(m, kWarps), (int64_t)num_sms * 16);
-    k_ins_edges_old<<<wgrid, kThreads, 0, s>>>(qoff.as<int64_t>(), qcols.as<int32_t>(), m, is_rep.as<uint8_t>(),
-                                               nuid.as<int32_t>(), ix.uid, ix.mem_off, ix.members,
-                                               uedges.as<int2>() + E0, d_ecur, E_cap - E0, d_err + 1);
+    const unsigned rgrid = (unsigned)std::min<int64_t>(ceil_div(nrep, kWarps), (int64_t)num_sms * 16);
+    k_ins_edges<<<rgrid, kThreads, 0, s>>>(roff.as<int64_t>(), rcols.as<int32_t>(), nrep, rep_u.as<int32_t>(),
+                                           uid.as<int32_t>(), mem_off.as<int64_t>(), members.as<int32_t>(), U0,
+                                           uedges.as<int2>() + E0, d_ecur, E_cap - E0, d_err + 1);
     TCR_LAUNCH_CHECK();
-    k_ins_edges_new<<<wgrid, kThreads, 0, s>>>(dn.off64.as<int64_t>(), dn.cols.as<int32_t>(), m,
-                                               is_rep.as<uint8_t>(), nuid.as<int32_t>(), uedges.as<int2>() + E0,
-                                               d_ecur, E_cap - E0, d_err + 1);
-    TCR_LAUNCH_CHECK();
+    const int t4 = tm.mark();
 
-    // 5. the grown CSR: degrees, offsets, old rows moved with their tails, new rows
-    DevBuf delta, deg, off64, toff, tcur, tcols, cols;
-    TCR_CHECK(delta.alloc(sizeof(int32_t) * (n0 > 0 ? n0 : 1), s));
+    // 5. the grown CSR: old rows gain tails, new rows are the closed rows of
+    //    their strings without themselves
+    DevBuf delta, deg, off64, toff, tcur, tcols, trow, cols;
+    TCR_CHECK(delta.alloc(sizeof(int32_t) * n0, s));
+    TCR_CHECK(toff.alloc(sizeof(int64_t) * (n0 + 1), s));
+    TCR_CHECK(tcur.alloc(sizeof(int32_t) * n0, s));
     TCR_CHECK(deg.alloc_owned(sizeof(int32_t) * N, s));
     TCR_CHECK(off64.alloc_owned(sizeof(int64_t) * (N + 1), s));
-    TCR_CHECK(toff.alloc(sizeof(int64_t) * (n0 + 1), s));
-    TCR_CHECK(tcur.alloc(sizeof(int32_t) * (n0 > 0 ? n0 : 1), s));
-    TCR_CHECK(tcols.alloc(sizeof(int32_t) * (nq > 0 ? nq : 1), s));
-    const int64_t nnz = g.nnz + 2 * nq + nn;
-    TCR_CHECK(cols.alloc_owned(sizeof(int32_t) * nnz, s));
     TCR_CUDA(cudaMemsetAsync(delta.as<void>(), 0, sizeof(int32_t) * n0, s));
     TCR_CUDA(cudaMemsetAsync(tcur.as<void>(), 0, sizeof(int32_t) * n0, s));
-    if (nq > 0) {
-        k_ins_delta<<<(unsigned)std::min<int64_t>(grid_for(nq), (int64_t)num_sms * 16), kThreads, 0, s>>>(
-            qcols.as<int32_t>(), nq, delta.as<int32_t>());
-        TCR_LAUNCH_CHECK();
-    }
-    k_ins_degree<<<grid_for(N), kThreads, 0, s>>>(g.degree, delta.as<int32_t>(), n0, qcnt.as<int32_t>(),
-                                                  dn.degree.as<int32_t>(), m, deg.as<int32_t>());
+    k_ins_delta<<<rgrid, kThreads, 0, s>>>(roff.as<int64_t>(), rcols.as<int32_t>(), nrep, nm_cnt.as<int32_t>(), n0,
+                                           delta.as<int32_t>());
+    TCR_LAUNCH_CHECK();
+    TCR_CHECK(scan_exclusive_i32_to_i64(delta.as<int32_t>(), toff.as<int64_t>(), n0, s));
+    k_ins_degree<<<grid_for(N), kThreads, 0, s>>>(g.degree, delta.as<int32_t>(), n0, nuid.as<int32_t>(),
+                                                  ridx.as<int32_t>(), rcnt.as<int32_t>(), m, deg.as<int32_t>());
     TCR_LAUNCH_CHECK();
     TCR_CHECK(scan_exclusive_i32_to_i64(deg.as<int32_t>(), off64.as<int64_t>(), N, s));
-    TCR_CHECK(scan_exclusive_i32_to_i64(delta.as<int32_t>(), toff.as<int64_t>(), n0, s));
-    if (nq > 0) {
-        k_ins_tails<<<wgrid, kThreads, 0, s>>>(qoff.as<int64_t>(), qcols.as<int32_t>(), m, n0, toff.as<int64_t>(),
-                                               tcur.as<int32_t>(), tcols.as<int32_t>());
+    int64_t sizes[2] = {0, 0};  // new entries of old rows, entries of the grown network
+    TCR_CUDA(cudaMemcpyAsync(&sizes[0], toff.as<int64_t>() + n0, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaMemcpyAsync(&sizes[1], off64.as<int64_t>() + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaStreamSynchronize(s));
+    const int64_t n_tail = sizes[0], nnz = sizes[1];
+    if (n_tail < 0 || nnz < g.nnz + n_tail) return TCRNET_EDEVICE;
+    TCR_CHECK(tcols.alloc(sizeof(int32_t) * (n_tail > 0 ? n_tail : 1), s));
+    TCR_CHECK(trow.alloc(sizeof(int32_t) * (n_tail > 0 ? n_tail : 1), s));
+    TCR_CHECK(cols.alloc_owned(sizeof(int32_t) * nnz, s));
+    if (n_tail > 0) {
+        k_ins_tails<<<rgrid, kThreads, 0, s>>>(roff.as<int64_t>(), rcols.as<int32_t>(), nrep, nm_off.as<int64_t>(),
+                                               nm_list.as<int32_t>(), n0, toff.as<int64_t>(), tcur.as<int32_t>(),
+                                               tcols.as<int32_t>(), trow.as<int32_t>());
         TCR_LAUNCH_CHECK();
         TCR_CHECK(sort_rows(toff.as<int64_t>(), tcols.as<int32_t>(), n0, s, num_sms));
     }
+    const int t5 = tm.mark();
     if (g.off64)
-        TCR_CHECK(csr_merge<int64_t>(g, static_cast<const int64_t*>(g.offsets), delta.as<int32_t>(),
-                                     off64.as<int64_t>(), toff.as<int64_t>(), tcols.as<int32_t>(), nq,
-                                     qoff.as<int64_t>(), qcols.as<int32_t>(), dn.off64.as<int64_t>(),
-                                     dn.cols.as<int32_t>(), m, cols.as<int32_t>(), s, num_sms));
+        TCR_CHECK(csr_merge<int64_t>(g, static_cast<const int64_t*>(g.offsets), delta.as<int32_t>(), n_tail,
+                                     off64.as<int64_t>(), toff.as<int64_t>(), tcols.as<int32_t>(),
+                                     trow.as<int32_t>(), roff.as<int64_t>(), rcols.as<int32_t>(),
+                                     nuid.as<int32_t>(), ridx.as<int32_t>(), m, cols.as<int32_t>(), s, num_sms));
     else
-        TCR_CHECK(csr_merge<int32_t>(g, static_cast<const int32_t*>(g.offsets), delta.as<int32_t>(),
-                                     off64.as<int64_t>(), toff.as<int64_t>(), tcols.as<int32_t>(), nq,
-                                     qoff.as<int64_t>(), qcols.as<int32_t>(), dn.off64.as<int64_t>(),
-                                     dn.cols.as<int32_t>(), m, cols.as<int32_t>(), s, num_sms));
+        TCR_CHECK(csr_merge<int32_t>(g, static_cast<const int32_t*>(g.offsets), delta.as<int32_t>(), n_tail,
+                                     off64.as<int64_t>(), toff.as<int64_t>(), tcols.as<int32_t>(),
+                                     trow.as<int32_t>(), roff.as<int64_t>(), rcols.as<int32_t>(),
+                                     nuid.as<int32_t>(), ridx.as<int32_t>(), m, cols.as<int32_t>(), s, num_sms));
+    const int t6 = tm.mark();
 
     // 6. sizes and error flags
     unsigned long long h_cnt[2] = {0, 0};
@@ -1785,6 +1932,14 @@ tcrnet_status deletion_insert(const DeletionIndex& ix, const CsrView& g, const P
     out.index.R = h_R;
     out.index.n = N;
     out.index.E = E0 + out.new_edges;
+    out.ms_phase[0] = tm.ms(t0, t1);  // distinct ids, multiplicities, member lists
+    out.ms_phase[1] = tm.ms(t1, t2);  // records
+    out.ms_phase[2] = tm.ms(t2, t3);  // closed rows (query of the represented strings)
+    out.ms_phase[3] = tm.ms(t3, t4);  // edges between distinct strings
+    out.ms_phase[4] = tm.ms(t4, t5);  // degrees, offsets, tail lists
+    out.ms_phase[5] = tm.ms(t5, t6);  // grown CSR (shifted copy, tails, new rows)
+    out.ms_phase[6] = 0.0;
+    out.ms_phase[7] = tm.ms(t0, t6);
     return TCRNET_OK;
 }
 

@@ -74,16 +74,19 @@ struct InsertResult {
     int64_t fresh = 0;      // new distinct strings
     int64_t new_edges = 0;  // new edges between distinct strings
     DeletionIndex index;    // index of the grown repertoire; the caller owns it
+    // with profiling: ids and members, records, query, distinct edges,
+    // degrees and tails, grown CSR, unused, total (ms)
+    double ms_phase[8] = {0};
 };
 
 // Network and index of a deletion build's repertoire (ix, g: n0 strings,
 // l_max = T >= 1) grown by the m strings of q (input order, not bucketed), as
-// nodes n0 .. n0+m-1, merged instead of rebuilt: the rows of the new strings
-// come from their query against ix and from the network of the new strings
-// alone; old rows gain the new neighbours at their ends; the index gains the
-// new distinct strings and their records in the same partitions. ix and g are
-// only read. The CSR equals that of a fresh build of the concatenation.
+// nodes n0 .. n0+m-1, merged instead of rebuilt: the index gains the new
+// distinct strings and their records in the same partitions; the new strings'
+// query against the grown index gives their rows (without themselves); old
+// rows gain the new neighbours at their ends. ix and g are only read. The CSR
+// equals that of a fresh build of the concatenation.
 tcrnet_status deletion_insert(const DeletionIndex& ix, const CsrView& g, const Packed& q, int T, InsertResult& out,
-                              cudaStream_t s, int num_sms);
+                              cudaStream_t s, int num_sms, bool profile = false);
 
 }  // namespace tcr
