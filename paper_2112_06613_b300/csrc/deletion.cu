@@ -1198,84 +1198,138 @@ struct IndexView {
     uint32_t P;
 };
 
-// Neighbours of query string q among the distinct resident strings, found
-// through q's own records (full string and every deletion) in the resident
-// partitions; each match is confirmed by content and each neighbour is found
-// exactly once (see the file comment; an identical resident string matches
-// full-to-full only, its deletion matches are skipped). Calls emit(u).
-template <typename Emit>
-__device__ __forceinline__ int64_t query_record(const IndexView& ix, const Canon& qc, int Lq, int p, int T,
-                                                Emit emit) {
-    const bool full = p < 0;
-    const Canon cq = full ? qc : delete_at(qc, p);
-    const bool q_rs = !full && run_start(qc, p);
-    if (!full && T < 1) return 0;
-    const uint64_t h = hash_canon(cq);
-    const uint32_t h32 = (uint32_t)h;
-    const uint32_t pid = part_of(h, ix.P);
-    const int64_t b0 = ix.poff[pid], b1 = ix.poff[pid + 1];
-    int64_t cnt = 0;
-    for (int64_t k = b0; k < b1; ++k) {
-        const uint64_t r = ix.recs[k];
-        if ((uint32_t)(r >> 32) != h32) continue;
-        const uint32_t rp = rec_p(r);
-        bool cand;
-        if (full) cand = (rp == kTagF) || (T >= 1 && rec_runstart(r));   // identical / q one shorter
-        else cand = (rp == kTagF) ? q_rs : (rp == (uint32_t)p);           // q one longer / one substitution
-        if (!cand) continue;
-        if (!canon_eq(cq, record_content(r, ix.ucanon))) continue;       // hash collision
-        const uint32_t u = rec_u(r);
-        if (!full && rp != kTagF && canon_eq(qc, load_canon(ix.ucanon + u))) continue;  // identical: counted once
-        emit(u);
-        ++cnt;
-    }
-    return cnt;
-}
-
+// Neighbours of a query string among the distinct resident strings, found
+// through the string's own records (full string and every deletion) in the
+// resident partitions; each match is confirmed by content and each neighbour is
+// found exactly once (see the file comment; an identical resident string
+// matches full-to-full only, its deletion matches are skipped).
+//
+// A warp takes one query string. Lane v computes the key of variant g0 + v
+// (-1: the full string) and its partition; the words of the (up to 32)
+// partitions are then read as one flat sequence, 32 consecutive words per
+// step, each lane finding the variant that owns its word by a binary search
+// over the partition sizes' prefix sums. COUNT adds the multiplicities of the
+// matches; WRITE emits their member lists at qoff[q] onwards (a lane copies
+// short lists itself, long ones are queued and copied by the whole warp).
 template <bool WRITE>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
 k_query(IndexView ix, const Canon* __restrict__ qcanon, const uint8_t* __restrict__ qlen, int64_t m, int T,
-        int64_t* __restrict__ qcount, const int64_t* __restrict__ qoff, int32_t* __restrict__ out) {
+        int64_t* __restrict__ qcount, const int64_t* __restrict__ qoff, int32_t* __restrict__ out,
+        int2* __restrict__ hits, unsigned long long* __restrict__ hit_cur, int64_t hit_cap) {
+    constexpr int kLaneCopyMax = 8, kQueued = 16;
+    __shared__ int64_t big_src[kWarps][kQueued], big_dst[kWarps][kQueued];
+    __shared__ int32_t big_len[kWarps][kQueued];
+    __shared__ int big_n[kWarps];
     const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
     const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < m; q += stride) {
         const Canon qc = load_canon(qcanon + q);
         const int Lq = qlen[q];
-        int64_t mine = 0;  // members this lane contributes
-        for (int p = lane - 1; p < Lq; p += 32)
-            query_record(ix, qc, Lq, p, T, [&](uint32_t u) { mine += ix.umult[u]; });
-        int64_t excl;
-        const int64_t total = warp_scan(mine, excl, lane);
-        if constexpr (!WRITE) {
-            if (lane == 0) qcount[q] = total;
-        } else {
-            // a lane copies short member lists itself and queues long ones
-            // (strings with many copies), which the whole warp copies after
-            constexpr int kLaneCopyMax = 8, kQueued = 16;
-            __shared__ int64_t big_src[kWarps][kQueued], big_dst[kWarps][kQueued];
-            __shared__ int32_t big_len[kWarps][kQueued];
-            __shared__ int big_n[kWarps];
-            const int w = threadIdx.x >> 5;
+        int64_t mine = 0;                           // COUNT: members found by this lane
+        int64_t base = WRITE ? qoff[q] : 0;         // WRITE: next output slot (warp-uniform)
+        if constexpr (WRITE) {
             if (lane == 0) big_n[w] = 0;
             __syncwarp();
-            int64_t pos = qoff[q] + excl;
-            for (int p = lane - 1; p < Lq; p += 32)
-                query_record(ix, qc, Lq, p, T, [&](uint32_t u) {
-                    const int64_t src = ix.mem_off[u];
-                    const int32_t mu = ix.umult[u];
-                    int slot = kQueued;
-                    if (mu > kLaneCopyMax) {
-                        slot = atomicAdd(&big_n[w], 1);
-                        if (slot < kQueued) {
-                            big_src[w][slot] = src;
-                            big_dst[w][slot] = pos;
-                            big_len[w][slot] = mu;
+        }
+        const int last = T >= 1 ? Lq - 1 : -1;      // l_max = 0: the full string only
+        for (int g0 = -1; g0 <= last; g0 += 32) {
+            const int p = g0 + lane;
+            const bool active = p <= last;
+            uint32_t h32 = 0;
+            int64_t b0 = 0;
+            int32_t sz = 0;  // partition sizes and their sums fit 32 bits
+            bool q_rs = false;
+            if (active) {
+                const Canon cq = p < 0 ? qc : delete_at(qc, p);
+                q_rs = p >= 0 && run_start(qc, p);
+                const uint64_t h = hash_canon(cq);
+                h32 = (uint32_t)h;
+                const uint32_t pid = part_of(h, ix.P);
+                b0 = ix.poff[pid];
+                sz = (int32_t)(ix.poff[pid + 1] - b0);
+            }
+            int32_t excl = sz;  // inclusive, then exclusive prefix sum over the lanes
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int32_t y = __shfl_up_sync(kFull, excl, d);
+                if (lane >= d) excl += y;
+            }
+            const int32_t S = __shfl_sync(kFull, excl, 31);
+            excl -= sz;
+            const int64_t rb = b0 - excl;  // word f of this lane's partition is recs[rb + f]
+            for (int32_t f0 = 0; f0 < S; f0 += 32) {
+                const int32_t f = f0 + lane;
+                int v = 0;  // owner: the last variant whose words start at or before f
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int32_t e = __shfl_sync(kFull, excl, v + step);
+                    if (e <= f) v += step;
+                }
+                const int64_t vrb = __shfl_sync(kFull, rb, v);
+                const uint32_t vh = __shfl_sync(kFull, h32, v);
+                const bool vq_rs = __shfl_sync(kFull, q_rs, v);
+                const int vp = g0 + v;
+                bool hit = false;
+                uint32_t u = 0;
+                if (f < S) {
+                    const uint64_t r = ix.recs[vrb + f];
+                    if ((uint32_t)(r >> 32) == vh) {
+                        const uint32_t rp = rec_p(r);
+                        const bool full = vp < 0;
+                        if (full) hit = (rp == kTagF) || (T >= 1 && rec_runstart(r));  // identical / q one shorter
+                        else hit = (rp == kTagF) ? vq_rs : (rp == (uint32_t)vp);       // q one longer / substitution
+                        if (hit) {
+                            const Canon cq = full ? qc : delete_at(qc, vp);
+                            hit = canon_eq(cq, record_content(r, ix.ucanon));          // hash collision
+                        }
+                        if (hit) {
+                            u = rec_u(r);
+                            if (!full && rp != kTagF && canon_eq(qc, load_canon(ix.ucanon + u)))
+                                hit = false;  // identical: counted once, full-to-full
                         }
                     }
-                    if (slot >= kQueued)
-                        for (int32_t y = 0; y < mu; ++y) out[pos + y] = ix.members[src + y];
-                    pos += mu;
-                });
+                }
+                const int32_t mu = hit ? ix.umult[u] : 0;
+                if constexpr (!WRITE) {
+                    mine += mu;
+                    // keep the match (query, distinct string) for the emit pass
+                    const unsigned hm = __ballot_sync(kFull, hit);
+                    if (hm && hits) {
+                        unsigned long long hb = 0;
+                        if (lane == 0) hb = atomicAdd(hit_cur, (unsigned long long)__popc(hm));
+                        hb = __shfl_sync(kFull, hb, 0);
+                        const int64_t slot = (int64_t)hb + __popc(hm & ((1u << lane) - 1u));
+                        if (hit && slot < hit_cap) hits[slot] = make_int2((int32_t)q, (int32_t)u);
+                    }
+                } else {
+                    if (!__any_sync(kFull, hit)) continue;
+                    int64_t ex;
+                    const int64_t tot = warp_scan((int64_t)mu, ex, lane);
+                    if (hit) {
+                        const int64_t src = ix.mem_off[u];
+                        const int64_t pos = base + ex;
+                        int slot = kQueued;
+                        if (mu > kLaneCopyMax) {
+                            slot = atomicAdd(&big_n[w], 1);
+                            if (slot < kQueued) {
+                                big_src[w][slot] = src;
+                                big_dst[w][slot] = pos;
+                                big_len[w][slot] = mu;
+                            }
+                        }
+                        if (slot >= kQueued)
+                            for (int32_t y = 0; y < mu; ++y) out[pos + y] = ix.members[src + y];
+                    }
+                    base += tot;
+                }
+            }
+        }
+        if constexpr (!WRITE) {
+            int64_t ex;
+            const int64_t total = warp_scan(mine, ex, lane);
+            if (lane == 0) qcount[q] = total;
+        } else {
             __syncwarp();
             const int nb = big_n[w] < kQueued ? big_n[w] : kQueued;
             for (int t = 0; t < nb; ++t) {
@@ -1284,6 +1338,38 @@ k_query(IndexView ix, const Canon* __restrict__ qcanon, const uint8_t* __restric
                 for (int32_t y = lane; y < len; y += 32) out[dst + y] = ix.members[src + y];
             }
             __syncwarp();
+        }
+    }
+}
+
+// Emit pass over the matches kept by the count pass: the member list of u at
+// qoff[q] + a slot taken from the query's cursor (rows are sorted afterwards).
+// Short lists are copied by their lane, long ones by the whole warp.
+__global__ void __launch_bounds__(kThreads)
+k_query_emit(IndexView ix, const int2* __restrict__ hits, int64_t nh, const int64_t* __restrict__ qoff,
+             int32_t* __restrict__ qcur, int32_t* __restrict__ out) {
+    constexpr int kLaneCopyMax = 8;
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t h0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; h0 < nh; h0 += nw * 32) {
+        const int64_t k = h0 + lane;
+        int64_t src = 0, pos = 0;
+        int32_t mu = 0;
+        if (k < nh) {
+            const int2 hq = hits[k];
+            src = ix.mem_off[hq.y];
+            mu = ix.umult[hq.y];
+            pos = qoff[hq.x] + atomicAdd(&qcur[hq.x], mu);
+            if (mu <= kLaneCopyMax)
+                for (int32_t y = 0; y < mu; ++y) out[pos + y] = ix.members[src + y];
+        }
+        unsigned todo = __ballot_sync(kFull, mu > kLaneCopyMax);
+        while (todo) {
+            const int j = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t js = __shfl_sync(kFull, src, j), jp = __shfl_sync(kFull, pos, j);
+            const int32_t jm = __shfl_sync(kFull, mu, j);
+            for (int32_t y = lane; y < jm; y += 32) out[jp + y] = ix.members[js + y];
         }
     }
 }
@@ -1300,18 +1386,43 @@ tcrnet_status deletion_query(const DeletionIndex& ix, const Packed& q, int T, De
     TCR_CHECK(qcnt.alloc(sizeof(int64_t) * m, s));
     TCR_CHECK(off64.alloc_owned(sizeof(int64_t) * (m + 1), s));
     const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(m, kWarps), (int64_t)num_sms * 32);
+    // the count pass keeps its matches (up to kHitsPerQuery per query on
+    // average); when they all fit, an emit pass over them replaces the second
+    // scan of the partitions
+    constexpr int64_t kHitsPerQuery = 64;
+    const int64_t hit_cap = std::max<int64_t>(1 << 16, std::min<int64_t>(kHitsPerQuery * m, 1LL << 27));
+    DevBuf hitbuf, hitcur;
+    int2* hits = nullptr;
+    if (hitbuf.alloc(sizeof(int2) * hit_cap, s) == TCRNET_OK &&
+        hitcur.alloc(sizeof(unsigned long long), s) == TCRNET_OK) {
+        TCR_CUDA(cudaMemsetAsync(hitcur.as<void>(), 0, sizeof(unsigned long long), s));
+        hits = hitbuf.as<int2>();
+    }
     k_query<false><<<grid, kThreads, 0, s>>>(v, q.canon_in.as<Canon>(), q.lens.as<uint8_t>(), m, T,
-                                             qcnt.as<int64_t>(), nullptr, nullptr);
+                                             qcnt.as<int64_t>(), nullptr, nullptr, hits,
+                                             hits ? hitcur.as<unsigned long long>() : nullptr, hit_cap);
     TCR_LAUNCH_CHECK();
     TCR_CHECK(scan_exclusive_i64(qcnt.as<int64_t>(), off64.as<int64_t>(), m, s));
     int64_t nnz = 0;
+    unsigned long long nh = ~0ull;
     TCR_CUDA(cudaMemcpyAsync(&nnz, off64.as<int64_t>() + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    if (hits) TCR_CUDA(cudaMemcpyAsync(&nh, hitcur.as<void>(), sizeof(nh), cudaMemcpyDeviceToHost, s));
     TCR_CUDA(cudaStreamSynchronize(s));
     TCR_CHECK(cols.alloc_owned(sizeof(int32_t) * nnz, s));
     TCR_CHECK(count.alloc_owned(sizeof(int32_t) * m, s));
     if (nnz > 0) {
-        k_query<true><<<grid, kThreads, 0, s>>>(v, q.canon_in.as<Canon>(), q.lens.as<uint8_t>(), m, T, nullptr,
-                                                off64.as<int64_t>(), cols.as<int32_t>());
+        if (hits && (int64_t)nh <= hit_cap) {
+            DevBuf qcur;
+            TCR_CHECK(qcur.alloc(sizeof(int32_t) * m, s));
+            TCR_CUDA(cudaMemsetAsync(qcur.as<void>(), 0, sizeof(int32_t) * m, s));
+            const unsigned egrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)nh, kThreads),
+                                                                                     (int64_t)num_sms * 16));
+            k_query_emit<<<egrid, kThreads, 0, s>>>(v, hits, (int64_t)nh, off64.as<int64_t>(), qcur.as<int32_t>(),
+                                                    cols.as<int32_t>());
+        } else {
+            k_query<true><<<grid, kThreads, 0, s>>>(v, q.canon_in.as<Canon>(), q.lens.as<uint8_t>(), m, T, nullptr,
+                                                    off64.as<int64_t>(), cols.as<int32_t>(), nullptr, nullptr, 0);
+        }
         TCR_LAUNCH_CHECK();
         TCR_CHECK(sort_rows(off64.as<int64_t>(), cols.as<int32_t>(), m, s, num_sms));
     }
@@ -1663,13 +1774,40 @@ tcrnet_status growth_cuts(const int32_t* grow, const OffT* old_off, const int64_
     return TCRNET_OK;
 }
 
+// The same copy when the cuts are dense (short pieces): a warp per piece
+// k = [cuts[k-1], cuts[k]) (piece 0 from 0, piece K to count).
+template <typename T>
+__global__ void k_piece_copy(const T* __restrict__ src, T* __restrict__ dst, int64_t count,
+                             const int64_t* __restrict__ cuts, const int64_t* __restrict__ shifts,
+                             const int64_t* __restrict__ K_ptr) {
+    const int lane = threadIdx.x & 31;
+    const int64_t K = *K_ptr;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k <= K; k += nw) {
+        const int64_t a = k == 0 ? 0 : cuts[k - 1];
+        const int64_t b = k == K ? count : cuts[k];
+        const int64_t sh = shifts[k];
+        for (int64_t t = a + lane; t < b; t += 32) dst[t + sh] = src[t];
+    }
+}
+
+// max_cuts bounds the number of cuts: many short pieces take the warp-per-piece
+// copy, few long ones the block-range copy.
 template <typename T>
 tcrnet_status shifted_copy(const T* src, T* dst, int64_t count, const DevBuf& cuts, const DevBuf& shifts,
-                           const int64_t* K_dev, cudaStream_t s, int num_sms) {
+                           const int64_t* K_dev, int64_t max_cuts, cudaStream_t s, int num_sms) {
     if (count <= 0) return TCRNET_OK;
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(count, 256 * 16), (int64_t)num_sms * 8));
-    k_shifted_copy<T><<<(unsigned)blocks, 256, 0, s>>>(src, dst, count, cuts.as<int64_t>(), shifts.as<int64_t>(),
-                                                       K_dev);
+    if (max_cuts > 0 && count / max_cuts < 256) {
+        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(max_cuts + 1, kWarps),
+                                                                       (int64_t)num_sms * 16));
+        k_piece_copy<T><<<(unsigned)blocks, kThreads, 0, s>>>(src, dst, count, cuts.as<int64_t>(),
+                                                              shifts.as<int64_t>(), K_dev);
+    } else {
+        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(count, 256 * 16),
+                                                                       (int64_t)num_sms * 8));
+        k_shifted_copy<T><<<(unsigned)blocks, 256, 0, s>>>(src, dst, count, cuts.as<int64_t>(),
+                                                           shifts.as<int64_t>(), K_dev);
+    }
     TCR_LAUNCH_CHECK();
     return TCRNET_OK;
 }
@@ -1682,7 +1820,8 @@ tcrnet_status csr_merge(const CsrView& g, const OffT* old_off, const int32_t* de
     const int64_t n0 = g.n;
     DevBuf cuts, shifts, pos;
     TCR_CHECK(growth_cuts<OffT>(delta, old_off, new_off, n0, std::min<int64_t>(n0, n_tail), cuts, shifts, pos, s));
-    TCR_CHECK(shifted_copy<int32_t>(g.cols, cols, g.nnz, cuts, shifts, pos.as<int64_t>() + n0, s, num_sms));
+    TCR_CHECK(shifted_copy<int32_t>(g.cols, cols, g.nnz, cuts, shifts, pos.as<int64_t>() + n0,
+                                    std::min<int64_t>(n0, n_tail), s, num_sms));
     if (n_tail > 0) {
         k_ins_fill_tails<OffT><<<(unsigned)std::min<int64_t>(grid_for(n_tail), (int64_t)num_sms * 16), kThreads, 0,
                                  s>>>(old_off, new_off, toff, tcols, trow, n0, cols);
@@ -1776,8 +1915,8 @@ tcrnet_status deletion_insert(const DeletionIndex& ix, const CsrView& g, const P
         DevBuf cuts, shifts, pos;
         TCR_CHECK(growth_cuts<int64_t>(pcnt.as<int32_t>(), ix.poff, poff.as<int64_t>(), P,
                                        std::min<int64_t>(P, m + q.lensum), cuts, shifts, pos, s));
-        TCR_CHECK(shifted_copy<uint64_t>(ix.recs, recs.as<uint64_t>(), R0, cuts, shifts, pos.as<int64_t>() + P, s,
-                                         num_sms));
+        TCR_CHECK(shifted_copy<uint64_t>(ix.recs, recs.as<uint64_t>(), R0, cuts, shifts, pos.as<int64_t>() + P,
+                                         std::min<int64_t>(P, m + q.lensum), s, num_sms));
     }
     k_records<true><<<grid_for(m), kThreads, 0, s>>>(ucanon.as<Canon>() + U0, flen.as<uint8_t>(), d_F, m,
                                                      (uint32_t)P, pcur.as<int32_t>(), poff.as<int64_t>(),
