@@ -284,12 +284,13 @@ def serve_leg(args, tn, torch, stream):
     arrivals (200/s) of queries (90%, log-uniform 1..50,000 strings) and inserts
     (10%, log-uniform 1,000..100,000 strings) for args.serve_seconds."""
     from paper_2112_06613_b300.serving import ServingEngine, latency_summary
-    from synthgen import generate_config2
+    from synthgen import generate, generate_config2
 
     rng = np.random.default_rng(11)
     base = generate_config2(args.serve_n, seed=100)
-    qpool = generate_config2(400_000, seed=101)
-    ipool = generate_config2(3_000_000, seed=102)
+    # queries and inserts are later draws of the same repertoire model
+    qpool = generate(400_000, seed=101, template_seed=100, ins_max=6, len_lo=10, len_hi=20)
+    ipool = generate(3_000_000, seed=102, template_seed=100, ins_max=6, len_lo=10, len_hi=20)
     rate = 200.0
     arrivals, t = [], 0.0
     while True:
@@ -580,9 +581,10 @@ def run_ours(args):
             }
         if "query" in legs:
             # --- queries against the resident repertoire (host in, host out)
-            from synthgen import generate_config2
+            from synthgen import generate
 
-            qsrc = generate_config2(200_000, seed=1000 + rank)
+            # queries drawn from the resident repertoire's model (same templates)
+            qsrc = generate(200_000, seed=1000 + rank, template_seed=rank, ins_max=6, len_lo=10, len_hi=20)
             qstr_off = qsrc.offsets
             rng = np.random.default_rng(7)
             resident = build(profile=False)
@@ -631,14 +633,16 @@ def run_ours(args):
             # --- inserts into the resident N = 8e5 network: merged (query + network
             #     of the new strings, grown rows and index) vs rebuilt; copy-on-write
             #     (tcrnet_extend), new strings in device memory
-            from synthgen import generate_config2
+            from synthgen import generate
 
-            ipool = generate_config2(100_000, seed=2000 + rank)
+            # later draws of the same repertoire model (same templates): the new
+            # strings join the resident network
+            ipool = generate(100_000, seed=2000 + rank, template_seed=rank, ins_max=6, len_lo=10, len_hi=20)
             ic = torch.from_numpy(ipool.chars).to(dev)
             io = torch.from_numpy(ipool.offsets).to(dev)
             ins = {}
             with build() as g:
-                for m_ins in (100, 1_000, 10_000, 100_000):
+                for m_ins in (100, 1_000, 10_000, 25_000):
                     row = {}
                     for mode, rebuild in (("merged", False), ("rebuilt", True)):
                         ts = []

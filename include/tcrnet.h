@@ -94,8 +94,9 @@ typedef struct tcrnet_options {
     int32_t insert_rebuild;   /* inserts (tcrnet_insert_ex, tcrnet_extend): 1 = rebuild
                                  the grown repertoire from scratch; 0 (default) =
                                  merge the new strings into the handle's network and
-                                 index where the handle allows it (deletion builds
-                                 with l_max = 1), which gives the same network */
+                                 index where that is cheaper (deletion builds with
+                                 l_max = 1, inserts of at most 1/32 of the resident
+                                 strings), which gives the same network */
     int32_t reserved[4];      /* must be zero */
 } tcrnet_options;
 

@@ -1258,22 +1258,36 @@ k_query(IndexView ix, const Canon* __restrict__ qcanon, const uint8_t* __restric
             const int32_t S = __shfl_sync(kFull, excl, 31);
             excl -= sz;
             const int64_t rb = b0 - excl;  // word f of this lane's partition is recs[rb + f]
-            for (int32_t f0 = 0; f0 < S; f0 += 32) {
-                const int32_t f = f0 + lane;
+            // kRounds steps of 32 words: their loads are issued before any is tested
+            constexpr int kRounds = 4;
+            for (int32_t f00 = 0; f00 < S; f00 += 32 * kRounds) {
+            uint64_t rr[kRounds];
+            int vv[kRounds];
+#pragma unroll
+            for (int t = 0; t < kRounds; ++t) {
+                const int32_t f = f00 + 32 * t + lane;
                 int v = 0;  // owner: the last variant whose words start at or before f
 #pragma unroll
                 for (int step = 16; step > 0; step >>= 1) {
                     const int32_t e = __shfl_sync(kFull, excl, v + step);
                     if (e <= f) v += step;
                 }
+                vv[t] = v;
                 const int64_t vrb = __shfl_sync(kFull, rb, v);
+                rr[t] = f < S ? ix.recs[vrb + f] : 0ull;
+            }
+#pragma unroll
+            for (int t = 0; t < kRounds; ++t) {
+                if (f00 + 32 * t >= S) break;  // warp-uniform
+                const int32_t f = f00 + 32 * t + lane;
+                const int v = vv[t];
                 const uint32_t vh = __shfl_sync(kFull, h32, v);
                 const bool vq_rs = __shfl_sync(kFull, q_rs, v);
                 const int vp = g0 + v;
                 bool hit = false;
                 uint32_t u = 0;
                 if (f < S) {
-                    const uint64_t r = ix.recs[vrb + f];
+                    const uint64_t r = rr[t];
                     if ((uint32_t)(r >> 32) == vh) {
                         const uint32_t rp = rec_p(r);
                         const bool full = vp < 0;
@@ -1323,6 +1337,7 @@ k_query(IndexView ix, const Canon* __restrict__ qcanon, const uint8_t* __restric
                     }
                     base += tot;
                 }
+            }
             }
         }
         if constexpr (!WRITE) {
@@ -1700,15 +1715,27 @@ __global__ void k_ins_tails(const int64_t* __restrict__ roff, const int32_t* __r
                 }
             }
         } else {
-            for (int64_t e = e0; e < e1; ++e) {
-                const int32_t i = rcols[e];
-                if (i >= n0) continue;
+            // 32 row entries at a time: each lane takes the slots of one entry
+            // (their atomics are in flight together), then the warp writes the
+            // c members for each of the 32 entries
+            for (int64_t e = e0; e < e1; e += 32) {
+                int32_t i = -1;
                 int64_t base = 0;
-                if (lane == 0) base = toff[i] + atomicAdd(&tcur[i], c);
-                base = __shfl_sync(kFull, base, 0);
-                for (int32_t k = lane; k < c; k += 32) {
-                    tcols[base + k] = (int32_t)(n0 + nm_list[a + k]);
-                    trow[base + k] = i;
+                if (e + lane < e1) {
+                    i = rcols[e + lane];
+                    if (i < n0) base = toff[i] + atomicAdd(&tcur[i], c);
+                    else i = -1;
+                }
+                unsigned todo = __ballot_sync(kFull, i >= 0);
+                while (todo) {
+                    const int t = __ffs(todo) - 1;
+                    todo &= todo - 1;
+                    const int32_t ti = __shfl_sync(kFull, i, t);
+                    const int64_t tb = __shfl_sync(kFull, base, t);
+                    for (int32_t k = lane; k < c; k += 32) {
+                        tcols[tb + k] = (int32_t)(n0 + nm_list[a + k]);
+                        trow[tb + k] = ti;
+                    }
                 }
             }
         }

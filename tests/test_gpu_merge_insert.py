@@ -14,7 +14,7 @@ import pytest
 
 import oracle
 import paper_2112_06613_b300 as tn
-from synthgen import from_strings, generate_config1
+from synthgen import from_strings, generate, generate_config1
 
 from csr_util import assert_csr_equal, check_invariants
 
@@ -65,7 +65,8 @@ def test_merged_insert_edge_cases():
 
 def test_many_small_merged_inserts_and_queries():
     base = generate_config1(20_000, seed=202).strings()
-    pool = generate_config1(6000, seed=203).strings() + base[:500]
+    # later draws of the same template model: the new strings join the network
+    pool = generate(6000, seed=203, template_seed=202).strings() + base[:500]
     rng = np.random.default_rng(7)
     rng.shuffle(pool)
     strs = list(base)
@@ -92,7 +93,7 @@ def test_many_small_merged_inserts_and_queries():
 
 def test_merged_insert_analytics_and_checkpoint(tmp_path):
     base = generate_config1(8000, seed=205).strings()
-    add = generate_config1(2500, seed=206).strings() + base[:200]
+    add = generate(200, seed=206, template_seed=205).strings() + base[:50]
     b = from_strings(add)
     strs = base + add
     keep = (np.random.default_rng(9).random(len(strs)) >= 0.25).astype(np.uint8)
@@ -115,7 +116,7 @@ def test_merged_insert_analytics_and_checkpoint(tmp_path):
     with tn.tcrnet_load(path) as h:
         assert h.stats()["merged_inserts"] == 1
         assert_same_as_fresh(h, strs, "restored merged handle", oracle_check=False)
-        more = generate_config1(700, seed=207).strings()
+        more = generate(200, seed=207, template_seed=205).strings()
         mb = from_strings(more)
         h.insert_flat(mb.chars, mb.offsets)
         assert h.stats()["merged_inserts"] == 2
@@ -124,7 +125,7 @@ def test_merged_insert_analytics_and_checkpoint(tmp_path):
 
 def test_merged_insert_int64_offsets_and_rebuild_option():
     base = generate_config1(6000, seed=208).strings()
-    add = generate_config1(900, seed=209).strings()
+    add = generate(150, seed=209, template_seed=208).strings()
     b = from_strings(add)
     rep = from_strings(base)
     with tn.tcrnet_build_flat(rep.chars, rep.offsets, 1, method="deletion", force_offsets64=True) as g:
@@ -147,12 +148,39 @@ def test_merged_insert_int64_offsets_and_rebuild_option():
 
 def test_large_insert_rebuilds():
     base = generate_config1(3000, seed=210).strings()
-    add = generate_config1(4000, seed=211).strings()  # larger than the repertoire: rebuilt
+    add = generate_config1(4000, seed=211).strings()  # above 1/32 of the repertoire: rebuilt
     b = from_strings(add)
     with fresh(base) as g:
-        small = from_strings(add[:100])
+        small = from_strings(add[:80])
         g.insert_flat(small.chars, small.offsets)
         assert g.stats()["merged_inserts"] == 1
         g.insert_flat(b.chars, b.offsets)
         assert g.stats()["merged_inserts"] == 0
-        assert_same_as_fresh(g, base + add[:100] + add, "rebuild after merge", oracle_check=False)
+        assert_same_as_fresh(g, base + add[:80] + add, "rebuild after merge", oracle_check=False)
+
+
+def test_merged_insert_allocation_failures_keep_the_handle():
+    """Every device allocation of a merged insert in turn fails: the call returns
+    TCRNET_ENOMEM and the handle keeps its network; then the insert succeeds."""
+    import ctypes
+
+    base = generate_config1(3000, seed=212).strings()
+    add = generate(60, seed=213, template_seed=212).strings() + base[:5]
+    b = from_strings(add)
+    lib = tn.load_library()
+    with fresh(base) as g:
+        before = csr_of(g)
+        failures = 0
+        for k in range(1, 400):
+            opt = tn.make_options(fail_alloc_at=k)
+            st = lib.tcrnet_insert_ex(g.handle, b.chars.ctypes.data, b.offsets.ctypes.data, b.n, tn.HOST,
+                                      ctypes.byref(opt))
+            if st == tn.OK:
+                break
+            assert st == tn.ENOMEM, (k, st)
+            failures += 1
+            after = csr_of(g)
+            assert_csr_equal(after[0], after[1], before[0], before[1], f"merged insert fail_alloc_at={k}")
+        assert failures >= 20
+        assert g.stats()["merged_inserts"] == 1
+        assert_same_as_fresh(g, base + add, "merged insert after failures")
