@@ -1198,6 +1198,19 @@ struct IndexView {
     uint32_t P;
 };
 
+// Exact check of a candidate match (equal 32-bit hash, fitting position tags)
+// between variant vp of query string qc (-1: the full string) and record r:
+// equal contents, and an identical resident string counted once (full to full).
+__device__ __forceinline__ bool verify_candidate(const IndexView& ix, const Canon& qc, uint64_t r, int vp,
+                                                 uint32_t& u) {
+    const bool full = vp < 0;
+    const Canon cq = full ? qc : delete_at(qc, vp);
+    if (!canon_eq(cq, record_content(r, ix.ucanon))) return false;  // hash collision
+    u = rec_u(r);
+    if (!full && rec_p(r) != kTagF && canon_eq(qc, load_canon(ix.ucanon + u))) return false;
+    return true;
+}
+
 // Neighbours of a query string among the distinct resident strings, found
 // through the string's own records (full string and every deletion) in the
 // resident partitions; each match is confirmed by content and each neighbour is
@@ -1220,13 +1233,47 @@ k_query(IndexView ix, const Canon* __restrict__ qcanon, const uint8_t* __restric
     __shared__ int64_t big_src[kWarps][kQueued], big_dst[kWarps][kQueued];
     __shared__ int32_t big_len[kWarps][kQueued];
     __shared__ int big_n[kWarps];
+    // COUNT: candidates wait in a per-warp queue and are verified 32 at a time,
+    // one per lane, instead of one lane at a time as they turn up
+    __shared__ uint64_t cand_r[kWarps][64];
+    __shared__ int8_t cand_p[kWarps][64];
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < m; q += stride) {
         const Canon qc = load_canon(qcanon + q);
         const int Lq = qlen[q];
         int64_t mine = 0;                           // COUNT: members found by this lane
+        int qn = 0;                                 // COUNT: queued candidates (warp-uniform)
+        auto flush = [&](int cnt) {                 // COUNT: verify the first cnt queued candidates
+            bool hit = false;
+            uint32_t u = 0;
+            if (lane < cnt) hit = verify_candidate(ix, qc, cand_r[w][lane], cand_p[w][lane], u);
+            mine += hit ? ix.umult[u] : 0;
+            const unsigned hm = __ballot_sync(kFull, hit);
+            if (hm && hits) {  // keep the match (query, distinct string) for the emit pass
+                unsigned long long hb = 0;
+                if (lane == 0) hb = atomicAdd(hit_cur, (unsigned long long)__popc(hm));
+                hb = __shfl_sync(kFull, hb, 0);
+                const int64_t slot = (int64_t)hb + __popc(hm & lt_mask);
+                if (hit && slot < hit_cap) hits[slot] = make_int2((int32_t)q, (int32_t)u);
+            }
+            const int rest = qn - cnt;
+            uint64_t tr = 0;
+            int8_t tp = 0;
+            if (lane < rest) {
+                tr = cand_r[w][cnt + lane];
+                tp = cand_p[w][cnt + lane];
+            }
+            __syncwarp();
+            if (lane < rest) {
+                cand_r[w][lane] = tr;
+                cand_p[w][lane] = tp;
+            }
+            __syncwarp();
+            qn = rest;
+        };
         int64_t base = WRITE ? qoff[q] : 0;         // WRITE: next output slot (warp-uniform)
         if constexpr (WRITE) {
             if (lane == 0) big_n[w] = 0;
@@ -1284,39 +1331,33 @@ k_query(IndexView ix, const Canon* __restrict__ qcanon, const uint8_t* __restric
                 const uint32_t vh = __shfl_sync(kFull, h32, v);
                 const bool vq_rs = __shfl_sync(kFull, q_rs, v);
                 const int vp = g0 + v;
-                bool hit = false;
-                uint32_t u = 0;
+                bool cand = false;  // equal hash and fitting position tags
                 if (f < S) {
                     const uint64_t r = rr[t];
                     if ((uint32_t)(r >> 32) == vh) {
                         const uint32_t rp = rec_p(r);
-                        const bool full = vp < 0;
-                        if (full) hit = (rp == kTagF) || (T >= 1 && rec_runstart(r));  // identical / q one shorter
-                        else hit = (rp == kTagF) ? vq_rs : (rp == (uint32_t)vp);       // q one longer / substitution
-                        if (hit) {
-                            const Canon cq = full ? qc : delete_at(qc, vp);
-                            hit = canon_eq(cq, record_content(r, ix.ucanon));          // hash collision
-                        }
-                        if (hit) {
-                            u = rec_u(r);
-                            if (!full && rp != kTagF && canon_eq(qc, load_canon(ix.ucanon + u)))
-                                hit = false;  // identical: counted once, full-to-full
-                        }
+                        if (vp < 0) cand = (rp == kTagF) || (T >= 1 && rec_runstart(r));  // identical / q one shorter
+                        else cand = (rp == kTagF) ? vq_rs : (rp == (uint32_t)vp);          // q one longer / substitution
                     }
                 }
-                const int32_t mu = hit ? ix.umult[u] : 0;
                 if constexpr (!WRITE) {
-                    mine += mu;
-                    // keep the match (query, distinct string) for the emit pass
-                    const unsigned hm = __ballot_sync(kFull, hit);
-                    if (hm && hits) {
-                        unsigned long long hb = 0;
-                        if (lane == 0) hb = atomicAdd(hit_cur, (unsigned long long)__popc(hm));
-                        hb = __shfl_sync(kFull, hb, 0);
-                        const int64_t slot = (int64_t)hb + __popc(hm & ((1u << lane) - 1u));
-                        if (hit && slot < hit_cap) hits[slot] = make_int2((int32_t)q, (int32_t)u);
+                    const unsigned cm = __ballot_sync(kFull, cand);
+                    if (cm) {
+                        if (cand) {
+                            const int slot = qn + __popc(cm & lt_mask);
+                            cand_r[w][slot] = rr[t];
+                            cand_p[w][slot] = (int8_t)vp;
+                        }
+                        qn += __popc(cm);
+                        if (qn >= 32) {
+                            __syncwarp();
+                            flush(32);
+                        }
                     }
                 } else {
+                    uint32_t u = 0;
+                    const bool hit = cand && verify_candidate(ix, qc, rr[t], vp, u);
+                    const int32_t mu = hit ? ix.umult[u] : 0;
                     if (!__any_sync(kFull, hit)) continue;
                     int64_t ex;
                     const int64_t tot = warp_scan((int64_t)mu, ex, lane);
@@ -1341,6 +1382,10 @@ k_query(IndexView ix, const Canon* __restrict__ qcanon, const uint8_t* __restric
             }
         }
         if constexpr (!WRITE) {
+            if (qn > 0) {
+                __syncwarp();
+                flush(qn);
+            }
             int64_t ex;
             const int64_t total = warp_scan(mine, ex, lane);
             if (lane == 0) qcount[q] = total;
