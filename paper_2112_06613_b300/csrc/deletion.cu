@@ -1711,93 +1711,116 @@ __global__ void k_ins_edges(const int64_t* __restrict__ roff, const int32_t* __r
     }
 }
 
-// New entries of old rows: old node i gains every new member of every
-// represented string whose closed row lists i.
-__global__ void k_ins_delta(const int64_t* __restrict__ roff, const int32_t* __restrict__ rcols, int64_t nrep,
-                            const int32_t* __restrict__ nm_cnt, int64_t n0, int32_t* __restrict__ delta) {
+// New entries of old rows. An old node i gains every new member of every
+// represented string whose closed row lists it; that set depends only on i's
+// distinct string x (all members of x are listed together), so it is built
+// once per x (its "tail") and copied to each old member of x. A closed row
+// stands for x by x's first old member. dcnt[x] = tail length of x.
+__global__ void k_ins_tail_count(const int64_t* __restrict__ roff, const int32_t* __restrict__ rcols, int64_t nrep,
+                                 const int32_t* __restrict__ nm_cnt, int64_t n0, const int32_t* __restrict__ uid,
+                                 const int64_t* __restrict__ mem_off_old, const int32_t* __restrict__ members_old,
+                                 int32_t* __restrict__ dcnt) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrep; r += nw) {
         const int32_t c = nm_cnt[r];
         for (int64_t e = roff[r] + lane; e < roff[r + 1]; e += 32) {
             const int32_t i = rcols[e];
-            if (i < n0) atomicAdd(&delta[i], c);
+            if (i >= n0) continue;
+            const int32_t x = uid[i];
+            if (members_old[mem_off_old[x]] == i) atomicAdd(&dcnt[x], c);
         }
     }
 }
 
-// Degrees of the grown network: a new node has its closed row minus itself.
-__global__ void k_ins_degree(const int32_t* __restrict__ deg_old, const int32_t* __restrict__ delta, int64_t n0,
-                             const int32_t* __restrict__ nuid, const int32_t* __restrict__ ridx,
-                             const int32_t* __restrict__ rcnt, int64_t m, int32_t* __restrict__ deg) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n0) deg[i] = deg_old[i] + delta[i];
-    else if (i < n0 + m) deg[i] = rcnt[ridx[nuid[i - n0]]] - 1;
-}
-
-// Tail lists of the old rows: old node i takes n0 + j for the new members j of
-// every closed row that lists it, at slots of its tail (sorted afterwards);
-// trow keeps the row of each slot. Few new members: a lane per row entry;
-// many: the whole warp per entry.
+// Tails of the old distinct strings: x takes n0 + j for the new members j of
+// every closed row that stands for it, at slots of its tail (sorted
+// afterwards). Few new members: a lane per row entry; many: 32 row entries
+// take their slots together, then the warp writes the members of each.
 __global__ void k_ins_tails(const int64_t* __restrict__ roff, const int32_t* __restrict__ rcols, int64_t nrep,
                             const int64_t* __restrict__ nm_off, const int32_t* __restrict__ nm_list, int64_t n0,
-                            const int64_t* __restrict__ toff, int32_t* __restrict__ tcur, int32_t* __restrict__ tcols,
-                            int32_t* __restrict__ trow) {
+                            const int32_t* __restrict__ uid, const int64_t* __restrict__ mem_off_old,
+                            const int32_t* __restrict__ members_old, const int64_t* __restrict__ dtoff,
+                            int32_t* __restrict__ dcur, int32_t* __restrict__ dtcols) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrep; r += nw) {
         const int64_t a = nm_off[r];
         const int32_t c = (int32_t)(nm_off[r + 1] - a);
         const int64_t e0 = roff[r], e1 = roff[r + 1];
-        if (c <= 4) {
-            for (int64_t e = e0 + lane; e < e1; e += 32) {
-                const int32_t i = rcols[e];
-                if (i >= n0) continue;
-                const int64_t base = toff[i] + atomicAdd(&tcur[i], c);
-                for (int32_t k = 0; k < c; ++k) {
-                    tcols[base + k] = (int32_t)(n0 + nm_list[a + k]);
-                    trow[base + k] = i;
+        for (int64_t e = e0; e < e1; e += 32) {
+            int64_t base = -1;
+            if (e + lane < e1) {
+                const int32_t i = rcols[e + lane];
+                if (i < n0) {
+                    const int32_t x = uid[i];
+                    if (members_old[mem_off_old[x]] == i) base = dtoff[x] + atomicAdd(&dcur[x], c);
                 }
             }
-        } else {
-            // 32 row entries at a time: each lane takes the slots of one entry
-            // (their atomics are in flight together), then the warp writes the
-            // c members for each of the 32 entries
-            for (int64_t e = e0; e < e1; e += 32) {
-                int32_t i = -1;
-                int64_t base = 0;
-                if (e + lane < e1) {
-                    i = rcols[e + lane];
-                    if (i < n0) base = toff[i] + atomicAdd(&tcur[i], c);
-                    else i = -1;
-                }
-                unsigned todo = __ballot_sync(kFull, i >= 0);
+            if (c <= 4) {
+                if (base >= 0)
+                    for (int32_t k = 0; k < c; ++k) dtcols[base + k] = (int32_t)(n0 + nm_list[a + k]);
+            } else {
+                unsigned todo = __ballot_sync(kFull, base >= 0);
                 while (todo) {
                     const int t = __ffs(todo) - 1;
                     todo &= todo - 1;
-                    const int32_t ti = __shfl_sync(kFull, i, t);
                     const int64_t tb = __shfl_sync(kFull, base, t);
-                    for (int32_t k = lane; k < c; k += 32) {
-                        tcols[tb + k] = (int32_t)(n0 + nm_list[a + k]);
-                        trow[tb + k] = ti;
-                    }
+                    for (int32_t k = lane; k < c; k += 32) dtcols[tb + k] = (int32_t)(n0 + nm_list[a + k]);
                 }
             }
         }
     }
 }
 
-// Tail lists of the old rows after their old entries, one thread per entry
-// (a row next to many new strings has a long tail).
+// Degrees of the grown network (old node: + its string's tail; new node: its
+// closed row minus itself) and the growth of each old row.
+__global__ void k_ins_degree(const int32_t* __restrict__ deg_old, const int32_t* __restrict__ dcnt,
+                             const int32_t* __restrict__ uid, int64_t n0, const int32_t* __restrict__ nuid,
+                             const int32_t* __restrict__ ridx, const int32_t* __restrict__ rcnt, int64_t m,
+                             int32_t* __restrict__ delta, int32_t* __restrict__ deg) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n0) {
+        const int32_t d = dcnt[uid[i]];
+        delta[i] = d;
+        deg[i] = deg_old[i] + d;
+    } else if (i < n0 + m) {
+        deg[i] = rcnt[ridx[nuid[i - n0]]] - 1;
+    }
+}
+
+// Tails copied after the old entries of each old row: a lane per row for short
+// tails, the whole warp for long ones.
 template <typename OffT>
 __global__ void k_ins_fill_tails(const OffT* __restrict__ old_off, const int64_t* __restrict__ new_off,
-                                 const int64_t* __restrict__ toff, const int32_t* __restrict__ tcols,
-                                 const int32_t* __restrict__ trow, int64_t n0, int32_t* __restrict__ cols) {
-    const int64_t nt = toff[n0];
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nt; e += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t i = trow[e];
-        const int64_t at = new_off[i] + ((int64_t)old_off[i + 1] - (int64_t)old_off[i]) + (e - toff[i]);
-        cols[at] = tcols[e];
+                                 const int32_t* __restrict__ uid, const int32_t* __restrict__ dcnt,
+                                 const int64_t* __restrict__ dtoff, const int32_t* __restrict__ dtcols, int64_t n0,
+                                 int32_t* __restrict__ cols) {
+    constexpr int kLaneTail = 8;
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; i0 < n0; i0 += nw * 32) {
+        const int64_t i = i0 + lane;
+        int32_t len = 0;
+        int64_t src = 0, dst = 0;
+        if (i < n0) {
+            const int32_t x = uid[i];
+            len = dcnt[x];
+            if (len > 0) {
+                src = dtoff[x];
+                dst = new_off[i] + ((int64_t)old_off[i + 1] - (int64_t)old_off[i]);
+                if (len <= kLaneTail)
+                    for (int32_t k = 0; k < len; ++k) cols[dst + k] = dtcols[src + k];
+            }
+        }
+        unsigned todo = __ballot_sync(kFull, len > kLaneTail);
+        while (todo) {
+            const int t = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t ts = __shfl_sync(kFull, src, t), td = __shfl_sync(kFull, dst, t);
+            const int32_t tl = __shfl_sync(kFull, len, t);
+            for (int32_t k = lane; k < tl; k += 32) cols[td + k] = dtcols[ts + k];
+        }
     }
 }
 
@@ -1886,17 +1909,17 @@ tcrnet_status shifted_copy(const T* src, T* dst, int64_t count, const DevBuf& cu
 
 template <typename OffT>
 tcrnet_status csr_merge(const CsrView& g, const OffT* old_off, const int32_t* delta, int64_t n_tail,
-                        const int64_t* new_off, const int64_t* toff, const int32_t* tcols, const int32_t* trow,
-                        const int64_t* roff, const int32_t* rcols, const int32_t* nuid, const int32_t* ridx,
-                        int64_t m, int32_t* cols, cudaStream_t s, int num_sms) {
+                        const int64_t* new_off, const int32_t* uid, const int32_t* dcnt, const int64_t* dtoff,
+                        const int32_t* dtcols, const int64_t* roff, const int32_t* rcols, const int32_t* nuid,
+                        const int32_t* ridx, int64_t m, int32_t* cols, cudaStream_t s, int num_sms) {
     const int64_t n0 = g.n;
     DevBuf cuts, shifts, pos;
     TCR_CHECK(growth_cuts<OffT>(delta, old_off, new_off, n0, std::min<int64_t>(n0, n_tail), cuts, shifts, pos, s));
     TCR_CHECK(shifted_copy<int32_t>(g.cols, cols, g.nnz, cuts, shifts, pos.as<int64_t>() + n0,
                                     std::min<int64_t>(n0, n_tail), s, num_sms));
     if (n_tail > 0) {
-        k_ins_fill_tails<OffT><<<(unsigned)std::min<int64_t>(grid_for(n_tail), (int64_t)num_sms * 16), kThreads, 0,
-                                 s>>>(old_off, new_off, toff, tcols, trow, n0, cols);
+        k_ins_fill_tails<OffT><<<(unsigned)std::min<int64_t>(ceil_div(n0, 32 * kWarps), (int64_t)num_sms * 16),
+                                 kThreads, 0, s>>>(old_off, new_off, uid, dcnt, dtoff, dtcols, n0, cols);
         TCR_LAUNCH_CHECK();
     }
     const unsigned wgrid = (unsigned)std::min<int64_t>(ceil_div(m, kWarps), (int64_t)num_sms * 16);
@@ -2066,51 +2089,57 @@ tcrnet_status deletion_insert(const DeletionIndex& ix, const CsrView& g, const P
     TCR_LAUNCH_CHECK();
     const int t4 = tm.mark();
 
-    // 5. the grown CSR: old rows gain tails, new rows are the closed rows of
-    //    their strings without themselves
-    DevBuf delta, deg, off64, toff, tcur, tcols, trow, cols;
+    // 5. the grown CSR: old rows gain the tails of their strings, new rows are
+    //    the closed rows of their strings without themselves
+    DevBuf dcnt, dtoff, dcur, dtcols, delta, deg, off64, toff, cols;
+    TCR_CHECK(dcnt.alloc(sizeof(int32_t) * U0, s));
+    TCR_CHECK(dtoff.alloc(sizeof(int64_t) * (U0 + 1), s));
+    TCR_CHECK(dcur.alloc(sizeof(int32_t) * U0, s));
     TCR_CHECK(delta.alloc(sizeof(int32_t) * n0, s));
     TCR_CHECK(toff.alloc(sizeof(int64_t) * (n0 + 1), s));
-    TCR_CHECK(tcur.alloc(sizeof(int32_t) * n0, s));
     TCR_CHECK(deg.alloc_owned(sizeof(int32_t) * N, s));
     TCR_CHECK(off64.alloc_owned(sizeof(int64_t) * (N + 1), s));
-    TCR_CUDA(cudaMemsetAsync(delta.as<void>(), 0, sizeof(int32_t) * n0, s));
-    TCR_CUDA(cudaMemsetAsync(tcur.as<void>(), 0, sizeof(int32_t) * n0, s));
-    k_ins_delta<<<rgrid, kThreads, 0, s>>>(roff.as<int64_t>(), rcols.as<int32_t>(), nrep, nm_cnt.as<int32_t>(), n0,
-                                           delta.as<int32_t>());
+    TCR_CUDA(cudaMemsetAsync(dcnt.as<void>(), 0, sizeof(int32_t) * U0, s));
+    TCR_CUDA(cudaMemsetAsync(dcur.as<void>(), 0, sizeof(int32_t) * U0, s));
+    k_ins_tail_count<<<rgrid, kThreads, 0, s>>>(roff.as<int64_t>(), rcols.as<int32_t>(), nrep, nm_cnt.as<int32_t>(),
+                                                n0, uid.as<int32_t>(), ix.mem_off, ix.members, dcnt.as<int32_t>());
+    TCR_LAUNCH_CHECK();
+    TCR_CHECK(scan_exclusive_i32_to_i64(dcnt.as<int32_t>(), dtoff.as<int64_t>(), U0, s));
+    k_ins_degree<<<grid_for(N), kThreads, 0, s>>>(g.degree, dcnt.as<int32_t>(), uid.as<int32_t>(), n0,
+                                                  nuid.as<int32_t>(), ridx.as<int32_t>(), rcnt.as<int32_t>(), m,
+                                                  delta.as<int32_t>(), deg.as<int32_t>());
     TCR_LAUNCH_CHECK();
     TCR_CHECK(scan_exclusive_i32_to_i64(delta.as<int32_t>(), toff.as<int64_t>(), n0, s));
-    k_ins_degree<<<grid_for(N), kThreads, 0, s>>>(g.degree, delta.as<int32_t>(), n0, nuid.as<int32_t>(),
-                                                  ridx.as<int32_t>(), rcnt.as<int32_t>(), m, deg.as<int32_t>());
-    TCR_LAUNCH_CHECK();
     TCR_CHECK(scan_exclusive_i32_to_i64(deg.as<int32_t>(), off64.as<int64_t>(), N, s));
-    int64_t sizes[2] = {0, 0};  // new entries of old rows, entries of the grown network
+    int64_t sizes[3] = {0, 0, 0};  // new entries of old rows, entries of the grown network, tail entries
     TCR_CUDA(cudaMemcpyAsync(&sizes[0], toff.as<int64_t>() + n0, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TCR_CUDA(cudaMemcpyAsync(&sizes[1], off64.as<int64_t>() + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaMemcpyAsync(&sizes[2], dtoff.as<int64_t>() + U0, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TCR_CUDA(cudaStreamSynchronize(s));
-    const int64_t n_tail = sizes[0], nnz = sizes[1];
-    if (n_tail < 0 || nnz < g.nnz + n_tail) return TCRNET_EDEVICE;
-    TCR_CHECK(tcols.alloc(sizeof(int32_t) * (n_tail > 0 ? n_tail : 1), s));
-    TCR_CHECK(trow.alloc(sizeof(int32_t) * (n_tail > 0 ? n_tail : 1), s));
+    const int64_t n_tail = sizes[0], nnz = sizes[1], n_dtail = sizes[2];
+    if (n_tail < 0 || n_dtail < 0 || nnz < g.nnz + n_tail) return TCRNET_EDEVICE;
+    TCR_CHECK(dtcols.alloc(sizeof(int32_t) * (n_dtail > 0 ? n_dtail : 1), s));
     TCR_CHECK(cols.alloc_owned(sizeof(int32_t) * nnz, s));
-    if (n_tail > 0) {
+    if (n_dtail > 0) {
         k_ins_tails<<<rgrid, kThreads, 0, s>>>(roff.as<int64_t>(), rcols.as<int32_t>(), nrep, nm_off.as<int64_t>(),
-                                               nm_list.as<int32_t>(), n0, toff.as<int64_t>(), tcur.as<int32_t>(),
-                                               tcols.as<int32_t>(), trow.as<int32_t>());
+                                               nm_list.as<int32_t>(), n0, uid.as<int32_t>(), ix.mem_off, ix.members,
+                                               dtoff.as<int64_t>(), dcur.as<int32_t>(), dtcols.as<int32_t>());
         TCR_LAUNCH_CHECK();
-        TCR_CHECK(sort_rows(toff.as<int64_t>(), tcols.as<int32_t>(), n0, s, num_sms));
+        TCR_CHECK(sort_rows(dtoff.as<int64_t>(), dtcols.as<int32_t>(), U0, s, num_sms));
     }
     const int t5 = tm.mark();
     if (g.off64)
         TCR_CHECK(csr_merge<int64_t>(g, static_cast<const int64_t*>(g.offsets), delta.as<int32_t>(), n_tail,
-                                     off64.as<int64_t>(), toff.as<int64_t>(), tcols.as<int32_t>(),
-                                     trow.as<int32_t>(), roff.as<int64_t>(), rcols.as<int32_t>(),
-                                     nuid.as<int32_t>(), ridx.as<int32_t>(), m, cols.as<int32_t>(), s, num_sms));
+                                     off64.as<int64_t>(), uid.as<int32_t>(), dcnt.as<int32_t>(),
+                                     dtoff.as<int64_t>(), dtcols.as<int32_t>(), roff.as<int64_t>(),
+                                     rcols.as<int32_t>(), nuid.as<int32_t>(), ridx.as<int32_t>(), m,
+                                     cols.as<int32_t>(), s, num_sms));
     else
         TCR_CHECK(csr_merge<int32_t>(g, static_cast<const int32_t*>(g.offsets), delta.as<int32_t>(), n_tail,
-                                     off64.as<int64_t>(), toff.as<int64_t>(), tcols.as<int32_t>(),
-                                     trow.as<int32_t>(), roff.as<int64_t>(), rcols.as<int32_t>(),
-                                     nuid.as<int32_t>(), ridx.as<int32_t>(), m, cols.as<int32_t>(), s, num_sms));
+                                     off64.as<int64_t>(), uid.as<int32_t>(), dcnt.as<int32_t>(),
+                                     dtoff.as<int64_t>(), dtcols.as<int32_t>(), roff.as<int64_t>(),
+                                     rcols.as<int32_t>(), nuid.as<int32_t>(), ridx.as<int32_t>(), m,
+                                     cols.as<int32_t>(), s, num_sms));
     const int t6 = tm.mark();
 
     // 6. sizes and error flags
