@@ -33,7 +33,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import Graph, load_library
+from . import Graph, TcrnetError, load_library
 
 
 @dataclass
@@ -63,7 +63,7 @@ class Request:
 
 class ServingEngine:
     def __init__(self, graph: Graph, slots: int = 4, max_batch_strings: int = 200_000,
-                 hbm_reserve_bytes: int = 4 << 30, device: int = 0):
+                 hbm_reserve_bytes: int = 4 << 30, device: int = 0, result_buffer_bytes: int = 64 << 20):
         import torch
 
         self.graph = graph
@@ -89,6 +89,12 @@ class ServingEngine:
         self._stop = False
         self._version = 0
         self._batches = 0
+        # per slot: pinned host buffers for query answers, allocated once (pinned
+        # allocations are slow and stall other work); larger answers use pageable
+        # arrays of their own
+        self._stage = [(torch.empty(max_batch_strings + 1, dtype=torch.int64, pin_memory=True),
+                        torch.empty(max(result_buffer_bytes // 4, 1), dtype=torch.int32, pin_memory=True))
+                       for _ in range(slots)]
         self._workers = [threading.Thread(target=self._run, args=(k,), daemon=True) for k in range(slots)]
         self.completed: list[Request] = []
 
@@ -197,7 +203,7 @@ class ServingEngine:
                 if batch[0].kind == "insert":
                     self._do_insert(batch[0], insert_stream)
                 else:
-                    self._do_queries(batch, stream)
+                    self._do_queries(batch, stream, slot)
             except BaseException as e:  # reported per request
                 for r in batch:
                     r.error = e
@@ -250,7 +256,7 @@ class ServingEngine:
                 self._turn += 1
                 self._cv.notify_all()
 
-    def _do_queries(self, batch: list[Request], stream):
+    def _do_queries(self, batch: list[Request], stream, slot: int = 0):
         if len(batch) == 1:
             chars, offsets = batch[0].chars, batch[0].offsets
         else:
@@ -265,12 +271,25 @@ class ServingEngine:
                 self._batches += 1
             res = Graph.borrowed(h).query_flat(chars, offsets, method="auto", stream=stream)
             try:
-                off, cols, _ = res.copy_csr()
+                # into this slot's pinned buffers (a copy to pageable memory goes
+                # through the driver's small staging buffers, slowly for long
+                # answers), then out into each request's own arrays
+                n, nnz, o64 = res.info()
+                off_t, cols_t = self._stage[slot]
+                if n + 1 <= off_t.numel() and nnz <= cols_t.numel():
+                    off_v = off_t.numpy()[:n + 1] if o64 else off_t.numpy().view(np.int32)[:n + 1]
+                    cols = cols_t.numpy()[:nnz]
+                else:  # larger than the slot's buffers: pageable arrays of its own
+                    off_v = np.empty(n + 1, dtype=np.int64 if o64 else np.int32)
+                    cols = np.empty(max(nnz, 1), dtype=np.int32)[:nnz]
+                st = load_library().tcrnet_copy_csr(res.handle, off_v.ctypes.data, cols.ctypes.data, None, 0)
+                if st != 0:
+                    raise TcrnetError(st, "tcrnet_copy_csr")
             finally:
                 res.free()
         finally:
             self._drop(h)
-        off = np.asarray(off, dtype=np.int64)
+        off = off_v.astype(np.int64)
         row = 0
         for r in batch:
             k = r.n_strings
