@@ -82,6 +82,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="0 skips the serving leg")
     ap.add_argument("--serve-n", type=int, default=2_000_000)
+    ap.add_argument("--insert-sizes", default="100,1000,10000,25000",
+                    help="comma list of insert sizes of the insert leg")
     ap.add_argument("--batched-reps", type=int, default=256, help="0 skips the batched leg")
     ap.add_argument("--no-extras", action="store_true", help="skip every leg after the timed step")
     ap.add_argument("--legs", default=",".join(LEGS),
@@ -642,7 +644,7 @@ def run_ours(args):
             io = torch.from_numpy(ipool.offsets).to(dev)
             ins = {}
             with build() as g:
-                for m_ins in (100, 1_000, 10_000, 25_000):
+                for m_ins in [int(x) for x in args.insert_sizes.split(",") if x]:
                     row = {}
                     for mode, rebuild in (("merged", False), ("rebuilt", True)):
                         ts = []
