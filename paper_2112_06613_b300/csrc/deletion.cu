@@ -1597,53 +1597,6 @@ __global__ void k_ins_cuts(const int32_t* __restrict__ grow, const OffT* __restr
     shifts[k + 1] = new_off[i + 1] - end;
 }
 
-// dst[t + shifts[k(t)]] = src[t], k(t) = number of cuts <= t. Each block moves
-// one contiguous range, finds the piece of its first element by a block-wide
-// 256-ary search and advances through the (sorted) cuts with its elements.
-template <typename T>
-__global__ void __launch_bounds__(256) k_shifted_copy(const T* __restrict__ src, T* __restrict__ dst, int64_t count,
-                                                      const int64_t* __restrict__ cuts,
-                                                      const int64_t* __restrict__ shifts,
-                                                      const int64_t* __restrict__ K_ptr) {
-    constexpr int kUnroll = 8;
-    const int64_t K = *K_ptr;
-    const int64_t nb = (int64_t)blockDim.x;
-    const int64_t per = ((count + gridDim.x - 1) / gridDim.x + nb - 1) / nb * nb;
-    const int64_t b0 = (int64_t)blockIdx.x * per;
-    const int64_t b1 = b0 + per < count ? b0 + per : count;
-    if (b0 >= b1) return;
-    // first index k with cuts[k] > b0, in [lo, hi]
-    int64_t lo = 0, hi = K;
-    while (hi > lo) {
-        const int64_t span = hi - lo;
-        const int64_t step = span <= nb ? 1 : (span + nb - 1) / nb;
-        const int64_t idx = lo + (int64_t)threadIdx.x * step;
-        const bool le = idx < hi && cuts[idx] <= b0;
-        const int c = __syncthreads_count(le);  // probes at or below b0 form a prefix
-        if (c == 0) break;                      // cuts[lo] > b0: the answer is lo
-        const int64_t nlo = lo + (int64_t)(c - 1) * step + 1;
-        hi = lo + (int64_t)c * step < hi ? lo + (int64_t)c * step : hi;
-        lo = nlo;
-        if (step == 1) break;  // every index in the span was probed
-    }
-    int64_t k = lo;
-    for (int64_t t0 = b0 + threadIdx.x; t0 < b1; t0 += (int64_t)kUnroll * blockDim.x) {
-        T v[kUnroll];
-#pragma unroll
-        for (int r = 0; r < kUnroll; ++r) {
-            const int64_t t = t0 + (int64_t)r * blockDim.x;
-            if (t < b1) v[r] = src[t];
-        }
-#pragma unroll
-        for (int r = 0; r < kUnroll; ++r) {
-            const int64_t t = t0 + (int64_t)r * blockDim.x;
-            if (t < b1) {
-                while (k < K && cuts[k] <= t) ++k;
-                dst[t + shifts[k]] = v[r];
-            }
-        }
-    }
-}
 
 // Distinct strings that the new strings take: the first new string of each
 // (first[u] = smallest j) represents it.
@@ -1869,40 +1822,58 @@ tcrnet_status growth_cuts(const int32_t* grow, const OffT* old_off, const int64_
     return TCRNET_OK;
 }
 
-// The same copy when the cuts are dense (short pieces): a warp per piece
-// k = [cuts[k-1], cuts[k]) (piece 0 from 0, piece K to count).
+// dst[t + shifts[k(t)]] = src[t], k(t) = number of cuts <= t (cuts sorted,
+// possibly equal). Each warp moves one contiguous range: it finds the piece of
+// its first element by a 32-way search over the cuts, then walks the pieces of
+// its range in order, copying each with all lanes (coalesced), whether the
+// pieces are long (few rows grow) or a few dozen elements (many do).
 template <typename T>
-__global__ void k_piece_copy(const T* __restrict__ src, T* __restrict__ dst, int64_t count,
-                             const int64_t* __restrict__ cuts, const int64_t* __restrict__ shifts,
-                             const int64_t* __restrict__ K_ptr) {
+__global__ void __launch_bounds__(kThreads) k_shifted_copy(const T* __restrict__ src, T* __restrict__ dst,
+                                                           int64_t count, const int64_t* __restrict__ cuts,
+                                                           const int64_t* __restrict__ shifts,
+                                                           const int64_t* __restrict__ K_ptr) {
     const int lane = threadIdx.x & 31;
     const int64_t K = *K_ptr;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k <= K; k += nw) {
-        const int64_t a = k == 0 ? 0 : cuts[k - 1];
-        const int64_t b = k == K ? count : cuts[k];
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t per = ((count + nw - 1) / nw + 31) / 32 * 32;
+    const int64_t b0 = gw * per;
+    const int64_t b1 = b0 + per < count ? b0 + per : count;
+    if (b0 >= b1) return;  // warp-uniform
+    // first k with cuts[k] > b0
+    int64_t lo = 0, hi = K;
+    while (hi - lo > 32) {
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t idx = lo + lane * step;
+        const int c = __popc(__ballot_sync(kFull, idx < hi && cuts[idx] <= b0));  // a prefix of the probes
+        if (c == 0) {
+            hi = lo;
+            break;
+        }
+        const int64_t nlo = lo + (int64_t)(c - 1) * step + 1;
+        hi = lo + (int64_t)c * step < hi ? lo + (int64_t)c * step : hi;
+        lo = nlo;
+    }
+    if (hi > lo) lo += __popc(__ballot_sync(kFull, lo + lane < hi && cuts[lo + lane] <= b0));
+    int64_t k = lo;
+    int64_t pos = b0;
+    while (pos < b1) {
+        while (k < K && cuts[k] <= pos) ++k;
+        const int64_t end = (k < K && cuts[k] < b1) ? cuts[k] : b1;
         const int64_t sh = shifts[k];
-        for (int64_t t = a + lane; t < b; t += 32) dst[t + sh] = src[t];
+        for (int64_t t = pos + lane; t < end; t += 32) dst[t + sh] = src[t];
+        pos = end;
     }
 }
 
-// max_cuts bounds the number of cuts: many short pieces take the warp-per-piece
-// copy, few long ones the block-range copy.
 template <typename T>
 tcrnet_status shifted_copy(const T* src, T* dst, int64_t count, const DevBuf& cuts, const DevBuf& shifts,
-                           const int64_t* K_dev, int64_t max_cuts, cudaStream_t s, int num_sms) {
+                           const int64_t* K_dev, cudaStream_t s, int num_sms) {
     if (count <= 0) return TCRNET_OK;
-    if (max_cuts > 0 && count / max_cuts < 256) {
-        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(max_cuts + 1, kWarps),
-                                                                       (int64_t)num_sms * 16));
-        k_piece_copy<T><<<(unsigned)blocks, kThreads, 0, s>>>(src, dst, count, cuts.as<int64_t>(),
-                                                              shifts.as<int64_t>(), K_dev);
-    } else {
-        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(count, 256 * 16),
-                                                                       (int64_t)num_sms * 8));
-        k_shifted_copy<T><<<(unsigned)blocks, 256, 0, s>>>(src, dst, count, cuts.as<int64_t>(),
-                                                           shifts.as<int64_t>(), K_dev);
-    }
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(count, (int64_t)kThreads * 64),
+                                                                   (int64_t)num_sms * 16));
+    k_shifted_copy<T><<<(unsigned)blocks, kThreads, 0, s>>>(src, dst, count, cuts.as<int64_t>(), shifts.as<int64_t>(),
+                                                            K_dev);
     TCR_LAUNCH_CHECK();
     return TCRNET_OK;
 }
@@ -1915,8 +1886,7 @@ tcrnet_status csr_merge(const CsrView& g, const OffT* old_off, const int32_t* de
     const int64_t n0 = g.n;
     DevBuf cuts, shifts, pos;
     TCR_CHECK(growth_cuts<OffT>(delta, old_off, new_off, n0, std::min<int64_t>(n0, n_tail), cuts, shifts, pos, s));
-    TCR_CHECK(shifted_copy<int32_t>(g.cols, cols, g.nnz, cuts, shifts, pos.as<int64_t>() + n0,
-                                    std::min<int64_t>(n0, n_tail), s, num_sms));
+    TCR_CHECK(shifted_copy<int32_t>(g.cols, cols, g.nnz, cuts, shifts, pos.as<int64_t>() + n0, s, num_sms));
     if (n_tail > 0) {
         k_ins_fill_tails<OffT><<<(unsigned)std::min<int64_t>(ceil_div(n0, 32 * kWarps), (int64_t)num_sms * 16),
                                  kThreads, 0, s>>>(old_off, new_off, uid, dcnt, dtoff, dtcols, n0, cols);
@@ -2010,8 +1980,8 @@ tcrnet_status deletion_insert(const DeletionIndex& ix, const CsrView& g, const P
         DevBuf cuts, shifts, pos;
         TCR_CHECK(growth_cuts<int64_t>(pcnt.as<int32_t>(), ix.poff, poff.as<int64_t>(), P,
                                        std::min<int64_t>(P, m + q.lensum), cuts, shifts, pos, s));
-        TCR_CHECK(shifted_copy<uint64_t>(ix.recs, recs.as<uint64_t>(), R0, cuts, shifts, pos.as<int64_t>() + P,
-                                         std::min<int64_t>(P, m + q.lensum), s, num_sms));
+        TCR_CHECK(shifted_copy<uint64_t>(ix.recs, recs.as<uint64_t>(), R0, cuts, shifts, pos.as<int64_t>() + P, s,
+                                         num_sms));
     }
     k_records<true><<<grid_for(m), kThreads, 0, s>>>(ucanon.as<Canon>() + U0, flen.as<uint8_t>(), d_F, m,
                                                      (uint32_t)P, pcur.as<int32_t>(), poff.as<int64_t>(),

@@ -184,3 +184,17 @@ def test_merged_insert_allocation_failures_keep_the_handle():
         assert failures >= 20
         assert g.stats()["merged_inserts"] == 1
         assert_same_as_fresh(g, base + add, "merged insert after failures")
+
+
+def test_merged_insert_of_resident_strings_only():
+    """Every new string equals a resident one: no fresh distinct string, no new
+    record; the copies join the member lists and the rows of their strings."""
+    base = generate_config1(5000, seed=214).strings()
+    add = base[:100] + base[:7] * 5
+    b = from_strings(add)
+    with fresh(base) as g:
+        n_unique = g.stats()["n_unique"]
+        g.insert_flat(b.chars, b.offsets)
+        st = g.stats()
+        assert st["merged_inserts"] == 1 and st["n_unique"] == n_unique
+        assert_same_as_fresh(g, base + add, "resident strings only")
