@@ -628,9 +628,47 @@ def run_ours(args):
                 if k >= 2:
                     e2e_ms.append(dt * 1e3)
             e_ms = statistics.mean(e2e_ms)
-            line["e2e"] = {"value": pairs_per_build / (e_ms / 1e3), "unit": UNIT, "ms_per_step": e_ms,
+            # pipelined: three host threads, each with its own stream and pinned
+            # result buffers, run their steps back to back, so one step's
+            # copies overlap the others' builds (the link is full duplex);
+            # whole-job throughput = all steps / wall time
+            depth = 3
+            bufs = [(torch.cuda.Stream(), off_h, cols_h, deg_h)] + [
+                (torch.cuda.Stream(), torch.empty(n + 1, dtype=torch.int32).pin_memory(),
+                 torch.empty(max(nnz, 1), dtype=torch.int32).pin_memory(),
+                 torch.empty(n, dtype=torch.int32).pin_memory()) for _ in range(depth - 1)]
+            per = max(4, args.e2e_steps // depth)
+            errors = []
+
+            def e2e_worker(k, steps):
+                try:
+                    st_k, o_k, c_k, d_k = bufs[k]
+                    for _ in range(steps):
+                        gk = tn.tcrnet_build_flat(hc, ho, 1, method=args.method, stream=st_k)
+                        gk.copy_csr(out=(o_k, c_k, d_k))
+                        gk.free()
+                except BaseException as exc:  # reported after the join
+                    errors.append(exc)
+
+            for k in range(depth):
+                e2e_worker(k, 1)  # warm each stream's path
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            workers = [threading.Thread(target=e2e_worker, args=(k, per)) for k in range(depth)]
+            for w in workers:
+                w.start()
+            for w in workers:
+                w.join()
+            torch.cuda.synchronize()
+            p_ms = 1e3 * (time.perf_counter() - t) / (per * depth)
+            if errors:
+                raise errors[0]
+            line["e2e"] = {"value": pairs_per_build / (p_ms / 1e3), "unit": UNIT, "ms_per_step": p_ms,
                            "h2d_bytes_per_step": int(rep.chars.nbytes + rep.offsets.nbytes),
-                           "d2h_bytes_per_step": int(4 * (n + 1) + 4 * nnz + 4 * n)}
+                           "d2h_bytes_per_step": int(4 * (n + 1) + 4 * nnz + 4 * n),
+                           "pipeline": f"{depth} host threads with their own streams and pinned buffers, "
+                                       f"{per * depth} steps, each step's upload, build and CSR download included",
+                           "serial_ms_per_step": e_ms, "serial_value": pairs_per_build / (e_ms / 1e3)}
         if "insert" in legs:
             # --- inserts into the resident N = 8e5 network: merged (query + network
             #     of the new strings, grown rows and index) vs rebuilt; copy-on-write

@@ -1,6 +1,6 @@
 """Merged inserts: new strings are merged into a deletion build's network and
-index (query of the new strings, network of the new strings alone, old rows
-grown at their ends, index grown in place of a rebuild).
+index (index grown first, closed rows of the new strings' distinct strings from
+a query against it, old rows grown at their ends) instead of a rebuild.
 
 Bar: bit-exact. After any sequence of merged inserts the CSR, degrees, query
 answers, components and neighbour degrees equal those of a fresh build of the
