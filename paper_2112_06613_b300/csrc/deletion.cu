@@ -1824,9 +1824,10 @@ tcrnet_status growth_cuts(const int32_t* grow, const OffT* old_off, const int64_
 
 // dst[t + shifts[k(t)]] = src[t], k(t) = number of cuts <= t (cuts sorted,
 // possibly equal). Each warp moves one contiguous range: it finds the piece of
-// its first element by a 32-way search over the cuts, then walks the pieces of
-// its range in order, copying each with all lanes (coalesced), whether the
-// pieces are long (few rows grow) or a few dozen elements (many do).
+// its first element by a 32-way search over the cuts, then copies 32
+// consecutive elements per instruction (coalesced), each lane advancing the
+// piece index to its own element, whether the pieces are long (few rows grow)
+// or a few dozen elements (many do).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_shifted_copy(const T* __restrict__ src, T* __restrict__ dst,
                                                            int64_t count, const int64_t* __restrict__ cuts,
@@ -1855,14 +1856,36 @@ __global__ void __launch_bounds__(kThreads) k_shifted_copy(const T* __restrict__
         lo = nlo;
     }
     if (hi > lo) lo += __popc(__ballot_sync(kFull, lo + lane < hi && cuts[lo + lane] <= b0));
+    // 128 consecutive elements per step (loads first); each lane advances a copy
+    // of the warp's piece index to its own element, lane 31's result carries on
     int64_t k = lo;
-    int64_t pos = b0;
-    while (pos < b1) {
-        while (k < K && cuts[k] <= pos) ++k;
-        const int64_t end = (k < K && cuts[k] < b1) ? cuts[k] : b1;
-        const int64_t sh = shifts[k];
-        for (int64_t t = pos + lane; t < end; t += 32) dst[t + sh] = src[t];
-        pos = end;
+    for (int64_t t0 = b0; t0 < b1; t0 += 128) {
+        T v[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int64_t t = t0 + 32 * r + lane;
+            if (t < b1) v[r] = src[t];
+        }
+        while (k < K && cuts[k] <= t0) ++k;
+        if (k >= K || cuts[k] >= t0 + 128) {  // the whole step lies in piece k
+            const int64_t sh = shifts[k];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int64_t t = t0 + 32 * r + lane;
+                if (t < b1) dst[t + sh] = v[r];
+            }
+            continue;
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int64_t t = t0 + 32 * r + lane;
+            int64_t kl = k;
+            if (t < b1) {
+                while (kl < K && cuts[kl] <= t) ++kl;
+                dst[t + shifts[kl]] = v[r];
+            }
+            k = __shfl_sync(kFull, kl, 31);
+        }
     }
 }
 
