@@ -850,32 +850,62 @@ __global__ void k_expand(const int32_t* __restrict__ uid, int64_t n, const int64
                 if (x != me && q < (int)D - 1) row[q++] = x;
             }
         }
+        // long rows, one per step with the whole warp: the first 128 entries of
+        // the next row are loaded before this row's are stored (eight loads per
+        // lane in flight)
         uint32_t todo = __ballot_sync(kFull, D > kLaneRow + 1);
-        while (todo) {
-            const int j = __ffs(todo) - 1;
+        int j = todo ? __ffs(todo) - 1 : -1;
+        int64_t js0 = 0, jo = 0;
+        int iD = 0;
+        int32_t x[4];
+        auto fetch = [&](int jj, int64_t& s0_, int64_t& o_, int& d_, int32_t (&v)[4]) {
+            s0_ = __shfl_sync(kFull, s0, jj);
+            d_ = (int)__shfl_sync(kFull, D, jj);
+            o_ = __shfl_sync(kFull, o, jj);
+            const int32_t me_ = (int32_t)(r0 + jj);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int k = lane + 32 * t;
+                v[t] = k < d_ ? S[s0_ + k] : me_;
+            }
+        };
+        if (j >= 0) fetch(j, js0, jo, iD, x);
+        while (j >= 0) {
             todo &= todo - 1;
-            const int64_t js0 = __shfl_sync(kFull, s0, j);
-            const int64_t jD = __shfl_sync(kFull, D, j);
-            const int64_t jo = __shfl_sync(kFull, o, j);
+            const int nj = todo ? __ffs(todo) - 1 : -1;
+            int64_t ns0 = 0, no = 0;
+            int nD = 0;
+            int32_t nx[4];
+            if (nj >= 0) fetch(nj, ns0, no, nD, nx);
             const int32_t me = (int32_t)(r0 + j);
-            const int32_t* su = S + js0;
             int32_t* row = cols + jo;
-            // four loads per lane in flight before their stores
-            const int iD = (int)jD;
-            for (int k0 = 0; k0 < iD; k0 += 128) {
-                int32_t x[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int k = lane + 32 * t;
+                const int q = k - (x[t] > me ? 1 : 0);
+                if (x[t] != me && q < iD - 1) row[q] = x[t];  // q < D - 1 always holds when i is in S_u
+            }
+            const int32_t* su = S + js0;
+            for (int k0 = 128; k0 < iD; k0 += 128) {  // the rest of a row longer than 128
+                int32_t y[4];
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     const int k = k0 + lane + 32 * t;
-                    x[t] = k < iD ? su[k] : me;
+                    y[t] = k < iD ? su[k] : me;
                 }
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     const int k = k0 + lane + 32 * t;
-                    const int q = k - (x[t] > me ? 1 : 0);
-                    if (x[t] != me && q < iD - 1) row[q] = x[t];  // q < D - 1 always holds when i is in S_u
+                    const int q = k - (y[t] > me ? 1 : 0);
+                    if (y[t] != me && q < iD - 1) row[q] = y[t];
                 }
             }
+            j = nj;
+            js0 = ns0;
+            jo = no;
+            iD = nD;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) x[t] = nx[t];
         }
     }
 }
