@@ -841,13 +841,21 @@ __global__ void k_expand(const int32_t* __restrict__ uid, int64_t n, const int64
             o = off[my];
         }
         if (D >= 2 && D <= kLaneRow + 1) {
+            // S_u is sorted and holds i: an entry above i moves one slot left,
+            // so the slots are known and eight loads go out before their stores
             const int32_t me = (int32_t)my;
             const int32_t* su = S + s0;
             int32_t* row = cols + o;
-            int q = 0;
-            for (int k = 0; k < (int)D; ++k) {
-                const int32_t x = su[k];
-                if (x != me && q < (int)D - 1) row[q++] = x;
+            const int iD = (int)D;
+            for (int k0 = 0; k0 < iD; k0 += 8) {
+                int32_t y[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) y[t] = k0 + t < iD ? su[k0 + t] : me;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int q = k0 + t - (y[t] > me ? 1 : 0);
+                    if (y[t] != me && q < iD - 1) row[q] = y[t];
+                }
             }
         }
         // long rows, one per step with the whole warp: the first 128 entries of
