@@ -795,14 +795,20 @@ k_closed_edges(const int2* __restrict__ edges, int64_t seg_cap, const unsigned l
         a = (t & 1) ? uv.y : uv.x;  // list owner
         b = (t & 1) ? uv.x : uv.y;  // neighbour whose members are appended
         mb = umult[b];
+        // a short member list is loaded before the slot atomic returns
+        const int32_t* rb = members + mem_off[b];
+        int32_t mv[kShort];
+#pragma unroll
+        for (int y = 0; y < kShort; ++y) mv[y] = y < mb ? rb[y] : 0;
         o = uoff[a] + atomicAdd(&ucur[a], mb);
         if (o + mb > uoff[a + 1]) {
             atomicExch(err, 1);
             mb = 0;
         }
         if (mb <= kShort) {
-            const int32_t* rb = members + mem_off[b];
-            for (int32_t y = 0; y < mb; ++y) S[o + y] = rb[y];
+#pragma unroll
+            for (int y = 0; y < kShort; ++y)
+                if (y < mb) S[o + y] = mv[y];
         }
     }
     unsigned longs = __ballot_sync(kFull, have && mb > kShort);
