@@ -58,9 +58,9 @@ INT_LANES_PER_SM = 128
 # from one ncu capture of the current kernels (profiles/k_join_small_n800000.md,
 # profiles/k_records_expand_n800000.md); None where no capture covers the phase.
 PHASE_TRAFFIC_N800000 = {
-    "join_weigh": 100.13e6 + 5.81e6 + 21.85e6 + 0.03e6,
-    "records": 21.91e6 + 86.58e6 + 105.56e6,
-    "expand": 83.94e6 + 200.01e6,
+    "join_weigh": 100.13e6 + 6.18e6 + 21.85e6 + 0.03e6,
+    "records": 21.91e6 + 86.48e6 + 105.33e6,
+    "expand": 84.22e6 + 198.65e6,
 }
 
 LEGS = ("tile", "query", "e2e", "insert", "analytics", "lmax2", "batched", "serving", "cpu")
