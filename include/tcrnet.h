@@ -230,7 +230,12 @@ tcrnet_status tcrnet_query(tcrnet_handle h, const char *const *queries, int64_t 
  * and query index describe the grown repertoire, exactly as a fresh build of
  * the concatenated input would (node ids of existing strings are unchanged);
  * previously returned device pointers (tcrnet_csr_device) become invalid. The
- * update is computed on the device from the handle's packed strings. On failure
+ * update is computed on the device from the handle's packed strings: a deletion
+ * build (l_max = 1) merges an insert of at most n/32 strings into its network
+ * and query index (the new strings' closed neighbourhoods from a query of the
+ * grown index, old rows grown at their ends); other inserts rebuild the grown
+ * repertoire (options.insert_rebuild forces that). Both give the network of a
+ * fresh build of the concatenation. On failure
  * (bad string: its index within the new batch is reported) the handle keeps its
  * previous network. Not for query-result handles (ESTATE). Callers must not use
  * the handle from another thread during the call.
