@@ -16,9 +16,11 @@
 //                       65..256 and 257..512 are listed and sorted by their own
 //                       kernels, so wide register arrays do not lower the
 //                       occupancy of the kernel that sorts the many short rows.
-//   513 .. 16384:       one 1024-thread block, shared-memory bitonic network
-//                       (such rows are few; one warp per row was the slowest
-//                       part of the sort).
+//   513 .. 16384:       shared-memory bitonic network with the stages of
+//                       partner distance < 256 in registers (warp chunks of 8
+//                       values per lane): rows up to 4096 by a 256-thread group
+//                       (four per block, named barriers), longer ones by the
+//                       1024-thread block.
 //   > 16384:            one block; 16384-value chunks sorted in shared memory,
 //                       then pairwise merges through a scratch buffer where each
 //                       value finds its output slot by binary search in the
@@ -43,29 +45,6 @@ __device__ __forceinline__ int next_pow2(int x) {
     int p = 1;
     while (p < x) p <<= 1;
     return p;
-}
-
-// Bitonic network over s[0, P) by `nthreads` cooperating threads with index t;
-// `sync` orders the stages. P and j are powers of two, so the pair index
-// arithmetic is shifts and masks.
-template <typename Sync>
-__device__ __forceinline__ void bitonic_smem(int32_t* s, int P, int t, int nthreads, Sync sync) {
-    for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            const int lj = __ffs(j) - 1;
-            for (int i = t; i < (P >> 1); i += nthreads) {
-                const int lo = ((i >> lj) << (lj + 1)) | (i & (j - 1));
-                const int hi = lo + j;
-                const bool up = (lo & k) == 0;
-                const int32_t x = s[lo], y = s[hi];
-                if ((x > y) == up) {
-                    s[lo] = y;
-                    s[hi] = x;
-                }
-            }
-            sync();
-        }
-    }
 }
 
 __device__ __forceinline__ void cmp_swap(int32_t& a, int32_t& b) {
@@ -140,6 +119,90 @@ __device__ __forceinline__ void warp_sort_regs(int32_t* __restrict__ row, int le
     }
 }
 
+// Bitonic stages on one warp's chunk of kChunkVals values of a shared-memory
+// network (positions c0 .. c0 + kChunkVals - 1, held K per lane at lane * K +
+// r): for each merge size k from k_first to k_last, the stages with partner
+// distance below the chunk size. Directions come from the global position, so
+// chunks of one network cooperate without block barriers for those stages.
+constexpr int kChunkK = 8;
+constexpr int kChunkVals = 32 * kChunkK;
+
+template <int J>
+__device__ __forceinline__ void chunk_reg_stage(int32_t (&v)[kChunkK], int pos0, int k) {
+#pragma unroll
+    for (int r = 0; r < kChunkK; ++r) {
+        if ((r & J) == 0) {
+            const int r2 = r | J;
+            const bool up = ((pos0 + r) & k) == 0;
+            const int32_t a = v[r], b = v[r2];
+            const int32_t mn = min(a, b), mx = max(a, b);
+            v[r] = up ? mn : mx;
+            v[r2] = up ? mx : mn;
+        }
+    }
+}
+
+__device__ __forceinline__ void chunk_stages(int32_t* s, int c0, int k_first, int k_last, int lane) {
+    constexpr int K = kChunkK;
+    static_assert(K == 8, "register stages are written out for 8 values per lane");
+    int32_t v[K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) v[r] = s[c0 + lane * K + r];
+    for (int k = k_first; k <= k_last; k <<= 1) {
+        for (int j = (k >> 1) < (kChunkVals >> 1) ? (k >> 1) : (kChunkVals >> 1); j > 0; j >>= 1) {
+            if (j == 4) chunk_reg_stage<4>(v, c0 + lane * K, k);
+            else if (j == 2) chunk_reg_stage<2>(v, c0 + lane * K, k);
+            else if (j == 1) chunk_reg_stage<1>(v, c0 + lane * K, k);
+            else {
+                const int jl = j / K;
+                const bool lower = (lane & jl) == 0;
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    const int32_t p = __shfl_xor_sync(kFull, v[r], jl);
+                    const bool up = ((c0 + lane * K + r) & k) == 0;
+                    v[r] = (lower == up) ? min(v[r], p) : max(v[r], p);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < K; ++r) s[c0 + lane * K + r] = v[r];
+}
+
+// Bitonic sort of s[0, P) (P a power of two, P >= kChunkVals) by nt threads
+// (t = index among them, a whole number of warps) that meet at bar(): stages
+// whose partners are a chunk or more apart go through shared memory with a
+// barrier each; all shorter ones run inside the warps' chunks in registers.
+template <typename Bar>
+__device__ __forceinline__ void group_bitonic(int32_t* s, int P, int t, int nt, Bar bar) {
+    const int lane = t & 31, warp = t >> 5, nwarps = nt >> 5;
+    const int nchunks = P / kChunkVals;
+    for (int c = warp; c < nchunks; c += nwarps) chunk_stages(s, c * kChunkVals, 2, kChunkVals, lane);
+    bar();
+    for (int k = 2 * kChunkVals; k <= P; k <<= 1) {
+        for (int j = k >> 1; j >= kChunkVals; j >>= 1) {
+            const int lj = __ffs(j) - 1;
+            for (int i = t; i < (P >> 1); i += nt) {
+                const int lo = ((i >> lj) << (lj + 1)) | (i & (j - 1));
+                const int hi = lo + j;
+                const bool up = (lo & k) == 0;
+                const int32_t x = s[lo], y = s[hi];
+                if ((x > y) == up) {
+                    s[lo] = y;
+                    s[hi] = x;
+                }
+            }
+            bar();
+        }
+        for (int c = warp; c < nchunks; c += nwarps) chunk_stages(s, c * kChunkVals, k, k, lane);
+        bar();
+    }
+}
+
+__device__ __forceinline__ void block_bitonic(int32_t* s, int P) {
+    group_bitonic(s, P, threadIdx.x, kBlockThreads, [] __device__() { __syncthreads(); });
+}
+
 // Rows of at most 64 values; longer rows are listed for the kernels below.
 // A warp takes 32 consecutive rows: each lane sorts its own row when it has at
 // most 8 values, then the warp sorts the rows of 9..64 values one by one.
@@ -206,23 +269,48 @@ k_sort_warp_mid(const int64_t* __restrict__ off, int32_t* __restrict__ cols, con
     }
 }
 
+// Rows of 513 .. kGroupCap values: four groups of 256 threads per block, each
+// on its own row and shared-memory quarter (named barriers), so a row of ~1,000
+// values does not leave most of a 1,024-thread block idle; longer rows: the
+// whole block; rows above kBlockCap are listed for the chunked sort.
+constexpr int kGroupThreads = 256;
+constexpr int kGroups = kBlockThreads / kGroupThreads;
+constexpr int kGroupCap = kBlockCap / kGroups;
+
 __global__ void __launch_bounds__(kBlockThreads)
 k_sort_block(const int64_t* __restrict__ off, int32_t* __restrict__ cols, const int32_t* __restrict__ rows,
              const int* __restrict__ nrows_ptr, int32_t* __restrict__ huge, int* __restrict__ nhuge) {
     extern __shared__ int32_t sbuf[];
     const int nrows = *nrows_ptr;
+    const int g = threadIdx.x / kGroupThreads, tg = threadIdx.x % kGroupThreads;
+    int32_t* gs = sbuf + g * kGroupCap;
+    auto gbar = [g] __device__() { asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kGroupThreads) : "memory"); };
+    for (int k = blockIdx.x * kGroups + g; k < nrows; k += gridDim.x * kGroups) {
+        const int64_t r = rows[k];
+        const int64_t base = off[r];
+        const int64_t len = off[r + 1] - base;
+        if (len > kGroupCap) continue;  // the whole block takes it below
+        const int P = max(next_pow2((int)len), kChunkVals);
+        for (int i = tg; i < P; i += kGroupThreads) gs[i] = i < len ? cols[base + i] : kInf;
+        gbar();
+        group_bitonic(gs, P, tg, kGroupThreads, gbar);
+        for (int i = tg; i < len; i += kGroupThreads) cols[base + i] = gs[i];
+        gbar();
+    }
+    __syncthreads();
     for (int k = blockIdx.x; k < nrows; k += gridDim.x) {
         const int64_t r = rows[k];
         const int64_t base = off[r];
         const int64_t len = off[r + 1] - base;
+        if (len <= kGroupCap) continue;
         if (len > kBlockCap) {
             if (threadIdx.x == 0) huge[atomicAdd(nhuge, 1)] = (int32_t)r;
             continue;
         }
-        const int P = next_pow2((int)len);
+        const int P = max(next_pow2((int)len), kChunkVals);
         for (int i = threadIdx.x; i < P; i += kBlockThreads) sbuf[i] = i < len ? cols[base + i] : kInf;
         __syncthreads();
-        bitonic_smem(sbuf, P, threadIdx.x, kBlockThreads, [] __device__() { __syncthreads(); });
+        block_bitonic(sbuf, P);
         for (int i = threadIdx.x; i < len; i += kBlockThreads) cols[base + i] = sbuf[i];
         __syncthreads();
     }
@@ -234,10 +322,10 @@ k_sort_chunks(int32_t* __restrict__ v, int64_t len) {
     extern __shared__ int32_t sbuf[];
     const int64_t c0 = (int64_t)blockIdx.x * kBlockCap;
     const int64_t cl = (len - c0) < (int64_t)kBlockCap ? (len - c0) : (int64_t)kBlockCap;
-    const int P = next_pow2((int)cl);
+    const int P = max(next_pow2((int)cl), kChunkVals);
     for (int i = threadIdx.x; i < P; i += kBlockThreads) sbuf[i] = i < cl ? v[c0 + i] : kInf;
     __syncthreads();
-    bitonic_smem(sbuf, P, threadIdx.x, kBlockThreads, [] __device__() { __syncthreads(); });
+    block_bitonic(sbuf, P);
     for (int i = threadIdx.x; i < cl; i += kBlockThreads) v[c0 + i] = sbuf[i];
 }
 
