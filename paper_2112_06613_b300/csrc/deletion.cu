@@ -900,18 +900,28 @@ __global__ void k_expand(const int32_t* __restrict__ uid, int64_t n, const int64
                 if (x[t] != me && q < iD - 1) row[q] = x[t];  // q < D - 1 always holds when i is in S_u
             }
             const int32_t* su = S + js0;
-            for (int k0 = 128; k0 < iD; k0 += 128) {  // the rest of a row longer than 128
+            if (iD > 128) {  // the rest of a long row: each chunk's loads go out before the previous chunk's stores
                 int32_t y[4];
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    const int k = k0 + lane + 32 * t;
+                    const int k = 128 + lane + 32 * t;
                     y[t] = k < iD ? su[k] : me;
                 }
+                for (int k0 = 128; k0 < iD; k0 += 128) {
+                    int32_t z[4];
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int k = k0 + lane + 32 * t;
-                    const int q = k - (y[t] > me ? 1 : 0);
-                    if (y[t] != me && q < iD - 1) row[q] = y[t];
+                    for (int t = 0; t < 4; ++t) {
+                        const int k = k0 + 128 + lane + 32 * t;
+                        z[t] = k < iD ? su[k] : me;
+                    }
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int k = k0 + lane + 32 * t;
+                        const int q = k - (y[t] > me ? 1 : 0);
+                        if (y[t] != me && q < iD - 1) row[q] = y[t];
+                    }
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) y[t] = z[t];
                 }
             }
             j = nj;
