@@ -468,3 +468,29 @@ def test_flat_offsets_checked_on_the_device(method):
     with tn.tcrnet_build_flat(chars, np.array([2, 7, 12, 16], np.int64), 1, method=method) as g:
         off, cols, _ = g.copy_csr()
     assert list(np.asarray(off)) == [0, 2, 3, 4] and list(cols) == [1, 2, 0, 0]
+
+
+@pytest.mark.parametrize("method", ["deletion", "tile"])
+def test_long_rows_of_every_sort_class(method):
+    """Cliques of identical strings joined to their one-substitution neighbours
+    give rows of known content in each row-sort class (warp registers, 256-thread
+    groups, whole block, chunked merge): row i = every node of the clique and of
+    the adjacent clique except i, ascending."""
+    sizes = [(300, 250), (1500, 900), (3000, 2500), (9000, 1000), (16000, 1500)]
+    strs, groups = [], []
+    for g, (a, b) in enumerate(sizes):
+        base = "CASS" + ALPHABET[g] * 6 + "QYF"
+        other = base[:5] + "W" + base[6:]  # one substitution away
+        lo = len(strs)
+        strs += [base] * a + [other] * b
+        groups.append((lo, lo + a + b))
+    rep = from_strings(strs)
+    with tn.tcrnet_build_flat(rep.chars, rep.offsets, 1, method=method) as g:
+        off, cols, deg = g.copy_csr()
+    off = np.asarray(off, dtype=np.int64)
+    check_invariants(off, cols, deg, len(strs))
+    for lo, hi in groups:
+        ids = np.arange(lo, hi, dtype=np.int32)
+        for i in (lo, lo + 1, (lo + hi) // 2, hi - 2, hi - 1):
+            row = cols[off[i]:off[i + 1]]
+            assert np.array_equal(row, ids[ids != i]), (method, lo, hi, i)
