@@ -10,16 +10,19 @@ requests keep arriving:
 - slots: `slots` worker threads, each with its own CUDA streams (queries on a
   high-priority stream, inserts on a low-priority one), so admitted requests
   overlap on the device (the C library releases the GIL);
-- inserts are copy-on-write (`tcrnet_extend`): the grown repertoire is built
-  into a new handle while queries keep running on the current one; the new
-  handle then replaces it (the caller's Graph adopts it) and the old one is
+- inserts are copy-on-write (`tcrnet_extend`): the grown network (merged
+  from the current one for small inserts, else rebuilt) goes into a new handle
+  while queries keep running on the current one; the new handle then replaces it (the caller's Graph adopts it) and the old one is
   freed after its last running query. Inserts apply one at a time in arrival
   order; queries that start before an insert's swap see the previous
   repertoire, later ones the grown one; each request records the repertoire
   version it ran on;
 - admission by memory: a request starts only when its estimated device memory
   fits in the free HBM reported by the driver minus a reserve (otherwise it
-  waits until running requests release theirs).
+  waits until running requests release theirs);
+- answers are copied into per-slot pinned host buffers allocated once, then
+  into each request's own arrays (a copy to pageable memory of a long answer
+  goes through the driver's small staging buffers).
 
 All computation happens in the CUDA library; this module only schedules calls.
 """
@@ -141,8 +144,9 @@ class ServingEngine:
         if kind == "query":
             # packed strings, records, counts, offsets, and the result lists (x4 margin)
             return int(strings * (96 + 4 * 4 * (mean_deg + 1)))
-        # an insert rebuilds the grown repertoire: scratch about 600 B per string
-        # plus the new CSR
+        # an insert builds the grown network into a new handle: at most about
+        # 600 B of scratch per string (a rebuild; a merge needs less) plus the
+        # new CSR
         return int((n + strings) * 600 + 4 * (nnz * (n + strings) / max(n, 1)))
 
     def _admissible(self, need: int) -> bool:
