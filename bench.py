@@ -753,9 +753,20 @@ def run_ours(args):
                 g2 = tn.tcrnet_build_flat(c2, o2, 2, stream=stream, profile=True)
                 st2 = g2.stats()
                 g2.free()
+                # per candidate pair the bit-parallel recurrence runs one step per
+                # letter of the row string, 17 integer operations per step (mask
+                # lookup, carry add, 3-input logic, shifts, score update): an
+                # estimate from the mean length, against the issue ceiling
+                mean_len = float(np.diff(r2.offsets).mean())
+                ops = st2["candidate_pairs"] * mean_len * 17.0
+                ach = ops / (st2["ms_count"] / 1e3)
+                peak = SMS * INT_LANES_PER_SM * sm_max_nominal * 1e6
                 lm2[str(n2)] = {"build_ms": st2["ms_total"], "count_pass_ms": st2["ms_count"],
                                 "candidate_pairs": st2["candidate_pairs"], "nnz": st2["nnz"],
-                                "candidate_pairs_per_s": st2["candidate_pairs"] / (st2["ms_count"] / 1e3)}
+                                "candidate_pairs_per_s": st2["candidate_pairs"] / (st2["ms_count"] / 1e3),
+                                "roofline": {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12,
+                                             "unit": "Tops/s", "frac": ach / peak,
+                                             "ops_per_pair": f"17 x mean length ({mean_len:.2f}), estimate"}}
             line["lmax2"] = lm2
         if "batched" in legs:
             # --- batched: uneven repertoires in one pass vs one plain build each
