@@ -198,3 +198,31 @@ def test_merged_insert_of_resident_strings_only():
         st = g.stats()
         assert st["merged_inserts"] == 1 and st["n_unique"] == n_unique
         assert_same_as_fresh(g, base + add, "resident strings only")
+
+
+def test_random_merged_inserts_over_a_tiny_alphabet():
+    """Strings of 1..7 letters over three letters: many duplicates, runs and
+    hubs. Random sequences of merged inserts, each compared with a fresh build."""
+    rng = np.random.default_rng(215)
+
+    def draw(k):
+        lens = rng.integers(1, 8, size=k)
+        return ["".join(rng.choice(list("ACD"), size=int(L))) for L in lens]
+
+    for trial in range(6):
+        base = draw(2400)
+        strs = list(base)
+        with fresh(base) as g:
+            for step in range(5):
+                add = draw(int(rng.integers(1, len(strs) // 32 + 1)))
+                b = from_strings(add)
+                g.insert_flat(b.chars, b.offsets)
+                strs += add
+                assert g.stats()["merged_inserts"] == step + 1
+            assert_same_as_fresh(g, strs, f"tiny alphabet trial {trial}", oracle_check=(trial == 0))
+            q = from_strings(draw(200))
+            with g.query_flat(q.chars, q.offsets) as r:
+                qo, qc, _ = csr_of(r)
+            full = from_strings(strs)
+            ro, rc = oracle.neighbors(full.chars, full.offsets, q.chars, q.offsets, max_dist=1)
+            assert_csr_equal(qo, qc, ro, rc, f"queries, trial {trial}")
