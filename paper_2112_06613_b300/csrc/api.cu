@@ -397,6 +397,14 @@ tcrnet_status flatten(const char* const* seqs, int64_t n, std::vector<uint8_t>& 
     return TCRNET_OK;
 }
 
+// The method AUTO stands for: the deletion method from its size cut-over on
+// (l_max <= 2), else the all-pairs kernels.
+int auto_method(int64_t n, int32_t T) {
+    if (T <= 1 && n >= kAutoDeletionMinN) return TCRNET_METHOD_DELETION;
+    if (T == 2 && n >= kAutoDeletion2MinN) return TCRNET_METHOD_DELETION;
+    return TCRNET_METHOD_TILE;
+}
+
 // Network of an encoded, bucketed repertoire (pk) into handle h by the method
 // the options select: CSR, degree, resident repertoire and, for the deletion
 // method, the query index.
@@ -404,8 +412,7 @@ tcrnet_status build_from_packed(tcrnet_graph* h, Packed& pk, int64_t n, int32_t 
                                 Phases& ph, cudaStream_t s, int sms, bool keep_index = true) {
     tcrnet_status st = TCRNET_OK;
     int method = opt.method;
-    if (method == TCRNET_METHOD_AUTO)
-        method = (n >= kAutoDeletionMinN && T <= 1) ? TCRNET_METHOD_DELETION : TCRNET_METHOD_TILE;
+    if (method == TCRNET_METHOD_AUTO) method = auto_method(n, T);
     h->stats.method = method;
     for (int L = 0; L < kMaxLen + 2; ++L) h->bucket_off[L] = pk.bucket_off[L];
     if (n == 0) {
@@ -467,7 +474,7 @@ tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n
     if (T < 0) return TCRNET_EINVAL;
     if (opt.method < TCRNET_METHOD_AUTO || opt.method > TCRNET_METHOD_DELETION) return TCRNET_EINVAL;
     if (opt.partition_target != 0 && (opt.partition_target < 4 || opt.partition_target > 128)) return TCRNET_EINVAL;
-    if (T > 1 && opt.method == TCRNET_METHOD_DELETION) return TCRNET_ENOTSUP;  // deletion join: l_max <= 1
+    if (T > 2 && opt.method == TCRNET_METHOD_DELETION) return TCRNET_ENOTSUP;  // deletion method: l_max <= 2
     if (rep_off) {
         // batched: one deletion-method pass over all repertoires
         if (T > 1 || opt.method == TCRNET_METHOD_TILE) return TCRNET_ENOTSUP;
@@ -477,7 +484,7 @@ tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n
         opt.method = TCRNET_METHOD_DELETION;
     }
     if (opt.method == TCRNET_METHOD_AUTO)  // decided before packing: only the tile method buckets
-        opt.method = (n >= kAutoDeletionMinN && T <= 1) ? TCRNET_METHOD_DELETION : TCRNET_METHOD_TILE;
+        opt.method = auto_method(n, T);
     DeviceGuard dg;
     TCR_CHECK(dg.set(opt.device));
     int dev = 0;

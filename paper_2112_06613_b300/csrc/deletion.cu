@@ -723,6 +723,191 @@ k_join_fallback(const int32_t* __restrict__ fb_list, const int* __restrict__ fb_
     }
 }
 
+// ---- 3'. l_max = 2: candidates from shared variants of up to two deletions --
+//
+// lev(a, b) <= 2 is at most two edits; a substitution at position i is the
+// deletion of i from both strings and an insertion into one the deletion of a
+// letter of the other, so a and b have equal variants with at most two
+// deletions each. Every pair of distinct strings with a variant of equal
+// 32-bit hash in the same partition is a candidate (a hash collision only
+// adds a candidate); candidates are deduplicated and each one is checked with
+// the exact bit-parallel distance, so the edges are exact. Deletions inside a
+// run of equal letters start at the run (two from one run: its first two),
+// which drops most repeated variants of a string.
+
+// fn(v) for the full string, every run-start deletion and every canonical
+// pair of deletions of c (length L).
+template <typename Fn>
+__device__ __forceinline__ void for_variants2(const Canon& c, int L, Fn fn) {
+    fn(c);
+    for (int p = 0; p < L; ++p) {
+        if (!run_start(c, p)) continue;
+        const Canon d = delete_at(c, p);
+        fn(d);
+        for (int q = p + 1; q < L; ++q)
+            if (q == p + 1 || run_start(c, q)) fn(delete_at(d, q - 1));  // position q of c is q - 1 of d
+    }
+}
+
+// Variants per distinct string (their sum sizes the records).
+__global__ void k_var2_count(const Canon* __restrict__ ucanon, const uint8_t* __restrict__ ulen,
+                             const int64_t* __restrict__ U_ptr, int64_t n, unsigned long long* __restrict__ total) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int cnt = 0;
+    if (u < n && u < *U_ptr) {
+        const Canon c = load_canon(ucanon + u);
+        const int L = ulen[u];
+        cnt = 1;
+        for (int p = 0; p < L; ++p) {
+            if (!run_start(c, p)) continue;
+            ++cnt;
+            for (int q = p + 1; q < L; ++q) cnt += (q == p + 1 || run_start(c, q)) ? 1 : 0;
+        }
+    }
+    // one atomic per warp
+    int x = cnt;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(kFull, x, d);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(total, (unsigned long long)x);
+}
+
+// Records (low 32 hash bits | u) of every variant: count per partition, or
+// scatter at slots from per-partition cursors.
+template <bool SCATTER>
+__global__ void k_var2_records(const Canon* __restrict__ ucanon, const uint8_t* __restrict__ ulen,
+                               const int64_t* __restrict__ U_ptr, int64_t n, uint32_t P, int32_t* __restrict__ pcnt,
+                               const int64_t* __restrict__ poff, uint64_t* __restrict__ recs) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n || u >= *U_ptr) return;
+    const Canon c = load_canon(ucanon + u);
+    for_variants2(c, ulen[u], [&](const Canon& v) {
+        const uint64_t h = hash_canon(v);
+        const uint32_t pid = part_of(h, P);
+        if constexpr (!SCATTER) {
+            atomicAdd(&pcnt[pid], 1);
+        } else {
+            recs[poff[pid] + atomicAdd(&pcnt[pid], 1)] = (h << 32) | (uint64_t)u;
+        }
+    });
+}
+
+// Candidate pairs (u < v) of every partition: records of equal hash and
+// different strings. A warp per partition compares 32 records with 32 at a
+// time. COUNT adds the candidates to *count, WRITE appends them at *cursor.
+template <bool WRITE>
+__global__ void __launch_bounds__(kThreads)
+k_var2_pairs(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __restrict__ recs,
+             unsigned long long* __restrict__ count, unsigned long long* __restrict__ cursor, int2* __restrict__ out,
+             int64_t cap) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long mine = 0;
+    for (int64_t pid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; pid < P; pid += nw) {
+        const int64_t b0 = poff[pid], b1 = poff[pid + 1];
+        if (b1 - b0 < 2) continue;
+        for (int64_t i0 = b0; i0 < b1; i0 += 32) {
+            const int64_t i = i0 + lane;
+            const uint64_t ri = i < b1 ? recs[i] : ~0ull;
+            for (int64_t j0 = i0; j0 < b1; j0 += 32) {
+                const uint64_t rj = j0 + lane < b1 ? recs[j0 + lane] : ~0ull;
+                for (int t = 0; t < 32; ++t) {
+                    const uint64_t r = __shfl_sync(kFull, rj, t);
+                    const int64_t j = j0 + t;
+                    const bool hit = i < b1 && j < b1 && j > i && (r >> 32) == (ri >> 32) &&
+                                     (uint32_t)r != (uint32_t)ri;
+                    if constexpr (!WRITE) {
+                        mine += hit ? 1 : 0;
+                    } else {
+                        warp_append_pairs(cursor, hit ? 1 : 0, [&](long long slot) {
+                            if (slot < cap) {
+                                const int32_t a = (int32_t)(uint32_t)ri, b = (int32_t)(uint32_t)r;
+                                out[slot] = a < b ? make_int2(a, b) : make_int2(b, a);
+                            }
+                        });
+                    }
+                }
+            }
+        }
+    }
+    if constexpr (!WRITE) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) mine += __shfl_xor_sync(kFull, mine, d);
+        if (lane == 0 && mine) atomicAdd(count, mine);
+    }
+}
+
+// Candidates grouped by their smaller string: count, then place.
+__global__ void k_cand_rows(const int2* __restrict__ cand, int64_t nc, const int64_t* __restrict__ coff,
+                            int32_t* __restrict__ ccur, int32_t* __restrict__ ccols, bool place) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nc; e += (int64_t)gridDim.x * blockDim.x) {
+        const int2 c = cand[e];
+        if (!place) atomicAdd(&ccur[c.x], 1);
+        else ccols[coff[c.x] + atomicAdd(&ccur[c.x], 1)] = c.y;
+    }
+}
+
+// Each distinct candidate (row u sorted, repeats adjacent) checked with the
+// bit-parallel distance (Myers 1999, Hyyro 2001: u's letter masks in shared
+// memory, v as the text); pairs within l_max = 2 become edges {u, v} with their
+// weights, appended at *ecur.
+__global__ void __launch_bounds__(kThreads)
+k_cand_verify(const int64_t* __restrict__ coff, const int32_t* __restrict__ ccols, const int64_t* __restrict__ U_ptr,
+              const Canon* __restrict__ ucanon, const uint8_t* __restrict__ ulen, Weigh weigh, int2* __restrict__ edges,
+              unsigned long long* __restrict__ ecur, int64_t cap, int* __restrict__ err) {
+    __shared__ uint64_t speq[kWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t U = *U_ptr;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < U; u += nw) {
+        const int64_t a = coff[u], b = coff[u + 1];
+        if (a == b) continue;
+        const Canon cu = load_canon(ucanon + u);
+        const int Lu = ulen[u];
+        // letter masks of u: lane k builds the mask of letter k + 1
+        uint64_t m = 0;
+        for (int k = 0; k < Lu; ++k)
+            if (code_at(cu, k) == (uint32_t)(lane + 1)) m |= 1ull << k;
+        speq[w][lane] = m;
+        __syncwarp();
+        const uint64_t top = 1ull << (Lu - 1);
+        for (int64_t e0 = a; e0 < b; e0 += 32) {
+            const int64_t e = e0 + lane;
+            bool edge = false;
+            int32_t v = -1;
+            if (e < b) {
+                v = ccols[e];
+                if (e == a || ccols[e - 1] != v) {  // first of its repeats
+                    const Canon cv = load_canon(ucanon + v);
+                    const int Lv = ulen[v];
+                    if (Lv - Lu <= 2 && Lu - Lv <= 2) {
+                        uint64_t vp = ~0ull, vn = 0;
+                        int score = Lu;
+                        for (int k = 0; k < Lv; ++k) {
+                            const uint64_t eq = speq[w][code_at(cv, k) - 1];
+                            const uint64_t xv = eq | vn;
+                            const uint64_t xh = (((eq & vp) + vp) ^ vp) | eq;
+                            uint64_t hp = vn | ~(xh | vp);
+                            uint64_t hn = vp & xh;
+                            score += ((hp & top) ? 1 : 0) - ((hn & top) ? 1 : 0);
+                            hp = (hp << 1) | 1ull;
+                            hn <<= 1;
+                            vp = hn | ~(xv | hp);
+                            vn = hp & xv;
+                        }
+                        edge = score <= 2;
+                    }
+                }
+            }
+            warp_append_pairs(ecur, edge ? 1 : 0, [&](long long slot) {
+                if (slot < cap) edges[slot] = make_int2((int32_t)u, v);
+                else atomicExch(err, 1);
+            });
+            if (edge) weigh((int32_t)u, v);
+        }
+        __syncwarp();
+    }
+}
+
 // ---- 4. closed neighbourhoods ---------------------------------------------
 
 // D_u = m_u + W_u (written into wsum in place); cursor starts after M_u;
@@ -941,7 +1126,7 @@ using Timer = EventMarks;
 tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaStream_t s, int num_sms, bool profile,
                              int partition_cap, bool keep_index, int partition_target, bool force_off64) {
     const int64_t n = pk.n;
-    if (n > kDeletionMaxN) return TCRNET_ENOTSUP;
+    if (n > kDeletionMaxN || T > 2) return TCRNET_ENOTSUP;
     const int cap = (partition_cap > 0 && partition_cap < kWarpCap) ? partition_cap : kWarpCap;
     Timer tm(profile, s);
     const int t0 = tm.mark();
@@ -1021,10 +1206,12 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     TCR_CHECK(uoff.alloc(sizeof(int64_t) * (n + 1), s));
     TCR_CUDA(cudaMemsetAsync(wsum.as<void>(), 0, sizeof(int32_t) * n, s));
     const Weigh weigh{umult.as<int32_t>(), wsum.as<int32_t>()};
-    const bool join = T >= 1;
+    const bool join = T == 1;   // the deletion join (l_max = 1)
+    const bool cand2 = T == 2;  // candidates of shared variants + exact check (l_max = 2)
     int64_t P = 1;
     int jgrid = 1;
     int t2 = t1, t3 = t1;
+    int64_t E2_cap = 0, R2 = 0;  // l_max = 2: edge buffer capacity, records
     if (join) {
         const int target = partition_target > 0 ? partition_target
                                                  : (R_max <= kTargetSwitchRecords ? kTargetPartSmall : kTargetPartLarge);
@@ -1069,6 +1256,73 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
                                                                 d_ecur, seg_cap);
         TCR_LAUNCH_CHECK();
         t3 = tm.mark();
+    } else if (cand2) {
+        // records of every variant with up to two deletions, partitioned by hash
+        DevBuf tot;
+        TCR_CHECK(tot.alloc(sizeof(unsigned long long) * 2, s));
+        TCR_CUDA(cudaMemsetAsync(tot.as<void>(), 0, sizeof(unsigned long long) * 2, s));
+        unsigned long long* d_tot = tot.as<unsigned long long>();
+        k_var2_count<<<grid_for(n), kThreads, 0, s>>>(ucanon.as<Canon>(), ulen.as<uint8_t>(), d_U, n, d_tot);
+        TCR_LAUNCH_CHECK();
+        unsigned long long h_tot = 0;
+        TCR_CUDA(cudaMemcpyAsync(&h_tot, d_tot, sizeof(h_tot), cudaMemcpyDeviceToHost, s));
+        TCR_CUDA(cudaStreamSynchronize(s));
+        R2 = (int64_t)h_tot;
+        const int target = partition_target > 0 ? partition_target : kTargetPartSmall;
+        P = std::max<int64_t>(1, std::min<int64_t>(R2 / target + 1, 1LL << 30));
+        DevBuf pcnt;
+        TCR_CHECK(pcnt.alloc(sizeof(int32_t) * P, s));
+        TCR_CHECK(poff.alloc(sizeof(int64_t) * (P + 1), s));
+        TCR_CHECK(recs.alloc(sizeof(uint64_t) * std::max<int64_t>(R2, 1), s));
+        TCR_CUDA(cudaMemsetAsync(pcnt.as<void>(), 0, sizeof(int32_t) * P, s));
+        k_var2_records<false><<<grid_for(n), kThreads, 0, s>>>(ucanon.as<Canon>(), ulen.as<uint8_t>(), d_U, n,
+                                                               (uint32_t)P, pcnt.as<int32_t>(), nullptr, nullptr);
+        TCR_LAUNCH_CHECK();
+        TCR_CHECK(scan_exclusive_i32_to_i64(pcnt.as<int32_t>(), poff.as<int64_t>(), P, s));
+        TCR_CUDA(cudaMemsetAsync(pcnt.as<void>(), 0, sizeof(int32_t) * P, s));
+        k_var2_records<true><<<grid_for(n), kThreads, 0, s>>>(ucanon.as<Canon>(), ulen.as<uint8_t>(), d_U, n,
+                                                              (uint32_t)P, pcnt.as<int32_t>(), poff.as<int64_t>(),
+                                                              recs.as<uint64_t>());
+        TCR_LAUNCH_CHECK();
+        t2 = tm.mark();
+        // candidate pairs: counted, then written
+        const unsigned pgrid = (unsigned)std::min<int64_t>(ceil_div(P, kWarps), (int64_t)num_sms * 16);
+        k_var2_pairs<false><<<pgrid, kThreads, 0, s>>>(poff.as<int64_t>(), P, recs.as<uint64_t>(), d_tot + 1,
+                                                       nullptr, nullptr, 0);
+        TCR_LAUNCH_CHECK();
+        TCR_CUDA(cudaMemcpyAsync(&h_tot, d_tot + 1, sizeof(h_tot), cudaMemcpyDeviceToHost, s));
+        TCR_CUDA(cudaStreamSynchronize(s));
+        const int64_t NC = (int64_t)h_tot;
+        DevBuf cand, ccur_b, coff, ccols;
+        TCR_CHECK(cand.alloc(sizeof(int2) * std::max<int64_t>(NC, 1), s));
+        TCR_CUDA(cudaMemsetAsync(d_tot + 1, 0, sizeof(unsigned long long), s));
+        k_var2_pairs<true><<<pgrid, kThreads, 0, s>>>(poff.as<int64_t>(), P, recs.as<uint64_t>(), nullptr,
+                                                      d_tot + 1, cand.as<int2>(), NC);
+        TCR_LAUNCH_CHECK();
+        recs.reset();
+        // candidates by their smaller string, sorted, repeats skipped, checked
+        TCR_CHECK(ccur_b.alloc(sizeof(int32_t) * n, s));
+        TCR_CHECK(coff.alloc(sizeof(int64_t) * (n + 1), s));
+        TCR_CHECK(ccols.alloc(sizeof(int32_t) * std::max<int64_t>(NC, 1), s));
+        TCR_CUDA(cudaMemsetAsync(ccur_b.as<void>(), 0, sizeof(int32_t) * n, s));
+        const unsigned cgrid = (unsigned)std::min<int64_t>(grid_for(NC), (int64_t)num_sms * 16);
+        k_cand_rows<<<cgrid, kThreads, 0, s>>>(cand.as<int2>(), NC, nullptr, ccur_b.as<int32_t>(), nullptr, false);
+        TCR_LAUNCH_CHECK();
+        TCR_CHECK(scan_exclusive_i32_to_i64(ccur_b.as<int32_t>(), coff.as<int64_t>(), n, s));
+        TCR_CUDA(cudaMemsetAsync(ccur_b.as<void>(), 0, sizeof(int32_t) * n, s));
+        k_cand_rows<<<cgrid, kThreads, 0, s>>>(cand.as<int2>(), NC, coff.as<int64_t>(), ccur_b.as<int32_t>(),
+                                               ccols.as<int32_t>(), true);
+        TCR_LAUNCH_CHECK();
+        cand.reset();
+        TCR_CHECK(sort_rows(coff.as<int64_t>(), ccols.as<int32_t>(), n, s, num_sms));
+        E2_cap = std::max<int64_t>(NC, 1);
+        TCR_CHECK(edges.alloc(sizeof(int2) * E2_cap, s));
+        const unsigned vgrid = (unsigned)std::min<int64_t>(ceil_div(n, kWarps), (int64_t)num_sms * 16);
+        k_cand_verify<<<vgrid, kThreads, 0, s>>>(coff.as<int64_t>(), ccols.as<int32_t>(), d_U, ucanon.as<Canon>(),
+                                                 ulen.as<uint8_t>(), weigh, edges.as<int2>(), d_ecur + kEdgeSegs,
+                                                 E2_cap, d_err + 1);
+        TCR_LAUNCH_CHECK();
+        t3 = tm.mark();
     }
 
     // ---- 4. list sizes D_u = m_u + W_u, list offsets, node degrees
@@ -1083,7 +1337,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     TCR_LAUNCH_CHECK();
     TCR_CHECK(scan_exclusive_i32_to_i64(deg.as<int32_t>(), off64.as<int64_t>(), n, s));
     int64_t sizes[2] = {0, 0};  // sum of D_u, nnz
-    unsigned long long segs[kEdgeSegs];
+    unsigned long long segs[kEdgeSegs + 1];  // per-segment edge counts, then the single-list count
     int h_dmax = 0;
     TCR_CUDA(cudaMemcpyAsync(&sizes[0], uoff.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TCR_CUDA(cudaMemcpyAsync(&sizes[1], off64.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -1097,6 +1351,11 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         E += (int64_t)segs[g];
         seg_max = std::max<int64_t>(seg_max, (int64_t)segs[g]);
         overflow = overflow || (int64_t)segs[g] > seg_cap;
+    }
+    if (cand2) {  // one contiguous edge list
+        E = (int64_t)segs[kEdgeSegs];
+        seg_max = E;
+        if (E > E2_cap) return TCRNET_EDEVICE;
     }
     int n_two_pass = 0;
     DevBuf Sbuf;
@@ -1137,6 +1396,11 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     // then append neighbour member lists
     int64_t fill_segs = kEdgeSegs, fill_cap = seg_cap;
     const unsigned long long* fill_counts = d_ecur;
+    if (cand2) {
+        fill_segs = 1;
+        fill_cap = E2_cap;
+        fill_counts = d_ecur + kEdgeSegs;
+    }
     if (join && overflow) {
         edges.reset();
         TCR_CHECK(edges.alloc(sizeof(int2) * E, s));
@@ -1166,7 +1430,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         if (keep_edges)  // the second pass wrote them contiguously
             TCR_CUDA(cudaMemcpyAsync(uedges.as<void>(), edges.as<void>(), sizeof(int2) * E, cudaMemcpyDeviceToDevice, s));
     }
-    if (join && E > 0) {
+    if ((join || cand2) && E > 0) {
         if (!keep_index) recs.reset();
         const dim3 fgrid(grid_for(2 * seg_max), (unsigned)fill_segs);
         k_closed_edges<<<fgrid, kThreads, 0, s>>>(edges.as<int2>(), fill_cap, fill_counts, umult.as<int32_t>(),
@@ -1195,6 +1459,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     TCR_CUDA(cudaMemcpyAsync(&h_U, d_U, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     if (join) TCR_CUDA(cudaMemcpyAsync(&h_R, poff.as<int64_t>() + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TCR_CUDA(cudaStreamSynchronize(s));
+    if (cand2) h_R = R2;
     if (h_err[0] || h_err[1]) return TCRNET_EDEVICE;
 
     out.off64 = std::move(off64);

@@ -40,10 +40,10 @@ def test_options_init_defaults():
     assert ctypes.sizeof(tn.tcrnet_options) == 4 * 3 + 4 + 8 + 4 + 32 + 4  # padded layout of the C struct
 
 
-@pytest.mark.parametrize("threshold,method,status", [(-1, "auto", tn.EINVAL), (2, "deletion", tn.ENOTSUP),
+@pytest.mark.parametrize("threshold,method,status", [(-1, "auto", tn.EINVAL), (3, "deletion", tn.ENOTSUP),
                                                      (6, "deletion", tn.ENOTSUP)])
 def test_threshold_rejected_before_device_work(threshold, method, status):
-    # negative l_max, and the deletion join with l_max >= 2, are refused before any device work
+    # negative l_max, and the deletion method with l_max >= 3, are refused before any device work
     with pytest.raises(tn.TcrnetError) as e:
         tn.tcrnet_build(["CASSF", "CASSG"], threshold=threshold, method=method)
     assert e.value.status == status

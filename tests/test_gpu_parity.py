@@ -494,3 +494,55 @@ def test_long_rows_of_every_sort_class(method):
         for i in (lo, lo + 1, (lo + hi) // 2, hi - 2, hi - 1):
             row = cols[off[i]:off[i + 1]]
             assert np.array_equal(row, ids[ids != i]), (method, lo, hi, i)
+
+
+def test_lmax2_deletion_method_exact():
+    """l_max = 2 through candidates of shared variants with up to two deletions
+    and the exact distance check: equal to the oracle and to the all-pairs
+    kernels on exhaustive tiny-alphabet sets, generator strings, edge strings
+    and strings across the 32-letter word boundary."""
+    cases = {
+        "tiny alphabet": from_strings(_all_strings("AC", 6) + _all_strings("ACD", 3)),
+        "generator": generate_config1(3000, seed=62),
+        "edge strings": from_strings(edge_strings()),
+    }
+    rng = np.random.default_rng(93)
+    alpha = np.array(list("ACDEFG"))
+    long_strs = []
+    for _ in range(200):
+        L = int(rng.integers(28, 47))
+        s = list(alpha[rng.integers(0, len(alpha), L)])
+        long_strs.append("".join(s))
+        for _ in range(3):
+            t = list(s)
+            for _ in range(int(rng.integers(1, 4))):
+                k = int(rng.integers(0, len(t)))
+                op = int(rng.integers(0, 3))
+                if op == 0:
+                    t[k] = alpha[rng.integers(0, len(alpha))]
+                elif op == 1 and len(t) > 1:
+                    del t[k]
+                elif len(t) < 48:
+                    t.insert(k, alpha[rng.integers(0, len(alpha))])
+            long_strs.append("".join(t))
+    cases["long strings"] = from_strings(long_strs)
+    for name, rep in cases.items():
+        off, cols, deg, st = gpu_csr(rep, 2, "deletion")
+        assert st["method"] == tn.METHOD_DELETION
+        ro, rc, _ = oracle_csr(rep, 2)
+        assert_csr_equal(off, cols, ro, rc, f"{name}: deletion l_max=2 vs oracle")
+        check_invariants(off, cols, deg, rep.n)
+        to, tc, _, _ = gpu_csr(rep, 2, "tile")
+        assert_csr_equal(off, cols, to, tc, f"{name}: deletion vs tile l_max=2")
+
+
+def test_lmax2_deletion_method_matches_tile_2e4():
+    rep = generate_config1(20_000, seed=64)
+    off, cols, deg, st = gpu_csr(rep, 2, "auto")
+    assert st["method"] == tn.METHOD_DELETION
+    to, tc, _, _ = gpu_csr(rep, 2, "tile")
+    assert_csr_equal(off, cols, to, tc, "auto (deletion) vs tile, l_max=2, 2e4 strings")
+    check_invariants(off, cols, deg, rep.n)
+    rows = sample_rows(deg, 40, seed=5, top=10)
+    roff, rcols = oracle.rows(rep.chars, rep.offsets, rows, max_dist=2)
+    assert_rows_equal(off, cols, rows, roff, rcols, "sampled oracle rows")
