@@ -740,33 +740,51 @@ def run_ours(args):
                                  "timing": "host time of each call, removal masks and outputs in device memory; "
                                            "deletion builds run on the graph of distinct strings"}
         if "lmax2" in legs:
-            # --- l_max = 2 (bit-parallel distance): the paper's assortativity setting of
-            #     4 x 8,000 sequences, and N = 1e5
+            # --- l_max = 2: the paper's assortativity setting of 4 x 8,000 sequences,
+            #     and N = 1e5, by the default method (deletion candidates + exact
+            #     distance) and by the all-pairs bit-parallel distance kernel
             from synthgen import generate_config1
 
             lm2 = {}
+            peak = SMS * INT_LANES_PER_SM * sm_max_nominal * 1e6
             for n2 in (32_000, 100_000):
                 r2 = generate_config1(n2, seed=7)
                 c2 = torch.from_numpy(r2.chars).to(dev)
                 o2 = torch.from_numpy(r2.offsets).to(dev)
-                tn.tcrnet_build_flat(c2, o2, 2, stream=stream).free()
-                g2 = tn.tcrnet_build_flat(c2, o2, 2, stream=stream, profile=True)
-                st2 = g2.stats()
-                g2.free()
-                # per candidate pair the bit-parallel recurrence runs one step per
-                # letter of the row string, 17 integer operations per step (mask
-                # lookup, carry add, 3-input logic, shifts, score update): an
-                # estimate from the mean length, against the issue ceiling
-                mean_len = float(np.diff(r2.offsets).mean())
-                ops = st2["candidate_pairs"] * mean_len * 17.0
-                ach = ops / (st2["ms_count"] / 1e3)
-                peak = SMS * INT_LANES_PER_SM * sm_max_nominal * 1e6
-                lm2[str(n2)] = {"build_ms": st2["ms_total"], "count_pass_ms": st2["ms_count"],
-                                "candidate_pairs": st2["candidate_pairs"], "nnz": st2["nnz"],
-                                "candidate_pairs_per_s": st2["candidate_pairs"] / (st2["ms_count"] / 1e3),
-                                "roofline": {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12,
-                                             "unit": "Tops/s", "frac": ach / peak,
-                                             "ops_per_pair": f"17 x mean length ({mean_len:.2f}), estimate"}}
+                row = {}
+                for label, meth in (("default", "auto"), ("all_pairs", "tile")):
+                    tn.tcrnet_build_flat(c2, o2, 2, method=meth, stream=stream).free()
+                    ts = []
+                    for _ in range(3):
+                        a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        a2.record(stream)
+                        g2 = tn.tcrnet_build_flat(c2, o2, 2, method=meth, stream=stream)
+                        b2.record(stream)
+                        b2.synchronize()
+                        st2 = g2.stats()
+                        g2.free()
+                        ts.append(a2.elapsed_time(b2))
+                    ms2 = statistics.median(ts)
+                    entry = {"build_ms": ms2, "method": {1: "tile", 2: "deletion"}.get(st2["method"], "?"),
+                             "nnz": st2["nnz"], "all_pairs_per_s": n2 * (n2 - 1) / 2 / (ms2 / 1e3)}
+                    if st2["method"] == tn.METHOD_DELETION:
+                        entry["candidates_checked"] = st2["candidate_pairs"]
+                        entry["variant_records"] = st2["n_records"]
+                    else:
+                        # per candidate pair the recurrence runs one step per letter of
+                        # the row string, 17 integer operations per step (an estimate
+                        # from the mean length), against the issue ceiling
+                        g3 = tn.tcrnet_build_flat(c2, o2, 2, method=meth, stream=stream, profile=True)
+                        st3 = g3.stats()
+                        g3.free()
+                        mean_len = float(np.diff(r2.offsets).mean())
+                        ach = st3["candidate_pairs"] * mean_len * 17.0 / (st3["ms_count"] / 1e3)
+                        entry.update({"candidate_pairs": st3["candidate_pairs"], "count_pass_ms": st3["ms_count"],
+                                      "roofline": {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12,
+                                                   "unit": "Tops/s", "frac": ach / peak,
+                                                   "ops_per_pair": f"17 x mean length ({mean_len:.2f}), estimate"}})
+                    row[label] = entry
+                lm2[str(n2)] = row
             line["lmax2"] = lm2
         if "batched" in legs:
             # --- batched: uneven repertoires in one pass vs one plain build each

@@ -25,9 +25,12 @@
  *  - Inputs are borrowed for the duration of the call and never retained.
  *  - Thresholds: any l_max >= 0 (negative: TCRNET_EINVAL). 0 and 1 (the paper's
  *    network-construction setting, Fig. performance) use closed-form tests or
- *    the deletion join; l_max >= 2 (the paper's analyses use 2 and 6) computes
- *    the distance bit-parallel on the tile path (TCRNET_METHOD_DELETION with
- *    l_max >= 2: TCRNET_ENOTSUP).
+ *    the deletion join; 2 (the paper's assortativity analysis) uses the
+ *    deletion method's candidates (strings sharing a variant with up to two
+ *    deletions) checked by the exact bit-parallel distance, or the all-pairs
+ *    distance kernel for small inputs; l_max >= 3 (the paper's LCC drawings use
+ *    6) computes the distance bit-parallel on the tile path
+ *    (TCRNET_METHOD_DELETION with l_max >= 3: TCRNET_ENOTSUP).
  *  - Work is ordered on the CUDA stream given in tcrnet_options (NULL: the
  *    legacy default stream). Calls return after the result is complete on the
  *    device unless stated otherwise.
@@ -57,7 +60,7 @@ typedef enum tcrnet_status {
     TCRNET_EINVAL = 1,    /* bad argument, empty string or non-monotone offsets */
     TCRNET_EBADCHAR = 2,  /* a character outside the 20-letter alphabet */
     TCRNET_ETOOLONG = 3,  /* a string longer than TCRNET_MAX_LEN */
-    TCRNET_ENOTSUP = 4,   /* combination not supported (deletion method with l_max >= 2, ...) */
+    TCRNET_ENOTSUP = 4,   /* combination not supported (deletion method with l_max >= 3, ...) */
     TCRNET_ENOMEM = 5,    /* device or host allocation failed; nothing leaked */
     TCRNET_EDEVICE = 6,   /* a CUDA error; the handle is poisoned */
     TCRNET_ETIMEOUT = 7,  /* a bounded device wait ran out; the handle is poisoned */
@@ -110,7 +113,9 @@ typedef struct tcrnet_stats {
     int32_t threshold;
     int64_t n;                /* nodes */
     int64_t nnz;              /* directed entries = 2 |E| */
-    int64_t candidate_pairs;  /* unordered pairs the tile kernel tested (tile path) */
+    int64_t candidate_pairs;  /* unordered pairs the tile kernel tested (tile path);
+                                 deletion path at l_max = 2: string pairs sharing a
+                                 variant, checked with the exact distance */
     int64_t n_unique;         /* distinct strings (deletion path) */
     int64_t n_records;        /* deletion-join records (deletion path) */
     int64_t unique_edges;     /* edges among distinct strings (deletion path) */
@@ -215,7 +220,7 @@ tcrnet_status tcrnet_query_flat(tcrnet_handle h, const uint8_t *chars, const int
 /* tcrnet_query_flat with options: opt->stream orders the call (NULL options or
  * stream: the build's stream); opt->method selects the search: AUTO (the
  * deletion index when the build kept one, i.e. a deletion-method build with
- * l_max >= 1, else the tile kernel), TILE, or DELETION (ENOTSUP without an
+ * l_max = 1, else the tile kernel), TILE, or DELETION (ENOTSUP without an
  * index). Both searches return identical lists. */
 tcrnet_status tcrnet_query_ex(tcrnet_handle h, const uint8_t *chars, const int64_t *offsets, int64_t m,
                               int32_t mem, const tcrnet_options *opt, tcrnet_handle *out);

@@ -434,6 +434,7 @@ tcrnet_status build_from_packed(tcrnet_graph* h, Packed& pk, int64_t n, int32_t 
         h->stats.n_unique = dr.n_unique;
         h->stats.n_records = dr.n_records;
         h->stats.unique_edges = dr.unique_edges;
+        h->stats.candidate_pairs = dr.candidates;  // l_max = 2: pairs checked with the exact distance
         h->stats.n_fallback = dr.n_fallback;
         h->stats.closed_total = dr.closed_total;
         h->stats.two_pass_join = dr.two_pass_join;

@@ -1211,7 +1211,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     int64_t P = 1;
     int jgrid = 1;
     int t2 = t1, t3 = t1;
-    int64_t E2_cap = 0, R2 = 0;  // l_max = 2: edge buffer capacity, records
+    int64_t E2_cap = 0, R2 = 0, NC2 = 0;  // l_max = 2: edge buffer capacity, records, candidates
     if (join) {
         const int target = partition_target > 0 ? partition_target
                                                  : (R_max <= kTargetSwitchRecords ? kTargetPartSmall : kTargetPartLarge);
@@ -1293,6 +1293,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         TCR_CUDA(cudaMemcpyAsync(&h_tot, d_tot + 1, sizeof(h_tot), cudaMemcpyDeviceToHost, s));
         TCR_CUDA(cudaStreamSynchronize(s));
         const int64_t NC = (int64_t)h_tot;
+        NC2 = NC;
         DevBuf cand, ccur_b, coff, ccols;
         TCR_CHECK(cand.alloc(sizeof(int2) * std::max<int64_t>(NC, 1), s));
         TCR_CUDA(cudaMemsetAsync(d_tot + 1, 0, sizeof(unsigned long long), s));
@@ -1469,6 +1470,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     out.nnz = nnz;
     out.n_unique = h_U;
     out.n_records = h_R;
+    out.candidates = NC2;
     out.unique_edges = E;
     out.n_fallback = h_err[2];
     out.closed_total = SD;

@@ -39,6 +39,7 @@ struct DeletionResult {
     int64_t n_unique = 0;
     int64_t n_records = 0;
     int64_t unique_edges = 0;
+    int64_t candidates = 0;    // l_max = 2: distinct-string pairs sharing a variant (before deduplication)
     int64_t n_fallback = 0;    // partitions joined by the exact quadratic fallback
     int64_t closed_total = 0;  // sum over distinct strings of closed-neighbourhood sizes
     int two_pass_join = 0;     // 1 when the edges overflowed the one-pass buffer
