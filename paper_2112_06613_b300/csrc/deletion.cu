@@ -49,6 +49,8 @@
 //     sorted (rowsort.cu). A node i of u has degree D_u - 1.
 //  5. expand: row i of the CSR is S_u without i (a streaming copy), so the
 //     long rows of frequent strings are sorted once, not once per copy.
+// l_max = 2 replaces steps 2-3 (section 3' below): candidates from shared
+// variants with up to two deletions, checked with the exact distance.
 #include <algorithm>
 #include <vector>
 

@@ -49,8 +49,10 @@ struct DeletionResult {
     DeletionIndex index;  // filled when the build keeps its index
 };
 
-// Test knob: partitions larger than `partition_cap` (<= the shared-memory
-// capacity; 0 = default) take the quadratic fallback.
+// Network of the packed strings at l_max = T (0, 1 or 2; ENOTSUP above). Test
+// knob: partitions larger than `partition_cap` (<= the shared-memory capacity;
+// 0 = default) take the quadratic fallback of the l_max = 1 join. The query
+// index is kept (keep_index) for l_max = 1 builds.
 tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaStream_t s, int num_sms,
                              bool profile, int partition_cap = 0, bool keep_index = false,
                              int partition_target = 0, bool force_off64 = false);
