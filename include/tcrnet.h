@@ -168,7 +168,7 @@ tcrnet_status tcrnet_build_flat(const uint8_t *chars, const int64_t *offsets, in
  * block-diagonal CSR: row i of repertoire r lists the global ids of i's
  * neighbours within r, so rows rep_offsets[r] .. rep_offsets[r+1] minus
  * rep_offsets[r] are exactly the network tcrnet_build_flat would return for
- * that repertoire alone. l_max <= 1 (deletion join; ENOTSUP otherwise or with
+ * that repertoire alone. l_max <= 2 (deletion method; ENOTSUP otherwise or with
  * TCRNET_METHOD_TILE). Batched handles answer no queries or inserts (ESTATE).
  */
 tcrnet_status tcrnet_build_batched(const uint8_t *chars, const int64_t *offsets, int64_t n,

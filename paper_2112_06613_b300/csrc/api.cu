@@ -478,7 +478,7 @@ tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n
     if (T > 2 && opt.method == TCRNET_METHOD_DELETION) return TCRNET_ENOTSUP;  // deletion method: l_max <= 2
     if (rep_off) {
         // batched: one deletion-method pass over all repertoires
-        if (T > 1 || opt.method == TCRNET_METHOD_TILE) return TCRNET_ENOTSUP;
+        if (T > 2 || opt.method == TCRNET_METHOD_TILE) return TCRNET_ENOTSUP;
         if (nrep < 1 || nrep > 65536 || rep_off[0] != 0 || rep_off[nrep] != n) return TCRNET_EINVAL;
         for (int64_t r = 0; r < nrep; ++r)
             if (rep_off[r + 1] < rep_off[r]) return TCRNET_EINVAL;

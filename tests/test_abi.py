@@ -69,7 +69,7 @@ def test_bad_method_rejected():
     ([0, 1], 1, tn.EINVAL),          # does not end at n
     ([1, 2], 1, tn.EINVAL),          # does not start at 0
     ([0, 2, 1, 2], 1, tn.EINVAL),    # decreasing
-    ([0, 2], 2, tn.ENOTSUP),         # batched builds use the l_max <= 1 deletion join
+    ([0, 2], 3, tn.ENOTSUP),         # batched builds use the deletion method: l_max <= 2
     ([0], 1, tn.EINVAL),             # no repertoire
 ])
 def test_batched_bounds_rejected_before_device_work(rep_offsets, threshold, status):

@@ -35,7 +35,7 @@ def batched_slices(flat, bounds, threshold=1):
     return tn.split_block_diagonal(off, cols, bounds), st
 
 
-@pytest.mark.parametrize("threshold", [0, 1])
+@pytest.mark.parametrize("threshold", [0, 1, 2])
 def test_batched_equals_per_repertoire_builds(threshold):
     reps = generate_batched(24, seed=5, lo=50, hi=6000)
     flat, bounds = concat(reps)
