@@ -793,20 +793,45 @@ __global__ void k_var2_records(const Canon* __restrict__ ucanon, const uint8_t* 
     });
 }
 
-// Candidate pairs (u < v) of every partition: records of equal hash and
-// different strings. A warp per partition compares 32 records with 32 at a
-// time. COUNT adds the candidates to *count, WRITE appends them at *cursor.
+// Candidate pairs of every partition: records of equal hash and different
+// strings, filed under the smaller string. COUNT adds one to rcnt[u] per
+// candidate {u, v} (u < v); WRITE stores v at coff[u] + a slot taken from
+// rcnt[u], so rows fill without a shared cursor. A warp takes a partition:
+// up to 32 records at once with two match steps (equal hash, equal record),
+// larger ones 32 by 32 records.
 template <bool WRITE>
 __global__ void __launch_bounds__(kThreads)
 k_var2_pairs(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __restrict__ recs,
-             unsigned long long* __restrict__ count, unsigned long long* __restrict__ cursor, int2* __restrict__ out,
-             int64_t cap) {
+             int32_t* __restrict__ rcnt, const int64_t* __restrict__ coff, int32_t* __restrict__ ccols) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned long long mine = 0;
+    auto emit = [&](uint32_t a, uint32_t b) {
+        const uint32_t lo = a < b ? a : b, hi = a < b ? b : a;
+        if constexpr (!WRITE) atomicAdd(&rcnt[lo], 1);
+        else ccols[coff[lo] + atomicAdd(&rcnt[lo], 1)] = (int32_t)hi;
+    };
     for (int64_t pid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; pid < P; pid += nw) {
         const int64_t b0 = poff[pid], b1 = poff[pid + 1];
         if (b1 - b0 < 2) continue;
+        if (b1 - b0 <= 32) {
+            const bool valid = b0 + lane < b1;
+            const uint64_t r = valid ? recs[b0 + lane] : 0;
+            const unsigned vmask = __ballot_sync(kFull, valid);
+            const unsigned peers = __match_any_sync(kFull, (uint32_t)(r >> 32)) & vmask;
+            const unsigned same = __match_any_sync(kFull, (unsigned long long)r) & vmask;
+            // lanes above this one with the same hash and another string
+            unsigned bits = valid ? peers & ~same & ((~0u << lane) << 1) : 0u;
+            const uint32_t u = (uint32_t)r;
+            while (__any_sync(kFull, bits)) {
+                const int j = bits ? __ffs(bits) - 1 : lane;
+                const uint32_t uj = __shfl_sync(kFull, u, j);
+                if (bits) {
+                    emit(u, uj);
+                    bits &= bits - 1;
+                }
+            }
+            continue;
+        }
         for (int64_t i0 = b0; i0 < b1; i0 += 32) {
             const int64_t i = i0 + lane;
             const uint64_t ri = i < b1 ? recs[i] : ~0ull;
@@ -815,51 +840,42 @@ k_var2_pairs(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __rest
                 for (int t = 0; t < 32; ++t) {
                     const uint64_t r = __shfl_sync(kFull, rj, t);
                     const int64_t j = j0 + t;
-                    const bool hit = i < b1 && j < b1 && j > i && (r >> 32) == (ri >> 32) &&
-                                     (uint32_t)r != (uint32_t)ri;
-                    if constexpr (!WRITE) {
-                        mine += hit ? 1 : 0;
-                    } else {
-                        warp_append_pairs(cursor, hit ? 1 : 0, [&](long long slot) {
-                            if (slot < cap) {
-                                const int32_t a = (int32_t)(uint32_t)ri, b = (int32_t)(uint32_t)r;
-                                out[slot] = a < b ? make_int2(a, b) : make_int2(b, a);
-                            }
-                        });
-                    }
+                    if (i < b1 && j < b1 && j > i && (r >> 32) == (ri >> 32) && (uint32_t)r != (uint32_t)ri)
+                        emit((uint32_t)ri, (uint32_t)r);
                 }
             }
         }
-    }
-    if constexpr (!WRITE) {
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) mine += __shfl_xor_sync(kFull, mine, d);
-        if (lane == 0 && mine) atomicAdd(count, mine);
-    }
-}
-
-// Candidates grouped by their smaller string: count, then place.
-__global__ void k_cand_rows(const int2* __restrict__ cand, int64_t nc, const int64_t* __restrict__ coff,
-                            int32_t* __restrict__ ccur, int32_t* __restrict__ ccols, bool place) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nc; e += (int64_t)gridDim.x * blockDim.x) {
-        const int2 c = cand[e];
-        if (!place) atomicAdd(&ccur[c.x], 1);
-        else ccols[coff[c.x] + atomicAdd(&ccur[c.x], 1)] = c.y;
     }
 }
 
 // Each distinct candidate (row u sorted, repeats adjacent) checked with the
 // bit-parallel distance (Myers 1999, Hyyro 2001: u's letter masks in shared
 // memory, v as the text); pairs within l_max = 2 become edges {u, v} with their
-// weights, appended at *ecur.
+// weights. A warp gathers its edges in shared memory and appends them at *ecur
+// a few hundred at a time (one atomic each).
+constexpr int kVerifyBuf = 256;
 __global__ void __launch_bounds__(kThreads)
 k_cand_verify(const int64_t* __restrict__ coff, const int32_t* __restrict__ ccols, const int64_t* __restrict__ U_ptr,
               const Canon* __restrict__ ucanon, const uint8_t* __restrict__ ulen, Weigh weigh, int2* __restrict__ edges,
               unsigned long long* __restrict__ ecur, int64_t cap, int* __restrict__ err) {
     __shared__ uint64_t speq[kWarps][32];
+    __shared__ int2 ebuf[kWarps][kVerifyBuf];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t U = *U_ptr;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int fill = 0;  // edges in this warp's buffer (warp-uniform)
+    auto flush = [&]() {
+        unsigned long long base = 0;
+        if (lane == 0 && fill) base = atomicAdd(ecur, (unsigned long long)fill);
+        base = __shfl_sync(kFull, base, 0);
+        for (int k = lane; k < fill; k += 32) {
+            const unsigned long long slot = base + (unsigned long long)k;
+            if ((int64_t)slot < cap) edges[slot] = ebuf[w][k];
+            else atomicExch(err, 1);
+        }
+        __syncwarp();
+        fill = 0;
+    };
     for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < U; u += nw) {
         const int64_t a = coff[u], b = coff[u + 1];
         if (a == b) continue;
@@ -900,14 +916,18 @@ k_cand_verify(const int64_t* __restrict__ coff, const int32_t* __restrict__ ccol
                     }
                 }
             }
-            warp_append_pairs(ecur, edge ? 1 : 0, [&](long long slot) {
-                if (slot < cap) edges[slot] = make_int2((int32_t)u, v);
-                else atomicExch(err, 1);
-            });
-            if (edge) weigh((int32_t)u, v);
+            const unsigned hits = __ballot_sync(kFull, edge);
+            if (edge) {
+                ebuf[w][fill + __popc(hits & lanemask_lt())] = make_int2((int32_t)u, v);
+                weigh((int32_t)u, v);
+            }
+            fill += __popc(hits);
+            __syncwarp();
+            if (fill > kVerifyBuf - 32) flush();
         }
         __syncwarp();
     }
+    flush();
 }
 
 // ---- 4. closed neighbourhoods ---------------------------------------------
@@ -1287,36 +1307,27 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
                                                               recs.as<uint64_t>());
         TCR_LAUNCH_CHECK();
         t2 = tm.mark();
-        // candidate pairs: counted, then written
+        // candidate pairs filed under their smaller string: counted per row,
+        // rows placed, then written; sorted rows put repeats side by side
         const unsigned pgrid = (unsigned)std::min<int64_t>(ceil_div(P, kWarps), (int64_t)num_sms * 16);
-        k_var2_pairs<false><<<pgrid, kThreads, 0, s>>>(poff.as<int64_t>(), P, recs.as<uint64_t>(), d_tot + 1,
-                                                       nullptr, nullptr, 0);
-        TCR_LAUNCH_CHECK();
-        TCR_CUDA(cudaMemcpyAsync(&h_tot, d_tot + 1, sizeof(h_tot), cudaMemcpyDeviceToHost, s));
-        TCR_CUDA(cudaStreamSynchronize(s));
-        const int64_t NC = (int64_t)h_tot;
-        NC2 = NC;
-        DevBuf cand, ccur_b, coff, ccols;
-        TCR_CHECK(cand.alloc(sizeof(int2) * std::max<int64_t>(NC, 1), s));
-        TCR_CUDA(cudaMemsetAsync(d_tot + 1, 0, sizeof(unsigned long long), s));
-        k_var2_pairs<true><<<pgrid, kThreads, 0, s>>>(poff.as<int64_t>(), P, recs.as<uint64_t>(), nullptr,
-                                                      d_tot + 1, cand.as<int2>(), NC);
-        TCR_LAUNCH_CHECK();
-        recs.reset();
-        // candidates by their smaller string, sorted, repeats skipped, checked
+        DevBuf ccur_b, coff, ccols;
         TCR_CHECK(ccur_b.alloc(sizeof(int32_t) * n, s));
         TCR_CHECK(coff.alloc(sizeof(int64_t) * (n + 1), s));
-        TCR_CHECK(ccols.alloc(sizeof(int32_t) * std::max<int64_t>(NC, 1), s));
         TCR_CUDA(cudaMemsetAsync(ccur_b.as<void>(), 0, sizeof(int32_t) * n, s));
-        const unsigned cgrid = (unsigned)std::min<int64_t>(grid_for(NC), (int64_t)num_sms * 16);
-        k_cand_rows<<<cgrid, kThreads, 0, s>>>(cand.as<int2>(), NC, nullptr, ccur_b.as<int32_t>(), nullptr, false);
+        k_var2_pairs<false><<<pgrid, kThreads, 0, s>>>(poff.as<int64_t>(), P, recs.as<uint64_t>(),
+                                                       ccur_b.as<int32_t>(), nullptr, nullptr);
         TCR_LAUNCH_CHECK();
         TCR_CHECK(scan_exclusive_i32_to_i64(ccur_b.as<int32_t>(), coff.as<int64_t>(), n, s));
+        int64_t NC = 0;
+        TCR_CUDA(cudaMemcpyAsync(&NC, coff.as<int64_t>() + n, sizeof(NC), cudaMemcpyDeviceToHost, s));
+        TCR_CUDA(cudaStreamSynchronize(s));
+        NC2 = NC;
+        TCR_CHECK(ccols.alloc(sizeof(int32_t) * std::max<int64_t>(NC, 1), s));
         TCR_CUDA(cudaMemsetAsync(ccur_b.as<void>(), 0, sizeof(int32_t) * n, s));
-        k_cand_rows<<<cgrid, kThreads, 0, s>>>(cand.as<int2>(), NC, coff.as<int64_t>(), ccur_b.as<int32_t>(),
-                                               ccols.as<int32_t>(), true);
+        k_var2_pairs<true><<<pgrid, kThreads, 0, s>>>(poff.as<int64_t>(), P, recs.as<uint64_t>(),
+                                                      ccur_b.as<int32_t>(), coff.as<int64_t>(), ccols.as<int32_t>());
         TCR_LAUNCH_CHECK();
-        cand.reset();
+        recs.reset();
         TCR_CHECK(sort_rows(coff.as<int64_t>(), ccols.as<int32_t>(), n, s, num_sms));
         E2_cap = std::max<int64_t>(NC, 1);
         TCR_CHECK(edges.alloc(sizeof(int2) * E2_cap, s));
