@@ -849,21 +849,27 @@ k_var2_pairs(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __rest
 }
 
 // Each distinct candidate (row u sorted, repeats adjacent) checked with the
-// bit-parallel distance (Myers 1999, Hyyro 2001: u's letter masks in shared
-// memory, v as the text); pairs within l_max = 2 become edges {u, v} with their
-// weights. A warp gathers its edges in shared memory and appends them at *ecur
-// a few hundred at a time (one atomic each).
-constexpr int kVerifyBuf = 256;
-__global__ void __launch_bounds__(kThreads)
+// bit-parallel distance (Myers 1999, Hyyro 2001). A warp walks rows and
+// queues their distinct candidates; each full queue of 32 is checked with one
+// pair per lane: the lane builds the letter masks of its u in its own column
+// of shared memory and runs the recurrence over v. Pairs within l_max = 2 (and
+// of one repertoire) become edges {u, v} with their weights; a warp gathers
+// its edges in shared memory and appends them at *ecur a hundred or so at a
+// time (one atomic each).
+constexpr int kVerifyWarps = 4;
+constexpr int kVerifyBuf = 128;
+constexpr int kSigma = 20;  // letter codes 1..20
+__global__ void __launch_bounds__(32 * kVerifyWarps)
 k_cand_verify(const int64_t* __restrict__ coff, const int32_t* __restrict__ ccols, const int64_t* __restrict__ U_ptr,
               const Canon* __restrict__ ucanon, const uint8_t* __restrict__ ulen, Weigh weigh, int2* __restrict__ edges,
               unsigned long long* __restrict__ ecur, int64_t cap, int* __restrict__ err) {
-    __shared__ uint64_t speq[kWarps][32];
-    __shared__ int2 ebuf[kWarps][kVerifyBuf];
+    __shared__ uint64_t peq[kVerifyWarps][kSigma][32];
+    __shared__ int2 queue[kVerifyWarps][64];
+    __shared__ int2 ebuf[kVerifyWarps][kVerifyBuf];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t U = *U_ptr;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    int fill = 0;  // edges in this warp's buffer (warp-uniform)
+    int qn = 0, fill = 0;  // queued pairs, buffered edges (warp-uniform)
     auto flush = [&]() {
         unsigned long long base = 0;
         if (lane == 0 && fill) base = atomicAdd(ecur, (unsigned long long)fill);
@@ -876,57 +882,73 @@ k_cand_verify(const int64_t* __restrict__ coff, const int32_t* __restrict__ ccol
         __syncwarp();
         fill = 0;
     };
+    auto check = [&](int cnt) {  // queue[0 .. cnt), cnt <= 32
+        bool edge = false;
+        int2 uv = make_int2(0, 0);
+        if (lane < cnt) {
+            uv = queue[w][lane];
+            const Canon cu = load_canon(ucanon + uv.x), cv = load_canon(ucanon + uv.y);
+            const int Lu = ulen[uv.x], Lv = ulen[uv.y];
+            const uint64_t tags = ((cu.w[0] ^ cv.w[0]) | (cu.w[1] ^ cv.w[1]) | (cu.w[2] ^ cv.w[2]) |
+                                   (cu.w[3] ^ cv.w[3])) & kTagBits;
+            if (tags == 0 && Lv - Lu <= 2 && Lu - Lv <= 2) {
+#pragma unroll
+                for (int c = 0; c < kSigma; ++c) peq[w][c][lane] = 0;
+                for (int k = 0; k < Lu; ++k) peq[w][code_at(cu, k) - 1][lane] |= 1ull << k;
+                const uint64_t top = 1ull << (Lu - 1);
+                uint64_t vp = ~0ull, vn = 0;
+                int score = Lu;
+                for (int k = 0; k < Lv; ++k) {
+                    const uint64_t eq = peq[w][code_at(cv, k) - 1][lane];
+                    const uint64_t xv = eq | vn;
+                    const uint64_t xh = (((eq & vp) + vp) ^ vp) | eq;
+                    uint64_t hp = vn | ~(xh | vp);
+                    uint64_t hn = vp & xh;
+                    score += ((hp & top) ? 1 : 0) - ((hn & top) ? 1 : 0);
+                    hp = (hp << 1) | 1ull;
+                    hn <<= 1;
+                    vp = hn | ~(xv | hp);
+                    vn = hp & xv;
+                }
+                edge = score <= 2;
+            }
+        }
+        const unsigned hits = __ballot_sync(kFull, edge);
+        if (edge) {
+            ebuf[w][fill + __popc(hits & lanemask_lt())] = uv;
+            weigh(uv.x, uv.y);
+        }
+        fill += __popc(hits);
+        __syncwarp();
+        if (fill > kVerifyBuf - 32) flush();
+    };
     for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < U; u += nw) {
         const int64_t a = coff[u], b = coff[u + 1];
-        if (a == b) continue;
-        const Canon cu = load_canon(ucanon + u);
-        const int Lu = ulen[u];
-        // letter masks of u: lane k builds the mask of letter k + 1
-        uint64_t m = 0;
-        for (int k = 0; k < Lu; ++k)
-            if (code_at(cu, k) == (uint32_t)(lane + 1)) m |= 1ull << k;
-        speq[w][lane] = m;
-        __syncwarp();
-        const uint64_t top = 1ull << (Lu - 1);
         for (int64_t e0 = a; e0 < b; e0 += 32) {
             const int64_t e = e0 + lane;
-            bool edge = false;
             int32_t v = -1;
+            bool first = false;
             if (e < b) {
                 v = ccols[e];
-                if (e == a || ccols[e - 1] != v) {  // first of its repeats
-                    const Canon cv = load_canon(ucanon + v);
-                    const int Lv = ulen[v];
-                    if (Lv - Lu <= 2 && Lu - Lv <= 2) {
-                        uint64_t vp = ~0ull, vn = 0;
-                        int score = Lu;
-                        for (int k = 0; k < Lv; ++k) {
-                            const uint64_t eq = speq[w][code_at(cv, k) - 1];
-                            const uint64_t xv = eq | vn;
-                            const uint64_t xh = (((eq & vp) + vp) ^ vp) | eq;
-                            uint64_t hp = vn | ~(xh | vp);
-                            uint64_t hn = vp & xh;
-                            score += ((hp & top) ? 1 : 0) - ((hn & top) ? 1 : 0);
-                            hp = (hp << 1) | 1ull;
-                            hn <<= 1;
-                            vp = hn | ~(xv | hp);
-                            vn = hp & xv;
-                        }
-                        edge = score <= 2;
-                    }
-                }
+                first = e == a || ccols[e - 1] != v;  // first of its repeats
             }
-            const unsigned hits = __ballot_sync(kFull, edge);
-            if (edge) {
-                ebuf[w][fill + __popc(hits & lanemask_lt())] = make_int2((int32_t)u, v);
-                weigh((int32_t)u, v);
-            }
-            fill += __popc(hits);
+            const unsigned m = __ballot_sync(kFull, first);
+            if (first) queue[w][qn + __popc(m & lanemask_lt())] = make_int2((int32_t)u, v);
+            qn += __popc(m);
             __syncwarp();
-            if (fill > kVerifyBuf - 32) flush();
+            if (qn >= 32) {
+                check(32);
+                const int rest = qn - 32;
+                const int2 t = lane < rest ? queue[w][32 + lane] : make_int2(0, 0);
+                __syncwarp();
+                if (lane < rest) queue[w][lane] = t;
+                __syncwarp();
+                qn = rest;
+            }
         }
-        __syncwarp();
     }
+    if (qn) check(qn);
+    __syncwarp();
     flush();
 }
 
@@ -1331,8 +1353,8 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         TCR_CHECK(sort_rows(coff.as<int64_t>(), ccols.as<int32_t>(), n, s, num_sms));
         E2_cap = std::max<int64_t>(NC, 1);
         TCR_CHECK(edges.alloc(sizeof(int2) * E2_cap, s));
-        const unsigned vgrid = (unsigned)std::min<int64_t>(ceil_div(n, kWarps), (int64_t)num_sms * 16);
-        k_cand_verify<<<vgrid, kThreads, 0, s>>>(coff.as<int64_t>(), ccols.as<int32_t>(), d_U, ucanon.as<Canon>(),
+        const unsigned vgrid = (unsigned)std::min<int64_t>(ceil_div(n, kVerifyWarps), (int64_t)num_sms * 32);
+        k_cand_verify<<<vgrid, 32 * kVerifyWarps, 0, s>>>(coff.as<int64_t>(), ccols.as<int32_t>(), d_U, ucanon.as<Canon>(),
                                                  ulen.as<uint8_t>(), weigh, edges.as<int2>(), d_ecur + kEdgeSegs,
                                                  E2_cap, d_err + 1);
         TCR_LAUNCH_CHECK();
