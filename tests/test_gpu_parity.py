@@ -536,6 +536,41 @@ def test_lmax2_deletion_method_exact():
         assert_csr_equal(off, cols, to, tc, f"{name}: deletion vs tile l_max=2")
 
 
+@pytest.mark.parametrize("target", [4, 24, 64, 128])
+def test_lmax2_partition_sizes(target):
+    """The l_max = 2 candidate pass with partitions of about `target` records:
+    partitions of up to 32 records take the one-warp match path, larger ones
+    are compared 32 by 32 records. The network is the same for every target."""
+    rep = generate_config1(12_000, seed=66)
+    off, cols, deg, st = gpu_csr(rep, 2, "deletion", partition_target=target)
+    to, tc, _, _ = gpu_csr(rep, 2, "tile")
+    assert_csr_equal(off, cols, to, tc, f"deletion (target {target}) vs tile, l_max=2")
+    check_invariants(off, cols, deg, rep.n)
+
+
+def test_lmax2_variant_shared_by_thousands():
+    """More than 4,000 distinct strings share one variant (a 10-letter string
+    with two letters inserted anywhere): one partition holds them all, with
+    over 12 million candidate pairs among its records."""
+    rng = np.random.default_rng(71)
+    base = "CASSLGQETQ"
+    letters = np.array(list(ALPHABET))
+    seen = set()
+    while len(seen) < 5000:
+        t = list(base)
+        for _ in range(2):
+            t.insert(int(rng.integers(0, len(t) + 1)), str(letters[rng.integers(0, len(letters))]))
+        seen.add("".join(t))
+    rep = from_strings(sorted(seen) + generate_config1(2000, seed=72).strings())
+    off, cols, deg, st = gpu_csr(rep, 2, "deletion")
+    to, tc, _, _ = gpu_csr(rep, 2, "tile")
+    assert_csr_equal(off, cols, to, tc, "deletion vs tile, l_max=2, one variant shared by 5,000 strings")
+    check_invariants(off, cols, deg, rep.n)
+    rows = sample_rows(deg, 20, seed=7, top=5)
+    roff, rcols = oracle.rows(rep.chars, rep.offsets, rows, max_dist=2)
+    assert_rows_equal(off, cols, rows, roff, rcols, "sampled oracle rows")
+
+
 def test_lmax2_deletion_method_matches_tile_2e4():
     rep = generate_config1(20_000, seed=64)
     off, cols, deg, st = gpu_csr(rep, 2, "auto")
