@@ -8,7 +8,7 @@ namespace tcr {
 // AUTO picks the deletion method from this many strings on (l_max <= 1), and
 // for l_max = 2 from kAutoDeletion2MinN on.
 constexpr int64_t kAutoDeletionMinN = 2048;
-constexpr int64_t kAutoDeletion2MinN = 3072;
+constexpr int64_t kAutoDeletion2MinN = 2560;
 
 // Largest input the deletion records can address (distinct-string ids use 25 bits).
 constexpr int64_t kDeletionMaxN = 1LL << 25;
