@@ -798,7 +798,7 @@ tcrnet_status extend_impl(tcrnet_handle h, const uint8_t* chars, const int64_t* 
     // next to the repertoire.
     const DeletionIndex& ix = h->ix;
     const bool merge = !tile && opt.insert_rebuild == 0 && m > 0 && m * kMergeMaxShare <= n_old && ix.valid() && ix.uid &&
-                       ix.n == n_old && h->threshold >= 1 && N <= kDeletionMaxN &&
+                       ix.n == n_old && h->threshold == 1 && N <= kDeletionMaxN &&
                        ix.R + m + pn.lensum <= kMergeMaxPartitionFill * ix.P;
     tcrnet_graph* g = new (std::nothrow) tcrnet_graph();
     if (!g) return TCRNET_ENOMEM;

@@ -1316,8 +1316,13 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         P = std::max<int64_t>(1, std::min<int64_t>(R2 / target + 1, 1LL << 30));
         DevBuf pcnt;
         TCR_CHECK(pcnt.alloc(sizeof(int32_t) * P, s));
-        TCR_CHECK(poff.alloc(sizeof(int64_t) * (P + 1), s));
-        TCR_CHECK(recs.alloc(sizeof(uint64_t) * std::max<int64_t>(R2, 1), s));
+        if (keep_index) {  // the variant records are the handle's query index
+            TCR_CHECK(poff.alloc_owned(sizeof(int64_t) * (P + 1), s));
+            TCR_CHECK(recs.alloc_owned(sizeof(uint64_t) * std::max<int64_t>(R2, 1), s));
+        } else {
+            TCR_CHECK(poff.alloc(sizeof(int64_t) * (P + 1), s));
+            TCR_CHECK(recs.alloc(sizeof(uint64_t) * std::max<int64_t>(R2, 1), s));
+        }
         TCR_CUDA(cudaMemsetAsync(pcnt.as<void>(), 0, sizeof(int32_t) * P, s));
         k_var2_records<false><<<grid_for(n), kThreads, 0, s>>>(ucanon.as<Canon>(), ulen.as<uint8_t>(), d_U, n,
                                                                (uint32_t)P, pcnt.as<int32_t>(), nullptr, nullptr);
@@ -1349,7 +1354,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         k_var2_pairs<true><<<pgrid, kThreads, 0, s>>>(poff.as<int64_t>(), P, recs.as<uint64_t>(),
                                                       ccur_b.as<int32_t>(), coff.as<int64_t>(), ccols.as<int32_t>());
         TCR_LAUNCH_CHECK();
-        recs.reset();
+        if (!keep_index) recs.reset();
         TCR_CHECK(sort_rows(coff.as<int64_t>(), ccols.as<int32_t>(), n, s, num_sms));
         E2_cap = std::max<int64_t>(NC, 1);
         TCR_CHECK(edges.alloc(sizeof(int2) * E2_cap, s));
@@ -1403,7 +1408,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     // that graph of U nodes instead of the n-node network); allocated before
     // the fork so the side stream may write it
     DevBuf uedges;
-    const bool keep_edges = keep_index && join && E > 0;
+    const bool keep_edges = keep_index && (join || cand2) && E > 0;
     if (keep_edges) TCR_CHECK(uedges.alloc_owned(sizeof(int2) * E, s));
     // each list's own members (after its member list exists), the narrowed
     // offsets and the kept edges go to the side stream, next to the neighbour
@@ -1419,7 +1424,9 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
                                                     Sbuf.as<int32_t>());
     TCR_LAUNCH_CHECK();
     if (off32.as<void>()) TCR_CHECK(narrow_offsets(off64.as<int64_t>(), off32.as<int32_t>(), n + 1, fs));
-    if (keep_edges && !overflow) {  // the one-pass buffer holds every edge: segments to one array
+    if (keep_edges && cand2) {  // already one contiguous list
+        TCR_CUDA(cudaMemcpyAsync(uedges.as<void>(), edges.as<void>(), sizeof(int2) * E, cudaMemcpyDeviceToDevice, fs));
+    } else if (keep_edges && !overflow) {  // the one-pass buffer holds every edge: segments to one array
         SegBases sb;
         sb.base[0] = 0;
         for (int g = 0; g < kEdgeSegs; ++g) sb.base[g + 1] = sb.base[g] + (int64_t)segs[g];
@@ -1510,7 +1517,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     out.n_fallback = h_err[2];
     out.closed_total = SD;
     out.two_pass_join = n_two_pass;
-    if (keep_index && join) {
+    if (keep_index && (join || cand2)) {
         out.index.ucanon = static_cast<Canon*>(ucanon.release());
         out.index.umult = static_cast<int32_t*>(umult.release());
         out.index.mem_off = static_cast<int64_t*>(mem_off.release());
@@ -1790,13 +1797,213 @@ k_query_emit(IndexView ix, const int2* __restrict__ hits, int64_t nh, const int6
     }
 }
 
+// ---- l_max = 2 queries against the resident variant records ----------------
+//
+// A query string's variants with up to two deletions (the run-start rule of
+// the records) are looked up in the resident partitions; every resident
+// distinct string with a record of equal 32-bit hash is a candidate (repeats
+// and hash collisions included: two strings within two edits share a variant,
+// so no neighbour is missed), and each distinct candidate is checked with the
+// exact bit-parallel distance, the query being the pattern.
+
+// Length of a canonical string: the number of its nonzero 5-bit codes.
+__device__ __forceinline__ int canon_len(const Canon& c) {
+    constexpr uint64_t kFieldLow = 0x84210842108421ull;  // bit 0 of each of the 12 fields
+    int L = 0;
+#pragma unroll
+    for (int w = 0; w < kCanonWords; ++w) {
+        const uint64_t x = c.w[w] & ~kTagBits;
+        L += __popcll((x | (x >> 1) | (x >> 2) | (x >> 3) | (x >> 4)) & kFieldLow);
+    }
+    return L;
+}
+
+// This lane's share of the variants of c (length L): the full string (lane 0)
+// and every variant whose first deletion is at position lane or lane + 32.
+template <typename Fn>
+__device__ __forceinline__ void lane_variants2(const Canon& c, int L, int lane, Fn fn) {
+    if (lane == 0) fn(c);
+    for (int p = lane; p < L; p += 32) {
+        if (!run_start(c, p)) continue;
+        const Canon d = delete_at(c, p);
+        fn(d);
+        for (int q = p + 1; q < L; ++q)
+            if (q == p + 1 || run_start(c, q)) fn(delete_at(d, q - 1));  // position q of c is q - 1 of d
+    }
+}
+
+// Candidates of each query, a warp per query: COUNT stores their number in
+// qcnt[j]; WRITE stores the candidate strings at qoff[j] onwards (slots from a
+// per-warp counter; both passes see the same records).
+template <bool WRITE>
+__global__ void __launch_bounds__(kThreads)
+k_q2_cand(IndexView ix, const Canon* __restrict__ qcanon, const uint8_t* __restrict__ qlen, int64_t m,
+          int64_t* __restrict__ qcnt, const int64_t* __restrict__ qoff, int32_t* __restrict__ out) {
+    __shared__ unsigned long long wpos[kWarps];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < m; j += nw) {
+        const Canon c = load_canon(qcanon + j);
+        const int L = qlen[j];
+        const int64_t base = WRITE ? qoff[j] : 0;
+        if (lane == 0) wpos[w] = 0;
+        __syncwarp();
+        long long cnt = 0;
+        lane_variants2(c, L, lane, [&](const Canon& v) {
+            const uint64_t h = hash_canon(v);
+            const uint32_t pid = part_of(h, ix.P);
+            for (int64_t k = ix.poff[pid], k1 = ix.poff[pid + 1]; k < k1; ++k) {
+                const uint64_t r = ix.recs[k];
+                if ((uint32_t)(r >> 32) != (uint32_t)h) continue;
+                if constexpr (!WRITE) ++cnt;
+                else out[base + (int64_t)atomicAdd(&wpos[w], 1ull)] = (int32_t)(uint32_t)r;
+            }
+        });
+        if constexpr (!WRITE) {
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(kFull, cnt, d);
+            if (lane == 0) qcnt[j] = cnt;
+        }
+        __syncwarp();
+    }
+}
+
+// Each query's distinct candidates (sorted row, repeats adjacent) checked with
+// the bit-parallel distance (Myers 1999, Hyyro 2001), the query's letter masks
+// in shared memory (lane k builds letter k + 1's), the candidate as the text:
+// flag[e] = 1 for a resident string within two edits, and ocnt[j] = the total
+// of their member counts.
+__global__ void __launch_bounds__(kThreads)
+k_q2_verify(IndexView ix, const Canon* __restrict__ qcanon, const uint8_t* __restrict__ qlen, int64_t m,
+            const int64_t* __restrict__ coff, const int32_t* __restrict__ ccols, uint8_t* __restrict__ flag,
+            int64_t* __restrict__ ocnt) {
+    __shared__ uint64_t speq[kWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < m; j += nw) {
+        const Canon cq = load_canon(qcanon + j);
+        const int Lq = qlen[j];
+        uint64_t mk = 0;
+        for (int k = 0; k < Lq; ++k)
+            if (code_at(cq, k) == (uint32_t)(lane + 1)) mk |= 1ull << k;
+        speq[w][lane] = mk;
+        __syncwarp();
+        const uint64_t top = 1ull << (Lq - 1);
+        long long tot = 0;
+        const int64_t a = coff[j], b = coff[j + 1];
+        for (int64_t e = a + lane; e < b; e += 32) {
+            const int32_t u = ccols[e];
+            uint8_t f = 0;
+            if (e == a || ccols[e - 1] != u) {  // first of its repeats
+                const Canon cu = load_canon(ix.ucanon + u);
+                const int Lu = canon_len(cu);
+                if (Lu - Lq <= 2 && Lq - Lu <= 2) {
+                    uint64_t vp = ~0ull, vn = 0;
+                    int score = Lq;
+                    for (int k = 0; k < Lu; ++k) {
+                        const uint64_t eq = speq[w][code_at(cu, k) - 1];
+                        const uint64_t xv = eq | vn;
+                        const uint64_t xh = (((eq & vp) + vp) ^ vp) | eq;
+                        uint64_t hp = vn | ~(xh | vp);
+                        uint64_t hn = vp & xh;
+                        score += ((hp & top) ? 1 : 0) - ((hn & top) ? 1 : 0);
+                        hp = (hp << 1) | 1ull;
+                        hn <<= 1;
+                        vp = hn | ~(xv | hp);
+                        vn = hp & xv;
+                    }
+                    f = score <= 2 ? 1 : 0;
+                }
+            }
+            flag[e] = f;
+            if (f) tot += ix.umult[u];
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) tot += __shfl_xor_sync(kFull, tot, d);
+        if (lane == 0) ocnt[j] = tot;
+        __syncwarp();
+    }
+}
+
+// The members of each query's accepted resident strings into its row at
+// ooff[j] onwards (a warp per query, the lanes over each member list).
+__global__ void __launch_bounds__(kThreads)
+k_q2_emit(IndexView ix, int64_t m, const int64_t* __restrict__ coff, const int32_t* __restrict__ ccols,
+          const uint8_t* __restrict__ flag, const int64_t* __restrict__ ooff, int32_t* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < m; j += nw) {
+        int64_t pos = ooff[j];
+        const int64_t a = coff[j], b = coff[j + 1];
+        for (int64_t e0 = a; e0 < b; e0 += 32) {
+            const int64_t e = e0 + lane;
+            const bool f = e < b && flag[e];
+            const int32_t u = f ? ccols[e] : 0;
+            for (unsigned bal = __ballot_sync(kFull, f); bal; bal &= bal - 1) {
+                const int32_t uu = __shfl_sync(kFull, u, __ffs(bal) - 1);
+                const int64_t m0 = ix.mem_off[uu], m1 = ix.mem_off[uu + 1];
+                for (int64_t k = m0 + lane; k < m1; k += 32) out[pos + (k - m0)] = ix.members[k];
+                pos += m1 - m0;
+            }
+        }
+    }
+}
+
 }  // namespace
+
+// l_max = 2: candidates of the query strings' variants, sorted per query,
+// checked, then the accepted strings' members, sorted per query.
+static tcrnet_status deletion_query2(const DeletionIndex& ix, const Packed& q, DevBuf& off64, DevBuf& cols,
+                                     DevBuf& count, int64_t* nnz_out, cudaStream_t s, int num_sms) {
+    const int64_t m = q.n;
+    IndexView v{ix.ucanon, ix.umult, ix.mem_off, ix.members, ix.recs, ix.poff, (uint32_t)ix.P};
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(m, kWarps), (int64_t)num_sms * 32);
+    DevBuf qcnt, coff, ccols, flag, ocnt;
+    TCR_CHECK(qcnt.alloc(sizeof(int64_t) * m, s));
+    TCR_CHECK(coff.alloc(sizeof(int64_t) * (m + 1), s));
+    k_q2_cand<false><<<grid, kThreads, 0, s>>>(v, q.canon_in.as<Canon>(), q.lens.as<uint8_t>(), m,
+                                               qcnt.as<int64_t>(), nullptr, nullptr);
+    TCR_LAUNCH_CHECK();
+    TCR_CHECK(scan_exclusive_i64(qcnt.as<int64_t>(), coff.as<int64_t>(), m, s));
+    int64_t NC = 0;
+    TCR_CUDA(cudaMemcpyAsync(&NC, coff.as<int64_t>() + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaStreamSynchronize(s));
+    TCR_CHECK(ccols.alloc(sizeof(int32_t) * std::max<int64_t>(NC, 1), s));
+    TCR_CHECK(flag.alloc(std::max<int64_t>(NC, 1), s));
+    TCR_CHECK(ocnt.alloc(sizeof(int64_t) * m, s));
+    if (NC > 0) {
+        k_q2_cand<true><<<grid, kThreads, 0, s>>>(v, q.canon_in.as<Canon>(), q.lens.as<uint8_t>(), m, nullptr,
+                                                  coff.as<int64_t>(), ccols.as<int32_t>());
+        TCR_LAUNCH_CHECK();
+        TCR_CHECK(sort_rows(coff.as<int64_t>(), ccols.as<int32_t>(), m, s, num_sms));
+    }
+    k_q2_verify<<<grid, kThreads, 0, s>>>(v, q.canon_in.as<Canon>(), q.lens.as<uint8_t>(), m, coff.as<int64_t>(),
+                                          ccols.as<int32_t>(), flag.as<uint8_t>(), ocnt.as<int64_t>());
+    TCR_LAUNCH_CHECK();
+    TCR_CHECK(off64.alloc_owned(sizeof(int64_t) * (m + 1), s));
+    TCR_CHECK(scan_exclusive_i64(ocnt.as<int64_t>(), off64.as<int64_t>(), m, s));
+    int64_t nnz = 0;
+    TCR_CUDA(cudaMemcpyAsync(&nnz, off64.as<int64_t>() + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TCR_CUDA(cudaStreamSynchronize(s));
+    TCR_CHECK(cols.alloc_owned(sizeof(int32_t) * nnz, s));
+    TCR_CHECK(count.alloc_owned(sizeof(int32_t) * m, s));
+    if (nnz > 0) {
+        k_q2_emit<<<grid, kThreads, 0, s>>>(v, m, coff.as<int64_t>(), ccols.as<int32_t>(), flag.as<uint8_t>(),
+                                            off64.as<int64_t>(), cols.as<int32_t>());
+        TCR_LAUNCH_CHECK();
+        TCR_CHECK(sort_rows(off64.as<int64_t>(), cols.as<int32_t>(), m, s, num_sms));
+    }
+    TCR_CHECK(degree_from_offsets(off64.as<int64_t>(), count.as<int32_t>(), m, s));
+    *nnz_out = nnz;
+    return TCRNET_OK;
+}
 
 tcrnet_status deletion_query(const DeletionIndex& ix, const Packed& q, int T, DevBuf& off64, DevBuf& cols,
                              DevBuf& count, int64_t* nnz_out, cudaStream_t s, int num_sms) {
     const int64_t m = q.n;
     *nnz_out = 0;
     if (!ix.valid()) return TCRNET_ESTATE;
+    if (T == 2) return deletion_query2(ix, q, off64, cols, count, nnz_out, s, num_sms);
     IndexView v{ix.ucanon, ix.umult, ix.mem_off, ix.members, ix.recs, ix.poff, (uint32_t)ix.P};
     DevBuf qcnt;
     TCR_CHECK(qcnt.alloc(sizeof(int64_t) * m, s));

@@ -12,7 +12,7 @@ from synthgen import from_strings, generate_config1
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("method,threshold", [("deletion", 1), ("tile", 1), ("tile", 2)])
+@pytest.mark.parametrize("method,threshold", [("deletion", 1), ("tile", 1), ("tile", 2), ("deletion", 2)])
 def test_components_and_removal(method, threshold):
     rep = generate_config1(20_000, seed=81)
     with tn.tcrnet_build_flat(rep.chars, rep.offsets, threshold, method=method) as g:
@@ -42,9 +42,10 @@ def test_components_edge_cases():
         assert labels.size == 0 and nc == 0 and lcc == 0
 
 
-def test_neighbor_degree():
+@pytest.mark.parametrize("threshold", [1, 2])
+def test_neighbor_degree(threshold):
     rep = generate_config1(20_000, seed=82)
-    with tn.tcrnet_build_flat(rep.chars, rep.offsets, 1) as g:
+    with tn.tcrnet_build_flat(rep.chars, rep.offsets, threshold) as g:
         off, cols, _ = g.copy_csr()
         knn = g.neighbor_degree()
     ref = analytics.neighbor_degree(np.asarray(off, dtype=np.int64), cols)

@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("method,n,threshold", [("deletion", 6000, 1), ("tile", 1500, 1), ("tile", 1200, 2),
-                                                ("deletion", 3000, 0)])
+                                                ("deletion", 3000, 0), ("deletion", 4000, 2)])
 def test_save_load_round_trip(tmp_path, method, n, threshold):
     rep = generate_config1(n, seed=101)
     path = str(tmp_path / "net.tcr")

@@ -27,7 +27,8 @@ def build(rep, method, fail_at=0, threshold=1):
     return st, (tn.Graph(h.value) if st == tn.OK else None)
 
 
-@pytest.mark.parametrize("method,n,threshold", [("deletion", 3000, 1), ("tile", 800, 1), ("tile", 600, 2)])
+@pytest.mark.parametrize("method,n,threshold", [("deletion", 3000, 1), ("tile", 800, 1), ("tile", 600, 2),
+                                                ("deletion", 3000, 2)])
 def test_every_build_allocation_failure_is_clean(method, n, threshold):
     rep = generate_config1(n, seed=91)
     st, g = build(rep, method, threshold=threshold)
@@ -53,12 +54,13 @@ def test_every_build_allocation_failure_is_clean(method, n, threshold):
     assert failures >= 5
 
 
-def test_query_and_insert_allocation_failures_keep_the_handle():
+@pytest.mark.parametrize("threshold", [1, 2])
+def test_query_and_insert_allocation_failures_keep_the_handle(threshold):
     base = generate_config1(3000, seed=92)
     add = generate_config1(400, seed=93)
     q = from_strings(add.strings()[:50])
     lib = tn.load_library()
-    with tn.tcrnet_build_flat(base.chars, base.offsets, 1, method="deletion") as g:
+    with tn.tcrnet_build_flat(base.chars, base.offsets, threshold, method="deletion") as g:
         before = g.copy_csr()
         with g.query_flat(q.chars, q.offsets) as r:
             qref = r.copy_csr()

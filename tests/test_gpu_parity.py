@@ -571,6 +571,68 @@ def test_lmax2_variant_shared_by_thousands():
     assert_rows_equal(off, cols, rows, roff, rcols, "sampled oracle rows")
 
 
+def _edited_queries(strs, rng, k):
+    """k resident strings, each with 0, 1 or 2 random edits (substitution,
+    deletion, insertion), plus strings with no neighbour at all."""
+    letters = np.array(list(ALPHABET))
+    out = []
+    for i in rng.choice(len(strs), k, replace=False):
+        t = list(strs[i])
+        for _ in range(int(rng.integers(0, 3))):
+            pos = int(rng.integers(0, len(t)))
+            op = int(rng.integers(0, 3))
+            if op == 0:
+                t[pos] = str(letters[rng.integers(0, len(letters))])
+            elif op == 1 and len(t) > 1:
+                del t[pos]
+            elif len(t) < 48:
+                t.insert(pos, str(letters[rng.integers(0, len(letters))]))
+        out.append("".join(t))
+    return out + ["A", "W" * 48, "CAAAF", "CAAF", "CASSLGQF"]
+
+
+def test_lmax2_index_queries_match_oracle_and_tile():
+    """Queries of an l_max = 2 deletion build go through its variant records
+    (method DELETION) and equal the all-pairs query and the oracle."""
+    rep = generate_config1(20_000, seed=75)
+    rng = np.random.default_rng(76)
+    q = from_strings(_edited_queries(rep.strings(), rng, 400))
+    with tn.tcrnet_build_flat(rep.chars, rep.offsets, 2) as g:
+        assert g.stats()["method"] == tn.METHOD_DELETION
+        with g.query_flat(q.chars, q.offsets) as r:
+            qo, qc, qd = r.copy_csr()
+            assert r.stats()["method"] == tn.METHOD_DELETION
+        with g.query_flat(q.chars, q.offsets, method="tile") as r:
+            to, tc, _ = r.copy_csr()
+    assert_csr_equal(qo, qc, to, tc, "l_max=2 index queries vs all-pairs queries")
+    ro, rc = oracle.neighbors(rep.chars, rep.offsets, q.chars, q.offsets, max_dist=2)
+    assert_csr_equal(qo, qc, ro, rc, "l_max=2 index queries vs oracle")
+    assert np.array_equal(np.asarray(qd), np.diff(np.asarray(qo, dtype=np.int64)))
+
+
+def test_lmax2_index_queries_edge_strings_and_shared_variant():
+    """Index queries at l_max = 2 on runs, seams, duplicates and a variant
+    shared by thousands of resident strings (rows of thousands of candidates)."""
+    rng = np.random.default_rng(77)
+    base = "CASSLGQETQ"
+    letters = np.array(list(ALPHABET))
+    crowd = set()
+    while len(crowd) < 3000:
+        t = list(base)
+        for _ in range(2):
+            t.insert(int(rng.integers(0, len(t) + 1)), str(letters[rng.integers(0, len(letters))]))
+        crowd.add("".join(t))
+    strs = edge_strings() + sorted(crowd) + edge_strings()[:50]
+    rep = from_strings(strs)
+    qs = from_strings(edge_strings()[:200] + [base, base[:-1], base + "F", "CASSLGQETQYF"] + sorted(crowd)[:30])
+    with tn.tcrnet_build_flat(rep.chars, rep.offsets, 2, method="deletion") as g:
+        with g.query_flat(qs.chars, qs.offsets) as r:
+            qo, qc, _ = r.copy_csr()
+            assert r.stats()["method"] == tn.METHOD_DELETION
+    ro, rc = oracle.neighbors(rep.chars, rep.offsets, qs.chars, qs.offsets, max_dist=2)
+    assert_csr_equal(qo, qc, ro, rc, "l_max=2 index queries, edge strings and a crowded variant")
+
+
 def test_lmax2_deletion_method_matches_tile_2e4():
     rep = generate_config1(20_000, seed=64)
     off, cols, deg, st = gpu_csr(rep, 2, "auto")
