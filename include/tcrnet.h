@@ -220,8 +220,11 @@ tcrnet_status tcrnet_query_flat(tcrnet_handle h, const uint8_t *chars, const int
 /* tcrnet_query_flat with options: opt->stream orders the call (NULL options or
  * stream: the build's stream); opt->method selects the search: AUTO (the
  * deletion index when the build kept one, i.e. a deletion-method build with
- * l_max = 1, else the tile kernel), TILE, or DELETION (ENOTSUP without an
- * index). Both searches return identical lists. */
+ * l_max = 1 or 2, else the tile kernel), TILE, or DELETION (ENOTSUP without an
+ * index). Both searches return identical lists. The l_max = 2 index holds the
+ * variant records of the build (every distinct string with up to two
+ * deletions); a query looks up its own variants and checks each distinct
+ * candidate with the exact distance. */
 tcrnet_status tcrnet_query_ex(tcrnet_handle h, const uint8_t *chars, const int64_t *offsets, int64_t m,
                               int32_t mem, const tcrnet_options *opt, tcrnet_handle *out);
 
