@@ -784,6 +784,28 @@ def run_ours(args):
                                                    "unit": "Tops/s", "frac": ach / peak,
                                                    "ops_per_pair": f"17 x mean length ({mean_len:.2f}), estimate"}})
                     row[label] = entry
+                if n2 == 100_000:
+                    # queries against the l_max = 2 build: its variant-record index
+                    # vs the all-pairs kernel, 1,000 strings of the resident model
+                    from synthgen import generate as _gen
+
+                    q2 = _gen(1000, seed=2024, template_seed=7, ins_max=6, len_lo=10, len_hi=20)
+                    qc2 = torch.from_numpy(q2.chars).to(dev)
+                    qo2 = torch.from_numpy(q2.offsets).to(dev)
+                    qrow = {}
+                    with tn.tcrnet_build_flat(c2, o2, 2, stream=stream) as g2:
+                        for qlabel, qm in (("index", "deletion"), ("all_pairs", "tile")):
+                            g2.query_flat(qc2, qo2, method=qm, stream=stream).free()
+                            qts = []
+                            for _ in range(5):
+                                t0 = time.perf_counter()
+                                rq = g2.query_flat(qc2, qo2, method=qm, stream=stream)
+                                qts.append((time.perf_counter() - t0) * 1e3)
+                                qn = rq.info()[1]
+                                rq.free()
+                            qrow[qlabel] = {"ms": statistics.median(qts), "answers": qn}
+                    qrow["timing"] = "host time of tcrnet_query_ex with its stream sync, median of 5; queries in device memory"
+                    row["query_1000"] = qrow
                 lm2[str(n2)] = row
             line["lmax2"] = lm2
         if "batched" in legs:
