@@ -348,8 +348,9 @@ class Graph:
 
     def insert_flat(self, chars, offsets, stream=None, profile=False, rebuild=False, fail_alloc_at=0):
         """Append strings in flat layout (numpy or torch, host or device) as new nodes.
-        A deletion build merges them into its network and index; rebuild=True
-        rebuilds the grown repertoire instead (same network)."""
+        A deletion build at l_max = 1 merges up to n/32 of them into its network
+        and index; other inserts, and rebuild=True, rebuild the grown repertoire
+        (same network)."""
         lib = load_library()
         cp, op, m, mem, keep = _flat_args(chars, offsets)
         opt = make_options(stream=stream, profile=profile, insert_rebuild=rebuild, fail_alloc_at=fail_alloc_at)

@@ -610,6 +610,26 @@ def test_lmax2_index_queries_match_oracle_and_tile():
     assert np.array_equal(np.asarray(qd), np.diff(np.asarray(qo, dtype=np.int64)))
 
 
+def test_lmax2_index_after_insert():
+    """An insert into an l_max = 2 deletion build rebuilds network and index:
+    queries afterwards see the new strings."""
+    rep = generate_config1(6000, seed=78)
+    add = generate_config1(800, seed=79)
+    rng = np.random.default_rng(80)
+    full = from_strings(rep.strings() + add.strings())
+    q = from_strings(_edited_queries(full.strings(), rng, 200))
+    with tn.tcrnet_build_flat(rep.chars, rep.offsets, 2, method="deletion") as g:
+        g.insert_flat(add.chars, add.offsets)
+        fo, fc, _ = g.copy_csr()
+        with g.query_flat(q.chars, q.offsets) as r:
+            qo, qc, _ = r.copy_csr()
+            assert r.stats()["method"] == tn.METHOD_DELETION
+    oo, oc, _ = oracle.network(full.chars, full.offsets, max_dist=2)
+    assert_csr_equal(fo, fc, oo, oc, "l_max=2 network after insert")
+    ro, rc = oracle.neighbors(full.chars, full.offsets, q.chars, q.offsets, max_dist=2)
+    assert_csr_equal(qo, qc, ro, rc, "l_max=2 index queries after insert")
+
+
 def test_lmax2_index_queries_edge_strings_and_shared_variant():
     """Index queries at l_max = 2 on runs, seams, duplicates and a variant
     shared by thousands of resident strings (rows of thousands of candidates)."""
