@@ -254,6 +254,21 @@ def test_full_size_8e5_sampled_rows_and_invariants():
     assert_csr_equal(off, cols, o2, c2, "tile vs deletion at 8e5")
 
 
+def test_lmax2_1e6_sampled_rows_and_invariants():
+    """l_max = 2 at 1e6 strings (the deletion method's candidates, nnz ~4.4e8):
+    global invariants in full, 200 sampled rows plus the 50 highest-degree rows
+    against the oracle's full neighbour lists."""
+    rep = generate_config1(1_000_000, seed=13)
+    with tn.tcrnet_build_flat(rep.chars, rep.offsets, 2) as g:
+        assert g.stats()["method"] == tn.METHOD_DELETION
+        off, cols, deg = g.copy_csr()
+    off = np.asarray(off, dtype=np.int64)
+    check_invariants(off, cols, deg, rep.n)
+    rows = sample_rows(deg, 200, seed=14, top=50)
+    roff, rcols = oracle.rows(rep.chars, rep.offsets, rows, max_dist=2)
+    assert_rows_equal(off, cols, rows, roff, rcols, "1e6 l_max=2 sampled rows")
+
+
 def test_full_size_8e6_sampled_rows_int64_offsets():
     # config 3: N = 8,000,000, insertion 0-9 aa, nnz > 2^31 -> int64 offsets
     from synthgen import generate_config3
