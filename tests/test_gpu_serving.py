@@ -77,13 +77,15 @@ def _split(strs, sizes):
     return out
 
 
-def test_engine_results_same_alone_and_in_mix():
+@pytest.mark.parametrize("threshold", [1, 2])
+def test_engine_results_same_alone_and_in_mix(threshold):
     base = generate_config1(30_000, seed=41)
     pool = generate_config1(40_000, seed=42).strings()
+    pool[::20] = base.strings()[: len(pool[::20])]  # queries with many neighbours as well
     rng = np.random.default_rng(3)
     sizes = [int(x) for x in np.exp(rng.uniform(0, np.log(3000), size=40))]
     reqs_in = _split(pool, sizes)
-    with tn.tcrnet_build_flat(base.chars, base.offsets, 1, method="deletion") as g:
+    with tn.tcrnet_build_flat(base.chars, base.offsets, threshold, method="deletion") as g:
         alone = []
         for q in reqs_in:
             with g.query_flat(q.chars, q.offsets) as r:
