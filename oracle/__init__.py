@@ -62,6 +62,10 @@ def _bind(path: str):
     lib.oracle_lists_free.restype = None
     lib.oracle_max_threads.argtypes = []
     lib.oracle_max_threads.restype = ctypes.c_int
+    lib.baseline_within.argtypes = [u8p, ctypes.c_int64, u8p, ctypes.c_int64, ctypes.c_int32]
+    lib.baseline_within.restype = ctypes.c_int
+    lib.baseline_neighbors.argtypes = lib.oracle_neighbors.argtypes
+    lib.baseline_neighbors.restype = lp
     return lib
 
 
@@ -105,7 +109,7 @@ def lev(a, b, lib=None) -> int:
 
 
 def neighbors(chars, offsets, qchars=None, qoffsets=None, self_index=None,
-              max_dist: int = 1, nthreads: int = 0, lib=None):
+              max_dist: int = 1, nthreads: int = 0, lib=None, _fn="oracle_neighbors"):
     """For each query, all repertoire indices within edit distance `max_dist`.
 
     Without queries, the queries are the repertoire itself with self-exclusion
@@ -130,8 +134,8 @@ def neighbors(chars, offsets, qchars=None, qoffsets=None, self_index=None,
     if self_index is not None:
         self_index = np.ascontiguousarray(self_index, dtype=np.int64)
         si = _i64(self_index)
-    res = lib.oracle_neighbors(_u8(chars), _i64(offsets), n, _u8(qchars), _i64(qoffsets), m,
-                               si, int(max_dist), int(nthreads))
+    res = getattr(lib, _fn)(_u8(chars), _i64(offsets), n, _u8(qchars), _i64(qoffsets), m,
+                            si, int(max_dist), int(nthreads))
     if not res:
         raise MemoryError("oracle_neighbors failed")
     try:
@@ -151,7 +155,7 @@ def network(chars, offsets, max_dist: int = 1, nthreads: int = 0, lib=None):
     return off, cols, np.diff(off).astype(np.int32)
 
 
-def rows(chars, offsets, row_ids, max_dist: int = 1, nthreads: int = 0, lib=None):
+def rows(chars, offsets, row_ids, max_dist: int = 1, nthreads: int = 0, lib=None, _fn="oracle_neighbors"):
     """Complete neighbour lists of selected rows of the network."""
     chars = np.ascontiguousarray(chars, dtype=np.uint8)
     offsets = np.ascontiguousarray(offsets, dtype=np.int64)
@@ -162,9 +166,39 @@ def rows(chars, offsets, row_ids, max_dist: int = 1, nthreads: int = 0, lib=None
     qchars = np.concatenate([chars[offsets[i]:offsets[i + 1]] for i in row_ids]) if row_ids.size \
         else np.zeros(0, dtype=np.uint8)
     return neighbors(chars, offsets, qchars, qoff, self_index=row_ids, max_dist=max_dist,
-                     nthreads=nthreads, lib=lib)
+                     nthreads=nthreads, lib=lib, _fn=_fn)
 
 
 def max_threads(lib=None) -> int:
     lib = lib or load()
     return int(lib.oracle_max_threads())
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline (not the oracle): the paper's early-abort per-pair test
+# (Methods "GPU-based network generation", Listing 1, restated correctly: the
+# row-minimum abort plus the length-difference skip). Used only to time the
+# paper's own algorithm on the host; pinned to the oracle by the test suite.
+
+def baseline_within(a, b, max_dist: int = 1, lib=None) -> bool:
+    """lev(a, b) <= max_dist by the early-abort table."""
+    lib = lib or load()
+    x = _bytes(a)
+    y = _bytes(b)
+    r = int(lib.baseline_within(_u8(x), len(x) - 1, _u8(y), len(y) - 1, int(max_dist)))
+    if r < 0:
+        raise MemoryError("baseline_within failed")
+    return bool(r)
+
+
+def baseline_network(chars, offsets, max_dist: int = 1, nthreads: int = 0, lib=None):
+    """Full network by the baseline test (offsets int64, cols int32, degree int32)."""
+    off, cols = neighbors(chars, offsets, max_dist=max_dist, nthreads=nthreads, lib=lib,
+                          _fn="baseline_neighbors")
+    return off, cols, np.diff(off).astype(np.int32)
+
+
+def baseline_rows(chars, offsets, row_ids, max_dist: int = 1, nthreads: int = 0, lib=None):
+    """Neighbour lists of selected rows by the baseline test."""
+    return rows(chars, offsets, row_ids, max_dist=max_dist, nthreads=nthreads, lib=lib,
+                _fn="baseline_neighbors")

@@ -32,6 +32,10 @@
  *
  * Strings are arbitrary byte strings here; alphabet checks belong to the
  * library under test, not to the definition.
+ *
+ * The file also holds the CPU baseline of the bench (baseline_within,
+ * baseline_neighbors: the paper's early-abort algorithm); it is not used as the
+ * oracle, and the test suite pins its answers to oracle_lev.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -99,6 +103,39 @@ typedef struct oracle_lists {
     int32_t *cols;    /* nnz */
 } oracle_lists;
 
+/* Concatenate m row lists into one CSR and free them; NULL if `failed` or on
+ * allocation failure. */
+static oracle_lists *lists_from_rows(ivec *rows, int64_t m, int failed) {
+    oracle_lists *out = (oracle_lists *)calloc(1, sizeof(oracle_lists));
+    if (out) {
+        out->rows = m;
+        out->offsets = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m + 1));
+        int64_t total = 0;
+        for (int64_t q = 0; q < m; ++q) total += rows[q].len;
+        out->nnz = total;
+        out->cols = (int32_t *)malloc(sizeof(int32_t) * (size_t)(total > 0 ? total : 1));
+        if (!out->offsets || !out->cols) failed = 1;
+        if (!failed) {
+            int64_t o = 0;
+            for (int64_t q = 0; q < m; ++q) {
+                out->offsets[q] = o;
+                if (rows[q].len) memcpy(out->cols + o, rows[q].v, sizeof(int32_t) * (size_t)rows[q].len);
+                o += rows[q].len;
+            }
+            out->offsets[m] = o;
+        }
+    }
+    for (int64_t q = 0; q < m; ++q) free(rows[q].v);
+    free(rows);
+    if (failed && out) {
+        free(out->offsets);
+        free(out->cols);
+        free(out);
+        out = NULL;
+    }
+    return out;
+}
+
 /*
  * For each query q in [0, m): every repertoire index j in [0, n), ascending,
  * with j != self_index[q] and lev(query_q, s_j) <= max_dist.
@@ -136,34 +173,95 @@ oracle_lists *oracle_neighbors(const uint8_t *chars, const int64_t *offsets, int
             }
         }
     }
-    oracle_lists *out = (oracle_lists *)calloc(1, sizeof(oracle_lists));
-    if (out) {
-        out->rows = m;
-        out->offsets = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m + 1));
-        int64_t total = 0;
-        for (int64_t q = 0; q < m; ++q) total += rows[q].len;
-        out->nnz = total;
-        out->cols = (int32_t *)malloc(sizeof(int32_t) * (size_t)(total > 0 ? total : 1));
-        if (!out->offsets || !out->cols) failed = 1;
-        if (!failed) {
-            int64_t o = 0;
-            for (int64_t q = 0; q < m; ++q) {
-                out->offsets[q] = o;
-                if (rows[q].len) memcpy(out->cols + o, rows[q].v, sizeof(int32_t) * (size_t)rows[q].len);
-                o += rows[q].len;
-            }
-            out->offsets[m] = o;
+    return lists_from_rows(rows, m, failed);
+}
+
+/*
+ * CPU BASELINE, not the oracle: the paper's own per-pair test (Methods
+ * "GPU-based network generation" and its Listing 1), restated correctly, for
+ * the timed CPU baseline of the bench. It answers "lev(a, b) <= max_dist?"
+ * with the same two-row table as oracle_lev, filled one row of `a` at a time,
+ * and stops as soon as every entry of the finished row exceeds max_dist: the
+ * smallest entry of a row never decreases from one row to the next (each entry
+ * extends an entry of the row above by a non-negative cost, or the entry to its
+ * left, whose chain starts at the row's first column i >= i - 1), so the final
+ * distance would exceed max_dist as well. Pairs whose lengths differ by more
+ * than max_dist are answered without a table, because the distance is at least
+ * the difference of the lengths. The answer equals oracle_lev(...) <= max_dist
+ * for every pair (pinned by the test suite); only the work differs.
+ */
+int baseline_within(const uint8_t *a, int64_t la, const uint8_t *b, int64_t lb, int32_t max_dist) {
+    int64_t dl = la > lb ? la - lb : lb - la;
+    if (dl > max_dist) return 0;
+    int stackbuf[2 * 130];
+    int *buf = stackbuf;
+    if (lb + 1 > 130) {
+        buf = (int *)malloc(sizeof(int) * 2 * (size_t)(lb + 1));
+        if (!buf) return -1;
+    }
+    int *row = buf;            /* row i - 1 of the table */
+    int *next = buf + (lb + 1); /* row i */
+    for (int64_t j = 0; j <= lb; ++j) row[j] = (int)j;
+    int within = 1;
+    for (int64_t i = 1; i <= la; ++i) {
+        next[0] = (int)i;
+        int row_min = next[0];
+        for (int64_t j = 1; j <= lb; ++j) {
+            int sub = row[j - 1] + ((a[i - 1] == b[j - 1]) ? 0 : 1);
+            int del = row[j] + 1;
+            int ins = next[j - 1] + 1;
+            int v = sub < del ? sub : del;
+            v = v < ins ? v : ins;
+            next[j] = v;
+            if (v < row_min) row_min = v;
+        }
+        int *t = row;
+        row = next;
+        next = t;
+        if (row_min > max_dist) { /* early abort: no later row can come back under the bound */
+            within = 0;
+            break;
         }
     }
-    for (int64_t q = 0; q < m; ++q) free(rows[q].v);
-    free(rows);
-    if (failed && out) {
-        free(out->offsets);
-        free(out->cols);
-        free(out);
-        out = NULL;
+    if (within) within = row[lb] <= max_dist;
+    if (buf != stackbuf) free(buf);
+    return within;
+}
+
+/*
+ * The network rows of the queries by baseline_within (same contract and
+ * output as oracle_neighbors; nthreads = 1 gives the single-core baseline).
+ */
+oracle_lists *baseline_neighbors(const uint8_t *chars, const int64_t *offsets, int64_t n,
+                                 const uint8_t *qchars, const int64_t *qoffsets, int64_t m,
+                                 const int64_t *self_index, int32_t max_dist, int32_t nthreads) {
+    ivec *rows = (ivec *)calloc((size_t)(m > 0 ? m : 1), sizeof(ivec));
+    if (!rows) return NULL;
+    int failed = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < m; ++q) {
+        const uint8_t *a = qchars + qoffsets[q];
+        int64_t la = qoffsets[q + 1] - qoffsets[q];
+        int64_t self = self_index ? self_index[q] : -1;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == self) continue;
+            int w = baseline_within(a, la, chars + offsets[j], offsets[j + 1] - offsets[j], max_dist);
+            if (w < 0) {
+                failed = 1;
+                break;
+            }
+            if (w && ivec_push(&rows[q], (int32_t)j)) {
+                failed = 1;
+                break;
+            }
+        }
     }
-    return out;
+    return lists_from_rows(rows, m, failed);
 }
 
 int64_t oracle_lists_rows(const oracle_lists *l) { return l->rows; }

@@ -268,3 +268,33 @@ def test_empty_and_single(oracle_lib):
     rep = from_strings(["CASSF"])
     off, cols, deg = oracle.network(rep.chars, rep.offsets, lib=oracle_lib)
     assert list(off) == [0, 0] and cols.size == 0
+
+
+# ---------------------------------------------------------------------------
+# Pins on the CPU baseline (the paper's early-abort test, timed by the bench)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("alphabet,max_len", [("AC", 6), ("ACG", 4)])
+def test_baseline_within_matches_recurrence_bruteforce(oracle_lib, alphabet, max_len):
+    """The row-minimum abort and the length skip change the work, never the
+    answer: lev(a, b) <= T for every pair and every T in 0..3."""
+    strs = all_strings(alphabet, max_len)
+    for a in strs:
+        for b in strs:
+            d = lev_recursive(a, b)
+            for t in range(4):
+                assert oracle.baseline_within(a, b, t, lib=oracle_lib) == (d <= t), (a, b, t)
+
+
+@pytest.mark.parametrize("threshold", [0, 1, 2])
+def test_baseline_network_equals_oracle(oracle_lib, threshold):
+    strs = generate_config1(1500, seed=41).strings() + ["CAAAF", "CAAF", "AAB", "AB", "W" * 30, "W" * 29]
+    rep = from_strings(strs)
+    off, cols, _ = oracle.network(rep.chars, rep.offsets, max_dist=threshold, lib=oracle_lib)
+    boff, bcols, _ = oracle.baseline_network(rep.chars, rep.offsets, max_dist=threshold, lib=oracle_lib)
+    assert np.array_equal(off, boff) and np.array_equal(cols, bcols)
+    # one core gives the same lists
+    rows_ = np.array([0, 7, 1499, 1500], dtype=np.int64)
+    r1 = oracle.baseline_rows(rep.chars, rep.offsets, rows_, max_dist=threshold, nthreads=1, lib=oracle_lib)
+    r2 = oracle.rows(rep.chars, rep.offsets, rows_, max_dist=threshold, lib=oracle_lib)
+    assert np.array_equal(r1[0], r2[0]) and np.array_equal(r1[1], r2[1])

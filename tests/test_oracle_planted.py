@@ -76,3 +76,42 @@ def test_planted_mistake_is_caught(tmp_path, name, orig, mut):
     lib_path = oracle.build(force=True, src=str(src), out=str(tmp_path / f"lib_{name}.so"))
     lib = oracle.load(lib_path)
     assert not _pins_pass(lib), f"planted mistake {name} was not caught by any pin"
+
+
+# Planted mistakes in the CPU baseline (the paper's early-abort test): each must
+# fail the baseline's pin against the recurrence.
+BASELINE_MUTATIONS = [
+    ("abort-at-bound", "if (row_min > max_dist) {", "if (row_min >= max_dist) {"),
+    ("length-skip-off-by-one", "if (dl > max_dist) return 0;", "if (dl >= max_dist) return 0;"),
+    ("no-final-check", "if (within) within = row[lb] <= max_dist;", ""),
+    ("row-min-is-last-entry", "if (v < row_min) row_min = v;", "row_min = v;"),
+]
+
+
+def _baseline_pins_pass(lib) -> bool:
+    try:
+        strs = all_strings("AC", 5)
+        for a in strs:
+            for b in strs:
+                d = lev_recursive(a, b)
+                for t in range(3):
+                    if oracle.baseline_within(a, b, t, lib=lib) != (d <= t):
+                        return False
+    except Exception:
+        return False
+    return True
+
+
+def test_unmutated_baseline_passes(oracle_lib):
+    assert _baseline_pins_pass(oracle_lib)
+
+
+@pytest.mark.parametrize("name,orig,mut", BASELINE_MUTATIONS, ids=[m[0] for m in BASELINE_MUTATIONS])
+def test_planted_baseline_mistake_is_caught(tmp_path, name, orig, mut):
+    text = open(SRC).read()
+    assert orig in text, f"mutation anchor for {name} not found"
+    src = tmp_path / f"baseline_{name}.c"
+    src.write_text(text.replace(orig, mut, 1))
+    lib_path = oracle.build(force=True, src=str(src), out=str(tmp_path / f"libb_{name}.so"))
+    lib = oracle.load(lib_path)
+    assert not _baseline_pins_pass(lib), f"planted baseline mistake {name} was not caught"
