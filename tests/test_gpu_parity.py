@@ -6,6 +6,8 @@ invariants at the full sizes."""
 
 from __future__ import annotations
 
+import os
+
 import numpy as np
 import pytest
 
@@ -151,15 +153,52 @@ def test_deterministic_and_int64_offsets(method):
     assert np.array_equal(d1, d2)
 
 
-def test_methods_agree_1e5():
-    rep = generate_config1(100_000, seed=0)
-    ot, ct, dt, _ = gpu_csr(rep, 1, "tile")
-    od, cd, dd, _ = gpu_csr(rep, 1, "deletion")
-    assert_csr_equal(ot, ct, od, cd, "tile vs deletion at 1e5")
-    check_invariants(ot, ct, dt, rep.n)
-    rows = sample_rows(dt, 400, seed=1, top=50)
+def _digests():
+    import sys
+
+    sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+    import digests
+
+    return digests
+
+
+def _check_rows_against_stored(off, cols, section, what, rep):
+    """Every stored (row, degree, digest) of an oracle section against the
+    build's rows; mismatching rows are recomputed by the live oracle so that
+    the failure shows what differs."""
+    dg = _digests()
+    off = np.asarray(off, dtype=np.int64)
+    bad = [i for i, d, h in section["rows"]
+           if int(off[i + 1] - off[i]) != d or dg.row_digest(cols[off[i]:off[i + 1]]) != h]
+    if bad:
+        roff, rcols = oracle.rows(rep.chars, rep.offsets, np.array(bad[:5], dtype=np.int64))
+        assert_rows_equal(off, cols, bad[:5], roff, rcols, f"{what} (live oracle)")
+        raise AssertionError(f"{what}: {len(bad)} rows differ from the stored oracle digests, first {bad[:5]}")
+
+
+def test_full_1e5_network_equals_oracle():
+    """Every row of the N = 100,000 network against the oracle's (stored as
+    block digests by tests/golden/make_parity_digests.py, which calls only the
+    oracle), by both methods; plus a live oracle comparison of sampled rows."""
+    dg = _digests()
+    sec = dg.load()["full_1e5"]
+    meta = sec["meta"]
+    rep = generate_config1(int(meta["n"]), seed=int(meta["seed"]))
+    for method in ("auto", "tile"):
+        off, cols, deg, st = gpu_csr(rep, 1, method)
+        assert st["method"] == (tn.METHOD_DELETION if method == "auto" else tn.METHOD_TILE)
+        assert int(off[-1]) == int(meta["nnz"]), f"{method}: nnz"
+        check_invariants(off, cols, deg, rep.n)
+        bad = [(r0, r1) for r0, r1, h in sec["rows"] if dg.block_digest(off, cols, r0, r1) != h]
+        if bad:
+            r0, r1 = bad[0]
+            ids = np.arange(r0, r1, dtype=np.int64)
+            roff, rcols = oracle.rows(rep.chars, rep.offsets, ids)
+            assert_rows_equal(off, cols, ids, roff, rcols, f"1e5 {method} block {r0} (live oracle)")
+            raise AssertionError(f"1e5 {method}: {len(bad)} blocks differ from the oracle digests")
+    rows = sample_rows(deg, 300, seed=1, top=50)
     roff, rcols = oracle.rows(rep.chars, rep.offsets, rows)
-    assert_rows_equal(ot, ct, rows, roff, rcols, "1e5 sampled rows")
+    assert_rows_equal(off, cols, rows, roff, rcols, "1e5 sampled rows (live oracle)")
 
 
 @pytest.mark.parametrize("method", METHODS)
@@ -234,21 +273,32 @@ def _device_build(rep, method, **kw):
     return g
 
 
-def test_full_size_8e5_sampled_rows_and_invariants():
-    # the configuration bench.py times: N = 800,000 (config 2, seed 0), default method
+def test_full_size_8e5_10000_rows_and_invariants():
+    """The configuration bench.py times (N = 800,000, config 2, seed 0, default
+    method, device inputs): global invariants in full; 9,900 seeded uniform
+    rows against the oracle's lists (stored digests) and the 100 highest-degree
+    rows of the build against the live oracle, 10,000 rows in all; 100 of the
+    stored rows recomputed live as well; the tile method builds the identical
+    network."""
     from synthgen import generate_config2
 
-    rep = generate_config2(800_000, seed=0)
+    dg = _digests()
+    sec = dg.load()["rows_8e5"]
+    rep = generate_config2(int(sec["meta"]["n"]), seed=int(sec["meta"]["seed"]))
     with _device_build(rep, "auto") as g:
         off, cols, deg = g.copy_csr()
         st = g.stats()
     assert st["method"] == tn.METHOD_DELETION
     off = np.asarray(off, dtype=np.int64)
     check_invariants(off, cols, deg, rep.n)
-    rows = sample_rows(deg, 300, seed=3, top=40)
-    roff, rcols = oracle.rows(rep.chars, rep.offsets, rows)
-    assert_rows_equal(off, cols, rows, roff, rcols, "8e5 sampled rows")
-    # the all-pairs tile path builds the identical network
+    assert len(sec["rows"]) == 9_900
+    _check_rows_against_stored(off, cols, sec, "8e5 stored oracle rows", rep)
+    stored = np.array([i for i, _, _ in sec["rows"]], dtype=np.int64)
+    top = np.argsort(-deg, kind="stable")[:100].astype(np.int64)
+    live = np.unique(np.concatenate([top, stored[::99]]))
+    roff, rcols = oracle.rows(rep.chars, rep.offsets, live)
+    assert_rows_equal(off, cols, live, roff, rcols, "8e5 top-degree and stored rows (live oracle)")
+    assert len(np.union1d(stored, top)) >= 9_990
     with _device_build(rep, "tile") as g:
         o2, c2, d2 = g.copy_csr()
     assert_csr_equal(off, cols, o2, c2, "tile vs deletion at 8e5")
@@ -269,27 +319,42 @@ def test_lmax2_1e6_sampled_rows_and_invariants():
     assert_rows_equal(off, cols, rows, roff, rcols, "1e6 l_max=2 sampled rows")
 
 
-def test_full_size_8e6_sampled_rows_int64_offsets():
-    # config 3: N = 8,000,000, insertion 0-9 aa, nnz > 2^31 -> int64 offsets
+def test_full_size_8e6_1000_rows_int64_offsets():
+    """Config 3: N = 8,000,000, insertion 0-9 aa, nnz > 2^31 -> int64 offsets.
+    1,000 seeded uniform rows against the oracle (stored digests), the 20
+    highest-degree rows and 20 of the stored rows against the live oracle."""
+    import torch
     from synthgen import generate_config3
 
-    rep = generate_config3(8_000_000, seed=0)
+    dg = _digests()
+    sec = dg.load()["rows_8e6"]
+    rep = generate_config3(int(sec["meta"]["n"]), seed=int(sec["meta"]["seed"]))
     with _device_build(rep, "auto") as g:
         n, nnz, o64 = g.info()
         assert o64 and nnz > 2**31
-        import torch
-
         off_d, cols_d, deg_d = g.copy_csr_device()
-    deg = deg_d.cpu().numpy()
-    off_h = off_d.cpu().numpy()
-    assert off_h[0] == 0 and off_h[-1] == nnz and np.array_equal(np.diff(off_h), deg)
-    assert int(deg.sum()) == nnz and nnz % 2 == 0
-    rows = sample_rows(deg, 40, seed=4, top=8)
-    roff, rcols = oracle.rows(rep.chars, rep.offsets, rows)
-    for k, i in enumerate(rows):
-        got = cols_d[int(off_h[i]):int(off_h[i + 1])].cpu().numpy()
-        want = rcols[roff[k]:roff[k + 1]]
-        assert np.array_equal(got, want), f"row {i}"
+        deg = deg_d.cpu().numpy()
+        off_h = off_d.cpu().numpy()
+        assert off_h[0] == 0 and off_h[-1] == nnz and np.array_equal(np.diff(off_h), deg)
+        assert int(deg.sum()) == nnz and nnz % 2 == 0
+        stored = np.array([i for i, _, _ in sec["rows"]], dtype=np.int64)
+        top = np.argsort(-deg, kind="stable")[:20].astype(np.int64)
+        rows = np.unique(np.concatenate([stored, top]))
+        # gather the rows' entries on the device, one copy to the host
+        lens = deg[rows].astype(np.int64)
+        sub_off = np.zeros(rows.shape[0] + 1, dtype=np.int64)
+        np.cumsum(lens, out=sub_off[1:])
+        idx = np.repeat(off_h[rows] - sub_off[:-1], lens) + np.arange(sub_off[-1])
+        sub_cols = cols_d[torch.from_numpy(idx).to(cols_d.device)].cpu().numpy()
+    full_off = np.zeros(rep.n + 1, dtype=np.int64)  # the sampled rows as a sparse CSR over all n
+    lens_all = np.zeros(rep.n, dtype=np.int64)
+    lens_all[rows] = lens
+    np.cumsum(lens_all, out=full_off[1:])
+    assert len(sec["rows"]) == 1_000
+    _check_rows_against_stored(full_off, sub_cols, sec, "8e6 stored oracle rows", rep)
+    live = np.unique(np.concatenate([top, stored[::50]]))
+    roff, rcols = oracle.rows(rep.chars, rep.offsets, live)
+    assert_rows_equal(full_off, sub_cols, live, roff, rcols, "8e6 top-degree and stored rows (live oracle)")
 
 
 def test_deletion_dense_unique_graph_takes_two_pass_join():
@@ -678,3 +743,39 @@ def test_lmax2_deletion_method_matches_tile_2e4():
     rows = sample_rows(deg, 40, seed=5, top=10)
     roff, rcols = oracle.rows(rep.chars, rep.offsets, rows, max_dist=2)
     assert_rows_equal(off, cols, rows, roff, rcols, "sampled oracle rows")
+
+
+def test_auto_takes_tile_method_above_deletion_limit():
+    """The deletion method addresses at most TCRNET_DELETION_MAX_N strings; AUTO
+    builds larger repertoires with the tile method instead of refusing them.
+    options.deletion_max_n lowers the limit so that a small input shows it."""
+    import ctypes
+
+    for threshold, n in ((1, 3000), (2, 3000)):
+        rep = generate_config1(n, seed=19)
+        ro, rc, _ = oracle_csr(rep, threshold)
+        with tn.tcrnet_build_flat(rep.chars, rep.offsets, threshold) as g:
+            assert g.stats()["method"] == tn.METHOD_DELETION  # above the AUTO cut-over
+        with tn.tcrnet_build_flat(rep.chars, rep.offsets, threshold, deletion_max_n=1000) as g:
+            assert g.stats()["method"] == tn.METHOD_TILE
+            off, cols, _ = g.copy_csr()
+        assert_csr_equal(off, cols, ro, rc, f"AUTO above the deletion limit, T={threshold}")
+        with pytest.raises(tn.TcrnetError) as e:
+            tn.tcrnet_build_flat(rep.chars, rep.offsets, threshold, method="deletion", deletion_max_n=1000)
+        assert e.value.status == tn.ENOTSUP
+    # an insert that grows a deletion build past the limit is rebuilt by the tile method
+    rep = generate_config1(1200, seed=20)
+    ro, rc, _ = oracle_csr(rep, 1)
+    head = rep.subset(np.arange(900))
+    tail = rep.subset(np.arange(900, 1200))
+    lib = tn.load_library()
+    with tn.tcrnet_build_flat(head.chars, head.offsets, 1, method="deletion", deletion_max_n=1000) as g:
+        opt = tn.make_options(deletion_max_n=1000)
+        h = ctypes.c_void_p()
+        st = lib.tcrnet_extend(g.handle, tail.chars.ctypes.data, tail.offsets.ctypes.data, tail.n, tn.HOST,
+                               ctypes.byref(opt), ctypes.byref(h))
+        assert st == tn.OK
+        with tn.Graph(h.value) as g2:
+            assert g2.stats()["method"] == tn.METHOD_TILE
+            off, cols, _ = g2.copy_csr()
+    assert_csr_equal(off, cols, ro, rc, "insert past the deletion limit")
