@@ -36,8 +36,10 @@
  *    device unless stated otherwise.
  *  - A handle is thread-compatible, not thread-safe: do not use one handle
  *    from two host threads at once.
- *  - TCRNET_EDEVICE / TCRNET_ETIMEOUT poison the handle being built or used;
- *    free it. No call leaves a sticky device error behind on purpose.
+ *  - TCRNET_EDEVICE poisons the handle being built or used; free it. The only
+ *    bounded device loop (the union-find of tcrnet_components) reports running
+ *    out as TCRNET_ETIMEOUT and leaves the handle usable. No call leaves a
+ *    sticky device error behind on purpose.
  *  - Memory spaces: arguments tagged `mem` are TCRNET_HOST (pageable or pinned
  *    host memory) or TCRNET_DEVICE (device memory of the handle's device).
  */
@@ -63,7 +65,7 @@ typedef enum tcrnet_status {
     TCRNET_ENOTSUP = 4,   /* combination not supported (deletion method with l_max >= 3, ...) */
     TCRNET_ENOMEM = 5,    /* device or host allocation failed; nothing leaked */
     TCRNET_EDEVICE = 6,   /* a CUDA error; the handle is poisoned */
-    TCRNET_ETIMEOUT = 7,  /* a bounded device wait ran out; the handle is poisoned */
+    TCRNET_ETIMEOUT = 7,  /* a bounded device loop ran out (analytics; the handle stays usable) */
     TCRNET_ESTATE = 8,    /* the handle cannot serve this call (e.g. query on a query result) */
     TCRNET_ECAPACITY = 9  /* input larger than a fixed-capacity entry point accepts */
 } tcrnet_status;
@@ -100,8 +102,20 @@ typedef struct tcrnet_options {
                                  index where that is cheaper (deletion builds with
                                  l_max = 1, inserts of at most 1/32 of the resident
                                  strings), which gives the same network */
-    int32_t reserved[4];      /* must be zero */
+    int32_t link_attempts;    /* testing (tcrnet_components_ex): attempts each edge of
+                                 the union-find may make to link its two roots before
+                                 the call gives up with TCRNET_ETIMEOUT; 0 = default
+                                 (2^20, never reached in practice) */
+    int32_t deletion_max_n;   /* testing: largest repertoire the deletion method takes;
+                                 0 = default (TCRNET_DELETION_MAX_N). AUTO builds
+                                 larger repertoires with the tile method; an explicit
+                                 TCRNET_METHOD_DELETION above it is TCRNET_ENOTSUP */
+    int32_t reserved[2];      /* must be zero */
 } tcrnet_options;
+
+/* Largest repertoire of the deletion method (distinct-string ids take 25 bits
+ * of a join record). Larger inputs are built by the tile method under AUTO. */
+#define TCRNET_DELETION_MAX_N (1 << 25)
 
 /* Defaults: AUTO method, current device, legacy default stream, no profiling. */
 void tcrnet_options_init(tcrnet_options *opt);
@@ -283,6 +297,16 @@ tcrnet_status tcrnet_extend(tcrnet_handle h, const uint8_t *chars, const int64_t
 tcrnet_status tcrnet_components(tcrnet_handle h, const uint8_t *keep, int32_t *labels, int32_t mem,
                                 int64_t *n_components, int64_t *largest);
 
+/* tcrnet_components with options: opt->stream orders the call (NULL options or
+ * stream: the handle's stream); opt->link_attempts bounds the attempts of each
+ * edge to link its two roots (testing; 0 = default). When an edge runs out of
+ * attempts the kernel records it and returns, every other edge is still
+ * processed, and the call reports TCRNET_ETIMEOUT with *n_components and
+ * *largest set to 0; labels are then undefined. The handle and the device stay
+ * usable: nothing waits without a bound. */
+tcrnet_status tcrnet_components_ex(tcrnet_handle h, const uint8_t *keep, int32_t *labels, int32_t mem,
+                                   const tcrnet_options *opt, int64_t *n_components, int64_t *largest);
+
 /* Average neighbour degree (Methods "Overview of network theory concepts",
  * <d_nn>): knn[i] = (sum over neighbours j of d(j)) / d(i), 0 for isolated nodes;
  * n doubles in memory space `mem`. */
@@ -323,9 +347,13 @@ const char *tcrnet_last_cuda_error(void);
 /*
  * Node degrees of the network of at most TCRNET_NOALLOC_MAX_N strings, without
  * allocating any memory. The paper has no counterpart: this entry point exists
- * for callers that cannot call cudaMalloc (code running while a CUDA graph is
- * being captured, programs whose device memory is fully reserved up front by
- * another allocator, hosts that forbid allocation after start-up).
+ * for callers that cannot call cudaMalloc. Two kinds of program are in that
+ * position: one whose device memory has been handed in full, at start-up, to
+ * another allocator (a framework's caching pool that reserves all free memory,
+ * so a new allocation fails or would have to evict its cache), and one that
+ * forbids device allocation after start-up to keep its latency bounded (an
+ * allocation can synchronise the device or map new pages). Every other entry
+ * point allocates its workspace and results itself.
  *
  * d_chars / d_offsets: the flat string layout of tcrnet_build_flat, in device
  * memory of the calling thread's current device. d_degree: device output of n
@@ -343,14 +371,43 @@ const char *tcrnet_last_cuda_error(void);
  * Working memory is one fixed file-scope device array of about 0.5 MB that
  * every device loading the library keeps until the process exits. The first
  * call on each device looks up that array's device address (a one-time set-up
- * step), so make the first call on a device before any stream capture. All
- * calls share the array and it keeps the previous call's contents (each call
- * clears what must start at zero), so calls that overlap on the GPU, from
- * different streams or host threads, race: serialise them.
+ * step) and keeps it for the life of the process, so make the first call on a
+ * device before any stream capture, and do not call this entry point on a
+ * device after cudaDeviceReset of that device in the same process (the kept
+ * address then refers to the old context). All calls share the array and it
+ * keeps the previous call's contents (each call clears what must start at
+ * zero), so calls that overlap on the GPU, from different streams or host
+ * threads, race: serialise them. The call waits for its stream before
+ * returning (it reads back the error word).
  */
 tcrnet_status tcrnet_degree_noalloc(const uint8_t *d_chars, const int64_t *d_offsets, int64_t n,
                                     int32_t threshold, int32_t *d_degree, void *stream,
                                     int64_t *bad_index);
+
+/* Kinds of tcrnet_probe_int_issue. */
+typedef enum tcrnet_probe_kind {
+    TCRNET_PROBE_LOP3 = 0,  /* three-input logic op */
+    TCRNET_PROBE_SHF = 1,   /* funnel shift */
+    TCRNET_PROBE_IADD = 2,  /* 32-bit add */
+    TCRNET_PROBE_IMAD = 3,  /* 32-bit multiply-add */
+    TCRNET_PROBE_POPC = 4,  /* xor, population count, add */
+    TCRNET_PROBE_MIX = 5    /* logic op, add and multiply-add in turn */
+} tcrnet_probe_kind;
+
+/*
+ * Integer-issue microbenchmark (a measurement aid; the paper has no
+ * counterpart). Launches one kernel on `stream` in which each of n_threads
+ * threads (a multiple of 256) runs `iters` rounds of independent dependency
+ * chains of 32-bit integer instructions of the given kind and writes one word
+ * to d_out[thread] (device memory of the current device, n_threads uint32,
+ * caller-owned). *ops_per_thread receives the integer instructions each
+ * thread issues in its rounds, so that a caller timing the launch with CUDA
+ * events on `stream` gets the per-SM integer rate the all-pairs tile kernel is
+ * bound by. Returns without waiting for the kernel. Errors: TCRNET_EINVAL for
+ * bad arguments, TCRNET_EDEVICE if the launch fails.
+ */
+tcrnet_status tcrnet_probe_int_issue(int32_t kind, int32_t iters, uint32_t *d_out, int64_t n_threads,
+                                     void *stream, int64_t *ops_per_thread);
 
 #ifdef __cplusplus
 }

@@ -28,6 +28,7 @@ OK, EINVAL, EBADCHAR, ETOOLONG, ENOTSUP, ENOMEM, EDEVICE, ETIMEOUT, ESTATE, ECAP
 STATUS_NAMES = ["OK", "EINVAL", "EBADCHAR", "ETOOLONG", "ENOTSUP", "ENOMEM", "EDEVICE", "ETIMEOUT", "ESTATE",
                 "ECAPACITY"]
 NOALLOC_MAX_N = 16384
+DELETION_MAX_N = 1 << 25
 METHOD_AUTO, METHOD_TILE, METHOD_DELETION = 0, 1, 2
 METHODS = {"auto": METHOD_AUTO, "tile": METHOD_TILE, "deletion": METHOD_DELETION}
 HOST, DEVICE = 0, 1
@@ -44,7 +45,9 @@ class tcrnet_options(ctypes.Structure):
         ("partition_target", ctypes.c_int32),
         ("fail_alloc_at", ctypes.c_int32),
         ("insert_rebuild", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 4),
+        ("link_attempts", ctypes.c_int32),
+        ("deletion_max_n", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
 
@@ -102,7 +105,8 @@ SYMBOLS = [
     "tcrnet_strerror", "tcrnet_last_error_index", "tcrnet_version", "tcrnet_last_cuda_error",
     "tcrnet_degree_noalloc", "tcrnet_query_ex", "tcrnet_insert_flat", "tcrnet_insert_ex", "tcrnet_insert",
     "tcrnet_components", "tcrnet_neighbor_degree", "tcrnet_build_batched",
-    "tcrnet_degree_histogram", "tcrnet_extend", "tcrnet_save", "tcrnet_load",
+    "tcrnet_degree_histogram", "tcrnet_extend", "tcrnet_save", "tcrnet_load", "tcrnet_components_ex",
+    "tcrnet_probe_int_issue",
 ]
 
 
@@ -147,6 +151,8 @@ def load_library(path: str = LIB_PATH):
         lib.tcrnet_build_batched.restype = ctypes.c_int
         lib.tcrnet_components.argtypes = [H, vp, vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]
         lib.tcrnet_components.restype = ctypes.c_int
+        lib.tcrnet_components_ex.argtypes = [H, vp, vp, i32, optp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        lib.tcrnet_components_ex.restype = ctypes.c_int
         lib.tcrnet_neighbor_degree.argtypes = [H, vp, i32]
         lib.tcrnet_neighbor_degree.restype = ctypes.c_int
         lib.tcrnet_insert_flat.argtypes = [H, vp, vp, i64, i32]
@@ -173,6 +179,8 @@ def load_library(path: str = LIB_PATH):
         lib.tcrnet_last_cuda_error.restype = ctypes.c_char_p
         lib.tcrnet_degree_noalloc.argtypes = [vp, vp, i64, i32, vp, vp, ctypes.POINTER(i64)]
         lib.tcrnet_degree_noalloc.restype = ctypes.c_int
+        lib.tcrnet_probe_int_issue.argtypes = [i32, i32, vp, i64, vp, ctypes.POINTER(i64)]
+        lib.tcrnet_probe_int_issue.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -198,7 +206,8 @@ def _stream_ptr(stream):
 
 
 def make_options(method="auto", device=None, stream=None, profile=False, force_offsets64=False,
-                 partition_cap=0, partition_target=0, fail_alloc_at=0, insert_rebuild=False):
+                 partition_cap=0, partition_target=0, fail_alloc_at=0, insert_rebuild=False,
+                 link_attempts=0, deletion_max_n=0):
     lib = load_library()
     o = tcrnet_options()
     lib.tcrnet_options_init(ctypes.byref(o))
@@ -212,6 +221,8 @@ def make_options(method="auto", device=None, stream=None, profile=False, force_o
     o.partition_target = int(partition_target)
     o.fail_alloc_at = int(fail_alloc_at)
     o.insert_rebuild = 1 if insert_rebuild else 0
+    o.link_attempts = int(link_attempts)
+    o.deletion_max_n = int(deletion_max_n)
     return o
 
 
@@ -302,9 +313,10 @@ class Graph:
     def query(self, queries):
         return tcrnet_query(self, queries)
 
-    def components(self, keep=None):
+    def components(self, keep=None, link_attempts=0, stream=None):
         """Connected components (host arrays): (labels int32 [n], n_components, largest).
-        keep: optional uint8 mask of the nodes that stay (node removal)."""
+        keep: optional uint8 mask of the nodes that stay (node removal).
+        link_attempts: testing bound of the union-find (0 = default)."""
         n, _, _ = self.info()
         labels = np.empty(max(n, 1), dtype=np.int32)
         kp = None
@@ -313,8 +325,9 @@ class Graph:
             assert keep.shape[0] == n
             kp = keep.ctypes.data
         nc, lc = ctypes.c_int64(), ctypes.c_int64()
-        _check(load_library().tcrnet_components(self._h, kp, labels.ctypes.data, HOST, ctypes.byref(nc),
-                                                ctypes.byref(lc)), "tcrnet_components")
+        opt = make_options(stream=stream, link_attempts=link_attempts)
+        _check(load_library().tcrnet_components_ex(self._h, kp, labels.ctypes.data, HOST, ctypes.byref(opt),
+                                                   ctypes.byref(nc), ctypes.byref(lc)), "tcrnet_components_ex")
         return labels[:n], nc.value, lc.value
 
     def degree_histogram(self, nbins=None):
@@ -419,11 +432,13 @@ def tcrnet_build(seqs, threshold: int = 1, method="auto", device=None, stream=No
 
 
 def tcrnet_build_flat(chars, offsets, threshold: int = 1, method="auto", device=None, stream=None,
-                      profile=False, force_offsets64=False, partition_cap=0, partition_target=0) -> Graph:
+                      profile=False, force_offsets64=False, partition_cap=0, partition_target=0,
+                      deletion_max_n=0) -> Graph:
     """Network of strings in flat layout (numpy arrays, or torch tensors on host or device)."""
     lib = load_library()
     cp, op, n, mem, keep = _flat_args(chars, offsets)
-    opt = make_options(method, device, stream, profile, force_offsets64, partition_cap, partition_target)
+    opt = make_options(method, device, stream, profile, force_offsets64, partition_cap, partition_target,
+                       deletion_max_n=deletion_max_n)
     h = ctypes.c_void_p()
     st = lib.tcrnet_build_flat(cp, op, n, mem, int(threshold), ctypes.byref(opt), ctypes.byref(h))
     del keep
@@ -507,15 +522,42 @@ def tcrnet_version() -> str:
 
 def tcrnet_degree_noalloc(chars, offsets, degree, threshold: int = 1, stream=None) -> None:
     """Node degrees into the preallocated device tensor `degree` (int32, n), for
-    callers that cannot allocate: torch CUDA tensors in, nothing allocated by
-    the library (see include/tcrnet.h). At most NOALLOC_MAX_N strings."""
+    callers that cannot allocate device memory: torch CUDA tensors in, nothing
+    allocated by the library (see include/tcrnet.h). At most NOALLOC_MAX_N
+    strings. The tensors must be contiguous and on the current CUDA device, and
+    `degree` must hold at least n entries: the kernels write degree[0..n), so
+    these are checked here before anything is launched."""
     import torch
 
-    assert chars.is_cuda and offsets.is_cuda and degree.is_cuda
-    assert chars.dtype == torch.uint8 and offsets.dtype == torch.int64 and degree.dtype == torch.int32
+    if not (chars.is_cuda and offsets.is_cuda and degree.is_cuda):
+        raise ValueError("tcrnet_degree_noalloc: chars, offsets and degree must be CUDA tensors")
+    if not (chars.dtype == torch.uint8 and offsets.dtype == torch.int64 and degree.dtype == torch.int32):
+        raise ValueError("tcrnet_degree_noalloc: dtypes must be uint8 chars, int64 offsets, int32 degree")
+    if not (chars.is_contiguous() and offsets.is_contiguous() and degree.is_contiguous()):
+        raise ValueError("tcrnet_degree_noalloc: tensors must be contiguous")
     n = offsets.numel() - 1
+    if n < 0 or degree.numel() < n:
+        raise ValueError(f"tcrnet_degree_noalloc: degree holds {degree.numel()} entries, {max(n, 0)} needed")
+    dev = torch.cuda.current_device()
+    if not (chars.device.index == dev and offsets.device.index == dev and degree.device.index == dev):
+        raise ValueError("tcrnet_degree_noalloc: tensors must be on the current CUDA device")
     bad = ctypes.c_int64(-1)
     st = load_library().tcrnet_degree_noalloc(chars.data_ptr(), offsets.data_ptr(), n, int(threshold),
                                               degree.data_ptr(), _stream_ptr(stream), ctypes.byref(bad))
     if st != OK:
         raise TcrnetError(st, "tcrnet_degree_noalloc", int(bad.value))
+
+
+PROBE_KINDS = {"lop3": 0, "shf": 1, "iadd": 2, "imad": 3, "popc": 4, "mix": 5}
+
+
+def tcrnet_probe_int_issue(kind: str, iters: int, out, stream=None) -> int:
+    """Launch the integer-issue microbenchmark on `stream` (a torch CUDA stream);
+    `out` is a contiguous uint32-sized (int32) CUDA tensor with one entry per
+    thread (a multiple of 256). Returns the integer instructions each thread
+    issues; the caller times the launch with CUDA events on the same stream."""
+    ops = ctypes.c_int64()
+    st = load_library().tcrnet_probe_int_issue(PROBE_KINDS[kind], int(iters), out.data_ptr(), out.numel(),
+                                               _stream_ptr(stream), ctypes.byref(ops))
+    _check(st, "tcrnet_probe_int_issue")
+    return ops.value

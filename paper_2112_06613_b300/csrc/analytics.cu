@@ -21,7 +21,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kMaxLinkRetries = 1 << 20;
+constexpr int kDefaultLinkAttempts = 1 << 20;
 
 __device__ __forceinline__ int32_t find_root(int32_t* parent, int32_t x) {
     volatile int32_t* vp = parent;
@@ -46,7 +46,7 @@ __global__ void k_cc_init(const uint8_t* __restrict__ keep, int64_t n, int32_t* 
 template <typename Off>
 __global__ void __launch_bounds__(kThreads)
 k_cc_link(const Off* __restrict__ off, const int32_t* __restrict__ cols, int64_t n, int32_t* parent,
-          int* __restrict__ err) {
+          int max_attempts, int* __restrict__ err) {
     const int lane = threadIdx.x & 31;
     const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += stride) {
@@ -57,7 +57,7 @@ k_cc_link(const Off* __restrict__ off, const int32_t* __restrict__ cols, int64_t
             if (j <= i || ((volatile int32_t*)parent)[j] < 0) continue;
             int32_t a = (int32_t)i, c = j;
             int it = 0;
-            for (; it < kMaxLinkRetries; ++it) {
+            for (; it < max_attempts; ++it) {
                 int32_t ra = find_root(parent, a), rc = find_root(parent, c);
                 if (ra == rc) break;
                 if (ra > rc) {
@@ -69,7 +69,7 @@ k_cc_link(const Off* __restrict__ off, const int32_t* __restrict__ cols, int64_t
                 a = ra;
                 c = rc;
             }
-            if (it == kMaxLinkRetries) atomicExch(err, 1);
+            if (it == max_attempts) atomicExch(err, 1);  // gave up on this edge; the host reports it
         }
     }
 }
@@ -181,13 +181,14 @@ __global__ void k_dcc_parent(const int32_t* __restrict__ present, int64_t U, int
     size[u] = 0;
 }
 
-__global__ void k_dcc_link(const int2* __restrict__ edges, int64_t E, int32_t* parent, int* __restrict__ err) {
+__global__ void k_dcc_link(const int2* __restrict__ edges, int64_t E, int32_t* parent, int max_attempts,
+                           int* __restrict__ err) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x) {
         const int2 e = edges[k];
         if (((volatile int32_t*)parent)[e.x] < 0 || ((volatile int32_t*)parent)[e.y] < 0) continue;
         int32_t a = e.x, c = e.y;
         int it = 0;
-        for (; it < kMaxLinkRetries; ++it) {
+        for (; it < max_attempts; ++it) {
             int32_t ra = find_root(parent, a), rc = find_root(parent, c);
             if (ra == rc) break;
             if (ra > rc) {
@@ -199,7 +200,7 @@ __global__ void k_dcc_link(const int2* __restrict__ edges, int64_t E, int32_t* p
             a = ra;
             c = rc;
         }
-        if (it == kMaxLinkRetries) atomicExch(err, 1);
+        if (it == max_attempts) atomicExch(err, 1);  // gave up on this edge; the host reports it
     }
 }
 
@@ -308,7 +309,9 @@ inline unsigned blocks_for(int64_t n, int per_block, int num_sms) {
 }  // namespace
 
 tcrnet_status components(const void* off, bool off64, const int32_t* cols, int64_t n, const uint8_t* keep,
-                         int32_t* labels, int64_t* n_components, int64_t* largest, cudaStream_t s, int num_sms) {
+                         int32_t* labels, int64_t* n_components, int64_t* largest, cudaStream_t s, int num_sms,
+                         int link_attempts) {
+    const int attempts = link_attempts > 0 ? link_attempts : kDefaultLinkAttempts;
     *n_components = 0;
     *largest = 0;
     if (n == 0) return TCRNET_OK;
@@ -322,9 +325,11 @@ tcrnet_status components(const void* off, bool off64, const int32_t* cols, int64
     TCR_LAUNCH_CHECK();
     const unsigned wb = blocks_for(n, kWarps, num_sms);
     if (off64)
-        k_cc_link<int64_t><<<wb, kThreads, 0, s>>>(static_cast<const int64_t*>(off), cols, n, parent.as<int32_t>(), err);
+        k_cc_link<int64_t><<<wb, kThreads, 0, s>>>(static_cast<const int64_t*>(off), cols, n, parent.as<int32_t>(),
+                                                   attempts, err);
     else
-        k_cc_link<int32_t><<<wb, kThreads, 0, s>>>(static_cast<const int32_t*>(off), cols, n, parent.as<int32_t>(), err);
+        k_cc_link<int32_t><<<wb, kThreads, 0, s>>>(static_cast<const int32_t*>(off), cols, n, parent.as<int32_t>(),
+                                                   attempts, err);
     TCR_LAUNCH_CHECK();
     k_cc_label<<<(unsigned)ceil_div(n, kThreads), kThreads, 0, s>>>(n, parent.as<int32_t>(), labels, size.as<int32_t>());
     TCR_LAUNCH_CHECK();
@@ -344,7 +349,8 @@ tcrnet_status components(const void* off, bool off64, const int32_t* cols, int64
 
 tcrnet_status components_distinct(const int32_t* uid, int64_t n, const int2* edges, int64_t E, int64_t U,
                                   const uint8_t* keep, int32_t* labels, int64_t* n_components, int64_t* largest,
-                                  cudaStream_t s, int num_sms) {
+                                  cudaStream_t s, int num_sms, int link_attempts) {
+    const int attempts = link_attempts > 0 ? link_attempts : kDefaultLinkAttempts;
     *n_components = 0;
     *largest = 0;
     if (n == 0) return TCRNET_OK;
@@ -365,7 +371,8 @@ tcrnet_status components_distinct(const int32_t* uid, int64_t n, const int2* edg
                                          size.as<int32_t>());
     TCR_LAUNCH_CHECK();
     if (E > 0) {
-        k_dcc_link<<<blocks_for(E, kThreads, num_sms), kThreads, 0, s>>>(edges, E, parent.as<int32_t>(), err);
+        k_dcc_link<<<blocks_for(E, kThreads, num_sms), kThreads, 0, s>>>(edges, E, parent.as<int32_t>(), attempts,
+                                                                         err);
         TCR_LAUNCH_CHECK();
     }
     k_dcc_flatten<<<gu, kThreads, 0, s>>>(U, parent.as<int32_t>(), root.as<int32_t>());

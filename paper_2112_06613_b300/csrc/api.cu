@@ -397,9 +397,18 @@ tcrnet_status flatten(const char* const* seqs, int64_t n, std::vector<uint8_t>& 
     return TCRNET_OK;
 }
 
+// Largest repertoire the deletion method takes under these options (its join
+// records hold 25-bit distinct-string ids; options.deletion_max_n lowers the
+// limit for tests).
+int64_t deletion_limit(const tcrnet_options& opt) {
+    return (opt.deletion_max_n > 0 && opt.deletion_max_n < kDeletionMaxN) ? (int64_t)opt.deletion_max_n
+                                                                          : kDeletionMaxN;
+}
+
 // The method AUTO stands for: the deletion method from its size cut-over on
-// (l_max <= 2), else the all-pairs kernels.
-int auto_method(int64_t n, int32_t T) {
+// (l_max <= 2) up to its limit, else the all-pairs kernels, which take any n.
+int auto_method(int64_t n, int32_t T, int64_t del_limit) {
+    if (n > del_limit) return TCRNET_METHOD_TILE;
     if (T <= 1 && n >= kAutoDeletionMinN) return TCRNET_METHOD_DELETION;
     if (T == 2 && n >= kAutoDeletion2MinN) return TCRNET_METHOD_DELETION;
     return TCRNET_METHOD_TILE;
@@ -412,7 +421,8 @@ tcrnet_status build_from_packed(tcrnet_graph* h, Packed& pk, int64_t n, int32_t 
                                 Phases& ph, cudaStream_t s, int sms, bool keep_index = true) {
     tcrnet_status st = TCRNET_OK;
     int method = opt.method;
-    if (method == TCRNET_METHOD_AUTO) method = auto_method(n, T);
+    if (method == TCRNET_METHOD_AUTO) method = auto_method(n, T, deletion_limit(opt));
+    if (method == TCRNET_METHOD_DELETION && n > deletion_limit(opt)) return TCRNET_ENOTSUP;
     h->stats.method = method;
     for (int L = 0; L < kMaxLen + 2; ++L) h->bucket_off[L] = pk.bucket_off[L];
     if (n == 0) {
@@ -475,17 +485,20 @@ tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n
     if (T < 0) return TCRNET_EINVAL;
     if (opt.method < TCRNET_METHOD_AUTO || opt.method > TCRNET_METHOD_DELETION) return TCRNET_EINVAL;
     if (opt.partition_target != 0 && (opt.partition_target < 4 || opt.partition_target > 128)) return TCRNET_EINVAL;
+    if (opt.link_attempts < 0 || opt.deletion_max_n < 0) return TCRNET_EINVAL;
     if (T > 2 && opt.method == TCRNET_METHOD_DELETION) return TCRNET_ENOTSUP;  // deletion method: l_max <= 2
+    if (opt.method == TCRNET_METHOD_DELETION && n > deletion_limit(opt)) return TCRNET_ENOTSUP;
     if (rep_off) {
         // batched: one deletion-method pass over all repertoires
         if (T > 2 || opt.method == TCRNET_METHOD_TILE) return TCRNET_ENOTSUP;
         if (nrep < 1 || nrep > 65536 || rep_off[0] != 0 || rep_off[nrep] != n) return TCRNET_EINVAL;
         for (int64_t r = 0; r < nrep; ++r)
             if (rep_off[r + 1] < rep_off[r]) return TCRNET_EINVAL;
+        if (n > deletion_limit(opt)) return TCRNET_ENOTSUP;  // one deletion pass over all repertoires
         opt.method = TCRNET_METHOD_DELETION;
     }
     if (opt.method == TCRNET_METHOD_AUTO)  // decided before packing: only the tile method buckets
-        opt.method = auto_method(n, T);
+        opt.method = auto_method(n, T, deletion_limit(opt));
     DeviceGuard dg;
     TCR_CHECK(dg.set(opt.device));
     int dev = 0;
@@ -742,7 +755,12 @@ tcrnet_status extend_impl(tcrnet_handle h, const uint8_t* chars, const int64_t* 
         opt.profile = opt_in->profile;
         opt.fail_alloc_at = opt_in->fail_alloc_at;
         opt.insert_rebuild = opt_in->insert_rebuild;
+        opt.deletion_max_n = opt_in->deletion_max_n;
+        if (opt.deletion_max_n < 0) return TCRNET_EINVAL;
     }
+    // past the deletion method's limit the grown repertoire is built by the
+    // tile method (the method AUTO would take)
+    if (opt.method == TCRNET_METHOD_DELETION && N > deletion_limit(opt)) opt.method = TCRNET_METHOD_TILE;
     AllocFaultScope fault_scope(opt.fail_alloc_at);
     DeviceGuard dg;
     TCR_CHECK(dg.set(h->device));
@@ -798,7 +816,7 @@ tcrnet_status extend_impl(tcrnet_handle h, const uint8_t* chars, const int64_t* 
     // next to the repertoire.
     const DeletionIndex& ix = h->ix;
     const bool merge = !tile && opt.insert_rebuild == 0 && m > 0 && m * kMergeMaxShare <= n_old && ix.valid() && ix.uid &&
-                       ix.n == n_old && h->threshold == 1 && N <= kDeletionMaxN &&
+                       ix.n == n_old && h->threshold == 1 && N <= deletion_limit(opt) &&
                        ix.R + m + pn.lensum <= kMergeMaxPartitionFill * ix.P;
     tcrnet_graph* g = new (std::nothrow) tcrnet_graph();
     if (!g) return TCRNET_ENOMEM;
@@ -905,10 +923,19 @@ tcrnet_status tcrnet_insert(tcrnet_handle h, const char* const* seqs, int64_t m)
 
 tcrnet_status tcrnet_components(tcrnet_handle h, const uint8_t* keep, int32_t* labels, int32_t mem,
                                 int64_t* n_components, int64_t* largest) {
+    return tcrnet_components_ex(h, keep, labels, mem, nullptr, n_components, largest);
+}
+
+tcrnet_status tcrnet_components_ex(tcrnet_handle h, const uint8_t* keep, int32_t* labels, int32_t mem,
+                                   const tcrnet_options* opt, int64_t* n_components, int64_t* largest) {
+    if (n_components) *n_components = 0;
+    if (largest) *largest = 0;
     if (!h || (mem != TCRNET_HOST && mem != TCRNET_DEVICE)) return TCRNET_EINVAL;
+    if (opt && opt->link_attempts < 0) return TCRNET_EINVAL;
+    const int attempts = opt ? opt->link_attempts : 0;
     DeviceGuard dg;
     TCR_CHECK(dg.set(h->device));
-    cudaStream_t s = h->stream;
+    cudaStream_t s = (opt && opt->stream) ? (cudaStream_t)opt->stream : h->stream;
     const int64_t n = h->n;
     int64_t nc = 0, lc = 0;
     if (n > 0) {
@@ -930,10 +957,10 @@ tcrnet_status tcrnet_components(tcrnet_handle h, const uint8_t* keep, int32_t* l
         }
         if (h->ix.uid) {  // a deletion build: the graph of distinct strings gives the same components
             TCR_CHECK(components_distinct(h->ix.uid, n, h->ix.uedges, h->ix.E, h->ix.U, k, labels ? lab : nullptr, &nc,
-                                          &lc, s, sm_count(h->device)));
+                                          &lc, s, sm_count(h->device), attempts));
         } else {
             TCR_CHECK(components(h->d_offsets, h->offsets64 != 0, h->d_cols, n, k, lab, &nc, &lc, s,
-                                 sm_count(h->device)));
+                                 sm_count(h->device), attempts));
         }
         if (mem == TCRNET_HOST && labels)
             TCR_CUDA(cudaMemcpyAsync(labels, lab, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));

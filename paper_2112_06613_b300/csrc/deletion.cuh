@@ -11,7 +11,8 @@ constexpr int64_t kAutoDeletionMinN = 2048;
 constexpr int64_t kAutoDeletion2MinN = 2560;
 
 // Largest input the deletion records can address (distinct-string ids use 25 bits).
-constexpr int64_t kDeletionMaxN = 1LL << 25;
+constexpr int64_t kDeletionMaxN = TCRNET_DELETION_MAX_N;
+static_assert(kDeletionMaxN == (1LL << 25), "record ids are 25 bits");
 
 // Resident query index of a deletion build (device pointers; owned by the
 // handle, freed with cudaFree): distinct strings, their multiplicities and

@@ -86,8 +86,11 @@ tcrnet_status dp_pass(const TileSide& rows, const TileSide& cols, bool sym, int 
 // ---- analytics.cu ---------------------------------------------------------
 // Connected components of the CSR restricted to keep[i] != 0 (keep may be null):
 // labels[i] = smallest node id of the component, -1 for removed nodes.
+// link_attempts bounds the link attempts of each edge (<= 0: the default
+// bound); TCRNET_ETIMEOUT when an edge ran out of them.
 tcrnet_status components(const void* off, bool off64, const int32_t* cols, int64_t n, const uint8_t* keep,
-                         int32_t* labels, int64_t* n_components, int64_t* largest, cudaStream_t s, int num_sms);
+                         int32_t* labels, int64_t* n_components, int64_t* largest, cudaStream_t s, int num_sms,
+                         int link_attempts = 0);
 // knn[i] = mean degree of i's neighbours (0 for isolated nodes).
 tcrnet_status degree_histogram(const int32_t* deg, int64_t n, int64_t* hist, int64_t nbins, int64_t* max_degree,
                                cudaStream_t s, int num_sms);
@@ -96,7 +99,7 @@ tcrnet_status degree_histogram(const int32_t* deg, int64_t n, int64_t* hist, int
 // members per string); identical results, work ~ U + E instead of nnz.
 tcrnet_status components_distinct(const int32_t* uid, int64_t n, const int2* edges, int64_t E, int64_t U,
                                   const uint8_t* keep, int32_t* labels, int64_t* n_components, int64_t* largest,
-                                  cudaStream_t s, int num_sms);
+                                  cudaStream_t s, int num_sms, int link_attempts = 0);
 tcrnet_status neighbor_degree_distinct(const int32_t* uid, int64_t n, const int2* edges, int64_t E,
                                        const int32_t* umult, int64_t U, double* knn, cudaStream_t s, int num_sms);
 tcrnet_status neighbor_degree(const void* off, bool off64, const int32_t* cols, int64_t n, double* knn,

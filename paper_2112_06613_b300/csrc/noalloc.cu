@@ -1,14 +1,15 @@
 // Node degrees without any device allocation (tcrnet_degree_noalloc).
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA graph is
-// being captured, applications whose memory is fully pre-reserved by another
-// allocator, or embedded hosts that forbid allocation after start-up. This
-// entry point serves them for small repertoires: it is a variant of the pair
-// test count pass that needs no workspace from the caller or from the
-// allocator. Its working memory (the packed strings, their lengths and an
-// error word) lives in one fixed-size file-scope device array,
-// g_noalloc_scratch, which every device that loads the library keeps until the
-// process exits (about 0.5 MB).
+// Some callers cannot call cudaMalloc: applications whose device memory was
+// handed in full to another allocator at start-up (a caching pool that
+// reserves all free memory), and services that forbid device allocation after
+// start-up because an allocation can synchronise the device or map pages and
+// so break their latency bound. This entry point serves them for small
+// repertoires: it is a variant of the pair test count pass that needs no
+// workspace from the caller or from the allocator. Its working memory (the
+// packed strings, their lengths and an error word) lives in one fixed-size
+// file-scope device array, g_noalloc_scratch, which every device that loads
+// the library keeps until the process exits (about 0.5 MB).
 //
 // The caller passes device inputs (chars, offsets) and a device output
 // (degree). Each call first clears the error word and the output, then packs
@@ -23,7 +24,9 @@
 //
 // All calls share the one array and it keeps the last call's contents, so
 // calls that overlap on the GPU (different streams, different host threads)
-// race and must be serialised by the caller.
+// race and must be serialised by the caller. The array's device address is
+// looked up once per device and kept for the process: after cudaDeviceReset
+// of a device this entry point must not be called on it again.
 #include <mutex>
 
 #include "common.cuh"

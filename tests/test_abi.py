@@ -123,3 +123,53 @@ def test_load_rejects_bad_files_before_device_work(tmp_path):
     assert lib.tcrnet_load(None, None, ctypes.byref(h)) == tn.EINVAL
     assert h.value is None
     assert lib.tcrnet_save(None, str(tmp_path / "x.tcr").encode()) == tn.EINVAL
+
+
+class _FakeCudaTensor:
+    """Stands in for a CUDA tensor so that the wrapper's argument checks can be
+    exercised without a device: nothing may reach the library."""
+
+    def __init__(self, dtype, numel):
+        self.dtype = dtype
+        self._numel = numel
+        self.is_cuda = True
+
+    def numel(self):
+        return self._numel
+
+    def is_contiguous(self):
+        return True
+
+    def data_ptr(self):
+        raise AssertionError("the library must not be called")
+
+
+def test_noalloc_short_degree_rejected_before_any_launch():
+    import torch
+
+    chars = _FakeCudaTensor(torch.uint8, 50)
+    offs = _FakeCudaTensor(torch.int64, 11)  # n = 10
+    with pytest.raises(ValueError, match="10 needed"):
+        tn.tcrnet_degree_noalloc(chars, offs, _FakeCudaTensor(torch.int32, 9), 1)
+    with pytest.raises(ValueError, match="dtypes"):
+        tn.tcrnet_degree_noalloc(chars, offs, _FakeCudaTensor(torch.int64, 10), 1)
+
+
+def test_new_option_knobs_validated():
+    lib = tn.load_library()
+    chars = np.frombuffer(b"CASSF", dtype=np.uint8)
+    offsets = np.array([0, 5], dtype=np.int64)
+    h = ctypes.c_void_p()
+    for kw in ({"link_attempts": -1}, {"deletion_max_n": -3}):
+        opt = tn.make_options(**kw)
+        assert lib.tcrnet_build_flat(chars.ctypes.data, offsets.ctypes.data, 1, tn.HOST, 1, ctypes.byref(opt),
+                                     ctypes.byref(h)) == tn.EINVAL
+    # an explicit deletion build above its (lowered) limit is refused before device work
+    opt = tn.make_options("deletion", deletion_max_n=1)
+    two = np.array([0, 2, 5], dtype=np.int64)
+    assert lib.tcrnet_build_flat(chars.ctypes.data, two.ctypes.data, 2, tn.HOST, 1, ctypes.byref(opt),
+                                 ctypes.byref(h)) == tn.ENOTSUP
+    assert h.value is None
+    nc, lc = ctypes.c_int64(5), ctypes.c_int64(5)
+    assert lib.tcrnet_components_ex(None, None, None, tn.HOST, None, ctypes.byref(nc), ctypes.byref(lc)) == tn.EINVAL
+    assert nc.value == 0 and lc.value == 0

@@ -1,5 +1,12 @@
 """GPU analytics on the device CSR against the CPU oracle (bit-exact labels,
-component counts and LCC sizes; neighbour-degree means to 1e-12)."""
+component counts and LCC sizes; neighbour-degree means to 1e-12).
+
+The reference analyses run on the oracle's own network (oracle.network), not
+on the CSR the library built, so the comparison reaches from the strings to
+the analysis (Methods "Computing LCC" and "Overview of network theory
+concepts")."""
+
+import functools
 
 import numpy as np
 import pytest
@@ -9,15 +16,24 @@ from oracle import analytics
 import paper_2112_06613_b300 as tn
 from synthgen import from_strings, generate_config1
 
+from csr_util import assert_csr_equal
+
 pytestmark = pytest.mark.gpu
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_case(n, seed, threshold):
+    rep = generate_config1(n, seed=seed)
+    off, cols, deg = oracle.network(rep.chars, rep.offsets, max_dist=threshold)
+    return rep, off, cols
 
 
 @pytest.mark.parametrize("method,threshold", [("deletion", 1), ("tile", 1), ("tile", 2), ("deletion", 2)])
 def test_components_and_removal(method, threshold):
-    rep = generate_config1(20_000, seed=81)
+    rep, off, cols = oracle_case(20_000, 81, threshold)
     with tn.tcrnet_build_flat(rep.chars, rep.offsets, threshold, method=method) as g:
-        off, cols, _ = g.copy_csr()
-        off = np.asarray(off, dtype=np.int64)
+        goff, gcols, _ = g.copy_csr()
+        assert_csr_equal(goff, gcols, off, cols, f"{method} T={threshold} network")
         labels, nc, lcc = g.components()
         ref = analytics.components(off, cols)
         assert np.array_equal(labels, ref)
@@ -44,12 +60,46 @@ def test_components_edge_cases():
 
 @pytest.mark.parametrize("threshold", [1, 2])
 def test_neighbor_degree(threshold):
-    rep = generate_config1(20_000, seed=82)
+    rep, off, cols = oracle_case(20_000, 82, threshold)
     with tn.tcrnet_build_flat(rep.chars, rep.offsets, threshold) as g:
-        off, cols, _ = g.copy_csr()
         knn = g.neighbor_degree()
-    ref = analytics.neighbor_degree(np.asarray(off, dtype=np.int64), cols)
+    ref = analytics.neighbor_degree(off, cols)
     assert np.allclose(knn, ref, rtol=0, atol=1e-12)
+
+
+def _k_clique_tile(n):
+    """n identical strings built by the tile method: the complete graph K_n on
+    the n-node CSR, where many edges race to link the same roots."""
+    return tn.tcrnet_build(["CASSLGQETQYF"] * n, 1, method="tile")
+
+
+def test_union_find_gives_up_with_etimeout_and_stays_usable():
+    """The bounded link loop of the components kernel, with its bound lowered
+    to one attempt per edge (options.link_attempts), runs out on a contended
+    complete graph: the kernel records it and returns, the call reports
+    TCRNET_ETIMEOUT, nothing waits without a bound, and the same handle then
+    answers a normal call exactly."""
+    n = 2000
+    with _k_clique_tile(n) as g:
+        assert g.stats()["method"] == tn.METHOD_TILE
+        seen = None
+        for _ in range(20):
+            try:
+                labels, nc, lcc = g.components(link_attempts=1)
+            except tn.TcrnetError as e:
+                seen = e.status
+                break
+            # an attempt that met no contention is still exact
+            assert (nc, lcc) == (1, n) and (labels == 0).all()
+        assert seen == tn.ETIMEOUT
+        labels, nc, lcc = g.components()
+        assert (nc, lcc) == (1, n) and (labels == 0).all()
+    # other handles and calls are unaffected
+    rep, off, cols = oracle_case(3_000, 84, 1)
+    with tn.tcrnet_build_flat(rep.chars, rep.offsets, 1) as g:
+        labels, nc, lcc = g.components()
+    ref = analytics.components(off, cols)
+    assert np.array_equal(labels, ref) and (nc, lcc) == analytics.largest_component(ref)
 
 
 @pytest.fixture(scope="module")
