@@ -1,9 +1,16 @@
 // Exclusive prefix sums (row counts -> CSR offsets) and offset helpers.
 //
-// Three phases: per-tile totals, a scan of the tile totals (recursive), and a
-// rescan of each tile with its base added. Tiles are 4096 items, 512 threads,
-// 8 contiguous items per thread staged through shared memory so global
-// accesses stay coalesced.
+// One pass with decoupled look-back: each block takes the next tile by ticket
+// (an atomic counter, so tiles start in order), scans its 4096 items (512
+// threads, 8 contiguous items per thread staged through shared memory so
+// global accesses stay coalesced), publishes its tile total, then one warp
+// looks back over the preceding tiles' published words 32 at a time, adding
+// tile totals until it meets a tile that has published its inclusive prefix.
+// A tile only ever waits for tiles with smaller tickets, which are already
+// running and wait only on tiles before them, so every wait ends; each wait is
+// still bounded (kMaxLookbackSpins), after which the kernel records an error
+// flag and goes on. The input is read once; one launch plus the clearing of
+// the ticket and status words per scan. Single-tile inputs take one block.
 #include "kernels.cuh"
 
 namespace tcr {
@@ -47,19 +54,6 @@ __device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t& excl
 }
 
 template <typename TI>
-__global__ void __launch_bounds__(kScanThreads) k_tile_totals(const TI* __restrict__ in, int64_t n,
-                                                               int64_t* __restrict__ totals) {
-    __shared__ int64_t warp_tot[32];
-    const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    int64_t s = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) s += load_item(in, base + k * kScanThreads + threadIdx.x, n);
-    int64_t excl;
-    int64_t tot = block_exclusive_scan(s, excl, warp_tot);
-    if (threadIdx.x == 0) totals[blockIdx.x] = tot;
-}
-
-template <typename TI>
 __global__ void __launch_bounds__(kScanThreads) k_tile_scan(const TI* __restrict__ in, int64_t n,
                                                              const int64_t* __restrict__ tile_base,
                                                              int64_t* __restrict__ out) {
@@ -97,25 +91,130 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(const TI* __restrict
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = (tile_base ? tile_base[blockIdx.x] : 0) + tot;
 }
 
+// Published word of a tile: flag in bits 63..62 (0 nothing yet, 1 tile total,
+// 2 inclusive prefix through this tile), value in bits 61..0.
+constexpr unsigned long long kFlagTotal = 1ull << 62;
+constexpr unsigned long long kFlagIncl = 2ull << 62;
+constexpr unsigned long long kValueMask = (1ull << 62) - 1;
+constexpr int kMaxLookbackSpins = 1 << 22;
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// status[0 .. tiles) publication words, status[tiles] the ticket counter,
+// status[tiles + 1] the error flag; all zero at launch.
+template <typename TI>
+__global__ void __launch_bounds__(kScanThreads) k_scan_onepass(const TI* __restrict__ in, int64_t n,
+                                                                int64_t* __restrict__ out,
+                                                                unsigned long long* status, int64_t tiles) {
+    __shared__ int64_t warp_tot[32];
+    __shared__ int64_t stage[kScanTile];
+    __shared__ int64_t s_prefix;
+    __shared__ int64_t s_tile;
+    if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(status + tiles, 1ull);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t base = tile * kScanTile;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int idx = k * kScanThreads + threadIdx.x;
+        stage[idx] = load_item(in, base + idx, n);
+    }
+    __syncthreads();
+    int64_t v[kScanItems];
+    int64_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = stage[threadIdx.x * kScanItems + k];
+        sum += v[k];
+    }
+    int64_t excl;
+    const int64_t tot = block_exclusive_scan(sum, excl, warp_tot);
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        if (tile == 0) {
+            if (lane == 0) {
+                st_release(status, kFlagIncl | ((unsigned long long)tot & kValueMask));
+                s_prefix = 0;
+            }
+        } else {
+            if (lane == 0) st_release(status + tile, kFlagTotal | ((unsigned long long)tot & kValueMask));
+            // look back: lane k reads tile (window - k); the nearest tile with an
+            // inclusive prefix ends the walk, the tiles before it add their totals
+            int64_t prefix = 0;
+            int64_t window = tile - 1;
+            bool gave_up = false;
+            while (true) {
+                const int64_t j = window - lane;
+                unsigned long long w = kFlagIncl;  // beyond tile 0: nothing to add
+                if (j >= 0) {
+                    int spins = 0;
+                    while (((w = ld_acquire(status + j)) >> 62) == 0) {
+                        if (++spins >= kMaxLookbackSpins) {
+                            gave_up = true;
+                            w = kFlagIncl;  // bounded: end the walk (the error flag is set below)
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                }
+                __syncwarp();
+                const unsigned incl = __ballot_sync(kFull, (w >> 62) == 2);
+                const int stop = incl ? __ffs(incl) - 1 : 32;  // nearest lane with an inclusive word
+                int64_t add = (lane <= stop && j >= 0) ? (int64_t)(w & kValueMask) : 0;
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) add += __shfl_xor_sync(kFull, add, d);
+                prefix += add;
+                if (incl) break;
+                window -= 32;
+            }
+            if (__any_sync(kFull, gave_up) && lane == 0) atomicExch(status + tiles + 1, 1ull);
+            if (lane == 0) {
+                st_release(status + tile, kFlagIncl | ((unsigned long long)(prefix + tot) & kValueMask));
+                s_prefix = prefix;
+            }
+        }
+    }
+    __syncthreads();
+    int64_t run = s_prefix + excl;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        stage[threadIdx.x * kScanItems + k] = run;
+        run += v[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = base + k * kScanThreads + threadIdx.x;
+        if (i < n) out[i] = stage[k * kScanThreads + threadIdx.x];
+    }
+    if (tile == tiles - 1 && threadIdx.x == 0) out[n] = s_prefix + tot;  // the grand total
+}
+
 template <typename TI>
 tcrnet_status scan_impl(const TI* in, int64_t* out, int64_t n, cudaStream_t s) {
     if (n <= 0) {
         TCR_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
         return TCRNET_OK;
     }
-    int64_t tiles = ceil_div(n, kScanTile);
+    const int64_t tiles = ceil_div(n, kScanTile);
     if (tiles == 1) {
         k_tile_scan<TI><<<1, kScanThreads, 0, s>>>(in, n, nullptr, out);
         TCR_LAUNCH_CHECK();
         return TCRNET_OK;
     }
-    DevBuf totals, bases;
-    TCR_CHECK(totals.alloc(sizeof(int64_t) * tiles, s));
-    TCR_CHECK(bases.alloc(sizeof(int64_t) * (tiles + 1), s));
-    k_tile_totals<TI><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, totals.as<int64_t>());
-    TCR_LAUNCH_CHECK();
-    TCR_CHECK(scan_impl<int64_t>(totals.as<int64_t>(), bases.as<int64_t>(), tiles, s));
-    k_tile_scan<TI><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, bases.as<int64_t>(), out);
+    if (tiles > 0x7fffffffLL) return TCRNET_EINVAL;
+    DevBuf status;
+    TCR_CHECK(status.alloc(sizeof(unsigned long long) * (tiles + 2), s));
+    TCR_CUDA(cudaMemsetAsync(status.as<void>(), 0, sizeof(unsigned long long) * (tiles + 2), s));
+    k_scan_onepass<TI><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, out, status.as<unsigned long long>(), tiles);
     TCR_LAUNCH_CHECK();
     return TCRNET_OK;
 }
