@@ -3,25 +3,36 @@
 
 One step = one complete network build of the N = 800,000-string synthetic
 repertoire (seed = rank) at l_max = 1 through the library's default method
-(validate + encode + bucket, distinct-string collapse, deletion-neighbourhood
-join, offsets, fill, per-row sort, int32 CSR export), with the inputs already
-in device memory. `value` is all-pairs comparisons resolved per second,
-N (N - 1) / 2 per build, summed over ranks (weak scaling: every rank builds its
-own repertoire; there is no collective on the data path).
+(validate + encode, distinct-string collapse, deletion-neighbourhood join,
+offsets, fill, per-row sort, int32 CSR export), with the inputs already in
+device memory. `value` is candidate pairs resolved per second: the unordered
+pairs whose lengths differ by at most l_max (same-length and +-1-length
+buckets; every other pair is farther apart than l_max, since the distance is
+at least the length difference), per build, summed over ranks (weak scaling:
+every rank builds its own repertoire; there is no collective on the data
+path). The deletion method never enumerates these pairs; the count is the work
+an all-pairs method must resolve, so methods and the CPU baselines compare on
+one unit.
 
 The same JSON line also carries:
-  edges_per_s    undirected edges produced per second;
-  tile           the all-pairs tile kernel (count pass) on the same workload:
-                 candidate pair tests per second and its integer-ALU roofline;
-  query          p50/p99 latency of query batches against the resident
-                 repertoire (host strings in, host neighbour lists out);
-  e2e            the same metric through the public API from pinned host
-                 buffers, including the upload and the read-back of the CSR;
-  roofline       the dominant phase of the step against measured HBM bandwidth;
-  cpu_baseline   the CPU oracle (plain Wagner-Fischer) on a bounded row sample.
+  all_pairs_per_s  N (N - 1) / 2 per build over the step time;
+  edges_per_s      undirected edges produced per second;
+  roofline         the dominant phase of the step against measured HBM bandwidth;
+  roofline_step    the whole build's algorithmic bytes over the step time;
+  peaks            the integer-issue microbenchmark (per-SM rates by instruction kind);
+  tile             the all-pairs tile kernel (count pass) on the same workload:
+                   candidate pair tests per second and its integer-issue roofline;
+  query            p50/p99 latency of query batches against the resident
+                   repertoire (host strings in, host neighbour lists out);
+  e2e              the same metric through the public API from pinned host
+                   buffers, including the upload and the read-back of the CSR;
+  cpu_baseline     the CPU oracle (plain Wagner-Fischer) on a bounded row sample,
+                   and the paper's own early-abort algorithm (all cores, one core).
 
 `--impl reference` times the CPU oracle alone (there is no reference library
 to install: the paper's code is not available) and prints the same metric.
+`--legs cpu_full` (not run by default) times full oracle builds at 1e4 and 1e5
+strings and 10,000-row samples at 8e5 for the baseline tables.
 """
 
 from __future__ import annotations
@@ -47,11 +58,18 @@ UNIT = "pairs/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6400.0
 SMS = 148
-# Integer issue ceiling per SM and clock: 4 schedulers x 1 warp-instruction x 32 lanes.
-# (Logic/shift ops alone issue at 64 lanes/clk on the ALU pipe; multiply-adds use the
-# FMA pipe; a mix of both is bounded by issue.) Measured with an in-bounds probe of
-# independent lop3 / shf / mad chains on this B300.
+# Nominal integer issue ceiling per SM and clock: 4 schedulers x 1 warp-instruction x
+# 32 lanes. The `peaks` leg measures the rates on the device (tcrnet_probe_int_issue:
+# independent chains of logic, shift, add, multiply-add and popc instructions) and
+# the tile roofline uses the measured ceiling when that leg runs.
 INT_LANES_PER_SM = 128
+# Minimal integer operations of the pair test on one 128-bit word pair (24 letters
+# of 5-bit codes): same length 2 XOR + 2 field folds (3 three-input logic ops each)
+# + 2 POPC + add + compare = 12; lengths L, L+1 about twice that plus the
+# count-leading/trailing-zero steps = 26. Longer strings take one more word pair
+# per 24 letters.
+OPS_SAME_PER_WORD = 12
+OPS_INDEL_PER_WORD = 26
 
 
 # DRAM bytes (read + write) per build of the phase's kernels at N = 800,000,
@@ -63,7 +81,8 @@ PHASE_TRAFFIC_N800000 = {
     "expand": 84.22e6 + 198.65e6,
 }
 
-LEGS = ("tile", "query", "e2e", "insert", "analytics", "lmax2", "batched", "serving", "cpu")
+LEGS = ("peaks", "tile", "query", "e2e", "insert", "analytics", "lmax2", "batched", "serving", "cpu")
+EXTRA_LEGS = ("cpu_full",)  # run only when named in --legs
 
 
 def parse_args():
@@ -87,7 +106,7 @@ def parse_args():
     ap.add_argument("--batched-reps", type=int, default=256, help="0 skips the batched leg")
     ap.add_argument("--no-extras", action="store_true", help="skip every leg after the timed step")
     ap.add_argument("--legs", default=",".join(LEGS),
-                    help="comma list of the legs run after the timed step (default: all)")
+                    help="comma list of the legs run after the timed step (default: all but cpu_full)")
     return ap.parse_args()
 
 
@@ -179,25 +198,147 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle legs
+# candidate pairs and the CPU legs
 
-def oracle_rate(rep, seconds, seed=0, rows_per_call=None):
-    """Oracle (plain Wagner-Fischer, all host cores) on sampled rows of the
-    network; returns (pairs/s, cores, rows, elapsed)."""
+def candidate_pairs(lengths, threshold=1):
+    """Unordered pairs whose lengths differ by at most `threshold`: the pairs an
+    all-pairs method must resolve (any other pair has a larger distance)."""
+    cnt = np.bincount(np.asarray(lengths, dtype=np.int64), minlength=64).astype(np.float64)
+    total = float((cnt * (cnt - 1) / 2).sum())
+    for d in range(1, threshold + 1):
+        total += float((cnt[:-d] * cnt[d:]).sum())
+    return total
+
+
+def row_candidates(lengths, rows, threshold=1):
+    """Candidate partners (other strings within `threshold` of its length) of each row."""
+    lengths = np.asarray(lengths, dtype=np.int64)
+    cnt = np.bincount(lengths, minlength=64)
+    cum = np.concatenate([[0], np.cumsum(cnt)])
+    L = lengths[rows]
+    lo = np.clip(L - threshold, 0, 63)
+    hi = np.clip(L + threshold + 1, 0, 64)
+    return cum[hi] - cum[lo] - 1
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def sampled_rate(rep, seconds, fn, nthreads, seed=0, rows_per_call=None, min_calls=1):
+    """Rows of the N-string network by `fn` (the oracle or the baseline) on seeded
+    row samples for about `seconds`. Returns a dict with the rate in candidate
+    pairs per second of a full build (elapsed time extrapolated from the rows
+    done to all N rows; the build resolves candidate_pairs(lengths) pairs) and in
+    all pairs per second."""
     import oracle
 
-    cores = oracle.max_threads()
+    cores = nthreads if nthreads > 0 else oracle.max_threads()
     rng = np.random.default_rng(seed)
     per = rows_per_call or max(1, cores)
-    done, pairs, t0 = 0, 0, time.perf_counter()
+    lens = rep.lengths()
+    cand_build = candidate_pairs(lens)
+    done, calls, t0 = 0, 0, time.perf_counter()
     while True:
         rows = rng.choice(rep.n, size=per, replace=False).astype(np.int64)
-        oracle.rows(rep.chars, rep.offsets, rows, max_dist=1, nthreads=cores)
+        fn(rep.chars, rep.offsets, rows, max_dist=1, nthreads=cores)
         done += per
-        pairs += per * (rep.n - 1)
+        calls += 1
         el = time.perf_counter() - t0
-        if el >= seconds:
-            return pairs / el, cores, done, el
+        if el >= seconds and calls >= min_calls:
+            break
+    build_s = el * rep.n / done  # extrapolated full build
+    return {"value": cand_build / build_s, "unit": UNIT, "cores": cores, "rows": done, "elapsed_s": el,
+            "extrapolated_build_s": build_s, "all_pairs_per_s": rep.n * (rep.n - 1) / 2 / build_s}
+
+
+def oracle_rate(rep, seconds, seed=0, rows_per_call=None):
+    """Oracle (plain Wagner-Fischer, all host cores) on sampled rows of the network."""
+    import oracle
+
+    return sampled_rate(rep, seconds, oracle.rows, 0, seed, rows_per_call)
+
+
+def cpu_leg(rep, seconds):
+    """cpu_baseline: the oracle as it stands on all host cores, plus the paper's
+    own algorithm (the early-abort table with the length skip) on all cores and
+    on one core, each on a bounded row sample of the same N-string network."""
+    import oracle
+
+    o = oracle_rate(rep, seconds)
+    b_all = sampled_rate(rep, seconds / 2, oracle.baseline_rows, 0, seed=1)
+    b_one = sampled_rate(rep, seconds / 2, oracle.baseline_rows, 1, seed=2)
+    model = cpu_model()
+    n = rep.n
+    return {
+        "value": o["value"], "unit": UNIT, "cores": o["cores"], "kind": "oracle", "cpu_model": model,
+        "sample": f"{o['rows']} seeded rows of the N={n} network, each the full Wagner-Fischer scan against "
+                  f"all {n} strings ({o['elapsed_s']:.1f} s); value = candidate pairs of one build over the "
+                  f"build time extrapolated from the rows done ({o['extrapolated_build_s']:.0f} s)",
+        "all_pairs_per_s": o["all_pairs_per_s"],
+        "listing1": {
+            "kind": "listing1", "value": b_all["value"], "unit": UNIT, "cores": b_all["cores"],
+            "single_core": b_one["value"], "cpu_model": model,
+            "extrapolated_build_s": b_all["extrapolated_build_s"],
+            "single_core_extrapolated_build_s": b_one["extrapolated_build_s"],
+            "sample": f"{b_all['rows']} rows on {b_all['cores']} cores ({b_all['elapsed_s']:.1f} s) and "
+                      f"{b_one['rows']} rows on one core ({b_one['elapsed_s']:.1f} s) of the N={n} network",
+            "algorithm": "the paper's per-pair test (Methods 'GPU-based network generation', Listing 1) "
+                         "restated correctly: two-row table with the row-minimum early abort, pairs with "
+                         "|length difference| > l_max skipped",
+        },
+    }
+
+
+def cpu_full_leg():
+    """Baseline tables: full oracle builds at 1e4 and 1e5 strings (all cores),
+    10,000 seeded rows at 8e5 (extrapolated x80 to the full build), the same for
+    the paper's early-abort algorithm, and that algorithm on one core (1,000 rows
+    at 8e5, extrapolated x800)."""
+    import oracle
+    from synthgen import generate_config1, generate_config2
+
+    out = {"cpu_model": cpu_model(), "cores": oracle.max_threads(), "runs": []}
+    for n in (10_000, 100_000):
+        rep = generate_config1(n, seed=0)
+        cand = candidate_pairs(rep.lengths())
+        for label, fn in (("oracle", oracle.network), ("listing1", oracle.baseline_network)):
+            t = time.perf_counter()
+            off, _, _ = fn(rep.chars, rep.offsets, max_dist=1)
+            el = time.perf_counter() - t
+            out["runs"].append({"run": f"{label}, full network", "n": n, "threads": out["cores"], "s": el,
+                                "candidate_pairs_per_s": cand / el, "all_pairs_per_s": n * (n - 1) / 2 / el,
+                                "nnz": int(off[-1])})
+    rep = generate_config2(800_000, seed=0)
+    cand = candidate_pairs(rep.lengths())
+    n = rep.n
+    rng = np.random.default_rng(3)
+    for label, fn, rows, threads in (("oracle", oracle.rows, 10_000, 0),
+                                     ("listing1", oracle.baseline_rows, 10_000, 0),
+                                     ("listing1", oracle.baseline_rows, 1_000, 1)):
+        ids = rng.choice(n, size=rows, replace=False).astype(np.int64)
+        t = time.perf_counter()
+        fn(rep.chars, rep.offsets, ids, max_dist=1, nthreads=threads)
+        el = time.perf_counter() - t
+        build_s = el * n / rows
+        out["runs"].append({"run": f"{label}, {rows} seeded rows, extrapolated x{n // rows}", "n": n,
+                            "threads": threads or out["cores"], "s": el, "extrapolated_build_s": build_s,
+                            "candidate_pairs_per_s": cand / build_s, "all_pairs_per_s": n * (n - 1) / 2 / build_s})
+    return out
 
 
 def run_reference(args):
@@ -210,6 +351,7 @@ def run_reference(args):
     cores = oracle.max_threads()
     rng = np.random.default_rng(1)
     per = max(1, cores)  # one row per core per step (about 0.3 s)
+    cand_build = candidate_pairs(rep.lengths())
 
     def step():
         rows = rng.choice(rep.n, size=per, replace=False).astype(np.int64)
@@ -221,16 +363,20 @@ def run_reference(args):
     for _ in range(args.steps):
         step()
     el = time.perf_counter() - t0
-    value = args.steps * per * (rep.n - 1) / el
+    build_s = el * rep.n / (args.steps * per)  # extrapolated full build
+    value = cand_build / build_s
     sample = (f"{per} sampled rows per step (each row: the query string against all {rep.n} strings), "
-              f"{args.steps} steps")
+              f"{args.steps} steps; value = candidate pairs of one build over the build time extrapolated "
+              f"from the rows done ({build_s:.0f} s)")
     line = {
         "impl": "reference",
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
         "config": dict(workload_config(args, "cpu-oracle"), inputs_resident=False, l2="not applicable (host)"),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                         "cpu_model": cpu_model()},
+        "all_pairs_per_s": rep.n * (rep.n - 1) / 2 / build_s,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -259,33 +405,71 @@ def aggregate_ranks(ms_local, pairs_per_build, edges_per_build, world, dist_mod=
 # ---------------------------------------------------------------------------
 # ours
 
-def tile_ops_per_pair(lengths):
-    """Algorithmic 32-bit integer operations of the tile test, summed over the
-    candidate pairs of every bucket pair (tile kernel)."""
-    cnt = np.bincount(lengths, minlength=50).astype(np.float64)
+def tile_alg_ops(lengths, threshold=1):
+    """Algorithmic integer operations of the all-pairs tile test over every
+    candidate pair: OPS_SAME_PER_WORD per same-length pair and
+    OPS_INDEL_PER_WORD per (L, L+1) pair, per 128-bit word pair of the longer
+    string (24 letters each). Returns (ops, candidate pairs)."""
+    cnt = np.bincount(np.asarray(lengths, dtype=np.int64), minlength=64).astype(np.float64)
     ops = 0.0
     pairs = 0.0
     for L in range(1, 49):
         nl = cnt[L]
         if nl == 0:
             continue
-        W = math.ceil(L / 6)
+        words = math.ceil(L / 24)
         same = nl * (nl - 1) / 2
-        ops += same * (5 * W + 2)   # per word: xor, or, sub, and-or, shift-accumulate; then m&(m-1)==0
+        ops += same * OPS_SAME_PER_WORD * words
         pairs += same
-        if L + 1 < 50 and cnt[L + 1] > 0:
-            W1 = math.ceil((L + 1) / 6)
+        if threshold >= 1 and cnt[L + 1] > 0:
             ind = nl * cnt[L + 1]
-            ops += ind * (10 * W1 + 3)  # two masks; then -m1, and-or, compare
+            ops += ind * OPS_INDEL_PER_WORD * math.ceil((L + 1) / 24)
             pairs += ind
     return ops, pairs
+
+
+def peaks_leg(tn, torch, dev, stream, sms):
+    """Integer-issue rates by instruction kind: each kind's microbenchmark kernel
+    (2,048 threads per SM, independent chains) timed with CUDA events on the
+    bench stream, median of 5 launches; rates per SM and clock at the SM clock
+    sampled during the leg."""
+    n_threads = sms * 2048
+    out = torch.empty(n_threads, dtype=torch.int32, device=dev)
+    iters = 4096
+    sampler = ClockSampler(dev.index or 0)
+    sampler.start()
+    time.sleep(0.3)
+    res = {}
+    for kind in tn.PROBE_KINDS:
+        tn.tcrnet_probe_int_issue(kind, 64, out, stream)  # warm-up
+        ts = []
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ops = tn.tcrnet_probe_int_issue(kind, iters, out, stream)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = statistics.median(ts)
+        res[kind] = {"ops_per_launch": float(ops) * n_threads, "ms": ms,
+                     "tops": float(ops) * n_threads / (ms / 1e3) / 1e12}
+    clocks = sampler.stop()
+    clk = (clocks or {}).get("sm_mhz") or 2032.0
+    for kind, r in res.items():
+        r["lanes_per_clk_per_sm"] = r["tops"] * 1e12 / (sms * clk * 1e6)
+    issue = max(r["tops"] for r in res.values())
+    return {"kinds": res, "sms": sms, "sm_mhz": clk, "clocks": clocks,
+            "issue_ceiling_tops": issue, "issue_ceiling_lanes_per_clk_per_sm": issue * 1e12 / (sms * clk * 1e6),
+            "alu_pipe_tops": res["lop3"]["tops"],
+            "method": "tcrnet_probe_int_issue: 8 independent rotating triples per thread, 4096 rounds, "
+                      "CUDA events on the bench stream, median of 5"}
 
 
 def serve_leg(args, tn, torch, stream):
     """Serving: resident repertoire of args.serve_n strings, open-loop Poisson
     arrivals (200/s) of queries (90%, log-uniform 1..50,000 strings) and inserts
     (10%, log-uniform 1,000..100,000 strings) for args.serve_seconds."""
-    from paper_2112_06613_b300.serving import ServingEngine, latency_summary
+    from paper_2112_06613_b300.serving import ServingEngine, latency_by_answer_size, latency_summary
     from synthgen import generate, generate_config2
 
     rng = np.random.default_rng(11)
@@ -339,6 +523,14 @@ def serve_leg(args, tn, torch, stream):
         "arrival_rate_per_s": rate, "duration_s": args.serve_seconds, "wall_s": wall,
         "requests": len(reqs), "errors": errors,
         "query": latency_summary(reqs, "query"), "insert": latency_summary(reqs, "insert"),
+        "query_by_answer_size": latency_by_answer_size(reqs),
+        "query_time_split": {
+            "mean_queue_ms": float(np.mean([1e3 * (r.t_start - r.t_arrival) for r in qs])) if qs else None,
+            "mean_call_ms": float(np.mean([1e3 * r.s_call for r in qs])) if qs else None,
+            "mean_copy_ms": float(np.mean([1e3 * r.s_copy for r in qs])) if qs else None,
+            "mean_split_ms": float(np.mean([1e3 * r.s_split for r in qs])) if qs else None,
+            "note": "per query request: waiting for a slot, the device call (with its stream sync), the copy "
+                    "of the shared batch answer to pinned host memory, the split into per-request arrays"},
         "throughput_requests_per_s": len(reqs) / wall,
         "query_strings_per_s": sum(r.n_strings for r in qs) / wall,
         "device_calls": len({r.batch_id for r in reqs}),
@@ -483,8 +675,10 @@ def run_ours(args):
     st0 = stats[-1]
     n = args.n
     pairs_per_build = n * (n - 1) / 2
+    cand_per_build = candidate_pairs(rep.lengths())
     edges = st0["nnz"] / 2
-    ms, value, edges_per_s = aggregate_ranks(statistics.mean(step_ms), pairs_per_build, edges, world, dist, dev)
+    ms, value, edges_per_s = aggregate_ranks(statistics.mean(step_ms), cand_per_build, edges, world, dist, dev)
+    all_pairs_per_s = world * pairs_per_build / (ms / 1e3)
     launches = int(sum(s["kernel_launches"] for s in stats))
     # per-phase times: the same build with CUDA-event marks between its phases,
     # run after the timed region (the marks cost ~45 us per build, so the timed
@@ -509,19 +703,29 @@ def run_ours(args):
     dom = max(phase_ms, key=phase_ms.get)
     nnz = st0["nnz"]
     U, R, E, SD = st0["n_unique"], st0["n_records"], st0["unique_edges"], st0["closed_total"]
-    alg_bytes = 1 if is_tile else {
+    # algorithmic bytes per phase (U distinct strings, R records, SD total
+    # closed-list length): what each phase must read and write at least once
+    phase_bytes = {} if is_tile else {
         "expand": 4 * nnz + 4 * SD + 8 * (n + 1) + 4 * n,  # write cols; read lists, offsets, ids
         "list_sort": 8 * SD + 8 * (U + 1),                # read + write lists, read offsets
         "join_fill": 8 * R + 8 * SD,                      # read records; read members, write lists
         "join_weigh": 8 * R,                              # read records
         "records": 32 * U + 8 * R,                        # read strings, scatter records
-        "dedup": 32 * n + 32 * U + 8 * n,
-        # read chars and offsets; write codes and lengths; bucketed copy (read, write codes + order)
-        "pack": int(rep.chars.nbytes) + 8 * (n + 1) + 33 * n + 33 * n + 36 * n,
-    }[dom]
+        "dedup": 32 * n + 32 * U + 8 * n,                 # read codes, write distinct strings, ids
+        "pack": int(rep.chars.nbytes) + 8 * (n + 1) + 33 * n,  # read chars + offsets; write codes + lengths
+    }
+    alg_bytes = phase_bytes.get(dom, 1)
     achieved = alg_bytes / (phase_ms[dom] / 1e3) / 1e9
+    roofline_step = None
+    if not is_tile:
+        step_bytes = float(sum(phase_bytes.values()))
+        sa = step_bytes / (ms / 1e3) / 1e9
+        roofline_step = {"bound": "hbm", "achieved": sa, "peak": hbm_peak, "unit": "GB/s", "frac": sa / hbm_peak,
+                         "alg_bytes_per_step": step_bytes, "ms_per_step": ms, "peak_kind": f"{peak_kind} hbm_gbs",
+                         "formula": "sum over phases: pack chars+8(n+1)+33n; dedup 72n+32U; records 32U+8R; "
+                                    "join 8R; fill 8R+8SD; list sort 8SD+8(U+1); expand 4nnz+4SD+8(n+1)+4n"}
     if is_tile:
-        ops, _ = tile_ops_per_pair(rep.lengths())
+        ops, _ = tile_alg_ops(rep.lengths())
         peak_ops = SMS * INT_LANES_PER_SM * sm_max_nominal * 1e6
         ach = ops / (phase_ms[dom] / 1e3)
         roofline_tile = {"bound": "alu", "kernel_phase": dom, "achieved": ach / 1e12, "peak": peak_ops / 1e12,
@@ -547,17 +751,24 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": workload_config(args, "deletion" if st0["method"] == 2 else "tile"),
+        "candidate_pairs_per_build": cand_per_build, "all_pairs_per_s": all_pairs_per_s,
+        "all_pairs_per_build": pairs_per_build,
         "edges_per_s": edges_per_s, "edges_per_build": edges, "nnz": nnz, "edge_write": edge_write,
-        "wall_s_timed_region": wall, "phases_ms": phase_ms, "roofline": roofline,
+        "wall_s_timed_region": wall, "phases_ms": phase_ms, "roofline": roofline, "roofline_step": roofline_step,
         "gpu_launches": launches, "clocks": clocks,
     }
 
     legs = set(args.legs.split(",")) - {""}
     if rank == 0 and not args.no_extras:
+        peaks = None
+        if "peaks" in legs:
+            # --- integer-issue rates of this device (the tile roofline's denominator)
+            peaks = peaks_leg(tn, torch, dev, stream, torch.cuda.get_device_properties(dev).multi_processor_count)
+            line["peaks"] = peaks
         if "tile" in legs:
-            # --- tile kernel: candidate pair tests per second vs the integer ALU roofline
+            # --- tile kernel: candidate pair tests per second vs the integer-issue roofline
             lens = rep.lengths()
-            ops, pairs = tile_ops_per_pair(lens)
+            ops, pairs = tile_alg_ops(lens)
             tstats = []
             build(method="tile").free()
             for _ in range(args.tile_steps):
@@ -569,17 +780,25 @@ def run_ours(args):
             tot_ms = statistics.mean(s["ms_total"] for s in tstats)
             cand = tstats[0]["candidate_pairs"]
             clk = (clocks or {}).get("sm_mhz") or sm_max_nominal
-            peak_ops = SMS * INT_LANES_PER_SM * sm_max_nominal * 1e6
-            peak_ops_clk = SMS * INT_LANES_PER_SM * clk * 1e6
+            nominal = SMS * INT_LANES_PER_SM * sm_max_nominal * 1e6
             ach_ops = ops / (cnt_ms / 1e3)
+            if peaks:  # the measured issue ceiling of this device
+                peak_ops = peaks["issue_ceiling_tops"] * 1e12
+                basis = (f"measured by the peaks leg: fastest instruction mix, "
+                         f"{peaks['issue_ceiling_lanes_per_clk_per_sm']:.1f} lanes/clk/SM at {peaks['sm_mhz']:.0f} MHz")
+            else:
+                peak_ops = nominal
+                basis = f"nominal: {SMS} SMs x {INT_LANES_PER_SM} int32 issue lanes x {sm_max_nominal:.0f} MHz"
             line["tile"] = {
                 "candidate_pairs": cand, "count_pass_ms": cnt_ms, "build_ms": tot_ms,
                 "candidate_pairs_per_s": cand / (cnt_ms / 1e3),
                 "all_pairs_per_s_build": pairs_per_build / (tot_ms / 1e3),
                 "roofline": {"bound": "alu", "achieved": ach_ops / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-                             "frac": ach_ops / peak_ops, "frac_at_sampled_clock": ach_ops / peak_ops_clk,
-                             "ops_per_launch": ops, "peak_basis": f"{SMS} SMs x {INT_LANES_PER_SM} int32 issue lanes x "
-                                                                   f"{sm_max_nominal:.0f} MHz (issue ceiling)"},
+                             "frac": ach_ops / peak_ops, "frac_of_nominal_issue": ach_ops / nominal,
+                             "ops_per_launch": ops, "peak_basis": basis,
+                             "ops_basis": f"{OPS_SAME_PER_WORD} per same-length and {OPS_INDEL_PER_WORD} per "
+                                          f"(L, L+1) candidate pair per 128-bit word pair (minimal test)",
+                             "sampled_sm_mhz": clk},
             }
         if "query" in legs:
             # --- queries against the resident repertoire (host in, host out)
@@ -663,12 +882,12 @@ def run_ours(args):
             p_ms = 1e3 * (time.perf_counter() - t) / (per * depth)
             if errors:
                 raise errors[0]
-            line["e2e"] = {"value": pairs_per_build / (p_ms / 1e3), "unit": UNIT, "ms_per_step": p_ms,
+            line["e2e"] = {"value": cand_per_build / (p_ms / 1e3), "unit": UNIT, "ms_per_step": p_ms,
                            "h2d_bytes_per_step": int(rep.chars.nbytes + rep.offsets.nbytes),
                            "d2h_bytes_per_step": int(4 * (n + 1) + 4 * nnz + 4 * n),
                            "pipeline": f"{depth} host threads with their own streams and pinned buffers, "
                                        f"{per * depth} steps, each step's upload, build and CSR download included",
-                           "serial_ms_per_step": e_ms, "serial_value": pairs_per_build / (e_ms / 1e3)}
+                           "serial_ms_per_step": e_ms, "serial_value": cand_per_build / (e_ms / 1e3)}
         if "insert" in legs:
             # --- inserts into the resident N = 8e5 network: merged (query + network
             #     of the new strings, grown rows and index) vs rebuilt; copy-on-write
@@ -746,7 +965,7 @@ def run_ours(args):
             from synthgen import generate_config1
 
             lm2 = {}
-            peak = SMS * INT_LANES_PER_SM * sm_max_nominal * 1e6
+            peak = peaks["issue_ceiling_tops"] * 1e12 if peaks else SMS * INT_LANES_PER_SM * sm_max_nominal * 1e6
             for n2 in (32_000, 100_000):
                 r2 = generate_config1(n2, seed=7)
                 c2 = torch.from_numpy(r2.chars).to(dev)
@@ -817,12 +1036,11 @@ def run_ours(args):
             if args.serve_seconds > 0:
                 line["serving"] = serve_leg(args, tn, torch, stream)
         if "cpu" in legs:
-            # --- CPU oracle on a bounded sample (rank 0, one GPU only)
+            # --- CPU oracle and the paper's algorithm on bounded samples (rank 0, one GPU only)
             if world == 1 and args.cpu_seconds > 0:
-                rate, cores, rows, el = oracle_rate(rep, args.cpu_seconds)
-                line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                        "sample": f"{rows} seeded rows of the N={n} network, each the full "
-                                                  f"Wagner-Fischer scan against all {n} strings ({el:.1f} s)"}
+                line["cpu_baseline"] = cpu_leg(rep, args.cpu_seconds)
+        if "cpu_full" in legs and world == 1:
+            line["cpu_full"] = cpu_full_leg()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -50,6 +50,14 @@ class Request:
     version: int = -1  # inserts applied before this request ran
     ticket: int = -1  # arrival order among inserts
     batch_id: int = -1  # device call that served it
+    # where a query's time went (seconds): the device call (tcrnet_query_ex with
+    # its stream sync), the copy of the batch's answer to the host, the split
+    # into per-request arrays; batch_entries = neighbour entries of the whole
+    # device call this request shared
+    s_call: float = 0.0
+    s_copy: float = 0.0
+    s_split: float = 0.0
+    batch_entries: int = 0
     offsets_out: np.ndarray | None = None
     cols_out: np.ndarray | None = None
     error: BaseException | None = None
@@ -62,6 +70,10 @@ class Request:
     @property
     def latency_s(self) -> float:
         return self.t_done - self.t_arrival
+
+    @property
+    def answer_entries(self) -> int:
+        return 0 if self.cols_out is None else int(self.cols_out.shape[0])
 
 
 class ServingEngine:
@@ -273,7 +285,9 @@ class ServingEngine:
             with self._cv:
                 bid = self._batches
                 self._batches += 1
+            t_call = time.perf_counter()
             res = Graph.borrowed(h).query_flat(chars, offsets, method="auto", stream=stream)
+            t_copy = time.perf_counter()
             try:
                 # into this slot's pinned buffers (a copy to pageable memory goes
                 # through the driver's small staging buffers, slowly for long
@@ -293,6 +307,7 @@ class ServingEngine:
                 res.free()
         finally:
             self._drop(h)
+        t_split = time.perf_counter()
         off = off_v.astype(np.int64)
         row = 0
         for r in batch:
@@ -303,6 +318,12 @@ class ServingEngine:
             r.version = version
             r.batch_id = bid
             row += k
+        t_end = time.perf_counter()
+        for r in batch:
+            r.s_call = t_copy - t_call
+            r.s_copy = t_split - t_copy
+            r.s_split = t_end - t_split
+            r.batch_entries = int(nnz)
 
 
 def latency_summary(reqs, kind: str):
@@ -311,3 +332,28 @@ def latency_summary(reqs, kind: str):
         return None
     return {"count": len(lat), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(np.mean(lat))}
+
+
+def latency_by_answer_size(reqs, edges=(0, 1_000, 10_000, 100_000, 1_000_000, 1 << 62)):
+    """Query latency binned by the entries of the device call's answer (the
+    batch a request shared), with the mean split of each bin's latency into
+    queueing, the device call, the host copy of the answer and the split."""
+    qs = [r for r in reqs if r.kind == "query" and r.error is None]
+    out = []
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        b = [r for r in qs if lo <= r.batch_entries < hi]
+        if not b:
+            continue
+        lat = np.array([1e3 * r.latency_s for r in b])
+        out.append({
+            "answer_entries": f"[{lo}, {hi})" if hi < (1 << 62) else f">= {lo}",
+            "count": len(b),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()),
+            "mean_queue_ms": float(np.mean([1e3 * (r.t_start - r.t_arrival) for r in b])),
+            "mean_call_ms": float(np.mean([1e3 * r.s_call for r in b])),
+            "mean_copy_ms": float(np.mean([1e3 * r.s_copy for r in b])),
+            "mean_split_ms": float(np.mean([1e3 * r.s_split for r in b])),
+            "mean_batch_entries": float(np.mean([r.batch_entries for r in b])),
+        })
+    return out
