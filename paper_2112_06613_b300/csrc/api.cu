@@ -84,6 +84,37 @@ thread_local DeviceArena* t_arena = nullptr;
 
 bool arena_active() { return t_arena != nullptr; }
 
+namespace {
+struct PinnedScratch {
+    void* p = nullptr;
+    void* dev = nullptr;
+    bool tried = false;
+    ~PinnedScratch() {
+        if (p) cudaFreeHost(p);  // at process exit the runtime may be gone: the error is ignored
+    }
+};
+thread_local PinnedScratch t_pinned;
+}  // namespace
+
+void* pinned_scratch() {
+    if (!t_pinned.tried) {
+        t_pinned.tried = true;
+        if (cudaHostAlloc(&t_pinned.p, kPinnedScratchBytes, cudaHostAllocPortable | cudaHostAllocMapped) !=
+            cudaSuccess) {
+            t_pinned.p = nullptr;
+            (void)cudaGetLastError();
+        } else if (cudaHostGetDevicePointer(&t_pinned.dev, t_pinned.p, 0) != cudaSuccess) {
+            t_pinned.dev = nullptr;
+            (void)cudaGetLastError();
+        }
+    }
+    return t_pinned.p;
+}
+
+void* pinned_scratch_device() {
+    return pinned_scratch() ? t_pinned.dev : nullptr;
+}
+
 const SideStream* leased_side_stream() {
     DeviceArena* a = t_arena;
     if (!a) return nullptr;
@@ -440,7 +471,10 @@ tcrnet_status build_from_packed(tcrnet_graph* h, Packed& pk, int64_t n, int32_t 
         DeletionResult dr;
         st = deletion_build(pk, T, dr, s, sms, opt.profile != 0, opt.partition_cap, keep_index,
                             opt.partition_target, opt.force_offsets64 != 0);
-        if (st != TCRNET_OK) return st;
+        if (st != TCRNET_OK) {
+            if (dr.bad_index >= 0) t_last_bad = dr.bad_index;  // the encoder's deferred error
+            return st;
+        }
         h->stats.n_unique = dr.n_unique;
         h->stats.n_records = dr.n_records;
         h->stats.unique_edges = dr.unique_edges;
@@ -533,12 +567,55 @@ tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n
     Packed pk;
     int64_t bad = -1;
     if (n > 0) {
+        // A deletion build at l_max <= 1 does not wait for the encoder: the
+        // total length (which sizes its records) is the byte span of the
+        // strings, offsets[n] - offsets[0], exact for valid input, and the
+        // encoder's error word is checked at the build's first readback. The
+        // span is read before the encoder runs (host inputs: on the host).
+        int64_t span = -1;
+        cudaEvent_t span_ready = nullptr;
+        int64_t* pin = static_cast<int64_t*>(pinned_scratch());
+        const bool defer = opt.method == TCRNET_METHOD_DELETION && T <= 1 && !rep_off && pin;
+        if (defer && mem == TCRNET_HOST) {
+            span = offsets[n] - offsets[0];
+        } else if (defer) {
+            TCR_CUDA(cudaMemcpyAsync(pin, in.d_offs, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            TCR_CUDA(cudaMemcpyAsync(pin + 1, in.d_offs + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            span_ready = event_acquire();
+            if (span_ready) TCR_CUDA(cudaEventRecord(span_ready, s));
+        }
         // chars are addressed as d_chars + (offsets[i] - base)
         st = pack_strings(in.d_chars - in.base, in.d_offs, n, pk, &bad, s, opt.method == TCRNET_METHOD_TILE,
-                          opt.method != TCRNET_METHOD_TILE && !rep_off, in.lo, in.hi);
+                          opt.method != TCRNET_METHOD_TILE && !rep_off, in.lo, in.hi, defer);
+        if (defer && mem != TCRNET_HOST) {
+            if (span_ready) {
+                const cudaError_t e = cudaEventSynchronize(span_ready);
+                event_release(span_ready);
+                if (e != cudaSuccess) return fail(TCRNET_EDEVICE);
+            } else if (cudaStreamSynchronize(s) != cudaSuccess) {
+                return fail(TCRNET_EDEVICE);
+            }
+            span = pin[1] - pin[0];
+        }
         if (st != TCRNET_OK) {
             t_last_bad = bad;
             return fail(st);
+        }
+        if (defer) {
+            if (span >= n && span <= (int64_t)kMaxLen * n) {
+                pk.lensum = span;
+            } else {  // not a valid input: the encoder has flagged it; report its error now
+                unsigned long long fl[2] = {0, 0};
+                if (cudaMemcpyAsync(fl, pk.flags.as<void>(), sizeof(fl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                    cudaStreamSynchronize(s) != cudaSuccess)
+                    return fail(TCRNET_EDEVICE);
+                st = pack_flags_status(fl[0], &bad);
+                if (st != TCRNET_OK) {
+                    t_last_bad = bad;
+                    return fail(st);
+                }
+                pk.lensum = (int64_t)fl[1];
+            }
         }
     }
     if (rep_off && n > 0) {

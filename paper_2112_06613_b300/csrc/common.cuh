@@ -149,13 +149,28 @@ int64_t launches_so_far();
 void* arena_carve(size_t bytes, cudaError_t* err);  // nullptr: no lease on this thread
 bool arena_active();
 // While the calling thread holds its device's workspace lease: a second stream
-// of that device and `count` (<= 4) events for forking independent work off the
-// call's stream and joining it back (null: no lease; run everything in order).
+// of that device and events for forking independent work off the call's
+// stream and joining it back (null: no lease; run everything in order).
+// ev[0..3] belong to the deletion build's phases, ev[4..5] to the row sort.
 struct SideStream {
     cudaStream_t stream = nullptr;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 const SideStream* leased_side_stream();
+
+// Page-locked host memory of the calling thread (kPinnedScratchBytes,
+// allocated on first use and kept for the thread's life) for small
+// device-to-host readbacks of counters, sizes and error words. Copies into it
+// are asynchronous, so a group of readbacks costs one stream synchronisation;
+// a copy into pageable memory waits for the device on its own (measured: four
+// pageable readbacks in a row left the GPU idle for ~80 us mid-build).
+// nullptr if page-locked memory cannot be had (callers fall back to pageable).
+constexpr size_t kPinnedScratchBytes = 4096;
+void* pinned_scratch();
+// The same memory as a device address (it is mapped), so a kernel can write a
+// group of readback values there directly: one small kernel instead of one
+// copy per value. nullptr if unavailable.
+void* pinned_scratch_device();
 
 // Events for the optional phase timing, recycled through a per-device pool so
 // that a profiled build does not create and destroy events on its critical path.

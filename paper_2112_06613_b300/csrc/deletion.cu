@@ -249,12 +249,17 @@ __global__ void k_members(const int32_t* __restrict__ uid, int64_t n, const int6
 
 constexpr int kRecBatch = 4;
 
+// The scatter writes nothing when the records counted exceed R_cap, the size
+// the record array was given (only invalid input, whose error the build reports
+// at its first readback, can get there).
 template <bool SCATTER>
 __global__ void k_records(const Canon* __restrict__ ucanon, const uint8_t* __restrict__ ulen,
                           const int64_t* __restrict__ U_ptr, int64_t n, uint32_t P, int32_t* __restrict__ pcnt,
-                          const int64_t* __restrict__ poff, uint64_t* __restrict__ recs, uint32_t u0 = 0) {
+                          const int64_t* __restrict__ poff, uint64_t* __restrict__ recs, uint32_t u0 = 0,
+                          int64_t R_cap = INT64_MAX) {
     const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= n || u >= *U_ptr) return;
+    if (SCATTER && poff[P] > R_cap) return;
     const Canon c = load_canon(ucanon + u);
     const int L = ulen[u];
     if constexpr (!SCATTER) {
@@ -445,7 +450,8 @@ k_join_small(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __rest
              int32_t* __restrict__ wsum, int64_t* __restrict__ pedges, const int64_t* __restrict__ eoff,
              int2* __restrict__ edges, unsigned long long* __restrict__ ecur, int64_t seg_cap,
              int32_t* __restrict__ big_list, int* __restrict__ big_count, int32_t* __restrict__ fb_list,
-             int* __restrict__ fb_count) {
+             int* __restrict__ fb_count, int64_t R_cap = INT64_MAX) {
+    if (poff[P] > R_cap) return;  // records beyond the array (invalid input): nothing is joined
     __shared__ uint64_t sbuf[kWarps][32];
     __shared__ int32_t smul[kWarps][32];
     __shared__ int2 sstage[WRITE ? 1 : kWarps][WRITE ? 1 : kStage];
@@ -1165,6 +1171,45 @@ __global__ void k_expand(const int32_t* __restrict__ uid, int64_t n, const int64
 
 using Timer = EventMarks;
 
+// Readbacks of the build, written by one small kernel straight into mapped
+// page-locked host memory (pinned_scratch_device): the sizes of the closed
+// lists and of the CSR, the per-segment edge counts, the longest list and the
+// encoder's error word in mid-build; the error counters and totals at the end.
+struct MidReadback {
+    int64_t sizes[2];                        // sum of D_u, nnz
+    unsigned long long segs[kEdgeSegs + 1];  // per-segment edge counts, then the single-list count
+    unsigned long long pack_error;           // encoder's first error word (0: none)
+    int dmax;
+};
+
+struct EndReadback {
+    int64_t U, R;
+    int err[4];  // the first four device counters
+};
+
+__global__ void k_mid_readback(const int64_t* __restrict__ sd, const int64_t* __restrict__ nnz,
+                               const unsigned long long* __restrict__ ecur, const int* __restrict__ dmax,
+                               const unsigned long long* __restrict__ pack_flags, MidReadback* dst) {
+    const int t = threadIdx.x;
+    if (t <= kEdgeSegs) dst->segs[t] = ecur[t];
+    if (t == 0) {
+        dst->sizes[0] = *sd;
+        dst->sizes[1] = *nnz;
+        dst->dmax = *dmax;
+        dst->pack_error = pack_flags ? *pack_flags : 0ull;
+    }
+}
+
+__global__ void k_end_readback(const int* __restrict__ err, const int64_t* __restrict__ U,
+                               const int64_t* __restrict__ R, EndReadback* dst) {
+    const int t = threadIdx.x;
+    if (t < 4) dst->err[t] = err[t];
+    if (t == 0) {
+        dst->U = *U;
+        dst->R = R ? *R : 0;
+    }
+}
+
 }  // namespace
 
 tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaStream_t s, int num_sms, bool profile,
@@ -1179,15 +1224,34 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     // the output sizes are known.
     const int64_t R_max = n + pk.lensum;
 
-    // device counters: [0] dedup error, [1] fill error, [2] fallback partitions,
-    // [3] partitions for the sorted join, [4] largest closed list; edge cursor
-    DevBuf errb, ecur_b;
-    TCR_CHECK(errb.alloc(sizeof(int) * 8, s));
-    TCR_CHECK(ecur_b.alloc(sizeof(unsigned long long) * (kEdgeSegs + 1), s));
-    TCR_CUDA(cudaMemsetAsync(errb.as<void>(), 0, sizeof(int) * 8, s));
-    TCR_CUDA(cudaMemsetAsync(ecur_b.as<void>(), 0, sizeof(unsigned long long) * (kEdgeSegs + 1), s));
-    int* d_err = errb.as<int>();
-    unsigned long long* d_ecur = ecur_b.as<unsigned long long>();  // [kEdgeSegs]: single-segment count
+    const bool join = T == 1;   // the deletion join (l_max = 1)
+    const bool cand2 = T == 2;  // candidates of shared variants + exact check (l_max = 2)
+    // partitions of the l_max = 1 join, sized from the record bound
+    int64_t P = 1;
+    if (join) {
+        const int target = partition_target > 0 ? partition_target
+                                                 : (R_max <= kTargetSwitchRecords ? kTargetPartSmall : kTargetPartLarge);
+        P = std::max<int64_t>(1, std::min<int64_t>(R_max / target + 1, 1LL << 30));
+    }
+    // Every counter of the build that starts at zero, cleared by one memset
+    // (u64 words): the edge cursors ([kEdgeSegs]: single-segment count), the
+    // distinct-string count, the device counters ([0] dedup error, [1] fill
+    // error, [2] fallback partitions, [3] partitions for the sorted join, [4]
+    // largest closed list), and the status words of the build's scans.
+    const int64_t w_scan_n = scan_status_words(n);
+    const int64_t w_scan_p = join ? scan_status_words(P) : 0;
+    const int64_t w_fixed = (kEdgeSegs + 1) + 1 + 4;
+    DevBuf zeroed;
+    TCR_CHECK(zeroed.alloc(sizeof(unsigned long long) * (w_fixed + 3 * w_scan_n + w_scan_p), s));
+    TCR_CUDA(cudaMemsetAsync(zeroed.as<void>(), 0, zeroed.bytes(), s));
+    unsigned long long* d_ecur = zeroed.as<unsigned long long>();
+    unsigned long long* d_ucount = d_ecur + (kEdgeSegs + 1);
+    int* d_err = reinterpret_cast<int*>(d_ucount + 1);
+    unsigned long long* st_members = d_ucount + 5;  // scan status words, one slice per scan
+    unsigned long long* st_uoff = st_members + w_scan_n;
+    unsigned long long* st_off64 = st_uoff + w_scan_n;
+    unsigned long long* st_poff = st_off64 + w_scan_n;
+    auto slice = [](unsigned long long* p, int64_t words) { return words > 0 ? p : nullptr; };
     // edges of the one-pass join: 2 x (records bound), split in kEdgeSegs segments
     const int64_t seg_cap = ceil_div(2 * R_max + 64, kEdgeSegs);
     const int64_t ecap = seg_cap * kEdgeSegs;
@@ -1195,14 +1259,12 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     // ---- 1. dedup
     int64_t S = 1024;
     while (S < 2 * n) S <<= 1;
-    DevBuf table, slot_of, slot_u, ucount;
+    DevBuf table, slot_of, slot_u;
     TCR_CHECK(table.alloc(sizeof(int32_t) * S, s));
     TCR_CHECK(slot_of.alloc(sizeof(int32_t) * n, s));
     TCR_CHECK(slot_u.alloc(sizeof(int32_t) * S, s));
-    TCR_CHECK(ucount.alloc(sizeof(int64_t), s));
     TCR_CUDA(cudaMemsetAsync(table.as<void>(), 0xff, sizeof(int32_t) * S, s));
-    TCR_CUDA(cudaMemsetAsync(ucount.as<void>(), 0, sizeof(int64_t), s));
-    const int64_t* d_U = ucount.as<int64_t>();  // number of distinct strings, on the device
+    const int64_t* d_U = reinterpret_cast<const int64_t*>(d_ucount);  // distinct strings, on the device
     DevBuf ucanon, ulen, umult, uid, mem_off, mcur, members, mpos;
     if (keep_index) TCR_CHECK(ucanon.alloc_owned(sizeof(Canon) * n, s));
     else TCR_CHECK(ucanon.alloc(sizeof(Canon) * n, s));
@@ -1220,8 +1282,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     TCR_CUDA(cudaMemsetAsync(umult.as<void>(), 0, sizeof(int32_t) * n, s));  // ids >= U stay 0
     k_dedup_insert<<<grid_for(n), kThreads, 0, s>>>(
         pk.canon_in.as<Canon>(), pk.lens.as<uint8_t>(), n, table.as<int32_t>(), (uint32_t)(S - 1),
-        slot_of.as<int32_t>(), slot_u.as<int32_t>(), reinterpret_cast<unsigned long long*>(ucount.as<int64_t>()),
-        ucanon.as<Canon>(), ulen.as<uint8_t>(), d_err);
+        slot_of.as<int32_t>(), slot_u.as<int32_t>(), d_ucount, ucanon.as<Canon>(), ulen.as<uint8_t>(), d_err);
     TCR_LAUNCH_CHECK();
     k_uid<<<grid_for(n), kThreads, 0, s>>>(slot_of.as<int32_t>(), slot_u.as<int32_t>(), n, uid.as<int32_t>(),
                                            umult.as<int32_t>());
@@ -1235,7 +1296,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         TCR_CUDA(cudaStreamWaitEvent(side->stream, side->ev[0], 0));
         ms = side->stream;
     }
-    TCR_CHECK(scan_exclusive_i32_to_i64(umult.as<int32_t>(), mem_off.as<int64_t>(), n, ms));
+    TCR_CHECK(scan_exclusive_i32_to_i64(umult.as<int32_t>(), mem_off.as<int64_t>(), n, ms, slice(st_members, w_scan_n)));
     TCR_CUDA(cudaMemsetAsync(mcur.as<void>(), 0, sizeof(int32_t) * n, ms));
     k_members<<<grid_for(n), kThreads, 0, ms>>>(uid.as<int32_t>(), n, mem_off.as<int64_t>(), mcur.as<int32_t>(),
                                                 members.as<int32_t>(), mpos.as<int32_t>());
@@ -1250,16 +1311,10 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     TCR_CHECK(uoff.alloc(sizeof(int64_t) * (n + 1), s));
     TCR_CUDA(cudaMemsetAsync(wsum.as<void>(), 0, sizeof(int32_t) * n, s));
     const Weigh weigh{umult.as<int32_t>(), wsum.as<int32_t>()};
-    const bool join = T == 1;   // the deletion join (l_max = 1)
-    const bool cand2 = T == 2;  // candidates of shared variants + exact check (l_max = 2)
-    int64_t P = 1;
     int jgrid = 1;
     int t2 = t1, t3 = t1;
     int64_t E2_cap = 0, R2 = 0, NC2 = 0;  // l_max = 2: edge buffer capacity, records, candidates
     if (join) {
-        const int target = partition_target > 0 ? partition_target
-                                                 : (R_max <= kTargetSwitchRecords ? kTargetPartSmall : kTargetPartLarge);
-        P = std::max<int64_t>(1, std::min<int64_t>(R_max / target + 1, 1LL << 30));
         TCR_CHECK(pcnt.alloc(sizeof(int32_t) * P, s));
         if (keep_index) TCR_CHECK(poff.alloc_owned(sizeof(int64_t) * (P + 1), s));
         else TCR_CHECK(poff.alloc(sizeof(int64_t) * (P + 1), s));
@@ -1275,11 +1330,12 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         k_records<false><<<rgrid, kThreads, 0, s>>>(ucanon.as<Canon>(), ulen.as<uint8_t>(), d_U, n,
                                                           (uint32_t)P, pcnt.as<int32_t>(), nullptr, nullptr);
         TCR_LAUNCH_CHECK();
-        TCR_CHECK(scan_exclusive_i32_to_i64(pcnt.as<int32_t>(), poff.as<int64_t>(), P, s));
-        TCR_CUDA(cudaMemsetAsync(pcnt.as<void>(), 0, sizeof(int32_t) * P, s));
+        // the scan clears the counts behind itself for the scatter's slot counters
+        TCR_CHECK(scan_exclusive_i32_to_i64(pcnt.as<int32_t>(), poff.as<int64_t>(), P, s, slice(st_poff, w_scan_p),
+                                            /*clear_input=*/true));
         k_records<true><<<rgrid, kThreads, 0, s>>>(ucanon.as<Canon>(), ulen.as<uint8_t>(), d_U, n,
                                                          (uint32_t)P, pcnt.as<int32_t>(), poff.as<int64_t>(),
-                                                         recs.as<uint64_t>());
+                                                         recs.as<uint64_t>(), 0u, R_max);
         TCR_LAUNCH_CHECK();
         t2 = tm.mark();
         // ---- 3a. join, pass 1: weighted degrees W_u
@@ -1287,7 +1343,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         k_join_small<false><<<jgrid, kThreads, 0, s>>>(
             poff.as<int64_t>(), P, recs.as<uint64_t>(), ucanon.as<Canon>(), umult.as<int32_t>(), cap, T,
             wsum.as<int32_t>(), pedges.as<int64_t>(), nullptr, edges.as<int2>(), d_ecur, seg_cap,
-            big_list.as<int32_t>(), d_err + 3, fb_list.as<int32_t>(), d_err + 2);
+            big_list.as<int32_t>(), d_err + 3, fb_list.as<int32_t>(), d_err + 2, R_max);
         TCR_LAUNCH_CHECK();
         k_join_sorted<false><<<num_sms * 4, kThreads, 0, s>>>(big_list.as<int32_t>(), d_err + 3, poff.as<int64_t>(),
                                                               recs.as<uint64_t>(), ucanon.as<Canon>(), T, weigh,
@@ -1373,19 +1429,37 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     k_closed_size<<<grid_for(n), kThreads, 0, s>>>(umult.as<int32_t>(), n, wsum.as<int32_t>(), ucur.as<int32_t>(),
                                                    d_err + 4);
     TCR_LAUNCH_CHECK();
-    TCR_CHECK(scan_exclusive_i32_to_i64(wsum.as<int32_t>(), uoff.as<int64_t>(), n, s));
+    TCR_CHECK(scan_exclusive_i32_to_i64(wsum.as<int32_t>(), uoff.as<int64_t>(), n, s, slice(st_uoff, w_scan_n)));
     k_node_degree<<<grid_for(n), kThreads, 0, s>>>(uid.as<int32_t>(), n, wsum.as<int32_t>(), deg.as<int32_t>());
     TCR_LAUNCH_CHECK();
-    TCR_CHECK(scan_exclusive_i32_to_i64(deg.as<int32_t>(), off64.as<int64_t>(), n, s));
-    int64_t sizes[2] = {0, 0};  // sum of D_u, nnz
-    unsigned long long segs[kEdgeSegs + 1];  // per-segment edge counts, then the single-list count
-    int h_dmax = 0;
-    TCR_CUDA(cudaMemcpyAsync(&sizes[0], uoff.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    TCR_CUDA(cudaMemcpyAsync(&sizes[1], off64.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    TCR_CUDA(cudaMemcpyAsync(segs, d_ecur, sizeof(segs), cudaMemcpyDeviceToHost, s));
-    TCR_CUDA(cudaMemcpyAsync(&h_dmax, d_err + 4, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TCR_CHECK(scan_exclusive_i32_to_i64(deg.as<int32_t>(), off64.as<int64_t>(), n, s, slice(st_off64, w_scan_n)));
+    // the sizes of the lists and of the CSR, the edge counts, the longest list
+    // and the encoder's error word come back in one synchronisation
+    static_assert(sizeof(MidReadback) <= kPinnedScratchBytes, "readback fits the pinned scratch");
+    MidReadback pageable;
+    MidReadback* rb = static_cast<MidReadback*>(pinned_scratch());
+    const unsigned long long* d_pack_flags = pk.flags.as<unsigned long long>();
+    if (rb && pinned_scratch_device()) {
+        k_mid_readback<<<1, 96, 0, s>>>(uoff.as<int64_t>() + n, off64.as<int64_t>() + n, d_ecur, d_err + 4,
+                                        d_pack_flags, static_cast<MidReadback*>(pinned_scratch_device()));
+        TCR_LAUNCH_CHECK();
+    } else {
+        if (!rb) rb = &pageable;
+        rb->pack_error = 0;
+        TCR_CUDA(cudaMemcpyAsync(&rb->sizes[0], uoff.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        TCR_CUDA(cudaMemcpyAsync(&rb->sizes[1], off64.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        TCR_CUDA(cudaMemcpyAsync(rb->segs, d_ecur, sizeof(rb->segs), cudaMemcpyDeviceToHost, s));
+        TCR_CUDA(cudaMemcpyAsync(&rb->dmax, d_err + 4, sizeof(int), cudaMemcpyDeviceToHost, s));
+        if (d_pack_flags)
+            TCR_CUDA(cudaMemcpyAsync(&rb->pack_error, d_pack_flags, sizeof(unsigned long long),
+                                     cudaMemcpyDeviceToHost, s));
+    }
     TCR_CUDA(cudaStreamSynchronize(s));
-    const int64_t SD = sizes[0], nnz = sizes[1];
+    TCR_CHECK(pack_flags_status(rb->pack_error, &out.bad_index));
+    unsigned long long segs[kEdgeSegs + 1];
+    for (int g = 0; g <= kEdgeSegs; ++g) segs[g] = rb->segs[g];
+    const int h_dmax = rb->dmax;
+    const int64_t SD = rb->sizes[0], nnz = rb->sizes[1];
     int64_t E = 0, seg_max = 0;
     bool overflow = false;
     for (int g = 0; g < kEdgeSegs; ++g) {
@@ -1496,12 +1570,24 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         uid.as<int32_t>(), n, uoff.as<int64_t>(), Sbuf.as<int32_t>(), off64.as<int64_t>(), cols.as<int32_t>());
     TCR_LAUNCH_CHECK();
     const int t6 = tm.mark();
-    int h_err[4] = {0, 0, 0, 0};  // the first four device counters
-    int64_t h_U = 0, h_R = 0;
-    TCR_CUDA(cudaMemcpyAsync(h_err, d_err, sizeof(h_err), cudaMemcpyDeviceToHost, s));
-    TCR_CUDA(cudaMemcpyAsync(&h_U, d_U, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    if (join) TCR_CUDA(cudaMemcpyAsync(&h_R, poff.as<int64_t>() + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    EndReadback pageable_end;
+    EndReadback* eb = static_cast<EndReadback*>(pinned_scratch());
+    if (eb && pinned_scratch_device()) {
+        k_end_readback<<<1, 32, 0, s>>>(d_err, d_U, join ? poff.as<int64_t>() + P : nullptr,
+                                        static_cast<EndReadback*>(pinned_scratch_device()));
+        TCR_LAUNCH_CHECK();
+    } else {
+        if (!eb) eb = &pageable_end;
+        eb->U = eb->R = 0;
+        TCR_CUDA(cudaMemcpyAsync(eb->err, d_err, sizeof(eb->err), cudaMemcpyDeviceToHost, s));
+        TCR_CUDA(cudaMemcpyAsync(&eb->U, d_U, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        if (join)
+            TCR_CUDA(cudaMemcpyAsync(&eb->R, poff.as<int64_t>() + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    }
     TCR_CUDA(cudaStreamSynchronize(s));
+    int h_err[4] = {eb->err[0], eb->err[1], eb->err[2], eb->err[3]};
+    const int64_t h_U = eb->U;
+    int64_t h_R = eb->R;
     if (cand2) h_R = R2;
     if (h_err[0] || h_err[1]) return TCRNET_EDEVICE;
 

@@ -44,6 +44,7 @@ struct DeletionResult {
     int64_t n_fallback = 0;    // partitions joined by the exact quadratic fallback
     int64_t closed_total = 0;  // sum over distinct strings of closed-neighbourhood sizes
     int two_pass_join = 0;     // 1 when the edges overflowed the one-pass buffer
+    int64_t bad_index = -1;    // input index of an encoder error found by the build (see pk.flags)
     double ms_join = 0, ms_scan = 0, ms_fill = 0, ms_sort = 0;
     // dedup, records, join count, join write, closed fill, closed sort, expand, total
     double ms_phase[8] = {0};
@@ -53,7 +54,11 @@ struct DeletionResult {
 // Network of the packed strings at l_max = T (0, 1 or 2; ENOTSUP above). Test
 // knob: partitions larger than `partition_cap` (<= the shared-memory capacity;
 // 0 = default) take the quadratic fallback of the l_max = 1 join. The query
-// index is kept (keep_index) for l_max = 1 builds.
+// index is kept (keep_index) for l_max = 1 builds. If the encoder's error word
+// (pk.flags) was not checked by the packing, the build checks it at its first
+// readback and returns the input error with out.bad_index; until then its
+// record kernels do nothing when the records counted exceed the n +
+// pk.lensum they were sized for (possible only for invalid input).
 tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaStream_t s, int num_sms,
                              bool profile, int partition_cap = 0, bool keep_index = false,
                              int partition_target = 0, bool force_off64 = false);

@@ -7,7 +7,14 @@ namespace tcr {
 
 // ---- scan.cu --------------------------------------------------------------
 // out[i] = sum_{k<i} in[k] for i in [0, n] (n + 1 outputs, out[n] = total).
-tcrnet_status scan_exclusive_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
+// zeroed_status: optional caller-provided status words, scan_status_words(n)
+// of them, all zero when the scan runs (a caller with several scans clears
+// them together; nullptr: the scan clears its own). clear_input: the scan
+// sets in[0 .. n) to zero behind itself (in place of a memset before the
+// input's next use as counters).
+int64_t scan_status_words(int64_t n);
+tcrnet_status scan_exclusive_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s,
+                                        unsigned long long* zeroed_status = nullptr, bool clear_input = false);
 tcrnet_status scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
 // int64 offsets -> int32 offsets (caller checked that they fit).
 tcrnet_status narrow_offsets(const int64_t* in, int32_t* out, int64_t count, cudaStream_t s);
@@ -24,7 +31,11 @@ struct Packed {
     DevBuf canon_in; // Canon[n], input order
     int64_t bucket_off[kMaxLen + 2] = {0};  // bucket L = [bucket_off[L], bucket_off[L+1])
     int64_t lensum = 0;                     // total length of the strings
+    DevBuf flags;  // device words of the encoder: [0] first error (~(index << 8 | status), 0: none), [1] total length
 };
+// Status of the encoder's error word (read back to the host): TCRNET_OK, or
+// the error with *bad_index set to the lowest offending input index.
+tcrnet_status pack_flags_status(unsigned long long first_error, int64_t* bad_index);
 // Encodes chars/offsets (device memory) into `out`. On a bad input returns the
 // status and sets *bad_index to the lowest offending input index. With
 // bucket = false only the input-order copy is made (no bucketed copy,
@@ -32,9 +43,13 @@ struct Packed {
 // keep (outside the call's workspace). Strings must lie in byte offsets
 // [lo, hi) of d_chars (TCRNET_EINVAL with the index otherwise; offsets that
 // decrease give an empty or negative length and fail the same way).
+// defer_check (only with bucket = false): return right after the encoder is
+// launched, without waiting for it; out.lensum is left at -1 and the caller
+// sets it (the byte span of the strings, exact for valid input), then reads
+// out.flags at its next synchronisation and reports pack_flags_status.
 tcrnet_status pack_strings(const uint8_t* d_chars, const int64_t* d_offsets, int64_t n, Packed& out,
                            int64_t* bad_index, cudaStream_t s, bool bucket = true, bool keep_input_order = false,
-                           int64_t lo = INT64_MIN, int64_t hi = INT64_MAX);
+                           int64_t lo = INT64_MIN, int64_t hi = INT64_MAX, bool defer_check = false);
 
 // Write repertoire numbers into the spare bits of input-order canon
 // (repertoire r = strings rep_off[r] .. rep_off[r+1]).

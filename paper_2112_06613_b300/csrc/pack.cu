@@ -59,7 +59,9 @@ k_encode(const uint8_t* __restrict__ chars, const int64_t* __restrict__ offs, in
             }
         }
         if (code_err) {
-            atomicMin(err, ((unsigned long long)i << 8) | code_err);
+            // the first error word holds the complement of (index << 8 | status)
+            // so that zero means "none" and the lowest index wins by atomicMax
+            atomicMax(err, ~(((unsigned long long)i << 8) | code_err));
             lens[i] = 0;
         } else {
             store_canon(canon + i, c);
@@ -200,9 +202,16 @@ tcrnet_status unbucket_strings(const Canon* canon, const int32_t* perm, const in
     return TCRNET_OK;
 }
 
+tcrnet_status pack_flags_status(unsigned long long first_error, int64_t* bad_index) {
+    if (first_error == 0) return TCRNET_OK;
+    const unsigned long long v = ~first_error;
+    *bad_index = (int64_t)(v >> 8);
+    return (tcrnet_status)(v & 0xff);
+}
+
 tcrnet_status pack_strings(const uint8_t* d_chars, const int64_t* d_offsets, int64_t n, Packed& out,
                            int64_t* bad_index, cudaStream_t s, bool bucket, bool keep_input_order, int64_t lo,
-                           int64_t hi) {
+                           int64_t hi, bool defer_check) {
     out.n = n;
     out.lensum = 0;
     *bad_index = -1;
@@ -221,21 +230,24 @@ tcrnet_status pack_strings(const uint8_t* d_chars, const int64_t* d_offsets, int
         TCR_CHECK(out.perm.alloc_owned(sizeof(int32_t) * n, s));
     }
     const int64_t ncnt = (int64_t)kBins * nblocks;
-    DevBuf blockcnt, blockoff, flags, bounds;
+    DevBuf blockcnt, blockoff, bounds;
     if (bucket) {
         TCR_CHECK(blockcnt.alloc(sizeof(int32_t) * ncnt, s));
         TCR_CHECK(blockoff.alloc(sizeof(int64_t) * (ncnt + 1), s));
         TCR_CHECK(bounds.alloc(sizeof(int64_t) * (kBins + 1), s));
     }
-    TCR_CHECK(flags.alloc(sizeof(unsigned long long) * 2, s));  // [0] first error, [1] total length
-    unsigned long long* d_flags = flags.as<unsigned long long>();
-    TCR_CUDA(cudaMemsetAsync(d_flags, 0xff, sizeof(unsigned long long), s));
-    TCR_CUDA(cudaMemsetAsync(d_flags + 1, 0, sizeof(unsigned long long), s));
+    TCR_CHECK(out.flags.alloc(sizeof(unsigned long long) * 2, s));  // [0] first error, [1] total length
+    unsigned long long* d_flags = out.flags.as<unsigned long long>();
+    TCR_CUDA(cudaMemsetAsync(d_flags, 0, 2 * sizeof(unsigned long long), s));
     k_encode<<<nblocks, kPackThreads, 0, s>>>(d_chars, d_offsets, n, lo, hi, out.canon_in.as<Canon>(),
                                               out.lens.as<uint8_t>(), bucket ? blockcnt.as<int32_t>() : nullptr,
                                               nblocks, d_flags, d_flags + 1);
     TCR_LAUNCH_CHECK();
-    unsigned long long h_flags[2] = {~0ull, 0};
+    if (defer_check && !bucket) {
+        out.lensum = -1;
+        return TCRNET_OK;
+    }
+    unsigned long long h_flags[2] = {0, 0};
     TCR_CUDA(cudaMemcpyAsync(h_flags, d_flags, sizeof(h_flags), cudaMemcpyDeviceToHost, s));
     int64_t h_bounds[kBins + 1];
     if (bucket) {
@@ -245,10 +257,7 @@ tcrnet_status pack_strings(const uint8_t* d_chars, const int64_t* d_offsets, int
         TCR_CUDA(cudaMemcpyAsync(h_bounds, bounds.as<void>(), sizeof(h_bounds), cudaMemcpyDeviceToHost, s));
     }
     TCR_CUDA(cudaStreamSynchronize(s));
-    if (h_flags[0] != ~0ull) {
-        *bad_index = (int64_t)(h_flags[0] >> 8);
-        return (tcrnet_status)(h_flags[0] & 0xff);
-    }
+    TCR_CHECK(pack_flags_status(h_flags[0], bad_index));
     out.lensum = (int64_t)h_flags[1];
     if (!bucket) return TCRNET_OK;
     for (int L = 0; L <= kBins; ++L) out.bucket_off[L] = h_bounds[L];

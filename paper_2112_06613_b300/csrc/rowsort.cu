@@ -370,21 +370,38 @@ tcrnet_status sort_rows(const int64_t* off, int32_t* cols, int64_t n, cudaStream
     k_sort_warp<<<(unsigned)blocks, kSortWarps * 32, 0, s>>>(off, cols, n, wide, cnt + 3, mid, cnt, big, cnt + 1);
     TCR_LAUNCH_CHECK();
     const bool known = max_len >= 0;  // a known bound skips the kernels of longer classes
+    const bool run_mid = !known || max_len > kWideMax;
+    const bool run_block = !known || max_len > 2 * kWideMax;
+    // The classes are disjoint rows: rows above 256 are sorted on the second
+    // stream of the workspace lease while this stream sorts 65..256.
+    const SideStream* side = (run_mid || run_block) ? leased_side_stream() : nullptr;
+    cudaStream_t s2 = s;
+    if (side) {
+        TCR_CUDA(cudaEventRecord(side->ev[4], s));
+        TCR_CUDA(cudaStreamWaitEvent(side->stream, side->ev[4], 0));
+        s2 = side->stream;
+    }
     if (!known || max_len > kShortMax) {
         k_sort_warp_wide<<<num_sms * 8, kSortWarps * 32, 0, s>>>(off, cols, wide, cnt + 3);
         TCR_LAUNCH_CHECK();
     }
-    if (!known || max_len > kWideMax) {
-        k_sort_warp_mid<16><<<num_sms * 4, kSortWarps * 32, 0, s>>>(off, cols, mid, cnt);
+    if (run_mid) {
+        k_sort_warp_mid<16><<<num_sms * 4, kSortWarps * 32, 0, s2>>>(off, cols, mid, cnt);
         TCR_LAUNCH_CHECK();
     }
-    if (known && max_len <= 2 * kWideMax) return TCRNET_OK;
+    if (run_block) {
+        const size_t smem = sizeof(int32_t) * kBlockCap;
+        TCR_CUDA(cudaFuncSetAttribute(k_sort_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        TCR_CUDA(cudaFuncSetAttribute(k_sort_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_sort_block<<<num_sms * 2, kBlockThreads, smem, s2>>>(off, cols, big, cnt + 1, huge_list, cnt + 2);
+        TCR_LAUNCH_CHECK();
+    }
+    if (side) {  // join the second stream back before anything reads the rows
+        TCR_CUDA(cudaEventRecord(side->ev[5], s2));
+        TCR_CUDA(cudaStreamWaitEvent(s, side->ev[5], 0));
+    }
+    if (!run_block || (known && max_len <= kBlockCap)) return TCRNET_OK;  // no row can be listed as huge
     const size_t smem = sizeof(int32_t) * kBlockCap;
-    TCR_CUDA(cudaFuncSetAttribute(k_sort_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    TCR_CUDA(cudaFuncSetAttribute(k_sort_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_sort_block<<<num_sms * 2, kBlockThreads, smem, s>>>(off, cols, big, cnt + 1, huge_list, cnt + 2);
-    TCR_LAUNCH_CHECK();
-    if (known && max_len <= kBlockCap) return TCRNET_OK;  // no row can be listed as huge
     int h_huge = 0;
     TCR_CUDA(cudaMemcpyAsync(&h_huge, cnt + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
     TCR_CUDA(cudaStreamSynchronize(s));

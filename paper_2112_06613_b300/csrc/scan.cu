@@ -110,10 +110,12 @@ __device__ __forceinline__ void st_release(unsigned long long* p, unsigned long 
 
 // status[0 .. tiles) publication words, status[tiles] the ticket counter,
 // status[tiles + 1] the error flag; all zero at launch.
+// `clear` (nullable) may be `in` itself: neither is declared restrict, and
+// each item is read into shared memory before it is cleared.
 template <typename TI>
-__global__ void __launch_bounds__(kScanThreads) k_scan_onepass(const TI* __restrict__ in, int64_t n,
-                                                                int64_t* __restrict__ out,
-                                                                unsigned long long* status, int64_t tiles) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_onepass(const TI* in, int64_t n, int64_t* __restrict__ out,
+                                                                unsigned long long* status, int64_t tiles,
+                                                                TI* clear) {
     __shared__ int64_t warp_tot[32];
     __shared__ int64_t stage[kScanTile];
     __shared__ int64_t s_prefix;
@@ -126,6 +128,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_onepass(const TI* __restr
     for (int k = 0; k < kScanItems; ++k) {
         const int idx = k * kScanThreads + threadIdx.x;
         stage[idx] = load_item(in, base + idx, n);
+    }
+    if (clear) {  // in place of a memset before the input's next use as counters
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            const int64_t i = base + k * kScanThreads + threadIdx.x;
+            if (i < n) clear[i] = 0;
+        }
     }
     __syncthreads();
     int64_t v[kScanItems];
@@ -199,7 +208,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_onepass(const TI* __restr
 }
 
 template <typename TI>
-tcrnet_status scan_impl(const TI* in, int64_t* out, int64_t n, cudaStream_t s) {
+tcrnet_status scan_impl(const TI* in, int64_t* out, int64_t n, cudaStream_t s,
+                        unsigned long long* zeroed_status = nullptr, bool clear_input = false) {
     if (n <= 0) {
         TCR_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
         return TCRNET_OK;
@@ -208,13 +218,19 @@ tcrnet_status scan_impl(const TI* in, int64_t* out, int64_t n, cudaStream_t s) {
     if (tiles == 1) {
         k_tile_scan<TI><<<1, kScanThreads, 0, s>>>(in, n, nullptr, out);
         TCR_LAUNCH_CHECK();
+        if (clear_input) TCR_CUDA(cudaMemsetAsync(const_cast<TI*>(in), 0, sizeof(TI) * n, s));
         return TCRNET_OK;
     }
     if (tiles > 0x7fffffffLL) return TCRNET_EINVAL;
     DevBuf status;
-    TCR_CHECK(status.alloc(sizeof(unsigned long long) * (tiles + 2), s));
-    TCR_CUDA(cudaMemsetAsync(status.as<void>(), 0, sizeof(unsigned long long) * (tiles + 2), s));
-    k_scan_onepass<TI><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, out, status.as<unsigned long long>(), tiles);
+    unsigned long long* st = zeroed_status;
+    if (!st) {
+        TCR_CHECK(status.alloc(sizeof(unsigned long long) * (tiles + 2), s));
+        TCR_CUDA(cudaMemsetAsync(status.as<void>(), 0, sizeof(unsigned long long) * (tiles + 2), s));
+        st = status.as<unsigned long long>();
+    }
+    k_scan_onepass<TI><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, out, st, tiles,
+                                                               clear_input ? const_cast<TI*>(in) : nullptr);
     TCR_LAUNCH_CHECK();
     return TCRNET_OK;
 }
@@ -238,8 +254,14 @@ inline unsigned grid_for(int64_t n, int threads) {
 
 }  // namespace
 
-tcrnet_status scan_exclusive_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s) {
-    return scan_impl<int32_t>(in, out, n, s);
+int64_t scan_status_words(int64_t n) {
+    const int64_t tiles = ceil_div(n, kScanTile);
+    return tiles > 1 ? tiles + 2 : 0;
+}
+
+tcrnet_status scan_exclusive_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s,
+                                        unsigned long long* zeroed_status, bool clear_input) {
+    return scan_impl<int32_t>(in, out, n, s, zeroed_status, clear_input);
 }
 
 tcrnet_status scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s) {

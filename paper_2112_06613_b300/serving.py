@@ -22,7 +22,8 @@ requests keep arriving:
   waits until running requests release theirs);
 - answers are copied into per-slot pinned host buffers allocated once, then
   into each request's own arrays (a copy to pageable memory of a long answer
-  goes through the driver's small staging buffers).
+  goes through the driver's small staging buffers); long answers are copied
+  out by a few host threads in parallel.
 
 All computation happens in the CUDA library; this module only schedules calls.
 """
@@ -30,6 +31,7 @@ All computation happens in the CUDA library; this module only schedules calls.
 from __future__ import annotations
 
 import collections
+import concurrent.futures as cf
 import threading
 import time
 from dataclasses import dataclass, field
@@ -78,7 +80,8 @@ class Request:
 
 class ServingEngine:
     def __init__(self, graph: Graph, slots: int = 4, max_batch_strings: int = 200_000,
-                 hbm_reserve_bytes: int = 4 << 30, device: int = 0, result_buffer_bytes: int = 64 << 20):
+                 hbm_reserve_bytes: int = 4 << 30, device: int = 0, result_buffer_bytes: int = 64 << 20,
+                 copy_threads: int = 4):
         import torch
 
         self.graph = graph
@@ -111,6 +114,10 @@ class ServingEngine:
                         torch.empty(max(result_buffer_bytes // 4, 1), dtype=torch.int32, pin_memory=True))
                        for _ in range(slots)]
         self._workers = [threading.Thread(target=self._run, args=(k,), daemon=True) for k in range(slots)]
+        # host copies of long answers are split over a few threads (numpy
+        # releases the GIL for them): one thread writing a fresh multi-MiB
+        # array, page faults included, was most of such a request's latency
+        self._copy_pool = cf.ThreadPoolExecutor(max_workers=copy_threads)
         self.completed: list[Request] = []
 
     # ---- lifecycle -----------------------------------------------------
@@ -126,6 +133,7 @@ class ServingEngine:
         if wait:
             for w in self._workers:
                 w.join()
+            self._copy_pool.shutdown(wait=True)
 
     def __enter__(self):
         return self.start()
@@ -272,6 +280,9 @@ class ServingEngine:
                 self._turn += 1
                 self._cv.notify_all()
 
+    def _copy_out(self, src: np.ndarray) -> np.ndarray:
+        return _parallel_copy(self._copy_pool, src)
+
     def _do_queries(self, batch: list[Request], stream, slot: int = 0):
         if len(batch) == 1:
             chars, offsets = batch[0].chars, batch[0].offsets
@@ -314,7 +325,7 @@ class ServingEngine:
             k = r.n_strings
             o = off[row:row + k + 1]
             r.offsets_out = o - o[0]
-            r.cols_out = cols[o[0]:o[-1]].copy()
+            r.cols_out = self._copy_out(cols[o[0]:o[-1]])
             r.version = version
             r.batch_id = bid
             row += k
@@ -324,6 +335,24 @@ class ServingEngine:
             r.s_copy = t_split - t_copy
             r.s_split = t_end - t_split
             r.batch_entries = int(nnz)
+
+
+_PARALLEL_COPY_MIN = 1 << 19  # entries (2 MiB of int32)
+
+
+def _parallel_copy(pool, src: np.ndarray) -> np.ndarray:
+    """A fresh copy of `src`, written in equal chunks by the pool's threads
+    when it is long."""
+    n = src.shape[0]
+    if n < _PARALLEL_COPY_MIN:
+        return src.copy()
+    dst = np.empty_like(src)
+    k = pool._max_workers
+    step = (n + k - 1) // k
+    futs = [pool.submit(np.copyto, dst[i * step:(i + 1) * step], src[i * step:(i + 1) * step]) for i in range(k)]
+    for f in futs:
+        f.result()
+    return dst
 
 
 def latency_summary(reqs, kind: str):
