@@ -12,8 +12,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <vector>
 #include <cstdio>
+#include <utility>
+#include <vector>
 
 #include "tcrnet.h"
 
@@ -104,6 +105,34 @@ __device__ __forceinline__ void warp_append_pairs(unsigned long long* cursor, in
 }
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Programmatic dependent launch (sm_90 and later). A kernel launched with
+// launch_dependent() may be scheduled while the kernel before it on the
+// stream is still finishing, which hides most of the launch gap between the
+// two. Such a kernel calls dep_entry() before anything else: it waits until
+// the kernel before it has completed and its writes are visible, then lets
+// the kernel after it be scheduled in turn. Launched normally, dep_entry()
+// returns at once, so a kernel may be launched either way.
+__device__ __forceinline__ void dep_entry() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                    Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Error record of the last failing CUDA call (diagnostics only).
 void note_cuda_error(cudaError_t e, const char* what, const char* file, int line);

@@ -225,6 +225,7 @@ __global__ void k_dedup_insert(const Canon* __restrict__ canon, const uint8_t* _
 // Distinct-string id of every node and the multiplicities m_u.
 __global__ void k_uid(const int32_t* __restrict__ slot_of, const int32_t* __restrict__ slot_u, int64_t n,
                       int32_t* __restrict__ uid, int32_t* __restrict__ umult) {
+    dep_entry();  // launched dependent on the kernel before it
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         const int32_t slot = slot_of[i];
@@ -257,6 +258,7 @@ __global__ void k_records(const Canon* __restrict__ ucanon, const uint8_t* __res
                           const int64_t* __restrict__ U_ptr, int64_t n, uint32_t P, int32_t* __restrict__ pcnt,
                           const int64_t* __restrict__ poff, uint64_t* __restrict__ recs, uint32_t u0 = 0,
                           int64_t R_cap = INT64_MAX) {
+    dep_entry();  // launched dependent on the kernel before it
     const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= n || u >= *U_ptr) return;
     if (SCATTER && poff[P] > R_cap) return;
@@ -451,6 +453,7 @@ k_join_small(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __rest
              int2* __restrict__ edges, unsigned long long* __restrict__ ecur, int64_t seg_cap,
              int32_t* __restrict__ big_list, int* __restrict__ big_count, int32_t* __restrict__ fb_list,
              int* __restrict__ fb_count, int64_t R_cap = INT64_MAX) {
+    dep_entry();  // launched dependent on the kernel before it
     if (poff[P] > R_cap) return;  // records beyond the array (invalid input): nothing is joined
     __shared__ uint64_t sbuf[kWarps][32];
     __shared__ int32_t smul[kWarps][32];
@@ -620,6 +623,7 @@ k_join_sorted(const int32_t* __restrict__ list, const int* __restrict__ count, c
               int64_t* __restrict__ pedges, const int64_t* __restrict__ eoff, int2* __restrict__ edges,
               unsigned long long* __restrict__ ecur, int64_t seg_cap, int32_t* __restrict__ fb_list,
               int* __restrict__ fb_count) {
+    dep_entry();  // launched dependent on the kernel before it
     __shared__ uint64_t sbuf[kWarps][kWarpCap];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint64_t* buf = sbuf[warp];
@@ -676,6 +680,7 @@ k_join_fallback(const int32_t* __restrict__ fb_list, const int* __restrict__ fb_
                 const uint64_t* __restrict__ recs, const Canon* __restrict__ ucanon, int T, Weigh weigh,
                 int64_t* __restrict__ pedges, const int64_t* __restrict__ eoff, int2* __restrict__ edges,
                 unsigned long long* __restrict__ ecur, int64_t seg_cap) {
+    dep_entry();  // launched dependent on the kernel before it
     __shared__ int64_t wtot[kWarps];
     const int nfb = *fb_count;
     for (int f = blockIdx.x; f < nfb; f += gridDim.x) {
@@ -964,6 +969,7 @@ k_cand_verify(const int64_t* __restrict__ coff, const int32_t* __restrict__ ccol
 // the largest D_u into *dmax.
 __global__ void k_closed_size(const int32_t* __restrict__ umult, int64_t U, int32_t* __restrict__ wsum,
                               int32_t* __restrict__ ucur, int* __restrict__ dmax) {
+    dep_entry();  // launched dependent on the kernel before it
     const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int d = 0;
     if (u < U) {
@@ -987,6 +993,7 @@ __global__ void k_closed_size(const int32_t* __restrict__ umult, int64_t U, int3
 
 __global__ void k_node_degree(const int32_t* __restrict__ uid, int64_t n, const int32_t* __restrict__ dsize,
                               int32_t* __restrict__ deg) {
+    dep_entry();  // launched dependent on the kernel before it
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) deg[i] = dsize[uid[i]] - 1;
 }
@@ -1190,6 +1197,7 @@ struct EndReadback {
 __global__ void k_mid_readback(const int64_t* __restrict__ sd, const int64_t* __restrict__ nnz,
                                const unsigned long long* __restrict__ ecur, const int* __restrict__ dmax,
                                const unsigned long long* __restrict__ pack_flags, MidReadback* dst) {
+    dep_entry();  // launched dependent on the kernel before it
     const int t = threadIdx.x;
     if (t <= kEdgeSegs) dst->segs[t] = ecur[t];
     if (t == 0) {
@@ -1202,6 +1210,7 @@ __global__ void k_mid_readback(const int64_t* __restrict__ sd, const int64_t* __
 
 __global__ void k_end_readback(const int* __restrict__ err, const int64_t* __restrict__ U,
                                const int64_t* __restrict__ R, EndReadback* dst) {
+    dep_entry();  // launched dependent on the kernel before it
     const int t = threadIdx.x;
     if (t < 4) dst->err[t] = err[t];
     if (t == 0) {
@@ -1280,13 +1289,22 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     else TCR_CHECK(members.alloc(sizeof(int32_t) * n, s));
     TCR_CHECK(mpos.alloc(sizeof(int32_t) * n, s));
     TCR_CUDA(cudaMemsetAsync(umult.as<void>(), 0, sizeof(int32_t) * n, s));  // ids >= U stay 0
+    // the join's counters are cleared here too, so that from the dedup on the
+    // kernels of this stream follow one another directly (dependent launches)
+    DevBuf pcnt, wsum;
+    TCR_CHECK(wsum.alloc(sizeof(int32_t) * n, s));
+    TCR_CUDA(cudaMemsetAsync(wsum.as<void>(), 0, sizeof(int32_t) * n, s));
+    if (join) {
+        TCR_CHECK(pcnt.alloc(sizeof(int32_t) * P, s));
+        TCR_CUDA(cudaMemsetAsync(pcnt.as<void>(), 0, sizeof(int32_t) * P, s));
+    }
     k_dedup_insert<<<grid_for(n), kThreads, 0, s>>>(
         pk.canon_in.as<Canon>(), pk.lens.as<uint8_t>(), n, table.as<int32_t>(), (uint32_t)(S - 1),
         slot_of.as<int32_t>(), slot_u.as<int32_t>(), d_ucount, ucanon.as<Canon>(), ulen.as<uint8_t>(), d_err);
     TCR_LAUNCH_CHECK();
-    k_uid<<<grid_for(n), kThreads, 0, s>>>(slot_of.as<int32_t>(), slot_u.as<int32_t>(), n, uid.as<int32_t>(),
-                                           umult.as<int32_t>());
-    TCR_LAUNCH_CHECK();
+    TCR_CUDA(launch_dependent(k_uid, dim3(grid_for(n)), dim3(kThreads), 0, s, slot_of.as<int32_t>(),
+                              slot_u.as<int32_t>(), n, uid.as<int32_t>(), umult.as<int32_t>()));
+    note_launch();
     // member lists M_u are first needed when the closed lists are filled: build
     // them on the side stream while the records and the join run
     const SideStream* side = leased_side_stream();
@@ -1305,17 +1323,14 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     const int t1 = tm.mark();
 
     // ---- 2. records
-    DevBuf pcnt, poff, recs, fb_list, big_list, pedges, eoff, wsum, ucur, uoff, edges;
-    TCR_CHECK(wsum.alloc(sizeof(int32_t) * n, s));
+    DevBuf poff, recs, fb_list, big_list, pedges, eoff, ucur, uoff, edges;
     TCR_CHECK(ucur.alloc(sizeof(int32_t) * n, s));
     TCR_CHECK(uoff.alloc(sizeof(int64_t) * (n + 1), s));
-    TCR_CUDA(cudaMemsetAsync(wsum.as<void>(), 0, sizeof(int32_t) * n, s));
     const Weigh weigh{umult.as<int32_t>(), wsum.as<int32_t>()};
     int jgrid = 1;
     int t2 = t1, t3 = t1;
     int64_t E2_cap = 0, R2 = 0, NC2 = 0;  // l_max = 2: edge buffer capacity, records, candidates
     if (join) {
-        TCR_CHECK(pcnt.alloc(sizeof(int32_t) * P, s));
         if (keep_index) TCR_CHECK(poff.alloc_owned(sizeof(int64_t) * (P + 1), s));
         else TCR_CHECK(poff.alloc(sizeof(int64_t) * (P + 1), s));
         if (keep_index) TCR_CHECK(recs.alloc_owned(sizeof(uint64_t) * R_max, s));
@@ -1325,36 +1340,37 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         TCR_CHECK(pedges.alloc(sizeof(int64_t) * P, s));
         TCR_CHECK(eoff.alloc(sizeof(int64_t) * (P + 1), s));
         TCR_CHECK(edges.alloc(sizeof(int2) * ecap, s));
-        TCR_CUDA(cudaMemsetAsync(pcnt.as<void>(), 0, sizeof(int32_t) * P, s));
         const unsigned rgrid = grid_for(n);
-        k_records<false><<<rgrid, kThreads, 0, s>>>(ucanon.as<Canon>(), ulen.as<uint8_t>(), d_U, n,
-                                                          (uint32_t)P, pcnt.as<int32_t>(), nullptr, nullptr);
-        TCR_LAUNCH_CHECK();
+        TCR_CUDA(launch_dependent(k_records<false>, dim3(rgrid), dim3(kThreads), 0, s, ucanon.as<Canon>(),
+                                  ulen.as<uint8_t>(), d_U, n, (uint32_t)P, pcnt.as<int32_t>(), nullptr, nullptr, 0u,
+                                  R_max));
+        note_launch();
         // the scan clears the counts behind itself for the scatter's slot counters
         TCR_CHECK(scan_exclusive_i32_to_i64(pcnt.as<int32_t>(), poff.as<int64_t>(), P, s, slice(st_poff, w_scan_p),
                                             /*clear_input=*/true));
-        k_records<true><<<rgrid, kThreads, 0, s>>>(ucanon.as<Canon>(), ulen.as<uint8_t>(), d_U, n,
-                                                         (uint32_t)P, pcnt.as<int32_t>(), poff.as<int64_t>(),
-                                                         recs.as<uint64_t>(), 0u, R_max);
-        TCR_LAUNCH_CHECK();
+        TCR_CUDA(launch_dependent(k_records<true>, dim3(rgrid), dim3(kThreads), 0, s, ucanon.as<Canon>(),
+                                  ulen.as<uint8_t>(), d_U, n, (uint32_t)P, pcnt.as<int32_t>(), poff.as<int64_t>(),
+                                  recs.as<uint64_t>(), 0u, R_max));
+        note_launch();
         t2 = tm.mark();
         // ---- 3a. join, pass 1: weighted degrees W_u
         jgrid = (int)std::min<int64_t>(ceil_div(P, 32 * kWarps), (int64_t)num_sms * 16);
-        k_join_small<false><<<jgrid, kThreads, 0, s>>>(
-            poff.as<int64_t>(), P, recs.as<uint64_t>(), ucanon.as<Canon>(), umult.as<int32_t>(), cap, T,
-            wsum.as<int32_t>(), pedges.as<int64_t>(), nullptr, edges.as<int2>(), d_ecur, seg_cap,
-            big_list.as<int32_t>(), d_err + 3, fb_list.as<int32_t>(), d_err + 2, R_max);
-        TCR_LAUNCH_CHECK();
-        k_join_sorted<false><<<num_sms * 4, kThreads, 0, s>>>(big_list.as<int32_t>(), d_err + 3, poff.as<int64_t>(),
-                                                              recs.as<uint64_t>(), ucanon.as<Canon>(), T, weigh,
-                                                              pedges.as<int64_t>(), nullptr, edges.as<int2>(), d_ecur,
-                                                              seg_cap, fb_list.as<int32_t>(), d_err + 2);
-        TCR_LAUNCH_CHECK();
-        k_join_fallback<false><<<num_sms * 2, kThreads, 0, s>>>(fb_list.as<int32_t>(), d_err + 2, poff.as<int64_t>(),
-                                                                recs.as<uint64_t>(), ucanon.as<Canon>(), T, weigh,
-                                                                pedges.as<int64_t>(), nullptr, edges.as<int2>(),
-                                                                d_ecur, seg_cap);
-        TCR_LAUNCH_CHECK();
+        TCR_CUDA(launch_dependent(k_join_small<false>, dim3(jgrid), dim3(kThreads), 0, s, poff.as<int64_t>(), P,
+                                  recs.as<uint64_t>(), ucanon.as<Canon>(), umult.as<int32_t>(), cap, T,
+                                  wsum.as<int32_t>(), pedges.as<int64_t>(), nullptr, edges.as<int2>(), d_ecur,
+                                  seg_cap, big_list.as<int32_t>(), d_err + 3, fb_list.as<int32_t>(), d_err + 2,
+                                  R_max));
+        note_launch();
+        TCR_CUDA(launch_dependent(k_join_sorted<false>, dim3(num_sms * 4), dim3(kThreads), 0, s,
+                                  big_list.as<int32_t>(), d_err + 3, poff.as<int64_t>(), recs.as<uint64_t>(),
+                                  ucanon.as<Canon>(), T, weigh, pedges.as<int64_t>(), nullptr, edges.as<int2>(),
+                                  d_ecur, seg_cap, fb_list.as<int32_t>(), d_err + 2));
+        note_launch();
+        TCR_CUDA(launch_dependent(k_join_fallback<false>, dim3(num_sms * 2), dim3(kThreads), 0, s,
+                                  fb_list.as<int32_t>(), d_err + 2, poff.as<int64_t>(), recs.as<uint64_t>(),
+                                  ucanon.as<Canon>(), T, weigh, pedges.as<int64_t>(), nullptr, edges.as<int2>(),
+                                  d_ecur, seg_cap));
+        note_launch();
         t3 = tm.mark();
     } else if (cand2) {
         // records of every variant with up to two deletions, partitioned by hash
@@ -1426,12 +1442,13 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     DevBuf deg, off64;
     TCR_CHECK(deg.alloc_owned(sizeof(int32_t) * n, s));  // results are handed to the handle
     TCR_CHECK(off64.alloc_owned(sizeof(int64_t) * (n + 1), s));
-    k_closed_size<<<grid_for(n), kThreads, 0, s>>>(umult.as<int32_t>(), n, wsum.as<int32_t>(), ucur.as<int32_t>(),
-                                                   d_err + 4);
-    TCR_LAUNCH_CHECK();
+    TCR_CUDA(launch_dependent(k_closed_size, dim3(grid_for(n)), dim3(kThreads), 0, s, umult.as<int32_t>(), n,
+                              wsum.as<int32_t>(), ucur.as<int32_t>(), d_err + 4));
+    note_launch();
     TCR_CHECK(scan_exclusive_i32_to_i64(wsum.as<int32_t>(), uoff.as<int64_t>(), n, s, slice(st_uoff, w_scan_n)));
-    k_node_degree<<<grid_for(n), kThreads, 0, s>>>(uid.as<int32_t>(), n, wsum.as<int32_t>(), deg.as<int32_t>());
-    TCR_LAUNCH_CHECK();
+    TCR_CUDA(launch_dependent(k_node_degree, dim3(grid_for(n)), dim3(kThreads), 0, s, uid.as<int32_t>(), n,
+                              wsum.as<int32_t>(), deg.as<int32_t>()));
+    note_launch();
     TCR_CHECK(scan_exclusive_i32_to_i64(deg.as<int32_t>(), off64.as<int64_t>(), n, s, slice(st_off64, w_scan_n)));
     // the sizes of the lists and of the CSR, the edge counts, the longest list
     // and the encoder's error word come back in one synchronisation
@@ -1440,9 +1457,10 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     MidReadback* rb = static_cast<MidReadback*>(pinned_scratch());
     const unsigned long long* d_pack_flags = pk.flags.as<unsigned long long>();
     if (rb && pinned_scratch_device()) {
-        k_mid_readback<<<1, 96, 0, s>>>(uoff.as<int64_t>() + n, off64.as<int64_t>() + n, d_ecur, d_err + 4,
-                                        d_pack_flags, static_cast<MidReadback*>(pinned_scratch_device()));
-        TCR_LAUNCH_CHECK();
+        TCR_CUDA(launch_dependent(k_mid_readback, dim3(1), dim3(96), 0, s, uoff.as<int64_t>() + n,
+                                  off64.as<int64_t>() + n, d_ecur, d_err + 4, d_pack_flags,
+                                  static_cast<MidReadback*>(pinned_scratch_device())));
+        note_launch();
     } else {
         if (!rb) rb = &pageable;
         rb->pack_error = 0;
@@ -1573,9 +1591,10 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     EndReadback pageable_end;
     EndReadback* eb = static_cast<EndReadback*>(pinned_scratch());
     if (eb && pinned_scratch_device()) {
-        k_end_readback<<<1, 32, 0, s>>>(d_err, d_U, join ? poff.as<int64_t>() + P : nullptr,
-                                        static_cast<EndReadback*>(pinned_scratch_device()));
-        TCR_LAUNCH_CHECK();
+        TCR_CUDA(launch_dependent(k_end_readback, dim3(1), dim3(32), 0, s, d_err, d_U,
+                                  join ? poff.as<int64_t>() + P : nullptr,
+                                  static_cast<EndReadback*>(pinned_scratch_device())));
+        note_launch();
     } else {
         if (!eb) eb = &pageable_end;
         eb->U = eb->R = 0;

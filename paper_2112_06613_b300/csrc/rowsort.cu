@@ -242,6 +242,7 @@ k_sort_warp(const int64_t* __restrict__ off, int32_t* __restrict__ cols, int64_t
 __global__ void __launch_bounds__(kSortWarps * 32)
 k_sort_warp_wide(const int64_t* __restrict__ off, int32_t* __restrict__ cols, const int32_t* __restrict__ rows,
                  const int* __restrict__ nrows) {
+    dep_entry();  // launched dependent on the kernel before it
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int count = *nrows;
     for (int64_t k = (int64_t)blockIdx.x * kSortWarps + warp; k < count; k += (int64_t)gridDim.x * kSortWarps) {
@@ -382,8 +383,9 @@ tcrnet_status sort_rows(const int64_t* off, int32_t* cols, int64_t n, cudaStream
         s2 = side->stream;
     }
     if (!known || max_len > kShortMax) {
-        k_sort_warp_wide<<<num_sms * 8, kSortWarps * 32, 0, s>>>(off, cols, wide, cnt + 3);
-        TCR_LAUNCH_CHECK();
+        TCR_CUDA(launch_dependent(k_sort_warp_wide, dim3(num_sms * 8), dim3(kSortWarps * 32), 0, s, off, cols,
+                                  wide, cnt + 3));
+        note_launch();
     }
     if (run_mid) {
         k_sort_warp_mid<16><<<num_sms * 4, kSortWarps * 32, 0, s2>>>(off, cols, mid, cnt);

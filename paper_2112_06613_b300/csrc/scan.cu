@@ -116,6 +116,7 @@ template <typename TI>
 __global__ void __launch_bounds__(kScanThreads) k_scan_onepass(const TI* in, int64_t n, int64_t* __restrict__ out,
                                                                 unsigned long long* status, int64_t tiles,
                                                                 TI* clear) {
+    dep_entry();  // launched dependent on the kernel before it
     __shared__ int64_t warp_tot[32];
     __shared__ int64_t stage[kScanTile];
     __shared__ int64_t s_prefix;
@@ -229,9 +230,9 @@ tcrnet_status scan_impl(const TI* in, int64_t* out, int64_t n, cudaStream_t s,
         TCR_CUDA(cudaMemsetAsync(status.as<void>(), 0, sizeof(unsigned long long) * (tiles + 2), s));
         st = status.as<unsigned long long>();
     }
-    k_scan_onepass<TI><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, out, st, tiles,
-                                                               clear_input ? const_cast<TI*>(in) : nullptr);
-    TCR_LAUNCH_CHECK();
+    TCR_CUDA(launch_dependent(k_scan_onepass<TI>, dim3((unsigned)tiles), dim3(kScanThreads), 0, s, in, n, out, st,
+                              tiles, clear_input ? const_cast<TI*>(in) : nullptr));
+    note_launch();
     return TCRNET_OK;
 }
 
