@@ -75,11 +75,7 @@ OPS_INDEL_PER_WORD = 26
 # DRAM bytes (read + write) per build of the phase's kernels at N = 800,000,
 # from one ncu capture of the current kernels (profiles/k_join_small_n800000.md,
 # profiles/k_records_expand_n800000.md); None where no capture covers the phase.
-PHASE_TRAFFIC_N800000 = {
-    "join_weigh": 100.13e6 + 6.18e6 + 21.85e6 + 0.03e6,
-    "records": 21.91e6 + 86.48e6 + 105.33e6,
-    "expand": 84.22e6 + 198.65e6,
-}
+PHASE_TRAFFIC_N800000 = {}  # filled from the current capture (see profiles/)
 
 LEGS = ("peaks", "tile", "query", "e2e", "insert", "analytics", "lmax2", "batched", "serving", "cpu")
 EXTRA_LEGS = ("cpu_full",)  # run only when named in --legs
@@ -156,7 +152,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "25"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
             return
@@ -646,13 +642,21 @@ def run_ours(args):
     def build(method=args.method, profile=True):
         return tn.tcrnet_build_flat(chars, offs, 1, method=method, stream=stream, profile=profile)
 
-    for _ in range(args.warmup):
-        build().free()
-    torch.cuda.synchronize()
-
+    # the clock sampler starts before the warm-up builds, so that it runs
+    # through the timed region without an idle pause in front of it (a 0.3 s
+    # sleep there let host and GPU fall into deeper idle states and made the
+    # first ~150 timed builds up to 20% slower, measured)
     sampler = ClockSampler(local)
     sampler.start()
-    time.sleep(0.3)
+    warm = 0
+    t_warm = time.perf_counter()
+    # at least W builds, then more (untimed) until the sampler reports, so that
+    # its samples cover the timed region even when that is short
+    while warm < args.warmup or (sampler.proc is not None and not sampler.lines
+                                 and time.perf_counter() - t_warm < 2.0):
+        build().free()
+        warm += 1
+    torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     stats = []
     if dist:
@@ -746,16 +750,20 @@ def run_ours(args):
                       "frac": ew / hbm_peak, "bytes_per_launch": 4 * nnz, "ms_per_launch": phase_ms["expand"],
                       "traffic": PHASE_TRAFFIC_N800000.get("expand") if n == 800_000 else None}
 
+    q = np.percentile(step_ms, [0, 10, 50, 90, 100])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step_distribution": {"min": float(q[0]), "p10": float(q[1]), "p50": float(q[2]), "p90": float(q[3]),
+                                     "max": float(q[4]), "note": "this rank's CUDA-event step times; "
+                                                                 "ms_per_step is their mean (max over ranks)"},
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": workload_config(args, "deletion" if st0["method"] == 2 else "tile"),
         "candidate_pairs_per_build": cand_per_build, "all_pairs_per_s": all_pairs_per_s,
         "all_pairs_per_build": pairs_per_build,
         "edges_per_s": edges_per_s, "edges_per_build": edges, "nnz": nnz, "edge_write": edge_write,
         "wall_s_timed_region": wall, "phases_ms": phase_ms, "roofline": roofline, "roofline_step": roofline_step,
-        "gpu_launches": launches, "clocks": clocks,
+        "gpu_launches": launches, "clocks": clocks, "warmup_builds": warm,
     }
 
     legs = set(args.legs.split(",")) - {""}

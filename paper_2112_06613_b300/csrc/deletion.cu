@@ -55,6 +55,7 @@
 #include <vector>
 
 #include "deletion.cuh"
+#include "lookback.cuh"
 
 namespace tcr {
 namespace {
@@ -991,6 +992,92 @@ __global__ void k_closed_size(const int32_t* __restrict__ umult, int64_t U, int3
     }
 }
 
+// Sizes of the closed lists and of the CSR rows with both offset scans, in
+// one launch of two independent look-back chains (lookback.cuh), blockIdx.y:
+// chain 0 scans D_u = m_u + W_u over the string ids u < n (list offsets uoff;
+// the list cursors start after the own members, ucur_u = m_u; the largest D_u
+// into *dmax), chain 1 scans d(i) = D_{u(i)} - 1 over the nodes (CSR offsets
+// off64, and the degree array). In place of k_closed_size, k_node_degree and
+// two scans (four launches, two look-back latencies in a row).
+__global__ void __launch_bounds__(kScanThreads)
+k_fill_sizes(const int32_t* __restrict__ wsum, const int32_t* __restrict__ umult, const int32_t* __restrict__ uid,
+             int64_t n, int32_t* __restrict__ ucur, int* __restrict__ dmax, int32_t* __restrict__ deg,
+             int64_t* __restrict__ uoff, int64_t* __restrict__ off64, unsigned long long* st_u,
+             unsigned long long* st_n, int64_t tiles) {
+    dep_entry();  // launched dependent on the kernel before it
+    __shared__ int64_t warp_tot[32];
+    __shared__ int64_t stage[kScanStage];
+    __shared__ int64_t s_prefix;
+    __shared__ int64_t s_tile;
+    __shared__ int s_max[kScanThreads / 32];
+    const bool nodes = blockIdx.y == 1;
+    unsigned long long* status = nodes ? st_n : st_u;
+    int64_t* out = nodes ? off64 : uoff;
+    if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(status + tiles, 1ull);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t base = tile * kScanTile;
+    int dm = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int idx = k * kScanThreads + threadIdx.x;
+        const int64_t i = base + idx;
+        int32_t v = 0;
+        if (i < n) {
+            if (nodes) {
+                const int32_t u = uid[i];
+                v = wsum[u] + umult[u] - 1;
+                deg[i] = v;
+            } else {
+                const int32_t m = umult[i];
+                v = wsum[i] + m;
+                ucur[i] = m;
+                dm = max(dm, v);
+            }
+        }
+        stage[scan_slot(idx)] = v;
+    }
+    if (!nodes) {  // block maximum of D_u, one atomic per block
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dm = max(dm, __shfl_xor_sync(kFull, dm, o));
+        if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = dm;
+    }
+    __syncthreads();
+    if (!nodes && threadIdx.x < 32) {
+        int d = threadIdx.x < kScanThreads / 32 ? s_max[threadIdx.x] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d = max(d, __shfl_xor_sync(kFull, d, o));
+        if (threadIdx.x == 0 && d > 0) atomicMax(dmax, d);
+    }
+    int64_t v[kScanItems];
+    int64_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = stage[scan_slot(threadIdx.x * kScanItems + k)];
+        sum += v[k];
+    }
+    int64_t excl;
+    const int64_t tot = scan_block_exclusive(sum, excl, warp_tot);
+    if (threadIdx.x < 32) {
+        const int64_t prefix = scan_lookback(tile, tot, status, tiles);
+        if (threadIdx.x == 0) s_prefix = prefix;
+    }
+    __syncthreads();
+    int64_t run = s_prefix + excl;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        stage[scan_slot(threadIdx.x * kScanItems + k)] = run;
+        run += v[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = base + k * kScanThreads + threadIdx.x;
+        if (i < n) out[i] = stage[scan_slot(k * kScanThreads + threadIdx.x)];
+    }
+    if (tile == tiles - 1 && threadIdx.x == 0) out[n] = s_prefix + tot;  // the grand total
+}
+
 __global__ void k_node_degree(const int32_t* __restrict__ uid, int64_t n, const int32_t* __restrict__ dsize,
                               int32_t* __restrict__ deg) {
     dep_entry();  // launched dependent on the kernel before it
@@ -1442,14 +1529,23 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     DevBuf deg, off64;
     TCR_CHECK(deg.alloc_owned(sizeof(int32_t) * n, s));  // results are handed to the handle
     TCR_CHECK(off64.alloc_owned(sizeof(int64_t) * (n + 1), s));
-    TCR_CUDA(launch_dependent(k_closed_size, dim3(grid_for(n)), dim3(kThreads), 0, s, umult.as<int32_t>(), n,
-                              wsum.as<int32_t>(), ucur.as<int32_t>(), d_err + 4));
-    note_launch();
-    TCR_CHECK(scan_exclusive_i32_to_i64(wsum.as<int32_t>(), uoff.as<int64_t>(), n, s, slice(st_uoff, w_scan_n)));
-    TCR_CUDA(launch_dependent(k_node_degree, dim3(grid_for(n)), dim3(kThreads), 0, s, uid.as<int32_t>(), n,
-                              wsum.as<int32_t>(), deg.as<int32_t>()));
-    note_launch();
-    TCR_CHECK(scan_exclusive_i32_to_i64(deg.as<int32_t>(), off64.as<int64_t>(), n, s, slice(st_off64, w_scan_n)));
+    if (w_scan_n > 0) {  // several tiles: sizes and both scans in one launch
+        const int64_t tiles = ceil_div(n, kScanTile);
+        TCR_CUDA(launch_dependent(k_fill_sizes, dim3((unsigned)tiles, 2), dim3(kScanThreads), 0, s,
+                                  wsum.as<int32_t>(), umult.as<int32_t>(), uid.as<int32_t>(), n, ucur.as<int32_t>(),
+                                  d_err + 4, deg.as<int32_t>(), uoff.as<int64_t>(), off64.as<int64_t>(), st_uoff,
+                                  st_off64, tiles));
+        note_launch();
+    } else {
+        TCR_CUDA(launch_dependent(k_closed_size, dim3(grid_for(n)), dim3(kThreads), 0, s, umult.as<int32_t>(), n,
+                                  wsum.as<int32_t>(), ucur.as<int32_t>(), d_err + 4));
+        note_launch();
+        TCR_CHECK(scan_exclusive_i32_to_i64(wsum.as<int32_t>(), uoff.as<int64_t>(), n, s));
+        TCR_CUDA(launch_dependent(k_node_degree, dim3(grid_for(n)), dim3(kThreads), 0, s, uid.as<int32_t>(), n,
+                                  wsum.as<int32_t>(), deg.as<int32_t>()));
+        note_launch();
+        TCR_CHECK(scan_exclusive_i32_to_i64(deg.as<int32_t>(), off64.as<int64_t>(), n, s));
+    }
     // the sizes of the lists and of the CSR, the edge counts, the longest list
     // and the encoder's error word come back in one synchronisation
     static_assert(sizeof(MidReadback) <= kPinnedScratchBytes, "readback fits the pinned scratch");

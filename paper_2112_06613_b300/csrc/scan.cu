@@ -1,56 +1,16 @@
 // Exclusive prefix sums (row counts -> CSR offsets) and offset helpers.
 //
-// One pass with decoupled look-back: each block takes the next tile by ticket
-// (an atomic counter, so tiles start in order), scans its 4096 items (512
-// threads, 8 contiguous items per thread staged through shared memory so
-// global accesses stay coalesced), publishes its tile total, then one warp
-// looks back over the preceding tiles' published words 32 at a time, adding
-// tile totals until it meets a tile that has published its inclusive prefix.
-// A tile only ever waits for tiles with smaller tickets, which are already
-// running and wait only on tiles before them, so every wait ends; each wait is
-// still bounded (kMaxLookbackSpins), after which the kernel records an error
-// flag and goes on. The input is read once; one launch plus the clearing of
-// the ticket and status words per scan. Single-tile inputs take one block.
+// One pass with decoupled look-back (lookback.cuh): one launch per scan, the
+// input read once. Single-tile inputs take one block without look-back.
 #include "kernels.cuh"
+#include "lookback.cuh"
 
 namespace tcr {
 namespace {
 
-constexpr int kScanThreads = 512;
-constexpr int kScanItems = 8;
-constexpr int kScanTile = kScanThreads * kScanItems;
-
 template <typename TI>
 __device__ __forceinline__ int64_t load_item(const TI* in, int64_t i, int64_t n) {
     return i < n ? (int64_t)in[i] : 0;
-}
-
-// Block-wide exclusive scan of one value per thread; returns the block total.
-__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t& excl, int64_t* warp_tot) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int64_t x = v;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        int64_t y = __shfl_up_sync(kFull, x, d);
-        if (lane >= d) x += y;
-    }
-    if (lane == 31) warp_tot[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        int64_t t = lane < (kScanThreads / 32) ? warp_tot[lane] : 0;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            int64_t y = __shfl_up_sync(kFull, t, d);
-            if (lane >= d) t += y;
-        }
-        if (lane < (kScanThreads / 32)) warp_tot[lane] = t;  // inclusive warp totals
-    }
-    __syncthreads();
-    int64_t base = warp > 0 ? warp_tot[warp - 1] : 0;
-    excl = base + x - v;
-    int64_t total = warp_tot[kScanThreads / 32 - 1];
-    __syncthreads();
-    return total;
 }
 
 template <typename TI>
@@ -58,54 +18,37 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(const TI* __restrict
                                                              const int64_t* __restrict__ tile_base,
                                                              int64_t* __restrict__ out) {
     __shared__ int64_t warp_tot[32];
-    __shared__ int64_t stage[kScanTile];
+    __shared__ int64_t stage[kScanStage];
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         int idx = k * kScanThreads + threadIdx.x;
-        stage[idx] = load_item(in, base + idx, n);
+        stage[scan_slot(idx)] = load_item(in, base + idx, n);
     }
     __syncthreads();
     int64_t v[kScanItems];
     int64_t s = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        v[k] = stage[threadIdx.x * kScanItems + k];
+        v[k] = stage[scan_slot(threadIdx.x * kScanItems + k)];
         s += v[k];
     }
     int64_t excl;
-    int64_t tot = block_exclusive_scan(s, excl, warp_tot);
+    int64_t tot = scan_block_exclusive(s, excl, warp_tot);
     int64_t run = excl + (tile_base ? tile_base[blockIdx.x] : 0);
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        stage[threadIdx.x * kScanItems + k] = run;
+        stage[scan_slot(threadIdx.x * kScanItems + k)] = run;
         run += v[k];
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         int64_t i = base + k * kScanThreads + threadIdx.x;
-        if (i < n) out[i] = stage[k * kScanThreads + threadIdx.x];
+        if (i < n) out[i] = stage[scan_slot(k * kScanThreads + threadIdx.x)];
     }
     // the last tile also writes the grand total at out[n]
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = (tile_base ? tile_base[blockIdx.x] : 0) + tot;
-}
-
-// Published word of a tile: flag in bits 63..62 (0 nothing yet, 1 tile total,
-// 2 inclusive prefix through this tile), value in bits 61..0.
-constexpr unsigned long long kFlagTotal = 1ull << 62;
-constexpr unsigned long long kFlagIncl = 2ull << 62;
-constexpr unsigned long long kValueMask = (1ull << 62) - 1;
-constexpr int kMaxLookbackSpins = 1 << 22;
-
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 // status[0 .. tiles) publication words, status[tiles] the ticket counter,
@@ -118,7 +61,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_onepass(const TI* in, int
                                                                 TI* clear) {
     dep_entry();  // launched dependent on the kernel before it
     __shared__ int64_t warp_tot[32];
-    __shared__ int64_t stage[kScanTile];
+    __shared__ int64_t stage[kScanStage];
     __shared__ int64_t s_prefix;
     __shared__ int64_t s_tile;
     if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(status + tiles, 1ull);
@@ -128,7 +71,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_onepass(const TI* in, int
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         const int idx = k * kScanThreads + threadIdx.x;
-        stage[idx] = load_item(in, base + idx, n);
+        stage[scan_slot(idx)] = load_item(in, base + idx, n);
     }
     if (clear) {  // in place of a memset before the input's next use as counters
 #pragma unroll
@@ -142,68 +85,27 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_onepass(const TI* in, int
     int64_t sum = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        v[k] = stage[threadIdx.x * kScanItems + k];
+        v[k] = stage[scan_slot(threadIdx.x * kScanItems + k)];
         sum += v[k];
     }
     int64_t excl;
-    const int64_t tot = block_exclusive_scan(sum, excl, warp_tot);
+    const int64_t tot = scan_block_exclusive(sum, excl, warp_tot);
     if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        if (tile == 0) {
-            if (lane == 0) {
-                st_release(status, kFlagIncl | ((unsigned long long)tot & kValueMask));
-                s_prefix = 0;
-            }
-        } else {
-            if (lane == 0) st_release(status + tile, kFlagTotal | ((unsigned long long)tot & kValueMask));
-            // look back: lane k reads tile (window - k); the nearest tile with an
-            // inclusive prefix ends the walk, the tiles before it add their totals
-            int64_t prefix = 0;
-            int64_t window = tile - 1;
-            bool gave_up = false;
-            while (true) {
-                const int64_t j = window - lane;
-                unsigned long long w = kFlagIncl;  // beyond tile 0: nothing to add
-                if (j >= 0) {
-                    int spins = 0;
-                    while (((w = ld_acquire(status + j)) >> 62) == 0) {
-                        if (++spins >= kMaxLookbackSpins) {
-                            gave_up = true;
-                            w = kFlagIncl;  // bounded: end the walk (the error flag is set below)
-                            break;
-                        }
-                        __nanosleep(32);
-                    }
-                }
-                __syncwarp();
-                const unsigned incl = __ballot_sync(kFull, (w >> 62) == 2);
-                const int stop = incl ? __ffs(incl) - 1 : 32;  // nearest lane with an inclusive word
-                int64_t add = (lane <= stop && j >= 0) ? (int64_t)(w & kValueMask) : 0;
-#pragma unroll
-                for (int d = 16; d > 0; d >>= 1) add += __shfl_xor_sync(kFull, add, d);
-                prefix += add;
-                if (incl) break;
-                window -= 32;
-            }
-            if (__any_sync(kFull, gave_up) && lane == 0) atomicExch(status + tiles + 1, 1ull);
-            if (lane == 0) {
-                st_release(status + tile, kFlagIncl | ((unsigned long long)(prefix + tot) & kValueMask));
-                s_prefix = prefix;
-            }
-        }
+        const int64_t prefix = scan_lookback(tile, tot, status, tiles);
+        if (threadIdx.x == 0) s_prefix = prefix;
     }
     __syncthreads();
     int64_t run = s_prefix + excl;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        stage[threadIdx.x * kScanItems + k] = run;
+        stage[scan_slot(threadIdx.x * kScanItems + k)] = run;
         run += v[k];
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         const int64_t i = base + k * kScanThreads + threadIdx.x;
-        if (i < n) out[i] = stage[k * kScanThreads + threadIdx.x];
+        if (i < n) out[i] = stage[scan_slot(k * kScanThreads + threadIdx.x)];
     }
     if (tile == tiles - 1 && threadIdx.x == 0) out[n] = s_prefix + tot;  // the grand total
 }
