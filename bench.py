@@ -245,7 +245,10 @@ def sampled_rate(rep, seconds, fn, nthreads, seed=0, rows_per_call=None, min_cal
 
     cores = nthreads if nthreads > 0 else oracle.max_threads()
     rng = np.random.default_rng(seed)
-    per = rows_per_call or max(1, cores)
+    # eight rows per thread and call: row times vary, and with one row per
+    # thread the threads idled at the end of every call (the sampled all-core
+    # rates came out 2-4x below those of a 10,000-row call)
+    per = rows_per_call or max(1, 8 * cores)
     lens = rep.lengths()
     cand_build = candidate_pairs(lens)
     done, calls, t0 = 0, 0, time.perf_counter()
@@ -346,7 +349,7 @@ def run_reference(args):
     rep = workload(args.n, 0)
     cores = oracle.max_threads()
     rng = np.random.default_rng(1)
-    per = max(1, cores)  # one row per core per step (about 0.3 s)
+    per = max(1, 4 * cores)  # four rows per thread per step (about 0.6 s; balanced across threads)
     cand_build = candidate_pairs(rep.lengths())
 
     def step():
