@@ -73,9 +73,14 @@ OPS_INDEL_PER_WORD = 26
 
 
 # DRAM bytes (read + write) per build of the phase's kernels at N = 800,000,
-# from one ncu capture of the current kernels (profiles/k_join_small_n800000.md,
-# profiles/k_records_expand_n800000.md); None where no capture covers the phase.
-PHASE_TRAFFIC_N800000 = {}  # filled from the current capture (see profiles/)
+# from one ncu capture of the current kernels (profiles/k_records_join_n800000.md,
+# profiles/k_sort_fill_expand_n800000.md); absent where no capture covers the phase.
+PHASE_TRAFFIC_N800000 = {
+    "records": 21.908e6 + 1.936e6 + 86.726e6 + 106.363e6,            # count, partition scan, scatter
+    "join_weigh": 100.093e6 + 6.612e6 + 21.848e6 + 0.027e6 + 0.015e6,  # small, sorted, fallback joins
+    "list_sort": 24.988e6 + 27.434e6 + 14.251e6 + 0.350e6,            # the four sort classes
+    "expand": 83.423e6 + 198.956e6,
+}
 
 LEGS = ("peaks", "tile", "query", "e2e", "insert", "analytics", "lmax2", "batched", "serving", "cpu")
 EXTRA_LEGS = ("cpu_full",)  # run only when named in --legs
