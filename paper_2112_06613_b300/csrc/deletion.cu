@@ -1568,8 +1568,25 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
             TCR_CUDA(cudaMemcpyAsync(&rb->pack_error, d_pack_flags, sizeof(unsigned long long),
                                      cudaMemcpyDeviceToHost, s));
     }
+    // int32 row offsets for the handle, allocated and narrowed on the second
+    // stream while the host waits for the readback (dropped below if nnz turns
+    // out to need int64 offsets)
+    // (allocated on the stream that writes it, so that freeing it on any
+    // early return is ordered after the narrowing)
+    DevBuf off32;
+    if (!force_off64 && n + 1 <= 0x7fffffffLL) {
+        cudaStream_t ns = s;
+        if (side) {
+            TCR_CUDA(cudaEventRecord(side->ev[6], s));
+            TCR_CUDA(cudaStreamWaitEvent(side->stream, side->ev[6], 0));
+            ns = side->stream;
+        }
+        TCR_CHECK(off32.alloc_owned(sizeof(int32_t) * (n + 1), ns));
+        TCR_CHECK(narrow_offsets(off64.as<int64_t>(), off32.as<int32_t>(), n + 1, ns));
+    }
     TCR_CUDA(cudaStreamSynchronize(s));
     TCR_CHECK(pack_flags_status(rb->pack_error, &out.bad_index));
+    if (off32.as<void>() && rb->sizes[1] > 0x7fffffffLL) off32.reset();  // int64 offsets after all
     unsigned long long segs[kEdgeSegs + 1];
     for (int g = 0; g <= kEdgeSegs; ++g) segs[g] = rb->segs[g];
     const int h_dmax = rb->dmax;
@@ -1589,18 +1606,12 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     int n_two_pass = 0;
     DevBuf Sbuf;
     TCR_CHECK(Sbuf.alloc(sizeof(int32_t) * SD, s));
-    // int32 row offsets for the handle
-    DevBuf off32;
-    if (!force_off64 && nnz <= 0x7fffffffLL) TCR_CHECK(off32.alloc_owned(sizeof(int32_t) * (n + 1), s));
     // a build handle keeps the edges between distinct strings (analytics run on
-    // that graph of U nodes instead of the n-node network); allocated before
-    // the fork so the side stream may write it
+    // that graph of U nodes instead of the n-node network)
     DevBuf uedges;
     const bool keep_edges = keep_index && (join || cand2) && E > 0;
-    if (keep_edges) TCR_CHECK(uedges.alloc_owned(sizeof(int2) * E, s));
-    // each list's own members (after its member list exists), the narrowed
-    // offsets and the kept edges go to the side stream, next to the neighbour
-    // appends on this one
+    // each list's own members (after its member list exists) and the kept
+    // edges go to the side stream, next to the neighbour appends on this one
     cudaStream_t fs = s;
     if (side) {
         TCR_CUDA(cudaEventRecord(side->ev[2], s));
@@ -1611,18 +1622,25 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     k_closed_self<<<grid_for(n), kThreads, 0, fs>>>(uid.as<int32_t>(), mpos.as<int32_t>(), n, uoff.as<int64_t>(),
                                                     Sbuf.as<int32_t>());
     TCR_LAUNCH_CHECK();
-    if (off32.as<void>()) TCR_CHECK(narrow_offsets(off64.as<int64_t>(), off32.as<int32_t>(), n + 1, fs));
-    if (keep_edges && cand2) {  // already one contiguous list
-        TCR_CUDA(cudaMemcpyAsync(uedges.as<void>(), edges.as<void>(), sizeof(int2) * E, cudaMemcpyDeviceToDevice, fs));
-    } else if (keep_edges && !overflow) {  // the one-pass buffer holds every edge: segments to one array
-        SegBases sb;
-        sb.base[0] = 0;
-        for (int g = 0; g < kEdgeSegs; ++g) sb.base[g + 1] = sb.base[g] + (int64_t)segs[g];
-        const dim3 cgrid(grid_for(std::max<int64_t>(seg_max, 1)), (unsigned)kEdgeSegs);
-        k_compact_edges<<<cgrid, kThreads, 0, fs>>>(edges.as<int2>(), seg_cap, sb, uedges.as<int2>());
-        TCR_LAUNCH_CHECK();
-    }
-    if (side) TCR_CUDA(cudaEventRecord(side->ev[3], fs));
+    // the kept edges of the usual cases are allocated and gathered after the
+    // neighbour appends are launched, so the allocation's host time overlaps them
+    const bool late_edges = keep_edges && (cand2 || !overflow);
+    auto gather_edges = [&]() -> tcrnet_status {
+        TCR_CHECK(uedges.alloc_owned(sizeof(int2) * E, fs));  // stream-ordered on the stream that fills it
+        if (cand2) {  // already one contiguous list
+            TCR_CUDA(cudaMemcpyAsync(uedges.as<void>(), edges.as<void>(), sizeof(int2) * E, cudaMemcpyDeviceToDevice,
+                                     fs));
+        } else {  // the one-pass buffer holds every edge: segments to one array
+            SegBases sb;
+            sb.base[0] = 0;
+            for (int g = 0; g < kEdgeSegs; ++g) sb.base[g + 1] = sb.base[g] + (int64_t)segs[g];
+            const dim3 cgrid(grid_for(std::max<int64_t>(seg_max, 1)), (unsigned)kEdgeSegs);
+            k_compact_edges<<<cgrid, kThreads, 0, fs>>>(edges.as<int2>(), seg_cap, sb, uedges.as<int2>());
+            TCR_LAUNCH_CHECK();
+        }
+        return TCRNET_OK;
+    };
+    if (keep_edges && !late_edges) TCR_CHECK(uedges.alloc_owned(sizeof(int2) * E, s));
     // ---- 3b. edges that did not fit: second join pass at scanned positions;
     // then append neighbour member lists
     int64_t fill_segs = kEdgeSegs, fill_cap = seg_cap;
@@ -1670,7 +1688,11 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
                                                             Sbuf.as<int32_t>(), d_err + 1);
         TCR_LAUNCH_CHECK();
     }
-    if (side) TCR_CUDA(cudaStreamWaitEvent(s, side->ev[3], 0));  // own members and offsets written
+    if (late_edges) TCR_CHECK(gather_edges());
+    if (side) {  // own members, narrowed offsets and kept edges written
+        TCR_CUDA(cudaEventRecord(side->ev[3], fs));
+        TCR_CUDA(cudaStreamWaitEvent(s, side->ev[3], 0));
+    }
     const int t4 = tm.mark();
     if (!keep_index) recs.reset();
     edges.reset();
