@@ -83,7 +83,7 @@ PHASE_TRAFFIC_N800000 = {
 }
 
 LEGS = ("peaks", "tile", "query", "e2e", "insert", "analytics", "lmax2", "batched", "serving", "cpu")
-EXTRA_LEGS = ("cpu_full",)  # run only when named in --legs
+EXTRA_LEGS = ("cpu_full", "n8e6")  # run only when named in --legs
 
 
 def parse_args():
@@ -343,6 +343,40 @@ def cpu_full_leg():
                             "threads": threads or out["cores"], "s": el, "extrapolated_build_s": build_s,
                             "candidate_pairs_per_s": cand / build_s, "all_pairs_per_s": n * (n - 1) / 2 / build_s})
     return out
+
+
+def large_leg(tn, torch, dev, stream, flush, steps=5):
+    """Config 3 (N = 8,000,000, insertion 0-9 aa, lengths 8-24, int64 CSR offsets):
+    builds by the default method from device inputs, CUDA events, L2 flushed."""
+    from synthgen import generate_config3
+
+    rep = generate_config3(8_000_000, seed=0)
+    chars = torch.from_numpy(rep.chars).to(dev)
+    offs = torch.from_numpy(rep.offsets).to(dev)
+    tn.tcrnet_build_flat(chars, offs, 1, stream=stream).free()
+    ts, st = [], None
+    for k in range(steps):
+        flush.fill_(k & 0xff)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g = tn.tcrnet_build_flat(chars, offs, 1, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        st = g.stats()
+        g.free()
+        ts.append(a.elapsed_time(b))
+    g = tn.tcrnet_build_flat(chars, offs, 1, stream=stream, profile=True)
+    ph = g.stats()["ms_phase"]
+    g.free()
+    ms = statistics.mean(ts)
+    cand = candidate_pairs(rep.lengths())
+    names = ["dedup", "records", "join_weigh", "join_fill", "unused", "list_sort", "expand"]
+    return {"n": rep.n, "build_ms": ms, "build_ms_min": min(ts), "builds": steps, "nnz": st["nnz"],
+            "distinct_strings": st["n_unique"], "records": st["n_records"], "fallback_partitions": st["n_fallback"],
+            "candidate_pairs_per_s": cand / (ms / 1e3), "edges_per_s": st["nnz"] / 2 / (ms / 1e3),
+            "edge_write_gbs": 4 * st["nnz"] / (ph[6] / 1e3) / 1e9 if ph[6] > 0 else None,
+            "phases_ms": {nm: ph[i] for i, nm in enumerate(names) if nm != "unused"},
+            "timing": f"CUDA events, mean of {steps} after 1 warm-up, L2 flushed; phases from one profiled build"}
 
 
 def run_reference(args):
@@ -778,285 +812,323 @@ def run_ours(args):
     if rank == 0 and not args.no_extras:
         peaks = None
         if "peaks" in legs:
-            # --- integer-issue rates of this device (the tile roofline's denominator)
-            peaks = peaks_leg(tn, torch, dev, stream, torch.cuda.get_device_properties(dev).multi_processor_count)
-            line["peaks"] = peaks
+            try:
+                # --- integer-issue rates of this device (the tile roofline's denominator)
+                peaks = peaks_leg(tn, torch, dev, stream, torch.cuda.get_device_properties(dev).multi_processor_count)
+                line["peaks"] = peaks
+            except Exception as exc:  # keep the line: record the failed leg
+                line.setdefault("leg_errors", {})["peaks"] = repr(exc)
         if "tile" in legs:
-            # --- tile kernel: candidate pair tests per second vs the integer-issue roofline
-            lens = rep.lengths()
-            ops, pairs = tile_alg_ops(lens)
-            tstats = []
-            build(method="tile").free()
-            for _ in range(args.tile_steps):
-                flush.fill_(1)
-                g = build(method="tile")
-                tstats.append(g.stats())
-                g.free()
-            cnt_ms = statistics.mean(s["ms_count"] for s in tstats)
-            tot_ms = statistics.mean(s["ms_total"] for s in tstats)
-            cand = tstats[0]["candidate_pairs"]
-            clk = (clocks or {}).get("sm_mhz") or sm_max_nominal
-            nominal = SMS * INT_LANES_PER_SM * sm_max_nominal * 1e6
-            ach_ops = ops / (cnt_ms / 1e3)
-            if peaks:  # the measured issue ceiling of this device
-                peak_ops = peaks["issue_ceiling_tops"] * 1e12
-                basis = (f"measured by the peaks leg: fastest instruction mix, "
-                         f"{peaks['issue_ceiling_lanes_per_clk_per_sm']:.1f} lanes/clk/SM at {peaks['sm_mhz']:.0f} MHz")
-            else:
-                peak_ops = nominal
-                basis = f"nominal: {SMS} SMs x {INT_LANES_PER_SM} int32 issue lanes x {sm_max_nominal:.0f} MHz"
-            line["tile"] = {
-                "candidate_pairs": cand, "count_pass_ms": cnt_ms, "build_ms": tot_ms,
-                "candidate_pairs_per_s": cand / (cnt_ms / 1e3),
-                "all_pairs_per_s_build": pairs_per_build / (tot_ms / 1e3),
-                "roofline": {"bound": "alu", "achieved": ach_ops / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-                             "frac": ach_ops / peak_ops, "frac_of_nominal_issue": ach_ops / nominal,
-                             "ops_per_launch": ops, "peak_basis": basis,
-                             "ops_basis": f"{OPS_SAME_PER_WORD} per same-length and {OPS_INDEL_PER_WORD} per "
-                                          f"(L, L+1) candidate pair per 128-bit word pair (minimal test)",
-                             "sampled_sm_mhz": clk},
-            }
+            try:
+                # --- tile kernel: candidate pair tests per second vs the integer-issue roofline
+                lens = rep.lengths()
+                ops, pairs = tile_alg_ops(lens)
+                tstats = []
+                build(method="tile").free()
+                for _ in range(args.tile_steps):
+                    flush.fill_(1)
+                    g = build(method="tile")
+                    tstats.append(g.stats())
+                    g.free()
+                cnt_ms = statistics.mean(s["ms_count"] for s in tstats)
+                tot_ms = statistics.mean(s["ms_total"] for s in tstats)
+                cand = tstats[0]["candidate_pairs"]
+                clk = (clocks or {}).get("sm_mhz") or sm_max_nominal
+                nominal = SMS * INT_LANES_PER_SM * sm_max_nominal * 1e6
+                ach_ops = ops / (cnt_ms / 1e3)
+                if peaks:  # the measured issue ceiling of this device
+                    peak_ops = peaks["issue_ceiling_tops"] * 1e12
+                    basis = (f"measured by the peaks leg: fastest instruction mix, "
+                             f"{peaks['issue_ceiling_lanes_per_clk_per_sm']:.1f} lanes/clk/SM at {peaks['sm_mhz']:.0f} MHz")
+                else:
+                    peak_ops = nominal
+                    basis = f"nominal: {SMS} SMs x {INT_LANES_PER_SM} int32 issue lanes x {sm_max_nominal:.0f} MHz"
+                line["tile"] = {
+                    "candidate_pairs": cand, "count_pass_ms": cnt_ms, "build_ms": tot_ms,
+                    "candidate_pairs_per_s": cand / (cnt_ms / 1e3),
+                    "all_pairs_per_s_build": pairs_per_build / (tot_ms / 1e3),
+                    "roofline": {"bound": "alu", "achieved": ach_ops / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+                                 "frac": ach_ops / peak_ops, "frac_of_nominal_issue": ach_ops / nominal,
+                                 "ops_per_launch": ops, "peak_basis": basis,
+                                 "ops_basis": f"{OPS_SAME_PER_WORD} per same-length and {OPS_INDEL_PER_WORD} per "
+                                              f"(L, L+1) candidate pair per 128-bit word pair (minimal test)",
+                                 "sampled_sm_mhz": clk},
+                }
+            except Exception as exc:  # keep the line: record the failed leg
+                line.setdefault("leg_errors", {})["tile"] = repr(exc)
         if "query" in legs:
-            # --- queries against the resident repertoire (host in, host out)
-            from synthgen import generate
+            try:
+                # --- queries against the resident repertoire (host in, host out)
+                from synthgen import generate
 
-            # queries drawn from the resident repertoire's model (same templates)
-            qsrc = generate(200_000, seed=1000 + rank, template_seed=rank, ins_max=6, len_lo=10, len_hi=20)
-            qstr_off = qsrc.offsets
-            rng = np.random.default_rng(7)
-            resident = build(profile=False)
-            lat, qn = [], []
-            for b in range(args.query_batches + 2):
-                m = int(round(math.exp(rng.uniform(0, math.log(50_000)))))
-                start = int(rng.integers(0, qsrc.n - m))
-                qo = (qstr_off[start:start + m + 1] - qstr_off[start]).astype(np.int64)
-                qc = qsrc.chars[qstr_off[start]:qstr_off[start + m]]
-                t = time.perf_counter()
-                r = resident.query_flat(qc, qo)
-                r.copy_csr()
-                dt = time.perf_counter() - t
-                r.free()
-                if b >= 2:
-                    lat.append(dt * 1e3)
-                    qn.append(m)
-            resident.free()
-            line["query"] = {"batches": len(lat), "batch_size": "log-uniform 1..50000", "p50_ms": float(np.percentile(lat, 50)),
-                             "p99_ms": float(np.percentile(lat, 99)), "queries_per_s": sum(qn) / (sum(lat) / 1e3),
-                             "method": "deletion index of the resident build (probe of the query strings own records)"}
+                # queries drawn from the resident repertoire's model (same templates)
+                qsrc = generate(200_000, seed=1000 + rank, template_seed=rank, ins_max=6, len_lo=10, len_hi=20)
+                qstr_off = qsrc.offsets
+                rng = np.random.default_rng(7)
+                resident = build(profile=False)
+                lat, qn = [], []
+                for b in range(args.query_batches + 2):
+                    m = int(round(math.exp(rng.uniform(0, math.log(50_000)))))
+                    start = int(rng.integers(0, qsrc.n - m))
+                    qo = (qstr_off[start:start + m + 1] - qstr_off[start]).astype(np.int64)
+                    qc = qsrc.chars[qstr_off[start]:qstr_off[start + m]]
+                    t = time.perf_counter()
+                    r = resident.query_flat(qc, qo)
+                    r.copy_csr()
+                    dt = time.perf_counter() - t
+                    r.free()
+                    if b >= 2:
+                        lat.append(dt * 1e3)
+                        qn.append(m)
+                resident.free()
+                line["query"] = {"batches": len(lat), "batch_size": "log-uniform 1..50000", "p50_ms": float(np.percentile(lat, 50)),
+                                 "p99_ms": float(np.percentile(lat, 99)), "queries_per_s": sum(qn) / (sum(lat) / 1e3),
+                                 "method": "deletion index of the resident build (probe of the query strings own records)"}
+            except Exception as exc:  # keep the line: record the failed leg
+                line.setdefault("leg_errors", {})["query"] = repr(exc)
         if "e2e" in legs:
-            # --- end to end: pinned host inputs in, CSR back in pinned host memory
-            hc = torch.from_numpy(rep.chars).pin_memory()
-            ho = torch.from_numpy(rep.offsets).pin_memory()
-            off_h = torch.empty(n + 1, dtype=torch.int32).pin_memory()
-            cols_h = torch.empty(max(nnz, 1), dtype=torch.int32).pin_memory()
-            deg_h = torch.empty(n, dtype=torch.int32).pin_memory()
-            e2e_ms = []
-            for k in range(args.e2e_steps + 2):
-                flush.fill_(2)
+            try:
+                # --- end to end: pinned host inputs in, CSR back in pinned host memory
+                hc = torch.from_numpy(rep.chars).pin_memory()
+                ho = torch.from_numpy(rep.offsets).pin_memory()
+                off_h = torch.empty(n + 1, dtype=torch.int32).pin_memory()
+                cols_h = torch.empty(max(nnz, 1), dtype=torch.int32).pin_memory()
+                deg_h = torch.empty(n, dtype=torch.int32).pin_memory()
+                e2e_ms = []
+                for k in range(args.e2e_steps + 2):
+                    flush.fill_(2)
+                    torch.cuda.synchronize()
+                    t = time.perf_counter()
+                    g = tn.tcrnet_build_flat(hc, ho, 1, method=args.method, stream=stream)
+                    g.copy_csr(out=(off_h, cols_h, deg_h))
+                    torch.cuda.synchronize()
+                    dt = time.perf_counter() - t
+                    g.free()
+                    if k >= 2:
+                        e2e_ms.append(dt * 1e3)
+                e_ms = statistics.mean(e2e_ms)
+                # pipelined: three host threads, each with its own stream and pinned
+                # result buffers, run their steps back to back, so one step's
+                # copies overlap the others' builds (the link is full duplex);
+                # whole-job throughput = all steps / wall time
+                depth = 3
+                bufs = [(torch.cuda.Stream(), off_h, cols_h, deg_h)] + [
+                    (torch.cuda.Stream(), torch.empty(n + 1, dtype=torch.int32).pin_memory(),
+                     torch.empty(max(nnz, 1), dtype=torch.int32).pin_memory(),
+                     torch.empty(n, dtype=torch.int32).pin_memory()) for _ in range(depth - 1)]
+                per = max(4, args.e2e_steps // depth)
+                errors = []
+
+                def e2e_worker(k, steps):
+                    try:
+                        st_k, o_k, c_k, d_k = bufs[k]
+                        for _ in range(steps):
+                            gk = tn.tcrnet_build_flat(hc, ho, 1, method=args.method, stream=st_k)
+                            gk.copy_csr(out=(o_k, c_k, d_k))
+                            gk.free()
+                    except BaseException as exc:  # reported after the join
+                        errors.append(exc)
+
+                for k in range(depth):
+                    e2e_worker(k, 1)  # warm each stream's path
                 torch.cuda.synchronize()
                 t = time.perf_counter()
-                g = tn.tcrnet_build_flat(hc, ho, 1, method=args.method, stream=stream)
-                g.copy_csr(out=(off_h, cols_h, deg_h))
+                workers = [threading.Thread(target=e2e_worker, args=(k, per)) for k in range(depth)]
+                for w in workers:
+                    w.start()
+                for w in workers:
+                    w.join()
                 torch.cuda.synchronize()
-                dt = time.perf_counter() - t
-                g.free()
-                if k >= 2:
-                    e2e_ms.append(dt * 1e3)
-            e_ms = statistics.mean(e2e_ms)
-            # pipelined: three host threads, each with its own stream and pinned
-            # result buffers, run their steps back to back, so one step's
-            # copies overlap the others' builds (the link is full duplex);
-            # whole-job throughput = all steps / wall time
-            depth = 3
-            bufs = [(torch.cuda.Stream(), off_h, cols_h, deg_h)] + [
-                (torch.cuda.Stream(), torch.empty(n + 1, dtype=torch.int32).pin_memory(),
-                 torch.empty(max(nnz, 1), dtype=torch.int32).pin_memory(),
-                 torch.empty(n, dtype=torch.int32).pin_memory()) for _ in range(depth - 1)]
-            per = max(4, args.e2e_steps // depth)
-            errors = []
-
-            def e2e_worker(k, steps):
-                try:
-                    st_k, o_k, c_k, d_k = bufs[k]
-                    for _ in range(steps):
-                        gk = tn.tcrnet_build_flat(hc, ho, 1, method=args.method, stream=st_k)
-                        gk.copy_csr(out=(o_k, c_k, d_k))
-                        gk.free()
-                except BaseException as exc:  # reported after the join
-                    errors.append(exc)
-
-            for k in range(depth):
-                e2e_worker(k, 1)  # warm each stream's path
-            torch.cuda.synchronize()
-            t = time.perf_counter()
-            workers = [threading.Thread(target=e2e_worker, args=(k, per)) for k in range(depth)]
-            for w in workers:
-                w.start()
-            for w in workers:
-                w.join()
-            torch.cuda.synchronize()
-            p_ms = 1e3 * (time.perf_counter() - t) / (per * depth)
-            if errors:
-                raise errors[0]
-            line["e2e"] = {"value": cand_per_build / (p_ms / 1e3), "unit": UNIT, "ms_per_step": p_ms,
-                           "h2d_bytes_per_step": int(rep.chars.nbytes + rep.offsets.nbytes),
-                           "d2h_bytes_per_step": int(4 * (n + 1) + 4 * nnz + 4 * n),
-                           "pipeline": f"{depth} host threads with their own streams and pinned buffers, "
-                                       f"{per * depth} steps, each step's upload, build and CSR download included",
-                           "serial_ms_per_step": e_ms, "serial_value": cand_per_build / (e_ms / 1e3)}
+                p_ms = 1e3 * (time.perf_counter() - t) / (per * depth)
+                if errors:
+                    raise errors[0]
+                line["e2e"] = {"value": cand_per_build / (p_ms / 1e3), "unit": UNIT, "ms_per_step": p_ms,
+                               "h2d_bytes_per_step": int(rep.chars.nbytes + rep.offsets.nbytes),
+                               "d2h_bytes_per_step": int(4 * (n + 1) + 4 * nnz + 4 * n),
+                               "pipeline": f"{depth} host threads with their own streams and pinned buffers, "
+                                           f"{per * depth} steps, each step's upload, build and CSR download included",
+                               "serial_ms_per_step": e_ms, "serial_value": cand_per_build / (e_ms / 1e3)}
+            except Exception as exc:  # keep the line: record the failed leg
+                line.setdefault("leg_errors", {})["e2e"] = repr(exc)
         if "insert" in legs:
-            # --- inserts into the resident N = 8e5 network: merged (query + network
-            #     of the new strings, grown rows and index) vs rebuilt; copy-on-write
-            #     (tcrnet_extend), new strings in device memory
-            from synthgen import generate
+            try:
+                # --- inserts into the resident N = 8e5 network: merged (query + network
+                #     of the new strings, grown rows and index) vs rebuilt; copy-on-write
+                #     (tcrnet_extend), new strings in device memory
+                from synthgen import generate
 
-            # later draws of the same repertoire model (same templates): the new
-            # strings join the resident network
-            ipool = generate(100_000, seed=2000 + rank, template_seed=rank, ins_max=6, len_lo=10, len_hi=20)
-            ic = torch.from_numpy(ipool.chars).to(dev)
-            io = torch.from_numpy(ipool.offsets).to(dev)
-            ins = {}
-            with build() as g:
-                for m_ins in [int(x) for x in args.insert_sizes.split(",") if x]:
-                    row = {}
-                    for mode, rebuild in (("merged", False), ("rebuilt", True)):
-                        ts = []
-                        for k in range(4):
-                            torch.cuda.synchronize()
-                            t = time.perf_counter()
-                            g2 = g.extend_flat(ic, io[:m_ins + 1], stream=stream, rebuild=rebuild)
-                            torch.cuda.synchronize()
-                            dt = 1e3 * (time.perf_counter() - t)
-                            if k == 0:
-                                st2 = g2.stats()
-                            g2.free()
-                            if k >= 1:
-                                ts.append(dt)
-                        row[f"{mode}_ms"] = statistics.median(ts)
-                        if mode == "merged":
-                            row["merged"] = st2["merged_inserts"] == 1
-                            row["nnz_after"] = st2["nnz"]
-                    row["speedup"] = row["rebuilt_ms"] / row["merged_ms"]
-                    ins[str(m_ins)] = row
-            line["insert"] = {"resident_strings": n, "sizes": ins,
-                              "timing": "host time of tcrnet_extend (copy-on-write insert) with a stream sync, median of 3 "
-                                        "after 1 warm-up; new strings already in device memory"}
+                # later draws of the same repertoire model (same templates): the new
+                # strings join the resident network
+                ipool = generate(100_000, seed=2000 + rank, template_seed=rank, ins_max=6, len_lo=10, len_hi=20)
+                ic = torch.from_numpy(ipool.chars).to(dev)
+                io = torch.from_numpy(ipool.offsets).to(dev)
+                ins = {}
+                with build() as g:
+                    for m_ins in [int(x) for x in args.insert_sizes.split(",") if x]:
+                        row = {}
+                        for mode, rebuild in (("merged", False), ("rebuilt", True)):
+                            ts = []
+                            for k in range(4):
+                                torch.cuda.synchronize()
+                                t = time.perf_counter()
+                                g2 = g.extend_flat(ic, io[:m_ins + 1], stream=stream, rebuild=rebuild)
+                                torch.cuda.synchronize()
+                                dt = 1e3 * (time.perf_counter() - t)
+                                if k == 0:
+                                    st2 = g2.stats()
+                                g2.free()
+                                if k >= 1:
+                                    ts.append(dt)
+                            row[f"{mode}_ms"] = statistics.median(ts)
+                            if mode == "merged":
+                                row["merged"] = st2["merged_inserts"] == 1
+                                row["nnz_after"] = st2["nnz"]
+                        row["speedup"] = row["rebuilt_ms"] / row["merged_ms"]
+                        ins[str(m_ins)] = row
+                line["insert"] = {"resident_strings": n, "sizes": ins,
+                                  "timing": "host time of tcrnet_extend (copy-on-write insert) with a stream sync, median of 3 "
+                                            "after 1 warm-up; new strings already in device memory"}
+            except Exception as exc:  # keep the line: record the failed leg
+                line.setdefault("leg_errors", {})["insert"] = repr(exc)
         if "analytics" in legs:
-            # --- analytics on the N = 8e5 network: LCC under random node removal
-            #     (normalisations of Methods "Computing LCC"), average neighbour degree
-            with build() as g:
-                ps = [0.0, 0.01, 0.1, 0.3, 0.49, 0.7, 0.89, 0.95, 0.98]
-                rng = np.random.default_rng(2024)
-                curve, t_cc = [], []
-                lcc0 = None
-                for p in ps:
-                    keep = (rng.random(n) >= p).astype(np.uint8)
-                    kt = torch.from_numpy(keep).to(dev)
-                    torch.cuda.synchronize()
-                    t = time.perf_counter()
-                    _, nc, lcc = _components_device(g, kt, tn)
-                    t_cc.append(1e3 * (time.perf_counter() - t))
-                    lcc0 = lcc if p == 0.0 else lcc0
-                    norm1 = lcc / ((1 - p) * n)
-                    curve.append({"p": p, "lcc": lcc, "components": nc, "lcc_norm1": norm1,
-                                  "lcc_norm2": norm1 / (lcc0 / n)})
-                knn_d = torch.empty(n, dtype=torch.float64, device=dev)
-                t_knn = []
-                for _ in range(5):  # output in device memory; host time of the call
-                    torch.cuda.synchronize()
-                    t = time.perf_counter()
-                    st = tn.load_library().tcrnet_neighbor_degree(g.handle, knn_d.data_ptr(), tn.DEVICE)
-                    t_knn.append(1e3 * (time.perf_counter() - t))
-                    if st != tn.OK:
-                        raise tn.TcrnetError(st, "tcrnet_neighbor_degree")
-            line["analytics"] = {"lcc_under_removal": curve, "components_ms_median": statistics.median(t_cc),
-                                 "neighbor_degree_ms": statistics.median(t_knn),
-                                 "mean_neighbor_degree": float(knn_d.mean().item()),
-                                 "timing": "host time of each call, removal masks and outputs in device memory; "
-                                           "deletion builds run on the graph of distinct strings"}
+            try:
+                # --- analytics on the N = 8e5 network: LCC under random node removal
+                #     (normalisations of Methods "Computing LCC"), average neighbour degree
+                with build() as g:
+                    ps = [0.0, 0.01, 0.1, 0.3, 0.49, 0.7, 0.89, 0.95, 0.98]
+                    rng = np.random.default_rng(2024)
+                    curve, t_cc = [], []
+                    lcc0 = None
+                    for p in ps:
+                        keep = (rng.random(n) >= p).astype(np.uint8)
+                        kt = torch.from_numpy(keep).to(dev)
+                        torch.cuda.synchronize()
+                        t = time.perf_counter()
+                        _, nc, lcc = _components_device(g, kt, tn)
+                        t_cc.append(1e3 * (time.perf_counter() - t))
+                        lcc0 = lcc if p == 0.0 else lcc0
+                        norm1 = lcc / ((1 - p) * n)
+                        curve.append({"p": p, "lcc": lcc, "components": nc, "lcc_norm1": norm1,
+                                      "lcc_norm2": norm1 / (lcc0 / n)})
+                    knn_d = torch.empty(n, dtype=torch.float64, device=dev)
+                    t_knn = []
+                    for _ in range(5):  # output in device memory; host time of the call
+                        torch.cuda.synchronize()
+                        t = time.perf_counter()
+                        st = tn.load_library().tcrnet_neighbor_degree(g.handle, knn_d.data_ptr(), tn.DEVICE)
+                        t_knn.append(1e3 * (time.perf_counter() - t))
+                        if st != tn.OK:
+                            raise tn.TcrnetError(st, "tcrnet_neighbor_degree")
+                line["analytics"] = {"lcc_under_removal": curve, "components_ms_median": statistics.median(t_cc),
+                                     "neighbor_degree_ms": statistics.median(t_knn),
+                                     "mean_neighbor_degree": float(knn_d.mean().item()),
+                                     "timing": "host time of each call, removal masks and outputs in device memory; "
+                                               "deletion builds run on the graph of distinct strings"}
+            except Exception as exc:  # keep the line: record the failed leg
+                line.setdefault("leg_errors", {})["analytics"] = repr(exc)
         if "lmax2" in legs:
-            # --- l_max = 2: the paper's assortativity setting of 4 x 8,000 sequences,
-            #     and N = 1e5, by the default method (deletion candidates + exact
-            #     distance) and by the all-pairs bit-parallel distance kernel
-            from synthgen import generate_config1
+            try:
+                # --- l_max = 2: the paper's assortativity setting of 4 x 8,000 sequences,
+                #     and N = 1e5, by the default method (deletion candidates + exact
+                #     distance) and by the all-pairs bit-parallel distance kernel
+                from synthgen import generate_config1
 
-            lm2 = {}
-            peak = peaks["issue_ceiling_tops"] * 1e12 if peaks else SMS * INT_LANES_PER_SM * sm_max_nominal * 1e6
-            for n2 in (32_000, 100_000):
-                r2 = generate_config1(n2, seed=7)
-                c2 = torch.from_numpy(r2.chars).to(dev)
-                o2 = torch.from_numpy(r2.offsets).to(dev)
-                row = {}
-                for label, meth in (("default", "auto"), ("all_pairs", "tile")):
-                    tn.tcrnet_build_flat(c2, o2, 2, method=meth, stream=stream).free()
-                    ts = []
-                    for _ in range(3):
-                        a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                        a2.record(stream)
-                        g2 = tn.tcrnet_build_flat(c2, o2, 2, method=meth, stream=stream)
-                        b2.record(stream)
-                        b2.synchronize()
-                        st2 = g2.stats()
-                        g2.free()
-                        ts.append(a2.elapsed_time(b2))
-                    ms2 = statistics.median(ts)
-                    entry = {"build_ms": ms2, "method": {1: "tile", 2: "deletion"}.get(st2["method"], "?"),
-                             "nnz": st2["nnz"], "all_pairs_per_s": n2 * (n2 - 1) / 2 / (ms2 / 1e3)}
-                    if st2["method"] == tn.METHOD_DELETION:
-                        entry["candidates_checked"] = st2["candidate_pairs"]
-                        entry["variant_records"] = st2["n_records"]
-                    else:
-                        # per candidate pair the recurrence runs one step per letter of
-                        # the row string, 17 integer operations per step (an estimate
-                        # from the mean length), against the issue ceiling
-                        g3 = tn.tcrnet_build_flat(c2, o2, 2, method=meth, stream=stream, profile=True)
-                        st3 = g3.stats()
-                        g3.free()
-                        mean_len = float(np.diff(r2.offsets).mean())
-                        ach = st3["candidate_pairs"] * mean_len * 17.0 / (st3["ms_count"] / 1e3)
-                        entry.update({"candidate_pairs": st3["candidate_pairs"], "count_pass_ms": st3["ms_count"],
-                                      "roofline": {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12,
-                                                   "unit": "Tops/s", "frac": ach / peak,
-                                                   "ops_per_pair": f"17 x mean length ({mean_len:.2f}), estimate"}})
-                    row[label] = entry
-                if n2 == 100_000:
-                    # queries against the l_max = 2 build: its variant-record index
-                    # vs the all-pairs kernel, 1,000 strings of the resident model
-                    from synthgen import generate as _gen
+                lm2 = {}
+                peak = peaks["issue_ceiling_tops"] * 1e12 if peaks else SMS * INT_LANES_PER_SM * sm_max_nominal * 1e6
+                for n2 in (32_000, 100_000):
+                    r2 = generate_config1(n2, seed=7)
+                    c2 = torch.from_numpy(r2.chars).to(dev)
+                    o2 = torch.from_numpy(r2.offsets).to(dev)
+                    row = {}
+                    for label, meth in (("default", "auto"), ("all_pairs", "tile")):
+                        tn.tcrnet_build_flat(c2, o2, 2, method=meth, stream=stream).free()
+                        ts = []
+                        for _ in range(3):
+                            a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                            a2.record(stream)
+                            g2 = tn.tcrnet_build_flat(c2, o2, 2, method=meth, stream=stream)
+                            b2.record(stream)
+                            b2.synchronize()
+                            st2 = g2.stats()
+                            g2.free()
+                            ts.append(a2.elapsed_time(b2))
+                        ms2 = statistics.median(ts)
+                        entry = {"build_ms": ms2, "method": {1: "tile", 2: "deletion"}.get(st2["method"], "?"),
+                                 "nnz": st2["nnz"], "all_pairs_per_s": n2 * (n2 - 1) / 2 / (ms2 / 1e3)}
+                        if st2["method"] == tn.METHOD_DELETION:
+                            entry["candidates_checked"] = st2["candidate_pairs"]
+                            entry["variant_records"] = st2["n_records"]
+                        else:
+                            # per candidate pair the recurrence runs one step per letter of
+                            # the row string, 17 integer operations per step (an estimate
+                            # from the mean length), against the issue ceiling
+                            g3 = tn.tcrnet_build_flat(c2, o2, 2, method=meth, stream=stream, profile=True)
+                            st3 = g3.stats()
+                            g3.free()
+                            mean_len = float(np.diff(r2.offsets).mean())
+                            ach = st3["candidate_pairs"] * mean_len * 17.0 / (st3["ms_count"] / 1e3)
+                            entry.update({"candidate_pairs": st3["candidate_pairs"], "count_pass_ms": st3["ms_count"],
+                                          "roofline": {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12,
+                                                       "unit": "Tops/s", "frac": ach / peak,
+                                                       "ops_per_pair": f"17 x mean length ({mean_len:.2f}), estimate"}})
+                        row[label] = entry
+                    if n2 == 100_000:
+                        # queries against the l_max = 2 build: its variant-record index
+                        # vs the all-pairs kernel, 1,000 strings of the resident model
+                        from synthgen import generate as _gen
 
-                    q2 = _gen(1000, seed=2024, template_seed=7, ins_max=6, len_lo=10, len_hi=20)
-                    qc2 = torch.from_numpy(q2.chars).to(dev)
-                    qo2 = torch.from_numpy(q2.offsets).to(dev)
-                    qrow = {}
-                    with tn.tcrnet_build_flat(c2, o2, 2, stream=stream) as g2:
-                        for qlabel, qm in (("index", "deletion"), ("all_pairs", "tile")):
-                            g2.query_flat(qc2, qo2, method=qm, stream=stream).free()
-                            qts = []
-                            for _ in range(5):
-                                t0 = time.perf_counter()
-                                rq = g2.query_flat(qc2, qo2, method=qm, stream=stream)
-                                qts.append((time.perf_counter() - t0) * 1e3)
-                                qn = rq.info()[1]
-                                rq.free()
-                            qrow[qlabel] = {"ms": statistics.median(qts), "answers": qn}
-                    qrow["timing"] = "host time of tcrnet_query_ex with its stream sync, median of 5; queries in device memory"
-                    row["query_1000"] = qrow
-                lm2[str(n2)] = row
-            line["lmax2"] = lm2
+                        q2 = _gen(1000, seed=2024, template_seed=7, ins_max=6, len_lo=10, len_hi=20)
+                        qc2 = torch.from_numpy(q2.chars).to(dev)
+                        qo2 = torch.from_numpy(q2.offsets).to(dev)
+                        qrow = {}
+                        with tn.tcrnet_build_flat(c2, o2, 2, stream=stream) as g2:
+                            for qlabel, qm in (("index", "deletion"), ("all_pairs", "tile")):
+                                g2.query_flat(qc2, qo2, method=qm, stream=stream).free()
+                                qts = []
+                                for _ in range(5):
+                                    t0 = time.perf_counter()
+                                    rq = g2.query_flat(qc2, qo2, method=qm, stream=stream)
+                                    qts.append((time.perf_counter() - t0) * 1e3)
+                                    qn = rq.info()[1]
+                                    rq.free()
+                                qrow[qlabel] = {"ms": statistics.median(qts), "answers": qn}
+                        qrow["timing"] = "host time of tcrnet_query_ex with its stream sync, median of 5; queries in device memory"
+                        row["query_1000"] = qrow
+                    lm2[str(n2)] = row
+                line["lmax2"] = lm2
+            except Exception as exc:  # keep the line: record the failed leg
+                line.setdefault("leg_errors", {})["lmax2"] = repr(exc)
         if "batched" in legs:
-            # --- batched: uneven repertoires in one pass vs one plain build each
-            if args.batched_reps > 0:
-                line["batched"] = batched_leg(args, tn, torch, stream, flush)
+            try:
+                # --- batched: uneven repertoires in one pass vs one plain build each
+                if args.batched_reps > 0:
+                    line["batched"] = batched_leg(args, tn, torch, stream, flush)
+            except Exception as exc:  # keep the line: record the failed leg
+                line.setdefault("leg_errors", {})["batched"] = repr(exc)
         if "serving" in legs:
-            # --- serving: resident repertoire, Poisson queries and inserts
-            if args.serve_seconds > 0:
-                line["serving"] = serve_leg(args, tn, torch, stream)
+            try:
+                # --- serving: resident repertoire, Poisson queries and inserts
+                if args.serve_seconds > 0:
+                    line["serving"] = serve_leg(args, tn, torch, stream)
+            except Exception as exc:  # keep the line: record the failed leg
+                line.setdefault("leg_errors", {})["serving"] = repr(exc)
         if "cpu" in legs:
-            # --- CPU oracle and the paper's algorithm on bounded samples (rank 0, one GPU only)
-            if world == 1 and args.cpu_seconds > 0:
-                line["cpu_baseline"] = cpu_leg(rep, args.cpu_seconds)
+            try:
+                # --- CPU oracle and the paper's algorithm on bounded samples (rank 0, one GPU only)
+                if world == 1 and args.cpu_seconds > 0:
+                    line["cpu_baseline"] = cpu_leg(rep, args.cpu_seconds)
+            except Exception as exc:  # keep the line: record the failed leg
+                line.setdefault("leg_errors", {})["cpu"] = repr(exc)
+        if "n8e6" in legs:
+            try:
+                line["n8e6"] = large_leg(tn, torch, dev, stream, flush)
+            except Exception as exc:  # keep the line: record the failed leg
+                line.setdefault("leg_errors", {})["n8e6"] = repr(exc)
         if "cpu_full" in legs and world == 1:
-            line["cpu_full"] = cpu_full_leg()
+            try:
+                line["cpu_full"] = cpu_full_leg()
+            except Exception as exc:  # keep the line: record the failed leg
+                line.setdefault("leg_errors", {})["cpu_full"] = repr(exc)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
