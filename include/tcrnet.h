@@ -88,9 +88,9 @@ typedef struct tcrnet_options {
     void *stream;             /* cudaStream_t; NULL = legacy default stream */
     int32_t profile;          /* 1: record per-phase CUDA-event times (tcrnet_stats) */
     int32_t partition_cap;    /* testing: deletion-join partitions larger than this
-                                 take the exact quadratic fallback; 0 = default */
+                                 take the quadratic join pass; 0 = default */
     int32_t partition_target; /* tuning: mean records per deletion-join partition,
-                                 4 .. 128; 0 = default (24 up to 2^25 records,
+                                 4 .. 128; 0 = default (12 up to 2^25 records,
                                  else 32). Any value gives the same network. */
     int32_t fail_alloc_at;    /* testing (host-side fault injection): the k-th device
                                  allocation of this call fails and the call returns
@@ -110,7 +110,14 @@ typedef struct tcrnet_options {
                                  0 = default (TCRNET_DELETION_MAX_N). AUTO builds
                                  larger repertoires with the tile method; an explicit
                                  TCRNET_METHOD_DELETION above it is TCRNET_ENOTSUP */
-    int32_t reserved[2];      /* must be zero */
+    int32_t record_hash_bits; /* testing: the deletion join keeps only this many low
+                                 bits (1 .. 31) of each record's 32-bit content hash,
+                                 so that variants of different contents match and
+                                 the join's confirmation by content has candidates
+                                 to reject; such a build keeps no query index.
+                                 0 = default (all 32 bits). Any value gives the same
+                                 network. */
+    int32_t reserved[1];      /* must be zero */
 } tcrnet_options;
 
 /* Largest repertoire of the deletion method (distinct-string ids take 25 bits
@@ -133,7 +140,8 @@ typedef struct tcrnet_stats {
     int64_t n_unique;         /* distinct strings (deletion path) */
     int64_t n_records;        /* deletion-join records (deletion path) */
     int64_t unique_edges;     /* edges among distinct strings (deletion path) */
-    int64_t n_fallback;       /* deletion-join partitions joined by the exact fallback */
+    int64_t n_fallback;       /* deletion-join partitions over the warp capacity
+                                 (joined by the quadratic pass) */
     int64_t kernel_launches;  /* CUDA kernels this call launched */
     int64_t closed_total;     /* deletion path: sum over distinct strings of |closed neighbourhood| */
     int64_t two_pass_join;    /* deletion path: 1 if the edges overflowed the one-pass buffer */

@@ -47,7 +47,8 @@ class tcrnet_options(ctypes.Structure):
         ("insert_rebuild", ctypes.c_int32),
         ("link_attempts", ctypes.c_int32),
         ("deletion_max_n", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 2),
+        ("record_hash_bits", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 1),
     ]
 
 
@@ -207,7 +208,7 @@ def _stream_ptr(stream):
 
 def make_options(method="auto", device=None, stream=None, profile=False, force_offsets64=False,
                  partition_cap=0, partition_target=0, fail_alloc_at=0, insert_rebuild=False,
-                 link_attempts=0, deletion_max_n=0):
+                 link_attempts=0, deletion_max_n=0, record_hash_bits=0):
     lib = load_library()
     o = tcrnet_options()
     lib.tcrnet_options_init(ctypes.byref(o))
@@ -223,6 +224,7 @@ def make_options(method="auto", device=None, stream=None, profile=False, force_o
     o.insert_rebuild = 1 if insert_rebuild else 0
     o.link_attempts = int(link_attempts)
     o.deletion_max_n = int(deletion_max_n)
+    o.record_hash_bits = int(record_hash_bits)
     return o
 
 
@@ -433,12 +435,12 @@ def tcrnet_build(seqs, threshold: int = 1, method="auto", device=None, stream=No
 
 def tcrnet_build_flat(chars, offsets, threshold: int = 1, method="auto", device=None, stream=None,
                       profile=False, force_offsets64=False, partition_cap=0, partition_target=0,
-                      deletion_max_n=0) -> Graph:
+                      deletion_max_n=0, record_hash_bits=0) -> Graph:
     """Network of strings in flat layout (numpy arrays, or torch tensors on host or device)."""
     lib = load_library()
     cp, op, n, mem, keep = _flat_args(chars, offsets)
     opt = make_options(method, device, stream, profile, force_offsets64, partition_cap, partition_target,
-                       deletion_max_n=deletion_max_n)
+                       deletion_max_n=deletion_max_n, record_hash_bits=record_hash_bits)
     h = ctypes.c_void_p()
     st = lib.tcrnet_build_flat(cp, op, n, mem, int(threshold), ctypes.byref(opt), ctypes.byref(h))
     del keep

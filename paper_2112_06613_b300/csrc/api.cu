@@ -469,8 +469,11 @@ tcrnet_status build_from_packed(tcrnet_graph* h, Packed& pk, int64_t n, int32_t 
         if (st != TCRNET_OK) return st;
     } else {
         DeletionResult dr;
+        // (a build with truncated record hashes keeps its index for the
+        // analytics, not for queries: they hash their variants in full)
+        const int hash_bits = (opt.record_hash_bits > 0 && opt.record_hash_bits < 32) ? opt.record_hash_bits : 32;
         st = deletion_build(pk, T, dr, s, sms, opt.profile != 0, opt.partition_cap, keep_index,
-                            opt.partition_target, opt.force_offsets64 != 0);
+                            opt.partition_target, opt.force_offsets64 != 0, hash_bits);
         if (st != TCRNET_OK) {
             if (dr.bad_index >= 0) t_last_bad = dr.bad_index;  // the encoder's deferred error
             return st;
@@ -520,6 +523,7 @@ tcrnet_status build_impl(const uint8_t* chars, const int64_t* offsets, int64_t n
     if (opt.method < TCRNET_METHOD_AUTO || opt.method > TCRNET_METHOD_DELETION) return TCRNET_EINVAL;
     if (opt.partition_target != 0 && (opt.partition_target < 4 || opt.partition_target > 128)) return TCRNET_EINVAL;
     if (opt.link_attempts < 0 || opt.deletion_max_n < 0) return TCRNET_EINVAL;
+    if (opt.record_hash_bits < 0 || opt.record_hash_bits > 32) return TCRNET_EINVAL;
     if (T > 2 && opt.method == TCRNET_METHOD_DELETION) return TCRNET_ENOTSUP;  // deletion method: l_max <= 2
     if (opt.method == TCRNET_METHOD_DELETION && n > deletion_limit(opt)) return TCRNET_ENOTSUP;
     if (rep_off) {

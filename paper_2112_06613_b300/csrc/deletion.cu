@@ -30,19 +30,20 @@
 //       bits 24..0   u
 //     hash-partitioned (high hash bits, 24 or 32 records per partition on
 //     average) in two passes (count, scatter).
-//  3. join: a partition of at most 32 records is joined by one warp step
-//     without sorting (lane k holds record k; warp match on the hash gives
-//     each record its group, on (hash, p) its run); larger ones by a warp that
-//     sorts its words in registers (bitonic network). Either way equal hashes
-//     are confirmed to be equal contents (exact), and the edges between
-//     distinct strings are every pair inside a run of equal (hash, p) (equal
-//     length, one substitution) and each run-start deletion record with the
-//     full record of the same content (one indel). Partitions over capacity
-//     or with a hash collision take an exact quadratic fallback. The join adds
-//     m_v to W_u (and m_u to W_v) for every edge {u, v} and writes the edges
-//     into a buffer of 2 x (records bound) entries (staged per warp in shared
-//     memory); if they do not fit, a second pass writes them at positions
-//     scanned from the per-partition counts.
+//  3. join: windows of whole consecutive partitions with at most 32 records
+//     are joined by one warp step without sorting (lane k holds record k;
+//     warp match on the hash gives each record its group, on (hash, p) its
+//     run); partitions of 33..128 records by a warp that sorts its words in
+//     registers (bitonic network), larger ones by a quadratic block pass. The
+//     candidate pairs are every pair inside a run of equal (hash, p) (equal
+//     length, one substitution) and each run-start deletion record with each
+//     full record of its hash group (one indel); they go into a buffer of
+//     2 x (records bound) entries (staged per warp in shared memory) or, if
+//     they do not fit, a second pass writes them at positions scanned from
+//     the per-partition counts. A confirmation pass then compares the two
+//     contents of every candidate (exact: equal contents make equal hashes,
+//     so no edge is missed, and a hash collision is rejected there) and adds
+//     m_v to W_u (and m_u to W_v) for every edge {u, v}.
 //  4. closed neighbourhoods: D_u = m_u + W_u; S_u = M_u followed by every
 //     M_v (appended at a slot taken from a per-string cursor; long member
 //     lists are copied by a whole warp), written once per distinct string and
@@ -63,11 +64,13 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kWarpCap = 128;     // records per partition joined by one warp
-// Default mean records per partition. Fewer records per partition make more of
-// them fit one warp's match step (<= 32); more partitions make the counters of
-// the record scatter colder. Measured on one B300 (8e5 strings: 24 best, 1.47 vs
-// 1.50 ms at 32; 8.9e6 strings: 32 best, 14.5 vs 14.8 ms at 24).
-constexpr int kTargetPartSmall = 24;
+// Default mean records per partition. Fewer records per partition fill the
+// join's 32-lane windows better (a window ends at a partition boundary) and
+// send fewer partitions to the sorted join; more partitions make the counters
+// of the record scatter colder. Measured on one B300 at 8e5 strings (build
+// 0.827 ms at 12, 0.830 at 16, 0.837 at 8, 0.852 at 24); 8.9e6 strings: 32
+// (an earlier join; 14.5 vs 14.8 ms at 24).
+constexpr int kTargetPartSmall = 12;
 constexpr int kTargetPartLarge = 32;
 constexpr int64_t kTargetSwitchRecords = 1LL << 25;
 constexpr uint32_t kTagF = 63;    // position tag of a full-string record
@@ -96,12 +99,20 @@ __device__ __forceinline__ uint64_t fmix64(uint64_t x) {
 // x, so strings equal up to their tag would collide for 1 in 16 tag pairs.
 // The gathered 16-bit tag times an odd constant keeps its lowest set bit below
 // bit 16, so a pure tag difference can never cancel.
+constexpr uint64_t kHashMul1 = 0x9e3779b97f4a7c15ULL;
+constexpr uint64_t kHashMul2 = 0xc2b2ae3d27d4eb4fULL;
+constexpr uint64_t kHashMul3 = 0x165667b19e3779f9ULL;
+constexpr uint64_t kHashMulTag = 0xd6e8feb86659fd93ULL;
+constexpr uint64_t kHashSeed = 0x243f6a8885a308d3ULL;
+
+__device__ __forceinline__ uint64_t canon_tag(const Canon& c) {
+    return (c.w[0] >> 60) | ((c.w[1] >> 56) & 0xF0ull) | ((c.w[2] >> 52) & 0xF00ull) | ((c.w[3] >> 48) & 0xF000ull);
+}
+
 __device__ __forceinline__ uint64_t hash_canon(const Canon& c) {
-    const uint64_t tag = (c.w[0] >> 60) | ((c.w[1] >> 56) & 0xF0ull) | ((c.w[2] >> 52) & 0xF00ull) |
-                         ((c.w[3] >> 48) & 0xF000ull);
-    const uint64_t x = c.w[0] + 0x9e3779b97f4a7c15ULL * c.w[1] + 0xc2b2ae3d27d4eb4fULL * c.w[2] +
-                       0x165667b19e3779f9ULL * c.w[3] + 0xd6e8feb86659fd93ULL * tag;
-    return fmix64(x ^ 0x243f6a8885a308d3ULL);
+    const uint64_t x = c.w[0] + kHashMul1 * c.w[1] + kHashMul2 * c.w[2] + kHashMul3 * c.w[3] +
+                       kHashMulTag * canon_tag(c);
+    return fmix64(x ^ kHashSeed);
 }
 
 __device__ __forceinline__ bool canon_eq(const Canon& a, const Canon& b) {
@@ -136,6 +147,48 @@ __device__ __forceinline__ bool run_start(const Canon& c, int p) {
     return p == 0 || code_at(c, p) != code_at(c, p - 1);
 }
 
+// fn(p, h, rs) for the full string (p = -1) and for each deletion position p
+// of a string of L letters, with h = hash_canon(p < 0 ? c : delete_at(c, p))
+// and rs = run_start(c, p), at a fraction of the work of those calls: the word
+// combination inside the hash is linear, and deleting p keeps the words before
+// p's word, shifts every word after it down by one letter and mixes the two
+// forms inside p's word. So the sum over the kept prefix and the sum over the
+// shifted suffix are formed once per string; a variant adds its mixed word
+// (two logic operations, one multiply) and runs the finaliser.
+template <typename Fn>
+__device__ __forceinline__ void for_each_variant_hash(const Canon& c, int L, Fn fn) {
+    uint64_t down[kCanonWords];  // word w shifted down one letter, the next word's first letter on top
+#pragma unroll
+    for (int w = 0; w < kCanonWords; ++w) {
+        const uint64_t cw = c.w[w] & ~kTagBits;
+        const uint64_t next = (w + 1 < kCanonWords) ? (c.w[w + 1] & 31ull) : 0ull;
+        down[w] = (cw >> 5) | (next << 55) | (c.w[w] & kTagBits);
+    }
+    const uint64_t mul[kCanonWords] = {1ull, kHashMul1, kHashMul2, kHashMul3};
+    const uint64_t t = kHashMulTag * canon_tag(c);
+    fn(-1, fmix64((c.w[0] + kHashMul1 * c.w[1] + kHashMul2 * c.w[2] + kHashMul3 * c.w[3] + t) ^ kHashSeed), false);
+    uint64_t pre = 0;  // words before w as they are
+    uint64_t suf = kHashMul1 * down[1] + kHashMul2 * down[2] + kHashMul3 * down[3] + t;  // words after w, shifted
+    uint32_t prev = 32u;  // letter before the position (none before 0; codes are < 32)
+#pragma unroll
+    for (int w = 0; w < kCanonWords; ++w) {
+        const int p0 = w * kCodesPerWord;
+        const int pend = L < p0 + kCodesPerWord ? L : p0 + kCodesPerWord;
+        uint64_t low = 0;  // positions of the word before p
+        uint64_t cur = c.w[w];
+        for (int p = p0; p < pend; ++p) {
+            const uint32_t code = (uint32_t)cur & 31u;
+            cur >>= 5;
+            const uint64_t mixed = (c.w[w] & low) | (down[w] & ~low);
+            fn(p, fmix64((pre + mul[w] * mixed + suf) ^ kHashSeed), code != prev);
+            prev = code;
+            low = (low << 5) | 31ull;
+        }
+        pre += mul[w] * c.w[w];
+        if (w + 1 < kCanonWords) suf -= mul[w + 1] * down[w + 1];
+    }
+}
+
 __device__ __forceinline__ Canon record_content(uint64_t rec, const Canon* __restrict__ ucanon) {
     const Canon c = load_canon(ucanon + rec_u(rec));
     const uint32_t p = rec_p(rec);
@@ -144,6 +197,12 @@ __device__ __forceinline__ Canon record_content(uint64_t rec, const Canon* __res
 
 __device__ __forceinline__ uint32_t part_of(uint64_t h, uint32_t P) {
     return (uint32_t)(((h >> 32) * (uint64_t)P) >> 32);
+}
+
+// Blocks per edge segment of k_confirm (grid-stride loop; the candidate counts
+// are not known on the host when it is launched): about eight blocks per SM.
+inline unsigned confirm_blocks_x(int num_sms) {
+    return (unsigned)std::max(1, num_sms * 8 / kEdgeSegs);
 }
 
 inline unsigned grid_for(int64_t n, int threads = kThreads) {
@@ -258,47 +317,47 @@ template <bool SCATTER>
 __global__ void k_records(const Canon* __restrict__ ucanon, const uint8_t* __restrict__ ulen,
                           const int64_t* __restrict__ U_ptr, int64_t n, uint32_t P, int32_t* __restrict__ pcnt,
                           const int64_t* __restrict__ poff, uint64_t* __restrict__ recs, uint32_t u0 = 0,
-                          int64_t R_cap = INT64_MAX) {
+                          int64_t R_cap = INT64_MAX, uint64_t hash_mask = 0xffffffffull) {
     dep_entry();  // launched dependent on the kernel before it
     const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= n || u >= *U_ptr) return;
     if (SCATTER && poff[P] > R_cap) return;
     const Canon c = load_canon(ucanon + u);
     const int L = ulen[u];
+    const uint64_t uid = (uint64_t)(u0 + (uint32_t)u);  // ids of a slice start at u0
     if constexpr (!SCATTER) {
-        for (int p = -1; p < L; ++p) {
-            const uint64_t h = hash_canon(p < 0 ? c : delete_at(c, p));
-            atomicAdd(&pcnt[part_of(h, P)], 1);
-        }
+        for_each_variant_hash(c, L, [&](int, uint64_t h, bool) { atomicAdd(&pcnt[part_of(h, P)], 1); });
     } else {
-    // kRecBatch records at a time: their slot atomics and offset loads are
-    // independent, so they are in flight together rather than one round trip each
-    for (int p0 = -1; p0 < L; p0 += kRecBatch) {
-        uint64_t rec[kRecBatch];
-        uint32_t pid[kRecBatch];
-        int32_t slot[kRecBatch];
-        int64_t base[kRecBatch];
-#pragma unroll
-        for (int t = 0; t < kRecBatch; ++t) {
-            const int p = p0 + t;
-            const bool full = p < 0;
-            const uint64_t h = hash_canon(full ? c : delete_at(c, p < L ? p : 0));
-            pid[t] = part_of(h, P);
-            const uint64_t tag = full ? ((uint64_t)kTagF << 26)
-                                      : (((uint64_t)p << 26) | (run_start(c, p < L ? p : 0) ? (1ull << 25) : 0ull));
-            rec[t] = (h << 32) | tag | (uint64_t)(u0 + (uint32_t)u);  // ids of a slice start at u0
-        }
-#pragma unroll
-        for (int t = 0; t < kRecBatch; ++t) {
-            if (p0 + t < L) {
-                slot[t] = atomicAdd(&pcnt[pid[t]], 1);
-                base[t] = poff[pid[t]];
+        // kRecBatch records at a time (a shift register of pending ones): their
+        // slot atomics and offset loads are independent, so they are in flight
+        // together rather than one round trip each
+        uint64_t r0 = 0, r1 = 0, r2 = 0, r3 = 0;
+        uint32_t q0 = 0, q1 = 0, q2 = 0, q3 = 0;
+        int pending = 0;
+        auto issue = [&](int k) {  // the k newest pending records (k <= kRecBatch)
+            int32_t s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+            int64_t b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+            if (k > 0) { s0 = atomicAdd(&pcnt[q0], 1); b0 = poff[q0]; }
+            if (k > 1) { s1 = atomicAdd(&pcnt[q1], 1); b1 = poff[q1]; }
+            if (k > 2) { s2 = atomicAdd(&pcnt[q2], 1); b2 = poff[q2]; }
+            if (k > 3) { s3 = atomicAdd(&pcnt[q3], 1); b3 = poff[q3]; }
+            if (k > 0) recs[b0 + s0] = r0;
+            if (k > 1) recs[b1 + s1] = r1;
+            if (k > 2) recs[b2 + s2] = r2;
+            if (k > 3) recs[b3 + s3] = r3;
+        };
+        for_each_variant_hash(c, L, [&](int p, uint64_t h, bool rs) {
+            const uint64_t tag = p < 0 ? ((uint64_t)kTagF << 26) : (((uint64_t)p << 26) | (rs ? (1ull << 25) : 0ull));
+            r3 = r2; r2 = r1; r1 = r0;
+            q3 = q2; q2 = q1; q1 = q0;
+            r0 = ((h & hash_mask) << 32) | tag | uid;  // (hash_mask: testing, fewer hash bits kept)
+            q0 = part_of(h, P);
+            if (++pending == kRecBatch) {
+                issue(kRecBatch);
+                pending = 0;
             }
-        }
-#pragma unroll
-        for (int t = 0; t < kRecBatch; ++t)
-            if (p0 + t < L) recs[base[t] + slot[t]] = rec[t];
-    }
+        });
+        issue(pending);
     }
 }
 
@@ -353,31 +412,43 @@ __device__ __forceinline__ void load_sort_store(const uint64_t* __restrict__ src
     for (int r = 0; r < K; ++r) buf[lane * K + r] = v[r];
 }
 
-// Edges initiated by sorted record k (see the file comment); calls emit(a, b).
+// A candidate pair of the join, one side per int32: the distinct string u in
+// bits 24..0 and the variant of it that matched in bits 30..25 (the deleted
+// position p, or kTagF for the full string). k_confirm compares the two
+// variants' contents and rewrites the entry as the plain edge (u, v), or as
+// (-1, -1) when the 32-bit hashes matched by accident.
+__device__ __forceinline__ int32_t cand_side(uint64_t rec) {
+    return (int32_t)(rec_u(rec) | (rec_p(rec) << 25));
+}
+
+// Candidates initiated by sorted record k (see the file comment); calls
+// emit(a, b) with encoded sides. Same-position partners are the later records
+// of k's run of equal (hash, p); a run-start deletion pairs with every full
+// record of its hash group (these sort to the group's end; more than one only
+// under a hash collision, which the confirmation sorts out).
 template <typename Emit>
-__device__ __forceinline__ int64_t record_edges(const uint64_t* buf, int k, int s, int T, Emit emit) {
+__device__ __forceinline__ int64_t record_cands(const uint64_t* buf, int k, int s, int T, Emit emit) {
     const uint64_t key = buf[k];
     if (rec_p(key) == kTagF) return 0;
-    const uint32_t u = rec_u(key);
+    const int32_t a = cand_side(key);
     int64_t cnt = 0;
     int k2 = k + 1;
-    for (; k2 < s && (buf[k2] >> 26) == (key >> 26); ++k2) {  // same content, same deleted position
-        emit((int32_t)u, (int32_t)rec_u(buf[k2]));
+    for (; k2 < s && (buf[k2] >> 26) == (key >> 26); ++k2) {  // same hash, same deleted position
+        emit(a, cand_side(buf[k2]));
         ++cnt;
     }
-    if (T >= 1 && rec_runstart(key)) {  // run-start deletion: look for the full record
+    if (T >= 1 && rec_runstart(key)) {
         int g = k2;
         while (g < s && (buf[g] >> 32) == (key >> 32)) ++g;
-        const uint64_t last = buf[g - 1];
-        if (rec_p(last) == kTagF) {
-            emit((int32_t)rec_u(last), (int32_t)u);
+        for (int f = g - 1; f >= k2 && rec_p(buf[f]) == kTagF; --f) {
+            emit(cand_side(buf[f]), a);
             ++cnt;
         }
     }
     return cnt;
 }
 
-// Pass 1 of the join: W_u += m_v and W_v += m_u for an edge {u, v}.
+// W_u += m_v and W_v += m_u for an edge {u, v}.
 struct Weigh {
     const int32_t* umult;
     int32_t* wsum;
@@ -387,89 +458,50 @@ struct Weigh {
     }
 };
 
-// Counting traversal with exactness check: every pair that would become an
-// edge is confirmed by comparing contents. A failed comparison means two
-// different contents share a 32-bit hash in this partition (bad = true); the
-// partition then goes to the exact fallback. A collision that could hide or
-// fake an edge always puts two different contents into some attempted pair
-// (same run of (hash, p), or a deletion record and the group's last full
-// record), so checking only attempted pairs is enough.
-__device__ __forceinline__ int64_t record_edges_checked(const uint64_t* buf, int k, int s, int T,
-                                                        const Canon* __restrict__ ucanon, bool& bad) {
-    const uint64_t key = buf[k];
-    if (rec_p(key) == kTagF) return 0;
-    // the run [r0, r1) of equal (hash, p) around k: every member is compared
-    // with the run's first record once (all equal to it => pairwise equal),
-    // instead of each member loading every later one (hot runs of a shared
-    // deletion variant made that a chain of dependent loads)
-    int r1 = k + 1;
-    while (r1 < s && (buf[r1] >> 26) == (key >> 26)) ++r1;
-    int r0 = k;
-    while (r0 > 0 && (buf[r0 - 1] >> 26) == (key >> 26)) --r0;
-    int64_t cnt = r1 - k - 1;
-    const bool indel_try = T >= 1 && rec_runstart(key);
-    uint64_t last = 0;
-    if (indel_try) {
-        int g = r1;
-        while (g < s && (buf[g] >> 32) == (key >> 32)) ++g;
-        last = buf[g - 1];
-    }
-    const bool indel = indel_try && rec_p(last) == kTagF;
-    if (r1 - r0 > 1 || indel) {
-        const Canon ck = record_content(key, ucanon);
-        if (k != r0 && !canon_eq(ck, record_content(buf[r0], ucanon))) bad = true;
-        if (indel) {
-            if (canon_eq(ck, record_content(last, ucanon))) ++cnt;
-            else bad = true;
-        }
-    }
-    return cnt;
-}
-
-// Join of the partitions of at most 32 records, without sorting. Lane k holds
-// record k; __match_any_sync on the 32-bit hash gives each lane its hash group
-// G, and G intersected with a match on p its run M of equal (hash, p) (two
-// 32-bit matches cost less than one on the 38-bit pair, measured). Same-position partners are the lanes of M above
-// this one (each pair once); a run-start deletion pairs with the group's full
-// record. Exactness as in the sorted path: every attempted pair is confirmed
-// by content, a group with two full records (two different contents under one
-// hash, since the strings are distinct) is a collision, and a collision sends
-// the partition to the exact fallback. Larger partitions are listed for
-// k_join_sorted (first pass) and skipped here; both passes take the same
-// decisions, so their counts agree.
-// First pass (WRITE = false): per-partition edge counts, weighted degrees
-// W_u += m_v, W_v += m_u, and every edge written into the capped segmented
-// buffer when it fits; a warp gathers its edges in shared memory and moves
-// them out kStage at a time (one cursor update per flush, coalesced stores).
-// Second pass (WRITE = true, only after an overflow): edges written at the
-// scanned positions eoff. The records of the next partition are loaded while
-// the current one is joined.
+// Join of the partitions of at most 32 records, without sorting. The records
+// of consecutive partitions are adjacent, so a warp step takes a window of
+// whole consecutive partitions holding at most 32 records: lane k holds record
+// k of the window. __match_any_sync on the 32-bit hash, restricted to the
+// lanes of the record's own partition, gives each lane its hash group G, and
+// G intersected with a match on p its run M of equal (hash, p) (two 32-bit
+// matches cost less than one on the 38-bit pair, measured). Same-position
+// candidates are the lanes of M above this one (each pair once); a run-start
+// deletion pairs with every full record of G. No content is read here: the
+// candidates are confirmed by k_confirm, so this pass streams the records and
+// issues only shuffles, votes and stores. Larger partitions are listed for
+// k_join_sorted / k_join_fallback (first pass) and skipped here; both passes
+// form the same windows, so their counts agree.
+// First pass (WRITE = false): candidate counts (a window's total at its first
+// partition, 0 at the others) and every candidate written into the capped
+// segmented buffer when it fits; a warp gathers its candidates in shared
+// memory and moves them out kStage at a time (one cursor update per flush,
+// coalesced stores). Second pass (WRITE = true, only after an overflow):
+// candidates written at the scanned positions eoff. The records of the next
+// window are loaded while the current one is joined.
 constexpr int kStage = 256;
 
 template <bool WRITE>
-__global__ void __launch_bounds__(kThreads, 6)
-k_join_small(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __restrict__ recs,
-             const Canon* __restrict__ ucanon, const int32_t* __restrict__ umult, int cap, int T,
-             int32_t* __restrict__ wsum, int64_t* __restrict__ pedges, const int64_t* __restrict__ eoff,
-             int2* __restrict__ edges, unsigned long long* __restrict__ ecur, int64_t seg_cap,
-             int32_t* __restrict__ big_list, int* __restrict__ big_count, int32_t* __restrict__ fb_list,
-             int* __restrict__ fb_count, int64_t R_cap = INT64_MAX) {
+__global__ void __launch_bounds__(kThreads)
+k_join_small(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __restrict__ recs, int cap, int T,
+             int64_t* __restrict__ pedges, const int64_t* __restrict__ eoff, int2* __restrict__ edges,
+             unsigned long long* __restrict__ ecur, int64_t seg_cap, int32_t* __restrict__ big_list,
+             int* __restrict__ big_count, int32_t* __restrict__ fb_list, int* __restrict__ fb_count,
+             int64_t R_cap = INT64_MAX) {
     dep_entry();  // launched dependent on the kernel before it
     if (poff[P] > R_cap) return;  // records beyond the array (invalid input): nothing is joined
     __shared__ uint64_t sbuf[kWarps][32];
-    __shared__ int32_t smul[kWarps][32];
     __shared__ int2 sstage[WRITE ? 1 : kWarps][WRITE ? 1 : kStage];
-    __shared__ Canon scanon[kWarps][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    Canon* cbuf = scanon[warp];
     uint64_t* buf = sbuf[warp];
-    int32_t* mul = smul[warp];
     int2* stage = sstage[WRITE ? 0 : warp];
     const uint32_t above = lane == 31 ? 0u : ~((2u << lane) - 1u);
+    const uint32_t upto = lane == 31 ? kFull : ((2u << lane) - 1u);  // lanes 0 .. lane
+    const uint32_t below = (1u << lane) - 1u;
     const int64_t wid = (int64_t)blockIdx.x * kWarps + warp;
     const int64_t nwarps = (int64_t)gridDim.x * kWarps;
     const int seg = (int)(wid & (kEdgeSegs - 1));
-    int fillc = 0;  // staged edges of this warp
+    const int small_max = cap < 32 ? cap : 32;
+    int fillc = 0;  // staged candidates of this warp
     auto flush = [&]() {
         __syncwarp();
         if (fillc) {
@@ -485,6 +517,7 @@ k_join_small(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __rest
         __syncwarp();
     };
     for (int64_t p0 = wid * 32; p0 < P; p0 += nwarps * 32) {
+        // lane k: partition p0 + k
         int64_t my_base = 0;
         int my_size = 0;
         if (p0 + lane < P) {
@@ -492,85 +525,79 @@ k_join_small(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __rest
             const int64_t sz = poff[p0 + lane + 1] - my_base;
             my_size = sz > 0x7fffffff ? 0x7fffffff : (int)sz;
         }
-        const int small_max = cap < 32 ? cap : 32;
+        const bool wable = p0 + lane < P && my_size <= small_max;  // joined in a window here
         if (!WRITE && p0 + lane < P) {  // lane-parallel hand-off of the other partitions
-            if (my_size > cap) {
-                fb_list[atomicAdd(fb_count, 1)] = (int32_t)(p0 + lane);
-                pedges[p0 + lane] = 0;
-            } else if (my_size > 32) {
-                big_list[atomicAdd(big_count, 1)] = (int32_t)(p0 + lane);
-            } else if (my_size < 2) {
-                pedges[p0 + lane] = 0;
-            }
+            if (my_size > cap) fb_list[atomicAdd(fb_count, 1)] = (int32_t)(p0 + lane);
+            else if (my_size > 32) big_list[atomicAdd(big_count, 1)] = (int32_t)(p0 + lane);
+            else pedges[p0 + lane] = 0;  // a window's first partition overwrites it with the window's count
         }
-        uint32_t todo = __ballot_sync(kFull, my_size >= 2 && my_size <= small_max);
-        int jn = todo ? __ffs(todo) - 1 : -1;
-        uint64_t rec_next = ~0ull;
-        int s_next = 0;
-        if (jn >= 0) {
-            const int64_t b = __shfl_sync(kFull, my_base, jn);
-            s_next = __shfl_sync(kFull, my_size, jn);
-            if (lane < s_next) rec_next = recs[b + lane];
+        const uint32_t wmask = __ballot_sync(kFull, wable);
+        const int wsize = wable ? my_size : 0;
+        int incl = wsize;  // inclusive prefix of the window-able sizes (each <= 32)
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, d);
+            if (lane >= d) incl += y;
         }
-        while (jn >= 0) {
-            const int j = jn;
-            const int s = s_next;
+        // the window starting at the first window-able lane >= from: partitions
+        // j .. e (consecutive, all window-able, at most 32 records), records
+        // [rb, rb + tot); false when no lane is left
+        auto window = [&](int from, int& j, int& e, int& tot, int64_t& rb) -> bool {
+            const uint32_t cand = from >= 32 ? 0u : (wmask & ~((1u << from) - 1u));
+            if (!cand) return false;
+            j = __ffs(cand) - 1;
+            const uint32_t stops = ~wmask & (j == 31 ? 0u : ~((2u << j) - 1u));
+            const int nb = stops ? __ffs(stops) - 1 : 32;  // first partition over the window size after j
+            const int excl_j = __shfl_sync(kFull, incl - wsize, j);
+            const uint32_t fit = __ballot_sync(kFull, lane >= j && lane < nb && incl - excl_j <= 32);
+            e = 31 - __clz(fit);
+            tot = __shfl_sync(kFull, incl, e) - excl_j;
+            rb = __shfl_sync(kFull, my_base, j);
+            return true;
+        };
+        int j = 0, e = 0, tot = 0;
+        int64_t rb = 0;
+        bool have = window(0, j, e, tot, rb);
+        uint64_t rec_next = (have && lane < tot) ? recs[rb + lane] : ~0ull;
+        while (have) {
+            const int wj = j, we = e, s = tot;
             const uint64_t rec = rec_next;
-            todo &= todo - 1;
-            jn = todo ? __ffs(todo) - 1 : -1;
-            if (jn >= 0) {  // prefetch the next partition's records
-                const int64_t b = __shfl_sync(kFull, my_base, jn);
-                s_next = __shfl_sync(kFull, my_size, jn);
-                rec_next = lane < s_next ? recs[b + lane] : ~0ull;
-            }
-            const int64_t pid = p0 + j;
+            // record lanes of each partition: bit (start offset) of every non-empty one
+            const int excl_j = __shfl_sync(kFull, incl - wsize, wj);
+            const uint32_t starts = __reduce_or_sync(
+                kFull, (lane >= wj && lane <= we && wsize > 0) ? (1u << (incl - wsize - excl_j)) : 0u);
+            have = window(we + 1, j, e, tot, rb);
+            rec_next = (have && lane < tot) ? recs[rb + lane] : ~0ull;  // prefetch the next window
+            if (s < 2) continue;  // no pair in this window (its partitions' counts stay 0)
             const bool act = lane < s;
+            // lanes [a, b) hold this record's partition
+            const uint32_t st_upto = starts & upto;
+            const int a = st_upto ? 31 - __clz(st_upto) : 0;
+            const uint32_t st_above = starts & above;
+            const int b = st_above ? __ffs(st_above) - 1 : s;
+            const uint32_t pmask = (b >= 32 ? kFull : ((1u << b) - 1u)) & ~((1u << a) - 1u);
             buf[lane] = rec;
             const uint32_t amask = (s >= 32) ? kFull : ((1u << s) - 1u);
-            const uint32_t G = __match_any_sync(kFull, (uint32_t)(rec >> 32)) & amask;
+            const uint32_t G = __match_any_sync(kFull, (uint32_t)(rec >> 32)) & amask & pmask;
             const uint32_t M = G & __match_any_sync(kFull, rec_p(rec));  // same hash and same p
             const bool isF = rec_p(rec) == kTagF;
             const uint32_t Gf = G & __ballot_sync(kFull, act && isF);
-            bool bad = act && __popc(Gf) > 1;
             const uint32_t partners = (act && !isF) ? (M & above) : 0u;
-            const bool indel = act && !isF && T >= 1 && rec_runstart(rec) && Gf != 0;
-            const bool grouped = act && __popc(G) > 1;
-            if (__any_sync(kFull, grouped)) {
-                // contents through shared memory (fewer shared-memory-pipe
-                // instructions than shuffling four words from two lanes)
-                Canon c;
-                if (grouped) {
-                    if (!WRITE) mul[lane] = umult[rec_u(rec)];
-                    c = record_content(rec, ucanon);
-                    store_canon(cbuf + lane, c);
-                }
-                __syncwarp();
-                if (act && !isF && __popc(M) > 1 && !canon_eq(c, load_canon_plain(cbuf + (__ffs(M) - 1)))) bad = true;
-                if (indel && !canon_eq(c, load_canon_plain(cbuf + (__ffs(Gf) - 1)))) bad = true;
-            }
-            __syncwarp();
-            if (__any_sync(kFull, bad)) {
-                if (!WRITE && lane == 0) {
-                    fb_list[atomicAdd(fb_count, 1)] = (int32_t)pid;
-                    pedges[pid] = 0;
-                }
-                __syncwarp();
-                continue;
-            }
-            // prefix sum of the per-lane counts (<= 32) by bit planes: votes and
+            const uint32_t fulls = (act && !isF && T >= 1 && rec_runstart(rec)) ? Gf : 0u;
+            // prefix sum of the per-lane counts (<= 63) by bit planes: votes and
             // population counts instead of shuffles
-            const int mine = __popc(partners) + (indel ? 1 : 0);
-            const uint32_t below = (1u << lane) - 1u;
+            const int mine = __popc(partners) + __popc(fulls);
             int excl = 0, total = 0;
 #pragma unroll
-            for (int b = 0; b < 6; ++b) {
-                const uint32_t plane = __ballot_sync(kFull, (mine >> b) & 1);
-                excl += __popc(plane & below) << b;
-                total += __popc(plane) << b;
+            for (int bp = 0; bp < 6; ++bp) {
+                const uint32_t plane = __ballot_sync(kFull, (mine >> bp) & 1);
+                excl += __popc(plane & below) << bp;
+                total += __popc(plane) << bp;
             }
-            const int32_t u = (int32_t)rec_u(rec);
+            __syncwarp();  // buf written by every lane
+            const int32_t me = cand_side(rec);
             if (!WRITE) {
-                if (lane == 0) pedges[pid] = total;
+                if (lane == wj) pedges[p0 + wj] = total;
                 if (total) {
                     // staged (total <= kStage) or written directly with its own cursor update
                     if (fillc + total > kStage) flush();
@@ -585,28 +612,15 @@ k_join_small(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __rest
                     } else {
                         fillc += total;
                     }
-                    if (mine) {
-                        const int32_t mu = mul[lane];
-                        for (uint32_t m = partners; m; m &= m - 1) {
-                            const int k = __ffs(m) - 1;
-                            const int32_t v = (int32_t)rec_u(buf[k]);
-                            atomicAdd(&wsum[u], mul[k]);
-                            atomicAdd(&wsum[v], mu);
-                            if (fits) *dst++ = make_int2(u, v);
-                        }
-                        if (indel) {
-                            const int k = __ffs(Gf) - 1;
-                            const int32_t v = (int32_t)rec_u(buf[k]);
-                            atomicAdd(&wsum[u], mul[k]);
-                            atomicAdd(&wsum[v], mu);
-                            if (fits) *dst++ = make_int2(v, u);
-                        }
+                    if (fits) {
+                        for (uint32_t m = partners; m; m &= m - 1) *dst++ = make_int2(me, cand_side(buf[__ffs(m) - 1]));
+                        for (uint32_t m = fulls; m; m &= m - 1) *dst++ = make_int2(cand_side(buf[__ffs(m) - 1]), me);
                     }
                 }
             } else if (mine) {
-                int64_t pos = eoff[pid] + excl;
-                for (uint32_t m = partners; m; m &= m - 1) edges[pos++] = make_int2(u, (int32_t)rec_u(buf[__ffs(m) - 1]));
-                if (indel) edges[pos++] = make_int2((int32_t)rec_u(buf[__ffs(Gf) - 1]), u);
+                int64_t pos = eoff[p0 + wj] + excl;
+                for (uint32_t m = partners; m; m &= m - 1) edges[pos++] = make_int2(me, cand_side(buf[__ffs(m) - 1]));
+                for (uint32_t m = fulls; m; m &= m - 1) edges[pos++] = make_int2(cand_side(buf[__ffs(m) - 1]), me);
             }
             __syncwarp();
         }
@@ -616,14 +630,13 @@ k_join_small(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __rest
 
 // Join of the listed partitions of 33 .. cap records: warp per partition,
 // register bitonic sort, runs of equal (hash, p) and hash groups scanned in
-// order (see record_edges / record_edges_checked).
+// order (record_cands); candidates as in k_join_small.
 template <bool WRITE>
 __global__ void __launch_bounds__(kThreads)
 k_join_sorted(const int32_t* __restrict__ list, const int* __restrict__ count, const int64_t* __restrict__ poff,
-              const uint64_t* __restrict__ recs, const Canon* __restrict__ ucanon, int T, Weigh weigh,
-              int64_t* __restrict__ pedges, const int64_t* __restrict__ eoff, int2* __restrict__ edges,
-              unsigned long long* __restrict__ ecur, int64_t seg_cap, int32_t* __restrict__ fb_list,
-              int* __restrict__ fb_count) {
+              const uint64_t* __restrict__ recs, int T, int64_t* __restrict__ pedges,
+              const int64_t* __restrict__ eoff, int2* __restrict__ edges, unsigned long long* __restrict__ ecur,
+              int64_t seg_cap) {
     dep_entry();  // launched dependent on the kernel before it
     __shared__ uint64_t sbuf[kWarps][kWarpCap];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -636,18 +649,8 @@ k_join_sorted(const int32_t* __restrict__ list, const int* __restrict__ count, c
         if (s <= 64) load_sort_store<2>(recs + base, s, buf, lane);
         else load_sort_store<4>(recs + base, s, buf, lane);
         __syncwarp();
-        // count the edges, confirming each one's contents (exact)
-        bool bad = false;
         int64_t mine = 0;
-        for (int k = lane; k < s; k += 32) mine += record_edges_checked(buf, k, s, T, ucanon, bad);
-        if (__any_sync(kFull, bad)) {
-            if (!WRITE && lane == 0) {
-                fb_list[atomicAdd(fb_count, 1)] = (int32_t)pid;
-                pedges[pid] = 0;
-            }
-            __syncwarp();
-            continue;
-        }
+        for (int k = lane; k < s; k += 32) mine += record_cands(buf, k, s, T, [](int32_t, int32_t) {});
         int64_t excl;
         const int64_t total = warp_scan(mine, excl, lane);
         if (!WRITE) {
@@ -657,32 +660,34 @@ k_join_sorted(const int32_t* __restrict__ list, const int* __restrict__ count, c
                 unsigned long long eb = 0;
                 if (lane == 0) eb = atomicAdd(&ecur[seg], (unsigned long long)total);
                 eb = __shfl_sync(kFull, eb, 0);
-                const bool fits = (int64_t)(eb + total) <= seg_cap;
-                int64_t pos = seg * seg_cap + (int64_t)eb + excl;
-                for (int k = lane; k < s; k += 32)
-                    record_edges(buf, k, s, T, [&](int32_t a, int32_t b) {
-                        weigh(a, b);
-                        if (fits) edges[pos++] = make_int2(a, b);
-                    });
+                if ((int64_t)(eb + total) <= seg_cap) {
+                    int64_t pos = seg * seg_cap + (int64_t)eb + excl;
+                    for (int k = lane; k < s; k += 32)
+                        record_cands(buf, k, s, T, [&](int32_t a, int32_t b) { edges[pos++] = make_int2(a, b); });
+                }
             }
         } else {
             int64_t pos = eoff[pid] + excl;
             for (int k = lane; k < s; k += 32)
-                record_edges(buf, k, s, T, [&](int32_t a, int32_t b) { edges[pos++] = make_int2(a, b); });
+                record_cands(buf, k, s, T, [&](int32_t a, int32_t b) { edges[pos++] = make_int2(a, b); });
         }
         __syncwarp();
     }
 }
 
-// Exact quadratic join of one partition (over capacity or with a hash collision).
+// Join of one partition over the warp capacity (cap records): a block tests
+// every pair of its records for the candidate conditions (equal 32-bit hash
+// and equal p, or a run-start deletion and a full record of equal hash),
+// without sorting; candidates as in k_join_small.
 template <bool WRITE>
 __global__ void __launch_bounds__(kThreads)
 k_join_fallback(const int32_t* __restrict__ fb_list, const int* __restrict__ fb_count, const int64_t* __restrict__ poff,
-                const uint64_t* __restrict__ recs, const Canon* __restrict__ ucanon, int T, Weigh weigh,
-                int64_t* __restrict__ pedges, const int64_t* __restrict__ eoff, int2* __restrict__ edges,
-                unsigned long long* __restrict__ ecur, int64_t seg_cap) {
+                const uint64_t* __restrict__ recs, int T, int64_t* __restrict__ pedges,
+                const int64_t* __restrict__ eoff, int2* __restrict__ edges, unsigned long long* __restrict__ ecur,
+                int64_t seg_cap) {
     dep_entry();  // launched dependent on the kernel before it
     __shared__ int64_t wtot[kWarps];
+    __shared__ unsigned long long sbase;
     const int nfb = *fb_count;
     for (int f = blockIdx.x; f < nfb; f += gridDim.x) {
         const int64_t pid = fb_list[f];
@@ -692,48 +697,81 @@ k_join_fallback(const int32_t* __restrict__ fb_list, const int* __restrict__ fb_
             int64_t cnt = 0;
             for (int64_t k1 = threadIdx.x; k1 < s; k1 += kThreads) {
                 const uint64_t r1 = recs[base + k1];
-                const uint32_t p1 = rec_p(r1);
-                if (p1 == kTagF) continue;  // deletion records initiate every edge
-                const Canon c1 = record_content(r1, ucanon);
-                const bool rs1 = rec_runstart(r1);
+                if (rec_p(r1) == kTagF) continue;  // deletion records initiate every candidate
+                const bool rs1 = T >= 1 && rec_runstart(r1);
                 for (int64_t k2 = 0; k2 < s; ++k2) {
-                    if (k2 == k1) continue;
                     const uint64_t r2 = recs[base + k2];
+                    if ((r2 >> 32) != (r1 >> 32) || k2 == k1) continue;
                     const uint32_t p2 = rec_p(r2);
-                    const bool same = (p2 == p1) && (k2 > k1);
-                    const bool indel = (T >= 1) && rs1 && (p2 == kTagF);
-                    if (!same && !indel) continue;
-                    if (!canon_eq(c1, record_content(r2, ucanon))) continue;
-                    if (same) emit((int32_t)rec_u(r1), (int32_t)rec_u(r2));
-                    else emit((int32_t)rec_u(r2), (int32_t)rec_u(r1));
-                    ++cnt;
+                    if (p2 == rec_p(r1) && k2 > k1) {
+                        emit(cand_side(r1), cand_side(r2));
+                        ++cnt;
+                    } else if (rs1 && p2 == kTagF) {
+                        emit(cand_side(r2), cand_side(r1));
+                        ++cnt;
+                    }
                 }
             }
             return cnt;
         };
+        const int64_t mine = scan_pairs([](int32_t, int32_t) {});
+        int64_t excl;
+        const int64_t total = block_scan(mine, excl, wtot);
         if (!WRITE) {
-            const int64_t mine = scan_pairs(weigh);
-            int64_t excl;
-            const int64_t total = block_scan(mine, excl, wtot);
             if (threadIdx.x == 0) pedges[pid] = total;
             if (total) {
                 const int seg = (int)(pid & (kEdgeSegs - 1));
-                __shared__ unsigned long long base;
-                if (threadIdx.x == 0) base = atomicAdd(&ecur[seg], (unsigned long long)total);
+                if (threadIdx.x == 0) sbase = atomicAdd(&ecur[seg], (unsigned long long)total);
                 __syncthreads();
-                if ((int64_t)(base + total) <= seg_cap) {
-                    int64_t pos = seg * seg_cap + (int64_t)base + excl;
+                if ((int64_t)(sbase + total) <= seg_cap) {
+                    int64_t pos = seg * seg_cap + (int64_t)sbase + excl;
                     scan_pairs([&](int32_t a, int32_t b) { edges[pos++] = make_int2(a, b); });
                 }
             }
         } else {
-            const int64_t mine = scan_pairs([](int32_t, int32_t) {});
-            int64_t excl;
-            block_scan(mine, excl, wtot);
             int64_t pos = eoff[pid] + excl;
             scan_pairs([&](int32_t a, int32_t b) { edges[pos++] = make_int2(a, b); });
         }
         __syncthreads();
+    }
+}
+
+// Confirmation of the join's candidates: the two variants an entry names are
+// compared by content; a match becomes the plain edge (u, v) and adds
+// W_u += m_v, W_v += m_u, a mismatch (equal 32-bit hashes of different
+// contents) becomes (-1, -1) and is counted. One thread per entry, so the
+// random reads of the two strings are many in flight at once. Over the
+// segmented one-pass buffer (grid.y = segment) nothing is done when a segment
+// overflowed: the second join pass then writes the complete list and this
+// kernel runs on it.
+__global__ void k_confirm(int2* __restrict__ edges, int64_t seg_cap, const unsigned long long* __restrict__ seg_count,
+                          int check_overflow, const Canon* __restrict__ ucanon, Weigh weigh,
+                          int* __restrict__ false_count) {
+    dep_entry();  // launched dependent on the kernel before it
+    if (check_overflow) {
+        __shared__ int over;
+        if (threadIdx.x == 0) over = 0;
+        __syncthreads();
+        if (threadIdx.x < kEdgeSegs && (int64_t)seg_count[threadIdx.x] > seg_cap) over = 1;
+        __syncthreads();
+        if (over) return;
+    }
+    const int64_t E = (int64_t)seg_count[blockIdx.y];
+    int2* seg = edges + blockIdx.y * seg_cap;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < E; t += (int64_t)gridDim.x * blockDim.x) {
+        const int2 e = seg[t];
+        const int32_t a = e.x & (int32_t)kUMask, b = e.y & (int32_t)kUMask;
+        const uint32_t pa = (uint32_t)e.x >> 25, pb = (uint32_t)e.y >> 25;
+        Canon ca = load_canon(ucanon + a), cb = load_canon(ucanon + b);
+        if (pa != kTagF) ca = delete_at(ca, (int)pa);
+        if (pb != kTagF) cb = delete_at(cb, (int)pb);
+        if (canon_eq(ca, cb)) {
+            weigh(a, b);
+            seg[t] = make_int2(a, b);
+        } else {
+            seg[t] = make_int2(-1, -1);
+            atomicAdd(false_count, 1);
+        }
     }
 }
 
@@ -1097,6 +1135,17 @@ __global__ void k_compact_edges(const int2* __restrict__ edges, int64_t seg_cap,
     if (t < b.base[g + 1] - b.base[g]) out[b.base[g] + t] = edges[(int64_t)g * seg_cap + t];
 }
 
+// The confirmed edges of a list that holds rejected candidates ((-1, -1)),
+// gathered at a shared cursor (grid.y = segment).
+__global__ void k_gather_edges(const int2* __restrict__ edges, int64_t seg_cap,
+                               const unsigned long long* __restrict__ seg_count, int2* __restrict__ out,
+                               unsigned long long* __restrict__ cursor) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)seg_count[blockIdx.y]) return;
+    const int2 e = edges[(int64_t)blockIdx.y * seg_cap + t];
+    if (e.x >= 0) out[atomicAdd(cursor, 1ull)] = e;
+}
+
 __global__ void k_closed_self(const int32_t* __restrict__ uid, const int32_t* __restrict__ mpos, int64_t n,
                               const int64_t* __restrict__ uoff, int32_t* __restrict__ S) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1116,11 +1165,13 @@ k_closed_edges(const int2* __restrict__ edges, int64_t seg_cap, const unsigned l
     // grid.y = edge segment; t = direction-expanded index inside the segment
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t E = (int64_t)seg_count[blockIdx.y];
-    const bool have = t < 2 * E;
+    bool have = t < 2 * E;
     int32_t a = 0, b = 0, mb = 0;
     int64_t o = 0;
+    int2 uv = make_int2(-1, -1);
+    if (have) uv = edges[blockIdx.y * seg_cap + (t >> 1)];
+    have = have && uv.x >= 0;  // a rejected candidate of the join is no edge
     if (have) {
-        const int2 uv = edges[blockIdx.y * seg_cap + (t >> 1)];
         a = (t & 1) ? uv.y : uv.x;  // list owner
         b = (t & 1) ? uv.x : uv.y;  // neighbour whose members are appended
         mb = umult[b];
@@ -1274,6 +1325,7 @@ struct MidReadback {
     unsigned long long segs[kEdgeSegs + 1];  // per-segment edge counts, then the single-list count
     unsigned long long pack_error;           // encoder's first error word (0: none)
     int dmax;
+    int nfalse;                              // candidates the confirmation rejected
 };
 
 struct EndReadback {
@@ -1290,7 +1342,8 @@ __global__ void k_mid_readback(const int64_t* __restrict__ sd, const int64_t* __
     if (t == 0) {
         dst->sizes[0] = *sd;
         dst->sizes[1] = *nnz;
-        dst->dmax = *dmax;
+        dst->dmax = dmax[0];
+        dst->nfalse = dmax[1];  // the counter after the longest-list maximum
         dst->pack_error = pack_flags ? *pack_flags : 0ull;
     }
 }
@@ -1309,7 +1362,8 @@ __global__ void k_end_readback(const int* __restrict__ err, const int64_t* __res
 }  // namespace
 
 tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaStream_t s, int num_sms, bool profile,
-                             int partition_cap, bool keep_index, int partition_target, bool force_off64) {
+                             int partition_cap, bool keep_index, int partition_target, bool force_off64,
+                             int record_hash_bits) {
     const int64_t n = pk.n;
     if (n > kDeletionMaxN || T > 2) return TCRNET_ENOTSUP;
     const int cap = (partition_cap > 0 && partition_cap < kWarpCap) ? partition_cap : kWarpCap;
@@ -1332,8 +1386,9 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     // Every counter of the build that starts at zero, cleared by one memset
     // (u64 words): the edge cursors ([kEdgeSegs]: single-segment count), the
     // distinct-string count, the device counters ([0] dedup error, [1] fill
-    // error, [2] fallback partitions, [3] partitions for the sorted join, [4]
-    // largest closed list), and the status words of the build's scans.
+    // error, [2] partitions for the quadratic join, [3] partitions for the
+    // sorted join, [4] largest closed list, [5] rejected candidates), and the
+    // status words of the build's scans.
     const int64_t w_scan_n = scan_status_words(n);
     const int64_t w_scan_p = join ? scan_status_words(P) : 0;
     const int64_t w_fixed = (kEdgeSegs + 1) + 1 + 4;
@@ -1430,33 +1485,35 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         const unsigned rgrid = grid_for(n);
         TCR_CUDA(launch_dependent(k_records<false>, dim3(rgrid), dim3(kThreads), 0, s, ucanon.as<Canon>(),
                                   ulen.as<uint8_t>(), d_U, n, (uint32_t)P, pcnt.as<int32_t>(), nullptr, nullptr, 0u,
-                                  R_max));
+                                  R_max, 0xffffffffull));
         note_launch();
         // the scan clears the counts behind itself for the scatter's slot counters
         TCR_CHECK(scan_exclusive_i32_to_i64(pcnt.as<int32_t>(), poff.as<int64_t>(), P, s, slice(st_poff, w_scan_p),
                                             /*clear_input=*/true));
         TCR_CUDA(launch_dependent(k_records<true>, dim3(rgrid), dim3(kThreads), 0, s, ucanon.as<Canon>(),
                                   ulen.as<uint8_t>(), d_U, n, (uint32_t)P, pcnt.as<int32_t>(), poff.as<int64_t>(),
-                                  recs.as<uint64_t>(), 0u, R_max));
+                                  recs.as<uint64_t>(), 0u, R_max,
+                                  record_hash_bits >= 32 ? 0xffffffffull : ((1ull << record_hash_bits) - 1ull)));
         note_launch();
         t2 = tm.mark();
-        // ---- 3a. join, pass 1: weighted degrees W_u
+        // ---- 3a. join, pass 1: candidate pairs, then their confirmation (edges, weighted degrees W_u)
         jgrid = (int)std::min<int64_t>(ceil_div(P, 32 * kWarps), (int64_t)num_sms * 16);
         TCR_CUDA(launch_dependent(k_join_small<false>, dim3(jgrid), dim3(kThreads), 0, s, poff.as<int64_t>(), P,
-                                  recs.as<uint64_t>(), ucanon.as<Canon>(), umult.as<int32_t>(), cap, T,
-                                  wsum.as<int32_t>(), pedges.as<int64_t>(), nullptr, edges.as<int2>(), d_ecur,
-                                  seg_cap, big_list.as<int32_t>(), d_err + 3, fb_list.as<int32_t>(), d_err + 2,
-                                  R_max));
+                                  recs.as<uint64_t>(), cap, T, pedges.as<int64_t>(), nullptr, edges.as<int2>(),
+                                  d_ecur, seg_cap, big_list.as<int32_t>(), d_err + 3, fb_list.as<int32_t>(),
+                                  d_err + 2, R_max));
         note_launch();
         TCR_CUDA(launch_dependent(k_join_sorted<false>, dim3(num_sms * 4), dim3(kThreads), 0, s,
-                                  big_list.as<int32_t>(), d_err + 3, poff.as<int64_t>(), recs.as<uint64_t>(),
-                                  ucanon.as<Canon>(), T, weigh, pedges.as<int64_t>(), nullptr, edges.as<int2>(),
-                                  d_ecur, seg_cap, fb_list.as<int32_t>(), d_err + 2));
+                                  big_list.as<int32_t>(), d_err + 3, poff.as<int64_t>(), recs.as<uint64_t>(), T,
+                                  pedges.as<int64_t>(), nullptr, edges.as<int2>(), d_ecur, seg_cap));
         note_launch();
         TCR_CUDA(launch_dependent(k_join_fallback<false>, dim3(num_sms * 2), dim3(kThreads), 0, s,
-                                  fb_list.as<int32_t>(), d_err + 2, poff.as<int64_t>(), recs.as<uint64_t>(),
-                                  ucanon.as<Canon>(), T, weigh, pedges.as<int64_t>(), nullptr, edges.as<int2>(),
-                                  d_ecur, seg_cap));
+                                  fb_list.as<int32_t>(), d_err + 2, poff.as<int64_t>(), recs.as<uint64_t>(), T,
+                                  pedges.as<int64_t>(), nullptr, edges.as<int2>(), d_ecur, seg_cap));
+        note_launch();
+        TCR_CUDA(launch_dependent(k_confirm, dim3(confirm_blocks_x(num_sms), kEdgeSegs), dim3(kThreads), 0, s,
+                                  edges.as<int2>(), seg_cap, (const unsigned long long*)d_ecur, 1,
+                                  (const Canon*)ucanon.as<Canon>(), weigh, d_err + 5));
         note_launch();
         t3 = tm.mark();
     } else if (cand2) {
@@ -1529,69 +1586,77 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     DevBuf deg, off64;
     TCR_CHECK(deg.alloc_owned(sizeof(int32_t) * n, s));  // results are handed to the handle
     TCR_CHECK(off64.alloc_owned(sizeof(int64_t) * (n + 1), s));
-    if (w_scan_n > 0) {  // several tiles: sizes and both scans in one launch
-        const int64_t tiles = ceil_div(n, kScanTile);
-        TCR_CUDA(launch_dependent(k_fill_sizes, dim3((unsigned)tiles, 2), dim3(kScanThreads), 0, s,
-                                  wsum.as<int32_t>(), umult.as<int32_t>(), uid.as<int32_t>(), n, ucur.as<int32_t>(),
-                                  d_err + 4, deg.as<int32_t>(), uoff.as<int64_t>(), off64.as<int64_t>(), st_uoff,
-                                  st_off64, tiles));
-        note_launch();
-    } else {
-        TCR_CUDA(launch_dependent(k_closed_size, dim3(grid_for(n)), dim3(kThreads), 0, s, umult.as<int32_t>(), n,
-                                  wsum.as<int32_t>(), ucur.as<int32_t>(), d_err + 4));
-        note_launch();
-        TCR_CHECK(scan_exclusive_i32_to_i64(wsum.as<int32_t>(), uoff.as<int64_t>(), n, s));
-        TCR_CUDA(launch_dependent(k_node_degree, dim3(grid_for(n)), dim3(kThreads), 0, s, uid.as<int32_t>(), n,
-                                  wsum.as<int32_t>(), deg.as<int32_t>()));
-        note_launch();
-        TCR_CHECK(scan_exclusive_i32_to_i64(deg.as<int32_t>(), off64.as<int64_t>(), n, s));
-    }
-    // the sizes of the lists and of the CSR, the edge counts, the longest list
-    // and the encoder's error word come back in one synchronisation
     static_assert(sizeof(MidReadback) <= kPinnedScratchBytes, "readback fits the pinned scratch");
     MidReadback pageable;
     MidReadback* rb = static_cast<MidReadback*>(pinned_scratch());
     const unsigned long long* d_pack_flags = pk.flags.as<unsigned long long>();
-    if (rb && pinned_scratch_device()) {
-        TCR_CUDA(launch_dependent(k_mid_readback, dim3(1), dim3(96), 0, s, uoff.as<int64_t>() + n,
-                                  off64.as<int64_t>() + n, d_ecur, d_err + 4, d_pack_flags,
-                                  static_cast<MidReadback*>(pinned_scratch_device())));
-        note_launch();
-    } else {
-        if (!rb) rb = &pageable;
-        rb->pack_error = 0;
-        TCR_CUDA(cudaMemcpyAsync(&rb->sizes[0], uoff.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        TCR_CUDA(cudaMemcpyAsync(&rb->sizes[1], off64.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        TCR_CUDA(cudaMemcpyAsync(rb->segs, d_ecur, sizeof(rb->segs), cudaMemcpyDeviceToHost, s));
-        TCR_CUDA(cudaMemcpyAsync(&rb->dmax, d_err + 4, sizeof(int), cudaMemcpyDeviceToHost, s));
-        if (d_pack_flags)
-            TCR_CUDA(cudaMemcpyAsync(&rb->pack_error, d_pack_flags, sizeof(unsigned long long),
-                                     cudaMemcpyDeviceToHost, s));
-    }
-    // int32 row offsets for the handle, allocated and narrowed on the second
-    // stream while the host waits for the readback (dropped below if nnz turns
-    // out to need int64 offsets)
-    // (allocated on the stream that writes it, so that freeing it on any
-    // early return is ordered after the narrowing)
     DevBuf off32;
-    if (!force_off64 && n + 1 <= 0x7fffffffLL) {
-        cudaStream_t ns = s;
-        if (side) {
-            TCR_CUDA(cudaEventRecord(side->ev[6], s));
-            TCR_CUDA(cudaStreamWaitEvent(side->stream, side->ev[6], 0));
-            ns = side->stream;
+    // the list sizes and offsets from W_u, then the sizes of the lists and of
+    // the CSR, the candidate counts, the longest list, the rejected candidates
+    // and the encoder's error word in one synchronisation
+    auto sizes_and_readback = [&]() -> tcrnet_status {
+        if (w_scan_n > 0) {  // several tiles: sizes and both scans in one launch
+            const int64_t tiles = ceil_div(n, kScanTile);
+            TCR_CUDA(launch_dependent(k_fill_sizes, dim3((unsigned)tiles, 2), dim3(kScanThreads), 0, s,
+                                      wsum.as<int32_t>(), umult.as<int32_t>(), uid.as<int32_t>(), n,
+                                      ucur.as<int32_t>(), d_err + 4, deg.as<int32_t>(), uoff.as<int64_t>(),
+                                      off64.as<int64_t>(), st_uoff, st_off64, tiles));
+            note_launch();
+        } else {
+            TCR_CUDA(launch_dependent(k_closed_size, dim3(grid_for(n)), dim3(kThreads), 0, s, umult.as<int32_t>(),
+                                      n, wsum.as<int32_t>(), ucur.as<int32_t>(), d_err + 4));
+            note_launch();
+            TCR_CHECK(scan_exclusive_i32_to_i64(wsum.as<int32_t>(), uoff.as<int64_t>(), n, s));
+            TCR_CUDA(launch_dependent(k_node_degree, dim3(grid_for(n)), dim3(kThreads), 0, s, uid.as<int32_t>(), n,
+                                      wsum.as<int32_t>(), deg.as<int32_t>()));
+            note_launch();
+            TCR_CHECK(scan_exclusive_i32_to_i64(deg.as<int32_t>(), off64.as<int64_t>(), n, s));
         }
-        TCR_CHECK(off32.alloc_owned(sizeof(int32_t) * (n + 1), ns));
-        TCR_CHECK(narrow_offsets(off64.as<int64_t>(), off32.as<int32_t>(), n + 1, ns));
-    }
-    TCR_CUDA(cudaStreamSynchronize(s));
-    TCR_CHECK(pack_flags_status(rb->pack_error, &out.bad_index));
-    if (off32.as<void>() && rb->sizes[1] > 0x7fffffffLL) off32.reset();  // int64 offsets after all
+        if (rb && pinned_scratch_device()) {
+            TCR_CUDA(launch_dependent(k_mid_readback, dim3(1), dim3(96), 0, s, uoff.as<int64_t>() + n,
+                                      off64.as<int64_t>() + n, d_ecur, d_err + 4, d_pack_flags,
+                                      static_cast<MidReadback*>(pinned_scratch_device())));
+            note_launch();
+        } else {
+            if (!rb) rb = &pageable;
+            rb->pack_error = 0;
+            TCR_CUDA(cudaMemcpyAsync(&rb->sizes[0], uoff.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            TCR_CUDA(cudaMemcpyAsync(&rb->sizes[1], off64.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                     s));
+            TCR_CUDA(cudaMemcpyAsync(rb->segs, d_ecur, sizeof(rb->segs), cudaMemcpyDeviceToHost, s));
+            TCR_CUDA(cudaMemcpyAsync(&rb->dmax, d_err + 4, sizeof(int), cudaMemcpyDeviceToHost, s));
+            TCR_CUDA(cudaMemcpyAsync(&rb->nfalse, d_err + 5, sizeof(int), cudaMemcpyDeviceToHost, s));
+            if (d_pack_flags)
+                TCR_CUDA(cudaMemcpyAsync(&rb->pack_error, d_pack_flags, sizeof(unsigned long long),
+                                         cudaMemcpyDeviceToHost, s));
+        }
+        // int32 row offsets for the handle, allocated and narrowed on the second
+        // stream while the host waits for the readback (dropped below if nnz
+        // turns out to need int64 offsets); allocated on the stream that writes
+        // it, so that freeing it on any early return is ordered after the narrowing
+        off32.reset();
+        if (!force_off64 && n + 1 <= 0x7fffffffLL) {
+            cudaStream_t ns = s;
+            if (side) {
+                TCR_CUDA(cudaEventRecord(side->ev[6], s));
+                TCR_CUDA(cudaStreamWaitEvent(side->stream, side->ev[6], 0));
+                ns = side->stream;
+            }
+            TCR_CHECK(off32.alloc_owned(sizeof(int32_t) * (n + 1), ns));
+            TCR_CHECK(narrow_offsets(off64.as<int64_t>(), off32.as<int32_t>(), n + 1, ns));
+        }
+        TCR_CUDA(cudaStreamSynchronize(s));
+        TCR_CHECK(pack_flags_status(rb->pack_error, &out.bad_index));
+        if (off32.as<void>() && rb->sizes[1] > 0x7fffffffLL) off32.reset();  // int64 offsets after all
+        return TCRNET_OK;
+    };
+    TCR_CHECK(sizes_and_readback());
     unsigned long long segs[kEdgeSegs + 1];
     for (int g = 0; g <= kEdgeSegs; ++g) segs[g] = rb->segs[g];
-    const int h_dmax = rb->dmax;
-    const int64_t SD = rb->sizes[0], nnz = rb->sizes[1];
-    int64_t E = 0, seg_max = 0;
+    int h_dmax = rb->dmax;
+    int64_t SD = rb->sizes[0], nnz = rb->sizes[1];
+    int64_t nfalse = rb->nfalse;  // rejected candidates, (-1, -1) in the list
+    int64_t E = 0, seg_max = 0;   // E: entries of the list (edges and rejected candidates)
     bool overflow = false;
     for (int g = 0; g < kEdgeSegs; ++g) {
         E += (int64_t)segs[g];
@@ -1603,13 +1668,63 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         seg_max = E;
         if (E > E2_cap) return TCRNET_EDEVICE;
     }
+    // ---- 3b. candidates that did not fit: second join pass at scanned
+    // positions, their confirmation, and the list sizes again from the
+    // complete weights
     int n_two_pass = 0;
+    int64_t fill_segs = kEdgeSegs, fill_cap = seg_cap;
+    const unsigned long long* fill_counts = d_ecur;
+    if (cand2) {
+        fill_segs = 1;
+        fill_cap = E2_cap;
+        fill_counts = d_ecur + kEdgeSegs;
+    }
+    if (join && overflow) {
+        edges.reset();
+        TCR_CHECK(edges.alloc(sizeof(int2) * E, s));
+        TCR_CHECK(scan_exclusive_i64(pedges.as<int64_t>(), eoff.as<int64_t>(), P, s));
+        k_join_small<true><<<jgrid, kThreads, 0, s>>>(poff.as<int64_t>(), P, recs.as<uint64_t>(), cap, T, nullptr,
+                                                      eoff.as<int64_t>(), edges.as<int2>(), nullptr, 0, nullptr,
+                                                      nullptr, nullptr, nullptr);
+        TCR_LAUNCH_CHECK();
+        k_join_sorted<true><<<num_sms * 4, kThreads, 0, s>>>(big_list.as<int32_t>(), d_err + 3, poff.as<int64_t>(),
+                                                             recs.as<uint64_t>(), T, nullptr, eoff.as<int64_t>(),
+                                                             edges.as<int2>(), nullptr, 0);
+        TCR_LAUNCH_CHECK();
+        k_join_fallback<true><<<num_sms * 2, kThreads, 0, s>>>(fb_list.as<int32_t>(), d_err + 2, poff.as<int64_t>(),
+                                                               recs.as<uint64_t>(), T, nullptr, eoff.as<int64_t>(),
+                                                               edges.as<int2>(), nullptr, 0);
+        TCR_LAUNCH_CHECK();
+        n_two_pass = 1;
+        // the list is now contiguous: one segment of E entries
+        const unsigned long long e64 = (unsigned long long)E;
+        TCR_CUDA(cudaMemcpyAsync(d_ecur + kEdgeSegs, &e64, sizeof(e64), cudaMemcpyHostToDevice, s));
+        fill_segs = 1;
+        fill_cap = E;
+        fill_counts = d_ecur + kEdgeSegs;
+        seg_max = E;
+        // the first confirmation skipped the overflowed buffer: weights from
+        // the complete list, then the sizes again (their status words and the
+        // longest-list maximum cleared first)
+        TCR_CUDA(cudaMemsetAsync(wsum.as<void>(), 0, sizeof(int32_t) * n, s));
+        TCR_CUDA(cudaMemsetAsync(d_err + 4, 0, 2 * sizeof(int), s));
+        if (w_scan_n > 0) TCR_CUDA(cudaMemsetAsync(st_uoff, 0, 2 * sizeof(unsigned long long) * w_scan_n, s));
+        k_confirm<<<dim3(grid_for(E), 1), kThreads, 0, s>>>(edges.as<int2>(), E, d_ecur + kEdgeSegs, 0,
+                                                           ucanon.as<Canon>(), weigh, d_err + 5);
+        TCR_LAUNCH_CHECK();
+        TCR_CHECK(sizes_and_readback());
+        h_dmax = rb->dmax;
+        SD = rb->sizes[0];
+        nnz = rb->sizes[1];
+        nfalse = rb->nfalse;
+    }
     DevBuf Sbuf;
     TCR_CHECK(Sbuf.alloc(sizeof(int32_t) * SD, s));
     // a build handle keeps the edges between distinct strings (analytics run on
     // that graph of U nodes instead of the n-node network)
     DevBuf uedges;
-    const bool keep_edges = keep_index && (join || cand2) && E > 0;
+    const int64_t E_true = E - nfalse;
+    const bool keep_edges = keep_index && (join || cand2) && E_true > 0;
     // each list's own members (after its member list exists) and the kept
     // edges go to the side stream, next to the neighbour appends on this one
     cudaStream_t fs = s;
@@ -1622,63 +1737,31 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     k_closed_self<<<grid_for(n), kThreads, 0, fs>>>(uid.as<int32_t>(), mpos.as<int32_t>(), n, uoff.as<int64_t>(),
                                                     Sbuf.as<int32_t>());
     TCR_LAUNCH_CHECK();
-    // the kept edges of the usual cases are allocated and gathered after the
-    // neighbour appends are launched, so the allocation's host time overlaps them
-    const bool late_edges = keep_edges && (cand2 || !overflow);
+    // the kept edges are allocated and gathered after the neighbour appends are
+    // launched, so the allocation's host time overlaps them
     auto gather_edges = [&]() -> tcrnet_status {
-        TCR_CHECK(uedges.alloc_owned(sizeof(int2) * E, fs));  // stream-ordered on the stream that fills it
-        if (cand2) {  // already one contiguous list
-            TCR_CUDA(cudaMemcpyAsync(uedges.as<void>(), edges.as<void>(), sizeof(int2) * E, cudaMemcpyDeviceToDevice,
-                                     fs));
-        } else {  // the one-pass buffer holds every edge: segments to one array
+        TCR_CHECK(uedges.alloc_owned(sizeof(int2) * E_true, fs));  // stream-ordered on the stream that fills it
+        if (cand2 || (n_two_pass && nfalse == 0)) {  // already one contiguous list
+            TCR_CUDA(cudaMemcpyAsync(uedges.as<void>(), edges.as<void>(), sizeof(int2) * E_true,
+                                     cudaMemcpyDeviceToDevice, fs));
+        } else if (nfalse == 0) {  // the one-pass buffer holds every edge: segments to one array
             SegBases sb;
             sb.base[0] = 0;
             for (int g = 0; g < kEdgeSegs; ++g) sb.base[g + 1] = sb.base[g] + (int64_t)segs[g];
             const dim3 cgrid(grid_for(std::max<int64_t>(seg_max, 1)), (unsigned)kEdgeSegs);
             k_compact_edges<<<cgrid, kThreads, 0, fs>>>(edges.as<int2>(), seg_cap, sb, uedges.as<int2>());
             TCR_LAUNCH_CHECK();
+        } else {  // rejected candidates among them (rare): edges gathered at a shared cursor
+            DevBuf cur;
+            TCR_CHECK(cur.alloc(sizeof(unsigned long long), fs));
+            TCR_CUDA(cudaMemsetAsync(cur.as<void>(), 0, sizeof(unsigned long long), fs));
+            const dim3 cgrid(grid_for(std::max<int64_t>(seg_max, 1)), (unsigned)fill_segs);
+            k_gather_edges<<<cgrid, kThreads, 0, fs>>>(edges.as<int2>(), fill_cap, fill_counts, uedges.as<int2>(),
+                                                       cur.as<unsigned long long>());
+            TCR_LAUNCH_CHECK();
         }
         return TCRNET_OK;
     };
-    if (keep_edges && !late_edges) TCR_CHECK(uedges.alloc_owned(sizeof(int2) * E, s));
-    // ---- 3b. edges that did not fit: second join pass at scanned positions;
-    // then append neighbour member lists
-    int64_t fill_segs = kEdgeSegs, fill_cap = seg_cap;
-    const unsigned long long* fill_counts = d_ecur;
-    if (cand2) {
-        fill_segs = 1;
-        fill_cap = E2_cap;
-        fill_counts = d_ecur + kEdgeSegs;
-    }
-    if (join && overflow) {
-        edges.reset();
-        TCR_CHECK(edges.alloc(sizeof(int2) * E, s));
-        TCR_CHECK(scan_exclusive_i64(pedges.as<int64_t>(), eoff.as<int64_t>(), P, s));
-        k_join_small<true><<<jgrid, kThreads, 0, s>>>(
-            poff.as<int64_t>(), P, recs.as<uint64_t>(), ucanon.as<Canon>(), umult.as<int32_t>(), cap, T, nullptr,
-            nullptr, eoff.as<int64_t>(), edges.as<int2>(), nullptr, 0, nullptr, nullptr, nullptr, nullptr);
-        TCR_LAUNCH_CHECK();
-        k_join_sorted<true><<<num_sms * 4, kThreads, 0, s>>>(big_list.as<int32_t>(), d_err + 3, poff.as<int64_t>(),
-                                                             recs.as<uint64_t>(), ucanon.as<Canon>(), T, weigh,
-                                                             nullptr, eoff.as<int64_t>(), edges.as<int2>(), nullptr,
-                                                             0, nullptr, nullptr);
-        TCR_LAUNCH_CHECK();
-        k_join_fallback<true><<<num_sms * 2, kThreads, 0, s>>>(fb_list.as<int32_t>(), d_err + 2, poff.as<int64_t>(),
-                                                               recs.as<uint64_t>(), ucanon.as<Canon>(), T, weigh,
-                                                               nullptr, eoff.as<int64_t>(), edges.as<int2>(),
-                                                               nullptr, 0);
-        TCR_LAUNCH_CHECK();
-        n_two_pass = 1;
-        // the edges are now contiguous: one segment of E
-        const unsigned long long e64 = (unsigned long long)E;
-        TCR_CUDA(cudaMemcpyAsync(d_ecur + kEdgeSegs, &e64, sizeof(e64), cudaMemcpyHostToDevice, s));
-        fill_segs = 1;
-        fill_cap = E;
-        fill_counts = d_ecur + kEdgeSegs;
-        seg_max = E;
-        if (keep_edges)  // the second pass wrote them contiguously
-            TCR_CUDA(cudaMemcpyAsync(uedges.as<void>(), edges.as<void>(), sizeof(int2) * E, cudaMemcpyDeviceToDevice, s));
-    }
     if ((join || cand2) && E > 0) {
         if (!keep_index) recs.reset();
         const dim3 fgrid(grid_for(2 * seg_max), (unsigned)fill_segs);
@@ -1688,7 +1771,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
                                                             Sbuf.as<int32_t>(), d_err + 1);
         TCR_LAUNCH_CHECK();
     }
-    if (late_edges) TCR_CHECK(gather_edges());
+    if (keep_edges) TCR_CHECK(gather_edges());
     if (side) {  // own members, narrowed offsets and kept edges written
         TCR_CUDA(cudaEventRecord(side->ev[3], fs));
         TCR_CUDA(cudaStreamWaitEvent(s, side->ev[3], 0));
@@ -1736,7 +1819,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     out.n_unique = h_U;
     out.n_records = h_R;
     out.candidates = NC2;
-    out.unique_edges = E;
+    out.unique_edges = E_true;
     out.n_fallback = h_err[2];
     out.closed_total = SD;
     out.two_pass_join = n_two_pass;
@@ -1749,11 +1832,12 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         out.index.poff = static_cast<int64_t*>(poff.release());
         out.index.uid = static_cast<int32_t*>(uid.release());
         out.index.uedges = static_cast<int2*>(uedges.release());
-        out.index.E = out.index.uedges ? E : 0;
+        out.index.E = out.index.uedges ? E_true : 0;
         out.index.U = h_U;
         out.index.P = P;
         out.index.R = h_R;
         out.index.n = n;
+        if (join && record_hash_bits < 32) out.index.hmask = (uint32_t)((1ull << record_hash_bits) - 1ull);
     }
     out.ms_phase[0] = tm.ms(t0, t1);  // dedup
     out.ms_phase[1] = tm.ms(t1, t2);  // records

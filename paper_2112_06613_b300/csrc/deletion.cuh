@@ -28,7 +28,10 @@ struct DeletionIndex {
     int2* uedges = nullptr;    // edges between distinct strings, each once
     int64_t U = 0, P = 0, n = 0, E = 0;
     int64_t R = 0;             // records (poff[P])
-    bool valid() const { return recs != nullptr; }
+    // bits of the 32-bit content hash the records keep (all but in a testing
+    // build, whose records then serve no queries or merged inserts)
+    uint32_t hmask = 0xffffffffu;
+    bool valid() const { return recs != nullptr && hmask == 0xffffffffu; }
 };
 
 struct DeletionResult {
@@ -41,7 +44,7 @@ struct DeletionResult {
     int64_t n_records = 0;
     int64_t unique_edges = 0;
     int64_t candidates = 0;    // l_max = 2: distinct-string pairs sharing a variant (before deduplication)
-    int64_t n_fallback = 0;    // partitions joined by the exact quadratic fallback
+    int64_t n_fallback = 0;    // partitions over the warp capacity, joined by the quadratic pass
     int64_t closed_total = 0;  // sum over distinct strings of closed-neighbourhood sizes
     int two_pass_join = 0;     // 1 when the edges overflowed the one-pass buffer
     int64_t bad_index = -1;    // input index of an encoder error found by the build (see pk.flags)
@@ -53,7 +56,7 @@ struct DeletionResult {
 
 // Network of the packed strings at l_max = T (0, 1 or 2; ENOTSUP above). Test
 // knob: partitions larger than `partition_cap` (<= the shared-memory capacity;
-// 0 = default) take the quadratic fallback of the l_max = 1 join. The query
+// 0 = default) take the quadratic pass of the l_max = 1 join. The query
 // index is kept (keep_index) for l_max = 1 builds. If the encoder's error word
 // (pk.flags) was not checked by the packing, the build checks it at its first
 // readback and returns the input error with out.bad_index; until then its
@@ -61,7 +64,7 @@ struct DeletionResult {
 // pk.lensum they were sized for (possible only for invalid input).
 tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaStream_t s, int num_sms,
                              bool profile, int partition_cap = 0, bool keep_index = false,
-                             int partition_target = 0, bool force_off64 = false);
+                             int partition_target = 0, bool force_off64 = false, int record_hash_bits = 32);
 
 // Neighbour lists (l_max = T) of packed query strings against a resident
 // index: CSR with int64 offsets (m + 1), columns, per-query counts.

@@ -47,6 +47,24 @@ def test_components_and_removal(method, threshold):
             assert (nc, lcc) == analytics.largest_component(ref)
 
 
+def test_components_on_kept_edges_after_rejected_candidates():
+    # the edges between distinct strings that a handle keeps for the analytics
+    # are gathered without the join's rejected candidates
+    rep, off, cols = oracle_case(20_000, 81, 1)
+    with tn.tcrnet_build_flat(rep.chars, rep.offsets, 1, method="deletion", record_hash_bits=3) as g:
+        goff, gcols, _ = g.copy_csr()
+        assert_csr_equal(goff, gcols, off, cols, "3-bit record hashes")
+        with tn.tcrnet_build_flat(rep.chars, rep.offsets, 1, method="deletion") as full:
+            assert g.stats()["unique_edges"] == full.stats()["unique_edges"]
+        labels, nc, lcc = g.components()
+        ref = analytics.components(off, cols)
+        assert np.array_equal(labels, ref)
+        assert (nc, lcc) == analytics.largest_component(ref)
+        keep = (np.random.default_rng(6).random(rep.n) >= 0.5).astype(np.uint8)
+        labels, _, _ = g.components(keep)
+        assert np.array_equal(labels, analytics.components(off, cols, keep))
+
+
 def test_components_edge_cases():
     with tn.tcrnet_build(["CASSF"] * 50 + ["W", "Y", "WY"], 1, method="deletion") as g:
         labels, nc, lcc = g.components()

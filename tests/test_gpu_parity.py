@@ -255,6 +255,36 @@ def test_deletion_exact_fallback_join():
     assert_csr_equal(off, cols, ro, rc, "fallback join")
 
 
+@pytest.mark.parametrize("bits", [1, 6])
+def test_deletion_join_rejects_candidates_of_truncated_hashes(bits):
+    # with only a few bits of each record's hash kept, variants of different
+    # contents in one partition match; the confirmation by content rejects
+    # those candidates and the network stays exact
+    rep = generate_config1(10_000, seed=13)
+    off, cols, deg, st = gpu_csr(rep, 1, "deletion", record_hash_bits=bits)
+    ro, rc, rd = oracle_csr(rep, 1)
+    assert_csr_equal(off, cols, ro, rc, f"{bits}-bit record hashes")
+    assert np.array_equal(deg, rd)
+    _, _, _, full = gpu_csr(rep, 1, "deletion")
+    assert st["unique_edges"] == full["unique_edges"] > 0
+    # and with a partition capacity that sends partitions to the quadratic join
+    off, cols, _, st = gpu_csr(rep, 1, "deletion", record_hash_bits=bits, partition_cap=4)
+    assert st["n_fallback"] > 0
+    assert_csr_equal(off, cols, ro, rc, f"{bits}-bit record hashes, quadratic join")
+
+
+def test_deletion_two_pass_join_with_rejected_candidates():
+    # an overflowing candidate list (dense unique graph) whose candidates
+    # include rejected ones: the weights come from the second pass only
+    letters = list(ALPHABET)
+    strs = letters + [a + b for a in letters for b in letters] + ["AA", "C", "CAS"]
+    rep = from_strings(strs)
+    off, cols, deg, st = gpu_csr(rep, 1, "deletion", record_hash_bits=2)
+    assert st["two_pass_join"] == 1
+    ro, rc, _ = oracle_csr(rep, 1)
+    assert_csr_equal(off, cols, ro, rc, "dense unique graph, 2-bit record hashes")
+
+
 def test_deletion_counts_distinct_strings():
     rep = generate_config1(30_000, seed=12)
     _, _, _, st = gpu_csr(rep, 1, "deletion")
