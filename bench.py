@@ -76,8 +76,8 @@ OPS_INDEL_PER_WORD = 26
 # from one ncu capture of the current kernels (profiles/k_records_join_n800000.md,
 # profiles/k_sort_fill_expand_n800000.md); absent where no capture covers the phase.
 PHASE_TRAFFIC_N800000 = {
-    "records": 21.908e6 + 1.936e6 + 86.726e6 + 106.363e6,            # count, partition scan, scatter
-    "join_weigh": 100.093e6 + 6.612e6 + 21.848e6 + 0.027e6 + 0.015e6,  # small, sorted, fallback joins
+    "records": 23.824e6 + 3.851e6 + 97.684e6 + 132.412e6,             # count, partition scan, scatter
+    "join": 79.981e6 + 3.851e6 + 1.275e6 + 0.052e6 + 32.083e6 + 0.017e6,  # windows, sorted, confirmation
     "list_sort": 24.988e6 + 27.434e6 + 14.251e6 + 0.350e6,            # the four sort classes
     "expand": 83.423e6 + 198.956e6,
 }
@@ -370,7 +370,7 @@ def large_leg(tn, torch, dev, stream, flush, steps=5):
     g.free()
     ms = statistics.mean(ts)
     cand = candidate_pairs(rep.lengths())
-    names = ["dedup", "records", "join_weigh", "join_fill", "unused", "list_sort", "expand"]
+    names = ["dedup", "records", "join", "join_fill", "unused", "list_sort", "expand"]
     return {"n": rep.n, "build_ms": ms, "build_ms_min": min(ts), "builds": steps, "nnz": st["nnz"],
             "distinct_strings": st["n_unique"], "records": st["n_records"], "fallback_partitions": st["n_fallback"],
             "candidate_pairs_per_s": cand / (ms / 1e3), "edges_per_s": st["nnz"] / 2 / (ms / 1e3),
@@ -739,7 +739,7 @@ def run_ours(args):
 
     is_tile = st0["method"] == 1
     # dominant phase of the step and its algorithmic bytes
-    names = ["dedup", "records", "join_weigh", "join_fill", "unused", "list_sort", "expand"]
+    names = ["dedup", "records", "join", "join_fill", "unused", "list_sort", "expand"]
     phase_ms = {nm: statistics.mean(s["ms_phase"][i] for s in pstats) for i, nm in enumerate(names) if nm != "unused"}
     phase_ms["pack"] = statistics.mean(s["ms_pack"] for s in pstats)
     if is_tile:
@@ -755,7 +755,7 @@ def run_ours(args):
         "expand": 4 * nnz + 4 * SD + 8 * (n + 1) + 4 * n,  # write cols; read lists, offsets, ids
         "list_sort": 8 * SD + 8 * (U + 1),                # read + write lists, read offsets
         "join_fill": 8 * R + 8 * SD,                      # read records; read members, write lists
-        "join_weigh": 8 * R,                              # read records
+        "join": 8 * R,                                    # read records (candidates, confirmation)
         "records": 32 * U + 8 * R,                        # read strings, scatter records
         "dedup": 32 * n + 32 * U + 8 * n,                 # read codes, write distinct strings, ids
         "pack": int(rep.chars.nbytes) + 8 * (n + 1) + 33 * n,  # read chars + offsets; write codes + lengths

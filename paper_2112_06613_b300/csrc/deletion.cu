@@ -579,6 +579,9 @@ k_join_small(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __rest
             buf[lane] = rec;
             const uint32_t amask = (s >= 32) ? kFull : ((1u << s) - 1u);
             const uint32_t G = __match_any_sync(kFull, (uint32_t)(rec >> 32)) & amask & pmask;
+            // no two records of a partition share a hash: the window has no candidate
+            // (its partitions' counts stay 0)
+            if (!__any_sync(kFull, (G & ~(1u << lane)) != 0u)) continue;
             const uint32_t M = G & __match_any_sync(kFull, rec_p(rec));  // same hash and same p
             const bool isF = rec_p(rec) == kTagF;
             const uint32_t Gf = G & __ballot_sync(kFull, act && isF);
@@ -758,20 +761,36 @@ __global__ void k_confirm(int2* __restrict__ edges, int64_t seg_cap, const unsig
     }
     const int64_t E = (int64_t)seg_count[blockIdx.y];
     int2* seg = edges + blockIdx.y * seg_cap;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < E; t += (int64_t)gridDim.x * blockDim.x) {
-        const int2 e = seg[t];
-        const int32_t a = e.x & (int32_t)kUMask, b = e.y & (int32_t)kUMask;
-        const uint32_t pa = (uint32_t)e.x >> 25, pb = (uint32_t)e.y >> 25;
-        Canon ca = load_canon(ucanon + a), cb = load_canon(ucanon + b);
-        if (pa != kTagF) ca = delete_at(ca, (int)pa);
-        if (pb != kTagF) cb = delete_at(cb, (int)pb);
-        if (canon_eq(ca, cb)) {
-            weigh(a, b);
-            seg[t] = make_int2(a, b);
-        } else {
-            seg[t] = make_int2(-1, -1);
-            atomicAdd(false_count, 1);
-        }
+    // two entries per step: their loads are in flight together
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < E; t += 2 * stride) {
+        const int64_t t2 = t + stride;
+        const bool two = t2 < E;
+        const int2 e1 = seg[t];
+        const int2 e2 = two ? seg[t2] : e1;
+        const int32_t a1 = e1.x & (int32_t)kUMask, b1 = e1.y & (int32_t)kUMask;
+        const int32_t a2 = e2.x & (int32_t)kUMask, b2 = e2.y & (int32_t)kUMask;
+        Canon ca1 = load_canon(ucanon + a1), cb1 = load_canon(ucanon + b1);
+        Canon ca2 = load_canon(ucanon + a2), cb2 = load_canon(ucanon + b2);
+        auto variant = [](Canon& c, int32_t side) {
+            const uint32_t p = (uint32_t)side >> 25;
+            if (p != kTagF) c = delete_at(c, (int)p);
+        };
+        variant(ca1, e1.x);
+        variant(cb1, e1.y);
+        variant(ca2, e2.x);
+        variant(cb2, e2.y);
+        auto finish = [&](int64_t k, int32_t a, int32_t b, bool same) {
+            if (same) {
+                weigh(a, b);
+                seg[k] = make_int2(a, b);
+            } else {
+                seg[k] = make_int2(-1, -1);
+                atomicAdd(false_count, 1);
+            }
+        };
+        finish(t, a1, b1, canon_eq(ca1, cb1));
+        if (two) finish(t2, a2, b2, canon_eq(ca2, cb2));
     }
 }
 
