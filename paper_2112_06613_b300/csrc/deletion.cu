@@ -308,7 +308,24 @@ __global__ void k_members(const int32_t* __restrict__ uid, int64_t n, const int6
 
 // ---- 2. records -----------------------------------------------------------
 
-constexpr int kRecBatch = 4;
+#ifndef TCR_REC_BATCH
+#define TCR_REC_BATCH 4
+#endif
+constexpr int kRecBatch = TCR_REC_BATCH;  // records of the scatter in flight per thread
+
+// Stores of the record scatter carry an L2 evict-last hint: the ~1e6 partition
+// write fronts each fill a 32-byte sector a few records at a time, and a line
+// the L2 evicts before its sector is complete makes the DRAM read it back and
+// merge it. (A per-instruction priority; no cache setting is changed.)
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ void st_keep(uint64_t* p, uint64_t v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol) : "memory");
+}
 
 // The scatter writes nothing when the records counted exceed R_cap, the size
 // the record array was given (only invalid input, whose error the build reports
@@ -331,27 +348,40 @@ __global__ void k_records(const Canon* __restrict__ ucanon, const uint8_t* __res
         // kRecBatch records at a time (a shift register of pending ones): their
         // slot atomics and offset loads are independent, so they are in flight
         // together rather than one round trip each
-        uint64_t r0 = 0, r1 = 0, r2 = 0, r3 = 0;
-        uint32_t q0 = 0, q1 = 0, q2 = 0, q3 = 0;
+        const uint64_t pol = l2_keep_policy();
+        uint64_t r[kRecBatch];
+        uint32_t q[kRecBatch];
+#pragma unroll
+        for (int j = 0; j < kRecBatch; ++j) {
+            r[j] = 0;
+            q[j] = 0;
+        }
         int pending = 0;
         auto issue = [&](int k) {  // the k newest pending records (k <= kRecBatch)
-            int32_t s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-            int64_t b0 = 0, b1 = 0, b2 = 0, b3 = 0;
-            if (k > 0) { s0 = atomicAdd(&pcnt[q0], 1); b0 = poff[q0]; }
-            if (k > 1) { s1 = atomicAdd(&pcnt[q1], 1); b1 = poff[q1]; }
-            if (k > 2) { s2 = atomicAdd(&pcnt[q2], 1); b2 = poff[q2]; }
-            if (k > 3) { s3 = atomicAdd(&pcnt[q3], 1); b3 = poff[q3]; }
-            if (k > 0) recs[b0 + s0] = r0;
-            if (k > 1) recs[b1 + s1] = r1;
-            if (k > 2) recs[b2 + s2] = r2;
-            if (k > 3) recs[b3 + s3] = r3;
+            int32_t sl[kRecBatch];
+            int64_t bs[kRecBatch];
+#pragma unroll
+            for (int j = 0; j < kRecBatch; ++j) {
+                sl[j] = 0;
+                bs[j] = 0;
+                if (j < k) {
+                    sl[j] = atomicAdd(&pcnt[q[j]], 1);
+                    bs[j] = poff[q[j]];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kRecBatch; ++j)
+                if (j < k) st_keep(recs + bs[j] + sl[j], r[j], pol);
         };
         for_each_variant_hash(c, L, [&](int p, uint64_t h, bool rs) {
             const uint64_t tag = p < 0 ? ((uint64_t)kTagF << 26) : (((uint64_t)p << 26) | (rs ? (1ull << 25) : 0ull));
-            r3 = r2; r2 = r1; r1 = r0;
-            q3 = q2; q2 = q1; q1 = q0;
-            r0 = ((h & hash_mask) << 32) | tag | uid;  // (hash_mask: testing, fewer hash bits kept)
-            q0 = part_of(h, P);
+#pragma unroll
+            for (int j = kRecBatch - 1; j > 0; --j) {
+                r[j] = r[j - 1];
+                q[j] = q[j - 1];
+            }
+            r[0] = (h << 32) | tag | uid;
+            q[0] = part_of(h, P);
             if (++pending == kRecBatch) {
                 issue(kRecBatch);
                 pending = 0;
