@@ -308,10 +308,7 @@ __global__ void k_members(const int32_t* __restrict__ uid, int64_t n, const int6
 
 // ---- 2. records -----------------------------------------------------------
 
-#ifndef TCR_REC_BATCH
-#define TCR_REC_BATCH 4
-#endif
-constexpr int kRecBatch = TCR_REC_BATCH;  // records of the scatter in flight per thread
+constexpr int kRecBatch = 4;  // records of the scatter in flight per thread (8 measured slower)
 
 // Stores of the record scatter carry an L2 evict-last hint: the ~1e6 partition
 // write fronts each fill a 32-byte sector a few records at a time, and a line
@@ -1260,6 +1257,8 @@ k_closed_edges(const int2* __restrict__ edges, int64_t seg_cap, const unsigned l
 // one after another, lanes along the row. S_u is sorted and contains i once,
 // so element x at position k goes to k - (x > i).
 constexpr int kLaneRow = 16;
+constexpr int kExpVec = 4;  // entries per lane of a long row in flight (8 measured slower)
+constexpr int kExpChunk = 32 * kExpVec;
 
 __global__ void k_expand(const int32_t* __restrict__ uid, int64_t n, const int64_t* __restrict__ uoff,
                          const int32_t* __restrict__ S, const int64_t* __restrict__ off, int32_t* __restrict__ cols) {
@@ -1293,21 +1292,21 @@ __global__ void k_expand(const int32_t* __restrict__ uid, int64_t n, const int64
                 }
             }
         }
-        // long rows, one per step with the whole warp: the first 128 entries of
+        // long rows, one per step with the whole warp: the first kExpChunk entries of
         // the next row are loaded before this row's are stored (eight loads per
         // lane in flight)
         uint32_t todo = __ballot_sync(kFull, D > kLaneRow + 1);
         int j = todo ? __ffs(todo) - 1 : -1;
         int64_t js0 = 0, jo = 0;
         int iD = 0;
-        int32_t x[4];
-        auto fetch = [&](int jj, int64_t& s0_, int64_t& o_, int& d_, int32_t (&v)[4]) {
+        int32_t x[kExpVec];
+        auto fetch = [&](int jj, int64_t& s0_, int64_t& o_, int& d_, int32_t (&v)[kExpVec]) {
             s0_ = __shfl_sync(kFull, s0, jj);
             d_ = (int)__shfl_sync(kFull, D, jj);
             o_ = __shfl_sync(kFull, o, jj);
             const int32_t me_ = (int32_t)(r0 + jj);
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
+            for (int t = 0; t < kExpVec; ++t) {
                 const int k = lane + 32 * t;
                 v[t] = k < d_ ? S[s0_ + k] : me_;
             }
@@ -1318,39 +1317,39 @@ __global__ void k_expand(const int32_t* __restrict__ uid, int64_t n, const int64
             const int nj = todo ? __ffs(todo) - 1 : -1;
             int64_t ns0 = 0, no = 0;
             int nD = 0;
-            int32_t nx[4];
+            int32_t nx[kExpVec];
             if (nj >= 0) fetch(nj, ns0, no, nD, nx);
             const int32_t me = (int32_t)(r0 + j);
             int32_t* row = cols + jo;
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
+            for (int t = 0; t < kExpVec; ++t) {
                 const int k = lane + 32 * t;
                 const int q = k - (x[t] > me ? 1 : 0);
                 if (x[t] != me && q < iD - 1) row[q] = x[t];  // q < D - 1 always holds when i is in S_u
             }
             const int32_t* su = S + js0;
-            if (iD > 128) {  // the rest of a long row: each chunk's loads go out before the previous chunk's stores
-                int32_t y[4];
+            if (iD > kExpChunk) {  // the rest of a long row: each chunk's loads go out before the previous chunk's stores
+                int32_t y[kExpVec];
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int k = 128 + lane + 32 * t;
+                for (int t = 0; t < kExpVec; ++t) {
+                    const int k = kExpChunk + lane + 32 * t;
                     y[t] = k < iD ? su[k] : me;
                 }
-                for (int k0 = 128; k0 < iD; k0 += 128) {
-                    int32_t z[4];
+                for (int k0 = kExpChunk; k0 < iD; k0 += kExpChunk) {
+                    int32_t z[kExpVec];
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        const int k = k0 + 128 + lane + 32 * t;
+                    for (int t = 0; t < kExpVec; ++t) {
+                        const int k = k0 + kExpChunk + lane + 32 * t;
                         z[t] = k < iD ? su[k] : me;
                     }
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) {
+                    for (int t = 0; t < kExpVec; ++t) {
                         const int k = k0 + lane + 32 * t;
                         const int q = k - (y[t] > me ? 1 : 0);
                         if (y[t] != me && q < iD - 1) row[q] = y[t];
                     }
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) y[t] = z[t];
+                    for (int t = 0; t < kExpVec; ++t) y[t] = z[t];
                 }
             }
             j = nj;
@@ -1358,7 +1357,7 @@ __global__ void k_expand(const int32_t* __restrict__ uid, int64_t n, const int64
             jo = no;
             iD = nD;
 #pragma unroll
-            for (int t = 0; t < 4; ++t) x[t] = nx[t];
+            for (int t = 0; t < kExpVec; ++t) x[t] = nx[t];
         }
     }
 }
