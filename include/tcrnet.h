@@ -157,6 +157,9 @@ typedef struct tcrnet_stats {
                                  total */
     int64_t merged_inserts;   /* inserts merged into this network since its last
                                  full build (0 after a build or a rebuild) */
+    int64_t rejected_candidates; /* deletion path, l_max = 1: candidate pairs of equal
+                                    32-bit hash whose contents differ (rejected by the
+                                    confirmation; hash collisions) */
 } tcrnet_stats;
 
 /* Opaque handle: a CSR (n rows) owned by the library in device memory, plus,

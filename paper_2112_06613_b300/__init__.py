@@ -75,6 +75,7 @@ class tcrnet_stats(ctypes.Structure):
         ("ms_total", ctypes.c_double),
         ("ms_phase", ctypes.c_double * 8),
         ("merged_inserts", ctypes.c_int64),
+        ("rejected_candidates", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -485,6 +485,7 @@ tcrnet_status build_from_packed(tcrnet_graph* h, Packed& pk, int64_t n, int32_t 
         h->stats.n_fallback = dr.n_fallback;
         h->stats.closed_total = dr.closed_total;
         h->stats.two_pass_join = dr.two_pass_join;
+        h->stats.rejected_candidates = dr.rejected;
         h->stats.ms_count = dr.ms_join;
         h->stats.ms_scan = dr.ms_scan;
         h->stats.ms_write = dr.ms_fill;
@@ -1109,7 +1110,7 @@ namespace {
 // resident strings (bucketed copy + order, or input-order copy + lengths),
 // then the deletion index when present.
 constexpr char kMagic[8] = {'T', 'C', 'R', 'N', 'E', 'T', 'C', 'K'};
-constexpr uint32_t kFileVersion = 3;
+constexpr uint32_t kFileVersion = 4;
 
 struct FileHeader {
     char magic[8];

@@ -377,7 +377,7 @@ __global__ void k_records(const Canon* __restrict__ ucanon, const uint8_t* __res
                 r[j] = r[j - 1];
                 q[j] = q[j - 1];
             }
-            r[0] = (h << 32) | tag | uid;
+            r[0] = ((h & hash_mask) << 32) | tag | uid;  // (hash_mask: testing, fewer hash bits kept)
             q[0] = part_of(h, P);
             if (++pending == kRecBatch) {
                 issue(kRecBatch);
@@ -1871,6 +1871,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     out.n_fallback = h_err[2];
     out.closed_total = SD;
     out.two_pass_join = n_two_pass;
+    out.rejected = nfalse;
     if (keep_index && (join || cand2)) {
         out.index.ucanon = static_cast<Canon*>(ucanon.release());
         out.index.umult = static_cast<int32_t*>(umult.release());

@@ -47,6 +47,7 @@ struct DeletionResult {
     int64_t n_fallback = 0;    // partitions over the warp capacity, joined by the quadratic pass
     int64_t closed_total = 0;  // sum over distinct strings of closed-neighbourhood sizes
     int two_pass_join = 0;     // 1 when the edges overflowed the one-pass buffer
+    int64_t rejected = 0;      // candidate pairs the confirmation rejected (hash collisions)
     int64_t bad_index = -1;    // input index of an encoder error found by the build (see pk.flags)
     double ms_join = 0, ms_scan = 0, ms_fill = 0, ms_sort = 0;
     // dedup, records, join count, join write, closed fill, closed sort, expand, total

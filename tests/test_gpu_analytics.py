@@ -54,6 +54,7 @@ def test_components_on_kept_edges_after_rejected_candidates():
     with tn.tcrnet_build_flat(rep.chars, rep.offsets, 1, method="deletion", record_hash_bits=3) as g:
         goff, gcols, _ = g.copy_csr()
         assert_csr_equal(goff, gcols, off, cols, "3-bit record hashes")
+        assert g.stats()["rejected_candidates"] > 0
         with tn.tcrnet_build_flat(rep.chars, rep.offsets, 1, method="deletion") as full:
             assert g.stats()["unique_edges"] == full.stats()["unique_edges"]
         labels, nc, lcc = g.components()

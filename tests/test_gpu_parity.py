@@ -265,6 +265,7 @@ def test_deletion_join_rejects_candidates_of_truncated_hashes(bits):
     ro, rc, rd = oracle_csr(rep, 1)
     assert_csr_equal(off, cols, ro, rc, f"{bits}-bit record hashes")
     assert np.array_equal(deg, rd)
+    assert st["rejected_candidates"] > 0  # the truncation did make candidates to reject
     _, _, _, full = gpu_csr(rep, 1, "deletion")
     assert st["unique_edges"] == full["unique_edges"] > 0
     # and with a partition capacity that sends partitions to the quadratic join
@@ -280,7 +281,7 @@ def test_deletion_two_pass_join_with_rejected_candidates():
     strs = letters + [a + b for a in letters for b in letters] + ["AA", "C", "CAS"]
     rep = from_strings(strs)
     off, cols, deg, st = gpu_csr(rep, 1, "deletion", record_hash_bits=2)
-    assert st["two_pass_join"] == 1
+    assert st["two_pass_join"] == 1 and st["rejected_candidates"] > 0
     ro, rc, _ = oracle_csr(rep, 1)
     assert_csr_equal(off, cols, ro, rc, "dense unique graph, 2-bit record hashes")
 
