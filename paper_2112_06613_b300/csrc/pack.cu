@@ -34,6 +34,7 @@ k_encode(const uint8_t* __restrict__ chars, const int64_t* __restrict__ offs, in
     for (int t = threadIdx.x; t < kBins; t += blockDim.x) cnt[t] = 0;
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * kPackThreads + threadIdx.x;
+    int bin = -1;  // length of a valid string (counted below), -1 otherwise
     if (i < n) {
         const int64_t s = offs[i];
         const int64_t len = offs[i + 1] - s;
@@ -49,12 +50,23 @@ k_encode(const uint8_t* __restrict__ chars, const int64_t* __restrict__ offs, in
             code_err = TCRNET_ETOOLONG;
         } else {
             const uint8_t* p = chars + s;
+            // word by word, up to the last word the string reaches (a 14-letter
+            // string decodes 24 positions, not 48)
+            const int ilen = (int)len;
 #pragma unroll
-            for (int k = 0; k < kMaxLen; ++k) {
-                if (k < len) {
-                    uint64_t v = lut[p[k]];
-                    if (v == 0) code_err = TCRNET_EBADCHAR;
-                    c.w[k / kCodesPerWord] |= v << (5 * (k % kCodesPerWord));
+            for (int w = 0; w < kCanonWords; ++w) {
+                if (w * kCodesPerWord < ilen) {
+                    uint64_t acc = 0;
+#pragma unroll
+                    for (int j = 0; j < kCodesPerWord; ++j) {
+                        const int k = w * kCodesPerWord + j;
+                        if (k < ilen) {
+                            const uint64_t v = lut[p[k]];
+                            if (v == 0) code_err = TCRNET_EBADCHAR;
+                            acc |= v << (5 * j);
+                        }
+                    }
+                    c.w[w] = acc;
                 }
             }
         }
@@ -66,9 +78,12 @@ k_encode(const uint8_t* __restrict__ chars, const int64_t* __restrict__ offs, in
         } else {
             store_canon(canon + i, c);
             lens[i] = (uint8_t)len;
-            atomicAdd(&cnt[len], 1);
+            bin = (int)len;
         }
     }
+    // lengths cluster on a few values: one shared-memory add per length per warp
+    const unsigned peers = __match_any_sync(kFull, bin);
+    if (bin >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cnt[bin], __popc(peers));
     __syncthreads();
     if (blockcnt)
         for (int t = threadIdx.x; t < kBins; t += blockDim.x) blockcnt[(int64_t)t * nblocks + blockIdx.x] = cnt[t];
