@@ -1468,6 +1468,12 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     if (keep_index) TCR_CHECK(ucanon.alloc_owned(sizeof(Canon) * n, s));
     else TCR_CHECK(ucanon.alloc(sizeof(Canon) * n, s));
     TCR_CHECK(ulen.alloc(n, s));
+    k_dedup_insert<<<grid_for(n), kThreads, 0, s>>>(
+        pk.canon_in.as<Canon>(), pk.lens.as<uint8_t>(), n, table.as<int32_t>(), (uint32_t)(S - 1),
+        slot_of.as<int32_t>(), slot_u.as<int32_t>(), d_ucount, ucanon.as<Canon>(), ulen.as<uint8_t>(), d_err);
+    TCR_LAUNCH_CHECK();
+    // the arrays the dedup does not use are allocated and cleared while it runs
+    // (the host's allocation calls were the GPU's wait before it)
     if (keep_index) TCR_CHECK(umult.alloc_owned(sizeof(int32_t) * n, s));
     else TCR_CHECK(umult.alloc(sizeof(int32_t) * n, s));
     if (keep_index) TCR_CHECK(uid.alloc_owned(sizeof(int32_t) * n, s));
@@ -1479,19 +1485,13 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     else TCR_CHECK(members.alloc(sizeof(int32_t) * n, s));
     TCR_CHECK(mpos.alloc(sizeof(int32_t) * n, s));
     TCR_CUDA(cudaMemsetAsync(umult.as<void>(), 0, sizeof(int32_t) * n, s));  // ids >= U stay 0
-    // the join's counters are cleared here too, so that from the dedup on the
-    // kernels of this stream follow one another directly (dependent launches)
-    DevBuf pcnt, wsum;
+    DevBuf pcnt, wsum;  // the join's counters
     TCR_CHECK(wsum.alloc(sizeof(int32_t) * n, s));
     TCR_CUDA(cudaMemsetAsync(wsum.as<void>(), 0, sizeof(int32_t) * n, s));
     if (join) {
         TCR_CHECK(pcnt.alloc(sizeof(int32_t) * P, s));
         TCR_CUDA(cudaMemsetAsync(pcnt.as<void>(), 0, sizeof(int32_t) * P, s));
     }
-    k_dedup_insert<<<grid_for(n), kThreads, 0, s>>>(
-        pk.canon_in.as<Canon>(), pk.lens.as<uint8_t>(), n, table.as<int32_t>(), (uint32_t)(S - 1),
-        slot_of.as<int32_t>(), slot_u.as<int32_t>(), d_ucount, ucanon.as<Canon>(), ulen.as<uint8_t>(), d_err);
-    TCR_LAUNCH_CHECK();
     TCR_CUDA(launch_dependent(k_uid, dim3(grid_for(n)), dim3(kThreads), 0, s, slot_of.as<int32_t>(),
                               slot_u.as<int32_t>(), n, uid.as<int32_t>(), umult.as<int32_t>()));
     note_launch();
