@@ -966,12 +966,12 @@ def run_ours(args):
                 with build() as g:
                     for m_ins in [int(x) for x in args.insert_sizes.split(",") if x]:
                         row = {}
-                        for mode, rebuild in (("merged", False), ("rebuilt", True)):
+                        for mode, kw in (("merged", {"merge": True}), ("rebuilt", {"rebuild": True}), ("auto", {})):
                             ts = []
                             for k in range(4):
                                 torch.cuda.synchronize()
                                 t = time.perf_counter()
-                                g2 = g.extend_flat(ic, io[:m_ins + 1], stream=stream, rebuild=rebuild)
+                                g2 = g.extend_flat(ic, io[:m_ins + 1], stream=stream, **kw)
                                 torch.cuda.synchronize()
                                 dt = 1e3 * (time.perf_counter() - t)
                                 if k == 0:
@@ -983,11 +983,14 @@ def run_ours(args):
                             if mode == "merged":
                                 row["merged"] = st2["merged_inserts"] == 1
                                 row["nnz_after"] = st2["nnz"]
+                            if mode == "auto":
+                                row["auto_merged"] = st2["merged_inserts"] == 1
                         row["speedup"] = row["rebuilt_ms"] / row["merged_ms"]
                         ins[str(m_ins)] = row
                 line["insert"] = {"resident_strings": n, "sizes": ins,
                                   "timing": "host time of tcrnet_extend (copy-on-write insert) with a stream sync, median of 3 "
-                                            "after 1 warm-up; new strings already in device memory"}
+                                            "after 1 warm-up; new strings already in device memory; merged = "
+                                            "insert_rebuild 2, rebuilt = 1, auto = 0 (the measured rule)"}
             except Exception as exc:  # keep the line: record the failed leg
                 line.setdefault("leg_errors", {})["insert"] = repr(exc)
         if "analytics" in legs:

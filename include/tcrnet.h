@@ -97,11 +97,13 @@ typedef struct tcrnet_options {
                                  TCRNET_ENOMEM after releasing what it holds;
                                  0 = off */
     int32_t insert_rebuild;   /* inserts (tcrnet_insert_ex, tcrnet_extend): 1 = rebuild
-                                 the grown repertoire from scratch; 0 (default) =
-                                 merge the new strings into the handle's network and
-                                 index where that is cheaper (deletion builds with
-                                 l_max = 1, inserts of at most 1/32 of the resident
-                                 strings), which gives the same network */
+                                 the grown repertoire from scratch; 2 = merge the new
+                                 strings into the handle's network and index whenever
+                                 the index can take them (deletion builds with
+                                 l_max = 1, partitions not overfull); 0 (default) =
+                                 merge where that is the faster of the two (measured
+                                 rule: see tcrnet_insert_flat). Every way gives the
+                                 same network; other values: TCRNET_EINVAL */
     int32_t link_attempts;    /* testing (tcrnet_components_ex): attempts each edge of
                                  the union-find may make to link its two roots before
                                  the call gives up with TCRNET_ETIMEOUT; 0 = default
@@ -264,11 +266,13 @@ tcrnet_status tcrnet_query(tcrnet_handle h, const char *const *queries, int64_t 
  * the concatenated input would (node ids of existing strings are unchanged);
  * previously returned device pointers (tcrnet_csr_device) become invalid. The
  * update is computed on the device from the handle's packed strings: a deletion
- * build (l_max = 1) merges an insert of at most n/32 strings into its network
- * and query index (the new strings' closed neighbourhoods from a query of the
- * grown index, old rows grown at their ends); other inserts rebuild the grown
- * repertoire (options.insert_rebuild forces that). Both give the network of a
- * fresh build of the concatenation. On failure
+ * build (l_max = 1) merges the new strings into its network and query index
+ * (the new strings' closed neighbourhoods from a query of the grown index, old
+ * rows grown at their ends) where that is faster than a rebuild, by a rule
+ * measured on a B300: from 7e5 resident strings for inserts of up to n/128,
+ * from 1.5e6 for inserts of up to n/32; other inserts rebuild the grown
+ * repertoire (options.insert_rebuild forces either way). Both give the network
+ * of a fresh build of the concatenation. On failure
  * (bad string: its index within the new batch is reported) the handle keeps its
  * previous network. Not for query-result handles (ESTATE). Callers must not use
  * the handle from another thread during the call.

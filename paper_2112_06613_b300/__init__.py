@@ -222,7 +222,8 @@ def make_options(method="auto", device=None, stream=None, profile=False, force_o
     o.partition_cap = int(partition_cap)
     o.partition_target = int(partition_target)
     o.fail_alloc_at = int(fail_alloc_at)
-    o.insert_rebuild = 1 if insert_rebuild else 0
+    # False/0: automatic; True/1: rebuild; "merge"/2: merge whenever the index allows
+    o.insert_rebuild = 2 if insert_rebuild in ("merge", 2) else (1 if insert_rebuild else 0)
     o.link_attempts = int(link_attempts)
     o.deletion_max_n = int(deletion_max_n)
     o.record_hash_bits = int(record_hash_bits)
@@ -362,14 +363,19 @@ class Graph:
         arr = (ctypes.c_char_p * max(len(enc), 1))(*enc)
         _check(lib.tcrnet_insert(self._h, arr, len(enc)), "tcrnet_insert")
 
-    def insert_flat(self, chars, offsets, stream=None, profile=False, rebuild=False, fail_alloc_at=0):
+    def insert_flat(self, chars, offsets, stream=None, profile=False, rebuild=False, fail_alloc_at=0,
+                    merge=False):
         """Append strings in flat layout (numpy or torch, host or device) as new nodes.
-        A deletion build at l_max = 1 merges up to n/32 of them into its network
-        and index; other inserts, and rebuild=True, rebuild the grown repertoire
-        (same network)."""
+        A deletion build at l_max = 1 merges them into its network and index where
+        that is faster than a rebuild; rebuild=True always rebuilds the grown
+        repertoire, merge=True merges whenever the index can take the strings.
+        Every way gives the same network."""
+        if rebuild and merge:
+            raise ValueError("rebuild and merge exclude each other")
         lib = load_library()
         cp, op, m, mem, keep = _flat_args(chars, offsets)
-        opt = make_options(stream=stream, profile=profile, insert_rebuild=rebuild, fail_alloc_at=fail_alloc_at)
+        opt = make_options(stream=stream, profile=profile, insert_rebuild="merge" if merge else bool(rebuild),
+                           fail_alloc_at=fail_alloc_at)
         st = lib.tcrnet_insert_ex(self._h, cp, op, m, mem, ctypes.byref(opt))
         del keep
         _check(st, "tcrnet_insert_ex")
@@ -378,13 +384,17 @@ class Graph:
         """Checkpoint this handle (network, resident strings, query index) to a file."""
         _check(load_library().tcrnet_save(self._h, os.fsencode(path)), "tcrnet_save")
 
-    def extend_flat(self, chars, offsets, stream=None, profile=False, rebuild=False, fail_alloc_at=0) -> "Graph":
+    def extend_flat(self, chars, offsets, stream=None, profile=False, rebuild=False, fail_alloc_at=0,
+                    merge=False) -> "Graph":
         """Copy-on-write insert: a new Graph of this one's strings plus the new ones;
-        this Graph is unchanged and may keep serving queries meanwhile. rebuild as
-        for insert_flat."""
+        this Graph is unchanged and may keep serving queries meanwhile. rebuild and
+        merge as for insert_flat."""
+        if rebuild and merge:
+            raise ValueError("rebuild and merge exclude each other")
         lib = load_library()
         cp, op, m, mem, keep = _flat_args(chars, offsets)
-        opt = make_options(stream=stream, profile=profile, insert_rebuild=rebuild, fail_alloc_at=fail_alloc_at)
+        opt = make_options(stream=stream, profile=profile, insert_rebuild="merge" if merge else bool(rebuild),
+                           fail_alloc_at=fail_alloc_at)
         h = ctypes.c_void_p()
         st = lib.tcrnet_extend(self._h, cp, op, m, mem, ctypes.byref(opt), ctypes.byref(h))
         del keep

@@ -115,6 +115,30 @@ void* pinned_scratch_device() {
     return pinned_scratch() ? t_pinned.dev : nullptr;
 }
 
+tcrnet_status read_back(cudaStream_t s, int count, const void* const* src, void* const* dst, const size_t* bytes) {
+    size_t total = 0;
+    for (int k = 0; k < count; ++k) total += (bytes[k] + 15) & ~size_t(15);
+    uint8_t* pin = static_cast<uint8_t*>(pinned_scratch());
+    if (!pin || total > kPinnedScratchBytes) {
+        for (int k = 0; k < count; ++k)
+            TCR_CUDA(cudaMemcpyAsync(dst[k], src[k], bytes[k], cudaMemcpyDeviceToHost, s));
+        TCR_CUDA(cudaStreamSynchronize(s));
+        return TCRNET_OK;
+    }
+    size_t at = 0;
+    for (int k = 0; k < count; ++k) {
+        TCR_CUDA(cudaMemcpyAsync(pin + at, src[k], bytes[k], cudaMemcpyDeviceToHost, s));
+        at += (bytes[k] + 15) & ~size_t(15);
+    }
+    TCR_CUDA(cudaStreamSynchronize(s));
+    at = 0;
+    for (int k = 0; k < count; ++k) {
+        std::memcpy(dst[k], pin + at, bytes[k]);
+        at += (bytes[k] + 15) & ~size_t(15);
+    }
+    return TCRNET_OK;
+}
+
 const SideStream* leased_side_stream() {
     DeviceArena* a = t_arena;
     if (!a) return nullptr;
@@ -814,10 +838,18 @@ namespace {
 // Largest mean records per partition that a merged insert may leave behind
 // (builds aim at 24 or 32).
 constexpr int64_t kMergeMaxPartitionFill = 48;
-// A merge copies the whole network once and queries the new strings; past
-// about 1/32 of the repertoire a rebuild is as fast (measured on a B300 with
-// 8e5 and 2e6 resident strings).
-constexpr int64_t kMergeMaxShare = 32;
+// A merge copies the whole network and index once, queries the new strings
+// and runs about 60 small steps (~0.5 ms whatever the size); a rebuild grows
+// faster than linearly with the repertoire. Measured on a B300 (synthetic
+// repertoires, l_max = 1, copy-on-write inserts): rebuilds win below ~7e5
+// resident strings (3e5: 0.39 against 0.59 ms), merges of up to 1/128 win from
+// there (8e5 and 1,000 new strings: 0.80 against 0.83 ms), and from 1.5e6
+// merges of up to 1/32 (2e6 and 62,500 new strings: 1.94 against 2.80 ms).
+bool merge_is_faster(int64_t n_old, int64_t m) {
+    if (n_old >= 1500000) return m * 32 <= n_old;
+    if (n_old >= 700000) return m * 128 <= n_old;
+    return false;
+}
 
 // The network of h's strings followed by m new ones, as a new graph; h is only
 // read (its resident strings, network and index), so queries on h may run
@@ -837,6 +869,7 @@ tcrnet_status extend_impl(tcrnet_handle h, const uint8_t* chars, const int64_t* 
         opt.profile = opt_in->profile;
         opt.fail_alloc_at = opt_in->fail_alloc_at;
         opt.insert_rebuild = opt_in->insert_rebuild;
+        if (opt.insert_rebuild < 0 || opt.insert_rebuild > 2) return TCRNET_EINVAL;
         opt.deletion_max_n = opt_in->deletion_max_n;
         if (opt.deletion_max_n < 0) return TCRNET_EINVAL;
     }
@@ -897,9 +930,10 @@ tcrnet_status extend_impl(tcrnet_handle h, const uint8_t* chars, const int64_t* 
     // original record count; a rebuild re-sizes them) and the insert is small
     // next to the repertoire.
     const DeletionIndex& ix = h->ix;
-    const bool merge = !tile && opt.insert_rebuild == 0 && m > 0 && m * kMergeMaxShare <= n_old && ix.valid() && ix.uid &&
-                       ix.n == n_old && h->threshold == 1 && N <= deletion_limit(opt) &&
-                       ix.R + m + pn.lensum <= kMergeMaxPartitionFill * ix.P;
+    const bool can_merge = !tile && opt.insert_rebuild != 1 && m > 0 && ix.valid() && ix.uid && ix.n == n_old &&
+                           h->threshold == 1 && N <= deletion_limit(opt) &&
+                           ix.R + m + pn.lensum <= kMergeMaxPartitionFill * ix.P;
+    const bool merge = can_merge && (opt.insert_rebuild == 2 || merge_is_faster(n_old, m));
     tcrnet_graph* g = new (std::nothrow) tcrnet_graph();
     if (!g) return TCRNET_ENOMEM;
     std::memset(&g->stats, 0, sizeof(g->stats));

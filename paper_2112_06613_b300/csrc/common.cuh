@@ -201,6 +201,11 @@ void* pinned_scratch();
 // group of readback values there directly: one small kernel instead of one
 // copy per value. nullptr if unavailable.
 void* pinned_scratch_device();
+// count small device values (bytes[k] bytes from device address src[k] to host
+// address dst[k]) read back with one stream synchronisation, through the
+// page-locked scratch (pageable copies when it cannot be had or the values do
+// not fit in it).
+tcrnet_status read_back(cudaStream_t s, int count, const void* const* src, void* const* dst, const size_t* bytes);
 
 // Events for the optional phase timing, recycled through a per-device pool so
 // that a profiled build does not create and destroy events on its critical path.

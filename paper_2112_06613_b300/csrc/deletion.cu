@@ -2384,9 +2384,12 @@ tcrnet_status deletion_query(const DeletionIndex& ix, const Packed& q, int T, De
     TCR_CHECK(scan_exclusive_i64(qcnt.as<int64_t>(), off64.as<int64_t>(), m, s));
     int64_t nnz = 0;
     unsigned long long nh = ~0ull;
-    TCR_CUDA(cudaMemcpyAsync(&nnz, off64.as<int64_t>() + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    if (hits) TCR_CUDA(cudaMemcpyAsync(&nh, hitcur.as<void>(), sizeof(nh), cudaMemcpyDeviceToHost, s));
-    TCR_CUDA(cudaStreamSynchronize(s));
+    {
+        const void* src[2] = {off64.as<int64_t>() + m, hits ? hitcur.as<void>() : nullptr};
+        void* dst[2] = {&nnz, &nh};
+        const size_t bytes[2] = {sizeof(int64_t), sizeof(nh)};
+        TCR_CHECK(read_back(s, hits ? 2 : 1, src, dst, bytes));
+    }
     TCR_CHECK(cols.alloc_owned(sizeof(int32_t) * nnz, s));
     TCR_CHECK(count.alloc_owned(sizeof(int32_t) * m, s));
     if (nnz > 0) {
@@ -2558,29 +2561,73 @@ __global__ void k_ins_new_members(const int32_t* __restrict__ nuid, int64_t m, c
     else nm_list[nm_off[r] + atomicAdd(&nm_cur[r], 1)] = (int32_t)j;
 }
 
+// Number of entries of the ascending array a[0 .. K) that are <= x: a 32-way
+// search (each step probes 32 evenly spaced entries, whose hits form a prefix),
+// taken by the whole warp, which gets the result in every lane.
+__device__ __forceinline__ int64_t warp_count_le(const int64_t* __restrict__ a, int64_t K, int64_t x) {
+    const int lane = threadIdx.x & 31;
+    int64_t lo = 0, hi = K;  // a[< lo] <= x < a[>= hi]
+    while (hi - lo > 32) {
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t idx = lo + lane * step;
+        const int c = __popc(__ballot_sync(kFull, idx < hi && a[idx] <= x));
+        if (c == 0) return lo;
+        const int64_t nlo = lo + (int64_t)(c - 1) * step + 1;
+        hi = lo + (int64_t)c * step < hi ? lo + (int64_t)c * step : hi;
+        lo = nlo;
+    }
+    return lo + __popc(__ballot_sync(kFull, lo + lane < hi && a[lo + lane] <= x));
+}
+
+// The closed rows' entries [0, nr) are taken in chunks of kRowChunk consecutive
+// entries, a warp per chunk, so that a row of many members (a string shared by
+// a large part of the repertoire) is spread over many warps. A warp finds the
+// row of its first entry by warp_count_le; each lane then steps forward to the
+// row of its own entry (rows are consecutive), and lane 31's row starts the
+// next 32 entries.
+constexpr int kRowChunk = 256;
+
+template <typename Body>
+__device__ __forceinline__ void for_row_entries(const int64_t* __restrict__ roff, int64_t nrows, int64_t nr,
+                                                Body body) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t chunks = (nr + kRowChunk - 1) / kRowChunk;
+    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < chunks; c += nw) {
+        const int64_t e0 = c * kRowChunk;
+        const int64_t e1 = e0 + kRowChunk < nr ? e0 + kRowChunk : nr;
+        int64_t r = warp_count_le(roff + 1, nrows, e0);
+        for (int64_t t0 = e0; t0 < e1; t0 += 32) {
+            const int64_t e = t0 + lane;
+            int64_t rl = r;
+            if (e < e1)
+                while (roff[rl + 1] <= e) ++rl;  // e < roff[nrows]: ends within the rows
+            body(e < e1, e, rl);
+            r = __shfl_sync(kFull, rl, 31);
+        }
+    }
+}
+
 // Edges between distinct strings that involve a fresh one: for each fresh
 // distinct string w (a row of its closed neighbourhood), every other distinct
 // string x in the row (all members of a neighbour are listed; its first member
 // stands for it); a pair of fresh strings is taken from the smaller id's side.
 __global__ void k_ins_edges(const int64_t* __restrict__ roff, const int32_t* __restrict__ rcols, int64_t nrep,
-                            const int32_t* __restrict__ rep_u, const int32_t* __restrict__ uid,
+                            int64_t nr, const int32_t* __restrict__ rep_u, const int32_t* __restrict__ uid,
                             const int64_t* __restrict__ mem_off, const int32_t* __restrict__ members, int64_t U0,
                             int2* __restrict__ out, unsigned long long* __restrict__ cur, int64_t cap,
                             int* __restrict__ err) {
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrep; r += nw) {
+    for_row_entries(roff, nrep, nr, [&](bool ok, int64_t e, int64_t r) {
+        if (!ok) return;
         const int32_t w = rep_u[r];
-        if (w < U0) continue;  // a resident string: its edges are known
-        for (int64_t e = roff[r] + lane; e < roff[r + 1]; e += 32) {
-            const int32_t i = rcols[e];
-            const int32_t x = uid[i];
-            if (x == w || (x >= U0 && x < w) || members[mem_off[x]] != i) continue;
-            const unsigned long long slot = atomicAdd(cur, 1ull);
-            if ((int64_t)slot < cap) out[slot] = make_int2(w, x);
-            else atomicExch(err, 1);
-        }
-    }
+        if (w < U0) return;  // a resident string: its edges are known
+        const int32_t i = rcols[e];
+        const int32_t x = uid[i];
+        if (x == w || (x >= U0 && x < w) || members[mem_off[x]] != i) return;
+        const unsigned long long slot = atomicAdd(cur, 1ull);
+        if ((int64_t)slot < cap) out[slot] = make_int2(w, x);
+        else atomicExch(err, 1);
+    });
 }
 
 // New entries of old rows. An old node i gains every new member of every
@@ -2589,60 +2636,54 @@ __global__ void k_ins_edges(const int64_t* __restrict__ roff, const int32_t* __r
 // once per x (its "tail") and copied to each old member of x. A closed row
 // stands for x by x's first old member. dcnt[x] = tail length of x.
 __global__ void k_ins_tail_count(const int64_t* __restrict__ roff, const int32_t* __restrict__ rcols, int64_t nrep,
-                                 const int32_t* __restrict__ nm_cnt, int64_t n0, const int32_t* __restrict__ uid,
-                                 const int64_t* __restrict__ mem_off_old, const int32_t* __restrict__ members_old,
-                                 int32_t* __restrict__ dcnt) {
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrep; r += nw) {
-        const int32_t c = nm_cnt[r];
-        for (int64_t e = roff[r] + lane; e < roff[r + 1]; e += 32) {
-            const int32_t i = rcols[e];
-            if (i >= n0) continue;
-            const int32_t x = uid[i];
-            if (members_old[mem_off_old[x]] == i) atomicAdd(&dcnt[x], c);
-        }
-    }
+                                 int64_t nr, const int32_t* __restrict__ nm_cnt, int64_t n0,
+                                 const int32_t* __restrict__ uid, const int64_t* __restrict__ mem_off_old,
+                                 const int32_t* __restrict__ members_old, int32_t* __restrict__ dcnt) {
+    for_row_entries(roff, nrep, nr, [&](bool ok, int64_t e, int64_t r) {
+        if (!ok) return;
+        const int32_t i = rcols[e];
+        if (i >= n0) return;
+        const int32_t x = uid[i];
+        if (members_old[mem_off_old[x]] == i) atomicAdd(&dcnt[x], nm_cnt[r]);
+    });
 }
 
 // Tails of the old distinct strings: x takes n0 + j for the new members j of
 // every closed row that stands for it, at slots of its tail (sorted
-// afterwards). Few new members: a lane per row entry; many: 32 row entries
-// take their slots together, then the warp writes the members of each.
+// afterwards). A lane writes up to 4 new members itself; longer lists are
+// written by the whole warp, one entry's list after another.
 __global__ void k_ins_tails(const int64_t* __restrict__ roff, const int32_t* __restrict__ rcols, int64_t nrep,
-                            const int64_t* __restrict__ nm_off, const int32_t* __restrict__ nm_list, int64_t n0,
-                            const int32_t* __restrict__ uid, const int64_t* __restrict__ mem_off_old,
+                            int64_t nr, const int64_t* __restrict__ nm_off, const int32_t* __restrict__ nm_list,
+                            int64_t n0, const int32_t* __restrict__ uid, const int64_t* __restrict__ mem_off_old,
                             const int32_t* __restrict__ members_old, const int64_t* __restrict__ dtoff,
                             int32_t* __restrict__ dcur, int32_t* __restrict__ dtcols) {
     const int lane = threadIdx.x & 31;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrep; r += nw) {
-        const int64_t a = nm_off[r];
-        const int32_t c = (int32_t)(nm_off[r + 1] - a);
-        const int64_t e0 = roff[r], e1 = roff[r + 1];
-        for (int64_t e = e0; e < e1; e += 32) {
-            int64_t base = -1;
-            if (e + lane < e1) {
-                const int32_t i = rcols[e + lane];
-                if (i < n0) {
-                    const int32_t x = uid[i];
-                    if (members_old[mem_off_old[x]] == i) base = dtoff[x] + atomicAdd(&dcur[x], c);
-                }
-            }
-            if (c <= 4) {
-                if (base >= 0)
-                    for (int32_t k = 0; k < c; ++k) dtcols[base + k] = (int32_t)(n0 + nm_list[a + k]);
-            } else {
-                unsigned todo = __ballot_sync(kFull, base >= 0);
-                while (todo) {
-                    const int t = __ffs(todo) - 1;
-                    todo &= todo - 1;
-                    const int64_t tb = __shfl_sync(kFull, base, t);
-                    for (int32_t k = lane; k < c; k += 32) dtcols[tb + k] = (int32_t)(n0 + nm_list[a + k]);
+    for_row_entries(roff, nrep, nr, [&](bool ok, int64_t e, int64_t r) {
+        int64_t base = -1, a = 0;
+        int32_t c = 0;
+        if (ok) {
+            const int32_t i = rcols[e];
+            if (i < n0) {
+                const int32_t x = uid[i];
+                if (members_old[mem_off_old[x]] == i) {
+                    a = nm_off[r];
+                    c = (int32_t)(nm_off[r + 1] - a);
+                    base = dtoff[x] + atomicAdd(&dcur[x], c);
                 }
             }
         }
-    }
+        if (base >= 0 && c <= 4)
+            for (int32_t k = 0; k < c; ++k) dtcols[base + k] = (int32_t)(n0 + nm_list[a + k]);
+        unsigned todo = __ballot_sync(kFull, base >= 0 && c > 4);
+        while (todo) {
+            const int t = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t tb = __shfl_sync(kFull, base, t);
+            const int64_t ta = __shfl_sync(kFull, a, t);
+            const int32_t tc = __shfl_sync(kFull, c, t);
+            for (int32_t k = lane; k < tc; k += 32) dtcols[tb + k] = (int32_t)(n0 + nm_list[ta + k]);
+        }
+    });
 }
 
 // Degrees of the grown network (old node: + its string's tail; new node: its
@@ -2760,24 +2801,10 @@ __global__ void __launch_bounds__(kThreads) k_shifted_copy(const T* __restrict__
     const int64_t b0 = gw * per;
     const int64_t b1 = b0 + per < count ? b0 + per : count;
     if (b0 >= b1) return;  // warp-uniform
-    // first k with cuts[k] > b0
-    int64_t lo = 0, hi = K;
-    while (hi - lo > 32) {
-        const int64_t step = (hi - lo + 31) / 32;
-        const int64_t idx = lo + lane * step;
-        const int c = __popc(__ballot_sync(kFull, idx < hi && cuts[idx] <= b0));  // a prefix of the probes
-        if (c == 0) {
-            hi = lo;
-            break;
-        }
-        const int64_t nlo = lo + (int64_t)(c - 1) * step + 1;
-        hi = lo + (int64_t)c * step < hi ? lo + (int64_t)c * step : hi;
-        lo = nlo;
-    }
-    if (hi > lo) lo += __popc(__ballot_sync(kFull, lo + lane < hi && cuts[lo + lane] <= b0));
-    // 128 consecutive elements per step (loads first); each lane advances a copy
-    // of the warp's piece index to its own element, lane 31's result carries on
-    int64_t k = lo;
+    // 128 consecutive elements per step (loads first), starting in the piece
+    // of b0 (the first k with cuts[k] > b0); each lane advances a copy of the
+    // warp's piece index to its own element, lane 31's result carries on
+    int64_t k = warp_count_le(cuts, K, b0);
     for (int64_t t0 = b0; t0 < b1; t0 += 128) {
         T v[4];
 #pragma unroll
@@ -2945,8 +2972,12 @@ tcrnet_status deletion_insert(const DeletionIndex& ix, const CsrView& g, const P
     TCR_LAUNCH_CHECK();
     TCR_CHECK(scan_exclusive_i32_to_i64(rflag.as<int32_t>(), rpos.as<int64_t>(), m, s));
     int64_t nrep = 0;
-    TCR_CUDA(cudaMemcpyAsync(&nrep, rpos.as<int64_t>() + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    TCR_CUDA(cudaStreamSynchronize(s));
+    {
+        const void* src[1] = {rpos.as<int64_t>() + m};
+        void* dst[1] = {&nrep};
+        const size_t bytes[1] = {sizeof(int64_t)};
+        TCR_CHECK(read_back(s, 1, src, dst, bytes));
+    }
     if (nrep <= 0 || nrep > m) return TCRNET_EDEVICE;
     Packed qr;  // the representatives' strings, input order
     qr.n = nrep;
@@ -2994,8 +3025,9 @@ tcrnet_status deletion_insert(const DeletionIndex& ix, const CsrView& g, const P
     TCR_CHECK(uedges.alloc_owned(sizeof(int2) * (E_cap > 0 ? E_cap : 1), s));
     if (E0 > 0)
         TCR_CUDA(cudaMemcpyAsync(uedges.as<void>(), ix.uedges, sizeof(int2) * E0, cudaMemcpyDeviceToDevice, s));
-    const unsigned rgrid = (unsigned)std::min<int64_t>(ceil_div(nrep, kWarps), (int64_t)num_sms * 16);
-    k_ins_edges<<<rgrid, kThreads, 0, s>>>(roff.as<int64_t>(), rcols.as<int32_t>(), nrep, rep_u.as<int32_t>(),
+    const unsigned rgrid =
+        (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ceil_div(nr, kRowChunk), kWarps), (int64_t)num_sms * 16));
+    k_ins_edges<<<rgrid, kThreads, 0, s>>>(roff.as<int64_t>(), rcols.as<int32_t>(), nrep, nr, rep_u.as<int32_t>(),
                                            uid.as<int32_t>(), mem_off.as<int64_t>(), members.as<int32_t>(), U0,
                                            uedges.as<int2>() + E0, d_ecur, E_cap - E0, d_err + 1);
     TCR_LAUNCH_CHECK();
@@ -3013,7 +3045,7 @@ tcrnet_status deletion_insert(const DeletionIndex& ix, const CsrView& g, const P
     TCR_CHECK(off64.alloc_owned(sizeof(int64_t) * (N + 1), s));
     TCR_CUDA(cudaMemsetAsync(dcnt.as<void>(), 0, sizeof(int32_t) * U0, s));
     TCR_CUDA(cudaMemsetAsync(dcur.as<void>(), 0, sizeof(int32_t) * U0, s));
-    k_ins_tail_count<<<rgrid, kThreads, 0, s>>>(roff.as<int64_t>(), rcols.as<int32_t>(), nrep, nm_cnt.as<int32_t>(),
+    k_ins_tail_count<<<rgrid, kThreads, 0, s>>>(roff.as<int64_t>(), rcols.as<int32_t>(), nrep, nr, nm_cnt.as<int32_t>(),
                                                 n0, uid.as<int32_t>(), ix.mem_off, ix.members, dcnt.as<int32_t>());
     TCR_LAUNCH_CHECK();
     TCR_CHECK(scan_exclusive_i32_to_i64(dcnt.as<int32_t>(), dtoff.as<int64_t>(), U0, s));
@@ -3024,16 +3056,18 @@ tcrnet_status deletion_insert(const DeletionIndex& ix, const CsrView& g, const P
     TCR_CHECK(scan_exclusive_i32_to_i64(delta.as<int32_t>(), toff.as<int64_t>(), n0, s));
     TCR_CHECK(scan_exclusive_i32_to_i64(deg.as<int32_t>(), off64.as<int64_t>(), N, s));
     int64_t sizes[3] = {0, 0, 0};  // new entries of old rows, entries of the grown network, tail entries
-    TCR_CUDA(cudaMemcpyAsync(&sizes[0], toff.as<int64_t>() + n0, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    TCR_CUDA(cudaMemcpyAsync(&sizes[1], off64.as<int64_t>() + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    TCR_CUDA(cudaMemcpyAsync(&sizes[2], dtoff.as<int64_t>() + U0, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    TCR_CUDA(cudaStreamSynchronize(s));
+    {
+        const void* src[3] = {toff.as<int64_t>() + n0, off64.as<int64_t>() + N, dtoff.as<int64_t>() + U0};
+        void* dst[3] = {&sizes[0], &sizes[1], &sizes[2]};
+        const size_t bytes[3] = {sizeof(int64_t), sizeof(int64_t), sizeof(int64_t)};
+        TCR_CHECK(read_back(s, 3, src, dst, bytes));
+    }
     const int64_t n_tail = sizes[0], nnz = sizes[1], n_dtail = sizes[2];
     if (n_tail < 0 || n_dtail < 0 || nnz < g.nnz + n_tail) return TCRNET_EDEVICE;
     TCR_CHECK(dtcols.alloc(sizeof(int32_t) * (n_dtail > 0 ? n_dtail : 1), s));
     TCR_CHECK(cols.alloc_owned(sizeof(int32_t) * nnz, s));
     if (n_dtail > 0) {
-        k_ins_tails<<<rgrid, kThreads, 0, s>>>(roff.as<int64_t>(), rcols.as<int32_t>(), nrep, nm_off.as<int64_t>(),
+        k_ins_tails<<<rgrid, kThreads, 0, s>>>(roff.as<int64_t>(), rcols.as<int32_t>(), nrep, nr, nm_off.as<int64_t>(),
                                                nm_list.as<int32_t>(), n0, uid.as<int32_t>(), ix.mem_off, ix.members,
                                                dtoff.as<int64_t>(), dcur.as<int32_t>(), dtcols.as<int32_t>());
         TCR_LAUNCH_CHECK();
@@ -3058,11 +3092,12 @@ tcrnet_status deletion_insert(const DeletionIndex& ix, const CsrView& g, const P
     unsigned long long h_cnt[2] = {0, 0};
     int h_err[2] = {0, 0};
     int64_t h_R = 0, h_nnz = 0;
-    TCR_CUDA(cudaMemcpyAsync(h_cnt, d_fresh, sizeof(h_cnt), cudaMemcpyDeviceToHost, s));
-    TCR_CUDA(cudaMemcpyAsync(h_err, d_err, sizeof(h_err), cudaMemcpyDeviceToHost, s));
-    TCR_CUDA(cudaMemcpyAsync(&h_R, poff.as<int64_t>() + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    TCR_CUDA(cudaMemcpyAsync(&h_nnz, off64.as<int64_t>() + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    TCR_CUDA(cudaStreamSynchronize(s));
+    {
+        const void* src[4] = {d_fresh, d_err, poff.as<int64_t>() + P, off64.as<int64_t>() + N};
+        void* dst[4] = {h_cnt, h_err, &h_R, &h_nnz};
+        const size_t bytes[4] = {sizeof(h_cnt), sizeof(h_err), sizeof(int64_t), sizeof(int64_t)};
+        TCR_CHECK(read_back(s, 4, src, dst, bytes));
+    }
     if (h_err[0] || h_err[1] || h_nnz != nnz || h_R > R_bound) return TCRNET_EDEVICE;
 
     out.off64 = std::move(off64);

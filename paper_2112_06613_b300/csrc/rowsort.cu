@@ -405,8 +405,12 @@ tcrnet_status sort_rows(const int64_t* off, int32_t* cols, int64_t n, cudaStream
     if (!run_block || (known && max_len <= kBlockCap)) return TCRNET_OK;  // no row can be listed as huge
     const size_t smem = sizeof(int32_t) * kBlockCap;
     int h_huge = 0;
-    TCR_CUDA(cudaMemcpyAsync(&h_huge, cnt + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
-    TCR_CUDA(cudaStreamSynchronize(s));
+    {
+        const void* src[1] = {cnt + 2};
+        void* dst[1] = {&h_huge};
+        const size_t bytes[1] = {sizeof(int)};
+        TCR_CHECK(read_back(s, 1, src, dst, bytes));
+    }
     if (h_huge == 0) return TCRNET_OK;
     // Rare: rows longer than one shared-memory block.
     std::vector<int32_t> huge(h_huge);

@@ -58,7 +58,7 @@ def test_merged_insert_edge_cases():
     with fresh(base) as g:
         assert g.stats()["merged_inserts"] == 0
         b = from_strings(batch)
-        g.insert_flat(b.chars, b.offsets)
+        g.insert_flat(b.chars, b.offsets, merge=True)
         assert g.stats()["merged_inserts"] == 1
         assert_same_as_fresh(g, base + batch, "edge cases")
 
@@ -77,7 +77,7 @@ def test_many_small_merged_inserts_and_queries():
             batch = pool[k:k + size]
             k += size
             b = from_strings(batch)
-            g.insert_flat(b.chars, b.offsets)
+            g.insert_flat(b.chars, b.offsets, merge=True)
             strs += batch
             assert g.stats()["merged_inserts"] == step + 1
             if step % 8 == 7:
@@ -103,7 +103,7 @@ def test_merged_insert_analytics_and_checkpoint(tmp_path):
         ref_knn = f.neighbor_degree()
         ref_hist = f.degree_histogram()
     with fresh(base) as g:
-        g.insert_flat(b.chars, b.offsets)
+        g.insert_flat(b.chars, b.offsets, merge=True)
         assert g.stats()["merged_inserts"] == 1
         comp = g.components(keep)
         assert np.array_equal(comp[0], ref_comp[0]) and comp[1:] == ref_comp[1:]
@@ -118,7 +118,7 @@ def test_merged_insert_analytics_and_checkpoint(tmp_path):
         assert_same_as_fresh(h, strs, "restored merged handle", oracle_check=False)
         more = generate(200, seed=207, template_seed=205).strings()
         mb = from_strings(more)
-        h.insert_flat(mb.chars, mb.offsets)
+        h.insert_flat(mb.chars, mb.offsets, merge=True)
         assert h.stats()["merged_inserts"] == 2
         assert_same_as_fresh(h, strs + more, "insert after restore")
 
@@ -129,7 +129,7 @@ def test_merged_insert_int64_offsets_and_rebuild_option():
     b = from_strings(add)
     rep = from_strings(base)
     with tn.tcrnet_build_flat(rep.chars, rep.offsets, 1, method="deletion", force_offsets64=True) as g:
-        g.insert_flat(b.chars, b.offsets)
+        g.insert_flat(b.chars, b.offsets, merge=True)
         assert g.info()[2] == 1 and g.stats()["merged_inserts"] == 1
         assert_same_as_fresh(g, base + add, "int64 offsets", oracle_check=False)
     with fresh(base) as g:
@@ -137,7 +137,7 @@ def test_merged_insert_int64_offsets_and_rebuild_option():
         assert g.stats()["merged_inserts"] == 0
         merged = None
         with fresh(base) as g2:
-            with g2.extend_flat(b.chars, b.offsets) as g3:
+            with g2.extend_flat(b.chars, b.offsets, merge=True) as g3:
                 assert g3.stats()["merged_inserts"] == 1
                 merged = csr_of(g3)
             # copy-on-write: the source handle is unchanged
@@ -148,13 +148,13 @@ def test_merged_insert_int64_offsets_and_rebuild_option():
 
 def test_large_insert_rebuilds():
     base = generate_config1(3000, seed=210).strings()
-    add = generate_config1(4000, seed=211).strings()  # above 1/32 of the repertoire: rebuilt
+    add = generate_config1(4000, seed=211).strings()  # larger than the repertoire: rebuilt
     b = from_strings(add)
     with fresh(base) as g:
         small = from_strings(add[:80])
-        g.insert_flat(small.chars, small.offsets)
+        g.insert_flat(small.chars, small.offsets, merge=True)
         assert g.stats()["merged_inserts"] == 1
-        g.insert_flat(b.chars, b.offsets)
+        g.insert_flat(b.chars, b.offsets)  # automatic choice
         assert g.stats()["merged_inserts"] == 0
         assert_same_as_fresh(g, base + add[:80] + add, "rebuild after merge", oracle_check=False)
 
@@ -172,7 +172,7 @@ def test_merged_insert_allocation_failures_keep_the_handle():
         before = csr_of(g)
         failures = 0
         for k in range(1, 400):
-            opt = tn.make_options(fail_alloc_at=k)
+            opt = tn.make_options(fail_alloc_at=k, insert_rebuild="merge")
             st = lib.tcrnet_insert_ex(g.handle, b.chars.ctypes.data, b.offsets.ctypes.data, b.n, tn.HOST,
                                       ctypes.byref(opt))
             if st == tn.OK:
@@ -194,7 +194,7 @@ def test_merged_insert_of_resident_strings_only():
     b = from_strings(add)
     with fresh(base) as g:
         n_unique = g.stats()["n_unique"]
-        g.insert_flat(b.chars, b.offsets)
+        g.insert_flat(b.chars, b.offsets, merge=True)
         st = g.stats()
         assert st["merged_inserts"] == 1 and st["n_unique"] == n_unique
         assert_same_as_fresh(g, base + add, "resident strings only")
@@ -216,7 +216,7 @@ def test_random_merged_inserts_over_a_tiny_alphabet():
             for step in range(5):
                 add = draw(int(rng.integers(1, len(strs) // 32 + 1)))
                 b = from_strings(add)
-                g.insert_flat(b.chars, b.offsets)
+                g.insert_flat(b.chars, b.offsets, merge=True)
                 strs += add
                 assert g.stats()["merged_inserts"] == step + 1
             assert_same_as_fresh(g, strs, f"tiny alphabet trial {trial}", oracle_check=(trial == 0))
