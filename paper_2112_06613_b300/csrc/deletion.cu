@@ -324,9 +324,11 @@ __device__ __forceinline__ void st_keep(uint64_t* p, uint64_t v, uint64_t pol) {
     asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol) : "memory");
 }
 
-// The scatter writes nothing when the records counted exceed R_cap, the size
-// the record array was given (only invalid input, whose error the build reports
-// at its first readback, can get there).
+// The scatter takes each record's absolute position from its partition's
+// cursor (pcnt, seeded with the partition start by the scan: one atomic and
+// one store per record, no offset load). It writes nothing when the records
+// counted exceed R_cap, the size the record array was given (only invalid
+// input, whose error the build reports at its first readback, can get there).
 template <bool SCATTER>
 __global__ void k_records(const Canon* __restrict__ ucanon, const uint8_t* __restrict__ ulen,
                           const int64_t* __restrict__ U_ptr, int64_t n, uint32_t P, int32_t* __restrict__ pcnt,
@@ -356,19 +358,11 @@ __global__ void k_records(const Canon* __restrict__ ucanon, const uint8_t* __res
         int pending = 0;
         auto issue = [&](int k) {  // the k newest pending records (k <= kRecBatch)
             int32_t sl[kRecBatch];
-            int64_t bs[kRecBatch];
 #pragma unroll
-            for (int j = 0; j < kRecBatch; ++j) {
-                sl[j] = 0;
-                bs[j] = 0;
-                if (j < k) {
-                    sl[j] = atomicAdd(&pcnt[q[j]], 1);
-                    bs[j] = poff[q[j]];
-                }
-            }
+            for (int j = 0; j < kRecBatch; ++j) sl[j] = j < k ? atomicAdd(&pcnt[q[j]], 1) : 0;
 #pragma unroll
             for (int j = 0; j < kRecBatch; ++j)
-                if (j < k) st_keep(recs + bs[j] + sl[j], r[j], pol);
+                if (j < k) st_keep(recs + sl[j], r[j], pol);
         };
         for_each_variant_hash(c, L, [&](int p, uint64_t h, bool rs) {
             const uint64_t tag = p < 0 ? ((uint64_t)kTagF << 26) : (((uint64_t)p << 26) | (rs ? (1ull << 25) : 0ull));
@@ -1535,9 +1529,10 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
                                   ulen.as<uint8_t>(), d_U, n, (uint32_t)P, pcnt.as<int32_t>(), nullptr, nullptr, 0u,
                                   R_max, 0xffffffffull));
         note_launch();
-        // the scan clears the counts behind itself for the scatter's slot counters
-        TCR_CHECK(scan_exclusive_i32_to_i64(pcnt.as<int32_t>(), poff.as<int64_t>(), P, s, slice(st_poff, w_scan_p),
-                                            /*clear_input=*/true));
+        // the scan turns the counts behind itself into the scatter's slot cursors
+        // (each at its partition's start)
+        TCR_CHECK(scan_exclusive_i32_to_i64_cursors(pcnt.as<int32_t>(), poff.as<int64_t>(), P, s,
+                                                    slice(st_poff, w_scan_p)));
         TCR_CUDA(launch_dependent(k_records<true>, dim3(rgrid), dim3(kThreads), 0, s, ucanon.as<Canon>(),
                                   ulen.as<uint8_t>(), d_U, n, (uint32_t)P, pcnt.as<int32_t>(), poff.as<int64_t>(),
                                   recs.as<uint64_t>(), 0u, R_max,
@@ -2489,13 +2484,15 @@ __global__ void k_ins_uid(const int32_t* __restrict__ slot_of, const int32_t* __
 }
 
 // Partition starts after the new records (poff_new = poff + exclusive counts of
-// the new records) and the slot cursor of each partition (its old size).
+// the new records) and the slot cursor of each partition: the absolute position
+// after its old records (positions fit int32: at most 2^25 strings of 48
+// letters, 1.6e9 records).
 __global__ void k_ins_part_base(const int64_t* __restrict__ poff, const int64_t* __restrict__ pscan, int64_t P,
                                 int64_t* __restrict__ poff_new, int32_t* __restrict__ pcur) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p > P) return;
     poff_new[p] = poff[p] + pscan[p];
-    if (p < P) pcur[p] = (int32_t)(poff[p + 1] - poff[p]);
+    if (p < P) pcur[p] = (int32_t)(poff[p] + pscan[p] + poff[p + 1] - poff[p]);  // after the partition's old records
 }
 
 // Segments (rows, partitions) that grow: flag[i] = grow[i] > 0.

@@ -15,6 +15,11 @@ namespace tcr {
 int64_t scan_status_words(int64_t n);
 tcrnet_status scan_exclusive_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s,
                                         unsigned long long* zeroed_status = nullptr, bool clear_input = false);
+// The same scan, and in[i] = out[i] behind itself: the counts become cursors at
+// the segments' starts, for slot atomics that return absolute positions
+// (callers guarantee out[n] < 2^31).
+tcrnet_status scan_exclusive_i32_to_i64_cursors(int32_t* in, int64_t* out, int64_t n, cudaStream_t s,
+                                                unsigned long long* zeroed_status = nullptr);
 tcrnet_status scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
 // int64 offsets -> int32 offsets (caller checked that they fit).
 tcrnet_status narrow_offsets(const int64_t* in, int32_t* out, int64_t count, cudaStream_t s);

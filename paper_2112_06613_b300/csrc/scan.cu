@@ -54,11 +54,12 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(const TI* __restrict
 // status[0 .. tiles) publication words, status[tiles] the ticket counter,
 // status[tiles + 1] the error flag; all zero at launch.
 // `clear` (nullable) may be `in` itself: neither is declared restrict, and
-// each item is read into shared memory before it is cleared.
+// each item is read into shared memory before it is overwritten: with zero,
+// or with its exclusive prefix when `seed` is set.
 template <typename TI>
 __global__ void __launch_bounds__(kScanThreads) k_scan_onepass(const TI* in, int64_t n, int64_t* __restrict__ out,
                                                                 unsigned long long* status, int64_t tiles,
-                                                                TI* clear) {
+                                                                TI* clear, bool seed = false) {
     dep_entry();  // launched dependent on the kernel before it
     __shared__ int64_t warp_tot[32];
     __shared__ int64_t stage[kScanStage];
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_onepass(const TI* in, int
         const int idx = k * kScanThreads + threadIdx.x;
         stage[scan_slot(idx)] = load_item(in, base + idx, n);
     }
-    if (clear) {  // in place of a memset before the input's next use as counters
+    if (clear && !seed) {  // in place of a memset before the input's next use as counters
 #pragma unroll
         for (int k = 0; k < kScanItems; ++k) {
             const int64_t i = base + k * kScanThreads + threadIdx.x;
@@ -105,14 +106,20 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_onepass(const TI* in, int
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         const int64_t i = base + k * kScanThreads + threadIdx.x;
-        if (i < n) out[i] = stage[scan_slot(k * kScanThreads + threadIdx.x)];
+        if (i < n) {
+            const int64_t o = stage[scan_slot(k * kScanThreads + threadIdx.x)];
+            out[i] = o;
+            if (seed) clear[i] = (TI)o;
+        }
     }
     if (tile == tiles - 1 && threadIdx.x == 0) out[n] = s_prefix + tot;  // the grand total
 }
 
+__global__ void k_narrow(const int64_t* __restrict__ in, int32_t* __restrict__ out, int64_t count);
+
 template <typename TI>
 tcrnet_status scan_impl(const TI* in, int64_t* out, int64_t n, cudaStream_t s,
-                        unsigned long long* zeroed_status = nullptr, bool clear_input = false) {
+                        unsigned long long* zeroed_status = nullptr, bool clear_input = false, bool seed = false) {
     if (n <= 0) {
         TCR_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
         return TCRNET_OK;
@@ -121,7 +128,16 @@ tcrnet_status scan_impl(const TI* in, int64_t* out, int64_t n, cudaStream_t s,
     if (tiles == 1) {
         k_tile_scan<TI><<<1, kScanThreads, 0, s>>>(in, n, nullptr, out);
         TCR_LAUNCH_CHECK();
-        if (clear_input) TCR_CUDA(cudaMemsetAsync(const_cast<TI*>(in), 0, sizeof(TI) * n, s));
+        if (seed) {
+            if constexpr (sizeof(TI) == sizeof(int32_t)) {
+                k_narrow<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(out, reinterpret_cast<int32_t*>(const_cast<TI*>(in)), n);
+                TCR_LAUNCH_CHECK();
+            } else {
+                return TCRNET_EINVAL;
+            }
+        } else if (clear_input) {
+            TCR_CUDA(cudaMemsetAsync(const_cast<TI*>(in), 0, sizeof(TI) * n, s));
+        }
         return TCRNET_OK;
     }
     if (tiles > 0x7fffffffLL) return TCRNET_EINVAL;
@@ -133,7 +149,7 @@ tcrnet_status scan_impl(const TI* in, int64_t* out, int64_t n, cudaStream_t s,
         st = status.as<unsigned long long>();
     }
     TCR_CUDA(launch_dependent(k_scan_onepass<TI>, dim3((unsigned)tiles), dim3(kScanThreads), 0, s, in, n, out, st,
-                              tiles, clear_input ? const_cast<TI*>(in) : nullptr));
+                              tiles, (clear_input || seed) ? const_cast<TI*>(in) : nullptr, seed));
     note_launch();
     return TCRNET_OK;
 }
@@ -165,6 +181,11 @@ int64_t scan_status_words(int64_t n) {
 tcrnet_status scan_exclusive_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s,
                                         unsigned long long* zeroed_status, bool clear_input) {
     return scan_impl<int32_t>(in, out, n, s, zeroed_status, clear_input);
+}
+
+tcrnet_status scan_exclusive_i32_to_i64_cursors(int32_t* in, int64_t* out, int64_t n, cudaStream_t s,
+                                                unsigned long long* zeroed_status) {
+    return scan_impl<int32_t>(in, out, n, s, zeroed_status, false, true);
 }
 
 tcrnet_status scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s) {
