@@ -1044,17 +1044,15 @@ k_cand_verify(const int64_t* __restrict__ coff, const int32_t* __restrict__ ccol
 
 // ---- 4. closed neighbourhoods ---------------------------------------------
 
-// D_u = m_u + W_u (written into wsum in place); cursor starts after M_u;
-// the largest D_u into *dmax.
+// D_u = m_u + W_u (written into wsum in place); the largest D_u into *dmax.
 __global__ void k_closed_size(const int32_t* __restrict__ umult, int64_t U, int32_t* __restrict__ wsum,
-                              int32_t* __restrict__ ucur, int* __restrict__ dmax) {
+                              int* __restrict__ dmax) {
     dep_entry();  // launched dependent on the kernel before it
     const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int d = 0;
     if (u < U) {
         d = wsum[u] + umult[u];
         wsum[u] = d;
-        ucur[u] = umult[u];
     }
     // block maximum, then one atomic per block
     __shared__ int wmax[kWarps];
@@ -1073,13 +1071,15 @@ __global__ void k_closed_size(const int32_t* __restrict__ umult, int64_t U, int3
 // Sizes of the closed lists and of the CSR rows with both offset scans, in
 // one launch of two independent look-back chains (lookback.cuh), blockIdx.y:
 // chain 0 scans D_u = m_u + W_u over the string ids u < n (list offsets uoff;
-// the list cursors start after the own members, ucur_u = m_u; the largest D_u
+// the list cursors start after the own members, at the absolute position
+// ucur_u = uoff_u + m_u (64-bit: the appends' atomics return positions in S,
+// no offset load); the largest D_u
 // into *dmax), chain 1 scans d(i) = D_{u(i)} - 1 over the nodes (CSR offsets
 // off64, and the degree array). In place of k_closed_size, k_node_degree and
 // two scans (four launches, two look-back latencies in a row).
 __global__ void __launch_bounds__(kScanThreads)
 k_fill_sizes(const int32_t* __restrict__ wsum, const int32_t* __restrict__ umult, const int32_t* __restrict__ uid,
-             int64_t n, int32_t* __restrict__ ucur, int* __restrict__ dmax, int32_t* __restrict__ deg,
+             int64_t n, unsigned long long* __restrict__ ucur, int* __restrict__ dmax, int32_t* __restrict__ deg,
              int64_t* __restrict__ uoff, int64_t* __restrict__ off64, unsigned long long* st_u,
              unsigned long long* st_n, int64_t tiles) {
     dep_entry();  // launched dependent on the kernel before it
@@ -1107,9 +1107,7 @@ k_fill_sizes(const int32_t* __restrict__ wsum, const int32_t* __restrict__ umult
                 v = wsum[u] + umult[u] - 1;
                 deg[i] = v;
             } else {
-                const int32_t m = umult[i];
-                v = wsum[i] + m;
-                ucur[i] = m;
+                v = wsum[i] + umult[i];
                 dm = max(dm, v);
             }
         }
@@ -1151,9 +1149,20 @@ k_fill_sizes(const int32_t* __restrict__ wsum, const int32_t* __restrict__ umult
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         const int64_t i = base + k * kScanThreads + threadIdx.x;
-        if (i < n) out[i] = stage[scan_slot(k * kScanThreads + threadIdx.x)];
+        if (i < n) {
+            const int64_t o = stage[scan_slot(k * kScanThreads + threadIdx.x)];
+            out[i] = o;
+            if (!nodes) ucur[i] = (unsigned long long)(o + umult[i]);
+        }
     }
     if (tile == tiles - 1 && threadIdx.x == 0) out[n] = s_prefix + tot;  // the grand total
+}
+
+// List cursors after the own members (the single-tile path of the sizes).
+__global__ void k_list_cursors(const int64_t* __restrict__ uoff, const int32_t* __restrict__ umult, int64_t n,
+                               unsigned long long* __restrict__ ucur) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n) ucur[u] = (unsigned long long)(uoff[u] + umult[u]);
 }
 
 __global__ void k_node_degree(const int32_t* __restrict__ uid, int64_t n, const int32_t* __restrict__ dsize,
@@ -1198,8 +1207,7 @@ __global__ void __launch_bounds__(kThreads)
 k_closed_edges(const int2* __restrict__ edges, int64_t seg_cap, const unsigned long long* __restrict__ seg_count,
                const int32_t* __restrict__ umult,
                const int64_t* __restrict__ mem_off, const int32_t* __restrict__ members,
-               const int64_t* __restrict__ uoff, int32_t* __restrict__ ucur, int32_t* __restrict__ S,
-               int* __restrict__ err) {
+               unsigned long long* __restrict__ ucur, int32_t* __restrict__ S, int64_t SD, int* __restrict__ err) {
     constexpr int kShort = 4;
     const int lane = threadIdx.x & 31;
     // grid.y = edge segment; t = direction-expanded index inside the segment
@@ -1220,8 +1228,8 @@ k_closed_edges(const int2* __restrict__ edges, int64_t seg_cap, const unsigned l
         int32_t mv[kShort];
 #pragma unroll
         for (int y = 0; y < kShort; ++y) mv[y] = y < mb ? rb[y] : 0;
-        o = uoff[a] + atomicAdd(&ucur[a], mb);
-        if (o + mb > uoff[a + 1]) {
+        o = (int64_t)atomicAdd(&ucur[a], (unsigned long long)mb);
+        if (o + mb > SD) {  // (weights that disagree with the list: an error, never a write past S)
             atomicExch(err, 1);
             mb = 0;
         }
@@ -1508,7 +1516,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
 
     // ---- 2. records
     DevBuf poff, recs, fb_list, big_list, pedges, eoff, ucur, uoff, edges;
-    TCR_CHECK(ucur.alloc(sizeof(int32_t) * n, s));
+    TCR_CHECK(ucur.alloc(sizeof(unsigned long long) * n, s));
     TCR_CHECK(uoff.alloc(sizeof(int64_t) * (n + 1), s));
     const Weigh weigh{umult.as<int32_t>(), wsum.as<int32_t>()};
     int jgrid = 1;
@@ -1642,14 +1650,17 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
             const int64_t tiles = ceil_div(n, kScanTile);
             TCR_CUDA(launch_dependent(k_fill_sizes, dim3((unsigned)tiles, 2), dim3(kScanThreads), 0, s,
                                       wsum.as<int32_t>(), umult.as<int32_t>(), uid.as<int32_t>(), n,
-                                      ucur.as<int32_t>(), d_err + 4, deg.as<int32_t>(), uoff.as<int64_t>(),
+                                      ucur.as<unsigned long long>(), d_err + 4, deg.as<int32_t>(), uoff.as<int64_t>(),
                                       off64.as<int64_t>(), st_uoff, st_off64, tiles));
             note_launch();
         } else {
             TCR_CUDA(launch_dependent(k_closed_size, dim3(grid_for(n)), dim3(kThreads), 0, s, umult.as<int32_t>(),
-                                      n, wsum.as<int32_t>(), ucur.as<int32_t>(), d_err + 4));
+                                      n, wsum.as<int32_t>(), d_err + 4));
             note_launch();
             TCR_CHECK(scan_exclusive_i32_to_i64(wsum.as<int32_t>(), uoff.as<int64_t>(), n, s));
+            k_list_cursors<<<grid_for(n), kThreads, 0, s>>>(uoff.as<int64_t>(), umult.as<int32_t>(), n,
+                                                            ucur.as<unsigned long long>());
+            TCR_LAUNCH_CHECK();
             TCR_CUDA(launch_dependent(k_node_degree, dim3(grid_for(n)), dim3(kThreads), 0, s, uid.as<int32_t>(), n,
                                       wsum.as<int32_t>(), deg.as<int32_t>()));
             note_launch();
@@ -1810,8 +1821,8 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         const dim3 fgrid(grid_for(2 * seg_max), (unsigned)fill_segs);
         k_closed_edges<<<fgrid, kThreads, 0, s>>>(edges.as<int2>(), fill_cap, fill_counts, umult.as<int32_t>(),
                                                             mem_off.as<int64_t>(), members.as<int32_t>(),
-                                                            uoff.as<int64_t>(), ucur.as<int32_t>(),
-                                                            Sbuf.as<int32_t>(), d_err + 1);
+                                                            ucur.as<unsigned long long>(), Sbuf.as<int32_t>(), SD,
+                                                            d_err + 1);
         TCR_LAUNCH_CHECK();
     }
     if (keep_edges) TCR_CHECK(gather_edges());
