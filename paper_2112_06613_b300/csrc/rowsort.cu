@@ -255,10 +255,9 @@ k_sort_warp_wide(const int64_t* __restrict__ off, int32_t* __restrict__ cols, co
     }
 }
 
-// Rows of 257..512 (K = 16) or 513..1024 (K = 32) values, listed by
-// k_sort_warp; one kernel per K so that each gets the registers it needs
-// (three blocks per SM: 80 registers with a 4-byte spill, against 128 and two
-// blocks unbounded; measured faster).
+// Rows of 257..512 values (K = 16), listed by k_sort_warp; a kernel of its own
+// so that it gets the registers it needs (three blocks per SM: 80 registers
+// with a 4-byte spill, against 128 and two blocks unbounded; measured faster).
 template <int K>
 __global__ void __launch_bounds__(kSortWarps * 32, 3)
 k_sort_warp_mid(const int64_t* __restrict__ off, int32_t* __restrict__ cols, const int32_t* __restrict__ mid,
