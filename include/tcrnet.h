@@ -424,6 +424,22 @@ typedef enum tcrnet_probe_kind {
 tcrnet_status tcrnet_probe_int_issue(int32_t kind, int32_t iters, uint32_t *d_out, int64_t n_threads,
                                      void *stream, int64_t *ops_per_thread);
 
+/*
+ * The per-row ordering step of the builds on its own (hot-path step a5: the
+ * CSR rows are placed in arrival order, then each row is sorted; Methods
+ * "Adjacency matrix" gives the matrix the rows stand for). Sorts every row
+ * segment d_cols[d_offsets[i] .. d_offsets[i+1]) ascending, in place, for
+ * i < n: rows of up to 512 values in registers, up to 16,384 in shared
+ * memory, longer ones by shared-memory chunks and stable pairwise merges.
+ * Values may repeat (the l_max = 2 candidate rows do). d_offsets: n + 1
+ * ascending int64 offsets, d_cols: int32 values, both device memory of the
+ * current device, caller-owned; stream: a cudaStream_t or NULL (the legacy
+ * default stream). Returns after the sort has finished. Errors: TCRNET_EINVAL
+ * for n < 0 or null pointers with n > 0, TCRNET_ENOMEM if scratch memory
+ * cannot be had, TCRNET_EDEVICE on a device error.
+ */
+tcrnet_status tcrnet_sort_rows(const int64_t *d_offsets, int32_t *d_cols, int64_t n, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

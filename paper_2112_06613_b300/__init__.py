@@ -108,7 +108,7 @@ SYMBOLS = [
     "tcrnet_degree_noalloc", "tcrnet_query_ex", "tcrnet_insert_flat", "tcrnet_insert_ex", "tcrnet_insert",
     "tcrnet_components", "tcrnet_neighbor_degree", "tcrnet_build_batched",
     "tcrnet_degree_histogram", "tcrnet_extend", "tcrnet_save", "tcrnet_load", "tcrnet_components_ex",
-    "tcrnet_probe_int_issue",
+    "tcrnet_probe_int_issue", "tcrnet_sort_rows",
 ]
 
 
@@ -183,6 +183,8 @@ def load_library(path: str = LIB_PATH):
         lib.tcrnet_degree_noalloc.restype = ctypes.c_int
         lib.tcrnet_probe_int_issue.argtypes = [i32, i32, vp, i64, vp, ctypes.POINTER(i64)]
         lib.tcrnet_probe_int_issue.restype = ctypes.c_int
+        lib.tcrnet_sort_rows.argtypes = [vp, vp, i64, vp]
+        lib.tcrnet_sort_rows.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -574,3 +576,28 @@ def tcrnet_probe_int_issue(kind: str, iters: int, out, stream=None) -> int:
                                                _stream_ptr(stream), ctypes.byref(ops))
     _check(st, "tcrnet_probe_int_issue")
     return ops.value
+
+
+def tcrnet_sort_rows(offsets, cols, stream=None):
+    """Sort every row segment cols[offsets[i]:offsets[i+1]] ascending in place on
+    the device (the builds' per-row ordering step). offsets: int64 CUDA tensor of
+    n + 1 ascending entries ending at cols.numel(); cols: int32 CUDA tensor."""
+    import torch
+
+    if offsets.dtype != torch.int64 or cols.dtype != torch.int32:
+        raise TypeError("offsets must be int64 and cols int32")
+    if not (offsets.is_cuda and cols.is_cuda) or offsets.device != cols.device:
+        raise ValueError("offsets and cols must be CUDA tensors on one device")
+    if offsets.device.index != torch.cuda.current_device():
+        raise ValueError("offsets and cols must be on the current device")
+    if not (offsets.is_contiguous() and cols.is_contiguous()) or offsets.dim() != 1 or cols.dim() != 1:
+        raise ValueError("offsets and cols must be contiguous 1-D tensors")
+    n = offsets.numel() - 1
+    if n < 0:
+        raise ValueError("offsets needs at least one entry")
+    if n > 0:
+        ends = offsets[[0, -1]].tolist()
+        if ends[0] != 0 or ends[1] != cols.numel() or bool((offsets[1:] < offsets[:-1]).any()):
+            raise ValueError("offsets must ascend from 0 to cols.numel()")
+    _check(load_library().tcrnet_sort_rows(offsets.data_ptr(), cols.data_ptr(), n, _stream_ptr(stream)),
+           "tcrnet_sort_rows")

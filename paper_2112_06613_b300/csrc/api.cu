@@ -1037,6 +1037,21 @@ tcrnet_status tcrnet_insert(tcrnet_handle h, const char* const* seqs, int64_t m)
     return tcrnet_insert_ex(h, chars.data(), offs.data(), m, TCRNET_HOST, nullptr);
 }
 
+tcrnet_status tcrnet_sort_rows(const int64_t* d_offsets, int32_t* d_cols, int64_t n, void* stream) {
+    t_last_bad = -1;
+    if (n < 0 || (n > 0 && (!d_offsets || !d_cols))) return TCRNET_EINVAL;
+    if (n == 0) return TCRNET_OK;
+    int dev = 0;
+    TCR_CUDA(cudaGetDevice(&dev));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    {
+        ArenaLease lease(dev, s);
+        TCR_CHECK(tcr::sort_rows(d_offsets, d_cols, n, s, sm_count(dev)));
+    }
+    TCR_CUDA(cudaStreamSynchronize(s));
+    return TCRNET_OK;
+}
+
 tcrnet_status tcrnet_components(tcrnet_handle h, const uint8_t* keep, int32_t* labels, int32_t mem,
                                 int64_t* n_components, int64_t* largest) {
     return tcrnet_components_ex(h, keep, labels, mem, nullptr, n_components, largest);

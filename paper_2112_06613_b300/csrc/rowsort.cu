@@ -2,8 +2,9 @@
 //
 // The write passes place a row's neighbours in arrival order (atomic cursors),
 // so each row segment is sorted afterwards; the result is then independent of
-// scheduling, i.e. bit-exact and deterministic. Values inside a row are
-// distinct node ids.
+// scheduling, i.e. bit-exact and deterministic. Values inside a CSR row are
+// distinct node ids; candidate rows (l_max = 2) hold repeats, which every
+// class below sorts too (the networks compare-exchange, the merges are stable).
 //
 //   len <= 8:           one lane, values in registers, Batcher's odd-even
 //                       merge network for 8 (19 comparators); a warp takes 32
@@ -332,7 +333,11 @@ k_sort_chunks(int32_t* __restrict__ v, int64_t len) {
     for (int i = threadIdx.x; i < cl; i += kBlockThreads) v[c0 + i] = sbuf[i];
 }
 
-// Merge adjacent sorted runs of length `run` from src into dst.
+// Merge adjacent sorted runs of length `run` from src into dst. Each value's
+// slot is its rank in its own run plus its rank in the partner run, counted
+// stably so that repeated values (candidate rows hold repeats) get distinct
+// slots: a value of the first run counts the partner's values below it, a
+// value of the second run the partner's values at or below it.
 __global__ void k_merge_runs(const int32_t* __restrict__ src, int32_t* __restrict__ dst, int64_t len, int64_t run) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t pair = i / (2 * run);
@@ -342,11 +347,10 @@ __global__ void k_merge_runs(const int32_t* __restrict__ src, int32_t* __restric
         const int64_t b1 = min(a0 + 2 * run, len);
         const int32_t x = src[i];
         const bool in_a = i < a1;
-        // rank of x in the partner run (values are distinct)
         int64_t lo = in_a ? b0 : a0, hi = in_a ? b1 : a1;
         while (lo < hi) {
             const int64_t mid = (lo + hi) >> 1;
-            if (src[mid] < x) lo = mid + 1; else hi = mid;
+            if (src[mid] < x || (!in_a && src[mid] == x)) lo = mid + 1; else hi = mid;
         }
         const int64_t rank_partner = lo - (in_a ? b0 : a0);
         const int64_t rank_own = i - (in_a ? a0 : b0);

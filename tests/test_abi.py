@@ -173,3 +173,12 @@ def test_new_option_knobs_validated():
     nc, lc = ctypes.c_int64(5), ctypes.c_int64(5)
     assert lib.tcrnet_components_ex(None, None, None, tn.HOST, None, ctypes.byref(nc), ctypes.byref(lc)) == tn.EINVAL
     assert nc.value == 0 and lc.value == 0
+
+
+def test_sort_rows_arguments_checked_before_device_work():
+    """tcrnet_sort_rows: a negative row count or missing arrays are rejected, and
+    zero rows return at once, all before any CUDA call."""
+    lib = tn.load_library()
+    assert lib.tcrnet_sort_rows(None, None, -1, None) == tn.EINVAL
+    assert lib.tcrnet_sort_rows(None, None, 3, None) == tn.EINVAL
+    assert lib.tcrnet_sort_rows(None, None, 0, None) == tn.OK
