@@ -144,6 +144,7 @@ const SideStream* leased_side_stream() {
     if (!a) return nullptr;
     if (!a->side_ok) {
         if (cudaStreamCreateWithFlags(&a->side.stream, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+        if (cudaStreamCreateWithFlags(&a->side.stream2, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
         for (auto& e : a->side.ev)
             if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
         a->side_ok = true;
@@ -228,7 +229,10 @@ ArenaLease::~ArenaLease() {
     // on its stream and on the side stream (an early error return may leave
     // forked work there)
     cudaStreamSynchronize(s_);
-    if (g_arenas[dev_].side_ok) cudaStreamSynchronize(g_arenas[dev_].side.stream);
+    if (g_arenas[dev_].side_ok) {
+        cudaStreamSynchronize(g_arenas[dev_].side.stream);
+        cudaStreamSynchronize(g_arenas[dev_].side.stream2);
+    }
     t_arena = nullptr;
     g_arenas[dev_].mu.unlock();
 }

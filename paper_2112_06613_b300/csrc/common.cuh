@@ -180,11 +180,13 @@ bool arena_active();
 // While the calling thread holds its device's workspace lease: a second stream
 // of that device and events for forking independent work off the call's
 // stream and joining it back (null: no lease; run everything in order).
-// ev[0..3] and ev[6] belong to the deletion build's phases, ev[4..5] to the
-// row sort.
+// ev[0..3] and ev[6] belong to the deletion build's phases, ev[4], ev[5] and
+// ev[7] to the row sort; stream2 is a third stream the row sort uses when its
+// long classes are listed in advance.
 struct SideStream {
     cudaStream_t stream = nullptr;
-    cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t stream2 = nullptr;
+    cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 const SideStream* leased_side_stream();
 

@@ -1070,6 +1070,8 @@ __global__ void k_closed_size(const int32_t* __restrict__ umult, int64_t U, int3
 
 // Sizes of the closed lists and of the CSR rows with both offset scans, in
 // one launch of two independent look-back chains (lookback.cuh), blockIdx.y:
+// (chain 0 also lists the long lists by row-sort class into cls_lists[c * n
+// + k], counts cls_cnt[c], for a list sort whose classes then start together)
 // chain 0 scans D_u = m_u + W_u over the string ids u < n (list offsets uoff;
 // the list cursors start after the own members, at the absolute position
 // ucur_u = uoff_u + m_u (64-bit: the appends' atomics return positions in S,
@@ -1081,7 +1083,7 @@ __global__ void __launch_bounds__(kScanThreads)
 k_fill_sizes(const int32_t* __restrict__ wsum, const int32_t* __restrict__ umult, const int32_t* __restrict__ uid,
              int64_t n, unsigned long long* __restrict__ ucur, int* __restrict__ dmax, int32_t* __restrict__ deg,
              int64_t* __restrict__ uoff, int64_t* __restrict__ off64, unsigned long long* st_u,
-             unsigned long long* st_n, int64_t tiles) {
+             unsigned long long* st_n, int64_t tiles, int32_t* __restrict__ cls_lists, int* __restrict__ cls_cnt) {
     dep_entry();  // launched dependent on the kernel before it
     __shared__ int64_t warp_tot[32];
     __shared__ int64_t stage[kScanStage];
@@ -1109,6 +1111,20 @@ k_fill_sizes(const int32_t* __restrict__ wsum, const int32_t* __restrict__ umult
             } else {
                 v = wsum[i] + umult[i];
                 dm = max(dm, v);
+            }
+        }
+        if (!nodes && cls_cnt) {  // long lists listed for their sort class, one atomic per warp and class
+            const int c = (i < n && v >= kSortWideMin) ? (v >= kSortBigMin ? 2 : (v >= kSortMidMin ? 1 : 0)) : -1;
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                const uint32_t m = __ballot_sync(kFull, c == cc);
+                if (m) {
+                    const int lead = __ffs(m) - 1;
+                    int base = 0;
+                    if ((int)(threadIdx.x & 31) == lead) base = atomicAdd(&cls_cnt[cc], __popc(m));
+                    base = __shfl_sync(kFull, base, lead);
+                    if (c == cc) cls_lists[cc * n + base + __popc(m & ((1u << (threadIdx.x & 31)) - 1u))] = (int32_t)i;
+                }
             }
         }
         stage[scan_slot(idx)] = v;
@@ -1437,18 +1453,18 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     // (u64 words): the edge cursors ([kEdgeSegs]: single-segment count), the
     // distinct-string count, the device counters ([0] dedup error, [1] fill
     // error, [2] partitions for the quadratic join, [3] partitions for the
-    // sorted join, [4] largest closed list, [5] rejected candidates), and the
-    // status words of the build's scans.
+    // sorted join, [4] largest closed list, [5] rejected candidates, [6..8]
+    // lists of the long sort classes), and the status words of the build's scans.
     const int64_t w_scan_n = scan_status_words(n);
     const int64_t w_scan_p = join ? scan_status_words(P) : 0;
-    const int64_t w_fixed = (kEdgeSegs + 1) + 1 + 4;
+    const int64_t w_fixed = (kEdgeSegs + 1) + 1 + 5;
     DevBuf zeroed;
     TCR_CHECK(zeroed.alloc(sizeof(unsigned long long) * (w_fixed + 3 * w_scan_n + w_scan_p), s));
     TCR_CUDA(cudaMemsetAsync(zeroed.as<void>(), 0, zeroed.bytes(), s));
     unsigned long long* d_ecur = zeroed.as<unsigned long long>();
     unsigned long long* d_ucount = d_ecur + (kEdgeSegs + 1);
     int* d_err = reinterpret_cast<int*>(d_ucount + 1);
-    unsigned long long* st_members = d_ucount + 5;  // scan status words, one slice per scan
+    unsigned long long* st_members = d_ucount + 6;  // scan status words, one slice per scan
     unsigned long long* st_uoff = st_members + w_scan_n;
     unsigned long long* st_off64 = st_uoff + w_scan_n;
     unsigned long long* st_poff = st_off64 + w_scan_n;
@@ -1641,7 +1657,8 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     MidReadback pageable;
     MidReadback* rb = static_cast<MidReadback*>(pinned_scratch());
     const unsigned long long* d_pack_flags = pk.flags.as<unsigned long long>();
-    DevBuf off32;
+    DevBuf off32, cls_lists;
+    if (w_scan_n > 0) TCR_CHECK(cls_lists.alloc(sizeof(int32_t) * 3 * n, s));  // long lists by sort class
     // the list sizes and offsets from W_u, then the sizes of the lists and of
     // the CSR, the candidate counts, the longest list, the rejected candidates
     // and the encoder's error word in one synchronisation
@@ -1651,7 +1668,8 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
             TCR_CUDA(launch_dependent(k_fill_sizes, dim3((unsigned)tiles, 2), dim3(kScanThreads), 0, s,
                                       wsum.as<int32_t>(), umult.as<int32_t>(), uid.as<int32_t>(), n,
                                       ucur.as<unsigned long long>(), d_err + 4, deg.as<int32_t>(), uoff.as<int64_t>(),
-                                      off64.as<int64_t>(), st_uoff, st_off64, tiles));
+                                      off64.as<int64_t>(), st_uoff, st_off64, tiles, cls_lists.as<int32_t>(),
+                                      d_err + 6));
             note_launch();
         } else {
             TCR_CUDA(launch_dependent(k_closed_size, dim3(grid_for(n)), dim3(kThreads), 0, s, umult.as<int32_t>(),
@@ -1761,7 +1779,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         // the complete list, then the sizes again (their status words and the
         // longest-list maximum cleared first)
         TCR_CUDA(cudaMemsetAsync(wsum.as<void>(), 0, sizeof(int32_t) * n, s));
-        TCR_CUDA(cudaMemsetAsync(d_err + 4, 0, 2 * sizeof(int), s));
+        TCR_CUDA(cudaMemsetAsync(d_err + 4, 0, 5 * sizeof(int), s));
         if (w_scan_n > 0) TCR_CUDA(cudaMemsetAsync(st_uoff, 0, 2 * sizeof(unsigned long long) * w_scan_n, s));
         k_confirm<<<dim3(grid_for(E), 1), kThreads, 0, s>>>(edges.as<int2>(), E, d_ecur + kEdgeSegs, 0,
                                                            ucanon.as<Canon>(), weigh, d_err + 5);
@@ -1833,7 +1851,13 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     const int t4 = tm.mark();
     if (!keep_index) recs.reset();
     edges.reset();
-    TCR_CHECK(sort_rows(uoff.as<int64_t>(), Sbuf.as<int32_t>(), n, s, num_sms, h_dmax));
+    SortClasses classes;  // the long lists, listed by the size scan
+    classes.wide = cls_lists.as<int32_t>();
+    classes.mid = classes.wide + n;
+    classes.big = classes.wide + 2 * n;
+    classes.counts = d_err + 6;
+    TCR_CHECK(sort_rows(uoff.as<int64_t>(), Sbuf.as<int32_t>(), n, s, num_sms, h_dmax,
+                        w_scan_n > 0 ? &classes : nullptr));
     const int t5 = tm.mark();
 
     // ---- 5. expand

@@ -126,11 +126,23 @@ tcrnet_status neighbor_degree(const void* off, bool off64, const int32_t* cols, 
                               cudaStream_t s, int num_sms);
 
 // ---- rowsort.cu -----------------------------------------------------------
-// Sort every row segment cols[off[i] .. off[i+1]) ascending (values distinct).
+// Rows of the long sort classes listed by the caller (row ids, counts on the
+// device): 65..256, 257..512 and more than 512 values. With them the classes'
+// kernels need not wait for the short-row kernel to list them and run beside
+// it on the workspace's side streams.
+constexpr int64_t kSortWideMin = 65, kSortMidMin = 257, kSortBigMin = 513;
+struct SortClasses {
+    const int32_t* wide = nullptr;
+    const int32_t* mid = nullptr;
+    const int32_t* big = nullptr;
+    const int* counts = nullptr;  // [0] wide, [1] mid, [2] big
+};
+// Sort every row segment cols[off[i] .. off[i+1]) ascending (repeats allowed).
 // max_len: an upper bound of the row lengths when the caller knows one (-1:
 // unknown; then the kernels of every class run and the host reads back how many
-// rows exceed a block's shared memory).
+// rows exceed a block's shared memory). pre: the long rows listed in advance
+// (nullable).
 tcrnet_status sort_rows(const int64_t* off, int32_t* cols, int64_t n, cudaStream_t s, int num_sms,
-                        int64_t max_len = -1);
+                        int64_t max_len = -1, const SortClasses* pre = nullptr);
 
 }  // namespace tcr

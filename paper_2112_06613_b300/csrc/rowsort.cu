@@ -37,6 +37,8 @@ namespace {
 constexpr int kLaneMax = 8;
 constexpr int kShortMax = 64;
 constexpr int kWideMax = 256;
+static_assert(kSortWideMin == kShortMax + 1 && kSortMidMin == kWideMax + 1 && kSortBigMin == 2 * kWideMax + 1,
+              "the classes a caller lists are the classes of the kernels below");
 constexpr int kBlockThreads = 1024;
 constexpr int kBlockCap = 16384;
 constexpr int kSortWarps = 8;
@@ -204,9 +206,10 @@ __device__ __forceinline__ void block_bitonic(int32_t* s, int P) {
     group_bitonic(s, P, threadIdx.x, kBlockThreads, [] __device__() { __syncthreads(); });
 }
 
-// Rows of at most 64 values; longer rows are listed for the kernels below.
-// A warp takes 32 consecutive rows: each lane sorts its own row when it has at
-// most 8 values, then the warp sorts the rows of 9..64 values one by one.
+// Rows of at most 64 values; longer rows are listed for the kernels below
+// (unless wide is null: the caller listed them). A warp takes 32 consecutive
+// rows: each lane sorts its own row when it has at most 8 values, then the
+// warp sorts the rows of 9..64 values one by one.
 __global__ void __launch_bounds__(kSortWarps * 32)
 k_sort_warp(const int64_t* __restrict__ off, int32_t* __restrict__ cols, int64_t n, int32_t* __restrict__ wide,
             int* __restrict__ nwide, int32_t* __restrict__ mid, int* __restrict__ nmid, int32_t* __restrict__ big,
@@ -224,6 +227,7 @@ k_sort_warp(const int64_t* __restrict__ off, int32_t* __restrict__ cols, int64_t
             len = len64 > (int64_t)kInf ? kInf : (int)len64;
         }
         if (len >= 2 && len <= kLaneMax) lane_sort8(cols + base, len);
+        else if (!wide) {}  // the long rows were listed by the caller
         else if (len > 2 * kWideMax) big[atomicAdd(nbig, 1)] = (int32_t)r;  // few, long: a block each
         else if (len > kWideMax) mid[atomicAdd(nmid, 1)] = (int32_t)r;
         else if (len > kShortMax) wide[atomicAdd(nwide, 1)] = (int32_t)r;
@@ -360,7 +364,49 @@ __global__ void k_merge_runs(const int32_t* __restrict__ src, int32_t* __restric
 
 }  // namespace
 
-tcrnet_status sort_rows(const int64_t* off, int32_t* cols, int64_t n, cudaStream_t s, int num_sms, int64_t max_len) {
+namespace {
+
+// The long classes listed in advance: the short-row kernel on s, 65..256 on
+// the first side stream, 257..512 then the block class on the second, all
+// started together; s waits for both side streams at the end.
+tcrnet_status sort_rows_listed(const int64_t* off, int32_t* cols, int64_t n, cudaStream_t s, int num_sms,
+                               int64_t max_len, const SortClasses& pre, const SideStream* side, int32_t* huge_list,
+                               int* nhuge) {
+    const bool run_wide = max_len < 0 || max_len >= kSortWideMin;
+    const bool run_mid = max_len < 0 || max_len >= kSortMidMin;
+    const bool run_block = max_len < 0 || max_len >= kSortBigMin;
+    TCR_CUDA(cudaEventRecord(side->ev[4], s));
+    TCR_CUDA(cudaStreamWaitEvent(side->stream, side->ev[4], 0));
+    TCR_CUDA(cudaStreamWaitEvent(side->stream2, side->ev[4], 0));
+    const int64_t blocks = std::min<int64_t>(ceil_div(n, 32 * kSortWarps), (int64_t)num_sms * 16);
+    k_sort_warp<<<(unsigned)blocks, kSortWarps * 32, 0, s>>>(off, cols, n, nullptr, nullptr, nullptr, nullptr,
+                                                               nullptr, nullptr);
+    TCR_LAUNCH_CHECK();
+    if (run_wide) {
+        k_sort_warp_wide<<<num_sms * 8, kSortWarps * 32, 0, side->stream>>>(off, cols, pre.wide, pre.counts);
+        TCR_LAUNCH_CHECK();
+    }
+    if (run_mid) {
+        k_sort_warp_mid<16><<<num_sms * 4, kSortWarps * 32, 0, side->stream2>>>(off, cols, pre.mid, pre.counts + 1);
+        TCR_LAUNCH_CHECK();
+    }
+    if (run_block) {
+        const size_t smem = sizeof(int32_t) * kBlockCap;
+        k_sort_block<<<num_sms * 2, kBlockThreads, smem, side->stream2>>>(off, cols, pre.big, pre.counts + 2,
+                                                                            huge_list, nhuge);
+        TCR_LAUNCH_CHECK();
+    }
+    TCR_CUDA(cudaEventRecord(side->ev[5], side->stream));
+    TCR_CUDA(cudaEventRecord(side->ev[7], side->stream2));
+    TCR_CUDA(cudaStreamWaitEvent(s, side->ev[5], 0));
+    TCR_CUDA(cudaStreamWaitEvent(s, side->ev[7], 0));
+    return TCRNET_OK;
+}
+
+}  // namespace
+
+tcrnet_status sort_rows(const int64_t* off, int32_t* cols, int64_t n, cudaStream_t s, int num_sms, int64_t max_len,
+                        const SortClasses* pre) {
     if (n <= 0) return TCRNET_OK;
     // lists: [0, n) rows of 257..512, [n, 2n) rows above 512, [2n, 3n) rows
     // above kBlockCap, [3n, 4n) rows of 65..256; counts in the same order
@@ -373,40 +419,48 @@ tcrnet_status sort_rows(const int64_t* off, int32_t* cols, int64_t n, cudaStream
     int32_t* huge_list = big + n;
     int32_t* wide = huge_list + n;
     int* cnt = counts.as<int>();
-    const int64_t blocks = std::min<int64_t>(ceil_div(n, 32 * kSortWarps), (int64_t)num_sms * 16);
-    k_sort_warp<<<(unsigned)blocks, kSortWarps * 32, 0, s>>>(off, cols, n, wide, cnt + 3, mid, cnt, big, cnt + 1);
-    TCR_LAUNCH_CHECK();
     const bool known = max_len >= 0;  // a known bound skips the kernels of longer classes
     const bool run_mid = !known || max_len > kWideMax;
     const bool run_block = !known || max_len > 2 * kWideMax;
-    // The classes are disjoint rows: rows above 256 are sorted on the second
-    // stream of the workspace lease while this stream sorts 65..256.
-    const SideStream* side = (run_mid || run_block) ? leased_side_stream() : nullptr;
-    cudaStream_t s2 = s;
-    if (side) {
-        TCR_CUDA(cudaEventRecord(side->ev[4], s));
-        TCR_CUDA(cudaStreamWaitEvent(side->stream, side->ev[4], 0));
-        s2 = side->stream;
-    }
-    if (!known || max_len > kShortMax) {
-        TCR_CUDA(launch_dependent(k_sort_warp_wide, dim3(num_sms * 8), dim3(kSortWarps * 32), 0, s, off, cols,
-                                  wide, cnt + 3));
-        note_launch();
-    }
-    if (run_mid) {
-        k_sort_warp_mid<16><<<num_sms * 4, kSortWarps * 32, 0, s2>>>(off, cols, mid, cnt);
-        TCR_LAUNCH_CHECK();
-    }
     if (run_block) {
         const size_t smem = sizeof(int32_t) * kBlockCap;
         TCR_CUDA(cudaFuncSetAttribute(k_sort_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         TCR_CUDA(cudaFuncSetAttribute(k_sort_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_sort_block<<<num_sms * 2, kBlockThreads, smem, s2>>>(off, cols, big, cnt + 1, huge_list, cnt + 2);
-        TCR_LAUNCH_CHECK();
     }
-    if (side) {  // join the second stream back before anything reads the rows
-        TCR_CUDA(cudaEventRecord(side->ev[5], s2));
-        TCR_CUDA(cudaStreamWaitEvent(s, side->ev[5], 0));
+    const SideStream* lside = pre ? leased_side_stream() : nullptr;
+    if (lside) {
+        TCR_CHECK(sort_rows_listed(off, cols, n, s, num_sms, max_len, *pre, lside, huge_list, cnt + 2));
+    } else {
+        const int64_t blocks = std::min<int64_t>(ceil_div(n, 32 * kSortWarps), (int64_t)num_sms * 16);
+        k_sort_warp<<<(unsigned)blocks, kSortWarps * 32, 0, s>>>(off, cols, n, wide, cnt + 3, mid, cnt, big, cnt + 1);
+        TCR_LAUNCH_CHECK();
+        // The classes are disjoint rows: rows above 256 are sorted on the second
+        // stream of the workspace lease while this stream sorts 65..256.
+        const SideStream* side = (run_mid || run_block) ? leased_side_stream() : nullptr;
+        cudaStream_t s2 = s;
+        if (side) {
+            TCR_CUDA(cudaEventRecord(side->ev[4], s));
+            TCR_CUDA(cudaStreamWaitEvent(side->stream, side->ev[4], 0));
+            s2 = side->stream;
+        }
+        if (!known || max_len > kShortMax) {
+            TCR_CUDA(launch_dependent(k_sort_warp_wide, dim3(num_sms * 8), dim3(kSortWarps * 32), 0, s, off, cols,
+                                      wide, cnt + 3));
+            note_launch();
+        }
+        if (run_mid) {
+            k_sort_warp_mid<16><<<num_sms * 4, kSortWarps * 32, 0, s2>>>(off, cols, mid, cnt);
+            TCR_LAUNCH_CHECK();
+        }
+        if (run_block) {
+            const size_t smem = sizeof(int32_t) * kBlockCap;
+            k_sort_block<<<num_sms * 2, kBlockThreads, smem, s2>>>(off, cols, big, cnt + 1, huge_list, cnt + 2);
+            TCR_LAUNCH_CHECK();
+        }
+        if (side) {  // join the second stream back before anything reads the rows
+            TCR_CUDA(cudaEventRecord(side->ev[5], s2));
+            TCR_CUDA(cudaStreamWaitEvent(s, side->ev[5], 0));
+        }
     }
     if (!run_block || (known && max_len <= kBlockCap)) return TCRNET_OK;  // no row can be listed as huge
     const size_t smem = sizeof(int32_t) * kBlockCap;
