@@ -479,6 +479,34 @@ struct Weigh {
     }
 };
 
+// The partitions that k_join_small leaves to the other two joins, listed
+// before it runs (from the partition offsets, while the records are
+// scattered): more than cap records for k_join_fallback, 33..cap for
+// k_join_sorted, so that those joins can run beside k_join_small on a side
+// stream. One atomic per warp and list.
+__global__ void k_part_classes(const int64_t* __restrict__ poff, int64_t P, int cap, int32_t* __restrict__ big_list,
+                               int* __restrict__ big_count, int32_t* __restrict__ fb_list, int* __restrict__ fb_count) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; p0 < P;
+         p0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = p0 + lane;
+        const int64_t sz = p < P ? poff[p + 1] - poff[p] : 0;
+        const bool fb = sz > cap, big = !fb && sz > 32;
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            const bool mine = l ? fb : big;
+            const uint32_t m = __ballot_sync(kFull, mine);
+            if (m) {
+                const int lead = __ffs(m) - 1;
+                int base = 0;
+                if (lane == lead) base = atomicAdd(l ? fb_count : big_count, __popc(m));
+                base = __shfl_sync(kFull, base, lead);
+                if (mine) (l ? fb_list : big_list)[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)p;
+            }
+        }
+    }
+}
+
 // Join of the partitions of at most 32 records, without sorting. The records
 // of consecutive partitions are adjacent, so a warp step takes a window of
 // whole consecutive partitions holding at most 32 records: lane k holds record
@@ -547,10 +575,14 @@ k_join_small(const int64_t* __restrict__ poff, int64_t P, const uint64_t* __rest
             my_size = sz > 0x7fffffff ? 0x7fffffff : (int)sz;
         }
         const bool wable = p0 + lane < P && my_size <= small_max;  // joined in a window here
-        if (!WRITE && p0 + lane < P) {  // lane-parallel hand-off of the other partitions
-            if (my_size > cap) fb_list[atomicAdd(fb_count, 1)] = (int32_t)(p0 + lane);
-            else if (my_size > 32) big_list[atomicAdd(big_count, 1)] = (int32_t)(p0 + lane);
-            else pedges[p0 + lane] = 0;  // a window's first partition overwrites it with the window's count
+        if (!WRITE && p0 + lane < P) {  // lane-parallel hand-off of the other partitions (unless listed before)
+            if (my_size > cap) {
+                if (fb_list) fb_list[atomicAdd(fb_count, 1)] = (int32_t)(p0 + lane);
+            } else if (my_size > 32) {
+                if (big_list) big_list[atomicAdd(big_count, 1)] = (int32_t)(p0 + lane);
+            } else {
+                pedges[p0 + lane] = 0;  // a window's first partition overwrites it with the window's count
+            }
         }
         const uint32_t wmask = __ballot_sync(kFull, wable);
         const int wsize = wable ? my_size : 0;
@@ -1557,27 +1589,56 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         // (each at its partition's start)
         TCR_CHECK(scan_exclusive_i32_to_i64_cursors(pcnt.as<int32_t>(), poff.as<int64_t>(), P, s,
                                                     slice(st_poff, w_scan_p)));
+        // the partitions over 32 records are listed on the second side stream
+        // while the records are scattered; their joins then run there beside
+        // k_join_small (without a lease: all in order on s, listed by k_join_small)
+        const SideStream* jside = side;
+        if (jside) {
+            TCR_CUDA(cudaEventRecord(jside->ev[4], s));
+            TCR_CUDA(cudaStreamWaitEvent(jside->stream2, jside->ev[4], 0));
+            k_part_classes<<<(unsigned)std::min<int64_t>(grid_for(P), (int64_t)num_sms * 8), kThreads, 0,
+                             jside->stream2>>>(poff.as<int64_t>(), P, cap, big_list.as<int32_t>(), d_err + 3,
+                                               fb_list.as<int32_t>(), d_err + 2);
+            TCR_LAUNCH_CHECK();
+        }
         TCR_CUDA(launch_dependent(k_records<true>, dim3(rgrid), dim3(kThreads), 0, s, ucanon.as<Canon>(),
                                   ulen.as<uint8_t>(), d_U, n, (uint32_t)P, pcnt.as<int32_t>(), poff.as<int64_t>(),
                                   recs.as<uint64_t>(), 0u, R_max,
                                   record_hash_bits >= 32 ? 0xffffffffull : ((1ull << record_hash_bits) - 1ull)));
         note_launch();
         t2 = tm.mark();
+        if (jside) {  // the records are in place: the sorted and quadratic joins on the side stream
+            TCR_CUDA(cudaEventRecord(jside->ev[5], s));
+            TCR_CUDA(cudaStreamWaitEvent(jside->stream2, jside->ev[5], 0));
+            k_join_sorted<false><<<num_sms * 4, kThreads, 0, jside->stream2>>>(
+                big_list.as<int32_t>(), d_err + 3, poff.as<int64_t>(), recs.as<uint64_t>(), T, pedges.as<int64_t>(),
+                nullptr, edges.as<int2>(), d_ecur, seg_cap);
+            TCR_LAUNCH_CHECK();
+            k_join_fallback<false><<<num_sms * 2, kThreads, 0, jside->stream2>>>(
+                fb_list.as<int32_t>(), d_err + 2, poff.as<int64_t>(), recs.as<uint64_t>(), T, pedges.as<int64_t>(),
+                nullptr, edges.as<int2>(), d_ecur, seg_cap);
+            TCR_LAUNCH_CHECK();
+            TCR_CUDA(cudaEventRecord(jside->ev[7], jside->stream2));
+        }
         // ---- 3a. join, pass 1: candidate pairs, then their confirmation (edges, weighted degrees W_u)
         jgrid = (int)std::min<int64_t>(ceil_div(P, 32 * kWarps), (int64_t)num_sms * 16);
         TCR_CUDA(launch_dependent(k_join_small<false>, dim3(jgrid), dim3(kThreads), 0, s, poff.as<int64_t>(), P,
                                   recs.as<uint64_t>(), cap, T, pedges.as<int64_t>(), nullptr, edges.as<int2>(),
-                                  d_ecur, seg_cap, big_list.as<int32_t>(), d_err + 3, fb_list.as<int32_t>(),
-                                  d_err + 2, R_max));
+                                  d_ecur, seg_cap, jside ? nullptr : big_list.as<int32_t>(), d_err + 3,
+                                  jside ? nullptr : fb_list.as<int32_t>(), d_err + 2, R_max));
         note_launch();
-        TCR_CUDA(launch_dependent(k_join_sorted<false>, dim3(num_sms * 4), dim3(kThreads), 0, s,
-                                  big_list.as<int32_t>(), d_err + 3, poff.as<int64_t>(), recs.as<uint64_t>(), T,
-                                  pedges.as<int64_t>(), nullptr, edges.as<int2>(), d_ecur, seg_cap));
-        note_launch();
-        TCR_CUDA(launch_dependent(k_join_fallback<false>, dim3(num_sms * 2), dim3(kThreads), 0, s,
-                                  fb_list.as<int32_t>(), d_err + 2, poff.as<int64_t>(), recs.as<uint64_t>(), T,
-                                  pedges.as<int64_t>(), nullptr, edges.as<int2>(), d_ecur, seg_cap));
-        note_launch();
+        if (jside) {
+            TCR_CUDA(cudaStreamWaitEvent(s, jside->ev[7], 0));  // all candidates written
+        } else {
+            TCR_CUDA(launch_dependent(k_join_sorted<false>, dim3(num_sms * 4), dim3(kThreads), 0, s,
+                                      big_list.as<int32_t>(), d_err + 3, poff.as<int64_t>(), recs.as<uint64_t>(), T,
+                                      pedges.as<int64_t>(), nullptr, edges.as<int2>(), d_ecur, seg_cap));
+            note_launch();
+            TCR_CUDA(launch_dependent(k_join_fallback<false>, dim3(num_sms * 2), dim3(kThreads), 0, s,
+                                      fb_list.as<int32_t>(), d_err + 2, poff.as<int64_t>(), recs.as<uint64_t>(), T,
+                                      pedges.as<int64_t>(), nullptr, edges.as<int2>(), d_ecur, seg_cap));
+            note_launch();
+        }
         TCR_CUDA(launch_dependent(k_confirm, dim3(confirm_blocks_x(num_sms), kEdgeSegs), dim3(kThreads), 0, s,
                                   edges.as<int2>(), seg_cap, (const unsigned long long*)d_ecur, 1,
                                   (const Canon*)ucanon.as<Canon>(), weigh, d_err + 5));
