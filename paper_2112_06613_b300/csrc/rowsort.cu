@@ -366,8 +366,8 @@ __global__ void k_merge_runs(const int32_t* __restrict__ src, int32_t* __restric
 
 namespace {
 
-// The long classes listed in advance: the short-row kernel on s, 65..256 on
-// the first side stream, 257..512 then the block class on the second, all
+// The long classes listed in advance: 65..256 on the first side stream,
+// 257..512 then the block class on the second, the short-row kernel on s, all
 // started together; s waits for both side streams at the end.
 tcrnet_status sort_rows_listed(const int64_t* off, int32_t* cols, int64_t n, cudaStream_t s, int num_sms,
                                int64_t max_len, const SortClasses& pre, const SideStream* side, int32_t* huge_list,
@@ -378,10 +378,6 @@ tcrnet_status sort_rows_listed(const int64_t* off, int32_t* cols, int64_t n, cud
     TCR_CUDA(cudaEventRecord(side->ev[4], s));
     TCR_CUDA(cudaStreamWaitEvent(side->stream, side->ev[4], 0));
     TCR_CUDA(cudaStreamWaitEvent(side->stream2, side->ev[4], 0));
-    const int64_t blocks = std::min<int64_t>(ceil_div(n, 32 * kSortWarps), (int64_t)num_sms * 16);
-    k_sort_warp<<<(unsigned)blocks, kSortWarps * 32, 0, s>>>(off, cols, n, nullptr, nullptr, nullptr, nullptr,
-                                                               nullptr, nullptr);
-    TCR_LAUNCH_CHECK();
     if (run_wide) {
         k_sort_warp_wide<<<num_sms * 8, kSortWarps * 32, 0, side->stream>>>(off, cols, pre.wide, pre.counts);
         TCR_LAUNCH_CHECK();
@@ -396,6 +392,12 @@ tcrnet_status sort_rows_listed(const int64_t* off, int32_t* cols, int64_t n, cud
                                                                             huge_list, nhuge);
         TCR_LAUNCH_CHECK();
     }
+    // the short rows last: the long classes' kernels take longer, so they are
+    // queued first and this one fills the SMs they leave
+    const int64_t blocks = std::min<int64_t>(ceil_div(n, 32 * kSortWarps), (int64_t)num_sms * 16);
+    k_sort_warp<<<(unsigned)blocks, kSortWarps * 32, 0, s>>>(off, cols, n, nullptr, nullptr, nullptr, nullptr,
+                                                               nullptr, nullptr);
+    TCR_LAUNCH_CHECK();
     TCR_CUDA(cudaEventRecord(side->ev[5], side->stream));
     TCR_CUDA(cudaEventRecord(side->ev[7], side->stream2));
     TCR_CUDA(cudaStreamWaitEvent(s, side->ev[5], 0));
