@@ -76,10 +76,10 @@ OPS_INDEL_PER_WORD = 26
 # from one ncu capture of the current kernels (profiles/k_records_join_n800000.md,
 # profiles/k_sort_fill_expand_n800000.md); absent where no capture covers the phase.
 PHASE_TRAFFIC_N800000 = {
-    "records": 23.824e6 + 3.853e6 + 89.461e6 + 76.134e6,              # count, partition scan, scatter
-    "join": 79.977e6 + 3.672e6 + 1.274e6 + 0.049e6 + 0.016e6 + 32.084e6 + 0.017e6,  # windows, sorted, fallback, confirmation
-    "list_sort": 25.030e6 + 27.435e6 + 14.248e6 + 0.349e6,            # the four sort classes
-    "expand": 83.667e6 + 198.972e6,
+    "records": 23.825e6 + 3.853e6 + 89.438e6 + 80.330e6,              # count, partition scan, scatter
+    "join": 79.972e6 + 3.721e6 + 1.241e6 + 0.016e6 + 0.016e6 + 32.095e6 + 0.022e6,  # windows, sorted, fallback, confirmation
+    "list_sort": 25.032e6 + 27.446e6 + 14.255e6 + 0.349e6,            # the four sort classes
+    "expand": 83.399e6 + 198.697e6,
 }
 
 LEGS = ("peaks", "tile", "query", "e2e", "insert", "analytics", "lmax2", "batched", "serving", "cpu")
