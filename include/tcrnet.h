@@ -425,9 +425,9 @@ tcrnet_status tcrnet_probe_int_issue(int32_t kind, int32_t iters, uint32_t *d_ou
                                      void *stream, int64_t *ops_per_thread);
 
 /*
- * The per-row ordering step of the builds on its own (hot-path step a5: the
- * CSR rows are placed in arrival order, then each row is sorted; Methods
- * "Adjacency matrix" gives the matrix the rows stand for). Sorts every row
+ * The per-row ordering step of the builds on its own (the CSR rows are
+ * placed in arrival order, then each row is sorted; Methods "Adjacency
+ * matrix" gives the matrix the rows stand for). Sorts every row
  * segment d_cols[d_offsets[i] .. d_offsets[i+1]) ascending, in place, for
  * i < n: rows of up to 512 values in registers, up to 16,384 in shared
  * memory, longer ones by shared-memory chunks and stable pairwise merges.

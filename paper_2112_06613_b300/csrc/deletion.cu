@@ -1,4 +1,5 @@
-// Deletion-neighbourhood method (hot-path step a7).
+// Deletion-neighbourhood method: the network of Methods "TCR network" (edges at
+// Levenshtein distance <= l_max) without testing all pairs.
 //
 // The paper computes a Levenshtein DP for every pair of the adjacency matrix
 // (Methods "GPU-based network generation"); its cost grows with N^2 while the

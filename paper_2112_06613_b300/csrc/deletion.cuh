@@ -1,4 +1,5 @@
-// Deletion-neighbourhood method (hot-path step a7): declarations.
+// Deletion-neighbourhood method (the network of Methods "TCR network" without testing
+// all pairs): declarations.
 #pragma once
 
 #include "kernels.cuh"

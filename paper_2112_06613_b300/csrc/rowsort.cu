@@ -1,4 +1,5 @@
-// Per-row ordering of the CSR columns (last part of hot-path step a5).
+// Per-row ordering of the CSR columns: each row's neighbours ascending (the rows of the
+// adjacency matrix of Methods "Adjacency matrix", stored sparse).
 //
 // The write passes place a row's neighbours in arrival order (atomic cursors),
 // so each row segment is sorted afterwards; the result is then independent of
