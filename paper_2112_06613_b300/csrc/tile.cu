@@ -1,4 +1,5 @@
-// All-pairs tile kernel over length buckets (hot-path steps a3 count, a5 write).
+// All-pairs tile kernel over length buckets (Methods "GPU-based network generation":
+// every pair tested, the matrix in tiles; a count pass, then a write pass).
 //
 // The paper fills the adjacency matrix block by block on the GPU, one
 // Levenshtein dynamic programme per entry with an early abort (Methods
