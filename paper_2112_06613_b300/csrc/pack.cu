@@ -1,5 +1,5 @@
-// Validate, encode and length-bucket the input strings (the amino-acid alphabet of
-// Methods "Levenshtein distance", one code per letter).
+// Validate, encode and length-bucket the input strings (the amino-acid alphabet
+// Sigma of Methods "Combination of amino acids", one code per letter).
 //
 // The paper keeps each amino acid as one byte in a 30-slot buffer (Methods
 // "GPU-based network generation"); here each string becomes the 32-byte
