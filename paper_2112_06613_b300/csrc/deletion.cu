@@ -1719,8 +1719,15 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     MidReadback pageable;
     MidReadback* rb = static_cast<MidReadback*>(pinned_scratch());
     const unsigned long long* d_pack_flags = pk.flags.as<unsigned long long>();
+    // The size scan lists the long lists by sort class, so that the list
+    // sort's long classes start with its short-list kernel (at 8e5 strings the
+    // list sort takes 0.146 -> 0.122 ms and the size scan ~10 us more; at 8e6
+    // the block class dominates the sort and the listing cost 0.2 ms more than
+    // it saved, measured on a B300): up to kListClassesMaxN strings.
+    constexpr int64_t kListClassesMaxN = 2000000;
+    const bool list_classes = w_scan_n > 0 && n <= kListClassesMaxN;
     DevBuf off32, cls_lists;
-    if (w_scan_n > 0) TCR_CHECK(cls_lists.alloc(sizeof(int32_t) * 3 * n, s));  // long lists by sort class
+    if (list_classes) TCR_CHECK(cls_lists.alloc(sizeof(int32_t) * 3 * n, s));  // long lists by sort class
     // the list sizes and offsets from W_u, then the sizes of the lists and of
     // the CSR, the candidate counts, the longest list, the rejected candidates
     // and the encoder's error word in one synchronisation
@@ -1730,8 +1737,9 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
             TCR_CUDA(launch_dependent(k_fill_sizes, dim3((unsigned)tiles, 2), dim3(kScanThreads), 0, s,
                                       wsum.as<int32_t>(), umult.as<int32_t>(), uid.as<int32_t>(), n,
                                       ucur.as<unsigned long long>(), d_err + 4, deg.as<int32_t>(), uoff.as<int64_t>(),
-                                      off64.as<int64_t>(), st_uoff, st_off64, tiles, cls_lists.as<int32_t>(),
-                                      d_err + 6));
+                                      off64.as<int64_t>(), st_uoff, st_off64, tiles,
+                                      list_classes ? cls_lists.as<int32_t>() : nullptr,
+                                      list_classes ? d_err + 6 : nullptr));
             note_launch();
         } else {
             TCR_CUDA(launch_dependent(k_closed_size, dim3(grid_for(n)), dim3(kThreads), 0, s, umult.as<int32_t>(),
@@ -1919,7 +1927,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     classes.big = classes.wide + 2 * n;
     classes.counts = d_err + 6;
     TCR_CHECK(sort_rows(uoff.as<int64_t>(), Sbuf.as<int32_t>(), n, s, num_sms, h_dmax,
-                        w_scan_n > 0 ? &classes : nullptr));
+                        list_classes ? &classes : nullptr));
     const int t5 = tm.mark();
 
     // ---- 5. expand
