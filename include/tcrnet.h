@@ -269,7 +269,7 @@ tcrnet_status tcrnet_query(tcrnet_handle h, const char *const *queries, int64_t 
  * build (l_max = 1) merges the new strings into its network and query index
  * (the new strings' closed neighbourhoods from a query of the grown index, old
  * rows grown at their ends) where that is faster than a rebuild, by a rule
- * measured on a B300: from 7e5 resident strings for inserts of up to n/128,
+ * measured on a B300: from 7e5 resident strings for inserts of up to n/2048,
  * from 1.5e6 for inserts of up to n/32; other inserts rebuild the grown
  * repertoire (options.insert_rebuild forces either way). Both give the network
  * of a fresh build of the concatenation. On failure

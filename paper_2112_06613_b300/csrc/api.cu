@@ -846,12 +846,13 @@ constexpr int64_t kMergeMaxPartitionFill = 48;
 // and runs about 60 small steps (~0.5 ms whatever the size); a rebuild grows
 // faster than linearly with the repertoire. Measured on a B300 (synthetic
 // repertoires, l_max = 1, copy-on-write inserts): rebuilds win below ~7e5
-// resident strings (3e5: 0.39 against 0.59 ms), merges of up to 1/128 win from
-// there (8e5 and 1,000 new strings: 0.80 against 0.83 ms), and from 1.5e6
-// merges of up to 1/32 (2e6 and 62,500 new strings: 1.94 against 2.80 ms).
+// resident strings (3e5: 0.39 against 0.59 ms), merges of a few hundred
+// strings win from there (8e5: 100 new strings 0.78 against 0.80 ms, 1,000
+// new strings 0.83 against 0.82 ms), and from 1.5e6 merges of up to 1/32 (2e6
+// and 62,500 new strings: 1.94 against 2.80 ms).
 bool merge_is_faster(int64_t n_old, int64_t m) {
     if (n_old >= 1500000) return m * 32 <= n_old;
-    if (n_old >= 700000) return m * 128 <= n_old;
+    if (n_old >= 700000) return m * 2048 <= n_old;
     return false;
 }
 
