@@ -286,6 +286,26 @@ def test_deletion_two_pass_join_with_rejected_candidates():
     assert_csr_equal(off, cols, ro, rc, "dense unique graph, 2-bit record hashes")
 
 
+@pytest.mark.parametrize("bits", [32, 3])
+def test_deletion_two_pass_join_with_multi_tile_scans(bits):
+    """Every string of 1..3 letters (8,420 strings, more than one scan tile):
+    the one-pass edge buffer overflows, so the second join pass runs and the
+    size scans (look-back chains, list cursors, lists of the long sort classes)
+    run a second time on the complete weights. bits = 3 adds rejected
+    candidates (3-bit record hashes)."""
+    letters = list(ALPHABET)
+    strs = letters + [a + b for a in letters for b in letters]
+    strs += [a + b + c for a in letters for b in letters for c in letters]
+    rep = from_strings(strs)
+    off, cols, deg, st = gpu_csr(rep, 1, "deletion", record_hash_bits=bits)
+    assert st["two_pass_join"] == 1
+    if bits < 32:
+        assert st["rejected_candidates"] > 0
+    ro, rc, _ = oracle_csr(rep, 1)
+    assert_csr_equal(off, cols, ro, rc, f"strings of 1..3 letters, {bits}-bit record hashes")
+    check_invariants(off, cols, deg, rep.n)
+
+
 def test_deletion_counts_distinct_strings():
     rep = generate_config1(30_000, seed=12)
     _, _, _, st = gpu_csr(rep, 1, "deletion")
