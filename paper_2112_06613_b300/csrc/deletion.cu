@@ -1257,7 +1257,7 @@ k_closed_edges(const int2* __restrict__ edges, int64_t seg_cap, const unsigned l
                const int32_t* __restrict__ umult,
                const int64_t* __restrict__ mem_off, const int32_t* __restrict__ members,
                unsigned long long* __restrict__ ucur, int32_t* __restrict__ S, int64_t SD, int* __restrict__ err) {
-    constexpr int kShort = 4;
+    constexpr int kShort = 8;  // (4: list fill 0.102 ms at 8e5; 8: 0.099; 16: 0.100)
     const int lane = threadIdx.x & 31;
     // grid.y = edge segment; t = direction-expanded index inside the segment
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
