@@ -283,6 +283,32 @@ __global__ void k_dedup_insert(const Canon* __restrict__ canon, const uint8_t* _
     slot_of[i] = -1;
 }
 
+// Every array of a build that starts at a fixed value, set in one launch before
+// the dedup (in place of five memsets, four of them between the dedup and the
+// kernels after it): the counter block, the dedup table (-1), the
+// multiplicities and weights (0) and, for the l_max = 1 join, the partition
+// counts (0).
+__global__ void k_build_clear(unsigned long long* __restrict__ zeroed, int64_t zwords, int32_t* __restrict__ table,
+                              int64_t S, int32_t* __restrict__ umult, int32_t* __restrict__ wsum, int64_t n,
+                              int32_t* __restrict__ pcnt, int64_t P) {
+    const int64_t total = zwords + S + 2 * n + P;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t k = t;
+        if (k < zwords) {
+            zeroed[k] = 0ull;
+        } else if ((k -= zwords) < S) {
+            table[k] = -1;
+        } else if ((k -= S) < n) {
+            umult[k] = 0;
+        } else if ((k -= n) < n) {
+            wsum[k] = 0;
+        } else {
+            pcnt[k - n] = 0;  // k - n < P
+        }
+    }
+}
+
 // Distinct-string id of every node and the multiplicities m_u.
 __global__ void k_uid(const int32_t* __restrict__ slot_of, const int32_t* __restrict__ slot_u, int64_t n,
                       int32_t* __restrict__ uid, int32_t* __restrict__ umult) {
@@ -1493,8 +1519,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     const int64_t w_fixed = (kEdgeSegs + 1) + 1 + 5;
     DevBuf zeroed;
     TCR_CHECK(zeroed.alloc(sizeof(unsigned long long) * (w_fixed + 3 * w_scan_n + w_scan_p), s));
-    TCR_CUDA(cudaMemsetAsync(zeroed.as<void>(), 0, zeroed.bytes(), s));
-    unsigned long long* d_ecur = zeroed.as<unsigned long long>();
+    unsigned long long* d_ecur = zeroed.as<unsigned long long>();  // cleared by k_build_clear
     unsigned long long* d_ucount = d_ecur + (kEdgeSegs + 1);
     int* d_err = reinterpret_cast<int*>(d_ucount + 1);
     unsigned long long* st_members = d_ucount + 6;  // scan status words, one slice per scan
@@ -1513,20 +1538,30 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     TCR_CHECK(table.alloc(sizeof(int32_t) * S, s));
     TCR_CHECK(slot_of.alloc(sizeof(int32_t) * n, s));
     TCR_CHECK(slot_u.alloc(sizeof(int32_t) * S, s));
-    TCR_CUDA(cudaMemsetAsync(table.as<void>(), 0xff, sizeof(int32_t) * S, s));
     const int64_t* d_U = reinterpret_cast<const int64_t*>(d_ucount);  // distinct strings, on the device
     DevBuf ucanon, ulen, umult, uid, mem_off, mcur, members, mpos;
     if (keep_index) TCR_CHECK(ucanon.alloc_owned(sizeof(Canon) * n, s));
     else TCR_CHECK(ucanon.alloc(sizeof(Canon) * n, s));
     TCR_CHECK(ulen.alloc(n, s));
+    if (keep_index) TCR_CHECK(umult.alloc_owned(sizeof(int32_t) * n, s));
+    else TCR_CHECK(umult.alloc(sizeof(int32_t) * n, s));
+    DevBuf pcnt, wsum;  // the join's counters
+    TCR_CHECK(wsum.alloc(sizeof(int32_t) * n, s));
+    if (join) TCR_CHECK(pcnt.alloc(sizeof(int32_t) * P, s));
+    {
+        const int64_t zwords = (int64_t)(zeroed.bytes() / sizeof(unsigned long long));
+        const int64_t total = zwords + S + 2 * n + (join ? P : 0);
+        k_build_clear<<<(unsigned)std::min<int64_t>(grid_for(total), (int64_t)num_sms * 8), kThreads, 0, s>>>(
+            zeroed.as<unsigned long long>(), zwords, table.as<int32_t>(), S, umult.as<int32_t>(), wsum.as<int32_t>(),
+            n, join ? pcnt.as<int32_t>() : nullptr, join ? P : 0);
+        TCR_LAUNCH_CHECK();
+    }
     k_dedup_insert<<<grid_for(n), kThreads, 0, s>>>(
         pk.canon_in.as<Canon>(), pk.lens.as<uint8_t>(), n, table.as<int32_t>(), (uint32_t)(S - 1),
         slot_of.as<int32_t>(), slot_u.as<int32_t>(), d_ucount, ucanon.as<Canon>(), ulen.as<uint8_t>(), d_err);
     TCR_LAUNCH_CHECK();
-    // the arrays the dedup does not use are allocated and cleared while it runs
-    // (the host's allocation calls were the GPU's wait before it)
-    if (keep_index) TCR_CHECK(umult.alloc_owned(sizeof(int32_t) * n, s));
-    else TCR_CHECK(umult.alloc(sizeof(int32_t) * n, s));
+    // the arrays the dedup does not use are allocated while it runs (the
+    // host's allocation calls were the GPU's wait before it)
     if (keep_index) TCR_CHECK(uid.alloc_owned(sizeof(int32_t) * n, s));
     else TCR_CHECK(uid.alloc(sizeof(int32_t) * n, s));
     if (keep_index) TCR_CHECK(mem_off.alloc_owned(sizeof(int64_t) * (n + 1), s));
@@ -1535,14 +1570,6 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     if (keep_index) TCR_CHECK(members.alloc_owned(sizeof(int32_t) * n, s));
     else TCR_CHECK(members.alloc(sizeof(int32_t) * n, s));
     TCR_CHECK(mpos.alloc(sizeof(int32_t) * n, s));
-    TCR_CUDA(cudaMemsetAsync(umult.as<void>(), 0, sizeof(int32_t) * n, s));  // ids >= U stay 0
-    DevBuf pcnt, wsum;  // the join's counters
-    TCR_CHECK(wsum.alloc(sizeof(int32_t) * n, s));
-    TCR_CUDA(cudaMemsetAsync(wsum.as<void>(), 0, sizeof(int32_t) * n, s));
-    if (join) {
-        TCR_CHECK(pcnt.alloc(sizeof(int32_t) * P, s));
-        TCR_CUDA(cudaMemsetAsync(pcnt.as<void>(), 0, sizeof(int32_t) * P, s));
-    }
     TCR_CUDA(launch_dependent(k_uid, dim3(grid_for(n)), dim3(kThreads), 0, s, slot_of.as<int32_t>(),
                               slot_u.as<int32_t>(), n, uid.as<int32_t>(), umult.as<int32_t>()));
     note_launch();
