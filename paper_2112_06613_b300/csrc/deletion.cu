@@ -1513,16 +1513,17 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     // distinct-string count, the device counters ([0] dedup error, [1] fill
     // error, [2] partitions for the quadratic join, [3] partitions for the
     // sorted join, [4] largest closed list, [5] rejected candidates, [6..8]
-    // lists of the long sort classes), and the status words of the build's scans.
+    // lists of the long sort classes, [10..13] the list sort's own counters),
+    // and the status words of the build's scans.
     const int64_t w_scan_n = scan_status_words(n);
     const int64_t w_scan_p = join ? scan_status_words(P) : 0;
-    const int64_t w_fixed = (kEdgeSegs + 1) + 1 + 5;
+    const int64_t w_fixed = (kEdgeSegs + 1) + 1 + 7;
     DevBuf zeroed;
     TCR_CHECK(zeroed.alloc(sizeof(unsigned long long) * (w_fixed + 3 * w_scan_n + w_scan_p), s));
     unsigned long long* d_ecur = zeroed.as<unsigned long long>();  // cleared by k_build_clear
     unsigned long long* d_ucount = d_ecur + (kEdgeSegs + 1);
     int* d_err = reinterpret_cast<int*>(d_ucount + 1);
-    unsigned long long* st_members = d_ucount + 6;  // scan status words, one slice per scan
+    unsigned long long* st_members = d_ucount + 8;  // scan status words, one slice per scan
     unsigned long long* st_uoff = st_members + w_scan_n;
     unsigned long long* st_off64 = st_uoff + w_scan_n;
     unsigned long long* st_poff = st_off64 + w_scan_n;
@@ -1953,6 +1954,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     classes.mid = classes.wide + n;
     classes.big = classes.wide + 2 * n;
     classes.counts = d_err + 6;
+    classes.zeroed4 = d_err + 10;
     TCR_CHECK(sort_rows(uoff.as<int64_t>(), Sbuf.as<int32_t>(), n, s, num_sms, h_dmax,
                         list_classes ? &classes : nullptr));
     const int t5 = tm.mark();

@@ -136,6 +136,7 @@ struct SortClasses {
     const int32_t* mid = nullptr;
     const int32_t* big = nullptr;
     const int* counts = nullptr;  // [0] wide, [1] mid, [2] big
+    int* zeroed4 = nullptr;       // four ints, zero at the call (the sort's own counters; nullable)
 };
 // Sort every row segment cols[off[i] .. off[i+1]) ascending (repeats allowed).
 // max_len: an upper bound of the row lengths when the caller knows one (-1:

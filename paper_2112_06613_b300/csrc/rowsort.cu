@@ -415,13 +415,16 @@ tcrnet_status sort_rows(const int64_t* off, int32_t* cols, int64_t n, cudaStream
     // above kBlockCap, [3n, 4n) rows of 65..256; counts in the same order
     DevBuf lists, counts;
     TCR_CHECK(lists.alloc(sizeof(int32_t) * 4 * n, s));
-    TCR_CHECK(counts.alloc(sizeof(int) * 4, s));
-    TCR_CUDA(cudaMemsetAsync(counts.as<void>(), 0, sizeof(int) * 4, s));
+    int* cnt = pre ? pre->zeroed4 : nullptr;  // a caller's zeroed counters save a memset
+    if (!cnt) {
+        TCR_CHECK(counts.alloc(sizeof(int) * 4, s));
+        TCR_CUDA(cudaMemsetAsync(counts.as<void>(), 0, sizeof(int) * 4, s));
+        cnt = counts.as<int>();
+    }
     int32_t* mid = lists.as<int32_t>();
     int32_t* big = mid + n;
     int32_t* huge_list = big + n;
     int32_t* wide = huge_list + n;
-    int* cnt = counts.as<int>();
     const bool known = max_len >= 0;  // a known bound skips the kernels of longer classes
     const bool run_mid = !known || max_len > kWideMax;
     const bool run_block = !known || max_len > 2 * kWideMax;
