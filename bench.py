@@ -76,10 +76,10 @@ OPS_INDEL_PER_WORD = 26
 # from one ncu capture of the current kernels (profiles/k_records_join_n800000.md,
 # profiles/k_sort_fill_expand_n800000.md); absent where no capture covers the phase.
 PHASE_TRAFFIC_N800000 = {
-    "records": 23.825e6 + 3.853e6 + 89.438e6 + 80.330e6,              # count, partition scan, scatter
-    "join": 79.972e6 + 3.721e6 + 1.241e6 + 0.016e6 + 0.016e6 + 32.095e6 + 0.022e6,  # windows, sorted, fallback, confirmation
-    "list_sort": 25.032e6 + 27.446e6 + 14.255e6 + 0.349e6,            # the four sort classes
-    "expand": 83.399e6 + 198.697e6,
+    "records": 23.824e6 + 3.853e6 + 89.421e6 + 74.904e6,              # count, partition scan, scatter
+    "join": 79.972e6 + 4.089e6 + 1.242e6 + 0.019e6 + 0.015e6 + 32.100e6 + 0.040e6,  # windows, sorted, fallback, confirmation
+    "list_sort": 25.039e6 + 27.430e6 + 14.242e6 + 0.350e6,            # the four sort classes
+    "expand": 83.515e6 + 198.961e6,
 }
 
 LEGS = ("peaks", "tile", "query", "e2e", "insert", "analytics", "lmax2", "batched", "serving", "cpu")
