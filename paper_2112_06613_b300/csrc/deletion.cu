@@ -1571,17 +1571,23 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
     if (keep_index) TCR_CHECK(members.alloc_owned(sizeof(int32_t) * n, s));
     else TCR_CHECK(members.alloc(sizeof(int32_t) * n, s));
     TCR_CHECK(mpos.alloc(sizeof(int32_t) * n, s));
-    TCR_CUDA(launch_dependent(k_uid, dim3(grid_for(n)), dim3(kThreads), 0, s, slot_of.as<int32_t>(),
-                              slot_u.as<int32_t>(), n, uid.as<int32_t>(), umult.as<int32_t>()));
-    note_launch();
-    // member lists M_u are first needed when the closed lists are filled: build
-    // them on the side stream while the records and the join run
+    // node ids, multiplicities and member lists M_u are first needed by the
+    // confirmation's weights and the closed lists: built on the side stream
+    // while the records and the join run (the records need only the distinct
+    // strings); s waits for them (ev[1]) before the confirmation
     const SideStream* side = leased_side_stream();
     cudaStream_t ms = s;
     if (side) {
         TCR_CUDA(cudaEventRecord(side->ev[0], s));
         TCR_CUDA(cudaStreamWaitEvent(side->stream, side->ev[0], 0));
         ms = side->stream;
+        k_uid<<<grid_for(n), kThreads, 0, ms>>>(slot_of.as<int32_t>(), slot_u.as<int32_t>(), n, uid.as<int32_t>(),
+                                                umult.as<int32_t>());
+        TCR_LAUNCH_CHECK();
+    } else {
+        TCR_CUDA(launch_dependent(k_uid, dim3(grid_for(n)), dim3(kThreads), 0, s, slot_of.as<int32_t>(),
+                                  slot_u.as<int32_t>(), n, uid.as<int32_t>(), umult.as<int32_t>()));
+        note_launch();
     }
     TCR_CHECK(scan_exclusive_i32_to_i64(umult.as<int32_t>(), mem_off.as<int64_t>(), n, ms, slice(st_members, w_scan_n)));
     TCR_CUDA(cudaMemsetAsync(mcur.as<void>(), 0, sizeof(int32_t) * n, ms));
@@ -1668,6 +1674,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
                                       pedges.as<int64_t>(), nullptr, edges.as<int2>(), d_ecur, seg_cap));
             note_launch();
         }
+        if (side) TCR_CUDA(cudaStreamWaitEvent(s, side->ev[1], 0));  // multiplicities for the weights
         TCR_CUDA(launch_dependent(k_confirm, dim3(confirm_blocks_x(num_sms), kEdgeSegs), dim3(kThreads), 0, s,
                                   edges.as<int2>(), seg_cap, (const unsigned long long*)d_ecur, 1,
                                   (const Canon*)ucanon.as<Canon>(), weigh, d_err + 5));
@@ -1732,6 +1739,7 @@ tcrnet_status deletion_build(const Packed& pk, int T, DeletionResult& out, cudaS
         E2_cap = std::max<int64_t>(NC, 1);
         TCR_CHECK(edges.alloc(sizeof(int2) * E2_cap, s));
         const unsigned vgrid = (unsigned)std::min<int64_t>(ceil_div(n, kVerifyWarps), (int64_t)num_sms * 32);
+        if (side) TCR_CUDA(cudaStreamWaitEvent(s, side->ev[1], 0));  // multiplicities for the weights
         k_cand_verify<<<vgrid, 32 * kVerifyWarps, 0, s>>>(coff.as<int64_t>(), ccols.as<int32_t>(), d_U, ucanon.as<Canon>(),
                                                  ulen.as<uint8_t>(), weigh, edges.as<int2>(), d_ecur + kEdgeSegs,
                                                  E2_cap, d_err + 1);
